@@ -1,0 +1,493 @@
+"""Pins of the CPU oracle against facts fixed outside it: exact arithmetic,
+brute force on tiny graphs, closed forms, the paper's worked example
+(Section 6), invariants of loading (Eq. 5) and finite differences.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_12911_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ----------------------------------------------------------------------------
+# fixed-point reductions
+# ----------------------------------------------------------------------------
+def _rne(fr: Fraction) -> int:
+    fl = math.floor(fr)
+    rem = fr - fl
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2 == 1):
+        return fl + 1
+    return fl
+
+
+def test_fx_rounding_matches_exact_rational():
+    rng = np.random.default_rng(1)
+    vals = list(rng.standard_normal(2000) * 10.0 ** rng.integers(-12, 18, 2000))
+    vals += [0.5 * 2.0 ** -32, 1.5 * 2.0 ** -32, 2.5 * 2.0 ** -32, -0.5 * 2.0 ** -32, 3.0, -7.25,
+             2.0 ** -40, 1e15 + 0.123, -(2.0 ** 60)]
+    for v in vals:
+        got, bad = oracle.to_fx(v)
+        assert bad == 0
+        assert got == _rne(Fraction(v) * (1 << 32)), v
+
+
+def test_fx_to_double_is_correctly_rounded():
+    rng = np.random.default_rng(2)
+    for _ in range(3000):
+        nbits = int(rng.integers(1, 126))
+        x = int(rng.integers(0, 1 << 62)) << max(nbits - 62, 0) | int(rng.integers(0, 1 << 30))
+        x &= (1 << nbits) - 1
+        if rng.random() < 0.5:
+            x = -x
+        want = float(Fraction(x, 1 << 32))   # Python rounds int/int correctly
+        assert oracle.fx_to_double(x) == want
+    # ties to even at the 53-bit boundary
+    x = ((1 << 53) + 1) << 40
+    assert oracle.fx_to_double(x) == float(Fraction(x, 1 << 32))
+
+
+# ----------------------------------------------------------------------------
+# BPR (Eq. 1) and the worked example (Section 6)
+# ----------------------------------------------------------------------------
+def _bpr_exact(c0, cap, flow, dt_h, a=Fraction(15, 100), b=4):
+    x = Fraction(flow) / (Fraction(cap) * Fraction(dt_h))
+    return Fraction(c0) * (1 + Fraction(a) * x ** b)
+
+
+def test_bpr_hand_values_and_quantisation():
+    net = synth.chain_network([10.0, 20.0, 0.02, 7.0], [800.0, 1800.0, 100.0, 50.0])
+    g = oracle.OracleGraph(net)
+    flow = np.array([200.0, 0.0, 3.0, 1e-9])
+    q, cost, rc = oracle.bpr(g, flow, 900.0)
+    assert rc == 0
+    for a in range(4):
+        want = _bpr_exact(int(net.fftime_q[a]), net.capacity[a], flow[a], Fraction(1, 4))
+        assert abs(cost[a] / 0.01 - float(want)) <= 1e-12 * float(want)
+        assert q[a] == max(1, math.floor(want + Fraction(1, 2)))
+    # NaN flow is reported
+    _, _, rc = oracle.bpr(g, np.array([np.nan, 0, 0, 0.0]), 900.0)
+    assert rc == oracle.ENONFINITE
+
+
+def _worked():
+    with open(os.path.join(HERE, "golden", "worked_example.json")) as fh:
+        ex = json.load(fh)
+    ff = [ex["links"][k][0] * 60.0 for k in ("l12", "l23", "l34", "l45")]
+    cap = [float(ex["links"][k][1]) for k in ("l12", "l23", "l34", "l45")]
+    return ex, synth.chain_network(ff, cap)
+
+
+def _od(roots, items):
+    roots = np.array(roots, dtype=np.int32)
+    ri = np.array([i[0] for i in items], dtype=np.int32)
+    src = np.array([i[1] for i in items], dtype=np.int32)
+    amt = np.array([int(round(i[2] * (1 << 32))) for i in items], dtype=np.int64)
+    return synth.Demand(roots, ri, src, amt)
+
+
+def test_worked_example_bpr_values():
+    ex, net = _worked()
+    g = oracle.OracleGraph(net)
+    # t1: 175 v/h for 15 min = 43.75 trips on l23; t2: 225 v/h = 56.25 trips on l34
+    q, cost, _ = oracle.bpr(g, np.array([0.0, 43.75, 56.25, 0.0]), 900.0)
+    l23, l34 = cost[1] / 60.0, cost[2] / 60.0
+    assert abs(l23 - 6.389) < 5e-4 and abs(l23 - ex["printed"]["l23_t1_minutes"]) < 0.1
+    assert abs(l34 - 12.4027) < 5e-4 and abs(l34 - ex["printed"]["l34_t2_minutes"]) < 0.1
+
+
+def test_worked_example_qdta_day():
+    """QDTA over four 15-minute periods: d14 is truncated at node 3 in t1
+    (node 2 reached at ~10.9 min, node 3 at ~17.3 min > 15) and finishes in
+    t2 together with d35; l45 carries only d35's trips."""
+    ex, net = _worked()
+    g = oracle.OracleGraph(net)
+    zones = np.array([3, 4], dtype=np.int32)   # paper nodes 4 and 5
+    d = [_od(zones, [(0, 0, 175 * 0.25)]), _od(zones, [(1, 2, 50 * 0.25)]),
+         _od(zones, []), _od(zones, [])]
+    flows, stats, nitems, rn, rc = oracle.run_day(g, zones, d, 900.0,
+                                                  oracle.make_params(oracle.STEP_SWEEP8,
+                                                                     oracle.STOP_REL_GAP, 50))
+    assert rc == 0 and rn == 0
+    assert ex["printed"]["residual_node_t1"] == 3
+    np.testing.assert_array_equal(flows[0], [43.75, 43.75, 0.0, 0.0])
+    np.testing.assert_array_equal(flows[1], [0.0, 0.0, 56.25, 12.5])
+    np.testing.assert_array_equal(flows[2], 0.0)
+    assert list(nitems) == [1, 2, 0, 0]      # residual 3->4 merged into t2
+
+
+def test_worked_example_sta():
+    """STA over the hour (no truncation): flows 175, 175, 225, 50 trips, i.e.
+    43.75/43.75/56.25/12.5 per 15 minutes (printed 44, 44, 57, 13)."""
+    ex, net = _worked()
+    g = oracle.OracleGraph(net)
+    zones = np.array([3, 4], dtype=np.int32)
+    od = oracle.OracleOD.of(_od(zones, [(0, 0, 175.0), (1, 2, 50.0)]))
+    f, st, rc = oracle.assign_interval(g, od, 3600.0,
+                                       oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_REL_GAP, 50))
+    assert rc == 0
+    np.testing.assert_array_equal(f, [175.0, 175.0, 225.0, 50.0])
+    p = ex["printed"]["sta_link_flows_vph"]
+    half_up = lambda v: math.floor(v + 0.5)   # the paper prints 12.5 as 13
+    assert half_up(f[0] / 4) == p["l12"] and half_up(f[1] / 4) == p["l23"] and half_up(f[3] / 4) == p["l45"]
+
+
+# ----------------------------------------------------------------------------
+# shortest paths against Floyd-Warshall and the smallest-id rule
+# ----------------------------------------------------------------------------
+def _floyd(net, q):
+    V = net.n_nodes
+    INF = np.iinfo(np.int64).max // 4
+    D = np.full((V, V), INF, dtype=np.int64)
+    np.fill_diagonal(D, 0)
+    for e in range(net.n_links):
+        a, b = net.tail[e], net.head[e]
+        D[a, b] = min(D[a, b], int(q[e]))
+    for k in range(V):
+        D = np.minimum(D, D[:, k:k + 1] + D[k:k + 1, :])
+    return D, INF
+
+
+@pytest.mark.parametrize("seed,equal", [(s, s % 3 == 0) for s in range(12)])
+def test_sssp_against_floyd_warshall(seed, equal):
+    rng = np.random.default_rng(seed)
+    V = int(rng.integers(2, 40))
+    net = synth.random_graph(V, int(rng.integers(0, 3 * V)), seed, max_q=5, equal_costs=equal)
+    g = oracle.OracleGraph(net)
+    q = net.fftime_q
+    D, INF = _floyd(net, q)
+    roots = np.arange(V, dtype=np.int32)
+    for direction in (oracle.DIR_TO_ROOT, oracle.DIR_FROM_ROOT):
+        parent, dist = oracle.sssp(g, q, roots, direction)
+        for r in range(V):
+            want = D[:, r] if direction == oracle.DIR_TO_ROOT else D[r, :]
+            np.testing.assert_array_equal(dist[r], np.where(want >= INF, oracle.DIST_INF, want))
+            for v in range(V):
+                if v == r:
+                    assert parent[r, v] == -1
+                    continue
+                # brute force: every link that starts (ends) some shortest path
+                if direction == oracle.DIR_TO_ROOT:
+                    ok = [e for e in range(net.n_links) if net.tail[e] == v
+                          and q[e] + D[net.head[e], r] == D[v, r]]
+                else:
+                    ok = [e for e in range(net.n_links) if net.head[e] == v
+                          and D[r, net.tail[e]] + q[e] == D[r, v]]
+                assert parent[r, v] == min(ok)
+
+
+# ----------------------------------------------------------------------------
+# loading: conservation (Eq. 5), the cost identity, the truncation rule (Eq. 2)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("dt_q", [np.iinfo(np.int64).max, 7, 15])
+def test_load_invariants(seed, dt_q):
+    rng = np.random.default_rng(100 + seed)
+    V = int(rng.integers(5, 30))
+    net = synth.random_graph(V, 2 * V, seed, max_q=6, equal_costs=(seed == 0))
+    g = oracle.OracleGraph(net)
+    dem = synth.random_demand(net, min(4, V), 40, seed, fractional=(seed % 2 == 1))
+    od = oracle.OracleOD.of(dem)
+    q = net.fftime_q
+    D, INF = _floyd(net, q)
+    parent, dist = oracle.sssp(g, q, dem.roots)
+    flow, stop, rc = oracle.load(g, q, parent, od, dt_q)
+    assert rc == 0
+    big = [int(x) for x in dem.amount_fx]
+    # identity: sum_a q_a g_a = sum_items amount * (elapsed at stop node)
+    lhs = sum(int(q[e]) * int(flow[e]) for e in range(net.n_links))
+    rhs = 0
+    for k in range(dem.n_items):
+        p, z, s = dem.src[k], dem.roots[dem.root_idx[k]], stop[k]
+        rhs += big[k] * int(D[p, z] - D[s, z])
+        # truncation: the stop node is reached at >= dt, its predecessor before dt
+        el = D[p, z] - D[s, z]
+        if s != z:
+            assert el >= dt_q
+        if dt_q == np.iinfo(np.int64).max:
+            assert s == z
+    assert lhs == rhs
+    # conservation at every node: inflow - outflow = arrivals/stops - departures
+    bal = np.zeros(V, dtype=object)
+    for e in range(net.n_links):
+        bal[net.head[e]] += int(flow[e])
+        bal[net.tail[e]] -= int(flow[e])
+    want = np.zeros(V, dtype=object)
+    for k in range(dem.n_items):
+        if stop[k] != dem.src[k]:
+            want[stop[k]] += big[k]
+            want[dem.src[k]] -= big[k]
+    assert list(bal) == list(want)
+
+
+def test_truncation_stops_at_first_node_reaching_dt():
+    # chain 0->1->2->3 with link times 5, 5, 5; dt = 10: node 2 is reached at
+    # exactly 10 and counts as reached, so links 0 and 1 are loaded.
+    net = synth.chain_network([0.05, 0.05, 0.05], [100.0, 100.0, 100.0])
+    g = oracle.OracleGraph(net)
+    q = net.fftime_q
+    od = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32),
+                         np.array([0], np.int32), np.array([1 << 32], np.int64))
+    parent, _ = oracle.sssp(g, q, od.roots)
+    for dt, wflow, wstop in [(10, [1, 1, 0], 2), (11, [1, 1, 1], 3), (15, [1, 1, 1], 3),
+                             (1, [1, 0, 0], 1), (0, [0, 0, 0], 0)]:
+        flow, stop, rc = oracle.load(g, q, parent, od, dt)
+        assert list(flow >> 32) == wflow and stop[0] == wstop
+
+
+# ----------------------------------------------------------------------------
+# Beckmann objective (Eq. 6) and its slope against quadrature
+# ----------------------------------------------------------------------------
+def test_objective_and_slope_against_quadrature():
+    from scipy.integrate import quad
+    rng = np.random.default_rng(5)
+    net = synth.random_graph(8, 10, 5)
+    g = oracle.OracleGraph(net)
+    L = net.n_links
+    dt_s = 900.0
+    f = rng.uniform(0, 300, L)
+    gfx = (rng.uniform(0, 300, L) * (1 << 32)).astype(np.int64)
+    gd = gfx.astype(np.float64) / (1 << 32)
+
+    def c(a, t):
+        return net.fftime_q[a] * (1 + 0.15 * (t / (net.capacity[a] * 0.25)) ** 4)
+
+    want = sum(quad(lambda s, a=a: c(a, s), 0, f[a], epsabs=0, epsrel=1e-13)[0] for a in range(L))
+    assert abs(oracle.objective(g, f, dt_s) - want) <= 1e-10 * want
+    for alpha in (0.0, 0.3, 1.0):
+        t = f + alpha * (gd - f)
+        want_slope = sum((gd[a] - f[a]) * c(a, t[a]) for a in range(L))
+        scale = sum(abs(gd[a] - f[a]) * c(a, t[a]) for a in range(L))
+        assert abs(oracle.slope(g, f, gfx, dt_s, alpha) - want_slope) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("mode", [oracle.STEP_PAPER_QN3, oracle.STEP_SWEEP8, oracle.STEP_EXACT])
+def test_line_search_against_dense_grid(mode):
+    from scipy.integrate import quad
+    rng = np.random.default_rng(11)
+    net = synth.random_graph(10, 15, 3)
+    g = oracle.OracleGraph(net)
+    L = net.n_links
+    f = rng.uniform(0, 400, L)
+    gfx = (rng.uniform(0, 400, L) * (1 << 32)).astype(np.int64)
+    gd = gfx / float(1 << 32)
+
+    def C(alpha):
+        t = f + alpha * (gd - f)
+        return sum(net.fftime_q[a] * (t[a] + 0.15 * net.capacity[a] * 0.25 / 5 *
+                                      (t[a] / (net.capacity[a] * 0.25)) ** 5) for a in range(L))
+
+    grid = np.linspace(0, 1, 20001)
+    vals = np.array([C(a) for a in grid])
+    best = grid[int(np.argmin(vals))]
+    alpha, passes, rc = oracle.line_search(g, f, gfx, 900.0, 1,
+                                           oracle.make_params(mode, oracle.STOP_NONE, 20))
+    assert rc == 0 and 0.0 <= alpha <= 1.0
+    assert abs(alpha - best) <= 2e-4
+    if mode == oracle.STEP_PAPER_QN3:
+        assert passes <= 19
+    # convexity of phi along the line
+    d = np.diff(vals)
+    assert np.all(np.diff(d) >= -1e-6 * np.abs(vals).max())
+
+
+# ----------------------------------------------------------------------------
+# equilibrium closed forms (Eq. 4 with strictly increasing costs)
+# ----------------------------------------------------------------------------
+def _two_links(ff1, ff2, cap1, cap2):
+    net = synth.Network(n_nodes=2, tail=np.array([0, 0], np.int32), head=np.array([1, 1], np.int32),
+                        fftime_q=np.array([ff1, ff2], np.int32),
+                        capacity=np.array([cap1, cap2], np.float64), length_m=np.zeros(2),
+                        link_class=np.zeros(2, np.int8), x=np.zeros(2), y=np.zeros(2))
+    return net
+
+
+def _solve(net, demand_trips, mode, dt_s=3600.0, it=400, tol=1e-7):
+    g = oracle.OracleGraph(net)
+    od = oracle.OracleOD(np.array([1], np.int32), np.array([0], np.int32), np.array([0], np.int32),
+                         np.array([int(demand_trips * (1 << 32))], np.int64))
+    return oracle.assign_interval(g, od, dt_s, oracle.make_params(mode, oracle.STOP_REL_GAP, it, tol))
+
+
+@pytest.mark.parametrize("mode", [oracle.STEP_SWEEP8, oracle.STEP_PAPER_QN3, oracle.STEP_EXACT])
+def test_two_identical_parallel_links_split_evenly(mode):
+    f, st, rc = _solve(_two_links(60000, 60000, 1000.0, 1000.0), 3000.0, mode)
+    assert rc >= 0
+    assert abs(f[0] - 1500.0) <= 1e-6 * 3000.0 and abs(f.sum() - 3000.0) < 1e-9
+
+
+def test_dominated_link_gets_nothing():
+    # link 2's free-flow time exceeds link 1's cost at full demand
+    net = _two_links(60000, 90000, 1000.0, 1000.0)
+    c1_full = 60000 * (1 + 0.15 * (1000 / 1000.0) ** 4)
+    assert 90000 > c1_full
+    for mode in (oracle.STEP_MSA, oracle.STEP_SWEEP8):
+        f, st, rc = _solve(net, 1000.0, mode, it=30)
+        assert f[1] == 0.0 and f[0] == 1000.0
+
+
+def test_asymmetric_two_links_equal_cost_root():
+    net = _two_links(60000, 72000, 1200.0, 800.0)
+    D = 2500.0
+
+    def diff(x):   # c1(x) - c2(D - x) with hourly flows over one hour
+        return (60000 * (1 + 0.15 * (x / 1200.0) ** 4)) - (72000 * (1 + 0.15 * ((D - x) / 800.0) ** 4))
+
+    lo, hi = 0.0, D
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if diff(mid) < 0 else (lo, mid)
+    x_star = 0.5 * (lo + hi)
+    for mode in (oracle.STEP_SWEEP8, oracle.STEP_EXACT, oracle.STEP_PAPER_QN3):
+        f, st, rc = _solve(net, D, mode, it=2000, tol=1e-8)
+        # quantised link times (0.01 s on ~10-20 min) bound the reachable accuracy
+        assert abs(f[0] - x_star) <= 2e-3 * D, (mode, f, x_star)
+
+
+def test_braess_network_wardrop():
+    # 0->1 (variable), 0->2 (long fixed), 1->3 (long fixed), 2->3 (variable), 1->2 bridge
+    ff = [60000, 150000, 150000, 60000, 6000]
+    cap = [500.0, 1e9, 1e9, 500.0, 1e9]
+    tail = np.array([0, 0, 1, 1, 2], np.int32)
+    head = np.array([1, 2, 2, 3, 3], np.int32)
+    order_ff = {(0, 1): (60000, 500.0), (0, 2): (150000, 1e9), (1, 2): (6000, 1e9),
+                (1, 3): (150000, 1e9), (2, 3): (60000, 500.0)}
+    fq = np.array([order_ff[(int(a), int(b))][0] for a, b in zip(tail, head)], np.int32)
+    cp = np.array([order_ff[(int(a), int(b))][1] for a, b in zip(tail, head)], np.float64)
+    net = synth.Network(n_nodes=4, tail=tail, head=head, fftime_q=fq, capacity=cp,
+                        length_m=np.zeros(5), link_class=np.zeros(5, np.int8),
+                        x=np.zeros(4), y=np.zeros(4))
+    g = oracle.OracleGraph(net)
+    D = 1000.0
+    od = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([0], np.int32),
+                         np.array([int(D * (1 << 32))], np.int64))
+    f, st, rc = oracle.assign_interval(g, od, 3600.0,
+                                       oracle.make_params(oracle.STEP_EXACT, oracle.STOP_REL_GAP, 5000, 1e-7))
+    _, cost, _ = oracle.bpr(g, f, 3600.0)
+    link = {(int(a), int(b)): e for e, (a, b) in enumerate(zip(tail, head))}
+    paths = [[(0, 1), (1, 3)], [(0, 2), (2, 3)], [(0, 1), (1, 2), (2, 3)]]
+    pc = [sum(cost[link[x]] for x in p) for p in paths]
+    best = min(pc)
+    # flows on each path from link flows (the network is small enough to solve)
+    for p, c in zip(paths, pc):
+        used = min(f[link[x]] for x in p) > 1e-6 * D
+        if used:
+            assert c <= best * (1 + 2e-4)
+        else:
+            assert c >= best * (1 - 2e-4)
+    assert abs(f[link[(0, 1)]] + f[link[(0, 2)]] - D) < 1e-6
+
+
+# ----------------------------------------------------------------------------
+# step rules and the residual demand (Alg. 4)
+# ----------------------------------------------------------------------------
+def test_msa_is_the_running_mean_of_aon_flows(small_instance):
+    g = oracle.OracleGraph(small_instance.net)
+    od = oracle.OracleOD.of(small_instance.demand[0])
+    f, st, rc, tape = oracle.assign_interval(g, od, 900.0,
+                                             oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 6),
+                                             tape=True)
+    L = g.n_links
+    K = tape.K.value
+    assert K == 6 and st["aon_calls"] == 7
+    acc = np.zeros(L)
+    for j in range(K + 1):
+        q = tape.q[j * L:(j + 1) * L]
+        par, _ = oracle.sssp(g, q, od.roots, want_dist=False)
+        gfx, _, _ = oracle.load(g, q, par, od, 90000)
+        acc += gfx / float(1 << 32)
+    np.testing.assert_allclose(f, acc / (K + 1), rtol=1e-12, atol=1e-9)
+
+
+def test_residual_conserves_trips_and_matches_flows_without_truncation(small_instance):
+    g = oracle.OracleGraph(small_instance.net)
+    od = oracle.OracleOD.of(small_instance.demand[0])
+    p = oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_REL_GAP, 60, 1e-3)
+    for dt in (600.0, 1e9):
+        f, st, rc, tape = oracle.assign_interval(g, od, dt, p, tape=True)
+        h, (rs, rr, ra), rc2 = oracle.residual(g, od, dt, tape, f)
+        assert rc2 == 0
+        K = tape.K.value
+        total_in = int(od.amount_fx.sum())
+        if dt > 1e8:
+            assert ra.shape[0] == 0
+            np.testing.assert_allclose(h / float(1 << 32), f, rtol=1e-9, atol=1e-6)
+        else:
+            assert ra.shape[0] > 0
+            assert np.all(rs != small_instance.demand[0].roots[rr])
+            assert int(ra.sum()) <= total_in + (K + 1) * od.src.shape[0]
+            # balance of h at nodes that are neither roots nor origins: what
+            # flows in and does not flow out is exactly what stopped there
+            V = g.n_nodes
+            bal = np.zeros(V, dtype=np.int64)
+            np.add.at(bal, small_instance.net.head, h)
+            np.add.at(bal, small_instance.net.tail, -h)
+            stopped = np.zeros(V, dtype=np.int64)
+            np.add.at(stopped, rs, ra)
+            free = np.ones(V, dtype=bool)
+            free[od.roots] = False
+            free[od.src] = False
+            np.testing.assert_array_equal(bal[free], stopped[free])
+
+
+# ----------------------------------------------------------------------------
+# adjoint against central finite differences (trees held fixed)
+# ----------------------------------------------------------------------------
+def _small_grid_case(seed=4):
+    net = synth.grid_network(6, seed)
+    zones = synth.pick_zones(net, 6, seed)
+    trips = synth.gravity_fixed_pairs(net, zones, 900, 800.0)
+    dem = synth.demand_from_matrix(zones, trips)
+    return net, dem
+
+
+@pytest.mark.parametrize("mode", [oracle.STEP_EXACT, oracle.STEP_MSA])
+def test_adjoint_matches_finite_differences(mode):
+    net, dem = _small_grid_case()
+    g = oracle.OracleGraph(net)
+    od = oracle.OracleOD.of(dem)
+    dt = 300.0
+    p = oracle.make_params(mode, oracle.STOP_NONE, 8)
+    f, st, rc, tape = oracle.assign_interval(g, od, dt, p, tape=True)
+    rng = np.random.default_rng(0)
+    L = g.n_links
+    S = rng.choice(L, max(2, L // 4), replace=False)
+    y = f[S] * rng.lognormal(0, 0.3, S.shape[0])
+
+    def loss(ff):
+        return float(((ff[S] - y) ** 2).sum())
+
+    dLdf = np.zeros(L)
+    dLdf[S] = 2 * (f[S] - y)
+    dd, dc, rcb = oracle.backward(g, od, dt, mode, tape, dLdf)
+    assert rcb == 0
+    for k in rng.choice(dem.n_items, 8, replace=False):
+        h = 1e-3 * dem.amount_fx[k]
+        vals = []
+        for sgn in (1, -1):
+            amt = dem.amount_fx.copy()
+            amt[k] += int(sgn * h)
+            ff, _ = oracle.replay(g, oracle.OracleOD(dem.roots, dem.root_idx, dem.src, amt), dt, p, tape)
+            vals.append(loss(ff))
+        fd = (vals[0] - vals[1]) / (2 * int(h) / float(1 << 32))
+        assert abs(fd - dd[k]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(dd).max()), (k, fd, dd[k])
+    if mode == oracle.STEP_MSA:
+        assert np.all(dc == 0.0)
+    else:
+        for a in rng.choice(L, 8, replace=False):
+            hc = 1e-3 * net.capacity[a]
+            vals = []
+            for sgn in (1, -1):
+                cap = net.capacity.copy()
+                cap[a] += sgn * hc
+                g2 = oracle.OracleGraph(net, capacity=cap)
+                ff, _ = oracle.replay(g2, od, dt, p, tape)
+                vals.append(loss(ff))
+            fd = (vals[0] - vals[1]) / (2 * hc)
+            assert abs(fd - dc[a]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(dc).max()), (a, fd, dc[a])
