@@ -1,0 +1,265 @@
+/*
+ * qdta.h -- C ABI of libqdta, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of quasi-dynamic traffic assignment (QDTA) from
+ * Chan et al., "Quasi-Dynamic Traffic Assignment using High Performance
+ * Computing", arXiv 2104.12911.
+ *
+ * Units and formats used by every call:
+ *   - nodes 0..V-1; links 0..L-1 sorted by (tail, head); link id = position;
+ *   - link times are int32 counts of the graph's time quantum (e.g. 0.01 s),
+ *     at least 1; distances are int64 counts of the quantum;
+ *   - trip amounts and all-or-nothing link flows are int64 fixed point with
+ *     32 fractional bits (1 trip = 2^32);
+ *   - FW link flows are float64 trips in the interval; capacities float64
+ *     vehicles per hour;
+ *   - every sum over links (objective, slopes, gap) is the exact sum of the
+ *     per-link terms each rounded to nearest-even at 2^-32, so results do not
+ *     depend on reduction order (and match the CPU oracle bit for bit).
+ *
+ * Memory: arguments named *_host are host memory; every other array is
+ * device memory on the graph's device, read or written in stream order on
+ * `stream` (a cudaStream_t passed as void*, NULL = legacy default stream).
+ * The caller owns all arrays it passes.  A graph handle owns a device copy
+ * of the network plus a grow-only workspace and must be used from one host
+ * thread / one stream at a time.
+ *
+ * Errors: every call returns a status (QDTA_OK = 0; negative = error, the
+ * outputs are undefined; positive = QDTA_ENOTCONV, the outputs are valid but
+ * the tolerance was not met within max_iter).  qdta_last_error() returns a
+ * thread-local message describing the last failure.  No C++ exception
+ * crosses this interface.
+ */
+#ifndef QDTA_H
+#define QDTA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QDTA_OK 0
+#define QDTA_EINVAL (-1)     /* invalid argument or graph */
+#define QDTA_ENOMEM (-2)     /* device allocation failed */
+#define QDTA_ECUDA (-3)      /* CUDA runtime error */
+#define QDTA_ETIMEOUT (-4)   /* a bounded device wait or loop gave up */
+#define QDTA_ENONFINITE (-5) /* a NaN/inf flow, capacity or cost, or a term beyond 2^68 */
+#define QDTA_EUNREACH (-6)   /* a destination is unreachable from an origin */
+#define QDTA_EOVERFLOW (-7)  /* a distance exceeded the packed range (2^(64-ceil(log2(L+1)))) */
+#define QDTA_ENOTCONV 1      /* valid result, tolerance not met within max_iter */
+
+#define QDTA_TO_ROOT 0   /* dist/parent toward the root (destination trees, reverse graph) */
+#define QDTA_FROM_ROOT 1 /* dist/parent from the root (origin trees, forward graph) */
+
+#define QDTA_STEP_MSA 0       /* alpha_k = 1/(k+1) (method of successive averages) */
+#define QDTA_STEP_PAPER_QN3 1 /* quasi-Newton on three objective values per sweep (Alg. 8-9, Eq. 9) */
+#define QDTA_STEP_SWEEP8 2    /* bracketing on the exact slope at eight step sizes per sweep */
+#define QDTA_STEP_EXACT 3     /* Newton on the exact slope to |d alpha| < 1e-14 (used by the adjoint) */
+
+#define QDTA_STOP_NONE 0      /* run exactly max_iter steps */
+#define QDTA_STOP_PAPER_OBJ 1 /* |C(f) - C(f_new)| / C(f) < tol (Section 4, Converged) */
+#define QDTA_STOP_REL_GAP 2   /* (sum c f - sum c g) / sum c f <= tol */
+
+#define QDTA_SCHEDULE_PLAIN 0 /* host launch loop, one host sync per decision */
+#define QDTA_SCHEDULE_GRAPH 1 /* whole FW loop in one CUDA graph with device-side control */
+
+#define QDTA_DIST_INF INT64_MAX
+
+typedef struct qdta_graph qdta_graph;
+typedef struct qdta_tape qdta_tape;
+
+/* Network description (host arrays, copied by qdta_graph_create).
+ * Section 3.1: G = (V, A) with capacity C_a and free-flow time c_{0,a}. */
+typedef struct {
+  int32_t n_nodes;             /* V >= 1 */
+  int32_t n_links;             /* L >= 0, L < 2^24 */
+  const int32_t *tail;         /* [L] nondecreasing */
+  const int32_t *head;         /* [L], ties in tail sorted by head */
+  const int32_t *fftime_q;     /* [L] free-flow time in quanta, >= 1 */
+  const double *capacity_vph;  /* [L] > 0, finite */
+  double alpha;                /* BPR alpha (Eq. 1), >= 0 */
+  int32_t beta;                /* BPR beta (Eq. 1), integer in [1, 16] */
+  double quantum_s;            /* seconds per time quantum, > 0 */
+} qdta_graph_desc;
+
+/* Demand of one interval, grouped by destination root (device arrays).
+ * Item k carries amount_fx[k] trips from node src[k] to node roots[root_idx[k]]
+ * (d_{p,q}(i) of Section 3.1). */
+typedef struct {
+  int32_t n_roots;
+  const int32_t *roots;      /* [n_roots] destination nodes */
+  int64_t n_items;
+  const int32_t *root_idx;   /* [n_items] in [0, n_roots) */
+  const int32_t *src;        /* [n_items] origin nodes */
+  const int64_t *amount_fx;  /* [n_items] >= 0 */
+} qdta_od;
+
+typedef struct {
+  int32_t step;        /* QDTA_STEP_* */
+  int32_t stop;        /* QDTA_STOP_* */
+  int32_t max_iter;    /* FW steps after the initial all-or-nothing, >= 0 */
+  int32_t ls_max;      /* L of Alg. 8: at most ls_max - 1 quasi-Newton sweeps; sweep cap otherwise */
+  double tol;          /* T0 of the stop rule */
+  double ls_dx;        /* finite-difference step of Eq. 9 */
+  double ls_t1;        /* T1 of Alg. 8 (relative slope: |C'| < T1 |C|) */
+  double ls_t2;        /* T2 of Alg. 8 / bracket width of SWEEP8 */
+  int32_t schedule;    /* QDTA_SCHEDULE_* */
+  int32_t record_tape; /* qdta_assign_interval: keep what qdta_backward needs */
+} qdta_params;
+
+typedef struct {
+  int32_t iterations;  /* accepted FW steps */
+  int32_t aon_calls;   /* shortest-path batches (all-or-nothing assignments) run */
+  int32_t ls_passes;   /* link sweeps spent in line searches */
+  int32_t converged;   /* 1 if the stop rule was met */
+  double rel_gap;      /* last measured gap (relative objective change in PAPER_OBJ mode) */
+  double objective;    /* Beckmann objective of the returned flows (quanta x trips) */
+  int64_t n_items;     /* demand items solved (after merging residual demand) */
+} qdta_stats;
+
+/* Output buffer for residual demand (device arrays, caller-owned). */
+typedef struct {
+  int64_t capacity;    /* entries available */
+  int32_t *root_idx;   /* [capacity] */
+  int32_t *src;        /* [capacity] stop node s, the new origin */
+  int64_t *amount_fx;  /* [capacity] */
+  int64_t count;       /* written by the library (host field): entries produced */
+} qdta_residual;
+
+/* Per-kernel CUDA-event timings accumulated while profiling is enabled
+ * (plain schedule only; graph launches record nothing here). */
+typedef struct {
+  int64_t sssp_launches;
+  double sssp_ms;
+  int64_t sssp_roots;       /* roots solved by those launches */
+  int64_t load_launches;
+  double load_ms;
+  int64_t sweep_launches;
+  double sweep_ms;
+} qdta_profile;
+
+/* ---------------------------------------------------------------------- */
+
+/* Copy the network to `device` and build its forward/reverse adjacency.
+ * Section 3.1 (graph, c_0, C), Eq. 1 (alpha, beta).  Returns QDTA_EINVAL on
+ * unsorted links, ids out of range, fftime_q < 1, capacity <= 0 or not
+ * finite, beta outside [1, 16], L >= 2^24. */
+int qdta_graph_create(const qdta_graph_desc *desc, int device, qdta_graph **out);
+int qdta_graph_destroy(qdta_graph *g);
+
+/* Batched single-source shortest paths (the Get_shortest_path of Alg. 3 and
+ * Alg. 7, for all nodes at once).  For each root r and node v:
+ * TO_ROOT: dist = shortest time v -> roots[r]; parent = the smallest link id
+ * among the links leaving v that begin a shortest path to the root.
+ * FROM_ROOT: dist = shortest time roots[r] -> v; parent = the smallest link
+ * id among the links entering v that end a shortest path from the root.
+ * parent = -1 at the root and at unreachable nodes (dist = QDTA_DIST_INF).
+ * cost_q [L] int32 >= 1; roots [R]; parent_link [R*V] row-major by root;
+ * dist [R*V] or NULL.  QDTA_EOVERFLOW if a distance exceeds the packed range. */
+int qdta_sssp_batch(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R,
+                    int32_t direction, int32_t *parent_link, int64_t *dist, void *stream);
+
+/* All-or-nothing loading with route truncation (Alg. 3, Eq. 2, Eq. 5).
+ * For every item, walk src -> root along parent_link (destination trees of
+ * qdta_sssp_batch with QDTA_TO_ROOT, one row per od->roots entry), adding
+ * cost_q to the elapsed time; link a is loaded iff the elapsed time at its
+ * tail is < dt_q; the walk stops at the first node whose elapsed time is
+ * >= dt_q or at the root.  flow_fx [L] is ACCUMULATED (integer atomics, so
+ * the result is exact and order-free).  stop_node [n_items] (nullable)
+ * receives each item's stop node s.  dt_q = INT64_MAX disables truncation.
+ * QDTA_EUNREACH if some root is unreachable from its item's origin. */
+int qdta_load_aon(qdta_graph *g, const int32_t *cost_q, const int32_t *parent_link,
+                  const qdta_od *od, int64_t dt_q, int64_t *flow_fx, int32_t *stop_node,
+                  void *stream);
+
+/* BPR link costs (Eq. 1): c_a = c0_a (1 + alpha (f_a / (C_a dt_h))^beta) in
+ * quanta, with f_a trips in an interval of dt_s seconds (dt_h = dt_s/3600),
+ * evaluated in float64 without contraction, x^beta as x*x*...*x.
+ * cost_s [L] (nullable) = c_a * quantum_s; cost_q [L] = clamp(floor(c_a + 0.5),
+ * 1, 2^31-1).  QDTA_ENONFINITE on a NaN/inf flow. */
+int qdta_bpr_costs(qdta_graph *g, const double *flow, double dt_s, double *cost_s,
+                   int32_t *cost_q, void *stream);
+
+/* Step size of one FW iteration (Alg. 8 with Alg. 9 / Eq. 7-9, or the
+ * SWEEP8 / EXACT / MSA rules): minimise C(f + alpha (g - f)) over [0, 1]
+ * with C the Beckmann objective (Eq. 6).  flow [L] f, aon_fx [L] g in fixed
+ * point, fw_iter = k >= 1 (the k-th step; Alg. 8 starts from 2/(2+k-1)).
+ * alpha_out_host, passes_out_host (nullable) are host scalars; the call
+ * synchronises `stream`. */
+int qdta_line_search(qdta_graph *g, const double *flow, const int64_t *aon_fx, double dt_s,
+                     int32_t fw_iter, const qdta_params *p, double *alpha_out_host,
+                     int32_t *passes_out_host, void *stream);
+
+/* One interval's static assignment by Frank-Wolfe (Alg. 2 / Alg. 6):
+ * initial all-or-nothing at free flow, then repeat {BPR costs; batched
+ * shortest paths; truncated loading; step size; convex update} until the
+ * stop rule holds or max_iter steps were taken.  flow_out [L] receives f.
+ * In PAPER_OBJ mode the iterate before the step that met the test is
+ * returned (the pseudo-code breaks before h = h_new).  stats_host
+ * (nullable).  With p->record_tape, *tape_out receives a tape for
+ * qdta_backward (the od arrays must stay alive and unchanged until the tape
+ * is destroyed).  Synchronises `stream`.  An interval with no items returns
+ * zero flows, converged. */
+int qdta_assign_interval(qdta_graph *g, const qdta_od *od, double dt_s, const qdta_params *p,
+                         double *flow_out, qdta_stats *stats_host, qdta_tape **tape_out,
+                         void *stream);
+
+/* One independent network / interval of a batch (device arrays). */
+typedef struct {
+  qdta_graph *graph;
+  qdta_od od;
+  double dt_s;
+  double *flow_out;  /* [L of graph] */
+} qdta_instance;
+
+/* Many independent intervals (e.g. different networks) solved together:
+ * with QDTA_SCHEDULE_GRAPH all instances run as parallel branches of one
+ * CUDA graph launch; with QDTA_SCHEDULE_PLAIN one after another.  Every
+ * graph must live on the same device.  stats_host [n_inst] (nullable). */
+int qdta_assign_batch(const qdta_instance *inst, int32_t n_inst, const qdta_params *p,
+                      qdta_stats *stats_host, void *stream);
+
+/* A day of N intervals (Alg. 1 / Alg. 5): for each interval i,
+ * d(i) = d_o(i) + d_r(i) (items merged by (root, origin), amounts summed),
+ * FW solve, then Residual_demand (Alg. 4): every path of every accepted
+ * all-or-nothing step is re-truncated with the final costs, weighted by its
+ * step weight; the truncated link flows form h(i) and the remainders form
+ * d_r(i+1).  d_orig_host [N] is a HOST array of qdta_od whose arrays are on
+ * the device; all share one root (zone) list: d_orig_host[0].roots with
+ * n_roots entries, and root_idx index it.  resid_in (nullable, device items
+ * over the same roots) is added to the first interval, so that a day can be
+ * resumed from a saved residual.  flow_out [N*L] receives h(i) row by row
+ * (trips, float64).  stats_host [N] (nullable).  resid_out (nullable)
+ * receives the residual left after the last interval.  Synchronises. */
+int qdta_run_day(qdta_graph *g, const qdta_od *d_orig_host, int32_t N, double dt_s,
+                 const qdta_params *p, const qdta_od *resid_in, double *flow_out,
+                 qdta_stats *stats_host, qdta_residual *resid_out, void *stream);
+
+/* Adjoint of the interval solve recorded in `tape` (not in the paper): the
+ * FW iteration is unrolled with the shortest-path trees and truncation
+ * masks held fixed (they are piecewise constant in the inputs); trees are
+ * recomputed from the taped int32 link times, not stored.  MSA steps are
+ * constants; line-search steps are differentiated through their optimality
+ * condition C'(alpha) = 0 (zero derivative when alpha is clipped to 0 or 1).
+ * dL_dflow [L] = dL/df of the returned flows; dL_ddemand [n_items] receives
+ * dL/d(amount in trips) per item (a path-sum gather along the trees, the
+ * transpose of loading); dL_dcap [L] dL/dC (vehicles per hour).  Synchronises. */
+int qdta_backward(qdta_tape *tape, const double *dL_dflow, double *dL_ddemand, double *dL_dcap,
+                  void *stream);
+int qdta_tape_destroy(qdta_tape *tape);
+/* iterations recorded (K) and items of the taped interval */
+int qdta_tape_info(const qdta_tape *tape, int32_t *K_out_host, int64_t *n_items_out_host);
+
+/* Enable / read / reset per-kernel event timings (plain schedule). */
+int qdta_profile_enable(qdta_graph *g, int32_t on);
+int qdta_profile_read(qdta_graph *g, qdta_profile *out_host);
+
+/* Message of the last failing call on this host thread (never NULL). */
+const char *qdta_last_error(void);
+/* Library version string. */
+const char *qdta_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QDTA_H */

@@ -140,42 +140,51 @@ static double pow_n(double x, int n) {
   return p;
 }
 
-/* c_a(t) = c0 * (1 + alpha * (t / (C * dt_h))^beta), in quanta.
- * Flow t is trips in the interval, so t / dt_h is an hourly rate (Eq. 1 with
- * the worked example's hourly demand). */
-static double link_cost(const or_graph *g, int a, double t, double dt_h) {
+/* Per link, with cp = C_a * dt_h (capacity over the interval):
+ *   inv = 1 / cp,  x = t * inv  (t trips in the interval, so t / dt_h is an
+ *   hourly rate: Eq. 1 read with the worked example's hourly demand);
+ *   c_a(t)  = c0 * (1 + alpha * x^beta)                       (Eq. 1, quanta)
+ *   B_a(t)  = c0 * (t + kb * x^(beta+1)),  kb = alpha cp / (beta+1)
+ *           = integral_0^t c_a(s) ds                            (Eq. 6)
+ * Each line is one rounded operation in the order written. */
+static double inv_cap(const or_graph *g, int a, double dt_h) {
   double cp = g->capacity[a] * dt_h;
-  double x = t / cp;
+  return 1.0 / cp;
+}
+
+static double link_cost(const or_graph *g, int a, double t, double dt_h) {
+  double x = t * inv_cap(g, a, dt_h);
   double p = pow_n(x, g->beta);
   double w = g->alpha * p;
   double u = 1.0 + w;
   return (double)g->fftime_q[a] * u;
 }
 
-/* d c_a / d t */
+/* d c_a / d t = c0 alpha beta x^(beta-1) / cp */
 static double link_cost_dt(const or_graph *g, int a, double t, double dt_h) {
-  double cp = g->capacity[a] * dt_h;
-  double x = t / cp;
+  double inv = inv_cap(g, a, dt_h);
+  double x = t * inv;
   double p = g->beta > 1 ? pow_n(x, g->beta - 1) : 1.0;
-  return (double)g->fftime_q[a] * g->alpha * (double)g->beta * p / cp;
+  double w = (double)g->fftime_q[a] * g->alpha;
+  w = w * (double)g->beta;
+  w = w * p;
+  return w * inv;
 }
 
-/* d c_a / d C_a  (capacity in veh/h) */
+/* d c_a / d C_a  (capacity in veh/h) = -c0 alpha beta x^beta / C */
 static double link_cost_dcap(const or_graph *g, int a, double t, double dt_h) {
-  double cp = g->capacity[a] * dt_h;
-  double x = t / cp;
+  double x = t * inv_cap(g, a, dt_h);
   double p = pow_n(x, g->beta);
   return -(double)g->fftime_q[a] * g->alpha * (double)g->beta * p / g->capacity[a];
 }
 
-/* integral_0^t c_a(s) ds = c0 * (t + alpha * C dt_h / (beta+1) * (t / (C dt_h))^(beta+1)) */
 static double beckmann(const or_graph *g, int a, double t, double dt_h) {
   double cp = g->capacity[a] * dt_h;
-  double x = t / cp;
+  double kb = g->alpha * cp;
+  kb = kb / (double)(g->beta + 1);
+  double x = t * inv_cap(g, a, dt_h);
   double p = pow_n(x, g->beta + 1);
-  double w = g->alpha * cp;
-  w = w * p;
-  w = w / (double)(g->beta + 1);
+  double w = kb * p;
   double u = t + w;
   return (double)g->fftime_q[a] * u;
 }
@@ -415,12 +424,14 @@ static i128 dphi_sum(const or_graph *g, const double *f, const double *gd, doubl
   return s;
 }
 
-/* phi''(alpha) = sum_a (g_a - f_a)^2 c_a'(t_a), plain double sum */
-static double ddphi(const or_graph *g, const double *f, const double *gd, double alpha, double dt_h) {
-  double s = 0.0;
+/* phi''(alpha) = sum_a fx((g_a - f_a)^2 * c_a'(t_a)) */
+static i128 ddphi_sum(const or_graph *g, const double *f, const double *gd, double alpha,
+                      double dt_h, int *bad) {
+  i128 s = 0;
   for (int a = 0; a < g->n_links; a++) {
     double d = gd[a] - f[a];
-    s += d * d * link_cost_dt(g, a, step_flow(f[a], gd[a], alpha), dt_h);
+    double dd = d * d;
+    s += fx_of(dd * link_cost_dt(g, a, step_flow(f[a], gd[a], alpha), dt_h), bad);
   }
   return s;
 }
@@ -495,7 +506,7 @@ static double ls_exact(const or_graph *g, const double *f, const double *gd, dou
   double lo = 0.0, hi = 1.0, alpha = 0.5;
   for (int it = 0; it < 200; it++) {
     i128 D = dphi_sum(g, f, gd, alpha, dt_h, bad);
-    double H = ddphi(g, f, gd, alpha, dt_h);
+    double H = fx_to_double(ddphi_sum(g, f, gd, alpha, dt_h, bad));
     (*passes)++;
     if (D == 0) return alpha;
     if (D < 0) lo = alpha; else hi = alpha;
