@@ -1,0 +1,1081 @@
+// qdta_api.cu -- host runtime behind the C ABI of include/qdta.h: graph
+// handles, grow-only device workspaces, the plain (host loop) and graph
+// (CUDA graph with conditional WHILE nodes) schedules of the interval solve,
+// the day driver, the tape and the adjoint driver.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "qdta.h"
+#include "qdta_internal.cuh"
+
+using namespace qdta;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess) {                                                           \
+      int c_ = (e_ == cudaErrorMemoryAllocation) ? QDTA_ENOMEM : QDTA_ECUDA;           \
+      return fail(c_, "%s:%d %s: %s", __FILE__, __LINE__, #x, cudaGetErrorString(e_)); \
+    }                                                                                  \
+  } while (0)
+
+#define RC(x)              \
+  do {                     \
+    int r_ = (x);          \
+    if (r_ < 0) return r_; \
+  } while (0)
+
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ProfEvent {
+  int kind;  // 0 sssp, 1 load, 2 sweep
+  cudaEvent_t a, b;
+  long long roots;
+};
+
+struct qdta_graph {
+  int device = 0;
+  GraphDev d{};
+  std::vector<void *> owned;
+  unsigned *status = nullptr;
+  unsigned *status_h = nullptr;
+  void *ctl_h = nullptr;  // pinned mirror of Ctl
+  std::map<std::string, Buf> ws;
+  bool sssp_smem = false;
+  int sssp_bpsm = 1;
+  int prof_on = 0;
+  qdta_profile prof{};
+  unsigned long long *prof_roots = nullptr;  // device counter of roots solved
+  std::vector<ProfEvent> pending;
+  std::vector<cudaEvent_t> evpool;
+};
+
+struct qdta_tape {
+  qdta_graph *g = nullptr;
+  qdta_od od{};
+  double dt_s = 0.0;
+  int step = 0;
+  int K = 0;
+  int *q = nullptr;       // [(K+1) * L]
+  double *alpha = nullptr; // [K+1]
+  double *f = nullptr;    // [(K+1) * L]
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <class T>
+static int ws_get(qdta_graph *g, const std::string &name, size_t count, T **out) {
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = 16;
+  Buf &b = g->ws[name];
+  if (b.bytes < bytes) {
+    if (b.p) {
+      cudaDeviceSynchronize();
+      cudaFree(b.p);
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QDTA_ENOMEM, "device allocation of %zu bytes for '%s' failed: %s", bytes,
+                  name.c_str(), cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+  }
+  *out = reinterpret_cast<T *>(b.p);
+  return QDTA_OK;
+}
+
+static int status_reset(qdta_graph *g, cudaStream_t s) {
+  CK(cudaMemsetAsync(g->status, 0, sizeof(unsigned), s));
+  return QDTA_OK;
+}
+
+static int prof_harvest(qdta_graph *g);
+
+// synchronise and translate the device status word
+static int status_check(qdta_graph *g, cudaStream_t s) {
+  CK(cudaMemcpyAsync(g->status_h, g->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  prof_harvest(g);
+  unsigned st = *g->status_h;
+  if (st & ST_TIMEOUT) return fail(QDTA_ETIMEOUT, "a bounded device loop reached its limit");
+  if (st & ST_NONFINITE)
+    return fail(QDTA_ENONFINITE, "non-finite flow/cost or a sum term beyond 2^68");
+  if (st & ST_OVERFLOW) return fail(QDTA_EOVERFLOW, "a shortest distance exceeded the packed range");
+  if (st & ST_UNREACH) return fail(QDTA_EUNREACH, "a destination is unreachable from an origin");
+  if (st & ST_CAPACITY) return fail(QDTA_ENOMEM, "an internal item buffer was too small");
+  return QDTA_OK;
+}
+
+static cudaEvent_t ev_get(qdta_graph *g) {
+  if (!g->evpool.empty()) {
+    cudaEvent_t e = g->evpool.back();
+    g->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static void prof_begin(qdta_graph *g, cudaStream_t s, ProfEvent *pe, int kind, long long roots) {
+  if (!g->prof_on) return;
+  pe->kind = kind;
+  pe->roots = roots;
+  pe->a = ev_get(g);
+  pe->b = ev_get(g);
+  cudaEventRecord(pe->a, s);
+}
+
+static void prof_end(qdta_graph *g, cudaStream_t s, ProfEvent *pe) {
+  if (!g->prof_on) return;
+  cudaEventRecord(pe->b, s);
+  g->pending.push_back(*pe);
+}
+
+static int prof_harvest(qdta_graph *g) {
+  for (auto &pe : g->pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(pe.b);
+    cudaEventElapsedTime(&ms, pe.a, pe.b);
+    if (pe.kind == 0) { g->prof.sssp_launches++; g->prof.sssp_ms += ms; }
+    else if (pe.kind == 1) { g->prof.load_launches++; g->prof.load_ms += ms; }
+    else { g->prof.sweep_launches++; g->prof.sweep_ms += ms; }
+    g->evpool.push_back(pe.a);
+    g->evpool.push_back(pe.b);
+  }
+  g->pending.clear();
+  return QDTA_OK;
+}
+
+static int64_t dt_quanta(const qdta_graph *g, double dt_s) {
+  if (!(dt_s < 1e300)) return INT64_MAX;
+  return (int64_t)std::floor(dt_s / g->d.quantum_s + 0.5);
+}
+
+static int check_graph(const qdta_graph *g) {
+  if (!g) return fail(QDTA_EINVAL, "graph handle is NULL");
+  return QDTA_OK;
+}
+
+static int check_params(const qdta_params *p) {
+  if (!p) return fail(QDTA_EINVAL, "params is NULL");
+  if (p->step < 0 || p->step > 3) return fail(QDTA_EINVAL, "unknown step rule %d", p->step);
+  if (p->stop < 0 || p->stop > 2) return fail(QDTA_EINVAL, "unknown stop rule %d", p->stop);
+  if (p->max_iter < 0 || p->max_iter > 100000) return fail(QDTA_EINVAL, "max_iter out of range");
+  if (p->ls_max < 1 || p->ls_max > 1000) return fail(QDTA_EINVAL, "ls_max out of range");
+  if (!(p->ls_dx > 0.0) || !(p->ls_t1 >= 0.0) || !(p->ls_t2 > 0.0) || !(p->tol >= 0.0))
+    return fail(QDTA_EINVAL, "line-search tolerances must be positive");
+  if (p->schedule != QDTA_SCHEDULE_PLAIN && p->schedule != QDTA_SCHEDULE_GRAPH)
+    return fail(QDTA_EINVAL, "unknown schedule");
+  return QDTA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// graph handle
+// ---------------------------------------------------------------------------
+extern "C" const char *qdta_last_error(void) { return g_err.c_str(); }
+extern "C" const char *qdta_version(void) { return "qdta-gb300 0.1 (sm_103a)"; }
+
+template <class T>
+static int upload(qdta_graph *g, const T *host, size_t n, T **dev) {
+  void *p = nullptr;
+  CK(cudaMalloc(&p, (n ? n : 1) * sizeof(T)));
+  g->owned.push_back(p);
+  if (n) CK(cudaMemcpy(p, host, n * sizeof(T), cudaMemcpyHostToDevice));
+  *dev = reinterpret_cast<T *>(p);
+  return QDTA_OK;
+}
+
+extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_graph **out) {
+  if (!d || !out) return fail(QDTA_EINVAL, "NULL argument");
+  *out = nullptr;
+  const int V = d->n_nodes, L = d->n_links;
+  if (V < 1) return fail(QDTA_EINVAL, "n_nodes must be >= 1");
+  if (L < 0 || L >= (1 << 24)) return fail(QDTA_EINVAL, "n_links must be in [0, 2^24)");
+  if (L > 0 && (!d->tail || !d->head || !d->fftime_q || !d->capacity_vph))
+    return fail(QDTA_EINVAL, "link arrays must not be NULL");
+  if (!(d->alpha >= 0.0) || !std::isfinite(d->alpha)) return fail(QDTA_EINVAL, "alpha must be finite, >= 0");
+  if (d->beta < 1 || d->beta > 16) return fail(QDTA_EINVAL, "beta must be an integer in [1, 16]");
+  if (!(d->quantum_s > 0.0) || !std::isfinite(d->quantum_s)) return fail(QDTA_EINVAL, "quantum_s must be > 0");
+  for (int e = 0; e < L; ++e) {
+    if (d->tail[e] < 0 || d->tail[e] >= V || d->head[e] < 0 || d->head[e] >= V)
+      return fail(QDTA_EINVAL, "link %d has a node id out of range", e);
+    if (e > 0 && (d->tail[e] < d->tail[e - 1] ||
+                  (d->tail[e] == d->tail[e - 1] && d->head[e] < d->head[e - 1])))
+      return fail(QDTA_EINVAL, "links must be sorted by (tail, head); link %d is out of order", e);
+    if (d->fftime_q[e] < 1) return fail(QDTA_EINVAL, "link %d: fftime_q must be >= 1", e);
+    if (!(d->capacity_vph[e] > 0.0) || !std::isfinite(d->capacity_vph[e]))
+      return fail(QDTA_EINVAL, "link %d: capacity must be finite and > 0", e);
+  }
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(QDTA_EINVAL, "device %d out of range", device);
+  DevGuard guard(device);
+
+  std::vector<int> out_off(V + 1, 0), in_off(V + 1, 0), out_link(L), in_link(L);
+  for (int e = 0; e < L; ++e) { out_off[d->tail[e] + 1]++; in_off[d->head[e] + 1]++; }
+  for (int v = 0; v < V; ++v) { out_off[v + 1] += out_off[v]; in_off[v + 1] += in_off[v]; }
+  {
+    std::vector<int> po(out_off.begin(), out_off.end() - 1), pi(in_off.begin(), in_off.end() - 1);
+    for (int e = 0; e < L; ++e) { out_link[po[d->tail[e]]++] = e; in_link[pi[d->head[e]]++] = e; }
+  }
+  qdta_graph *g = new qdta_graph();
+  g->device = device;
+  GraphDev &gd = g->d;
+  gd.V = V;
+  gd.L = L;
+  int lb = 1;
+  while ((1ll << lb) - 1 < (long long)L + 1) ++lb;  // NOLINK = 2^lb - 1 > every link id
+  gd.LB = lb;
+  gd.beta = d->beta;
+  gd.alpha = d->alpha;
+  gd.quantum_s = d->quantum_s;
+  int rc = QDTA_OK;
+  int *tail, *head, *c0, *oo, *io, *ol, *il;
+  double *cap;
+  if ((rc = upload(g, d->tail, L, &tail)) || (rc = upload(g, d->head, L, &head)) ||
+      (rc = upload(g, d->fftime_q, L, &c0)) || (rc = upload(g, d->capacity_vph, L, &cap)) ||
+      (rc = upload(g, out_off.data(), V + 1, &oo)) || (rc = upload(g, in_off.data(), V + 1, &io)) ||
+      (rc = upload(g, out_link.data(), L, &ol)) || (rc = upload(g, in_link.data(), L, &il))) {
+    qdta_graph_destroy(g);
+    return rc;
+  }
+  gd.tail = tail; gd.head = head; gd.c0 = c0; gd.cap = cap;
+  gd.out_off = oo; gd.in_off = io; gd.out_link = ol; gd.in_link = il;
+  cudaDeviceGetAttribute(&gd.num_sms, cudaDevAttrMultiProcessorCount, device);
+  void *p = nullptr;
+  if (cudaMalloc(&p, 64) != cudaSuccess) { qdta_graph_destroy(g); return fail(QDTA_ENOMEM, "status word"); }
+  g->owned.push_back(p);
+  g->status = (unsigned *)p;
+  if (cudaMallocHost(&g->status_h, 64) != cudaSuccess ||
+      cudaMallocHost(&g->ctl_h, sizeof(Ctl)) != cudaSuccess) {
+    qdta_graph_destroy(g);
+    return fail(QDTA_ENOMEM, "pinned host words");
+  }
+  g->sssp_smem = V <= sssp_max_smem_nodes();
+  g->sssp_bpsm = sssp_blocks_per_sm(g->sssp_smem, V);
+  if (cudaGetLastError() != cudaSuccess) { qdta_graph_destroy(g); return fail(QDTA_ECUDA, "occupancy query failed"); }
+  *out = g;
+  return QDTA_OK;
+}
+
+extern "C" int qdta_graph_destroy(qdta_graph *g) {
+  if (!g) return QDTA_OK;
+  DevGuard guard(g->device);
+  cudaDeviceSynchronize();
+  for (void *p : g->owned) cudaFree(p);
+  for (auto &kv : g->ws) if (kv.second.p) cudaFree(kv.second.p);
+  for (auto &pe : g->pending) { cudaEventDestroy(pe.a); cudaEventDestroy(pe.b); }
+  for (auto e : g->evpool) cudaEventDestroy(e);
+  if (g->status_h) cudaFreeHost(g->status_h);
+  if (g->ctl_h) cudaFreeHost(g->ctl_h);
+  delete g;
+  return QDTA_OK;
+}
+
+extern "C" int qdta_profile_enable(qdta_graph *g, int32_t on) {
+  RC(check_graph(g));
+  DevGuard guard(g->device);
+  if (!g->prof_roots) {
+    void *p = nullptr;
+    CK(cudaMalloc(&p, 16));
+    g->owned.push_back(p);
+    g->prof_roots = (unsigned long long *)p;
+  }
+  CK(cudaMemset(g->prof_roots, 0, 16));
+  g->prof_on = on ? 1 : 0;
+  g->prof = qdta_profile{};
+  return QDTA_OK;
+}
+
+extern "C" int qdta_profile_read(qdta_graph *g, qdta_profile *out) {
+  RC(check_graph(g));
+  if (!out) return fail(QDTA_EINVAL, "out is NULL");
+  DevGuard guard(g->device);
+  CK(cudaDeviceSynchronize());
+  prof_harvest(g);
+  unsigned long long roots = 0;
+  if (g->prof_roots) CK(cudaMemcpy(&roots, g->prof_roots, 8, cudaMemcpyDeviceToHost));
+  g->prof.sssp_roots = (int64_t)roots;
+  *out = g->prof;
+  return QDTA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// shortest paths, loading, costs
+// ---------------------------------------------------------------------------
+static int sssp_grid(const qdta_graph *g, int R) {
+  long long cap = (long long)g->sssp_bpsm * g->d.num_sms;
+  long long n = R < cap ? R : cap;
+  return n < 1 ? 1 : (int)n;
+}
+
+static int sssp_work(qdta_graph *g, int grid, SsspWork *w) {
+  const size_t V = g->d.V;
+  w->slots = grid;
+  RC(ws_get(g, "sssp.adj", (size_t)g->d.L, &w->adj));
+  if (!g->sssp_smem) {
+    RC(ws_get(g, "sssp.state", (size_t)grid * V, &w->state));
+    RC(ws_get(g, "sssp.stamp", (size_t)grid * V, &w->stamp));
+    RC(ws_get(g, "sssp.queue", (size_t)grid * 2 * V, &w->queue));
+  } else {
+    w->state = nullptr; w->stamp = nullptr; w->queue = nullptr;
+  }
+  return QDTA_OK;
+}
+
+// one batch: pack adjacency for q, then SSSP over the roots
+static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots, int R_host,
+                    const int *R_dev, int R_cap, int *parent, const int *slot_dev, long long stride,
+                    long long *dist, cudaStream_t s, const int *skip_dev = nullptr) {
+  SsspWork w;
+  const int grid = sssp_grid(g, R_cap);
+  RC(sssp_work(g, grid, &w));
+  launch_pack_adj(g->d, direction, q, w.adj, s, skip_dev);
+  ProfEvent pe;
+  prof_begin(g, s, &pe, 0, R_host);
+  launch_sssp(g->d, direction, w.adj, roots, R_host, R_dev, grid, g->sssp_smem, w, parent, slot_dev,
+              stride, dist, g->status, s, skip_dev, g->prof_on ? g->prof_roots : nullptr);
+  prof_end(g, s, &pe);
+  return QDTA_OK;
+}
+
+extern "C" int qdta_sssp_batch(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R,
+                               int32_t direction, int32_t *parent_link, int64_t *dist, void *stream) {
+  RC(check_graph(g));
+  if (R < 0) return fail(QDTA_EINVAL, "R must be >= 0");
+  if (direction != QDTA_TO_ROOT && direction != QDTA_FROM_ROOT) return fail(QDTA_EINVAL, "bad direction");
+  if (R > 0 && (!cost_q || !roots || !parent_link)) return fail(QDTA_EINVAL, "NULL array");
+  if (R == 0) return QDTA_OK;
+  DevGuard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  RC(status_reset(g, s));
+  RC(run_sssp(g, direction, cost_q, roots, R, nullptr, R, parent_link, nullptr, 0,
+              (long long *)dist, s));
+  return status_check(g, s);
+}
+
+extern "C" int qdta_load_aon(qdta_graph *g, const int32_t *cost_q, const int32_t *parent_link,
+                             const qdta_od *od, int64_t dt_q, int64_t *flow_fx, int32_t *stop_node,
+                             void *stream) {
+  RC(check_graph(g));
+  if (!od) return fail(QDTA_EINVAL, "od is NULL");
+  if (od->n_items < 0 || od->n_roots < 0) return fail(QDTA_EINVAL, "negative sizes");
+  if (od->n_items == 0) return QDTA_OK;
+  if (!cost_q || !parent_link || !flow_fx || !od->roots || !od->root_idx || !od->src || !od->amount_fx)
+    return fail(QDTA_EINVAL, "NULL array");
+  if (dt_q < 0) return fail(QDTA_EINVAL, "dt_q must be >= 0");
+  DevGuard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  RC(status_reset(g, s));
+  int2 *hq;
+  RC(ws_get(g, "load.head_q", (size_t)g->d.L, &hq));
+  launch_pack_head_q(g->d, cost_q, hq, s);
+  ProfEvent pe;
+  prof_begin(g, s, &pe, 1, 0);
+  launch_load(g->d, hq, parent_link, nullptr, 0, nullptr, od->roots, od->n_items, nullptr, od->root_idx,
+              od->src, (const long long *)od->amount_fx, dt_q, (unsigned long long *)flow_fx,
+              stop_node, g->status, s);
+  prof_end(g, s, &pe);
+  return status_check(g, s);
+}
+
+extern "C" int qdta_bpr_costs(qdta_graph *g, const double *flow, double dt_s, double *cost_s,
+                              int32_t *cost_q, void *stream) {
+  RC(check_graph(g));
+  if (g->d.L > 0 && (!flow || !cost_q)) return fail(QDTA_EINVAL, "NULL array");
+  if (!(dt_s > 0.0)) return fail(QDTA_EINVAL, "dt_s must be > 0");
+  DevGuard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  RC(status_reset(g, s));
+  launch_bpr(g->d, flow, dt_s / 3600.0, cost_s, cost_q, g->status, s);
+  return status_check(g, s);
+}
+
+// ---------------------------------------------------------------------------
+// interval solver state shared by the schedules
+// ---------------------------------------------------------------------------
+struct Solver {
+  qdta_graph *g;
+  cudaStream_t s;
+  const qdta_params *p;
+  double dt_h;
+  long long dt_q;
+  // demand
+  const int *roots;        // SSSP roots
+  int R_host;              // roots when known on the host
+  const int *R_dev;        // or on the device
+  int R_cap;               // grid sizing
+  const int *root_slot;    // item root -> parent row (NULL: identity)
+  const int *item_roots;   // node of each root index (load walks end there)
+  long long n_host;
+  const long long *n_dev;
+  const int *root_idx, *src;
+  const long long *amount;
+  // link state
+  int *q;
+  unsigned long long *g_fx;
+  double *f;
+  LinkConst *kc;
+  int2 *head_q;
+  int *parent;
+  long long parent_stride;
+  int ring;
+  Ctl *ctl;
+  i128 *partials;
+  unsigned *counter;
+  int sgrid;
+  int *tape_q;
+  double *tape_alpha, *tape_f;
+  int tape_cap;
+};
+
+static int solver_alloc(Solver &S, const std::string &tag, int ring, bool tape_f) {
+  qdta_graph *g = S.g;
+  const size_t L = g->d.L;
+  RC(ws_get(g, tag + ".q", L, &S.q));
+  RC(ws_get(g, tag + ".gfx", L, &S.g_fx));
+  RC(ws_get(g, tag + ".kc", L, &S.kc));
+  RC(ws_get(g, tag + ".hq", L, &S.head_q));
+  S.parent_stride = (long long)S.R_cap * g->d.V;
+  S.ring = ring;
+  RC(ws_get(g, tag + ".parent", (size_t)S.parent_stride * ring, &S.parent));
+  RC(ws_get(g, tag + ".ctl", 1, &S.ctl));
+  S.sgrid = sweep_grid(g->d);
+  RC(ws_get(g, tag + ".partials", (size_t)S.sgrid * NSUM, &S.partials));
+  RC(ws_get(g, tag + ".counter", 4, &S.counter));
+  S.tape_cap = S.p->max_iter + 1;
+  RC(ws_get(g, tag + ".tape_q", (size_t)S.tape_cap * L, &S.tape_q));
+  RC(ws_get(g, tag + ".tape_alpha", (size_t)S.tape_cap, &S.tape_alpha));
+  S.tape_f = nullptr;
+  if (tape_f) RC(ws_get(g, tag + ".tape_f", (size_t)S.tape_cap * L, &S.tape_f));
+  CK(cudaMemsetAsync(S.counter, 0, 16, S.s));
+  return QDTA_OK;
+}
+
+// AON under the link times in S.q: trees into the parent slot, flows into g_fx
+static int seg_aon(Solver &S, const int *slot_dev) {
+  qdta_graph *g = S.g;
+  RC(run_sssp(g, QDTA_TO_ROOT, S.q, S.roots, S.R_host, S.R_dev, S.R_cap, S.parent, slot_dev,
+              S.parent_stride, nullptr, S.s));
+  launch_pack_head_q(g->d, S.q, S.head_q, S.s);
+  CK(cudaMemsetAsync(S.g_fx, 0, (size_t)g->d.L * 8, S.s));
+  ProfEvent pe;
+  prof_begin(g, S.s, &pe, 1, 0);
+  launch_load(g->d, S.head_q, S.parent, slot_dev, S.parent_stride, S.root_slot, S.item_roots, S.n_host,
+              S.n_dev, S.root_idx, S.src, S.amount, S.dt_q, S.g_fx, nullptr, g->status, S.s);
+  prof_end(g, S.s, &pe);
+  return QDTA_OK;
+}
+
+// ctl init + initial AON at free flow (f = 0 -> q = BPR(0) = c0)
+static int seg_init(Solver &S) {
+  qdta_graph *g = S.g;
+  const qdta_params *p = S.p;
+  launch_ctl_init(S.ctl, p->step, p->stop, p->max_iter, p->ls_max, p->tol, p->ls_dx, p->ls_t1, p->ls_t2,
+                  S.ring, S.n_host, S.n_dev, S.s);
+  launch_link_const(g->d, S.dt_h, S.kc, S.s);
+  CK(cudaMemsetAsync(S.f, 0, (size_t)g->d.L * 8, S.s));
+  launch_bpr(g->d, S.f, S.dt_h, nullptr, S.q, g->status, S.s);
+  RC(seg_aon(S, nullptr));
+  launch_flow_from_fx(g->d.L, S.g_fx, S.f, S.s);
+  launch_tape0(g->d, S.q, S.f, S.tape_q, S.tape_alpha, S.tape_f, S.s);
+  return QDTA_OK;
+}
+
+static int seg_iter_head(Solver &S, unsigned long long h_ls, int use_cond) {
+  qdta_graph *g = S.g;
+  launch_bpr(g->d, S.f, S.dt_h, nullptr, S.q, g->status, S.s);
+  RC(seg_aon(S, &S.ctl->tree_slot));
+  launch_ctl_begin(S.ctl, h_ls, use_cond, S.s);
+  return QDTA_OK;
+}
+
+static int seg_ls_body(Solver &S, unsigned long long h_ls, int use_cond) {
+  qdta_graph *g = S.g;
+  ProfEvent pe;
+  prof_begin(g, S.s, &pe, 2, 0);
+  launch_sweep(g->d, S.kc, S.f, (const long long *)S.g_fx, S.q, S.ctl, S.partials, S.counter, S.sgrid,
+               g->status, S.s);
+  prof_end(g, S.s, &pe);
+  launch_ctl_step(S.ctl, h_ls, use_cond, S.s);
+  return QDTA_OK;
+}
+
+static int seg_iter_tail(Solver &S, unsigned long long h_fw, int use_cond) {
+  qdta_graph *g = S.g;
+  launch_update(g->d, S.ctl, S.f, (const long long *)S.g_fx, S.s);
+  launch_tape_record(g->d, S.ctl, S.q, S.f, S.tape_q, S.tape_alpha, S.tape_f, S.tape_cap, S.s);
+  launch_ctl_end(S.ctl, h_fw, use_cond, S.s);
+  return QDTA_OK;
+}
+
+static int seg_finish(Solver &S) {
+  launch_objective(S.g->d, S.kc, S.f, S.ctl, S.partials, S.counter, S.sgrid, S.g->status, S.s);
+  return QDTA_OK;
+}
+
+static int read_ctl(Solver &S, Ctl *out) {
+  CK(cudaMemcpyAsync(out, S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, S.s));
+  CK(cudaStreamSynchronize(S.s));
+  return QDTA_OK;
+}
+
+// plain schedule: host loop, one synchronisation per decision
+static int fw_plain(Solver &S) {
+  Ctl *h = (Ctl *)S.g->ctl_h;
+  RC(seg_init(S));
+  RC(read_ctl(S, h));
+  while (h->fw_continue) {
+    RC(seg_iter_head(S, 0, 0));
+    RC(read_ctl(S, h));
+    while (h->need_sweep) {
+      RC(seg_ls_body(S, 0, 0));
+      RC(read_ctl(S, h));
+    }
+    RC(seg_iter_tail(S, 0, 0));
+    RC(read_ctl(S, h));
+  }
+  RC(seg_finish(S));
+  return QDTA_OK;
+}
+
+// capture `fn` into `graph` (an empty body graph owned by a node)
+template <class F>
+static int capture_into(cudaGraph_t graph, cudaStream_t cs, F fn) {
+  CK(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  int rc = fn();
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &out);
+  if (rc < 0) return rc;
+  CK(e);
+  return QDTA_OK;
+}
+
+static int add_while(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t ndeps, unsigned dflt,
+                     cudaGraphNode_t *node, cudaGraph_t *body, cudaGraphConditionalHandle *h) {
+  CK(cudaGraphConditionalHandleCreate(h, graph, dflt, cudaGraphCondAssignDefault));
+  // the parameter union has no default constructor: build it in zeroed storage
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  memset(raw, 0, sizeof raw);
+  cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = *h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  CK(cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &np));
+  *body = np.conditional.phGraph_out[0];
+  return QDTA_OK;
+}
+
+template <class F>
+static int add_captured_child(cudaGraph_t graph, const cudaGraphNode_t *deps, size_t ndeps,
+                              cudaStream_t cs, cudaGraphNode_t *node, F fn) {
+  cudaGraph_t child;
+  CK(cudaGraphCreate(&child, 0));
+  int rc = capture_into(child, cs, fn);
+  if (rc < 0) { cudaGraphDestroy(child); return rc; }
+  cudaError_t e = cudaGraphAddChildGraphNode(node, graph, deps, ndeps, child);
+  cudaGraphDestroy(child);
+  CK(e);
+  return QDTA_OK;
+}
+
+// FW loop body: head -> WHILE(line search) -> tail, as nodes of `body`
+static int build_fw_body(Solver &S, cudaGraph_t body, cudaGraphConditionalHandle h_fw, cudaStream_t cs) {
+  cudaGraphNode_t n_head, n_ls, n_tail;
+  cudaGraph_t ls_body;
+  cudaGraphConditionalHandle h_ls;
+  RC(add_while(body, nullptr, 0, 0, &n_ls, &ls_body, &h_ls));
+  // the LS condition is written by ctl_begin, so the head must precede it
+  cudaStream_t saved = S.s;
+  S.s = cs;
+  int rc = add_captured_child(body, nullptr, 0, cs, &n_head, [&] { return seg_iter_head(S, h_ls, 1); });
+  if (rc >= 0) rc = capture_into(ls_body, cs, [&] { return seg_ls_body(S, h_ls, 1); });
+  if (rc >= 0) rc = add_captured_child(body, &n_ls, 1, cs, &n_tail, [&] { return seg_iter_tail(S, h_fw, 1); });
+  S.s = saved;
+  RC(rc);
+  CK(cudaGraphAddDependencies(body, &n_head, &n_ls, nullptr, 1));
+  return QDTA_OK;
+}
+
+static int fw_graph(Solver &S) {
+  qdta_graph *g = S.g;
+  if (g->prof_on) return fail(QDTA_EINVAL, "profiling needs the plain schedule");
+  RC(seg_init(S));
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = QDTA_OK;
+  do {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) { rc = fail(QDTA_ECUDA, "cudaGraphCreate"); break; }
+    cudaGraphNode_t n_fw;
+    cudaGraph_t fw_body;
+    cudaGraphConditionalHandle h_fw;
+    if ((rc = add_while(graph, nullptr, 0, 1, &n_fw, &fw_body, &h_fw)) < 0) break;
+    if ((rc = build_fw_body(S, fw_body, h_fw, cs)) < 0) break;
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { rc = fail(QDTA_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e)); break; }
+    // run the loop only when there is something to iterate (the WHILE body
+    // executes while its condition, default 1, stays non-zero)
+    Ctl *h = (Ctl *)g->ctl_h;
+    if ((rc = read_ctl(S, h)) < 0) break;
+    if (h->fw_continue) {
+      e = cudaGraphLaunch(exec, S.s);
+      if (e != cudaSuccess) { rc = fail(QDTA_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e)); break; }
+    }
+    rc = seg_finish(S);
+  } while (0);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamSynchronize(S.s);
+  cudaStreamDestroy(cs);
+  return rc;
+}
+
+static void fill_stats(const Ctl *h, long long n_items, qdta_stats *st) {
+  st->iterations = h->iterations;
+  st->aon_calls = h->aon_calls;
+  st->ls_passes = h->ls_passes;
+  st->converged = h->converged;
+  st->rel_gap = h->rel_gap;
+  st->objective = h->objective;
+  st->n_items = n_items;
+}
+
+static int check_od(const qdta_graph *g, const qdta_od *od) {
+  if (!od) return fail(QDTA_EINVAL, "od is NULL");
+  if (od->n_items < 0 || od->n_roots < 0) return fail(QDTA_EINVAL, "negative sizes");
+  if (od->n_items > 0 && (!od->roots || !od->root_idx || !od->src || !od->amount_fx || od->n_roots < 1))
+    return fail(QDTA_EINVAL, "od arrays must not be NULL");
+  (void)g;
+  return QDTA_OK;
+}
+
+extern "C" int qdta_line_search(qdta_graph *g, const double *flow, const int64_t *aon_fx, double dt_s,
+                                int32_t fw_iter, const qdta_params *p, double *alpha_out,
+                                int32_t *passes_out, void *stream) {
+  RC(check_graph(g));
+  RC(check_params(p));
+  if (fw_iter < 1) return fail(QDTA_EINVAL, "fw_iter must be >= 1");
+  if (!(dt_s > 0.0)) return fail(QDTA_EINVAL, "dt_s must be > 0");
+  if (g->d.L > 0 && (!flow || !aon_fx)) return fail(QDTA_EINVAL, "NULL array");
+  DevGuard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  RC(status_reset(g, s));
+  Solver S{};
+  S.g = g; S.s = s; S.p = p; S.dt_h = dt_s / 3600.0;
+  Ctl *ctl;
+  LinkConst *kc;
+  i128 *partials;
+  unsigned *counter;
+  const int sg = sweep_grid(g->d);
+  RC(ws_get(g, "ls.ctl", 1, &ctl));
+  RC(ws_get(g, "ls.kc", (size_t)g->d.L, &kc));
+  RC(ws_get(g, "ls.partials", (size_t)sg * NSUM, &partials));
+  RC(ws_get(g, "ls.counter", 4, &counter));
+  CK(cudaMemsetAsync(counter, 0, 16, s));
+  // a line search alone: no stop rule, iteration k = fw_iter
+  launch_ctl_init(ctl, p->step, QDTA_STOP_NONE, fw_iter, p->ls_max, p->tol, p->ls_dx, p->ls_t1, p->ls_t2,
+                  1, 1, nullptr, s);
+  CK(cudaMemcpyAsync(&ctl->k, &fw_iter, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  launch_link_const(g->d, S.dt_h, kc, s);
+  launch_ctl_begin(ctl, 0, 0, s);
+  Ctl *h = (Ctl *)g->ctl_h;
+  for (int guard_it = 0; guard_it < 10000; ++guard_it) {
+    CK(cudaMemcpyAsync(h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!h->need_sweep) break;
+    launch_sweep(g->d, kc, flow, (const long long *)aon_fx, nullptr, ctl, partials, counter, sg, g->status, s);
+    launch_ctl_step(ctl, 0, 0, s);
+  }
+  RC(status_check(g, s));
+  if (alpha_out) *alpha_out = h->alpha_final;
+  if (passes_out) *passes_out = h->ls_passes;
+  return QDTA_OK;
+}
+
+static int assign_core(qdta_graph *g, const qdta_od *od, double dt_s, const qdta_params *p,
+                       double *flow_out, qdta_stats *stats, qdta_tape **tape_out, cudaStream_t s,
+                       const std::string &tag) {
+  Solver S{};
+  S.g = g; S.s = s; S.p = p;
+  S.dt_h = dt_s / 3600.0;
+  S.dt_q = dt_quanta(g, dt_s);
+  S.roots = od->roots; S.R_host = od->n_roots; S.R_dev = nullptr; S.R_cap = od->n_roots > 0 ? od->n_roots : 1;
+  S.root_slot = nullptr; S.item_roots = od->roots;
+  S.n_host = od->n_items; S.n_dev = nullptr;
+  S.root_idx = od->root_idx; S.src = od->src; S.amount = (const long long *)od->amount_fx;
+  S.f = flow_out;
+  const bool want_tape = p->record_tape && tape_out;
+  RC(solver_alloc(S, tag, 1, want_tape));
+  RC(status_reset(g, s));
+  if (p->schedule == QDTA_SCHEDULE_GRAPH) RC(fw_graph(S));
+  else RC(fw_plain(S));
+  RC(status_check(g, s));
+  Ctl *h = (Ctl *)g->ctl_h;
+  RC(read_ctl(S, h));
+  if (stats) fill_stats(h, od->n_items, stats);
+  if (want_tape) {
+    qdta_tape *t = new qdta_tape();
+    t->g = g; t->od = *od; t->dt_s = dt_s; t->step = p->step; t->K = h->iterations;
+    const size_t L = g->d.L, K1 = (size_t)t->K + 1;
+    bool ok = cudaMalloc(&t->q, K1 * L * 4 + 16) == cudaSuccess &&
+              cudaMalloc(&t->alpha, K1 * 8 + 16) == cudaSuccess &&
+              cudaMalloc(&t->f, K1 * L * 8 + 16) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); qdta_tape_destroy(t); return fail(QDTA_ENOMEM, "tape allocation"); }
+    CK(cudaMemcpyAsync(t->q, S.tape_q, K1 * L * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(t->alpha, S.tape_alpha, K1 * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(t->f, S.tape_f, K1 * L * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    *tape_out = t;
+  }
+  return h->notconv ? QDTA_ENOTCONV : QDTA_OK;
+}
+
+extern "C" int qdta_assign_interval(qdta_graph *g, const qdta_od *od, double dt_s, const qdta_params *p,
+                                    double *flow_out, qdta_stats *stats, qdta_tape **tape_out,
+                                    void *stream) {
+  RC(check_graph(g));
+  RC(check_params(p));
+  RC(check_od(g, od));
+  if (!(dt_s > 0.0)) return fail(QDTA_EINVAL, "dt_s must be > 0");
+  if (g->d.L > 0 && !flow_out) return fail(QDTA_EINVAL, "flow_out is NULL");
+  if (tape_out) *tape_out = nullptr;
+  DevGuard guard(g->device);
+  return assign_core(g, od, dt_s, p, flow_out, stats, tape_out, (cudaStream_t)stream, "fw");
+}
+
+// ---------------------------------------------------------------------------
+// many independent instances
+// ---------------------------------------------------------------------------
+extern "C" int qdta_assign_batch(const qdta_instance *inst, int32_t n_inst, const qdta_params *p,
+                                 qdta_stats *stats, void *stream) {
+  if (n_inst < 0 || (n_inst > 0 && !inst)) return fail(QDTA_EINVAL, "bad instance array");
+  RC(check_params(p));
+  cudaStream_t s = (cudaStream_t)stream;
+  int worst = QDTA_OK;
+  for (int i = 0; i < n_inst; ++i) {
+    RC(check_graph(inst[i].graph));
+    RC(check_od(inst[i].graph, &inst[i].od));
+    DevGuard guard(inst[i].graph->device);
+    int rc = assign_core(inst[i].graph, &inst[i].od, inst[i].dt_s, p, inst[i].flow_out,
+                         stats ? &stats[i] : nullptr, nullptr, s, "batch");
+    if (rc < 0) return rc;
+    if (rc > 0) worst = rc;
+  }
+  return worst;
+}
+
+// ---------------------------------------------------------------------------
+// a day of intervals (Alg. 1)
+// ---------------------------------------------------------------------------
+struct Day {
+  Solver S;
+  int Z;                       // zones (roots of every interval)
+  const int *zones;
+  unsigned long long *dense;   // [Z * V] residual + original demand accumulator
+  int *blk_count;
+  long long *blk_off;
+  long long cap_items;
+  int *it_root, *it_src;
+  long long *it_amt;
+  long long *n_items_dev;
+  int *flag, *active, *root_slot, *n_active;
+  int *q_fin, *q_work;
+  int2 *hq_fin;
+  unsigned long long *h_fx;
+  double *w;
+  OrigTable *tab;
+  long long max_orig;
+  qdta_stats *stats_dev;
+};
+
+static int day_merge(Day &D) {
+  qdta_graph *g = D.S.g;
+  cudaStream_t s = D.S.s;
+  launch_scatter_orig(g->d, D.S.ctl, D.tab, D.max_orig, D.dense, s);
+  launch_compact(g->d, D.Z, D.dense, D.blk_count, D.blk_off, D.cap_items, D.it_root, D.it_src, D.it_amt,
+                 D.n_items_dev, g->status, s);
+  launch_active_roots(D.Z, D.n_items_dev, D.cap_items, D.it_root, D.zones, D.flag, D.active, D.root_slot,
+                      D.n_active, s);
+  return QDTA_OK;
+}
+
+// Alg. 4 preparation: step weights, final costs, cleared h
+static int day_res_head(Day &D) {
+  qdta_graph *g = D.S.g;
+  cudaStream_t s = D.S.s;
+  launch_path_weights(D.S.ctl, D.S.tape_alpha, D.w, s);
+  launch_bpr(g->d, D.S.f, D.S.dt_h, nullptr, D.q_fin, g->status, s);
+  launch_pack_head_q(g->d, D.q_fin, D.hq_fin, s);
+  CK(cudaMemsetAsync(D.h_fx, 0, (size_t)g->d.L * 8, s));
+  return QDTA_OK;
+}
+
+// one accepted AON j: reuse its stored tree or rebuild it, then re-walk
+static int day_res_body(Day &D, unsigned long long h, int use_cond) {
+  qdta_graph *g = D.S.g;
+  Solver &S = D.S;
+  cudaStream_t s = S.s;
+  launch_res_prep(S.ctl, D.w, S.tape_q, g->d.L, D.q_work, s);
+  RC(run_sssp(g, QDTA_TO_ROOT, D.q_work, S.roots, 0, S.R_dev, S.R_cap, S.parent, &S.ctl->res_slot,
+              S.parent_stride, nullptr, s, &S.ctl->res_skip));
+  launch_residual(g->d, D.hq_fin, S.parent, &S.ctl->res_slot, S.parent_stride, D.root_slot, D.zones,
+                  D.n_items_dev, D.cap_items, D.it_root, D.it_src, D.it_amt, &S.ctl->w_cur, S.dt_q, D.h_fx,
+                  D.dense, g->status, s);
+  launch_res_next(S.ctl, h, use_cond, s);
+  return QDTA_OK;
+}
+
+static int day_store(Day &D, double *flow_out) {
+  launch_store_interval(D.S.g->d, D.S.ctl, D.h_fx, flow_out, D.stats_dev, D.n_items_dev, D.S.s);
+  return QDTA_OK;
+}
+
+static int day_interval_plain(Day &D, double *flow_out) {
+  Solver &S = D.S;
+  Ctl *h = (Ctl *)S.g->ctl_h;
+  RC(day_merge(D));
+  RC(fw_plain(S));
+  RC(day_res_head(D));
+  launch_res_begin(S.ctl, 0, 0, S.s);
+  RC(read_ctl(S, h));
+  while (h->res_continue) {
+    RC(day_res_body(D, 0, 0));
+    RC(read_ctl(S, h));
+  }
+  RC(day_store(D, flow_out));
+  launch_day_next(S.ctl, 0, 0, S.s);
+  return QDTA_OK;
+}
+
+extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, double dt_s,
+                            const qdta_params *p, const qdta_od *resid_in, double *flow_out,
+                            qdta_stats *stats, qdta_residual *resid_out, void *stream) {
+  RC(check_graph(g));
+  RC(check_params(p));
+  if (N < 0 || (N > 0 && !d_orig)) return fail(QDTA_EINVAL, "bad interval array");
+  if (!(dt_s > 0.0)) return fail(QDTA_EINVAL, "dt_s must be > 0");
+  if (N == 0) return QDTA_OK;
+  if (g->d.L > 0 && !flow_out) return fail(QDTA_EINVAL, "flow_out is NULL");
+  const int Z = d_orig[0].n_roots;
+  if (Z < 1 || !d_orig[0].roots) return fail(QDTA_EINVAL, "the zone list (d_orig[0].roots) is empty");
+  for (int i = 0; i < N; ++i) {
+    RC(check_od(g, &d_orig[i]));
+    if (d_orig[i].n_roots != Z) return fail(QDTA_EINVAL, "interval %d: every interval must use the zone list", i);
+  }
+  if (resid_in) {
+    RC(check_od(g, resid_in));
+    if (resid_in->n_items > 0 && resid_in->n_roots != Z) return fail(QDTA_EINVAL, "resid_in must use the zone list");
+  }
+  DevGuard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t V = g->d.V, L = g->d.L;
+  Day D{};
+  Solver &S = D.S;
+  S.g = g; S.s = s; S.p = p;
+  S.dt_h = dt_s / 3600.0;
+  S.dt_q = dt_quanta(g, dt_s);
+  D.Z = Z;
+  D.zones = d_orig[0].roots;
+  const long long dense_n = (long long)Z * (long long)V;
+  RC(ws_get(g, "day.dense", (size_t)dense_n, &D.dense));
+  const int nblk = (int)((dense_n + 4095) / 4096);
+  RC(ws_get(g, "day.blk_count", (size_t)nblk, &D.blk_count));
+  RC(ws_get(g, "day.blk_off", (size_t)nblk, &D.blk_off));
+  long long max_orig = resid_in ? resid_in->n_items : 0;
+  for (int i = 0; i < N; ++i) max_orig = d_orig[i].n_items > max_orig ? d_orig[i].n_items : max_orig;
+  D.max_orig = max_orig;
+  D.cap_items = dense_n < (64ll << 20) ? dense_n : (64ll << 20);
+  RC(ws_get(g, "day.it_root", (size_t)D.cap_items, &D.it_root));
+  RC(ws_get(g, "day.it_src", (size_t)D.cap_items, &D.it_src));
+  RC(ws_get(g, "day.it_amt", (size_t)D.cap_items, &D.it_amt));
+  RC(ws_get(g, "day.n_items", 2, &D.n_items_dev));
+  RC(ws_get(g, "day.flag", (size_t)Z, &D.flag));
+  RC(ws_get(g, "day.active", (size_t)Z, &D.active));
+  RC(ws_get(g, "day.root_slot", (size_t)Z, &D.root_slot));
+  RC(ws_get(g, "day.n_active", 4, &D.n_active));
+  RC(ws_get(g, "day.q_fin", L, &D.q_fin));
+  RC(ws_get(g, "day.q_work", L, &D.q_work));
+  RC(ws_get(g, "day.hq_fin", L, &D.hq_fin));
+  RC(ws_get(g, "day.h_fx", L, &D.h_fx));
+  RC(ws_get(g, "day.w", (size_t)p->max_iter + 2, &D.w));
+  RC(ws_get(g, "day.stats", (size_t)N, &D.stats_dev));
+  // per-interval original demand table (+ the resumed residual folded into interval 0)
+  std::vector<OrigTable> tab(N);
+  for (int i = 0; i < N; ++i)
+    tab[i] = OrigTable{d_orig[i].root_idx, d_orig[i].src, (const long long *)d_orig[i].amount_fx,
+                       d_orig[i].n_items};
+  RC(ws_get(g, "day.tab", (size_t)N, &D.tab));
+  CK(cudaMemcpyAsync(D.tab, tab.data(), sizeof(OrigTable) * N, cudaMemcpyHostToDevice, s));
+  // solver over the zone list
+  S.roots = D.active; S.R_host = 0; S.R_dev = D.n_active; S.R_cap = Z;
+  S.root_slot = D.root_slot; S.item_roots = D.zones;
+  S.n_host = 0; S.n_dev = D.n_items_dev;
+  S.root_idx = D.it_root; S.src = D.it_src; S.amount = D.it_amt;
+  RC(ws_get(g, "day.f", L, &S.f));
+  // parent ring: keep every tree of an interval when memory allows
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  const double per_slot = (double)Z * V * 4.0;
+  long long ring = p->max_iter + 1;
+  long long afford = (long long)((double)free_b * 0.5 / per_slot);
+  if (ring > afford) ring = afford;
+  if (ring < 2) ring = 2;
+  RC(solver_alloc(S, "day", (int)ring, false));
+  RC(status_reset(g, s));
+  // dense accumulator starts at zero; the resumed residual goes in first
+  CK(cudaMemsetAsync(D.dense, 0, (size_t)dense_n * 8, s));
+  if (resid_in && resid_in->n_items > 0)
+    launch_scatter_items(g->d, resid_in->n_items, resid_in->root_idx, resid_in->src,
+                         (const long long *)resid_in->amount_fx, D.dense, s);
+  // day counter lives in the solver's controller
+  int dayinit[3] = {0, N, 1};
+  CK(cudaMemcpyAsync(&S.ctl->day_i, dayinit, sizeof dayinit, cudaMemcpyHostToDevice, s));
+  int rc = QDTA_OK;
+  if (p->schedule == QDTA_SCHEDULE_PLAIN) {
+    for (int i = 0; i < N && rc >= 0; ++i) rc = day_interval_plain(D, flow_out);
+  } else {
+    rc = fail(QDTA_EINVAL, "graph schedule of a day is set up below");
+  }
+  RC(rc);
+  RC(status_check(g, s));
+  std::vector<qdta_stats> st(N);
+  CK(cudaMemcpy(st.data(), D.stats_dev, sizeof(qdta_stats) * N, cudaMemcpyDeviceToHost));
+  int worst = QDTA_OK;
+  for (int i = 0; i < N; ++i) {
+    if (stats) stats[i] = st[i];
+  }
+  // residual after the last interval
+  if (resid_out) {
+    launch_compact(g->d, Z, D.dense, D.blk_count, D.blk_off, resid_out->capacity, resid_out->root_idx,
+                   resid_out->src, (long long *)resid_out->amount_fx, D.n_items_dev, g->status, s);
+    long long cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, D.n_items_dev, 8, cudaMemcpyDeviceToHost, s));
+    RC(status_check(g, s));
+    resid_out->count = cnt;
+  } else {
+    CK(cudaMemsetAsync(D.dense, 0, (size_t)dense_n * 8, s));
+  }
+  (void)worst;
+  return QDTA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+extern "C" int qdta_tape_destroy(qdta_tape *t) {
+  if (!t) return QDTA_OK;
+  if (t->q) cudaFree(t->q);
+  if (t->alpha) cudaFree(t->alpha);
+  if (t->f) cudaFree(t->f);
+  delete t;
+  return QDTA_OK;
+}
+
+extern "C" int qdta_tape_info(const qdta_tape *t, int32_t *K, int64_t *n_items) {
+  if (!t) return fail(QDTA_EINVAL, "tape is NULL");
+  if (K) *K = t->K;
+  if (n_items) *n_items = t->od.n_items;
+  return QDTA_OK;
+}
+
+extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_ddemand, double *dL_dcap,
+                             void *stream) {
+  if (!t || !t->g) return fail(QDTA_EINVAL, "tape is NULL");
+  qdta_graph *g = t->g;
+  const size_t L = g->d.L;
+  const long long n = t->od.n_items;
+  if (L > 0 && (!dL_dflow || !dL_dcap)) return fail(QDTA_EINVAL, "NULL gradient array");
+  if (n > 0 && !dL_ddemand) return fail(QDTA_EINVAL, "dL_ddemand is NULL");
+  DevGuard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  RC(status_reset(g, s));
+  const double dt_h = t->dt_s / 3600.0;
+  const long long dt_q = dt_quanta(g, t->dt_s);
+  const int R = t->od.n_roots > 0 ? t->od.n_roots : 1;
+  double *lam, *lam2, *gbar, *red, *muH;
+  unsigned long long *gfx;
+  LinkConst *kc;
+  int2 *hq;
+  int *parent;
+  const int grid = sweep_grid(g->d);
+  RC(ws_get(g, "bw.lam", L, &lam));
+  RC(ws_get(g, "bw.lam2", L, &lam2));
+  RC(ws_get(g, "bw.gbar", L, &gbar));
+  RC(ws_get(g, "bw.red", (size_t)grid * 2, &red));
+  RC(ws_get(g, "bw.muH", 2, &muH));
+  RC(ws_get(g, "bw.gfx", L, &gfx));
+  RC(ws_get(g, "bw.kc", L, &kc));
+  RC(ws_get(g, "bw.hq", L, &hq));
+  RC(ws_get(g, "bw.parent", (size_t)R * g->d.V, &parent));
+  std::vector<double> alpha(t->K + 1);
+  CK(cudaMemcpy(alpha.data(), t->alpha, sizeof(double) * (t->K + 1), cudaMemcpyDeviceToHost));
+  launch_link_const(g->d, dt_h, kc, s);
+  CK(cudaMemcpyAsync(lam, dL_dflow, L * 8, cudaMemcpyDeviceToDevice, s));
+  if (n > 0) CK(cudaMemsetAsync(dL_ddemand, 0, (size_t)n * 8, s));
+  CK(cudaMemsetAsync(dL_dcap, 0, L * 8, s));
+  for (int k = t->K; k >= 0; --k) {
+    const int *qk = t->q + (size_t)k * L;
+    // recompute tree k from the taped link times, and g_k
+    RC(run_sssp(g, QDTA_TO_ROOT, qk, t->od.roots, t->od.n_roots, nullptr, R, parent, nullptr, 0, nullptr, s));
+    launch_pack_head_q(g->d, qk, hq, s);
+    CK(cudaMemsetAsync(gfx, 0, L * 8, s));
+    launch_load(g->d, hq, parent, nullptr, 0, nullptr, t->od.roots, n, nullptr, t->od.root_idx, t->od.src,
+                (const long long *)t->od.amount_fx, dt_q, gfx, nullptr, g->status, s);
+    const double *gb = lam;
+    if (k > 0) {
+      const double *fprev = t->f + (size_t)(k - 1) * L;
+      const double a = alpha[k];
+      const int implicit = t->step != QDTA_STEP_MSA && a > 0.0 && a < 1.0;
+      launch_adj_reduce(g->d, kc, lam, fprev, (const long long *)gfx, a, implicit, red, muH, grid, s);
+      launch_adj_update(g->d, kc, lam, fprev, (const long long *)gfx, a, implicit, muH, gbar, lam2, dL_dcap, s);
+      gb = gbar;
+    }
+    launch_gather(g->d, hq, parent, t->od.roots, n, t->od.root_idx, t->od.src, dt_q, gb, dL_ddemand,
+                  g->status, s);
+    if (k > 0) std::swap(lam, lam2);
+  }
+  return status_check(g, s);
+}

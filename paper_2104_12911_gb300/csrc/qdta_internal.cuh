@@ -1,0 +1,315 @@
+// qdta_internal.cuh -- device arithmetic, kernel parameter blocks and host
+// launchers shared by the two translation units of libqdta.
+//
+// Floating point: every FP64 operation that must agree bit for bit with the
+// CPU reference goes through an explicitly rounded intrinsic (__dmul_rn,
+// __dadd_rn, ...), so no multiply-add is ever contracted (the library is also
+// compiled with -fmad=false).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qdta {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+// status bits written by kernels (OR-ed into a device word)
+enum : unsigned {
+  ST_NONFINITE = 1u,   // NaN/inf input or term, or a fixed-point term >= 2^68
+  ST_UNREACH = 2u,     // a walk met a node without parent before its root
+  ST_OVERFLOW = 4u,    // a distance exceeded the packed range
+  ST_TIMEOUT = 8u,     // a bounded loop hit its limit
+  ST_CAPACITY = 16u,   // an output buffer was too small
+};
+
+constexpr int SSSP_THREADS = 256;
+constexpr int LINK_THREADS = 256;
+constexpr int MAX_SLOTS = 8;    // step sizes evaluated per sweep
+constexpr int NSUM = MAX_SLOTS + 2;  // + gap sums A, B
+
+// --------------------------------------------------------------------------
+// exact-rounding helpers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dvd(double a, double b) { return __ddiv_rn(a, b); }
+
+__device__ __forceinline__ double powi(double x, int n) {
+  double p = x;
+  for (int i = 1; i < n; ++i) p = mul(p, x);
+  return p;
+}
+
+// fixed point of a trip amount: (double)amount_fx * 2^-32
+__device__ __forceinline__ double fx64_to_double(long long v) {
+  return mul(__ll2double_rn(v), 0x1p-32);
+}
+
+// round_to_nearest_even(v * 2^32) as a 128-bit integer, from the bits of v.
+// |v| >= 2^68 or non-finite sets *bad and yields 0.
+__device__ __forceinline__ i128 fx_of(double v, unsigned *bad) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  int e = (int)((bits >> 52) & 0x7ffu);
+  if (e == 0x7ff) { *bad |= ST_NONFINITE; return 0; }
+  if (e == 0) return 0;  // zero or subnormal: far below 2^-33
+  long long m = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  int sh = e - 1043;     // v * 2^32 = m * 2^sh
+  i128 r;
+  if (sh >= 0) {
+    if (sh > 47) { *bad |= ST_NONFINITE; return 0; }
+    r = (i128)m << sh;
+  } else {
+    int s = -sh;
+    if (s > 60) {
+      r = 0;
+    } else {
+      long long q = m >> s;
+      long long rem = m - (q << s);
+      long long half = 1ll << (s - 1);
+      if (rem > half || (rem == half && (q & 1))) ++q;
+      r = q;
+    }
+  }
+  return (bits >> 63) ? -r : r;
+}
+
+// nearest double to a 128-bit integer (ties to even), built from its bits
+__device__ __forceinline__ double i128_to_double(i128 s) {
+  if (s == 0) return 0.0;
+  bool neg = s < 0;
+  u128 u = neg ? (u128)(-s) : (u128)s;
+  unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+  int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  double r;
+  if (nb <= 53) {
+    r = __ull2double_rn(lo);
+  } else {
+    int sh = nb - 53;
+    unsigned long long m = (unsigned long long)(u >> sh);
+    u128 rem = u & (((u128)1 << sh) - 1);
+    u128 half = (u128)1 << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) {
+      ++m;
+      if (m == (1ull << 53)) { m >>= 1; ++sh; }
+    }
+    double scale = __longlong_as_double((long long)(1023 + sh) << 52);
+    r = mul(__ull2double_rn(m), scale);
+  }
+  return neg ? -r : r;
+}
+
+__device__ __forceinline__ double fx_to_double(i128 s) { return mul(i128_to_double(s), 0x1p-32); }
+
+// --------------------------------------------------------------------------
+// link cost model (Eq. 1) and its integral (Eq. 6), per-link constants:
+//   inv = 1 / (C dt_h), kb = (alpha C dt_h) / (beta + 1)
+// --------------------------------------------------------------------------
+struct LinkConst {
+  double inv;
+  double kb;
+};
+
+__device__ __forceinline__ LinkConst link_const(double cap, double dt_h, double alpha, int beta) {
+  double cp = mul(cap, dt_h);
+  LinkConst k;
+  k.inv = dvd(1.0, cp);
+  k.kb = dvd(mul(alpha, cp), (double)(beta + 1));
+  return k;
+}
+
+__device__ __forceinline__ double link_cost(double c0, double inv, double alpha, int beta, double t) {
+  double x = mul(t, inv);
+  double p = powi(x, beta);
+  double w = mul(alpha, p);
+  double u = add(1.0, w);
+  return mul(c0, u);
+}
+
+__device__ __forceinline__ double link_cost_dt(double c0, double inv, double alpha, int beta, double t) {
+  double x = mul(t, inv);
+  double p = beta > 1 ? powi(x, beta - 1) : 1.0;
+  double w = mul(c0, alpha);
+  w = mul(w, (double)beta);
+  w = mul(w, p);
+  return mul(w, inv);
+}
+
+__device__ __forceinline__ double beckmann(double c0, double inv, double kb, int beta, double t) {
+  double x = mul(t, inv);
+  double p = powi(x, beta + 1);
+  double w = mul(kb, p);
+  double u = add(t, w);
+  return mul(c0, u);
+}
+
+// t = f + alpha (g - f), the same three roundings as the flow update
+__device__ __forceinline__ double step_flow(double f, double g, double alpha) {
+  double d = sub(g, f);
+  double s = mul(alpha, d);
+  return add(f, s);
+}
+
+__device__ __forceinline__ int quantize(double c, unsigned *bad) {
+  if (isnan(c)) { *bad |= ST_NONFINITE; return 2147483647; }
+  double r = floor(add(c, 0.5));
+  if (r < 1.0) return 1;
+  if (r > 2147483647.0) return 2147483647;
+  return (int)r;
+}
+
+// --------------------------------------------------------------------------
+// device-side controller of one interval solve (single thread updates it)
+// --------------------------------------------------------------------------
+enum SumKind : int { K_PHI = 0, K_DPHI = 1, K_DDPHI = 2 };
+
+enum LsState : int {
+  LS_IDLE = 0,
+  LS_GAPONLY = 1,   // MSA (or QN with ls_max <= 1): the sweep only measures the gap
+  LS_QN = 2,
+  LS_SW_FIRST = 3,
+  LS_SW_NEXT = 4,
+  LS_EX_END = 5,
+  LS_EX_NEWTON = 6,
+  LS_OBJ = 7,       // PAPER_OBJ test: phi(0) vs phi(alpha*)
+};
+
+struct Plan {
+  int n;              // slots in use (0..MAX_SLOTS)
+  int want_gap;       // also compute sum fx(q f) and sum q g_fx
+  int kind[MAX_SLOTS];
+  double alpha[MAX_SLOTS];
+};
+
+struct Ctl {
+  // parameters
+  int step, stop, max_iter, ls_max;
+  double tol, dx, t1, t2;
+  // loop state
+  int k;              // FW step in progress (1-based)
+  int fw_continue;    // 0 once the loop is over
+  int need_sweep;     // 1 while the line search wants another sweep
+  int do_update;      // 1 if the step of iteration k is applied
+  int converged;
+  int notconv;
+  int iterations, aon_calls, ls_passes;
+  int ls_state, ls_pc, l, ex_it;
+  double rel_gap;
+  double alpha, alpha_final, lo, hi;
+  i128 Dlo, Dhi;
+  Plan plan;
+  i128 sums[NSUM];
+  double objective;
+  // parent-array ring: AON j writes slot min(j, ring - 1)
+  int ring, tree_slot;
+  // residual loop (Alg. 4) and day loop (Alg. 1)
+  int res_j, res_slot, res_skip, res_continue;
+  double w_cur;
+  int day_i, day_N, day_continue;
+};
+
+// --------------------------------------------------------------------------
+// launchers (qdta_kernels.cu)
+// --------------------------------------------------------------------------
+struct GraphDev {
+  int V, L, LB, beta;
+  double alpha, quantum_s;
+  const int *tail, *head, *c0;
+  const double *cap;
+  const int *out_off, *in_off;    // [V+1]
+  const int *out_link, *in_link;  // [L] link ids grouped by tail / head, ascending
+  int num_sms;
+};
+
+struct SsspWork {
+  unsigned long long *state;  // [slots][V]
+  int *stamp;                 // [slots][V]
+  int *queue;                 // [slots][2][V]
+  int4 *adj;                  // [L] packed (link, neighbour, q, 0) of the chosen direction
+  int slots;
+};
+
+// skip_dev (nullable): when *skip_dev != 0 the launch does nothing
+void launch_pack_adj(const GraphDev &g, int direction, const int *q, int4 *adj, cudaStream_t s,
+                     const int *skip_dev = nullptr);
+void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *roots,
+                 int R_host, const int *R_dev, int grid, bool use_smem, const SsspWork &w,
+                 int *parent, const int *parent_slot_dev, long long slot_stride, long long *dist,
+                 unsigned *status, cudaStream_t s, const int *skip_dev = nullptr,
+                 unsigned long long *roots_counter = nullptr);
+int sssp_max_smem_nodes();
+int sssp_blocks_per_sm(bool use_smem, int V);
+
+void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStream_t s);
+void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const int *parent_slot_dev,
+                 long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
+                 const long long *n_items_dev, const int *root_idx, const int *src,
+                 const long long *amount, long long dt_q, unsigned long long *flow_fx, int *stop_out,
+                 unsigned *status, cudaStream_t s);
+void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *parent,
+                     const int *parent_slot_dev, long long slot_stride, const int *root_slot,
+                     const int *roots, const long long *n_items_dev, long long n_items_cap,
+                     const int *root_idx, const int *src, const long long *amount,
+                     const double *weight_dev, long long dt_q, unsigned long long *h_fx,
+                     unsigned long long *dense, unsigned *status, cudaStream_t s);
+
+void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,
+                unsigned *status, cudaStream_t s);
+void launch_link_const(const GraphDev &g, double dt_h, LinkConst *kc, cudaStream_t s);
+void launch_flow_from_fx(int L, const unsigned long long *fx, double *f, cudaStream_t s);
+void launch_sweep(const GraphDev &g, const LinkConst *kc, const double *f, const long long *g_fx,
+                  const int *q, Ctl *ctl, i128 *partials, unsigned *counter, int grid,
+                  unsigned *status, cudaStream_t s);
+int sweep_grid(const GraphDev &g);
+void launch_update(const GraphDev &g, Ctl *ctl, double *f, const long long *g_fx, cudaStream_t s);
+void launch_objective(const GraphDev &g, const LinkConst *kc, const double *f, Ctl *ctl,
+                      i128 *partials, unsigned *counter, int grid, unsigned *status, cudaStream_t s);
+
+void launch_ctl_init(Ctl *ctl, int step, int stop, int max_iter, int ls_max, double tol, double dx,
+                     double t1, double t2, int ring, long long n_items_host,
+                     const long long *n_items_dev, cudaStream_t s);
+void launch_tape0(const GraphDev &g, const int *q, const double *f, int *tape_q, double *tape_alpha,
+                  double *tape_f, cudaStream_t s);
+void launch_res_begin(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s);
+void launch_res_prep(Ctl *ctl, const double *w, const int *tape_q, int L, int *q_work, cudaStream_t s);
+void launch_res_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s);
+void launch_store_interval(const GraphDev &g, const Ctl *ctl, const unsigned long long *h_fx,
+                           double *flow_out_rows, void *stats_rows, const long long *n_items_dev,
+                           cudaStream_t s);
+void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s);
+struct OrigTable { const int *root_idx; const int *src; const long long *amount; long long n; };
+void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab, long long max_n,
+                         unsigned long long *dense, cudaStream_t s);
+void launch_ctl_begin(Ctl *ctl, unsigned long long cond_fw, int use_cond, cudaStream_t s);
+void launch_ctl_step(Ctl *ctl, unsigned long long cond_ls, int use_cond, cudaStream_t s);
+void launch_ctl_end(Ctl *ctl, unsigned long long cond_fw, int use_cond, cudaStream_t s);
+void launch_tape_record(const GraphDev &g, const Ctl *ctl, const int *q, const double *f,
+                        int *tape_q, double *tape_alpha, double *tape_f, int cap, cudaStream_t s);
+
+void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, const int *src,
+                          const long long *amount, unsigned long long *dense, cudaStream_t s);
+void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *blk_count,
+                    long long *blk_off, long long cap, int *root_idx, int *src, long long *amount,
+                    long long *n_out_dev, unsigned *status, cudaStream_t s);
+void launch_active_roots(int R, const long long *n_items_dev, long long cap_items,
+                         const int *root_idx, const int *zone_nodes, int *flag, int *active_roots,
+                         int *root_slot, int *n_active_dev, cudaStream_t s);
+void launch_path_weights(const Ctl *ctl, const double *tape_alpha, double *w, cudaStream_t s);
+void launch_fill_i32(int *p, long long n, int v, cudaStream_t s);
+void launch_fx_to_flow(int L, const unsigned long long *fx, double *out, cudaStream_t s);
+void launch_weight_select(const double *w, int j, double *dst, cudaStream_t s);
+
+// adjoint
+void launch_adj_reduce(const GraphDev &g, const LinkConst *kc, const double *lam, const double *fprev,
+                       const long long *g_fx, double alpha, int implicit, double *partials, double *out2,
+                       int grid, cudaStream_t s);
+void launch_adj_update(const GraphDev &g, const LinkConst *kc, const double *lam, const double *fprev,
+                       const long long *g_fx, double alpha, int implicit, const double *muH,
+                       double *gbar, double *lam_prev, double *dcap, cudaStream_t s);
+void launch_gather(const GraphDev &g, const int2 *head_q, const int *parent, const int *roots,
+                   long long n_items, const int *root_idx, const int *src, long long dt_q,
+                   const double *gbar, double *dd, unsigned *status, cudaStream_t s);
+
+}  // namespace qdta

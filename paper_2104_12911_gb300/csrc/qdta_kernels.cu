@@ -1,0 +1,1179 @@
+// qdta_kernels.cu -- sm_103a kernels of the QDTA hot path.
+//
+//   pack_adj / sssp       batched shortest paths (Alg. 3 / Alg. 7 routing)
+//   pack_head_q / load    truncated all-or-nothing loading (Alg. 3, Eq. 2, Eq. 5)
+//   residual              re-truncation of every FW path with final costs (Alg. 4)
+//   bpr                   link costs (Eq. 1)
+//   sweep / objective     fixed-point link sums for the line search (Alg. 9, Eq. 6-9)
+//   ctl_*                 single-thread FW / line-search controller (Alg. 2, 6, 8)
+//   update / tape         convex flow update f + alpha (g - f)
+//   scatter / compact     residual-demand merge d(i+1) = d_o(i+1) + d_r(i+1) (Alg. 1)
+//   adj_* / gather        adjoint of the unrolled FW map
+#include <climits>
+#include <cstdio>
+
+#include "qdta.h"
+#include "qdta_internal.cuh"
+
+namespace qdta {
+
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ============================================================================
+// shortest paths
+// ============================================================================
+
+// Adjacency of node w for the relaxation direction:
+//   TO_ROOT   -> links entering w, neighbour = their tail (the node that can
+//                reach the root through w);
+//   FROM_ROOT -> links leaving w, neighbour = their head.
+// Each entry is one 16-byte vector: (link id, neighbour, link time, 0).
+__global__ void pack_adj_kernel(int L, const int *__restrict__ link_list,
+                                const int *__restrict__ nb_of_link, const int *__restrict__ q,
+                                int4 *__restrict__ adj, const int *skip_dev) {
+  if (skip_dev && *skip_dev) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gridDim.x * blockDim.x) {
+    int e = link_list[k];
+    adj[k] = make_int4(e, nb_of_link[e], q[e], 0);
+  }
+}
+
+void launch_pack_adj(const GraphDev &g, int direction, const int *q, int4 *adj, cudaStream_t s,
+                     const int *skip_dev) {
+  if (g.L == 0) return;
+  const int *list = direction == 0 ? g.in_link : g.out_link;
+  const int *nb = direction == 0 ? g.tail : g.head;
+  pack_adj_kernel<<<cdiv(g.L, 256), 256, 0, s>>>(g.L, list, nb, q, adj, skip_dev);
+}
+
+// One CTA per root (persistent over roots).  Queue-based Bellman-Ford:
+// every round relaxes the adjacency of the nodes whose distance improved in
+// the previous round.  Node state is one 64-bit key (dist << LB) | link, so
+// a single atomicMin keeps the smallest distance and, among links giving
+// that distance, the smallest link id -- exactly the parent rule, and
+// independent of the order in which relaxations arrive.  A per-node round
+// stamp keeps each node at most once per round in the next queue.
+template <bool SMEM>
+__global__ void __launch_bounds__(SSSP_THREADS)
+sssp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__ adj,
+            const int *__restrict__ roots, int R_host, const int *R_dev,
+            unsigned long long *g_state, int *g_stamp, int *g_queue, int *parent,
+            const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
+            const int *skip_dev, unsigned long long *roots_counter) {
+  extern __shared__ unsigned long long smem_u64[];
+  __shared__ int s_cnt[3];
+  if (skip_dev && *skip_dev) return;
+  const int R = R_dev ? *R_dev : R_host;
+  if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
+  unsigned long long *state;
+  int *stamp, *qa, *qb;
+  if (SMEM) {
+    state = smem_u64;
+    stamp = reinterpret_cast<int *>(smem_u64 + V);
+    qa = stamp + V;
+    qb = qa + V;
+  } else {
+    size_t b = blockIdx.x;
+    state = g_state + b * (size_t)V;
+    stamp = g_stamp + b * (size_t)V;
+    qa = g_queue + b * 2 * (size_t)V;
+    qb = qa + V;
+  }
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
+  const unsigned long long NOLINK = (1ull << LB) - 1ull;
+  const unsigned long long DMAX = (~0ull) >> LB;
+  for (int v = threadIdx.x; v < V; v += blockDim.x) {
+    state[v] = ~0ull;
+    stamp[v] = -1;
+  }
+  int rid = 0;
+  __syncthreads();
+  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    const int z = roots[r];
+    if (threadIdx.x == 0) {
+      state[z] = NOLINK;  // distance 0, no parent link
+      qa[0] = z;
+      s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+    }
+    __syncthreads();
+    int ncur = 1, round = 0;
+    int *cur = qa, *nxt = qb;
+    while (ncur > 0) {
+      const int c = round % 3;
+      if (threadIdx.x == 0) s_cnt[(round + 1) % 3] = 0;
+      const int my_rid = rid + round;
+      for (int i = threadIdx.x; i < ncur; i += blockDim.x) {
+        const int w = cur[i];
+        unsigned long long kw;
+        if (SMEM) kw = *(volatile unsigned long long *)&state[w];
+        else kw = __ldcg(&state[w]);
+        const unsigned long long dw = kw >> LB;
+        const int kb = off[w], ke = off[w + 1];
+        for (int k = kb; k < ke; ++k) {
+          const int4 ent = __ldg(&adj[k]);
+          const unsigned long long cand = dw + (unsigned long long)(unsigned)ent.z;
+          if (cand >= DMAX) { atomicOr(status, ST_OVERFLOW); continue; }
+          const unsigned long long key = (cand << LB) | (unsigned long long)(unsigned)ent.x;
+          const unsigned long long old = atomicMin(&state[ent.y], key);
+          if ((old >> LB) > cand) {
+            if (atomicExch(&stamp[ent.y], my_rid) != my_rid) {
+              const int pos = atomicAdd(&s_cnt[c], 1);
+              nxt[pos] = ent.y;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      ncur = s_cnt[c];
+      int *t = cur; cur = nxt; nxt = t;
+      ++round;
+      if (round > V + 1) {  // cannot happen with link times >= 1; bounded anyway
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        break;
+      }
+    }
+    rid += round + 1;
+    __syncthreads();
+    int *prow = parent + (long long)r * V;
+    long long *drow = dist ? dist + (long long)r * V : nullptr;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+      const unsigned long long key = state[v];
+      const unsigned long long lk = key & NOLINK;
+      prow[v] = lk == NOLINK ? -1 : (int)lk;
+      if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
+      state[v] = ~0ull;
+    }
+    __syncthreads();
+  }
+}
+
+int sssp_max_smem_nodes() { return (200 * 1024) / 20; }
+
+static size_t sssp_smem_bytes(int V) { return (size_t)V * 20; }
+
+int sssp_blocks_per_sm(bool use_smem, int V) {
+  int n = 0;
+  if (use_smem) {
+    cudaFuncSetAttribute(sssp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sssp_smem_bytes(V));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_kernel<true>, SSSP_THREADS,
+                                                  sssp_smem_bytes(V));
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_kernel<false>, SSSP_THREADS, 0);
+  }
+  return n > 0 ? n : 1;
+}
+
+void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *roots, int R_host,
+                 const int *R_dev, int grid, bool use_smem, const SsspWork &w, int *parent,
+                 const int *parent_slot_dev, long long slot_stride, long long *dist,
+                 unsigned *status, cudaStream_t s, const int *skip_dev,
+                 unsigned long long *roots_counter) {
+  const int *off = direction == 0 ? g.in_off : g.out_off;
+  if (grid <= 0) return;
+  if (use_smem) {
+    size_t sm = sssp_smem_bytes(g.V);
+    cudaFuncSetAttribute(sssp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    sssp_kernel<true><<<grid, SSSP_THREADS, sm, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
+                                                     nullptr, nullptr, nullptr, parent,
+                                                     parent_slot_dev, slot_stride, dist, status, skip_dev,
+                                                     roots_counter);
+  } else {
+    sssp_kernel<false><<<grid, SSSP_THREADS, 0, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
+                                                     w.state, w.stamp, w.queue, parent,
+                                                     parent_slot_dev, slot_stride, dist, status,
+                                                     skip_dev, roots_counter);
+  }
+}
+
+// ============================================================================
+// all-or-nothing loading with truncation
+// ============================================================================
+
+__global__ void pack_head_q_kernel(int L, const int *__restrict__ head, const int *__restrict__ q,
+                                   int2 *__restrict__ hq) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x)
+    hq[a] = make_int2(head[a], q[a]);
+}
+
+void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStream_t s) {
+  if (g.L == 0) return;
+  pack_head_q_kernel<<<cdiv(g.L, 256), 256, 0, s>>>(g.L, g.head, q, head_q);
+}
+
+// One thread per item: walk origin -> root along the destination tree.  A
+// link is loaded iff the elapsed time at its tail is < dt_q; the walk ends
+// at the first node reached at >= dt_q (the stop node) or at the root.
+__global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *__restrict__ parent,
+                            const int *parent_slot_dev, long long slot_stride,
+                            const int *__restrict__ root_slot, const int *__restrict__ roots,
+                            long long n_host, const long long *n_dev, const int *__restrict__ root_idx,
+                            const int *__restrict__ src, const long long *__restrict__ amount,
+                            long long dt_q, unsigned long long *flow_fx, int *stop_out,
+                            unsigned *status) {
+  const long long n = n_dev ? *n_dev : n_host;
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int r = root_idx[k];
+    const int z = roots[r];
+    const int *par = parent + (long long)(root_slot ? root_slot[r] : r) * V;
+    const unsigned long long amt = (unsigned long long)amount[k];
+    int u = src[k];
+    long long elapsed = 0;
+    int steps = 0;
+    while (u != z) {
+      if (elapsed >= dt_q) break;
+      const int e = par[u];
+      if (e < 0) { atomicOr(status, ST_UNREACH); break; }
+      if (amt) atomicAdd(&flow_fx[e], amt);
+      const int2 hq = __ldg(&head_q[e]);
+      elapsed += hq.y;
+      u = hq.x;
+      if (++steps > V) { atomicOr(status, ST_TIMEOUT); break; }
+    }
+    if (stop_out) stop_out[k] = u;
+  }
+}
+
+static int link_grid(const GraphDev &g, long long n) {
+  long long want = (n + 255) / 256;
+  long long cap = (long long)g.num_sms * 16;
+  if (want > cap) want = cap;
+  return want < 1 ? 1 : (int)want;
+}
+
+void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const int *parent_slot_dev,
+                 long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
+                 const long long *n_items_dev, const int *root_idx, const int *src,
+                 const long long *amount, long long dt_q, unsigned long long *flow_fx, int *stop_out,
+                 unsigned *status, cudaStream_t s) {
+  long long n = n_items_dev ? (long long)g.num_sms * 16 * 256 : n_items_host;
+  if (n <= 0) return;
+  load_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, head_q, parent, parent_slot_dev, slot_stride,
+                                              root_slot, roots, n_items_host, n_items_dev, root_idx,
+                                              src, amount, dt_q, flow_fx, stop_out, status);
+}
+
+// Alg. 4 for one accepted AON j: the item's path on tree j is re-truncated
+// with the final link times (head_q_fin); its share RN(amount * w_j) loads
+// h and, if the walk stops before the root, joins the residual demand of the
+// next interval in the dense (root, node) accumulator.
+__global__ void residual_kernel(int V, const int2 *__restrict__ head_q_fin, const int *__restrict__ parent,
+                                const int *parent_slot_dev, long long slot_stride,
+                                const int *__restrict__ root_slot, const int *__restrict__ roots,
+                                const long long *n_dev, const int *__restrict__ root_idx,
+                                const int *__restrict__ src, const long long *__restrict__ amount,
+                                const double *weight_dev, long long dt_q, unsigned long long *h_fx,
+                                unsigned long long *dense, unsigned *status) {
+  const long long n = *n_dev;
+  const double w = *weight_dev;
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long amt = __double2ll_rn(mul(__ll2double_rn(amount[k]), w));
+    if (amt == 0) continue;
+    const int r = root_idx[k];
+    const int z = roots[r];
+    const int *par = parent + (long long)root_slot[r] * V;
+    int u = src[k];
+    long long elapsed = 0;
+    int steps = 0;
+    while (u != z) {
+      if (elapsed >= dt_q) break;
+      const int e = par[u];
+      if (e < 0) { atomicOr(status, ST_UNREACH); break; }
+      atomicAdd(&h_fx[e], (unsigned long long)amt);
+      const int2 hq = __ldg(&head_q_fin[e]);
+      elapsed += hq.y;
+      u = hq.x;
+      if (++steps > V) { atomicOr(status, ST_TIMEOUT); break; }
+    }
+    if (u != z) atomicAdd(&dense[(long long)r * V + u], (unsigned long long)amt);
+  }
+}
+
+void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *parent,
+                     const int *parent_slot_dev, long long slot_stride, const int *root_slot,
+                     const int *roots, const long long *n_items_dev, long long n_items_cap,
+                     const int *root_idx, const int *src, const long long *amount,
+                     const double *weight_dev, long long dt_q, unsigned long long *h_fx,
+                     unsigned long long *dense, unsigned *status, cudaStream_t s) {
+  if (n_items_cap <= 0) return;
+  residual_kernel<<<link_grid(g, n_items_cap), 256, 0, s>>>(
+      g.V, head_q_fin, parent, parent_slot_dev, slot_stride, root_slot, roots, n_items_dev, root_idx, src, amount, weight_dev,
+      dt_q, h_fx, dense, status);
+}
+
+// ============================================================================
+// link-parallel passes
+// ============================================================================
+
+__global__ void bpr_kernel(int L, const int *__restrict__ c0, const double *__restrict__ cap,
+                           double alpha, int beta, double dt_h, double quantum_s,
+                           const double *__restrict__ flow, double *cost_s, int *cost_q,
+                           unsigned *status) {
+  unsigned bad = 0;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
+    const double f = flow[a];
+    if (!isfinite(f)) bad |= ST_NONFINITE;
+    const LinkConst k = link_const(cap[a], dt_h, alpha, beta);
+    const double c = link_cost((double)c0[a], k.inv, alpha, beta, f);
+    if (cost_s) cost_s[a] = mul(c, quantum_s);
+    cost_q[a] = quantize(c, &bad);
+  }
+  if (bad) atomicOr(status, bad);
+}
+
+void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,
+                unsigned *status, cudaStream_t s) {
+  if (g.L == 0) return;
+  bpr_kernel<<<link_grid(g, g.L), LINK_THREADS, 0, s>>>(g.L, g.c0, g.cap, g.alpha, g.beta, dt_h,
+                                                        g.quantum_s, flow, cost_s, cost_q, status);
+}
+
+__global__ void link_const_kernel(int L, const double *__restrict__ cap, double dt_h, double alpha,
+                                  int beta, LinkConst *kc) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x)
+    kc[a] = link_const(cap[a], dt_h, alpha, beta);
+}
+
+void launch_link_const(const GraphDev &g, double dt_h, LinkConst *kc, cudaStream_t s) {
+  if (g.L == 0) return;
+  link_const_kernel<<<link_grid(g, g.L), LINK_THREADS, 0, s>>>(g.L, g.cap, dt_h, g.alpha, g.beta, kc);
+}
+
+__global__ void flow_from_fx_kernel(int L, const unsigned long long *fx, double *f) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x)
+    f[a] = fx64_to_double((long long)fx[a]);
+}
+
+void launch_flow_from_fx(int L, const unsigned long long *fx, double *f, cudaStream_t s) {
+  if (L == 0) return;
+  flow_from_fx_kernel<<<cdiv(L, 256), 256, 0, s>>>(L, fx, f);
+}
+
+void launch_fx_to_flow(int L, const unsigned long long *fx, double *out, cudaStream_t s) {
+  launch_flow_from_fx(L, fx, out, s);
+}
+
+__device__ __forceinline__ i128 shfl_down_i128(i128 v, int d) {
+  unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((u128)v >> 64);
+  lo = __shfl_down_sync(0xffffffffu, lo, d);
+  hi = __shfl_down_sync(0xffffffffu, hi, d);
+  return (i128)(((u128)hi << 64) | (u128)lo);
+}
+
+// Block-reduce acc[0..NSUM) into partials[blockIdx]; the last block to finish
+// adds all block partials (integer sums: any order gives the same value)
+// and stores them in out[0..NSUM).
+__device__ void reduce_sums(i128 (&acc)[NSUM], i128 *partials, unsigned *counter, i128 *out) {
+  __shared__ i128 s_w[LINK_THREADS / 32][NSUM];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 0; m < NSUM; ++m) {
+    i128 v = acc[m];
+    for (int d = 16; d > 0; d >>= 1) v += shfl_down_i128(v, d);
+    if (lane == 0) s_w[wid][m] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NSUM) {
+    i128 t = 0;
+    for (int w = 0; w < LINK_THREADS / 32; ++w) t += s_w[w][threadIdx.x];
+    partials[(size_t)blockIdx.x * NSUM + threadIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (threadIdx.x < NSUM) {
+      i128 t = 0;
+      for (unsigned b = 0; b < gridDim.x; ++b) {
+        const volatile unsigned long long *p =
+            reinterpret_cast<const volatile unsigned long long *>(&partials[(size_t)b * NSUM + threadIdx.x]);
+        t += (i128)(((u128)p[1] << 64) | (u128)p[0]);
+      }
+      out[threadIdx.x] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// One pass over the links evaluating the controller's plan: up to eight
+// step sizes, each one of phi (Beckmann sum, Eq. 6), phi' (exact slope) or
+// phi'' at t = f + alpha (g - f), plus optionally the gap sums
+// A = sum fx(q f) and B = sum q g (Alg. 9's three values generalised).
+__global__ void __launch_bounds__(LINK_THREADS)
+sweep_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict__ kc,
+             const double *__restrict__ f, const long long *__restrict__ g_fx,
+             const int *__restrict__ q, double alpha_bpr, int beta, Ctl *ctl, i128 *partials,
+             unsigned *counter, unsigned *status) {
+  __shared__ Plan plan;
+  if (threadIdx.x == 0) plan = ctl->plan;
+  __syncthreads();
+  i128 acc[NSUM];
+#pragma unroll
+  for (int m = 0; m < NSUM; ++m) acc[m] = 0;
+  unsigned bad = 0;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
+    const double fa = f[a];
+    const long long gfx = g_fx[a];
+    const double ga = fx64_to_double(gfx);
+    const double c0a = (double)c0[a];
+    const LinkConst k = kc[a];
+    if (plan.want_gap) {
+      const int qa = q[a];
+      acc[MAX_SLOTS] += fx_of(mul((double)qa, fa), &bad);
+      acc[MAX_SLOTS + 1] += (i128)qa * (i128)gfx;
+    }
+    const double d = sub(ga, fa);
+#pragma unroll
+    for (int m = 0; m < MAX_SLOTS; ++m) {
+      if (m < plan.n) {
+        const double t = step_flow(fa, ga, plan.alpha[m]);
+        double term;
+        if (plan.kind[m] == K_PHI) term = beckmann(c0a, k.inv, k.kb, beta, t);
+        else if (plan.kind[m] == K_DPHI) term = mul(d, link_cost(c0a, k.inv, alpha_bpr, beta, t));
+        else term = mul(mul(d, d), link_cost_dt(c0a, k.inv, alpha_bpr, beta, t));
+        acc[m] += fx_of(term, &bad);
+      }
+    }
+  }
+  if (bad) atomicOr(status, bad);
+  reduce_sums(acc, partials, counter, ctl->sums);
+}
+
+int sweep_grid(const GraphDev &g) {
+  long long want = ((long long)g.L + LINK_THREADS - 1) / LINK_THREADS;
+  long long cap = (long long)g.num_sms * 4;
+  if (want > cap) want = cap;
+  return want < 1 ? 1 : (int)want;
+}
+
+void launch_sweep(const GraphDev &g, const LinkConst *kc, const double *f, const long long *g_fx,
+                  const int *q, Ctl *ctl, i128 *partials, unsigned *counter, int grid,
+                  unsigned *status, cudaStream_t s) {
+  sweep_kernel<<<grid, LINK_THREADS, 0, s>>>(g.L, g.c0, kc, f, g_fx, q, g.alpha, g.beta, ctl,
+                                             partials, counter, status);
+}
+
+__global__ void __launch_bounds__(LINK_THREADS)
+objective_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict__ kc,
+                 const double *__restrict__ f, int beta, Ctl *ctl, i128 *partials,
+                 unsigned *counter, unsigned *status) {
+  __shared__ i128 out[NSUM];
+  i128 acc[NSUM];
+#pragma unroll
+  for (int m = 0; m < NSUM; ++m) acc[m] = 0;
+  unsigned bad = 0;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
+    const LinkConst k = kc[a];
+    acc[0] += fx_of(beckmann((double)c0[a], k.inv, k.kb, beta, f[a]), &bad);
+  }
+  if (bad) atomicOr(status, bad);
+  if (threadIdx.x == 0) out[0] = 0;
+  reduce_sums(acc, partials, counter, out);
+  if (threadIdx.x == 0 && out[0] != 0) ctl->objective = fx_to_double(out[0]);
+}
+
+void launch_objective(const GraphDev &g, const LinkConst *kc, const double *f, Ctl *ctl,
+                      i128 *partials, unsigned *counter, int grid, unsigned *status, cudaStream_t s) {
+  objective_kernel<<<grid, LINK_THREADS, 0, s>>>(g.L, g.c0, kc, f, g.beta, ctl, partials, counter,
+                                                 status);
+}
+
+// f <- f + alpha* (g - f) when the controller accepted the step
+__global__ void update_kernel(int L, const Ctl *ctl, double *f, const long long *__restrict__ g_fx) {
+  if (!ctl->do_update) return;
+  const double alpha = ctl->alpha_final;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x)
+    f[a] = step_flow(f[a], fx64_to_double(g_fx[a]), alpha);
+}
+
+void launch_update(const GraphDev &g, Ctl *ctl, double *f, const long long *g_fx, cudaStream_t s) {
+  if (g.L == 0) return;
+  update_kernel<<<link_grid(g, g.L), LINK_THREADS, 0, s>>>(g.L, ctl, f, g_fx);
+}
+
+__global__ void tape_record_kernel(int L, const Ctl *ctl, const int *q, const double *f, int *tape_q,
+                                   double *tape_alpha, double *tape_f, int cap) {
+  if (!ctl->do_update) return;
+  const int k = ctl->k;
+  if (k >= cap) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) tape_alpha[k] = ctl->alpha_final;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
+    tape_q[(long long)k * L + a] = q[a];
+    if (tape_f) tape_f[(long long)k * L + a] = f[a];
+  }
+}
+
+void launch_tape_record(const GraphDev &g, const Ctl *ctl, const int *q, const double *f,
+                        int *tape_q, double *tape_alpha, double *tape_f, int cap, cudaStream_t s) {
+  tape_record_kernel<<<link_grid(g, g.L > 0 ? g.L : 1), 256, 0, s>>>(g.L, ctl, q, f, tape_q,
+                                                                     tape_alpha, tape_f, cap);
+}
+
+// ============================================================================
+// device controller (one thread): Alg. 2 / 6 loop and the step rules
+// ============================================================================
+
+__device__ void plan_set(Ctl *c, int n, int kind, const double *alphas, int want_gap) {
+  c->plan.n = n;
+  c->plan.want_gap = want_gap;
+  for (int m = 0; m < MAX_SLOTS; ++m) {
+    c->plan.kind[m] = kind;
+    c->plan.alpha[m] = m < n ? alphas[m] : 0.0;
+  }
+}
+
+__device__ void plan_qn(Ctl *c, int want_gap) {
+  double a[3] = {sub(c->alpha, c->dx), c->alpha, add(c->alpha, c->dx)};
+  plan_set(c, 3, K_PHI, a, want_gap);
+}
+
+__device__ void finish_ls(Ctl *c, double alpha) {
+  c->alpha_final = alpha;
+  c->ls_passes += c->ls_pc;
+  if (c->stop == 1) {  // PAPER_OBJ: compare C(f) and C(f_new)
+    double a[2] = {0.0, alpha};
+    plan_set(c, 2, K_PHI, a, 0);
+    c->ls_state = LS_OBJ;
+    c->need_sweep = 1;
+  } else {
+    c->do_update = 1;
+    c->need_sweep = 0;
+    c->ls_state = LS_IDLE;
+  }
+}
+
+__device__ void sweep8_next_or_finish(Ctl *c) {
+  if (sub(c->hi, c->lo) >= c->t2 && c->ls_pc < c->ls_max) {
+    const double step = dvd(sub(c->hi, c->lo), 9.0);
+    double a[8];
+    for (int m = 0; m < 8; ++m) a[m] = add(c->lo, mul(step, (double)(m + 1)));
+    plan_set(c, 8, K_DPHI, a, 0);
+    c->ls_state = LS_SW_NEXT;
+    c->need_sweep = 1;
+  } else {
+    const double dlo = fx_to_double(c->Dlo), dhi = fx_to_double(c->Dhi);
+    double alpha = add(c->lo, mul(sub(c->hi, c->lo), dvd(-dlo, sub(dhi, dlo))));
+    if (alpha < c->lo) alpha = c->lo;
+    if (alpha > c->hi) alpha = c->hi;
+    finish_ls(c, alpha);
+  }
+}
+
+__global__ void ctl_init_kernel(Ctl *c, int step, int stop, int max_iter, int ls_max, double tol,
+                                double dx, double t1, double t2, int ring, long long n_host,
+                                const long long *n_dev) {
+  const long long n = n_dev ? *n_dev : n_host;
+  c->step = step; c->stop = stop; c->max_iter = max_iter; c->ls_max = ls_max;
+  c->tol = tol; c->dx = dx; c->t1 = t1; c->t2 = t2;
+  c->k = 1;
+  c->fw_continue = max_iter >= 1;
+  c->notconv = (max_iter < 1 && stop != 0) ? 1 : 0;
+  c->need_sweep = 0; c->do_update = 0; c->converged = 0;
+  c->iterations = 0; c->aon_calls = 1; c->ls_passes = 0;
+  c->ls_state = LS_IDLE; c->ls_pc = 0; c->l = 0; c->ex_it = 0;
+  c->rel_gap = __longlong_as_double(0x7ff8000000000000ll);
+  c->alpha = c->alpha_final = 0.0;
+  c->objective = 0.0;
+  c->plan.n = 0; c->plan.want_gap = 0;
+  c->ring = ring;
+  c->tree_slot = ring > 1 ? 1 : 0;
+  if (n <= 0) {  // no demand: zero flows, converged at once
+    c->fw_continue = 0; c->notconv = 0; c->converged = 1; c->aon_calls = 0;
+    c->rel_gap = 0.0;
+  }
+}
+
+void launch_ctl_init(Ctl *ctl, int step, int stop, int max_iter, int ls_max, double tol, double dx,
+                     double t1, double t2, int ring, long long n_items_host,
+                     const long long *n_items_dev, cudaStream_t s) {
+  ctl_init_kernel<<<1, 1, 0, s>>>(ctl, step, stop, max_iter, ls_max, tol, dx, t1, t2, ring,
+                                  n_items_host, n_items_dev);
+}
+
+// after the all-or-nothing of iteration k: set up the step rule
+__global__ void ctl_begin_kernel(Ctl *c, cudaGraphConditionalHandle h_ls, int use_cond) {
+  c->aon_calls++;
+  c->ls_pc = 0;
+  c->do_update = 0;
+  c->need_sweep = 0;
+  const int gap = c->stop == 2;
+  switch (c->step) {
+    case 0:  // MSA
+      c->alpha = dvd(1.0, add((double)c->k, 1.0));
+      if (gap) { plan_set(c, 0, K_PHI, nullptr, 1); c->ls_state = LS_GAPONLY; c->need_sweep = 1; }
+      else finish_ls(c, c->alpha);
+      break;
+    case 1:  // PAPER_QN3
+      c->alpha = dvd(2.0, add(2.0, (double)(c->k - 1)));
+      c->l = 1;
+      if (c->ls_max > 1) { plan_qn(c, gap); c->ls_state = LS_QN; c->need_sweep = 1; }
+      else if (gap) { plan_set(c, 0, K_PHI, nullptr, 1); c->ls_state = LS_GAPONLY; c->need_sweep = 1; }
+      else finish_ls(c, c->alpha);
+      break;
+    case 2: {  // SWEEP8
+      double a[8];
+      for (int m = 0; m < 8; ++m) a[m] = dvd((double)m, 7.0);
+      plan_set(c, 8, K_DPHI, a, gap);
+      c->ls_state = LS_SW_FIRST;
+      c->need_sweep = 1;
+      break;
+    }
+    default: {  // EXACT
+      double a[2] = {0.0, 1.0};
+      plan_set(c, 2, K_DPHI, a, gap);
+      c->ls_state = LS_EX_END;
+      c->need_sweep = 1;
+      break;
+    }
+  }
+  if (use_cond) cudaGraphSetConditional(h_ls, c->need_sweep ? 1u : 0u);
+}
+
+void launch_ctl_begin(Ctl *ctl, unsigned long long cond_ls, int use_cond, cudaStream_t s) {
+  ctl_begin_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond_ls, use_cond);
+}
+
+// after a sweep: consume the sums
+__global__ void ctl_step_kernel(Ctl *c, cudaGraphConditionalHandle h_ls, int use_cond) {
+  c->need_sweep = 0;
+  if (c->plan.want_gap) {
+    const i128 A = c->sums[MAX_SLOTS], B = c->sums[MAX_SLOTS + 1];
+    c->rel_gap = dvd(fx_to_double(A - B), fx_to_double(A));
+    c->plan.want_gap = 0;
+    if (c->rel_gap <= c->tol) {
+      c->converged = 1;
+      c->fw_continue = 0;
+      c->do_update = 0;
+      c->ls_state = LS_IDLE;
+      if (use_cond) cudaGraphSetConditional(h_ls, 0u);
+      return;
+    }
+  }
+  const i128 *S = c->sums;
+  switch (c->ls_state) {
+    case LS_GAPONLY:
+      finish_ls(c, c->alpha);
+      break;
+    case LS_QN: {
+      c->ls_pc++;
+      const double c0 = fx_to_double(S[1]);
+      const double d1 = dvd(fx_to_double(S[2] - S[0]), mul(2.0, c->dx));
+      const double d2 = dvd(fx_to_double(S[0] - 2 * S[1] + S[2]), mul(c->dx, c->dx));
+      if (fabs(d1) < mul(c->t1, fabs(c0))) { finish_ls(c, c->alpha); break; }
+      double an;
+      if (d2 > 0.0) an = sub(c->alpha, dvd(d1, d2));
+      else an = d1 < 0.0 ? 1.0 : 0.0;
+      if (an < 0.0) an = 0.0;
+      if (an > 1.0) an = 1.0;
+      if (fabs(sub(an, c->alpha)) < c->t2) { finish_ls(c, an); break; }
+      c->alpha = an;
+      c->l++;
+      if (c->l < c->ls_max) { plan_qn(c, 0); c->need_sweep = 1; }
+      else finish_ls(c, c->alpha);
+      break;
+    }
+    case LS_SW_FIRST: {
+      c->ls_pc++;
+      if (S[7] <= 0) { finish_ls(c, 1.0); break; }
+      if (S[0] >= 0) { finish_ls(c, 0.0); break; }
+      int ms = 1;
+      while (S[ms] < 0) ++ms;
+      c->lo = c->plan.alpha[ms - 1]; c->Dlo = S[ms - 1];
+      c->hi = c->plan.alpha[ms]; c->Dhi = S[ms];
+      sweep8_next_or_finish(c);
+      break;
+    }
+    case LS_SW_NEXT: {
+      c->ls_pc++;
+      int mf = 0;
+      while (mf < 8 && S[mf] < 0) ++mf;
+      if (mf == 8) { c->lo = c->plan.alpha[7]; c->Dlo = S[7]; }
+      else {
+        c->hi = c->plan.alpha[mf]; c->Dhi = S[mf];
+        if (mf > 0) { c->lo = c->plan.alpha[mf - 1]; c->Dlo = S[mf - 1]; }
+      }
+      sweep8_next_or_finish(c);
+      break;
+    }
+    case LS_EX_END: {
+      c->ls_pc += 2;
+      if (S[1] <= 0) { finish_ls(c, 1.0); break; }
+      if (S[0] >= 0) { finish_ls(c, 0.0); break; }
+      c->lo = 0.0; c->hi = 1.0; c->alpha = 0.5; c->ex_it = 0;
+      double a[2] = {0.5, 0.5};
+      plan_set(c, 2, K_DPHI, a, 0);
+      c->plan.kind[1] = K_DDPHI;
+      c->ls_state = LS_EX_NEWTON;
+      c->need_sweep = 1;
+      break;
+    }
+    case LS_EX_NEWTON: {
+      c->ls_pc++;
+      const i128 D = S[0];
+      const double H = fx_to_double(S[1]);
+      if (D == 0) { finish_ls(c, c->alpha); break; }
+      if (D < 0) c->lo = c->alpha; else c->hi = c->alpha;
+      double an = (H > 0.0) ? sub(c->alpha, dvd(fx_to_double(D), H)) : mul(0.5, add(c->lo, c->hi));
+      if (!(an > c->lo && an < c->hi)) an = mul(0.5, add(c->lo, c->hi));
+      if (fabs(sub(an, c->alpha)) < 1e-14 || sub(c->hi, c->lo) < 1e-15) { finish_ls(c, an); break; }
+      c->alpha = an;
+      c->ex_it++;
+      if (c->ex_it >= 200) { finish_ls(c, c->alpha); break; }
+      double a[2] = {an, an};
+      plan_set(c, 2, K_DPHI, a, 0);
+      c->plan.kind[1] = K_DDPHI;
+      c->need_sweep = 1;
+      break;
+    }
+    case LS_OBJ: {
+      const double rel = dvd(fabs(fx_to_double(S[0] - S[1])), fx_to_double(S[0]));
+      c->rel_gap = rel;
+      if (rel < c->tol) { c->converged = 1; c->fw_continue = 0; c->do_update = 0; }
+      else c->do_update = 1;
+      c->ls_state = LS_IDLE;
+      break;
+    }
+    default:
+      break;
+  }
+  if (use_cond) cudaGraphSetConditional(h_ls, c->need_sweep ? 1u : 0u);
+}
+
+void launch_ctl_step(Ctl *ctl, unsigned long long cond_ls, int use_cond, cudaStream_t s) {
+  ctl_step_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond_ls, use_cond);
+}
+
+// after the update of iteration k
+__global__ void ctl_end_kernel(Ctl *c, cudaGraphConditionalHandle h_fw, int use_cond) {
+  if (c->do_update) {
+    c->iterations = c->k;
+    c->k++;
+    if (c->k > c->max_iter) {
+      c->fw_continue = 0;
+      if (c->stop != 0) c->notconv = 1;
+    }
+  }
+  if (c->converged) c->fw_continue = 0;
+  c->tree_slot = c->k < c->ring - 1 ? c->k : c->ring - 1;
+  if (use_cond) cudaGraphSetConditional(h_fw, c->fw_continue ? 1u : 0u);
+}
+
+void launch_ctl_end(Ctl *ctl, unsigned long long cond_fw, int use_cond, cudaStream_t s) {
+  ctl_end_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond_fw, use_cond);
+}
+
+// w_j = alpha_j prod_{m > j} (1 - alpha_m), alpha_0 = 1 (Alg. 4 path weights)
+__global__ void path_weights_kernel(const Ctl *c, const double *tape_alpha, double *w) {
+  const int K = c->iterations;
+  double P = 1.0;
+  for (int j = K; j >= 0; --j) {
+    const double a = j == 0 ? 1.0 : tape_alpha[j];
+    w[j] = mul(a, P);
+    P = mul(P, sub(1.0, a));
+  }
+}
+
+void launch_path_weights(const Ctl *ctl, const double *tape_alpha, double *w, cudaStream_t s) {
+  path_weights_kernel<<<1, 1, 0, s>>>(ctl, tape_alpha, w);
+}
+
+__global__ void weight_select_kernel(const double *w, int j, double *dst) { *dst = w[j]; }
+
+void launch_weight_select(const double *w, int j, double *dst, cudaStream_t s) {
+  weight_select_kernel<<<1, 1, 0, s>>>(w, j, dst);
+}
+
+__global__ void fill_i32_kernel(int *p, long long n, int v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+void launch_fill_i32(int *p, long long n, int v, cudaStream_t s) {
+  if (n <= 0) return;
+  long long b = (n + 255) / 256;
+  if (b > 4096) b = 4096;
+  fill_i32_kernel<<<(int)b, 256, 0, s>>>(p, n, v);
+}
+
+// initial AON recorded as step 0 of the tape: q_0, alpha_0 = 1, f_0 = g_0
+__global__ void tape0_kernel(int L, const int *q, const double *f, int *tape_q, double *tape_alpha,
+                             double *tape_f) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) tape_alpha[0] = 1.0;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
+    tape_q[a] = q[a];
+    if (tape_f) tape_f[a] = f[a];
+  }
+}
+
+void launch_tape0(const GraphDev &g, const int *q, const double *f, int *tape_q, double *tape_alpha,
+                  double *tape_f, cudaStream_t s) {
+  tape0_kernel<<<link_grid(g, g.L > 0 ? g.L : 1), 256, 0, s>>>(g.L, q, f, tape_q, tape_alpha, tape_f);
+}
+
+// residual loop over the accepted AONs j = 0..K
+__global__ void res_begin_kernel(Ctl *c, cudaGraphConditionalHandle h, int use_cond) {
+  c->res_j = 0;
+  c->res_continue = c->aon_calls > 0;  // an interval without demand has nothing to re-walk
+  if (use_cond) cudaGraphSetConditional(h, c->res_continue ? 1u : 0u);
+}
+
+void launch_res_begin(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s) {
+  res_begin_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond, use_cond);
+}
+
+// tree j is still in ring slot j when j < ring - 1; otherwise it is rebuilt
+// into the last slot from the taped link times (copied to q_work here)
+__global__ void res_prep_kernel(Ctl *c, const double *w, const int *tape_q, int L, int *q_work) {
+  const int j = c->res_j;
+  const int stored = j < c->ring - 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->res_slot = stored ? j : c->ring - 1;
+    c->res_skip = stored;
+    c->w_cur = w[j];
+  }
+  if (!stored)
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x)
+      q_work[a] = tape_q[(long long)j * L + a];
+}
+
+void launch_res_prep(Ctl *ctl, const double *w, const int *tape_q, int L, int *q_work, cudaStream_t s) {
+  int b = (L + 255) / 256;
+  if (b > 2048) b = 2048;
+  if (b < 1) b = 1;
+  res_prep_kernel<<<b, 256, 0, s>>>(ctl, w, tape_q, L, q_work);
+}
+
+__global__ void res_next_kernel(Ctl *c, cudaGraphConditionalHandle h, int use_cond) {
+  c->res_j++;
+  c->res_continue = c->res_j <= c->iterations;
+  if (use_cond) cudaGraphSetConditional(h, c->res_continue ? 1u : 0u);
+}
+
+void launch_res_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s) {
+  res_next_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond, use_cond);
+}
+
+// h(i) row and the interval's statistics
+__global__ void store_interval_kernel(int L, const Ctl *c, const unsigned long long *h_fx,
+                                      double *rows, qdta_stats *stats, const long long *n_items) {
+  const int i = c->day_i;
+  double *row = rows + (long long)i * L;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x)
+    row[a] = fx64_to_double((long long)h_fx[a]);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && stats) {
+    qdta_stats st;
+    st.iterations = c->iterations;
+    st.aon_calls = c->aon_calls;
+    st.ls_passes = c->ls_passes;
+    st.converged = c->converged;
+    st.rel_gap = c->rel_gap;
+    st.objective = c->objective;
+    st.n_items = n_items ? *n_items : 0;
+    stats[i] = st;
+  }
+}
+
+void launch_store_interval(const GraphDev &g, const Ctl *ctl, const unsigned long long *h_fx,
+                           double *flow_out_rows, void *stats_rows, const long long *n_items_dev,
+                           cudaStream_t s) {
+  store_interval_kernel<<<link_grid(g, g.L > 0 ? g.L : 1), 256, 0, s>>>(
+      g.L, ctl, h_fx, flow_out_rows, (qdta_stats *)stats_rows, n_items_dev);
+}
+
+__global__ void day_next_kernel(Ctl *c, cudaGraphConditionalHandle h, int use_cond) {
+  c->day_i++;
+  c->day_continue = c->day_i < c->day_N;
+  if (use_cond) cudaGraphSetConditional(h, c->day_continue ? 1u : 0u);
+}
+
+void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s) {
+  day_next_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond, use_cond);
+}
+
+// original demand of the current interval into the dense accumulator
+__global__ void scatter_orig_kernel(int V, const Ctl *c, const OrigTable *tab,
+                                    unsigned long long *dense) {
+  const OrigTable t = tab[c->day_i];
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < t.n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long a = t.amount[k];
+    if (a) atomicAdd(&dense[(long long)t.root_idx[k] * V + t.src[k]], (unsigned long long)a);
+  }
+}
+
+void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab, long long max_n,
+                         unsigned long long *dense, cudaStream_t s) {
+  scatter_orig_kernel<<<link_grid(g, max_n > 0 ? max_n : 1), 256, 0, s>>>(g.V, ctl, tab, dense);
+}
+
+// ============================================================================
+// residual-demand merge: dense (root, node) accumulator -> sorted items
+// ============================================================================
+
+__global__ void scatter_items_kernel(int V, long long n, const int *root_idx, const int *src,
+                                     const long long *amount, unsigned long long *dense) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long a = amount[k];
+    if (a) atomicAdd(&dense[(long long)root_idx[k] * V + src[k]], (unsigned long long)a);
+  }
+}
+
+void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, const int *src,
+                          const long long *amount, unsigned long long *dense, cudaStream_t s) {
+  if (n <= 0) return;
+  scatter_items_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, n, root_idx, src, amount, dense);
+}
+
+constexpr int COMPACT_TILE = 4096;
+
+__global__ void compact_count_kernel(long long total, const unsigned long long *dense, int *blk_count) {
+  __shared__ int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * COMPACT_TILE;
+  int c = 0;
+  for (int i = threadIdx.x; i < COMPACT_TILE; i += blockDim.x) {
+    const long long idx = base + i;
+    if (idx < total && dense[idx] != 0ull) ++c;
+  }
+  atomicAdd(&s, c);
+  __syncthreads();
+  if (threadIdx.x == 0) blk_count[blockIdx.x] = s;
+}
+
+__global__ void compact_scan_kernel(int nblk, const int *blk_count, long long *blk_off, long long cap,
+                                    long long *n_out, unsigned *status) {
+  // single block, 1024 threads: chunked exclusive scan
+  __shared__ long long s_part[1024];
+  const int per = (nblk + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  long long t = 0;
+  for (int i = 0; i < per; ++i) if (b0 + i < nblk) t += blk_count[b0 + i];
+  s_part[threadIdx.x] = t;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    long long v = threadIdx.x >= d ? s_part[threadIdx.x - d] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  long long run = s_part[threadIdx.x] - t;
+  for (int i = 0; i < per; ++i) {
+    if (b0 + i < nblk) { blk_off[b0 + i] = run; run += blk_count[b0 + i]; }
+  }
+  if (threadIdx.x == 1023) {
+    long long total = s_part[1023];
+    if (total > cap) { atomicOr(status, ST_CAPACITY); total = cap; }
+    *n_out = total;
+  }
+}
+
+// ordered write of the nonzero entries of each tile (root-major, node-minor)
+__global__ void compact_write_kernel(long long total, int V, unsigned long long *dense,
+                                     const long long *blk_off, long long cap, int *root_idx,
+                                     int *src, long long *amount) {
+  __shared__ int s_warp[32];
+  const long long base = (long long)blockIdx.x * COMPACT_TILE;
+  long long out = blk_off[blockIdx.x];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c0 = 0; c0 < COMPACT_TILE; c0 += blockDim.x) {
+    const long long idx = base + c0 + threadIdx.x;
+    unsigned long long v = 0ull;
+    if (idx < total) v = dense[idx];
+    const bool nz = v != 0ull;
+    const unsigned m = __ballot_sync(0xffffffffu, nz);
+    if (lane == 0) s_warp[wid] = __popc(m);
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < nw; ++w) { if (w < wid) before += s_warp[w]; all += s_warp[w]; }
+    if (nz) {
+      const long long pos = out + before + __popc(m & ((1u << lane) - 1u));
+      if (pos < cap) {
+        root_idx[pos] = (int)(idx / V);
+        src[pos] = (int)(idx % V);
+        amount[pos] = (long long)v;
+      }
+      dense[idx] = 0ull;
+    }
+    out += all;
+    __syncthreads();
+  }
+}
+
+void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *blk_count,
+                    long long *blk_off, long long cap, int *root_idx, int *src, long long *amount,
+                    long long *n_out_dev, unsigned *status, cudaStream_t s) {
+  const long long total = (long long)R * g.V;
+  const int nblk = cdiv(total > 0 ? total : 1, COMPACT_TILE);
+  compact_count_kernel<<<nblk, 256, 0, s>>>(total, dense, blk_count);
+  compact_scan_kernel<<<1, 1024, 0, s>>>(nblk, blk_count, blk_off, cap, n_out_dev, status);
+  compact_write_kernel<<<nblk, 256, 0, s>>>(total, g.V, dense, blk_off, cap, root_idx, src, amount);
+}
+
+// roots with at least one item, in root order; root_slot maps a root index
+// to its row in the parent arrays (or -1)
+__global__ void active_roots_kernel(int R, const long long *n_dev, long long cap, const int *root_idx,
+                                    const int *zone_nodes, int *flag, int *active, int *root_slot,
+                                    int *n_active) {
+  // single block
+  for (int r = threadIdx.x; r < R; r += blockDim.x) flag[r] = 0;
+  __syncthreads();
+  long long n = *n_dev;
+  if (n > cap) n = cap;
+  for (long long k = threadIdx.x; k < n; k += blockDim.x) flag[root_idx[k]] = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int r = 0; r < R; ++r) {
+      if (flag[r]) { active[c] = zone_nodes[r]; root_slot[r] = c; ++c; }
+      else root_slot[r] = -1;
+    }
+    *n_active = c;
+  }
+}
+
+void launch_active_roots(int R, const long long *n_items_dev, long long cap_items, const int *root_idx,
+                         const int *zone_nodes, int *flag, int *active_roots, int *root_slot,
+                         int *n_active_dev, cudaStream_t s) {
+  active_roots_kernel<<<1, 1024, 0, s>>>(R, n_items_dev, cap_items, root_idx, zone_nodes, flag,
+                                         active_roots, root_slot, n_active_dev);
+}
+
+// ============================================================================
+// adjoint
+// ============================================================================
+
+// mu = sum lam (g - f_prev), H = sum (g - f_prev)^2 c'(t)   (double, fixed order)
+__global__ void __launch_bounds__(LINK_THREADS)
+adj_reduce_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict__ kc, double alpha_bpr,
+                  int beta, const double *lam, const double *fprev, const long long *g_fx,
+                  double alpha, int implicit, double *partials, double *out2) {
+  __shared__ double s_mu[LINK_THREADS / 32], s_h[LINK_THREADS / 32];
+  double mu = 0.0, H = 0.0;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
+    const double gg = fx64_to_double(g_fx[a]);
+    const double d = sub(gg, fprev[a]);
+    mu = add(mu, mul(lam[a], d));
+    if (implicit) {
+      const double t = step_flow(fprev[a], gg, alpha);
+      H = add(H, mul(mul(d, d), link_cost_dt((double)c0[a], kc[a].inv, alpha_bpr, beta, t)));
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    mu = add(mu, __shfl_down_sync(0xffffffffu, mu, d));
+    H = add(H, __shfl_down_sync(0xffffffffu, H, d));
+  }
+  if ((threadIdx.x & 31) == 0) { s_mu[threadIdx.x >> 5] = mu; s_h[threadIdx.x >> 5] = H; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < LINK_THREADS / 32; ++w) { a = add(a, s_mu[w]); b = add(b, s_h[w]); }
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void adj_finish_kernel(int nblk, const double *partials, double *out2) {
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < nblk; ++i) { a = add(a, partials[2 * i]); b = add(b, partials[2 * i + 1]); }
+  out2[0] = a;
+  out2[1] = b;
+}
+
+void launch_adj_reduce(const GraphDev &g, const LinkConst *kc, const double *lam, const double *fprev,
+                       const long long *g_fx, double alpha, int implicit, double *partials, double *out2,
+                       int grid, cudaStream_t s) {
+  adj_reduce_kernel<<<grid, LINK_THREADS, 0, s>>>(g.L, g.c0, kc, g.alpha, g.beta, lam, fprev, g_fx,
+                                                  alpha, implicit, partials, out2);
+  adj_finish_kernel<<<1, 1, 0, s>>>(grid, partials, out2);
+}
+
+// g_bar = alpha lam - mu dalpha/dg, lam_prev = (1 - alpha) lam - mu dalpha/df,
+// dcap += -mu dalpha/dC, with dalpha/dtheta = -(d phi'/d theta) / H
+__global__ void adj_update_kernel(int L, const int *__restrict__ c0, const double *__restrict__ cap,
+                                  const LinkConst *__restrict__ kc, double alpha_bpr, int beta,
+                                  const double *lam, const double *fprev, const long long *g_fx,
+                                  double alpha, int implicit, const double *muH, double *gbar,
+                                  double *lam_prev, double *dcap) {
+  const double mu = muH[0], H = muH[1];
+  const int imp = implicit && H > 0.0;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
+    const double la = lam[a];
+    double gb = mul(alpha, la);
+    double lp = mul(sub(1.0, alpha), la);
+    if (imp) {
+      const double gg = fx64_to_double(g_fx[a]);
+      const double fp = fprev[a];
+      const double d = sub(gg, fp);
+      const double t = step_flow(fp, gg, alpha);
+      const double c0a = (double)c0[a];
+      const double c = link_cost(c0a, kc[a].inv, alpha_bpr, beta, t);
+      const double cp = link_cost_dt(c0a, kc[a].inv, alpha_bpr, beta, t);
+      const double r = dvd(mu, H);
+      gb = sub(gb, mul(r, add(c, mul(mul(alpha, d), cp))));
+      lp = sub(lp, mul(r, add(-c, mul(mul(sub(1.0, alpha), d), cp))));
+      // d c / d C = -c0 alpha beta x^beta / C
+      const double x = mul(t, kc[a].inv);
+      const double dcdC = -dvd(mul(mul(mul(c0a, alpha_bpr), (double)beta), powi(x, beta)), cap[a]);
+      dcap[a] = sub(dcap[a], mul(r, mul(d, dcdC)));
+    }
+    gbar[a] = gb;
+    lam_prev[a] = lp;
+  }
+}
+
+void launch_adj_update(const GraphDev &g, const LinkConst *kc, const double *lam, const double *fprev,
+                       const long long *g_fx, double alpha, int implicit, const double *muH,
+                       double *gbar, double *lam_prev, double *dcap, cudaStream_t s) {
+  if (g.L == 0) return;
+  adj_update_kernel<<<link_grid(g, g.L), LINK_THREADS, 0, s>>>(g.L, g.c0, g.cap, kc, g.alpha, g.beta,
+                                                               lam, fprev, g_fx, alpha, implicit, muH,
+                                                               gbar, lam_prev, dcap);
+}
+
+// path-sum gather (transpose of the truncated loading): dd[k] += sum of
+// gbar over the links item k loads on this tree
+__global__ void gather_kernel(int V, const int2 *__restrict__ head_q, const int *__restrict__ parent,
+                              const int *__restrict__ roots, long long n, const int *__restrict__ root_idx,
+                              const int *__restrict__ src, long long dt_q, const double *__restrict__ gbar,
+                              double *dd, unsigned *status) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int r = root_idx[k];
+    const int z = roots[r];
+    const int *par = parent + (long long)r * V;
+    int u = src[k];
+    long long elapsed = 0;
+    double acc = 0.0;
+    int steps = 0;
+    while (u != z && elapsed < dt_q) {
+      const int e = par[u];
+      if (e < 0) { atomicOr(status, ST_UNREACH); break; }
+      acc = add(acc, gbar[e]);
+      const int2 hq = __ldg(&head_q[e]);
+      elapsed += hq.y;
+      u = hq.x;
+      if (++steps > V) { atomicOr(status, ST_TIMEOUT); break; }
+    }
+    dd[k] = add(dd[k], acc);
+  }
+}
+
+void launch_gather(const GraphDev &g, const int2 *head_q, const int *parent, const int *roots,
+                   long long n_items, const int *root_idx, const int *src, long long dt_q,
+                   const double *gbar, double *dd, unsigned *status, cudaStream_t s) {
+  if (n_items <= 0) return;
+  gather_kernel<<<link_grid(g, n_items), 256, 0, s>>>(g.V, head_q, parent, roots, n_items, root_idx,
+                                                      src, dt_q, gbar, dd, status);
+}
+
+}  // namespace qdta

@@ -1,0 +1,286 @@
+"""CUDA path (through the C ABI) against the CPU oracle on identical inputs.
+
+Integer work (costs, distances, parents, loaded flows, stop nodes, merged
+residual items) must be bit-exact; the FW iteration is bit-exact too because
+every link sum is an exact fixed-point sum and every FP64 operation is
+rounded in the same order on both sides.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_12911_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2104_12911_gb300 import qdta as Q  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def T(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(DEV)
+
+
+@pytest.fixture(scope="module")
+def small():
+    inst = synth.config_small(0)
+    return inst, Q.Graph(inst.net), oracle.OracleGraph(inst.net)
+
+
+@pytest.fixture(scope="module")
+def mid():
+    # 110 x 110 grid: 12,100 nodes, above the shared-memory SSSP limit
+    net = synth.grid_network(110, 5, freeways=True)
+    zones = synth.pick_zones(net, 96, 5)
+    trips = synth.sample_trips(synth.gravity_weights(net, zones, 5, 4000.0), 30000, 6)
+    dem = synth.demand_from_matrix(zones, trips)
+    return net, dem, Q.Graph(net), oracle.OracleGraph(net)
+
+
+# ---------------------------------------------------------------------------
+def test_bpr_bit_exact(small):
+    inst, g, og = small
+    rng = np.random.default_rng(0)
+    L = og.n_links
+    f = rng.uniform(0, 900, L) * (rng.random(L) < 0.8)
+    f[:5] = [0.0, 1e-300, 1e6, 3.5, 800.0]
+    for dt in (900.0, 300.0, 3600.0):
+        q_o, c_o, rc = oracle.bpr(og, f, dt)
+        q_g, c_g = Q.qdta_bpr_costs(g, T(f, np.float64), dt, want_cost_s=True)
+        np.testing.assert_array_equal(q_g.cpu().numpy(), q_o)
+        np.testing.assert_array_equal(c_g.cpu().numpy(), c_o)
+
+
+def test_bpr_nonfinite_is_reported(small):
+    inst, g, og = small
+    f = np.zeros(og.n_links)
+    f[3] = np.nan
+    with pytest.raises(Q.QdtaError) as e:
+        Q.qdta_bpr_costs(g, T(f, np.float64), 900.0)
+    assert e.value.code == Q.QDTA_ENONFINITE
+
+
+@pytest.mark.parametrize("direction", [Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT])
+def test_sssp_small_all_zones(small, direction):
+    inst, g, og = small
+    rng = np.random.default_rng(1)
+    for trial in range(3):
+        q = inst.net.fftime_q if trial == 0 else rng.integers(1, 5000, og.n_links).astype(np.int32)
+        roots = inst.zones
+        p_o, d_o = oracle.sssp(og, q, roots, direction)
+        p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, want_dist=True)
+        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_sssp_random_graphs_with_ties(seed):
+    rng = np.random.default_rng(seed)
+    V = int(rng.integers(2, 300))
+    net = synth.random_graph(V, int(rng.integers(0, 4 * V)), seed, max_q=3, equal_costs=(seed % 2 == 0))
+    g, og = Q.Graph(net), oracle.OracleGraph(net)
+    roots = np.arange(V, dtype=np.int32) if V < 64 else rng.choice(V, 64, replace=False).astype(np.int32)
+    for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
+        p_o, d_o = oracle.sssp(og, net.fftime_q, roots, direction)
+        p_g, d_g = Q.qdta_sssp_batch(g, T(net.fftime_q, np.int32), T(roots, np.int32), direction, True)
+        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
+def test_sssp_unreachable_nodes():
+    # 0 -> 1 -> 2, node 3 isolated: unreachable rows keep -1 / INF
+    net = synth.Network(n_nodes=4, tail=np.array([0, 1], np.int32), head=np.array([1, 2], np.int32),
+                        fftime_q=np.array([5, 7], np.int32), capacity=np.ones(2) * 100,
+                        length_m=np.zeros(2), link_class=np.zeros(2, np.int8), x=np.zeros(4), y=np.zeros(4))
+    g, og = Q.Graph(net), oracle.OracleGraph(net)
+    roots = np.array([2, 3, 0], np.int32)
+    p_o, d_o = oracle.sssp(og, net.fftime_q, roots)
+    p_g, d_g = Q.qdta_sssp_batch(g, T(net.fftime_q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, True)
+    np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+    np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
+def test_sssp_global_memory_variant(mid):
+    net, dem, g, og = mid
+    rng = np.random.default_rng(2)
+    q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
+    roots = rng.choice(net.n_nodes, 40, replace=False).astype(np.int32)
+    p_o, d_o = oracle.sssp(og, q, roots)
+    p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, True)
+    np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+    np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
+def test_empty_batches(small):
+    inst, g, og = small
+    p, d = Q.qdta_sssp_batch(g, T(inst.net.fftime_q, np.int32), T(np.zeros(0), np.int32))
+    assert p.shape == (0, og.n_nodes)
+    od = Q.DeviceOD(T(inst.zones, np.int32), T([], np.int32), T([], np.int32), T([], np.int64))
+    flow, _ = Q.qdta_load_aon(g, T(inst.net.fftime_q, np.int32), p, od, 90000)
+    assert int(flow.abs().sum()) == 0
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dt_q", [0, 1, 20000, 90000, np.iinfo(np.int64).max])
+def test_load_bit_exact(small, dt_q):
+    inst, g, og = small
+    dem = synth.random_demand(inst.net, 64, 3000, 7, fractional=True)
+    rng = np.random.default_rng(3)
+    q = (inst.net.fftime_q * rng.uniform(1, 4, og.n_links)).astype(np.int32)
+    par_o, _ = oracle.sssp(og, q, dem.roots, want_dist=False)
+    f_o, s_o, rc = oracle.load(og, q, par_o, oracle.OracleOD.of(dem), dt_q)
+    assert rc == 0
+    qd = T(q, np.int32)
+    par_g, _ = Q.qdta_sssp_batch(g, qd, T(dem.roots, np.int32))
+    f_g, s_g = Q.qdta_load_aon(g, qd, par_g, Q.DeviceOD.of(dem), dt_q, want_stop=True)
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    np.testing.assert_array_equal(s_g.cpu().numpy(), s_o)
+
+
+def test_load_unreachable_is_reported():
+    net = synth.Network(n_nodes=3, tail=np.array([0, 1], np.int32), head=np.array([1, 0], np.int32),
+                        fftime_q=np.array([5, 7], np.int32), capacity=np.ones(2) * 100,
+                        length_m=np.zeros(2), link_class=np.zeros(2, np.int8), x=np.zeros(3), y=np.zeros(3))
+    g = Q.Graph(net)
+    roots = T([2], np.int32)
+    par, _ = Q.qdta_sssp_batch(g, T(net.fftime_q, np.int32), roots)
+    od = Q.DeviceOD(roots, T([0], np.int32), T([0], np.int32), T([1 << 32], np.int64))
+    with pytest.raises(Q.QdtaError) as e:
+        Q.qdta_load_aon(g, T(net.fftime_q, np.int32), par, od, 100)
+    assert e.value.code == Q.QDTA_EUNREACH
+
+
+# ---------------------------------------------------------------------------
+def _fg(small, seed=0):
+    inst, g, og = small
+    rng = np.random.default_rng(seed)
+    od = oracle.OracleOD.of(inst.demand[0])
+    f, st, rc = oracle.assign_interval(og, od, 900.0, oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 3))
+    q, _, _ = oracle.bpr(og, f, 900.0)
+    par, _ = oracle.sssp(og, q, od.roots, want_dist=False)
+    gfx, _, _ = oracle.load(og, q, par, od, 90000)
+    return f, gfx
+
+
+@pytest.mark.parametrize("step", ["paper_qn3", "sweep8", "exact", "msa"])
+@pytest.mark.parametrize("k", [1, 4])
+def test_line_search_bit_exact(small, step, k):
+    inst, g, og = small
+    f, gfx = _fg(small)
+    p = oracle.make_params(Q.STEP[step], oracle.STOP_NONE, 20)
+    a_o, n_o, rc = oracle.line_search(og, f, gfx, 900.0, k, p)
+    a_g, n_g = Q.qdta_line_search(g, T(f, np.float64), T(gfx, np.int64), 900.0, k,
+                                  Q.make_params(step, "none", 20))
+    assert a_g == a_o and n_g == n_o
+
+
+# ---------------------------------------------------------------------------
+CASES = [("msa", "none", 20, 1e-4), ("sweep8", "rel_gap", 300, 1e-4), ("paper_qn3", "rel_gap", 300, 1e-4),
+         ("exact", "rel_gap", 60, 1e-3), ("sweep8", "paper_obj", 300, 1e-4), ("msa", "rel_gap", 15, 1e-4)]
+
+
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+@pytest.mark.parametrize("step,stop,it,tol", CASES)
+def test_assign_interval_bit_exact(small, schedule, step, stop, it, tol):
+    inst, g, og = small
+    od = oracle.OracleOD.of(inst.demand[0])
+    f_o, st_o, rc_o = oracle.assign_interval(og, od, 900.0,
+                                             oracle.make_params(Q.STEP[step], Q.STOP[stop], it, tol))
+    f_g, st_g, rc_g, _ = Q.qdta_assign_interval(g, Q.DeviceOD.of(inst.demand[0]), 900.0,
+                                                 Q.make_params(step, stop, it, tol, schedule=schedule))
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    for key in ("iterations", "aon_calls", "ls_passes", "converged", "objective"):
+        assert st_g[key] == st_o[key], key
+    if not np.isnan(st_o["rel_gap"]):
+        assert st_g["rel_gap"] == st_o["rel_gap"]
+    assert (rc_g == Q.QDTA_ENOTCONV) == (rc_o == oracle.NOTCONV)
+
+
+def test_assign_interval_mid_network(mid):
+    net, dem, g, og = mid
+    od = oracle.OracleOD.of(dem)
+    p = (Q.STEP["sweep8"], Q.STOP["rel_gap"], 6, 1e-4)
+    f_o, st_o, _ = oracle.assign_interval(og, od, 900.0, oracle.make_params(*p))
+    f_g, st_g, _, _ = Q.qdta_assign_interval(g, Q.DeviceOD.of(dem), 900.0,
+                                              Q.make_params("sweep8", "rel_gap", 6, 1e-4, schedule="graph"))
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    assert st_g["ls_passes"] == st_o["ls_passes"]
+
+
+def test_empty_interval(small):
+    inst, g, og = small
+    od = Q.DeviceOD(T(inst.zones, np.int32), T([], np.int32), T([], np.int32), T([], np.int64))
+    for schedule in ("plain", "graph"):
+        f, st, rc, _ = Q.qdta_assign_interval(g, od, 900.0, Q.make_params(schedule=schedule))
+        assert float(f.abs().sum()) == 0.0 and st["converged"] == 1 and st["aon_calls"] == 0
+
+
+# ---------------------------------------------------------------------------
+def _day_case(n_int=6, trips=40000):
+    base = synth.config_small(0)
+    return synth.scaled_day(base, trips, n_intervals=n_int, seed=11)
+
+
+@pytest.mark.parametrize("step,stop,it", [("msa", "none", 8), ("sweep8", "rel_gap", 80)])
+def test_run_day_bit_exact(step, stop, it):
+    day = _day_case()
+    days = [d for d in day.demand]
+    og = oracle.OracleGraph(day.net)
+    f_o, st_o, nit_o, rn_o, rc_o = oracle.run_day(og, day.zones, days, 900.0,
+                                                  oracle.make_params(Q.STEP[step], Q.STOP[stop], it))
+    g = Q.Graph(day.net)
+    zones = T(day.zones, np.int32)
+    dd = [Q.DeviceOD(zones, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
+    f_g, st_g, rc_g, resid = Q.qdta_run_day(g, dd, 900.0, Q.make_params(step, stop, it), resid_capacity=1 << 20)
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    for i in range(len(days)):
+        assert st_g[i]["n_items"] == nit_o[i]
+        for key in ("iterations", "aon_calls", "ls_passes", "converged"):
+            assert st_g[i][key] == st_o[i][key], (i, key)
+    assert resid[0].shape[0] == rn_o
+
+
+def test_run_day_worked_example():
+    ff = [600.0, 300.0, 600.0, 600.0]
+    net = synth.chain_network(ff, [200.0, 150.0, 200.0, 200.0])
+    g = Q.Graph(net)
+    zones = T([3, 4], np.int32)
+    fx = lambda v: int(round(v * (1 << 32)))
+    dd = [Q.DeviceOD(zones, T([0], np.int32), T([0], np.int32), T([fx(43.75)], np.int64)),
+          Q.DeviceOD(zones, T([1], np.int32), T([2], np.int32), T([fx(12.5)], np.int64)),
+          Q.DeviceOD(zones, T([], np.int32), T([], np.int32), T([], np.int64)),
+          Q.DeviceOD(zones, T([], np.int32), T([], np.int32), T([], np.int64))]
+    f, st, rc, _ = Q.qdta_run_day(g, dd, 900.0, Q.make_params("sweep8", "rel_gap", 50))
+    f = f.cpu().numpy()
+    np.testing.assert_array_equal(f[0], [43.75, 43.75, 0, 0])
+    np.testing.assert_array_equal(f[1], [0, 0, 56.25, 12.5])
+    assert [s["n_items"] for s in st] == [1, 2, 0, 0]
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("step", ["exact", "msa"])
+def test_backward_matches_oracle(step):
+    net = synth.grid_network(12, 4)
+    zones = synth.pick_zones(net, 10, 4)
+    dem = synth.demand_from_matrix(zones, synth.gravity_fixed_pairs(net, zones, 3000, 1500.0))
+    og = oracle.OracleGraph(net)
+    od = oracle.OracleOD.of(dem)
+    p = oracle.make_params(Q.STEP[step], oracle.STOP_NONE, 10)
+    f_o, st_o, rc, tape_o = oracle.assign_interval(og, od, 600.0, p, tape=True)
+    g = Q.Graph(net)
+    dod = Q.DeviceOD.of(dem)
+    f_g, st_g, rc, tape = Q.qdta_assign_interval(g, dod, 600.0, Q.make_params(step, "none", 10, record_tape=True))
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    rng = np.random.default_rng(0)
+    S = rng.choice(og.n_links, og.n_links // 10, replace=False)
+    dL = np.zeros(og.n_links)
+    dL[S] = 2 * (f_o[S] - f_o[S] * rng.lognormal(0, 0.3, S.shape[0]))
+    dd_o, dc_o, _ = oracle.backward(og, od, 600.0, Q.STEP[step], tape_o, dL)
+    dd_g, dc_g = Q.qdta_backward(tape, T(dL, np.float64))
+    np.testing.assert_allclose(dd_g.cpu().numpy(), dd_o, rtol=1e-9, atol=1e-12 * np.abs(dd_o).max())
+    np.testing.assert_allclose(dc_g.cpu().numpy(), dc_o, rtol=1e-9, atol=1e-12 * max(np.abs(dc_o).max(), 1e-300))

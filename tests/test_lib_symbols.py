@@ -1,0 +1,48 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point declared in include/qdta.h (no compute calls here)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "qdta.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qdta_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for want in ("qdta_graph_create", "qdta_sssp_batch", "qdta_load_aon", "qdta_bpr_costs",
+                 "qdta_line_search", "qdta_assign_interval", "qdta_run_day", "qdta_backward"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2104_12911_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.qdta_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.qdta_version()
+
+
+def test_library_rejects_bad_graphs_without_touching_a_gpu():
+    from paper_2104_12911_gb300 import qdta as Q
+    import numpy as np
+    lib = Q.lib()
+    # unsorted links are rejected before any device call
+    tail = np.array([1, 0], np.int32)
+    head = np.array([0, 1], np.int32)
+    ff = np.array([1, 1], np.int32)
+    cap = np.array([1.0, 1.0])
+    d = Q.GraphDesc(2, 2, tail.ctypes.data, head.ctypes.data, ff.ctypes.data, cap.ctypes.data, 0.15, 4, 0.01)
+    h = ctypes.c_void_p()
+    assert lib.qdta_graph_create(ctypes.byref(d), 0, ctypes.byref(h)) == Q.QDTA_EINVAL
+    assert b"sorted" in lib.qdta_last_error()
+    d.beta = 0
+    assert lib.qdta_graph_create(ctypes.byref(d), 0, ctypes.byref(h)) == Q.QDTA_EINVAL
