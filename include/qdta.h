@@ -136,6 +136,8 @@ typedef struct {
   double load_ms;
   int64_t sweep_launches;
   double sweep_ms;
+  int64_t kernel_launches;  /* all kernels this library launched (process-wide, any schedule;
+                               graph schedules count each captured kernel once) */
 } qdta_profile;
 
 /* ---------------------------------------------------------------------- */

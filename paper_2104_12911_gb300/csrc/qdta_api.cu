@@ -335,6 +335,7 @@ extern "C" int qdta_profile_read(qdta_graph *g, qdta_profile *out) {
   unsigned long long roots = 0;
   if (g->prof_roots) CK(cudaMemcpy(&roots, g->prof_roots, 8, cudaMemcpyDeviceToHost));
   g->prof.sssp_roots = (int64_t)roots;
+  g->prof.kernel_launches = launch_count();
   *out = g->prof;
   return QDTA_OK;
 }
@@ -488,6 +489,8 @@ static int solver_alloc(Solver &S, const std::string &tag, int ring, bool tape_f
   S.tape_f = nullptr;
   if (tape_f) RC(ws_get(g, tag + ".tape_f", (size_t)S.tape_cap * L, &S.tape_f));
   CK(cudaMemsetAsync(S.counter, 0, 16, S.s));
+  SsspWork w;
+  RC(sssp_work(g, sssp_grid(g, S.R_cap), &w));  // nothing is allocated while capturing
   return QDTA_OK;
 }
 
@@ -890,6 +893,67 @@ static int day_interval_plain(Day &D, double *flow_out) {
   return QDTA_OK;
 }
 
+// the whole day as one CUDA graph: WHILE(interval) { merge + initial AON;
+// WHILE(FW step) { head; WHILE(line-search sweep) {...}; tail }; residual
+// head; WHILE(accepted AON j) { re-walk }; store }
+static int day_graph(Day &D, double *flow_out) {
+  Solver &S = D.S;
+  qdta_graph *g = S.g;
+  if (g->prof_on) return fail(QDTA_EINVAL, "profiling needs the plain schedule");
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = S.s;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = QDTA_OK;
+  do {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) { rc = fail(QDTA_ECUDA, "cudaGraphCreate"); break; }
+    cudaGraphNode_t n_day, n_a, n_fw, n_b, n_res, n_c;
+    cudaGraph_t day_body, fw_body, res_body;
+    cudaGraphConditionalHandle h_day, h_fw, h_res;
+    if ((rc = add_while(graph, nullptr, 0, 1, &n_day, &day_body, &h_day)) < 0) break;
+    if ((rc = add_while(day_body, nullptr, 0, 0, &n_fw, &fw_body, &h_fw)) < 0) break;
+    if ((rc = add_while(day_body, nullptr, 0, 0, &n_res, &res_body, &h_res)) < 0) break;
+    S.s = cs;
+    rc = add_captured_child(day_body, nullptr, 0, cs, &n_a, [&]() -> int {
+      RC(day_merge(D));
+      RC(seg_init(S));
+      launch_set_cond(S.ctl, 0, h_fw, cs);
+      return QDTA_OK;
+    });
+    if (rc >= 0) rc = build_fw_body(S, fw_body, h_fw, cs);
+    if (rc >= 0)
+      rc = add_captured_child(day_body, &n_fw, 1, cs, &n_b, [&]() -> int {
+        RC(seg_finish(S));
+        RC(day_res_head(D));
+        launch_res_begin(S.ctl, h_res, 1, cs);
+        return QDTA_OK;
+      });
+    if (rc >= 0) rc = capture_into(res_body, cs, [&]() -> int { return day_res_body(D, h_res, 1); });
+    if (rc >= 0)
+      rc = add_captured_child(day_body, &n_res, 1, cs, &n_c, [&]() -> int {
+        RC(day_store(D, flow_out));
+        launch_day_next(S.ctl, h_day, 1, cs);
+        return QDTA_OK;
+      });
+    S.s = saved;
+    if (rc < 0) break;
+    cudaError_t e = cudaGraphAddDependencies(day_body, &n_a, &n_fw, nullptr, 1);
+    if (e == cudaSuccess) e = cudaGraphAddDependencies(day_body, &n_b, &n_res, nullptr, 1);
+    if (e != cudaSuccess) { rc = fail(QDTA_ECUDA, "graph edges: %s", cudaGetErrorString(e)); break; }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { rc = fail(QDTA_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e)); break; }
+    e = cudaGraphLaunch(exec, S.s);
+    if (e != cudaSuccess) { rc = fail(QDTA_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e)); break; }
+  } while (0);
+  S.s = saved;
+  cudaStreamSynchronize(S.s);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  return rc;
+}
+
 extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, double dt_s,
                             const qdta_params *p, const qdta_od *resid_in, double *flow_out,
                             qdta_stats *stats, qdta_residual *resid_out, void *stream) {
@@ -977,7 +1041,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   if (p->schedule == QDTA_SCHEDULE_PLAIN) {
     for (int i = 0; i < N && rc >= 0; ++i) rc = day_interval_plain(D, flow_out);
   } else {
-    rc = fail(QDTA_EINVAL, "graph schedule of a day is set up below");
+    rc = day_graph(D, flow_out);
   }
   RC(rc);
   RC(status_check(g, s));

@@ -9,6 +9,7 @@
 //   update / tape         convex flow update f + alpha (g - f)
 //   scatter / compact     residual-demand merge d(i+1) = d_o(i+1) + d_r(i+1) (Alg. 1)
 //   adj_* / gather        adjoint of the unrolled FW map
+#include <atomic>
 #include <climits>
 #include <cstdio>
 
@@ -16,6 +17,11 @@
 #include "qdta_internal.cuh"
 
 namespace qdta {
+
+// kernels launched (or captured) by the launchers below, host-side count
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+#define COUNT_LAUNCH() g_launches.fetch_add(1)
 
 static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -43,6 +49,7 @@ void launch_pack_adj(const GraphDev &g, int direction, const int *q, int4 *adj, 
   if (g.L == 0) return;
   const int *list = direction == 0 ? g.in_link : g.out_link;
   const int *nb = direction == 0 ? g.tail : g.head;
+  COUNT_LAUNCH();
   pack_adj_kernel<<<cdiv(g.L, 256), 256, 0, s>>>(g.L, list, nb, q, adj, skip_dev);
 }
 
@@ -174,11 +181,13 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
   if (use_smem) {
     size_t sm = sssp_smem_bytes(g.V);
     cudaFuncSetAttribute(sssp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    COUNT_LAUNCH();
     sssp_kernel<true><<<grid, SSSP_THREADS, sm, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
                                                      nullptr, nullptr, nullptr, parent,
                                                      parent_slot_dev, slot_stride, dist, status, skip_dev,
                                                      roots_counter);
   } else {
+    COUNT_LAUNCH();
     sssp_kernel<false><<<grid, SSSP_THREADS, 0, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
                                                      w.state, w.stamp, w.queue, parent,
                                                      parent_slot_dev, slot_stride, dist, status,
@@ -198,6 +207,7 @@ __global__ void pack_head_q_kernel(int L, const int *__restrict__ head, const in
 
 void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStream_t s) {
   if (g.L == 0) return;
+  COUNT_LAUNCH();
   pack_head_q_kernel<<<cdiv(g.L, 256), 256, 0, s>>>(g.L, g.head, q, head_q);
 }
 
@@ -250,6 +260,7 @@ void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const
                  unsigned *status, cudaStream_t s) {
   long long n = n_items_dev ? (long long)g.num_sms * 16 * 256 : n_items_host;
   if (n <= 0) return;
+  COUNT_LAUNCH();
   load_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, head_q, parent, parent_slot_dev, slot_stride,
                                               root_slot, roots, n_items_host, n_items_dev, root_idx,
                                               src, amount, dt_q, flow_fx, stop_out, status);
@@ -300,6 +311,7 @@ void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *paren
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
                      unsigned long long *dense, unsigned *status, cudaStream_t s) {
   if (n_items_cap <= 0) return;
+  COUNT_LAUNCH();
   residual_kernel<<<link_grid(g, n_items_cap), 256, 0, s>>>(
       g.V, head_q_fin, parent, parent_slot_dev, slot_stride, root_slot, roots, n_items_dev, root_idx, src, amount, weight_dev,
       dt_q, h_fx, dense, status);
@@ -328,6 +340,7 @@ __global__ void bpr_kernel(int L, const int *__restrict__ c0, const double *__re
 void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,
                 unsigned *status, cudaStream_t s) {
   if (g.L == 0) return;
+  COUNT_LAUNCH();
   bpr_kernel<<<link_grid(g, g.L), LINK_THREADS, 0, s>>>(g.L, g.c0, g.cap, g.alpha, g.beta, dt_h,
                                                         g.quantum_s, flow, cost_s, cost_q, status);
 }
@@ -340,6 +353,7 @@ __global__ void link_const_kernel(int L, const double *__restrict__ cap, double 
 
 void launch_link_const(const GraphDev &g, double dt_h, LinkConst *kc, cudaStream_t s) {
   if (g.L == 0) return;
+  COUNT_LAUNCH();
   link_const_kernel<<<link_grid(g, g.L), LINK_THREADS, 0, s>>>(g.L, g.cap, dt_h, g.alpha, g.beta, kc);
 }
 
@@ -350,6 +364,7 @@ __global__ void flow_from_fx_kernel(int L, const unsigned long long *fx, double 
 
 void launch_flow_from_fx(int L, const unsigned long long *fx, double *f, cudaStream_t s) {
   if (L == 0) return;
+  COUNT_LAUNCH();
   flow_from_fx_kernel<<<cdiv(L, 256), 256, 0, s>>>(L, fx, f);
 }
 
@@ -456,6 +471,7 @@ int sweep_grid(const GraphDev &g) {
 void launch_sweep(const GraphDev &g, const LinkConst *kc, const double *f, const long long *g_fx,
                   const int *q, Ctl *ctl, i128 *partials, unsigned *counter, int grid,
                   unsigned *status, cudaStream_t s) {
+  COUNT_LAUNCH();
   sweep_kernel<<<grid, LINK_THREADS, 0, s>>>(g.L, g.c0, kc, f, g_fx, q, g.alpha, g.beta, ctl,
                                              partials, counter, status);
 }
@@ -481,6 +497,7 @@ objective_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict_
 
 void launch_objective(const GraphDev &g, const LinkConst *kc, const double *f, Ctl *ctl,
                       i128 *partials, unsigned *counter, int grid, unsigned *status, cudaStream_t s) {
+  COUNT_LAUNCH();
   objective_kernel<<<grid, LINK_THREADS, 0, s>>>(g.L, g.c0, kc, f, g.beta, ctl, partials, counter,
                                                  status);
 }
@@ -495,6 +512,7 @@ __global__ void update_kernel(int L, const Ctl *ctl, double *f, const long long 
 
 void launch_update(const GraphDev &g, Ctl *ctl, double *f, const long long *g_fx, cudaStream_t s) {
   if (g.L == 0) return;
+  COUNT_LAUNCH();
   update_kernel<<<link_grid(g, g.L), LINK_THREADS, 0, s>>>(g.L, ctl, f, g_fx);
 }
 
@@ -512,6 +530,7 @@ __global__ void tape_record_kernel(int L, const Ctl *ctl, const int *q, const do
 
 void launch_tape_record(const GraphDev &g, const Ctl *ctl, const int *q, const double *f,
                         int *tape_q, double *tape_alpha, double *tape_f, int cap, cudaStream_t s) {
+  COUNT_LAUNCH();
   tape_record_kernel<<<link_grid(g, g.L > 0 ? g.L : 1), 256, 0, s>>>(g.L, ctl, q, f, tape_q,
                                                                      tape_alpha, tape_f, cap);
 }
@@ -593,6 +612,7 @@ __global__ void ctl_init_kernel(Ctl *c, int step, int stop, int max_iter, int ls
 void launch_ctl_init(Ctl *ctl, int step, int stop, int max_iter, int ls_max, double tol, double dx,
                      double t1, double t2, int ring, long long n_items_host,
                      const long long *n_items_dev, cudaStream_t s) {
+  COUNT_LAUNCH();
   ctl_init_kernel<<<1, 1, 0, s>>>(ctl, step, stop, max_iter, ls_max, tol, dx, t1, t2, ring,
                                   n_items_host, n_items_dev);
 }
@@ -637,6 +657,7 @@ __global__ void ctl_begin_kernel(Ctl *c, cudaGraphConditionalHandle h_ls, int us
 }
 
 void launch_ctl_begin(Ctl *ctl, unsigned long long cond_ls, int use_cond, cudaStream_t s) {
+  COUNT_LAUNCH();
   ctl_begin_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond_ls, use_cond);
 }
 
@@ -747,7 +768,19 @@ __global__ void ctl_step_kernel(Ctl *c, cudaGraphConditionalHandle h_ls, int use
 }
 
 void launch_ctl_step(Ctl *ctl, unsigned long long cond_ls, int use_cond, cudaStream_t s) {
+  COUNT_LAUNCH();
   ctl_step_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond_ls, use_cond);
+}
+
+// copy a controller flag into a conditional handle (graph schedules)
+__global__ void set_cond_kernel(const Ctl *c, int which, cudaGraphConditionalHandle h) {
+  const int v = which == 0 ? c->fw_continue : which == 1 ? c->need_sweep : c->res_continue;
+  cudaGraphSetConditional(h, v ? 1u : 0u);
+}
+
+void launch_set_cond(const Ctl *ctl, int which, unsigned long long cond, cudaStream_t s) {
+  COUNT_LAUNCH();
+  set_cond_kernel<<<1, 1, 0, s>>>(ctl, which, (cudaGraphConditionalHandle)cond);
 }
 
 // after the update of iteration k
@@ -766,6 +799,7 @@ __global__ void ctl_end_kernel(Ctl *c, cudaGraphConditionalHandle h_fw, int use_
 }
 
 void launch_ctl_end(Ctl *ctl, unsigned long long cond_fw, int use_cond, cudaStream_t s) {
+  COUNT_LAUNCH();
   ctl_end_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond_fw, use_cond);
 }
 
@@ -781,12 +815,14 @@ __global__ void path_weights_kernel(const Ctl *c, const double *tape_alpha, doub
 }
 
 void launch_path_weights(const Ctl *ctl, const double *tape_alpha, double *w, cudaStream_t s) {
+  COUNT_LAUNCH();
   path_weights_kernel<<<1, 1, 0, s>>>(ctl, tape_alpha, w);
 }
 
 __global__ void weight_select_kernel(const double *w, int j, double *dst) { *dst = w[j]; }
 
 void launch_weight_select(const double *w, int j, double *dst, cudaStream_t s) {
+  COUNT_LAUNCH();
   weight_select_kernel<<<1, 1, 0, s>>>(w, j, dst);
 }
 
@@ -800,6 +836,7 @@ void launch_fill_i32(int *p, long long n, int v, cudaStream_t s) {
   if (n <= 0) return;
   long long b = (n + 255) / 256;
   if (b > 4096) b = 4096;
+  COUNT_LAUNCH();
   fill_i32_kernel<<<(int)b, 256, 0, s>>>(p, n, v);
 }
 
@@ -815,6 +852,7 @@ __global__ void tape0_kernel(int L, const int *q, const double *f, int *tape_q, 
 
 void launch_tape0(const GraphDev &g, const int *q, const double *f, int *tape_q, double *tape_alpha,
                   double *tape_f, cudaStream_t s) {
+  COUNT_LAUNCH();
   tape0_kernel<<<link_grid(g, g.L > 0 ? g.L : 1), 256, 0, s>>>(g.L, q, f, tape_q, tape_alpha, tape_f);
 }
 
@@ -826,6 +864,7 @@ __global__ void res_begin_kernel(Ctl *c, cudaGraphConditionalHandle h, int use_c
 }
 
 void launch_res_begin(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s) {
+  COUNT_LAUNCH();
   res_begin_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond, use_cond);
 }
 
@@ -848,6 +887,7 @@ void launch_res_prep(Ctl *ctl, const double *w, const int *tape_q, int L, int *q
   int b = (L + 255) / 256;
   if (b > 2048) b = 2048;
   if (b < 1) b = 1;
+  COUNT_LAUNCH();
   res_prep_kernel<<<b, 256, 0, s>>>(ctl, w, tape_q, L, q_work);
 }
 
@@ -858,6 +898,7 @@ __global__ void res_next_kernel(Ctl *c, cudaGraphConditionalHandle h, int use_co
 }
 
 void launch_res_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s) {
+  COUNT_LAUNCH();
   res_next_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond, use_cond);
 }
 
@@ -884,6 +925,7 @@ __global__ void store_interval_kernel(int L, const Ctl *c, const unsigned long l
 void launch_store_interval(const GraphDev &g, const Ctl *ctl, const unsigned long long *h_fx,
                            double *flow_out_rows, void *stats_rows, const long long *n_items_dev,
                            cudaStream_t s) {
+  COUNT_LAUNCH();
   store_interval_kernel<<<link_grid(g, g.L > 0 ? g.L : 1), 256, 0, s>>>(
       g.L, ctl, h_fx, flow_out_rows, (qdta_stats *)stats_rows, n_items_dev);
 }
@@ -895,6 +937,7 @@ __global__ void day_next_kernel(Ctl *c, cudaGraphConditionalHandle h, int use_co
 }
 
 void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s) {
+  COUNT_LAUNCH();
   day_next_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond, use_cond);
 }
 
@@ -911,6 +954,7 @@ __global__ void scatter_orig_kernel(int V, const Ctl *c, const OrigTable *tab,
 
 void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab, long long max_n,
                          unsigned long long *dense, cudaStream_t s) {
+  COUNT_LAUNCH();
   scatter_orig_kernel<<<link_grid(g, max_n > 0 ? max_n : 1), 256, 0, s>>>(g.V, ctl, tab, dense);
 }
 
@@ -930,6 +974,7 @@ __global__ void scatter_items_kernel(int V, long long n, const int *root_idx, co
 void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, const int *src,
                           const long long *amount, unsigned long long *dense, cudaStream_t s) {
   if (n <= 0) return;
+  COUNT_LAUNCH();
   scatter_items_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, n, root_idx, src, amount, dense);
 }
 
@@ -1014,8 +1059,11 @@ void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *bl
                     long long *n_out_dev, unsigned *status, cudaStream_t s) {
   const long long total = (long long)R * g.V;
   const int nblk = cdiv(total > 0 ? total : 1, COMPACT_TILE);
+  COUNT_LAUNCH();
   compact_count_kernel<<<nblk, 256, 0, s>>>(total, dense, blk_count);
+  COUNT_LAUNCH();
   compact_scan_kernel<<<1, 1024, 0, s>>>(nblk, blk_count, blk_off, cap, n_out_dev, status);
+  COUNT_LAUNCH();
   compact_write_kernel<<<nblk, 256, 0, s>>>(total, g.V, dense, blk_off, cap, root_idx, src, amount);
 }
 
@@ -1044,6 +1092,7 @@ __global__ void active_roots_kernel(int R, const long long *n_dev, long long cap
 void launch_active_roots(int R, const long long *n_items_dev, long long cap_items, const int *root_idx,
                          const int *zone_nodes, int *flag, int *active_roots, int *root_slot,
                          int *n_active_dev, cudaStream_t s) {
+  COUNT_LAUNCH();
   active_roots_kernel<<<1, 1024, 0, s>>>(R, n_items_dev, cap_items, root_idx, zone_nodes, flag,
                                          active_roots, root_slot, n_active_dev);
 }
@@ -1092,8 +1141,10 @@ __global__ void adj_finish_kernel(int nblk, const double *partials, double *out2
 void launch_adj_reduce(const GraphDev &g, const LinkConst *kc, const double *lam, const double *fprev,
                        const long long *g_fx, double alpha, int implicit, double *partials, double *out2,
                        int grid, cudaStream_t s) {
+  COUNT_LAUNCH();
   adj_reduce_kernel<<<grid, LINK_THREADS, 0, s>>>(g.L, g.c0, kc, g.alpha, g.beta, lam, fprev, g_fx,
                                                   alpha, implicit, partials, out2);
+  COUNT_LAUNCH();
   adj_finish_kernel<<<1, 1, 0, s>>>(grid, partials, out2);
 }
 
@@ -1135,6 +1186,7 @@ void launch_adj_update(const GraphDev &g, const LinkConst *kc, const double *lam
                        const long long *g_fx, double alpha, int implicit, const double *muH,
                        double *gbar, double *lam_prev, double *dcap, cudaStream_t s) {
   if (g.L == 0) return;
+  COUNT_LAUNCH();
   adj_update_kernel<<<link_grid(g, g.L), LINK_THREADS, 0, s>>>(g.L, g.c0, g.cap, kc, g.alpha, g.beta,
                                                                lam, fprev, g_fx, alpha, implicit, muH,
                                                                gbar, lam_prev, dcap);
@@ -1172,6 +1224,7 @@ void launch_gather(const GraphDev &g, const int2 *head_q, const int *parent, con
                    long long n_items, const int *root_idx, const int *src, long long dt_q,
                    const double *gbar, double *dd, unsigned *status, cudaStream_t s) {
   if (n_items <= 0) return;
+  COUNT_LAUNCH();
   gather_kernel<<<link_grid(g, n_items), 256, 0, s>>>(g.V, head_q, parent, roots, n_items, root_idx,
                                                       src, dt_q, gbar, dd, status);
 }

@@ -68,7 +68,8 @@ class Residual(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("sssp_launches", C.c_int64), ("sssp_ms", C.c_double), ("sssp_roots", C.c_int64),
                 ("load_launches", C.c_int64), ("load_ms", C.c_double),
-                ("sweep_launches", C.c_int64), ("sweep_ms", C.c_double)]
+                ("sweep_launches", C.c_int64), ("sweep_ms", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

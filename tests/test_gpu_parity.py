@@ -226,8 +226,9 @@ def _day_case(n_int=6, trips=40000):
     return synth.scaled_day(base, trips, n_intervals=n_int, seed=11)
 
 
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
 @pytest.mark.parametrize("step,stop,it", [("msa", "none", 8), ("sweep8", "rel_gap", 80)])
-def test_run_day_bit_exact(step, stop, it):
+def test_run_day_bit_exact(step, stop, it, schedule):
     day = _day_case()
     days = [d for d in day.demand]
     og = oracle.OracleGraph(day.net)
@@ -236,7 +237,8 @@ def test_run_day_bit_exact(step, stop, it):
     g = Q.Graph(day.net)
     zones = T(day.zones, np.int32)
     dd = [Q.DeviceOD(zones, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
-    f_g, st_g, rc_g, resid = Q.qdta_run_day(g, dd, 900.0, Q.make_params(step, stop, it), resid_capacity=1 << 20)
+    f_g, st_g, rc_g, resid = Q.qdta_run_day(g, dd, 900.0, Q.make_params(step, stop, it, schedule=schedule),
+                                            resid_capacity=1 << 20)
     np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
     for i in range(len(days)):
         assert st_g[i]["n_items"] == nit_o[i]
@@ -245,7 +247,8 @@ def test_run_day_bit_exact(step, stop, it):
     assert resid[0].shape[0] == rn_o
 
 
-def test_run_day_worked_example():
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+def test_run_day_worked_example(schedule):
     ff = [600.0, 300.0, 600.0, 600.0]
     net = synth.chain_network(ff, [200.0, 150.0, 200.0, 200.0])
     g = Q.Graph(net)
@@ -255,7 +258,7 @@ def test_run_day_worked_example():
           Q.DeviceOD(zones, T([1], np.int32), T([2], np.int32), T([fx(12.5)], np.int64)),
           Q.DeviceOD(zones, T([], np.int32), T([], np.int32), T([], np.int64)),
           Q.DeviceOD(zones, T([], np.int32), T([], np.int32), T([], np.int64))]
-    f, st, rc, _ = Q.qdta_run_day(g, dd, 900.0, Q.make_params("sweep8", "rel_gap", 50))
+    f, st, rc, _ = Q.qdta_run_day(g, dd, 900.0, Q.make_params("sweep8", "rel_gap", 50, schedule=schedule))
     f = f.cpu().numpy()
     np.testing.assert_array_equal(f[0], [43.75, 43.75, 0, 0])
     np.testing.assert_array_equal(f[1], [0, 0, 56.25, 12.5])
