@@ -115,6 +115,7 @@ typedef struct {
   double rel_gap;      /* last measured gap (relative objective change in PAPER_OBJ mode) */
   double objective;    /* Beckmann objective of the returned flows (quanta x trips) */
   int64_t n_items;     /* demand items solved (after merging residual demand) */
+  double dual_gap;     /* last relative duality gap (sum c f - sum c g) / sum c f, any stop rule */
 } qdta_stats;
 
 /* Output buffer for residual demand (device arrays, caller-owned). */
@@ -138,6 +139,8 @@ typedef struct {
   double sweep_ms;
   int64_t kernel_launches;  /* all kernels this library launched (process-wide, any schedule;
                                graph schedules count each captured kernel once) */
+  int64_t sssp_rounds;      /* frontier rounds summed over the roots solved */
+  int64_t sssp_relaxations; /* link relaxations summed over the roots solved */
 } qdta_profile;
 
 /* ---------------------------------------------------------------------- */

@@ -61,7 +61,8 @@ class Params(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("aon_calls", C.c_int32), ("ls_passes", C.c_int32),
-                ("converged", C.c_int32), ("rel_gap", C.c_double), ("objective", C.c_double)]
+                ("converged", C.c_int32), ("rel_gap", C.c_double), ("objective", C.c_double),
+                ("dual_gap", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

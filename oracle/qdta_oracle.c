@@ -79,8 +79,9 @@ typedef struct {
   int32_t aon_calls;    /* shortest-path batches run (including the initial one) */
   int32_t ls_passes;    /* link sweeps spent in line searches */
   int32_t converged;
-  double rel_gap;       /* last measured relative gap (NaN if none) */
+  double rel_gap;       /* last value of the stop-rule measure (NaN if none) */
   double objective;     /* Beckmann objective of the returned flows, quantum*trips */
+  double dual_gap;      /* last relative duality gap (sum c f - sum c g) / sum c f */
 } or_stats;
 
 /* ------------------------------------------------------------------------ */
@@ -609,12 +610,14 @@ static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or
   for (int64_t k = 0; k < od->n_items; k++) used[od->root_idx[k]] = 1;
   memset(st, 0, sizeof(*st));
   st->rel_gap = NAN;
+  st->dual_gap = NAN;
 
   /* initial AON at free flow: q = BPR(0) */
   for (int a = 0; a < L; a++) f_out[a] = 0.0;
   if (od->n_items == 0) {          /* no demand: zero flows, converged at once */
     st->converged = 1;
     st->rel_gap = 0.0;
+    st->dual_gap = 0.0;
     if (tape) { tape->K = 0; tape->alpha[0] = 1.0; memset(tape->f, 0, (size_t)L * 8);
                 or_bpr(g, f_out, dt_s, NULL, tape->q); }
     goto done;
@@ -638,15 +641,19 @@ static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or
     st->aon_calls++;
     if (rc) break;
     for (int a = 0; a < L; a++) gd[a] = (double)g_fx[a] * 0x1p-32;
-    if (p->stop == STOP_REL_GAP) {
-      /* gap = (sum q f - sum q g) / sum q f with q the costs at f */
+    {
+      /* relative duality gap (sum q f - sum q g) / sum q f with q the costs
+       * at f, measured every iteration; the REL_GAP rule stops on it */
       i128 A = 0, B = 0;
       for (int a = 0; a < L; a++) {
         A += fx_of((double)q[a] * f_out[a], &bad);
         B += (i128)q[a] * (i128)g_fx[a];
       }
-      st->rel_gap = fx_to_double(A - B) / fx_to_double(A);
-      if (st->rel_gap <= p->tol) { st->converged = 1; break; }
+      st->dual_gap = fx_to_double(A - B) / fx_to_double(A);
+      if (p->stop == STOP_REL_GAP) {
+        st->rel_gap = st->dual_gap;
+        if (st->rel_gap <= p->tol) { st->converged = 1; break; }
+      }
     }
     int passes = 0;
     double alpha = choose_step(g, f_out, gd, dt_h, k, p, &passes, &bad);

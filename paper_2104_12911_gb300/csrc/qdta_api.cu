@@ -316,11 +316,11 @@ extern "C" int qdta_profile_enable(qdta_graph *g, int32_t on) {
   DevGuard guard(g->device);
   if (!g->prof_roots) {
     void *p = nullptr;
-    CK(cudaMalloc(&p, 16));
+    CK(cudaMalloc(&p, 32));
     g->owned.push_back(p);
     g->prof_roots = (unsigned long long *)p;
   }
-  CK(cudaMemset(g->prof_roots, 0, 16));
+  CK(cudaMemset(g->prof_roots, 0, 32));
   g->prof_on = on ? 1 : 0;
   g->prof = qdta_profile{};
   return QDTA_OK;
@@ -332,9 +332,11 @@ extern "C" int qdta_profile_read(qdta_graph *g, qdta_profile *out) {
   DevGuard guard(g->device);
   CK(cudaDeviceSynchronize());
   prof_harvest(g);
-  unsigned long long roots = 0;
-  if (g->prof_roots) CK(cudaMemcpy(&roots, g->prof_roots, 8, cudaMemcpyDeviceToHost));
-  g->prof.sssp_roots = (int64_t)roots;
+  unsigned long long cnt[3] = {0, 0, 0};
+  if (g->prof_roots) CK(cudaMemcpy(cnt, g->prof_roots, 24, cudaMemcpyDeviceToHost));
+  g->prof.sssp_roots = (int64_t)cnt[0];
+  g->prof.sssp_rounds = (int64_t)cnt[1];
+  g->prof.sssp_relaxations = (int64_t)cnt[2];
   g->prof.kernel_launches = launch_count();
   *out = g->prof;
   return QDTA_OK;
@@ -514,7 +516,7 @@ static int seg_init(Solver &S) {
   qdta_graph *g = S.g;
   const qdta_params *p = S.p;
   launch_ctl_init(S.ctl, p->step, p->stop, p->max_iter, p->ls_max, p->tol, p->ls_dx, p->ls_t1, p->ls_t2,
-                  S.ring, S.n_host, S.n_dev, S.s);
+                  S.ring, S.n_host, S.n_dev, 1, S.s);
   launch_link_const(g->d, S.dt_h, S.kc, S.s);
   CK(cudaMemsetAsync(S.f, 0, (size_t)g->d.L * 8, S.s));
   launch_bpr(g->d, S.f, S.dt_h, nullptr, S.q, g->status, S.s);
@@ -683,6 +685,7 @@ static void fill_stats(const Ctl *h, long long n_items, qdta_stats *st) {
   st->rel_gap = h->rel_gap;
   st->objective = h->objective;
   st->n_items = n_items;
+  st->dual_gap = h->dual_gap;
 }
 
 static int check_od(const qdta_graph *g, const qdta_od *od) {
@@ -719,7 +722,7 @@ extern "C" int qdta_line_search(qdta_graph *g, const double *flow, const int64_t
   CK(cudaMemsetAsync(counter, 0, 16, s));
   // a line search alone: no stop rule, iteration k = fw_iter
   launch_ctl_init(ctl, p->step, QDTA_STOP_NONE, fw_iter, p->ls_max, p->tol, p->ls_dx, p->ls_t1, p->ls_t2,
-                  1, 1, nullptr, s);
+                  1, 1, nullptr, 0, s);
   CK(cudaMemcpyAsync(&ctl->k, &fw_iter, sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
   launch_link_const(g->d, S.dt_h, kc, s);

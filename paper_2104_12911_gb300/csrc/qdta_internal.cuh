@@ -196,7 +196,7 @@ struct Ctl {
   int notconv;
   int iterations, aon_calls, ls_passes;
   int ls_state, ls_pc, l, ex_it;
-  double rel_gap;
+  double rel_gap, dual_gap;
   double alpha, alpha_final, lo, hi;
   i128 Dlo, Dhi;
   Plan plan;
@@ -208,6 +208,7 @@ struct Ctl {
   int res_j, res_slot, res_skip, res_continue;
   double w_cur;
   int day_i, day_N, day_continue;
+  int gap_on;  // measure the duality gap (needs the iteration's link times)
 };
 
 // --------------------------------------------------------------------------
@@ -272,7 +273,7 @@ void launch_objective(const GraphDev &g, const LinkConst *kc, const double *f, C
 
 void launch_ctl_init(Ctl *ctl, int step, int stop, int max_iter, int ls_max, double tol, double dx,
                      double t1, double t2, int ring, long long n_items_host,
-                     const long long *n_items_dev, cudaStream_t s);
+                     const long long *n_items_dev, int gap_on, cudaStream_t s);
 void launch_tape0(const GraphDev &g, const int *q, const double *f, int *tape_q, double *tape_alpha,
                   double *tape_f, cudaStream_t s);
 void launch_res_begin(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s);

@@ -105,6 +105,7 @@ sssp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__
     __syncthreads();
     int ncur = 1, round = 0;
     int *cur = qa, *nxt = qb;
+    unsigned long long my_relax = 0;
     while (ncur > 0) {
       const int c = round % 3;
       if (threadIdx.x == 0) s_cnt[(round + 1) % 3] = 0;
@@ -116,6 +117,7 @@ sssp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__
         else kw = __ldcg(&state[w]);
         const unsigned long long dw = kw >> LB;
         const int kb = off[w], ke = off[w + 1];
+        my_relax += (unsigned long long)(ke - kb);
         for (int k = kb; k < ke; ++k) {
           const int4 ent = __ldg(&adj[k]);
           const unsigned long long cand = dw + (unsigned long long)(unsigned)ent.z;
@@ -140,11 +142,147 @@ sssp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__
       }
     }
     rid += round + 1;
+    if (roots_counter) {  // work counters: [1] rounds, [2] relaxations
+      if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
+      atomicAdd(roots_counter + 2, my_relax);
+    }
     __syncthreads();
     int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
     for (int v = threadIdx.x; v < V; v += blockDim.x) {
       const unsigned long long key = state[v];
+      const unsigned long long lk = key & NOLINK;
+      prow[v] = lk == NOLINK ? -1 : (int)lk;
+      if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
+      state[v] = ~0ull;
+    }
+    __syncthreads();
+  }
+}
+
+// Global-memory variant for graphs whose per-root state does not fit in
+// shared memory.  Same queue Bellman-Ford and packed keys as above, laid out
+// for memory-level parallelism: four lanes per frontier node (one in-link
+// each), NPT frontier nodes per lane group in flight, and an L2 read of the
+// target's key before the atomic, so relaxations that cannot improve (most
+// of them) cost a load instead of an atomic.
+constexpr int SSSP2_THREADS = 128;
+constexpr int SSSP2_NPT = 4;
+
+__global__ void __launch_bounds__(SSSP2_THREADS)
+sssp_ilp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__ adj,
+                const int *__restrict__ roots, int R_host, const int *R_dev,
+                unsigned long long *g_state, int *g_stamp, int *g_queue, int *parent,
+                const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
+                const int *skip_dev, unsigned long long *roots_counter) {
+  __shared__ int s_cnt[3];
+  if (skip_dev && *skip_dev) return;
+  const int R = R_dev ? *R_dev : R_host;
+  if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
+  const size_t b = blockIdx.x;
+  unsigned long long *state = g_state + b * (size_t)V;
+  int *stamp = g_stamp + b * (size_t)V;
+  int *qa = g_queue + b * 2 * (size_t)V;
+  int *qb = qa + V;
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
+  const unsigned long long NOLINK = (1ull << LB) - 1ull;
+  const unsigned long long DMAX = (~0ull) >> LB;
+  constexpr int NQ = SSSP2_THREADS / 4;
+  const int quad = threadIdx.x >> 2, lane4 = threadIdx.x & 3;
+  for (int v = threadIdx.x; v < V; v += blockDim.x) {
+    state[v] = ~0ull;
+    stamp[v] = -1;
+  }
+  int rid = 0;
+  __syncthreads();
+  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    const int z = roots[r];
+    if (threadIdx.x == 0) {
+      state[z] = NOLINK;
+      qa[0] = z;
+      s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+    }
+    __syncthreads();
+    int ncur = 1, round = 0;
+    int *cur = qa, *nxt = qb;
+    unsigned long long my_relax = 0;
+    while (ncur > 0) {
+      const int c = round % 3;
+      if (threadIdx.x == 0) s_cnt[(round + 1) % 3] = 0;
+      const int my_rid = rid + round;
+      for (int base = 0; base < ncur; base += NQ * SSSP2_NPT) {
+        int w[SSSP2_NPT], kb[SSSP2_NPT], ke[SSSP2_NPT];
+        unsigned long long dw[SSSP2_NPT];
+#pragma unroll
+        for (int j = 0; j < SSSP2_NPT; ++j) {
+          const int i = base + j * NQ + quad;
+          w[j] = i < ncur ? __ldcg(&cur[i]) : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < SSSP2_NPT; ++j) {
+          kb[j] = 0; ke[j] = 0; dw[j] = 0;
+          if (w[j] >= 0) {
+            kb[j] = __ldg(&off[w[j]]) + lane4;
+            ke[j] = __ldg(&off[w[j] + 1]);
+            dw[j] = __ldcg(&state[w[j]]) >> LB;
+          }
+        }
+        bool more = true;
+        while (more) {
+          int4 ent[SSSP2_NPT];
+          unsigned long long tk[SSSP2_NPT];
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j)
+            if (kb[j] < ke[j]) ent[j] = __ldg(&adj[kb[j]]);
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j)
+            if (kb[j] < ke[j]) tk[j] = __ldcg(&state[ent[j].y]);
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j) {
+            if (kb[j] < ke[j]) {
+              ++my_relax;
+              const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
+              if (cand >= DMAX) {
+                atomicOr(status, ST_OVERFLOW);
+              } else {
+                const unsigned long long key = (cand << LB) | (unsigned long long)(unsigned)ent[j].x;
+                if (key < tk[j]) {
+                  const unsigned long long old = atomicMin(&state[ent[j].y], key);
+                  if ((old >> LB) > cand && atomicExch(&stamp[ent[j].y], my_rid) != my_rid) {
+                    const int pos = atomicAdd(&s_cnt[c], 1);
+                    nxt[pos] = ent[j].y;
+                  }
+                }
+              }
+            }
+          }
+          more = false;
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j) {
+            kb[j] += 4;
+            more |= kb[j] < ke[j];
+          }
+        }
+      }
+      __syncthreads();
+      ncur = s_cnt[c];
+      int *t = cur; cur = nxt; nxt = t;
+      ++round;
+      if (round > V + 1) {
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        break;
+      }
+    }
+    rid += round + 1;
+    if (roots_counter) {
+      if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
+      atomicAdd(roots_counter + 2, my_relax);
+    }
+    __syncthreads();
+    int *prow = parent + (long long)r * V;
+    long long *drow = dist ? dist + (long long)r * V : nullptr;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+      const unsigned long long key = __ldcg(&state[v]);
       const unsigned long long lk = key & NOLINK;
       prow[v] = lk == NOLINK ? -1 : (int)lk;
       if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
@@ -166,7 +304,7 @@ int sssp_blocks_per_sm(bool use_smem, int V) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_kernel<true>, SSSP_THREADS,
                                                   sssp_smem_bytes(V));
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_kernel<false>, SSSP_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_ilp_kernel, SSSP2_THREADS, 0);
   }
   return n > 0 ? n : 1;
 }
@@ -188,7 +326,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                                                      roots_counter);
   } else {
     COUNT_LAUNCH();
-    sssp_kernel<false><<<grid, SSSP_THREADS, 0, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
+    sssp_ilp_kernel<<<grid, SSSP2_THREADS, 0, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
                                                      w.state, w.stamp, w.queue, parent,
                                                      parent_slot_dev, slot_stride, dist, status,
                                                      skip_dev, roots_counter);
@@ -439,7 +577,7 @@ sweep_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict__ kc
     const double ga = fx64_to_double(gfx);
     const double c0a = (double)c0[a];
     const LinkConst k = kc[a];
-    if (plan.want_gap) {
+    if (plan.want_gap && q) {
       const int qa = q[a];
       acc[MAX_SLOTS] += fx_of(mul((double)qa, fa), &bad);
       acc[MAX_SLOTS + 1] += (i128)qa * (i128)gfx;
@@ -587,7 +725,7 @@ __device__ void sweep8_next_or_finish(Ctl *c) {
 
 __global__ void ctl_init_kernel(Ctl *c, int step, int stop, int max_iter, int ls_max, double tol,
                                 double dx, double t1, double t2, int ring, long long n_host,
-                                const long long *n_dev) {
+                                const long long *n_dev, int gap_on) {
   const long long n = n_dev ? *n_dev : n_host;
   c->step = step; c->stop = stop; c->max_iter = max_iter; c->ls_max = ls_max;
   c->tol = tol; c->dx = dx; c->t1 = t1; c->t2 = t2;
@@ -598,23 +736,26 @@ __global__ void ctl_init_kernel(Ctl *c, int step, int stop, int max_iter, int ls
   c->iterations = 0; c->aon_calls = 1; c->ls_passes = 0;
   c->ls_state = LS_IDLE; c->ls_pc = 0; c->l = 0; c->ex_it = 0;
   c->rel_gap = __longlong_as_double(0x7ff8000000000000ll);
+  c->dual_gap = c->rel_gap;
   c->alpha = c->alpha_final = 0.0;
   c->objective = 0.0;
   c->plan.n = 0; c->plan.want_gap = 0;
   c->ring = ring;
+  c->gap_on = gap_on;
   c->tree_slot = ring > 1 ? 1 : 0;
   if (n <= 0) {  // no demand: zero flows, converged at once
     c->fw_continue = 0; c->notconv = 0; c->converged = 1; c->aon_calls = 0;
     c->rel_gap = 0.0;
+    c->dual_gap = 0.0;
   }
 }
 
 void launch_ctl_init(Ctl *ctl, int step, int stop, int max_iter, int ls_max, double tol, double dx,
                      double t1, double t2, int ring, long long n_items_host,
-                     const long long *n_items_dev, cudaStream_t s) {
+                     const long long *n_items_dev, int gap_on, cudaStream_t s) {
   COUNT_LAUNCH();
   ctl_init_kernel<<<1, 1, 0, s>>>(ctl, step, stop, max_iter, ls_max, tol, dx, t1, t2, ring,
-                                  n_items_host, n_items_dev);
+                                  n_items_host, n_items_dev, gap_on);
 }
 
 // after the all-or-nothing of iteration k: set up the step rule
@@ -623,7 +764,9 @@ __global__ void ctl_begin_kernel(Ctl *c, cudaGraphConditionalHandle h_ls, int us
   c->ls_pc = 0;
   c->do_update = 0;
   c->need_sweep = 0;
-  const int gap = c->stop == 2;
+  // the duality gap is measured on the first sweep of every iteration of a
+  // FW solve (a stand-alone line search has no link times to measure it with)
+  const int gap = c->gap_on;
   switch (c->step) {
     case 0:  // MSA
       c->alpha = dvd(1.0, add((double)c->k, 1.0));
@@ -666,9 +809,10 @@ __global__ void ctl_step_kernel(Ctl *c, cudaGraphConditionalHandle h_ls, int use
   c->need_sweep = 0;
   if (c->plan.want_gap) {
     const i128 A = c->sums[MAX_SLOTS], B = c->sums[MAX_SLOTS + 1];
-    c->rel_gap = dvd(fx_to_double(A - B), fx_to_double(A));
+    c->dual_gap = dvd(fx_to_double(A - B), fx_to_double(A));
     c->plan.want_gap = 0;
-    if (c->rel_gap <= c->tol) {
+    if (c->stop == 2) c->rel_gap = c->dual_gap;
+    if (c->stop == 2 && c->rel_gap <= c->tol) {
       c->converged = 1;
       c->fw_continue = 0;
       c->do_update = 0;
@@ -918,6 +1062,7 @@ __global__ void store_interval_kernel(int L, const Ctl *c, const unsigned long l
     st.rel_gap = c->rel_gap;
     st.objective = c->objective;
     st.n_items = n_items ? *n_items : 0;
+    st.dual_gap = c->dual_gap;
     stats[i] = st;
   }
 }

@@ -54,7 +54,7 @@ class Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("aon_calls", C.c_int32), ("ls_passes", C.c_int32),
                 ("converged", C.c_int32), ("rel_gap", C.c_double), ("objective", C.c_double),
-                ("n_items", C.c_int64)]
+                ("n_items", C.c_int64), ("dual_gap", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,7 +69,8 @@ class Profile(C.Structure):
     _fields_ = [("sssp_launches", C.c_int64), ("sssp_ms", C.c_double), ("sssp_roots", C.c_int64),
                 ("load_launches", C.c_int64), ("load_ms", C.c_double),
                 ("sweep_launches", C.c_int64), ("sweep_ms", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("sssp_rounds", C.c_int64),
+                ("sssp_relaxations", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
