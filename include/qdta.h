@@ -255,6 +255,33 @@ int qdta_tape_destroy(qdta_tape *tape);
 /* iterations recorded (K) and items of the taped interval */
 int qdta_tape_info(const qdta_tape *tape, int32_t *K_out_host, int64_t *n_items_out_host);
 
+/* Batched shortest paths that allocate no device memory.
+ *
+ * The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc at the moment they need shortest paths -- for example code that
+ * runs while its stream is being captured into a CUDA graph (an allocation
+ * there is an illegal call under the default capture mode), latency-critical
+ * loops where an allocation can stall, or processes whose device memory is
+ * fully reserved up front by another allocator.  qdta_sssp_batch, by
+ * contrast, grows a workspace with cudaMalloc the first time it sees a
+ * larger graph.
+ *
+ * Same arguments, results and error codes as qdta_sssp_batch, for graphs
+ * with at most QDTA_NOALLOC_MAX_LINKS links whose per-root state fits in
+ * shared memory (at most 10,240 nodes); larger graphs are rejected with
+ * QDTA_EINVAL and a message saying which limit was exceeded.  The graph
+ * handle must already exist (qdta_graph_create allocates).  The only scratch
+ * is a file-scope device array of QDTA_NOALLOC_MAX_LINKS 16-byte entries
+ * (1 MiB), which every GPU that loads the library keeps until the process
+ * exits.  The first call on a device looks up that array's device address;
+ * make it before any stream capture.  Every call shares the array and
+ * rewrites the part it uses before reading it, so calls that overlap on the
+ * GPU (different streams or threads on one device) race and must be
+ * serialised by the caller.  Synchronises `stream`. */
+#define QDTA_NOALLOC_MAX_LINKS 65536
+int qdta_sssp_batch_noalloc(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R,
+                            int32_t direction, int32_t *parent_link, int64_t *dist, void *stream);
+
 /* Enable / read / reset per-kernel event timings (plain schedule). */
 int qdta_profile_enable(qdta_graph *g, int32_t on);
 int qdta_profile_read(qdta_graph *g, qdta_profile *out_host);

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1144,5 +1145,61 @@ extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_dd
                   g->status, s);
     if (k > 0) std::swap(lam, lam2);
   }
+  return status_check(g, s);
+}
+
+// ---------------------------------------------------------------------------
+// batched shortest paths without device allocation
+// ---------------------------------------------------------------------------
+// The packed adjacency that qdta_sssp_batch keeps in its grow-only workspace
+// lives here in a fixed device array instead; the shared-memory SSSP kernel
+// needs no other global scratch.
+static __device__ __align__(256) int4 g_noalloc_adj[QDTA_NOALLOC_MAX_LINKS];
+
+static std::mutex g_noalloc_mu;
+static int4 *g_noalloc_ptr[256];
+
+// device address of g_noalloc_adj on `dev` (looked up once per device, with
+// that device current; host code must not use the symbol itself as a pointer)
+static int noalloc_scratch(int dev, int4 **out) {
+  if (dev < 0 || dev >= 256) return fail(QDTA_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_adj);
+    if (e != cudaSuccess)
+      return fail(QDTA_ECUDA, "cudaGetSymbolAddress of the no-allocation scratch failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = reinterpret_cast<int4 *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return QDTA_OK;
+}
+
+extern "C" int qdta_sssp_batch_noalloc(qdta_graph *g, const int32_t *cost_q, const int32_t *roots,
+                                       int32_t R, int32_t direction, int32_t *parent_link,
+                                       int64_t *dist, void *stream) {
+  RC(check_graph(g));
+  if (R < 0) return fail(QDTA_EINVAL, "R must be >= 0");
+  if (direction != QDTA_TO_ROOT && direction != QDTA_FROM_ROOT) return fail(QDTA_EINVAL, "bad direction");
+  if (g->d.L > QDTA_NOALLOC_MAX_LINKS)
+    return fail(QDTA_EINVAL, "graph has %d links; the no-allocation variant holds at most %d",
+                g->d.L, QDTA_NOALLOC_MAX_LINKS);
+  if (!g->sssp_smem)
+    return fail(QDTA_EINVAL, "graph has %d nodes; the no-allocation variant needs the per-root state "
+                "in shared memory (at most %d nodes)", g->d.V, sssp_max_smem_nodes());
+  if (R > 0 && (!cost_q || !roots || !parent_link)) return fail(QDTA_EINVAL, "NULL array");
+  if (R == 0) return QDTA_OK;
+  DevGuard guard(g->device);
+  int4 *adj = nullptr;
+  RC(noalloc_scratch(g->device, &adj));
+  cudaStream_t s = (cudaStream_t)stream;
+  RC(status_reset(g, s));
+  // every entry [0, L) is rewritten before the kernel reads it
+  launch_pack_adj(g->d, direction, cost_q, adj, s);
+  SsspWork w{};
+  w.adj = adj;
+  launch_sssp(g->d, direction, adj, roots, R, nullptr, sssp_grid(g, R), true, w, parent_link, nullptr,
+              0, (long long *)dist, g->status, s);
   return status_check(g, s);
 }

@@ -100,6 +100,7 @@ def lib():
                 "qdta_graph_create": [P, C.c_int, P],
                 "qdta_graph_destroy": [P],
                 "qdta_sssp_batch": [P, P, P, I32, I32, P, P, P],
+                "qdta_sssp_batch_noalloc": [P, P, P, I32, I32, P, P, P],
                 "qdta_load_aon": [P, P, P, P, I64, P, P, P],
                 "qdta_bpr_costs": [P, P, D, P, P, P],
                 "qdta_line_search": [P, P, P, D, I32, P, P, P, P],
@@ -208,6 +209,15 @@ def qdta_sssp_batch(g: Graph, cost_q, roots, direction=QDTA_TO_ROOT, want_dist=F
     dist = torch.empty((R, g.n_nodes), dtype=torch.int64, device=g.device) if want_dist else None
     _check(lib().qdta_sssp_batch(g.h, _ptr(cost_q), _ptr(roots), R, int(direction), _ptr(parent),
                                  _ptr(dist), _stream()))
+    return parent, dist
+
+
+def qdta_sssp_batch_noalloc(g: Graph, cost_q, roots, direction=QDTA_TO_ROOT, want_dist=False):
+    R = int(roots.shape[0])
+    parent = torch.empty((R, g.n_nodes), dtype=torch.int32, device=g.device)
+    dist = torch.empty((R, g.n_nodes), dtype=torch.int64, device=g.device) if want_dist else None
+    _check(lib().qdta_sssp_batch_noalloc(g.h, _ptr(cost_q), _ptr(roots), R, int(direction), _ptr(parent),
+                                         _ptr(dist), _stream()))
     return parent, dist
 
 
