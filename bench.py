@@ -233,7 +233,9 @@ def sssp_only(args):
     print(json.dumps({"metric": "SSSP batch (metro grid)", "roots": R, "ms_per_launch": ms,
                       "gteps": R * L / (ms * 1e-3) / 1e9, "alg_gbs": b_alg / (ms * 1e-3) / 1e9,
                       "rounds_per_root": p["sssp_rounds"] / max(p["sssp_roots"], 1),
-                      "relax_per_link": p["sssp_relaxations"] / max(p["sssp_roots"], 1) / L}), flush=True)
+                      "relax_per_link": p["sssp_relaxations"] / max(p["sssp_roots"], 1) / L,
+                      "cell_activations_per_root": p["sssp_cell_activations"] / max(p["sssp_roots"], 1)}),
+          flush=True)
 
 
 def main():

@@ -141,6 +141,7 @@ typedef struct {
                                graph schedules count each captured kernel once) */
   int64_t sssp_rounds;      /* frontier rounds summed over the roots solved */
   int64_t sssp_relaxations; /* link relaxations summed over the roots solved */
+  int64_t sssp_cell_activations; /* cell activations (cell-partitioned kernel) */
 } qdta_profile;
 
 /* ---------------------------------------------------------------------- */
@@ -220,7 +221,8 @@ typedef struct {
 /* Many independent intervals (e.g. different networks) solved together:
  * with QDTA_SCHEDULE_GRAPH all instances run as parallel branches of one
  * CUDA graph launch; with QDTA_SCHEDULE_PLAIN one after another.  Every
- * graph must live on the same device.  stats_host [n_inst] (nullable). */
+ * graph must live on the same device and appear once (each handle holds one
+ * workspace).  stats_host [n_inst] (nullable).  Synchronises. */
 int qdta_assign_batch(const qdta_instance *inst, int32_t n_inst, const qdta_params *p,
                       qdta_stats *stats_host, void *stream);
 

@@ -5,7 +5,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -69,6 +72,14 @@ struct qdta_graph {
   unsigned long long *prof_roots = nullptr;  // device counter of roots solved
   std::vector<ProfEvent> pending;
   std::vector<cudaEvent_t> evpool;
+  // cell partition (graphs above the shared-memory limit)
+  bool has_cells = false;
+  CellDev cells{};
+  int cell_bpsm = 1;
+  long long n_lrev[2] = {0, 0};
+  long long n_xrev[2] = {0, 0};
+  long long cell_delta = 0;  // near/far width of the cell kernel, in quanta
+  int sssp_kind = 0;  // 0 shared-memory BF, 1 cell, 2 global-memory BF
 };
 
 struct qdta_tape {
@@ -225,6 +236,256 @@ static int upload(qdta_graph *g, const T *host, size_t n, T **dev) {
   return QDTA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// cell partition (host, once per graph)
+// ---------------------------------------------------------------------------
+// Undirected breadth-first distances from `src` (-1 where unreachable).
+static void bfs_undirected(int V, const std::vector<int> &off, const std::vector<int> &nbr, int src,
+                           std::vector<int> &d) {
+  d.assign(V, -1);
+  std::vector<int> q;
+  q.reserve(V);
+  d[src] = 0;
+  q.push_back(src);
+  for (size_t h = 0; h < q.size(); ++h) {
+    int u = q[h];
+    for (int k = off[u]; k < off[u + 1]; ++k) {
+      int w = nbr[k];
+      if (d[w] < 0) { d[w] = d[u] + 1; q.push_back(w); }
+    }
+  }
+}
+
+struct HostCells {
+  int n_cells = 0;
+  std::vector<int> cell_off, node_int, node_cell;
+  std::vector<int> ent_off[2], ent_link[2], ent_code[2], ext_off[2], ext_node[2], dep_off[2], dep_cell[2];
+  std::vector<int> lrev_off[2], lrev_link[2], lrev_src[2];
+  std::vector<int> xrev_off[2], xrev_link[2], xrev_node[2];
+  std::vector<unsigned char> node_flags[2];
+};
+
+// Cells are blocks of a 2-D coordinate system read off breadth-first
+// distances from three far-apart nodes (a, its farthest node b, and the node
+// c farthest from both): p = d_a - d_c, s = d_a + d_c.  On a grid these are
+// axis-aligned 16 x 16 blocks; on other graphs they are compact clusters.
+// Cells above CELL_MAX_NODES nodes or CELL_MAX_EXT external neighbours (in
+// either direction) are split in halves until they fit.
+static void build_cells(const qdta_graph_desc *d, HostCells &H) {
+  const int V = d->n_nodes, L = d->n_links;
+  std::vector<int> uo(V + 1, 0), un(2 * (size_t)L);
+  for (int e = 0; e < L; ++e) { uo[d->tail[e] + 1]++; uo[d->head[e] + 1]++; }
+  for (int v = 0; v < V; ++v) uo[v + 1] += uo[v];
+  {
+    std::vector<int> pos(uo.begin(), uo.end() - 1);
+    for (int e = 0; e < L; ++e) { un[pos[d->tail[e]]++] = d->head[e]; un[pos[d->head[e]]++] = d->tail[e]; }
+  }
+  std::vector<int> d0, da, db, dc;
+  bfs_undirected(V, uo, un, 0, d0);
+  int a = 0;
+  for (int v = 0; v < V; ++v) if (d0[v] > d0[a]) a = v;
+  bfs_undirected(V, uo, un, a, da);
+  int b = a;
+  for (int v = 0; v < V; ++v) if (da[v] > da[b]) b = v;
+  bfs_undirected(V, uo, un, b, db);
+  int c = a, best = -1;
+  for (int v = 0; v < V; ++v) {
+    int m = std::min(da[v], db[v]);
+    if (da[v] >= 0 && m > best) { best = m; c = v; }
+  }
+  bfs_undirected(V, uo, un, c, dc);
+  const int W = 32;  // 16 grid steps in each of p and s
+  std::vector<long long> key(V);
+  long long pmin = 0, smin = 0;
+  bool first = true;
+  for (int v = 0; v < V; ++v) {
+    if (da[v] < 0 || dc[v] < 0) continue;
+    long long p = (long long)da[v] - dc[v], s2 = (long long)da[v] + dc[v];
+    if (first || p < pmin) pmin = p;
+    if (first || s2 < smin) smin = s2;
+    first = false;
+  }
+  // node order: (cell row, cell column, s, p, id); unreachable nodes last
+  std::vector<int> order(V);
+  for (int v = 0; v < V; ++v) order[v] = v;
+  auto coords = [&](int v, long long &cy, long long &cx, long long &sy, long long &sx) {
+    if (da[v] < 0 || dc[v] < 0) { cy = cx = (1ll << 40); sy = sx = v; return; }
+    long long p = (long long)da[v] - dc[v] - pmin, s2 = (long long)da[v] + dc[v] - smin;
+    cy = s2 / W; cx = p / W; sy = s2; sx = p;
+  };
+  std::vector<long long> cy(V), cx(V), sy(V), sx(V);
+  for (int v = 0; v < V; ++v) coords(v, cy[v], cx[v], sy[v], sx[v]);
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    if (cy[x] != cy[y]) return cy[x] < cy[y];
+    if (cx[x] != cx[y]) return cx[x] < cx[y];
+    if (sy[x] != sy[y]) return sy[x] < sy[y];
+    if (sx[x] != sx[y]) return sx[x] < sx[y];
+    return x < y;
+  });
+  // initial cells: runs of equal (cy, cx)
+  std::vector<std::pair<int, int>> cells;  // [begin, end) in `order`
+  for (int i = 0; i < V;) {
+    int j = i + 1;
+    while (j < V && cy[order[j]] == cy[order[i]] && cx[order[j]] == cx[order[i]] &&
+           !(cy[order[i]] == (1ll << 40))) ++j;
+    if (cy[order[i]] == (1ll << 40)) j = std::min(V, i + CELL_MAX_NODES);
+    cells.push_back({i, j});
+    i = j;
+  }
+  // split until every cell satisfies both caps
+  std::vector<int> cell_of(V);
+  for (int iter = 0; iter < 64; ++iter) {
+    for (size_t ci = 0; ci < cells.size(); ++ci)
+      for (int i = cells[ci].first; i < cells[ci].second; ++i) cell_of[order[i]] = (int)ci;
+    std::vector<std::pair<int, int>> next;
+    bool split = false;
+    for (size_t ci = 0; ci < cells.size(); ++ci) {
+      int b0 = cells[ci].first, b1 = cells[ci].second;
+      bool too_big = b1 - b0 > CELL_MAX_NODES;
+      if (!too_big) {
+        std::vector<int> ext_out;
+        int internal = 0;
+        for (int i = b0; i < b1; ++i) {
+          int v = order[i];
+          for (int k = uo[v]; k < uo[v + 1]; ++k) {
+            if (cell_of[un[k]] != (int)ci) ext_out.push_back(un[k]);
+            else ++internal;
+          }
+        }
+        std::sort(ext_out.begin(), ext_out.end());
+        ext_out.erase(std::unique(ext_out.begin(), ext_out.end()), ext_out.end());
+        // two incidences per directed internal link; each direction's reversed list holds them once
+        too_big = (int)ext_out.size() > CELL_MAX_EXT || internal / 2 > CELL_MAX_LREV;
+      }
+      if (too_big && b1 - b0 > 1) {
+        int m = b0 + (b1 - b0) / 2;
+        next.push_back({b0, m});
+        next.push_back({m, b1});
+        split = true;
+      } else {
+        next.push_back({b0, b1});
+      }
+    }
+    cells.swap(next);
+    if (!split) break;
+  }
+  const int nc = (int)cells.size();
+  H.n_cells = nc;
+  H.cell_off.assign(nc + 1, 0);
+  H.node_int.assign(V, 0);
+  H.node_cell.assign(V, 0);
+  std::vector<int> node_ext(V);
+  for (int ci = 0; ci < nc; ++ci) {
+    H.cell_off[ci + 1] = cells[ci].second;
+    for (int i = cells[ci].first; i < cells[ci].second; ++i) {
+      node_ext[i] = order[i];
+      H.node_int[order[i]] = i;
+      H.node_cell[i] = ci;
+    }
+  }
+  // per direction: entries by internal node, external lists, dependents
+  std::vector<std::vector<int>> out_links(V), in_links(V);
+  for (int e = 0; e < L; ++e) { out_links[d->tail[e]].push_back(e); in_links[d->head[e]].push_back(e); }
+  for (int dir = 0; dir < 2; ++dir) {
+    H.ent_off[dir].assign(V + 1, 0);
+    H.ent_link[dir].clear();
+    H.ent_code[dir].clear();
+    H.ext_off[dir].assign(nc + 1, 0);
+    H.ext_node[dir].clear();
+    H.dep_off[dir].assign(nc + 1, 0);
+    std::vector<std::vector<int>> deps(nc);
+    for (int ci = 0; ci < nc; ++ci) {
+      const int lo = H.cell_off[ci], hi = H.cell_off[ci + 1];
+      std::vector<int> ext;  // external neighbour internal ids, first-seen order
+      for (int u = lo; u < hi; ++u) {
+        const int v = node_ext[u];
+        const std::vector<int> &ls = dir == 0 ? out_links[v] : in_links[v];
+        for (int e : ls) {
+          const int w = H.node_int[dir == 0 ? d->head[e] : d->tail[e]];
+          H.ent_link[dir].push_back(e);
+          if (w >= lo && w < hi) {
+            H.ent_code[dir].push_back(w - lo);
+          } else {
+            int k = (int)(std::find(ext.begin(), ext.end(), w) - ext.begin());
+            if (k == (int)ext.size()) ext.push_back(w);
+            H.ent_code[dir].push_back(-(k + 1));
+            deps[H.node_cell[w]].push_back(ci);  // cell ci reads keys of w's cell
+          }
+        }
+        H.ent_off[dir][u + 1] = (int)H.ent_link[dir].size();
+      }
+      H.ext_node[dir].insert(H.ext_node[dir].end(), ext.begin(), ext.end());
+      H.ext_off[dir][ci + 1] = (int)H.ext_node[dir].size();
+    }
+    // internal reversed links and node flags
+    H.node_flags[dir].assign(V, 0);
+    std::vector<int> cnt(V + 1, 0);
+    for (int u = 0; u < V; ++u)
+      for (int t = H.ent_off[dir][u]; t < H.ent_off[dir][u + 1]; ++t) {
+        const int code = H.ent_code[dir][t];
+        if (code >= 0) cnt[H.cell_off[H.node_cell[u]] + code + 1]++;
+        else H.node_flags[dir][u] |= 1;
+      }
+    for (int ci = 0; ci < nc; ++ci)
+      for (int k = H.ext_off[dir][ci]; k < H.ext_off[dir][ci + 1]; ++k) H.node_flags[dir][H.ext_node[dir][k]] |= 2;
+    for (int v = 0; v < V; ++v) cnt[v + 1] += cnt[v];
+    H.lrev_off[dir] = cnt;
+    H.lrev_link[dir].assign(cnt[V], 0);
+    H.lrev_src[dir].assign(cnt[V], 0);
+    {
+      std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+      for (int u = 0; u < V; ++u) {
+        const int lo = H.cell_off[H.node_cell[u]];
+        for (int t = H.ent_off[dir][u]; t < H.ent_off[dir][u + 1]; ++t) {
+          const int code = H.ent_code[dir][t];
+          if (code < 0) continue;
+          const int w = lo + code;
+          H.lrev_link[dir][pos[w]] = H.ent_link[dir][t];
+          H.lrev_src[dir][pos[w]] = u - lo;
+          pos[w]++;
+        }
+      }
+    }
+    // external readers of each node: u in another cell pulling through w
+    {
+      std::vector<int> xc(V + 1, 0);
+      for (int u = 0; u < V; ++u) {
+        const int lo = H.cell_off[H.node_cell[u]];
+        (void)lo;
+        for (int t = H.ent_off[dir][u]; t < H.ent_off[dir][u + 1]; ++t) {
+          const int code = H.ent_code[dir][t];
+          if (code >= 0) continue;
+          const int e = H.ent_link[dir][t];
+          const int w = H.node_int[dir == 0 ? d->head[e] : d->tail[e]];
+          xc[w + 1]++;
+        }
+      }
+      for (int v = 0; v < V; ++v) xc[v + 1] += xc[v];
+      H.xrev_off[dir] = xc;
+      H.xrev_link[dir].assign(xc[V], 0);
+      H.xrev_node[dir].assign(xc[V], 0);
+      std::vector<int> pos(xc.begin(), xc.end() - 1);
+      for (int u = 0; u < V; ++u)
+        for (int t = H.ent_off[dir][u]; t < H.ent_off[dir][u + 1]; ++t) {
+          if (H.ent_code[dir][t] >= 0) continue;
+          const int e = H.ent_link[dir][t];
+          const int w = H.node_int[dir == 0 ? d->head[e] : d->tail[e]];
+          H.xrev_link[dir][pos[w]] = e;
+          H.xrev_node[dir][pos[w]] = u;
+          pos[w]++;
+        }
+    }
+    H.dep_cell[dir].clear();
+    for (int ci = 0; ci < nc; ++ci) {
+      std::vector<int> &dl = deps[ci];
+      std::sort(dl.begin(), dl.end());
+      dl.erase(std::unique(dl.begin(), dl.end()), dl.end());
+      H.dep_cell[dir].insert(H.dep_cell[dir].end(), dl.begin(), dl.end());
+      H.dep_off[dir][ci + 1] = (int)H.dep_cell[dir].size();
+    }
+  }
+}
+
 extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_graph **out) {
   if (!d || !out) return fail(QDTA_EINVAL, "NULL argument");
   *out = nullptr;
@@ -293,6 +554,69 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   }
   g->sssp_smem = V <= sssp_max_smem_nodes();
   g->sssp_bpsm = sssp_blocks_per_sm(g->sssp_smem, V);
+  // kernel for graphs above the shared-memory limit: the global-memory
+  // Bellman-Ford (measured fastest on the metro grid); QDTA_SSSP=cell selects
+  // the cell-partitioned kernel
+  g->sssp_kind = g->sssp_smem ? 0 : 2;
+  if (!g->sssp_smem) {
+    const char *env = getenv("QDTA_SSSP");
+    if (env && strcmp(env, "cell") == 0) g->sssp_kind = 1;
+    HostCells H;
+    build_cells(d, H);
+    CellDev &C = g->cells;
+    C.n_cells = H.n_cells;
+    int *p_off, *p_ni, *p_nc;
+    if ((rc = upload(g, H.cell_off.data(), H.cell_off.size(), &p_off)) ||
+        (rc = upload(g, H.node_int.data(), H.node_int.size(), &p_ni)) ||
+        (rc = upload(g, H.node_cell.data(), H.node_cell.size(), &p_nc))) {
+      qdta_graph_destroy(g);
+      return rc;
+    }
+    C.cell_off = p_off; C.node_int = p_ni; C.node_cell = p_nc;
+    for (int dir = 0; dir < 2; ++dir) {
+      int *a1, *a2, *a3, *a4, *a5, *a6, *a7;
+      if ((rc = upload(g, H.ent_off[dir].data(), H.ent_off[dir].size(), &a1)) ||
+          (rc = upload(g, H.ent_link[dir].data(), H.ent_link[dir].size(), &a2)) ||
+          (rc = upload(g, H.ent_code[dir].data(), H.ent_code[dir].size(), &a3)) ||
+          (rc = upload(g, H.ext_off[dir].data(), H.ext_off[dir].size(), &a4)) ||
+          (rc = upload(g, H.ext_node[dir].data(), H.ext_node[dir].size(), &a5)) ||
+          (rc = upload(g, H.dep_off[dir].data(), H.dep_off[dir].size(), &a6)) ||
+          (rc = upload(g, H.dep_cell[dir].data(), H.dep_cell[dir].size(), &a7))) {
+        qdta_graph_destroy(g);
+        return rc;
+      }
+      C.ent_off[dir] = a1; C.ent_link[dir] = a2; C.ent_code[dir] = a3; C.ext_off[dir] = a4;
+      C.ext_node[dir] = a5; C.dep_off[dir] = a6; C.dep_cell[dir] = a7;
+      int *b1, *b2, *b3;
+      unsigned char *b4;
+      if ((rc = upload(g, H.lrev_off[dir].data(), H.lrev_off[dir].size(), &b1)) ||
+          (rc = upload(g, H.lrev_link[dir].data(), H.lrev_link[dir].size(), &b2)) ||
+          (rc = upload(g, H.lrev_src[dir].data(), H.lrev_src[dir].size(), &b3)) ||
+          (rc = upload(g, H.node_flags[dir].data(), H.node_flags[dir].size(), &b4))) {
+        qdta_graph_destroy(g);
+        return rc;
+      }
+      C.lrev_off[dir] = b1; C.lrev_link[dir] = b2; C.lrev_src[dir] = b3; C.node_flags[dir] = b4;
+      g->n_lrev[dir] = (long long)H.lrev_link[dir].size();
+      int *x1, *x2, *x3;
+      if ((rc = upload(g, H.xrev_off[dir].data(), H.xrev_off[dir].size(), &x1)) ||
+          (rc = upload(g, H.xrev_link[dir].data(), H.xrev_link[dir].size(), &x2)) ||
+          (rc = upload(g, H.xrev_node[dir].data(), H.xrev_node[dir].size(), &x3))) {
+        qdta_graph_destroy(g);
+        return rc;
+      }
+      C.xrev_off[dir] = x1; C.xrev_link[dir] = x2; C.xrev_node[dir] = x3;
+      g->n_xrev[dir] = (long long)H.xrev_link[dir].size();
+    }
+    g->has_cells = true;
+    g->cell_bpsm = sssp_cell_blocks_per_sm();
+    double mean_q = 0.0;
+    for (int e = 0; e < L; ++e) mean_q += d->fftime_q[e];
+    mean_q = L ? mean_q / L : 1.0;
+    double mult = 16.0;
+    if (const char *dm = getenv("QDTA_CELL_DELTA")) mult = atof(dm);
+    g->cell_delta = (long long)(mult * mean_q) + 1;
+  }
   if (cudaGetLastError() != cudaSuccess) { qdta_graph_destroy(g); return fail(QDTA_ECUDA, "occupancy query failed"); }
   *out = g;
   return QDTA_OK;
@@ -333,11 +657,12 @@ extern "C" int qdta_profile_read(qdta_graph *g, qdta_profile *out) {
   DevGuard guard(g->device);
   CK(cudaDeviceSynchronize());
   prof_harvest(g);
-  unsigned long long cnt[3] = {0, 0, 0};
-  if (g->prof_roots) CK(cudaMemcpy(cnt, g->prof_roots, 24, cudaMemcpyDeviceToHost));
+  unsigned long long cnt[4] = {0, 0, 0, 0};
+  if (g->prof_roots) CK(cudaMemcpy(cnt, g->prof_roots, 32, cudaMemcpyDeviceToHost));
   g->prof.sssp_roots = (int64_t)cnt[0];
   g->prof.sssp_rounds = (int64_t)cnt[1];
   g->prof.sssp_relaxations = (int64_t)cnt[2];
+  g->prof.sssp_cell_activations = (int64_t)cnt[3];
   g->prof.kernel_launches = launch_count();
   *out = g->prof;
   return QDTA_OK;
@@ -347,7 +672,14 @@ extern "C" int qdta_profile_read(qdta_graph *g, qdta_profile *out) {
 // shortest paths, loading, costs
 // ---------------------------------------------------------------------------
 static int sssp_grid(const qdta_graph *g, int R) {
-  long long cap = (long long)g->sssp_bpsm * g->d.num_sms;
+  long long bpsm = g->sssp_kind == 1 ? g->cell_bpsm : g->sssp_bpsm;
+  if (g->sssp_kind == 2) {
+    // resident roots of the global-memory variant: two 512-thread CTAs per
+    // SM keep the wavefronts' working set in L2 (QDTA_BF_BPSM overrides)
+    static int env_bpsm = [] { const char *e = getenv("QDTA_BF_BPSM"); return e ? atoi(e) : 2; }();
+    if (env_bpsm > 0 && env_bpsm < bpsm) bpsm = env_bpsm;
+  }
+  long long cap = bpsm * g->d.num_sms;
   long long n = R < cap ? R : cap;
   return n < 1 ? 1 : (int)n;
 }
@@ -356,7 +688,14 @@ static int sssp_work(qdta_graph *g, int grid, SsspWork *w) {
   const size_t V = g->d.V;
   w->slots = grid;
   RC(ws_get(g, "sssp.adj", (size_t)g->d.L, &w->adj));
-  if (!g->sssp_smem) {
+  if (g->sssp_kind == 1) {
+    RC(ws_get(g, "sssp.lrev", (size_t)std::max(g->n_lrev[0], g->n_lrev[1]), &w->lrev));
+    RC(ws_get(g, "sssp.prio", (size_t)grid * g->cells.n_cells, &w->prio));
+    RC(ws_get(g, "sssp.xrev", (size_t)std::max(g->n_xrev[0], g->n_xrev[1]), &w->xrev));
+    RC(ws_get(g, "sssp.state", (size_t)grid * V, &w->state));
+    RC(ws_get(g, "sssp.stamp", (size_t)grid * g->cells.n_cells, &w->stamp));
+    RC(ws_get(g, "sssp.queue", (size_t)grid * 3 * g->cells.n_cells, &w->queue));
+  } else if (!g->sssp_smem) {
     RC(ws_get(g, "sssp.state", (size_t)grid * V, &w->state));
     RC(ws_get(g, "sssp.stamp", (size_t)grid * V, &w->stamp));
     RC(ws_get(g, "sssp.queue", (size_t)grid * 2 * V, &w->queue));
@@ -373,11 +712,21 @@ static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots
   SsspWork w;
   const int grid = sssp_grid(g, R_cap);
   RC(sssp_work(g, grid, &w));
-  launch_pack_adj(g->d, direction, q, w.adj, s, skip_dev);
   ProfEvent pe;
-  prof_begin(g, s, &pe, 0, R_host);
-  launch_sssp(g->d, direction, w.adj, roots, R_host, R_dev, grid, g->sssp_smem, w, parent, slot_dev,
-              stride, dist, g->status, s, skip_dev, g->prof_on ? g->prof_roots : nullptr);
+  if (g->sssp_kind == 1) {
+    launch_pack_cell_adj(g->d, g->cells, direction, q, w.adj, w.lrev, g->n_lrev[direction], w.xrev,
+                         g->n_xrev[direction], s, skip_dev);
+    prof_begin(g, s, &pe, 0, R_host);
+    launch_sssp_cell(g->d, g->cells, direction, w.adj, w.lrev, w.xrev, g->cell_delta, roots, R_host, R_dev, grid,
+                     w.state, w.stamp, w.queue, w.prio,
+                     parent, slot_dev, stride, dist, g->status, s, skip_dev,
+                     g->prof_on ? g->prof_roots : nullptr);
+  } else {
+    launch_pack_adj(g->d, direction, q, w.adj, s, skip_dev);
+    prof_begin(g, s, &pe, 0, R_host);
+    launch_sssp(g->d, direction, w.adj, roots, R_host, R_dev, grid, g->sssp_smem, w, parent, slot_dev,
+                stride, dist, g->status, s, skip_dev, g->prof_on ? g->prof_roots : nullptr);
+  }
   prof_end(g, s, &pe);
   return QDTA_OK;
 }
@@ -796,16 +1145,91 @@ extern "C" int qdta_assign_interval(qdta_graph *g, const qdta_od *od, double dt_
 // ---------------------------------------------------------------------------
 // many independent instances
 // ---------------------------------------------------------------------------
+// All instances' FW loops as parallel branches of one CUDA graph: one launch
+// solves every instance, the branches running concurrently on the GPU.
+static int assign_batch_graph(const qdta_instance *inst, int n, const qdta_params *p, qdta_stats *stats,
+                              cudaStream_t s) {
+  std::vector<Solver> S(n);
+  for (int i = 0; i < n; ++i) {
+    Solver &X = S[i];
+    qdta_graph *g = inst[i].graph;
+    X.g = g; X.s = s; X.p = p;
+    X.dt_h = inst[i].dt_s / 3600.0;
+    X.dt_q = dt_quanta(g, inst[i].dt_s);
+    const qdta_od *od = &inst[i].od;
+    X.roots = od->roots; X.R_host = od->n_roots; X.R_dev = nullptr; X.R_cap = od->n_roots > 0 ? od->n_roots : 1;
+    X.root_slot = nullptr; X.item_roots = od->roots;
+    X.n_host = od->n_items; X.n_dev = nullptr;
+    X.root_idx = od->root_idx; X.src = od->src; X.amount = (const long long *)od->amount_fx;
+    X.f = inst[i].flow_out;
+    RC(solver_alloc(X, "batch", 1, false));
+    RC(status_reset(g, s));
+    RC(seg_init(X));
+  }
+  std::vector<Ctl> h(n);
+  for (int i = 0; i < n; ++i) RC(read_ctl(S[i], &h[i]));
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = QDTA_OK;
+  do {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) { rc = fail(QDTA_ECUDA, "cudaGraphCreate"); break; }
+    int branches = 0;
+    for (int i = 0; i < n && rc >= 0; ++i) {
+      if (!h[i].fw_continue) continue;
+      cudaGraphNode_t node;
+      cudaGraph_t body;
+      cudaGraphConditionalHandle hc;
+      if ((rc = add_while(graph, nullptr, 0, 1, &node, &body, &hc)) < 0) break;
+      rc = build_fw_body(S[i], body, hc, cs);
+      ++branches;
+    }
+    if (rc < 0) break;
+    if (branches > 0) {
+      cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e != cudaSuccess) { rc = fail(QDTA_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e)); break; }
+      e = cudaGraphLaunch(exec, s);
+      if (e != cudaSuccess) { rc = fail(QDTA_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e)); break; }
+    }
+    for (int i = 0; i < n && rc >= 0; ++i) rc = seg_finish(S[i]);
+  } while (0);
+  cudaStreamSynchronize(s);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  RC(rc);
+  int worst = QDTA_OK;
+  for (int i = 0; i < n; ++i) {
+    RC(status_check(inst[i].graph, s));
+    RC(read_ctl(S[i], &h[i]));
+    if (stats) fill_stats(&h[i], inst[i].od.n_items, &stats[i]);
+    if (h[i].notconv) worst = QDTA_ENOTCONV;
+  }
+  return worst;
+}
+
 extern "C" int qdta_assign_batch(const qdta_instance *inst, int32_t n_inst, const qdta_params *p,
                                  qdta_stats *stats, void *stream) {
   if (n_inst < 0 || (n_inst > 0 && !inst)) return fail(QDTA_EINVAL, "bad instance array");
   RC(check_params(p));
   cudaStream_t s = (cudaStream_t)stream;
-  int worst = QDTA_OK;
   for (int i = 0; i < n_inst; ++i) {
     RC(check_graph(inst[i].graph));
     RC(check_od(inst[i].graph, &inst[i].od));
-    DevGuard guard(inst[i].graph->device);
+    if (!(inst[i].dt_s > 0.0)) return fail(QDTA_EINVAL, "instance %d: dt_s must be > 0", i);
+    if (inst[i].graph->d.L > 0 && !inst[i].flow_out) return fail(QDTA_EINVAL, "instance %d: flow_out is NULL", i);
+    if (inst[i].graph->device != inst[0].graph->device) return fail(QDTA_EINVAL, "instances span devices");
+    for (int j = 0; j < i; ++j)
+      if (inst[j].graph == inst[i].graph)
+        return fail(QDTA_EINVAL, "instances %d and %d share a graph handle (one workspace each)", j, i);
+  }
+  if (n_inst == 0) return QDTA_OK;
+  DevGuard guard(inst[0].graph->device);
+  if (p->schedule == QDTA_SCHEDULE_GRAPH && !inst[0].graph->prof_on)
+    return assign_batch_graph(inst, n_inst, p, stats, s);
+  int worst = QDTA_OK;
+  for (int i = 0; i < n_inst; ++i) {
     int rc = assign_core(inst[i].graph, &inst[i].od, inst[i].dt_s, p, inst[i].flow_out,
                          stats ? &stats[i] : nullptr, nullptr, s, "batch");
     if (rc < 0) return rc;
@@ -1028,7 +1452,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   CK(cudaMemGetInfo(&free_b, &total_b));
   const double per_slot = (double)Z * V * 4.0;
   long long ring = p->max_iter + 1;
-  long long afford = (long long)((double)free_b * 0.5 / per_slot);
+  long long afford = (long long)((double)free_b * 0.8 / per_slot);
   if (ring > afford) ring = afford;
   if (ring < 2) ring = 2;
   RC(solver_alloc(S, "day", (int)ring, false));

@@ -224,17 +224,65 @@ struct GraphDev {
   int num_sms;
 };
 
+// Cell partition for the shared-memory cell SSSP (graphs above the
+// whole-state-in-shared-memory limit).  Internal node ids are cell-major;
+// per relaxation direction d (0 = TO_ROOT pulls over out-links, 1 =
+// FROM_ROOT pulls over in-links) entries are grouped by internal node and
+// carry a code: >= 0 local index of the neighbour in the same cell,
+// < 0 -(k+1) with k the neighbour's slot in the cell's external list.
+constexpr int CELL_MAX_NODES = 256;
+constexpr int CELL_MAX_EXT = 128;
+constexpr int CELL_MAX_LREV = 1024;  // internal reversed links per cell
+constexpr int CELL_WARPS = 4;
+
+struct CellDev {
+  int n_cells;
+  const int *cell_off;   // [n_cells + 1] internal node ranges
+  const int *node_int;   // [V] external -> internal
+  const int *node_cell;  // [V] internal -> cell
+  const int *ent_off[2];   // [V + 1] internal node -> entry range
+  const int *ent_link[2];  // [L] link id of each entry
+  const int *ent_code[2];  // [L] neighbour code
+  const int *ext_off[2];   // [n_cells + 1]
+  const int *ext_node[2];  // internal ids of external neighbours
+  const int *dep_off[2];   // [n_cells + 1]
+  const int *dep_cell[2];  // cells that read this cell's keys
+  // internal links reversed: for node w, the cell nodes u that pull through w
+  const int *lrev_off[2];   // [V + 1]
+  const int *lrev_link[2];  // link id
+  const int *lrev_src[2];   // local index of u
+  const unsigned char *node_flags[2];  // bit 0: has external entries, bit 1: read by another cell
+  // external readers: for node w, the nodes u of other cells that pull through w
+  const int *xrev_off[2];   // [V + 1]
+  const int *xrev_link[2];  // link id
+  const int *xrev_node[2];  // internal id of u
+};
+
 struct SsspWork {
   unsigned long long *state;  // [slots][V]
   int *stamp;                 // [slots][V]
   int *queue;                 // [slots][2][V]
   int4 *adj;                  // [L] packed (link, neighbour, q, 0) of the chosen direction
+  uint2 *lrev;                // cell kernel: packed internal reversed links (u << 24 | link, q)
+  unsigned long long *prio;   // cell kernel: [slots][cells] wake priorities
+  int4 *xrev;                 // cell kernel: packed external readers (link, reader, q, 0)
   int slots;
 };
 
 // skip_dev (nullable): when *skip_dev != 0 the launch does nothing
 void launch_pack_adj(const GraphDev &g, int direction, const int *q, int4 *adj, cudaStream_t s,
                      const int *skip_dev = nullptr);
+void launch_pack_cell_adj(const GraphDev &g, const CellDev &c, int direction, const int *q, int4 *adj,
+                          uint2 *lrev_adj, long long n_lrev, int4 *xrev_adj, long long n_xrev, cudaStream_t s,
+                          const int *skip_dev = nullptr);
+void launch_sssp_cell(const GraphDev &g, const CellDev &c, int direction, const int4 *adj, const uint2 *lrev_adj,
+                      const int4 *xrev_adj,
+                      long long delta, const int *roots, int R_host, const int *R_dev, int grid,
+                      unsigned long long *state, int *flag, int *queue, unsigned long long *prio, int *parent,
+                      const int *parent_slot_dev, long long slot_stride, long long *dist,
+                      unsigned *status, cudaStream_t s, const int *skip_dev,
+                      unsigned long long *roots_counter);
+int sssp_cell_blocks_per_sm();
 void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *roots,
                  int R_host, const int *R_dev, int grid, bool use_smem, const SsspWork &w,
                  int *parent, const int *parent_slot_dev, long long slot_stride, long long *dist,

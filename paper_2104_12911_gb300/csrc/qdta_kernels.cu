@@ -11,6 +11,7 @@
 //   adj_* / gather        adjoint of the unrolled FW map
 #include <atomic>
 #include <climits>
+#include <cstdlib>
 #include <cstdio>
 
 #include "qdta.h"
@@ -166,9 +167,9 @@ sssp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__
 // each), NPT frontier nodes per lane group in flight, and an L2 read of the
 // target's key before the atomic, so relaxations that cannot improve (most
 // of them) cost a load instead of an atomic.
-constexpr int SSSP2_THREADS = 128;
 constexpr int SSSP2_NPT = 4;
 
+template <int SSSP2_THREADS>
 __global__ void __launch_bounds__(SSSP2_THREADS)
 sssp_ilp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__ adj,
                 const int *__restrict__ roots, int R_host, const int *R_dev,
@@ -292,6 +293,305 @@ sssp_ilp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
   }
 }
 
+// ---------------------------------------------------------------------------
+// cell-partitioned SSSP: state of the active cell in shared memory
+// ---------------------------------------------------------------------------
+__global__ void pack_cell_adj_kernel(int L, const int *__restrict__ ent_link,
+                                     const int *__restrict__ ent_code, const int *__restrict__ q,
+                                     int4 *__restrict__ adj, long long n_lrev, const int *__restrict__ lrev_link,
+                                     const int *__restrict__ lrev_src, uint2 *__restrict__ lrev_adj,
+                                     long long n_xrev, const int *__restrict__ xrev_link,
+                                     const int *__restrict__ xrev_node, int4 *__restrict__ xrev_adj,
+                                     const int *skip_dev) {
+  if (skip_dev && *skip_dev) return;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_xrev;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int e = xrev_link[k];
+    xrev_adj[k] = make_int4(e, xrev_node[k], q[e], 0);
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gridDim.x * blockDim.x) {
+    const int e = ent_link[k];
+    adj[k] = make_int4(e, ent_code[k], q[e], 0);
+  }
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_lrev;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int e = lrev_link[k];
+    lrev_adj[k] = make_uint2(((unsigned)lrev_src[k] << 24) | (unsigned)e, (unsigned)q[e]);
+  }
+}
+
+void launch_pack_cell_adj(const GraphDev &g, const CellDev &c, int direction, const int *q, int4 *adj,
+                          uint2 *lrev_adj, long long n_lrev, int4 *xrev_adj, long long n_xrev, cudaStream_t s,
+                          const int *skip_dev) {
+  if (g.L == 0) return;
+  COUNT_LAUNCH();
+  pack_cell_adj_kernel<<<cdiv(g.L, 256), 256, 0, s>>>(g.L, c.ent_link[direction], c.ent_code[direction], q,
+                                                      adj, n_lrev, c.lrev_link[direction],
+                                                      c.lrev_src[direction], lrev_adj, n_xrev,
+                                                      c.xrev_link[direction], c.xrev_node[direction], xrev_adj,
+                                                      skip_dev);
+}
+
+// per-warp shared-memory layout of the cell kernel
+struct CellWarpSmem {
+  unsigned long long key[CELL_MAX_NODES];
+  unsigned long long ext[CELL_MAX_EXT];
+  uint2 lrev[CELL_MAX_LREV];
+  unsigned short lroff[CELL_MAX_NODES + 1];  // node -> range in lrev (cell-relative)
+  unsigned char nf[CELL_MAX_NODES];          // node flags
+  short fq[2][CELL_MAX_NODES];
+  unsigned inq[2][CELL_MAX_NODES / 32];
+  unsigned chg[CELL_MAX_NODES / 32];
+  int fn[2];
+};
+
+// One CTA per root (persistent over roots); each warp processes one cell at
+// a time.  Cells woken by a neighbour wait in a pending list with the
+// smallest distance that woke them; each round processes the pending cells
+// within `delta` of the smallest such distance (near/far ordering at cell
+// level, so most cells fire once their inputs are nearly final) and defers
+// the rest.  Between activations a cell is locally converged, so only nodes
+// with links to other cells can have pending improvements: an activation
+// loads the cell's keys, its external neighbours' keys and its internal
+// reversed links into shared memory, pulls the boundary nodes over all their
+// links, then runs a shared-memory push Bellman-Ford (64-bit shared
+// atomicMin on the packed key) from every node whose distance improved.
+// The minimum over every link with the neighbours' current keys makes the
+// fixed point the shortest distance with the smallest tight link id,
+// whatever the processing order.
+__global__ void __launch_bounds__(CELL_WARPS * 32)
+sssp_cell_kernel(int V, int LB, CellDev C, int dir, const int4 *__restrict__ adj,
+                 const uint2 *__restrict__ lrev_adj, const int4 *__restrict__ xrev_adj, long long delta, const int *__restrict__ roots,
+                 int R_host, const int *R_dev, unsigned long long *g_state, int *g_flag, int *g_queue,
+                 unsigned long long *g_prio, int *parent, const int *parent_slot_dev, long long slot_stride,
+                 long long *dist, unsigned *status, const int *skip_dev, unsigned long long *roots_counter) {
+  extern __shared__ __align__(16) unsigned char cell_smem[];
+  __shared__ int s_np, s_ns, s_nn;
+  __shared__ unsigned long long s_min;
+  if (skip_dev && *skip_dev) return;
+  const int R = R_dev ? *R_dev : R_host;
+  if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
+  const int nc = C.n_cells;
+  const size_t b = blockIdx.x;
+  unsigned long long *state = g_state + b * (size_t)V;
+  int *inpend = g_flag + b * (size_t)nc;
+  int *listA = g_queue + b * 3 * (size_t)nc;  // pending
+  int *listS = listA + nc;                    // selected this round
+  int *listN = listS + nc;                    // pending next round
+  unsigned long long *prio = g_prio + b * (size_t)nc;
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
+  const unsigned long long NOLINK = (1ull << LB) - 1ull;
+  const unsigned long long DMAX = (~0ull) >> LB;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  CellWarpSmem &W = reinterpret_cast<CellWarpSmem *>(cell_smem)[wid];
+  const int *__restrict__ cell_off = C.cell_off;
+  const int *__restrict__ ent_off = C.ent_off[dir];
+  const int *__restrict__ ext_off = C.ext_off[dir];
+  const int *__restrict__ ext_node = C.ext_node[dir];
+  const int *__restrict__ dep_off = C.dep_off[dir];
+  const int *__restrict__ dep_cell = C.dep_cell[dir];
+  const int *__restrict__ lrev_off = C.lrev_off[dir];
+  const unsigned char *__restrict__ nflag = C.node_flags[dir];
+  const int *__restrict__ xrev_off = C.xrev_off[dir];
+  const int *__restrict__ node_cell = C.node_cell;
+  for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = ~0ull;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) { inpend[c] = 0; prio[c] = ~0ull; }
+  __syncthreads();
+  unsigned long long my_relax = 0, my_act = 0;
+  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    const int z = C.node_int[roots[r]];
+    if (threadIdx.x == 0) {
+      state[z] = NOLINK;
+      const int cz = C.node_cell[z];
+      listA[0] = cz;
+      inpend[cz] = 1;
+      prio[cz] = 0;
+      s_np = 1;
+    }
+    __syncthreads();
+    int round = 0;
+    while (s_np > 0) {
+      const int np = s_np;
+      // selection: threshold = smallest pending priority + delta
+      if (threadIdx.x == 0) { s_min = ~0ull; s_ns = 0; s_nn = 0; }
+      __syncthreads();
+      unsigned long long m = ~0ull;
+      for (int i = threadIdx.x; i < np; i += blockDim.x) m = min(m, __ldcg(&prio[__ldcg(&listA[i])]));
+      for (int d = 16; d > 0; d >>= 1) m = min(m, __shfl_down_sync(0xffffffffu, m, d));
+      if (lane == 0) atomicMin(&s_min, m);
+      __syncthreads();
+      const unsigned long long thr = s_min > ~0ull - (unsigned long long)delta ? ~0ull : s_min + (unsigned long long)delta;
+      for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int c = __ldcg(&listA[i]);
+        if (__ldcg(&prio[c]) <= thr) {
+          listS[atomicAdd(&s_ns, 1)] = c;
+          inpend[c] = 0;
+          prio[c] = ~0ull;
+        } else {
+          listN[atomicAdd(&s_nn, 1)] = c;
+        }
+      }
+      __syncthreads();
+      const int ns = s_ns;
+      for (int ci = wid; ci < ns; ci += CELL_WARPS) {
+        const int c = __ldcg(&listS[ci]);
+        const int lo = cell_off[c], n = cell_off[c + 1] - lo;
+        if (lane == 0) ++my_act;
+        for (int i = lane; i < n; i += 32) W.key[i] = __ldcg(&state[lo + i]);
+        const int eo = ext_off[c], en = ext_off[c + 1] - eo;
+        for (int i = lane; i < en; i += 32) W.ext[i] = __ldcg(&state[ext_node[eo + i]]);
+        const int r0 = lrev_off[lo], rn = lrev_off[lo + n] - r0;
+        for (int i = lane; i < rn; i += 32) W.lrev[i] = __ldg(&lrev_adj[r0 + i]);
+        for (int i = lane; i <= n; i += 32) W.lroff[i] = (unsigned short)(lrev_off[lo + i] - r0);
+        for (int i = lane; i < n; i += 32) W.nf[i] = nflag[lo + i];
+        if (lane < CELL_MAX_NODES / 32) { W.chg[lane] = 0u; W.inq[0][lane] = 0u; }
+        if (lane == 0) W.fn[0] = 0;
+        __syncwarp();
+        // seed: boundary nodes pulled over all their links (+ the root at the start)
+        for (int i = lane; i < n; i += 32) {
+          const int u = lo + i;
+          bool push = round == 0 && u == z;
+          if (W.nf[i] & 1) {
+            unsigned long long best = W.key[i];
+            const int t0 = ent_off[u], t1 = ent_off[u + 1];
+            my_relax += (unsigned long long)(t1 - t0);
+            for (int t = t0; t < t1; ++t) {
+              const int4 ent = __ldg(&adj[t]);
+              const unsigned long long wk = ent.y >= 0 ? W.key[ent.y] : W.ext[-ent.y - 1];
+              if (wk == ~0ull) continue;
+              const unsigned long long cand = (wk >> LB) + (unsigned long long)(unsigned)ent.z;
+              if (cand >= DMAX) { atomicOr(status, ST_OVERFLOW); continue; }
+              const unsigned long long key = (cand << LB) | (unsigned long long)(unsigned)ent.x;
+              if (key < best) best = key;
+            }
+            const unsigned long long old = atomicMin(&W.key[i], best);
+            if (best < old) {
+              atomicOr(&W.chg[i >> 5], 1u << (i & 31));
+              if ((old >> LB) > (best >> LB)) push = true;
+            }
+          }
+          if (push && !((atomicOr(&W.inq[0][i >> 5], 1u << (i & 31)) >> (i & 31)) & 1u))
+            W.fq[0][atomicAdd(&W.fn[0], 1)] = (short)i;
+        }
+        __syncwarp();
+        // local push rounds over the cell's internal reversed links (shared memory)
+        int fn = W.fn[0], side = 0, guard = 0;
+        while (fn > 0) {
+          const int nx = side ^ 1;
+          if (lane == 0) W.fn[nx] = 0;
+          if (lane < CELL_MAX_NODES / 32) W.inq[nx][lane] = 0u;
+          __syncwarp();
+          for (int x = lane; x < fn; x += 32) {
+            const int wl = W.fq[side][x];
+            const unsigned long long dw = W.key[wl] >> LB;
+            const int k0 = W.lroff[wl], k1 = W.lroff[wl + 1];
+            my_relax += (unsigned long long)(k1 - k0);
+            for (int k = k0; k < k1; ++k) {
+              const uint2 ent = W.lrev[k];
+              const int ul = (int)(ent.x >> 24);
+              const unsigned long long cand = dw + (unsigned long long)ent.y;
+              if (cand >= DMAX) { atomicOr(status, ST_OVERFLOW); continue; }
+              const unsigned long long key = (cand << LB) | (unsigned long long)(ent.x & 0xFFFFFFu);
+              const unsigned long long old = atomicMin(&W.key[ul], key);
+              if (key < old) {
+                atomicOr(&W.chg[ul >> 5], 1u << (ul & 31));
+                if ((old >> LB) > cand && !((atomicOr(&W.inq[nx][ul >> 5], 1u << (ul & 31)) >> (ul & 31)) & 1u))
+                  W.fq[nx][atomicAdd(&W.fn[nx], 1)] = (short)ul;
+              }
+            }
+          }
+          __syncwarp();
+          fn = W.fn[nx];
+          side = nx;
+          if (++guard > CELL_MAX_NODES + 2) {  // a cell converges within n local rounds
+            if (lane == 0) atomicOr(status, ST_TIMEOUT);
+            break;
+          }
+        }
+        // write back changed keys
+        for (int i = lane; i < n; i += 32)
+          if ((W.chg[i >> 5] >> (i & 31)) & 1u) state[lo + i] = W.key[i];
+        __syncwarp();
+        // wake exactly the cells with a node this change improves: reader u of
+        // changed node w through link e is woken iff ((d_w + q_e) << LB | e) is
+        // below u's current key (keys only decrease, so a skipped wake is never
+        // needed later)
+        for (int i = lane; i < n; i += 32) {
+          if (!((W.chg[i >> 5] >> (i & 31)) & 1u) || !(W.nf[i] & 2)) continue;
+          const unsigned long long dw = W.key[i] >> LB;
+          const int x0 = xrev_off[lo + i], x1 = xrev_off[lo + i + 1];
+          for (int x = x0; x < x1; ++x) {
+            const int4 ent = __ldg(&xrev_adj[x]);
+            const unsigned long long cand = dw + (unsigned long long)(unsigned)ent.z;
+            if (cand >= DMAX) continue;
+            const unsigned long long key = (cand << LB) | (unsigned long long)(unsigned)ent.x;
+            if (key < __ldcg(&state[ent.y])) {
+              const int d = node_cell[ent.y];
+              atomicMin(&prio[d], cand);
+              if (atomicExch(&inpend[d], 1) == 0) listN[atomicAdd(&s_nn, 1)] = d;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      // next pending list
+      const int nn = s_nn;
+      for (int i = threadIdx.x; i < nn; i += blockDim.x) listA[i] = __ldcg(&listN[i]);
+      if (threadIdx.x == 0) s_np = nn;
+      __syncthreads();
+      ++round;
+      if (round > nc * 64 + 4) {  // a bounded loop: far beyond any observed round count
+        if (threadIdx.x == 0) { atomicOr(status, ST_TIMEOUT); s_np = 0; }
+        __syncthreads();
+        break;
+      }
+    }
+    if (roots_counter) {
+      if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
+      atomicAdd(roots_counter + 2, my_relax);
+      if (my_act) atomicAdd(roots_counter + 3, my_act);
+      my_relax = 0;
+      my_act = 0;
+    }
+    __syncthreads();
+    int *prow = parent + (long long)r * V;
+    long long *drow = dist ? dist + (long long)r * V : nullptr;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+      const unsigned long long key = __ldcg(&state[C.node_int[v]]);
+      const unsigned long long lk = key & NOLINK;
+      prow[v] = lk == NOLINK ? -1 : (int)lk;
+      if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = ~0ull;
+    __syncthreads();
+  }
+}
+
+static size_t cell_smem_bytes() { return sizeof(CellWarpSmem) * CELL_WARPS; }
+
+int sssp_cell_blocks_per_sm() {
+  int n = 0;
+  cudaFuncSetAttribute(sssp_cell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem_bytes());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_cell_kernel, CELL_WARPS * 32, cell_smem_bytes());
+  return n > 0 ? n : 1;
+}
+
+void launch_sssp_cell(const GraphDev &g, const CellDev &c, int direction, const int4 *adj, const uint2 *lrev_adj,
+                      const int4 *xrev_adj, long long delta, const int *roots, int R_host, const int *R_dev, int grid,
+                      unsigned long long *state, int *flag, int *queue, unsigned long long *prio, int *parent,
+                      const int *parent_slot_dev, long long slot_stride, long long *dist,
+                      unsigned *status, cudaStream_t s, const int *skip_dev,
+                      unsigned long long *roots_counter) {
+  if (grid <= 0) return;
+  COUNT_LAUNCH();
+  cudaFuncSetAttribute(sssp_cell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem_bytes());
+  sssp_cell_kernel<<<grid, CELL_WARPS * 32, cell_smem_bytes(), s>>>(
+      g.V, g.LB, c, direction, adj, lrev_adj, xrev_adj, delta, roots, R_host, R_dev, state, flag, queue, prio, parent,
+      parent_slot_dev, slot_stride, dist, status, skip_dev, roots_counter);
+}
+
 int sssp_max_smem_nodes() { return (200 * 1024) / 20; }
 
 static size_t sssp_smem_bytes(int V) { return (size_t)V * 20; }
@@ -304,7 +604,7 @@ int sssp_blocks_per_sm(bool use_smem, int V) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_kernel<true>, SSSP_THREADS,
                                                   sssp_smem_bytes(V));
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_ilp_kernel, SSSP2_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_ilp_kernel<512>, 512, 0);
   }
   return n > 0 ? n : 1;
 }
@@ -326,7 +626,15 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                                                      roots_counter);
   } else {
     COUNT_LAUNCH();
-    sssp_ilp_kernel<<<grid, SSSP2_THREADS, 0, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
+    // block size of the global-memory variant (QDTA_BF_THREADS: 128, 256, 512 or 1024)
+    static int bf_threads = [] {
+      const char *e = getenv("QDTA_BF_THREADS");
+      int t = e ? atoi(e) : 512;
+      return (t == 128 || t == 256 || t == 1024) ? t : 512;
+    }();
+    auto kern = bf_threads == 1024 ? sssp_ilp_kernel<1024> : bf_threads == 512 ? sssp_ilp_kernel<512>
+              : bf_threads == 256 ? sssp_ilp_kernel<256> : sssp_ilp_kernel<128>;
+    kern<<<grid, bf_threads, 0, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
                                                      w.state, w.stamp, w.queue, parent,
                                                      parent_slot_dev, slot_stride, dist, status,
                                                      skip_dev, roots_counter);

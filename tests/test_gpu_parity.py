@@ -288,3 +288,53 @@ def test_backward_matches_oracle(step):
     dd_g, dc_g = Q.qdta_backward(tape, T(dL, np.float64))
     np.testing.assert_allclose(dd_g.cpu().numpy(), dd_o, rtol=1e-9, atol=1e-12 * np.abs(dd_o).max())
     np.testing.assert_allclose(dc_g.cpu().numpy(), dc_o, rtol=1e-9, atol=1e-12 * max(np.abs(dc_o).max(), 1e-300))
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+def test_assign_batch_matches_oracle(schedule):
+    """Independent networks of different sizes solved in one call."""
+    cases = []
+    for n, z, trips, seed in [(12, 8, 2000, 1), (20, 16, 6000, 2), (110, 40, 20000, 3)]:
+        net = synth.grid_network(n, seed, freeways=n > 64)
+        zones = synth.pick_zones(net, z, seed)
+        dem = synth.demand_from_matrix(zones, synth.sample_trips(
+            synth.gravity_weights(net, zones, seed, 3000.0), trips, seed))
+        cases.append((net, dem))
+    params = ("sweep8", "rel_gap", 40, 1e-4)
+    items, graphs = [], []
+    for net, dem in cases:
+        g = Q.Graph(net)
+        graphs.append(g)
+        items.append((g, Q.DeviceOD.of(dem), 900.0, torch.empty(net.n_links, dtype=torch.float64, device=DEV)))
+    stats, rc = Q.qdta_assign_batch(items, Q.make_params(*params, schedule=schedule))
+    for (net, dem), it, st in zip(cases, items, stats):
+        og = oracle.OracleGraph(net)
+        f_o, st_o, _ = oracle.assign_interval(og, oracle.OracleOD.of(dem), 900.0,
+                                              oracle.make_params(Q.STEP[params[0]], Q.STOP[params[1]], params[2],
+                                                                 params[3]))
+        np.testing.assert_array_equal(it[3].cpu().numpy(), f_o)
+        assert st["iterations"] == st_o["iterations"] and st["ls_passes"] == st_o["ls_passes"]
+
+
+def test_autograd_function_matches_oracle_adjoint():
+    from paper_2104_12911_gb300 import autograd as AG
+    net = synth.grid_network(10, 6)
+    zones = synth.pick_zones(net, 8, 6)
+    dem = synth.demand_from_matrix(zones, synth.gravity_fixed_pairs(net, zones, 2000, 1200.0))
+    od = Q.DeviceOD.of(dem)
+    amounts = torch.tensor(dem.amount_fx / float(1 << 32), dtype=torch.float64, device=DEV, requires_grad=True)
+    cap = torch.tensor(net.capacity, dtype=torch.float64, device=DEV, requires_grad=True)
+    params = Q.make_params("exact", "none", 6)
+    f = AG.assign(net, od, amounts, cap, 600.0, params)
+    rng = np.random.default_rng(1)
+    w = torch.tensor(rng.standard_normal(net.n_links), dtype=torch.float64, device=DEV)
+    (f * w).sum().backward()
+    og = oracle.OracleGraph(net)
+    ood = oracle.OracleOD.of(dem)
+    f_o, _, _, tape_o = oracle.assign_interval(og, ood, 600.0, oracle.make_params(oracle.STEP_EXACT,
+                                                                                 oracle.STOP_NONE, 6), tape=True)
+    np.testing.assert_array_equal(f.detach().cpu().numpy(), f_o)
+    dd_o, dc_o, _ = oracle.backward(og, ood, 600.0, oracle.STEP_EXACT, tape_o, w.cpu().numpy())
+    np.testing.assert_allclose(amounts.grad.cpu().numpy(), dd_o, rtol=1e-9, atol=1e-12 * np.abs(dd_o).max())
+    np.testing.assert_allclose(cap.grad.cpu().numpy(), dc_o, rtol=1e-9, atol=1e-12 * max(np.abs(dc_o).max(), 1e-300))
