@@ -680,6 +680,7 @@ static int sssp_grid(const qdta_graph *g, int R) {
     if (env_bpsm > 0 && env_bpsm < bpsm) bpsm = env_bpsm;
   }
   long long cap = bpsm * g->d.num_sms;
+  if (g->sssp_kind == 2) R = (R + sssp_group_size() - 1) / sssp_group_size();  // CTAs, G roots each
   long long n = R < cap ? R : cap;
   return n < 1 ? 1 : (int)n;
 }
@@ -696,9 +697,10 @@ static int sssp_work(qdta_graph *g, int grid, SsspWork *w) {
     RC(ws_get(g, "sssp.stamp", (size_t)grid * g->cells.n_cells, &w->stamp));
     RC(ws_get(g, "sssp.queue", (size_t)grid * 3 * g->cells.n_cells, &w->queue));
   } else if (!g->sssp_smem) {
-    RC(ws_get(g, "sssp.state", (size_t)grid * V, &w->state));
-    RC(ws_get(g, "sssp.stamp", (size_t)grid * V, &w->stamp));
-    RC(ws_get(g, "sssp.queue", (size_t)grid * 2 * V, &w->queue));
+    const size_t G = (size_t)sssp_group_size();
+    RC(ws_get(g, "sssp.state", (size_t)grid * G * V, &w->state));
+    RC(ws_get(g, "sssp.stamp", (size_t)grid * G * V, &w->stamp));
+    RC(ws_get(g, "sssp.queue", (size_t)grid * 2 * G * V, &w->queue));
   } else {
     w->state = nullptr; w->stamp = nullptr; w->queue = nullptr;
   }

@@ -289,6 +289,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                  unsigned *status, cudaStream_t s, const int *skip_dev = nullptr,
                  unsigned long long *roots_counter = nullptr);
 int sssp_max_smem_nodes();
+int sssp_group_size();  // roots per CTA of the global-memory kernel
 long long launch_count();
 // which: 0 = fw_continue, 1 = need_sweep, 2 = res_continue
 void launch_set_cond(const Ctl *ctl, int which, unsigned long long cond, cudaStream_t s);

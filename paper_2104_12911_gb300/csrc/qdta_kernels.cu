@@ -592,6 +592,290 @@ void launch_sssp_cell(const GraphDev &g, const CellDev &c, int direction, const 
       parent_slot_dev, slot_stride, dist, status, skip_dev, roots_counter);
 }
 
+// Several roots per CTA in lockstep: the frontier holds (root slot, node)
+// entries of G roots, so each round's latency (a few dependent L2 trips and
+// one barrier) is paid once for G roots.  Per-root state, stamps and keys are
+// as in sssp_ilp_kernel; entries carry the slot in their top 4 bits.
+template <int THREADS, int G>
+__global__ void __launch_bounds__(THREADS)
+sssp_group_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__ adj,
+                  const int *__restrict__ roots, int R_host, const int *R_dev,
+                  unsigned long long *g_state, int *g_stamp, int *g_queue, int *parent,
+                  const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
+                  const int *skip_dev, unsigned long long *roots_counter) {
+  __shared__ int s_cnt[3];
+  if (skip_dev && *skip_dev) return;
+  const int R = R_dev ? *R_dev : R_host;
+  if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
+  const size_t b = blockIdx.x;
+  unsigned long long *state = g_state + b * (size_t)G * V;
+  int *stamp = g_stamp + b * (size_t)G * V;
+  int *qa = g_queue + b * 2 * (size_t)G * V;
+  int *qb = qa + (size_t)G * V;
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
+  const unsigned long long NOLINK = (1ull << LB) - 1ull;
+  const unsigned long long DMAX = (~0ull) >> LB;
+  constexpr int NQ = THREADS / 4;
+  const int quad = threadIdx.x >> 2, lane4 = threadIdx.x & 3;
+  for (size_t v = threadIdx.x; v < (size_t)G * V; v += blockDim.x) {
+    state[v] = ~0ull;
+    stamp[v] = -1;
+  }
+  int rid = 0;
+  __syncthreads();
+  for (int r0 = blockIdx.x * G; r0 < R; r0 += gridDim.x * G) {
+    const int ng = min(G, R - r0);
+    if (threadIdx.x < ng) {
+      const int z = roots[r0 + threadIdx.x];
+      state[(size_t)threadIdx.x * V + z] = NOLINK;
+      qa[threadIdx.x] = (threadIdx.x << 28) | z;
+    }
+    if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+    __syncthreads();
+    int ncur = ng, round = 0;
+    int *cur = qa, *nxt = qb;
+    unsigned long long my_relax = 0;
+    while (ncur > 0) {
+      const int c = round % 3;
+      if (threadIdx.x == 0) s_cnt[(round + 1) % 3] = 0;
+      const int my_rid = rid + round;
+      for (int base = 0; base < ncur; base += NQ * SSSP2_NPT) {
+        int w[SSSP2_NPT], kb[SSSP2_NPT], ke[SSSP2_NPT];
+        size_t sb[SSSP2_NPT];
+        unsigned long long dw[SSSP2_NPT];
+#pragma unroll
+        for (int j = 0; j < SSSP2_NPT; ++j) {
+          const int i = base + j * NQ + quad;
+          const int ent = i < ncur ? __ldcg(&cur[i]) : -1;
+          w[j] = ent < 0 ? -1 : (ent & 0x0FFFFFFF);
+          sb[j] = ent < 0 ? 0 : (size_t)(ent >> 28) * V;
+        }
+#pragma unroll
+        for (int j = 0; j < SSSP2_NPT; ++j) {
+          kb[j] = 0; ke[j] = 0; dw[j] = 0;
+          if (w[j] >= 0) {
+            kb[j] = __ldg(&off[w[j]]) + lane4;
+            ke[j] = __ldg(&off[w[j] + 1]);
+            dw[j] = __ldcg(&state[sb[j] + w[j]]) >> LB;
+          }
+        }
+        bool more = true;
+        while (more) {
+          int4 ent[SSSP2_NPT];
+          unsigned long long tk[SSSP2_NPT];
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j)
+            if (kb[j] < ke[j]) ent[j] = __ldg(&adj[kb[j]]);
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j)
+            if (kb[j] < ke[j]) tk[j] = __ldcg(&state[sb[j] + ent[j].y]);
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j) {
+            if (kb[j] < ke[j]) {
+              ++my_relax;
+              const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
+              if (cand >= DMAX) {
+                atomicOr(status, ST_OVERFLOW);
+              } else {
+                const unsigned long long key = (cand << LB) | (unsigned long long)(unsigned)ent[j].x;
+                if (key < tk[j]) {
+                  const unsigned long long old = atomicMin(&state[sb[j] + ent[j].y], key);
+                  if ((old >> LB) > cand && atomicExch(&stamp[sb[j] + ent[j].y], my_rid) != my_rid) {
+                    const int pos = atomicAdd(&s_cnt[c], 1);
+                    nxt[pos] = (int)((sb[j] / V) << 28) | ent[j].y;
+                  }
+                }
+              }
+            }
+          }
+          more = false;
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j) {
+            kb[j] += 4;
+            more |= kb[j] < ke[j];
+          }
+        }
+      }
+      __syncthreads();
+      ncur = s_cnt[c];
+      int *t = cur; cur = nxt; nxt = t;
+      ++round;
+      if (round > V + 1) {
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        break;
+      }
+    }
+    rid += round + 1;
+    if (roots_counter) {
+      if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round * ng);
+      atomicAdd(roots_counter + 2, my_relax);
+    }
+    __syncthreads();
+    for (int gi = 0; gi < ng; ++gi) {
+      int *prow = parent + (long long)(r0 + gi) * V;
+      long long *drow = dist ? dist + (long long)(r0 + gi) * V : nullptr;
+      unsigned long long *st = state + (size_t)gi * V;
+      for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        const unsigned long long key = __ldcg(&st[v]);
+        const unsigned long long lk = key & NOLINK;
+        prow[v] = lk == NOLINK ? -1 : (int)lk;
+        if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
+        st[v] = ~0ull;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int sssp_group_size() {
+  static int gsz = [] {
+    const char *e = getenv("QDTA_BF_GROUP");
+    int g = e ? atoi(e) : 1;
+    return (g == 2 || g == 4 || g == 8) ? g : 1;
+  }();
+  return gsz;
+}
+
+// Global-memory keys with the round bookkeeping in shared memory: the
+// frontier queues (with a global overflow) and the "already queued" marks,
+// kept as two bitmaps of V bits that alternate with the round parity (the
+// bits of the queue being read are cleared as it is read, so the bitmap is
+// clean again two rounds later).  This takes the frontier read and the
+// dedupe atomic off the chain of dependent L2 trips of every relaxation.
+constexpr int SMQ_CAP = 3072;  // queue entries per buffer in shared memory
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__ adj,
+                const int *__restrict__ roots, int R_host, const int *R_dev,
+                unsigned long long *g_state, int *g_queue, int *parent,
+                const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
+                const int *skip_dev, unsigned long long *roots_counter) {
+  extern __shared__ __align__(16) unsigned smq_smem[];
+  __shared__ int s_cnt[3];
+  if (skip_dev && *skip_dev) return;
+  const int R = R_dev ? *R_dev : R_host;
+  if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
+  const int W = (V + 31) >> 5;
+  unsigned *bm0 = smq_smem, *bm1 = smq_smem + W;
+  int *sq0 = reinterpret_cast<int *>(smq_smem + 2 * W), *sq1 = sq0 + SMQ_CAP;
+  const size_t b = blockIdx.x;
+  unsigned long long *state = g_state + b * (size_t)V;
+  int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;  // overflow beyond SMQ_CAP
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
+  const unsigned long long NOLINK = (1ull << LB) - 1ull;
+  const unsigned long long DMAX = (~0ull) >> LB;
+  constexpr int NQ = THREADS / 4;
+  const int quad = threadIdx.x >> 2, lane4 = threadIdx.x & 3;
+  for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = ~0ull;
+  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) smq_smem[i] = 0u;
+  __syncthreads();
+  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    const int z = roots[r];
+    if (threadIdx.x == 0) {
+      state[z] = NOLINK;
+      sq0[0] = z;
+      s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+    }
+    __syncthreads();
+    int ncur = 1, round = 0;
+    int *scur = sq0, *snxt = sq1, *gcur = gq0, *gnxt = gq1;
+    unsigned *bcur = bm1, *bnxt = bm0;  // the root's queue entry has no mark
+    unsigned long long my_relax = 0;
+    while (ncur > 0) {
+      const int c = round % 3;
+      if (threadIdx.x == 0) s_cnt[(round + 1) % 3] = 0;
+      for (int base = 0; base < ncur; base += NQ * SSSP2_NPT) {
+        int w[SSSP2_NPT], kb[SSSP2_NPT], ke[SSSP2_NPT];
+        unsigned long long dw[SSSP2_NPT];
+#pragma unroll
+        for (int j = 0; j < SSSP2_NPT; ++j) {
+          const int i = base + j * NQ + quad;
+          w[j] = i < ncur ? (i < SMQ_CAP ? scur[i] : __ldcg(&gcur[i - SMQ_CAP])) : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < SSSP2_NPT; ++j) {
+          kb[j] = 0; ke[j] = 0; dw[j] = 0;
+          if (w[j] >= 0) {
+            if (lane4 == 0) atomicAnd(&bcur[w[j] >> 5], ~(1u << (w[j] & 31)));
+            kb[j] = __ldg(&off[w[j]]) + lane4;
+            ke[j] = __ldg(&off[w[j] + 1]);
+            dw[j] = __ldcg(&state[w[j]]) >> LB;
+          }
+        }
+        bool more = true;
+        while (more) {
+          int4 ent[SSSP2_NPT];
+          unsigned long long tk[SSSP2_NPT];
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j)
+            if (kb[j] < ke[j]) ent[j] = __ldg(&adj[kb[j]]);
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j)
+            if (kb[j] < ke[j]) tk[j] = __ldcg(&state[ent[j].y]);
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j) {
+            if (kb[j] < ke[j]) {
+              ++my_relax;
+              const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
+              if (cand >= DMAX) {
+                atomicOr(status, ST_OVERFLOW);
+              } else {
+                const unsigned long long key = (cand << LB) | (unsigned long long)(unsigned)ent[j].x;
+                if (key < tk[j]) {
+                  const unsigned long long old = atomicMin(&state[ent[j].y], key);
+                  const int y = ent[j].y;
+                  if ((old >> LB) > cand && !((atomicOr(&bnxt[y >> 5], 1u << (y & 31)) >> (y & 31)) & 1u)) {
+                    const int pos = atomicAdd(&s_cnt[c], 1);
+                    if (pos < SMQ_CAP) snxt[pos] = y;
+                    else gnxt[pos - SMQ_CAP] = y;
+                  }
+                }
+              }
+            }
+          }
+          more = false;
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j) {
+            kb[j] += 4;
+            more |= kb[j] < ke[j];
+          }
+        }
+      }
+      __syncthreads();
+      ncur = s_cnt[c];
+      int *t = scur; scur = snxt; snxt = t;
+      t = gcur; gcur = gnxt; gnxt = t;
+      unsigned *tb = bcur; bcur = bnxt; bnxt = tb;
+      ++round;
+      if (round > V + 1) {
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        break;
+      }
+    }
+    if (roots_counter) {
+      if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
+      atomicAdd(roots_counter + 2, my_relax);
+    }
+    __syncthreads();
+    // an early exit (timeout) can leave marks behind: clear both bitmaps
+    if (round > V + 1)
+      for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) smq_smem[i] = 0u;
+    int *prow = parent + (long long)r * V;
+    long long *drow = dist ? dist + (long long)r * V : nullptr;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+      const unsigned long long key = __ldcg(&state[v]);
+      const unsigned long long lk = key & NOLINK;
+      prow[v] = lk == NOLINK ? -1 : (int)lk;
+      if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
+      state[v] = ~0ull;
+    }
+    __syncthreads();
+  }
+}
+
+size_t sssp_smq_smem_bytes(int V) { return (size_t)2 * ((V + 31) / 32) * 4 + (size_t)2 * SMQ_CAP * 4; }
+
 int sssp_max_smem_nodes() { return (200 * 1024) / 20; }
 
 static size_t sssp_smem_bytes(int V) { return (size_t)V * 20; }
@@ -634,6 +918,19 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
     }();
     auto kern = bf_threads == 1024 ? sssp_ilp_kernel<1024> : bf_threads == 512 ? sssp_ilp_kernel<512>
               : bf_threads == 256 ? sssp_ilp_kernel<256> : sssp_ilp_kernel<128>;
+    const int G = sssp_group_size();
+    const size_t smq = sssp_smq_smem_bytes(g.V);
+    if (G == 1 && smq <= 96 * 1024 && !getenv("QDTA_BF_NOSMQ")) {
+      cudaFuncSetAttribute(sssp_smq_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+      sssp_smq_kernel<512><<<grid, 512, smq, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev, w.state, w.queue,
+                                                   parent, parent_slot_dev, slot_stride, dist, status, skip_dev,
+                                                   roots_counter);
+      return;
+    }
+    if (G == 2) kern = sssp_group_kernel<512, 2>;
+    else if (G == 4) kern = sssp_group_kernel<512, 4>;
+    else if (G == 8) kern = sssp_group_kernel<512, 8>;
+    if (G > 1) bf_threads = 512;
     kern<<<grid, bf_threads, 0, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
                                                      w.state, w.stamp, w.queue, parent,
                                                      parent_slot_dev, slot_stride, dist, status,
