@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="day_metro", choices=["day_metro", "day_small", "sssp_metro"])
     ap.add_argument("--roots", type=int, default=2000, help="sssp_metro: destination roots per batch")
+    ap.add_argument("--intervals", default=None,
+                    help="a:b -- run only intervals a..b-1 of the day (profiling captures; not a bench line)")
     ap.add_argument("--max-iter", type=int, default=200)
     ap.add_argument("--stop", default="paper_obj", choices=["paper_obj", "rel_gap"])
     ap.add_argument("--no-plain", action="store_true")
@@ -264,6 +266,11 @@ def main():
     dev = torch.device("cuda", local)
     t_gen = time.perf_counter()
     inst, cfg = make_workload(args.workload)
+    if args.intervals:
+        a, b = (int(x) for x in args.intervals.split(":"))
+        inst.demand = inst.demand[a:b]
+        cfg["workload"] += f" -- intervals {a}..{b - 1} only (profiling slice)"
+        cfg["intervals"] = b - a
     t_gen = time.perf_counter() - t_gen
     cfg["parallelism"] = f"replicas x{world} (one independent day per GPU)"
     g = Q.Graph(inst.net, local)

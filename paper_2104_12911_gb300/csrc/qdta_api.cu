@@ -610,6 +610,34 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
     }
     g->has_cells = true;
     g->cell_bpsm = sssp_cell_blocks_per_sm();
+    // locality order for the global-memory kernel: cell-major internal ids
+    // (QDTA_NO_REORDER keeps the external order)
+    if (!getenv("QDTA_NO_REORDER")) {
+      std::vector<int> node_ext(V);
+      for (int v = 0; v < V; ++v) node_ext[H.node_int[v]] = v;
+      for (int dir = 0; dir < 2; ++dir) {
+        const int *ooff = dir == 0 ? in_off.data() : out_off.data();
+        const int *olnk = dir == 0 ? in_link.data() : out_link.data();
+        const int *nbof = dir == 0 ? d->tail : d->head;
+        std::vector<int> po(V + 1, 0), pl(L), pn(L);
+        for (int u = 0; u < V; ++u) {
+          const int v = node_ext[u];
+          po[u + 1] = po[u] + (ooff[v + 1] - ooff[v]);
+          for (int k = ooff[v], t = po[u]; k < ooff[v + 1]; ++k, ++t) {
+            pl[t] = olnk[k];
+            pn[t] = H.node_int[nbof[olnk[k]]];
+          }
+        }
+        int *q1, *q2, *q3;
+        if ((rc = upload(g, po.data(), po.size(), &q1)) || (rc = upload(g, pl.data(), pl.size(), &q2)) ||
+            (rc = upload(g, pn.data(), pn.size(), &q3))) {
+          qdta_graph_destroy(g);
+          return rc;
+        }
+        gd.perm_off[dir] = q1; gd.perm_link[dir] = q2; gd.perm_nb[dir] = q3;
+      }
+      gd.node_int = C.node_int;
+    }
     double mean_q = 0.0;
     for (int e = 0; e < L; ++e) mean_q += d->fftime_q[e];
     mean_q = L ? mean_q / L : 1.0;
@@ -724,7 +752,8 @@ static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots
                      parent, slot_dev, stride, dist, g->status, s, skip_dev,
                      g->prof_on ? g->prof_roots : nullptr);
   } else {
-    launch_pack_adj(g->d, direction, q, w.adj, s, skip_dev);
+    if (g->sssp_kind == 2 && sssp_uses_perm(g->d)) launch_pack_perm_adj(g->d, direction, q, w.adj, s, skip_dev);
+    else launch_pack_adj(g->d, direction, q, w.adj, s, skip_dev);
     prof_begin(g, s, &pe, 0, R_host);
     launch_sssp(g->d, direction, w.adj, roots, R_host, R_dev, grid, g->sssp_smem, w, parent, slot_dev,
                 stride, dist, g->status, s, skip_dev, g->prof_on ? g->prof_roots : nullptr);

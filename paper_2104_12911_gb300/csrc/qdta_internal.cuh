@@ -222,6 +222,13 @@ struct GraphDev {
   const int *out_off, *in_off;    // [V+1]
   const int *out_link, *in_link;  // [L] link ids grouped by tail / head, ascending
   int num_sms;
+  // locality order for the global-memory SSSP (nullable): internal node ids
+  // in cell order; per direction the adjacency of each internal node as link
+  // ids and neighbours' internal ids
+  const int *node_int;             // [V] external -> internal
+  const int *perm_off[2];          // [V + 1]
+  const int *perm_link[2];         // [L]
+  const int *perm_nb[2];           // [L]
 };
 
 // Cell partition for the shared-memory cell SSSP (graphs above the
@@ -272,6 +279,8 @@ struct SsspWork {
 // skip_dev (nullable): when *skip_dev != 0 the launch does nothing
 void launch_pack_adj(const GraphDev &g, int direction, const int *q, int4 *adj, cudaStream_t s,
                      const int *skip_dev = nullptr);
+void launch_pack_perm_adj(const GraphDev &g, int direction, const int *q, int4 *adj, cudaStream_t s,
+                          const int *skip_dev = nullptr);
 void launch_pack_cell_adj(const GraphDev &g, const CellDev &c, int direction, const int *q, int4 *adj,
                           uint2 *lrev_adj, long long n_lrev, int4 *xrev_adj, long long n_xrev, cudaStream_t s,
                           const int *skip_dev = nullptr);
@@ -290,6 +299,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                  unsigned long long *roots_counter = nullptr);
 int sssp_max_smem_nodes();
 int sssp_group_size();  // roots per CTA of the global-memory kernel
+bool sssp_uses_perm(const GraphDev &g);  // global-memory launch reads the locality-ordered adjacency
 long long launch_count();
 // which: 0 = fw_continue, 1 = need_sweep, 2 = res_continue
 void launch_set_cond(const Ctl *ctl, int which, unsigned long long cond, cudaStream_t s);

@@ -45,6 +45,23 @@ __global__ void pack_adj_kernel(int L, const int *__restrict__ link_list,
   }
 }
 
+__global__ void pack_perm_adj_kernel(int L, const int *__restrict__ perm_link, const int *__restrict__ perm_nb,
+                                     const int *__restrict__ q, int4 *__restrict__ adj, const int *skip_dev) {
+  if (skip_dev && *skip_dev) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gridDim.x * blockDim.x) {
+    const int e = perm_link[k];
+    adj[k] = make_int4(e, perm_nb[k], q[e], 0);
+  }
+}
+
+void launch_pack_perm_adj(const GraphDev &g, int direction, const int *q, int4 *adj, cudaStream_t s,
+                          const int *skip_dev) {
+  if (g.L == 0) return;
+  COUNT_LAUNCH();
+  pack_perm_adj_kernel<<<cdiv(g.L, 256), 256, 0, s>>>(g.L, g.perm_link[direction], g.perm_nb[direction], q, adj,
+                                                      skip_dev);
+}
+
 void launch_pack_adj(const GraphDev &g, int direction, const int *q, int4 *adj, cudaStream_t s,
                      const int *skip_dev) {
   if (g.L == 0) return;
@@ -587,6 +604,8 @@ void launch_sssp_cell(const GraphDev &g, const CellDev &c, int direction, const 
   if (grid <= 0) return;
   COUNT_LAUNCH();
   cudaFuncSetAttribute(sssp_cell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem_bytes());
+  cudaFuncSetAttribute(sssp_cell_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
   sssp_cell_kernel<<<grid, CELL_WARPS * 32, cell_smem_bytes(), s>>>(
       g.V, g.LB, c, direction, adj, lrev_adj, xrev_adj, delta, roots, R_host, R_dev, state, flag, queue, prio, parent,
       parent_slot_dev, slot_stride, dist, status, skip_dev, roots_counter);
@@ -750,7 +769,7 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
                 const int *__restrict__ roots, int R_host, const int *R_dev,
                 unsigned long long *g_state, int *g_queue, int *parent,
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
-                const int *skip_dev, unsigned long long *roots_counter) {
+                const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
   if (skip_dev && *skip_dev) return;
@@ -771,7 +790,7 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
   for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) smq_smem[i] = 0u;
   __syncthreads();
   for (int r = blockIdx.x; r < R; r += gridDim.x) {
-    const int z = roots[r];
+    const int z = node_int ? node_int[roots[r]] : roots[r];
     if (threadIdx.x == 0) {
       state[z] = NOLINK;
       sq0[0] = z;
@@ -864,17 +883,25 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
     int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
     for (int v = threadIdx.x; v < V; v += blockDim.x) {
-      const unsigned long long key = __ldcg(&state[v]);
+      const unsigned long long key = __ldcg(&state[node_int ? node_int[v] : v]);
       const unsigned long long lk = key & NOLINK;
       prow[v] = lk == NOLINK ? -1 : (int)lk;
       if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
-      state[v] = ~0ull;
     }
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = ~0ull;
     __syncthreads();
   }
 }
 
 size_t sssp_smq_smem_bytes(int V) { return (size_t)2 * ((V + 31) / 32) * 4 + (size_t)2 * SMQ_CAP * 4; }
+
+// the global-memory launch runs the shared-memory-queue kernel (which reads
+// the locality-ordered adjacency when the graph has one)
+bool sssp_uses_smq(const GraphDev &g) {
+  return sssp_group_size() == 1 && sssp_smq_smem_bytes(g.V) <= 96 * 1024 && !getenv("QDTA_BF_NOSMQ");
+}
+bool sssp_uses_perm(const GraphDev &g) { return g.node_int != nullptr && sssp_uses_smq(g); }
 
 int sssp_max_smem_nodes() { return (200 * 1024) / 20; }
 
@@ -903,6 +930,8 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
   if (use_smem) {
     size_t sm = sssp_smem_bytes(g.V);
     cudaFuncSetAttribute(sssp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(sssp_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
     COUNT_LAUNCH();
     sssp_kernel<true><<<grid, SSSP_THREADS, sm, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
                                                      nullptr, nullptr, nullptr, parent,
@@ -920,11 +949,21 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
               : bf_threads == 256 ? sssp_ilp_kernel<256> : sssp_ilp_kernel<128>;
     const int G = sssp_group_size();
     const size_t smq = sssp_smq_smem_bytes(g.V);
-    if (G == 1 && smq <= 96 * 1024 && !getenv("QDTA_BF_NOSMQ")) {
+    if (sssp_uses_smq(g)) {
+      // Two 86.5 KB CTAs per SM need a ~196 KB shared-memory carveout; the
+      // rest of the unified 256 KB stays L1 (the adjacency gathers want it:
+      // 55 ms per batch at 196 KB vs 84 ms at the 228 KB maximum).  Pinning
+      // the preference gives stream launches and graph kernel nodes the
+      // same configuration.  The percentage is rounded up to a supported
+      // size: 85 % of 228 KB asks for 194 KB and gets the 196 KB step (86 %
+      // would round up to 228 KB).  QDTA_SMQ_CARVEOUT overrides, in percent.
       cudaFuncSetAttribute(sssp_smq_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
-      sssp_smq_kernel<512><<<grid, 512, smq, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev, w.state, w.queue,
-                                                   parent, parent_slot_dev, slot_stride, dist, status, skip_dev,
-                                                   roots_counter);
+      static int carve = [] { const char *e = getenv("QDTA_SMQ_CARVEOUT"); return e ? atoi(e) : 85; }();
+      cudaFuncSetAttribute(sssp_smq_kernel<512>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+      const bool perm = g.node_int != nullptr;
+      sssp_smq_kernel<512><<<grid, 512, smq, s>>>(g.V, g.LB, perm ? g.perm_off[direction] : off, adj, roots, R_host,
+                                                   R_dev, w.state, w.queue, parent, parent_slot_dev, slot_stride,
+                                                   dist, status, skip_dev, roots_counter, perm ? g.node_int : nullptr);
       return;
     }
     if (G == 2) kern = sssp_group_kernel<512, 2>;

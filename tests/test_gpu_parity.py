@@ -105,13 +105,22 @@ def test_sssp_unreachable_nodes():
     np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-def test_sssp_global_memory_variant(mid):
-    net, dem, g, og = mid
+@pytest.mark.parametrize("variant", ["default", "no_reorder", "global_queues", "cell"])
+@pytest.mark.parametrize("direction", [Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT])
+def test_sssp_large_graph_variants(mid, variant, direction, monkeypatch):
+    """Graphs above the shared-memory limit: every kernel variant, both
+    directions, bit-exact against Dijkstra."""
+    net, dem, _, og = mid
+    env = {"default": {}, "no_reorder": {"QDTA_NO_REORDER": "1"},
+           "global_queues": {"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "cell": {"QDTA_SSSP": "cell"}}[variant]
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    g = Q.Graph(net)
     rng = np.random.default_rng(2)
     q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
     roots = rng.choice(net.n_nodes, 40, replace=False).astype(np.int32)
-    p_o, d_o = oracle.sssp(og, q, roots)
-    p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, True)
+    p_o, d_o = oracle.sssp(og, q, roots, direction)
+    p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
     np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
     np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
