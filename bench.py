@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="day_metro", choices=["day_metro", "day_small", "sssp_metro"])
+    ap.add_argument("--workload", default="day_metro",
+                    choices=["day_metro", "day_small", "sssp_metro", "batch32"])
     ap.add_argument("--roots", type=int, default=2000, help="sssp_metro: destination roots per batch")
     ap.add_argument("--intervals", default=None,
                     help="a:b -- run only intervals a..b-1 of the day (profiling captures; not a bench line)")
@@ -240,10 +241,56 @@ def sssp_only(args):
           flush=True)
 
 
+def batch32(args):
+    """Many independent networks, one interval each: 32 grids with n spaced
+    geometrically from 64 to 700, zones 100 -> 3,000 and trips 10k -> 400k,
+    solved as parallel branches of one CUDA graph launch vs one network at a
+    time (plain launches)."""
+    import torch
+    from paper_2104_12911_gb300 import qdta as Q, synth
+    k = np.arange(32)
+    ns = np.rint(64 * (700 / 64) ** (k / 31)).astype(int)
+    zs = np.rint(100 * (3000 / 100) ** (k / 31)).astype(int)
+    ts = np.rint(10_000 * (400_000 / 10_000) ** (k / 31)).astype(int)
+    items, links = [], 0
+    for i in range(32):
+        net = synth.grid_network(int(ns[i]), 100 + i, freeways=True)
+        zones = synth.pick_zones(net, int(zs[i]), 100 + i)
+        dem = synth.demand_from_matrix(zones, synth.sample_trips(
+            synth.gravity_weights(net, zones, 100 + i, 10000.0), int(ts[i]), 200 + i))
+        g = Q.Graph(net)
+        items.append((g, Q.DeviceOD.of(dem), 900.0, torch.empty(net.n_links, dtype=torch.float64, device="cuda")))
+        links += net.n_links
+    res = {}
+    for sched in ("graph", "plain"):
+        p = Q.make_params("sweep8", args.stop, args.max_iter, 1e-4, schedule=sched)
+        for _ in range(args.warmup):
+            Q.qdta_assign_batch(items, p)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            stats, rc = Q.qdta_assign_batch(items, p)
+        e1.record()
+        torch.cuda.synchronize()
+        res[sched] = (e0.elapsed_time(e1) / args.steps, stats)
+    st = res["graph"][1]
+    print(json.dumps({"metric": "32 independent networks, one interval each, seconds", "workload": "batch32",
+                      "links_total": links, "one_graph_launch_s": res["graph"][0] / 1e3,
+                      "one_at_a_time_s": res["plain"][0] / 1e3,
+                      "speedup": res["plain"][0] / res["graph"][0],
+                      "fw_iterations": [s["iterations"] for s in st],
+                      "converged": int(sum(s["converged"] for s in st)),
+                      "stop": args.stop, "max_iter": args.max_iter}), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "sssp_metro":
         sssp_only(args)
+        return
+    if args.workload == "batch32":
+        batch32(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

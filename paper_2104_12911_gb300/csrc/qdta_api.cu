@@ -109,12 +109,26 @@ struct DevGuard {
   }
 };
 
+// Host-side fault injection for tests: QDTA_FAULT=alloc:<n> makes the n-th
+// workspace allocation of the process (counting from 1) fail as if the device
+// were out of memory.  Nothing is injected on the device.
+static bool inject_alloc_fault() {
+  static long long target = [] {
+    const char *e = getenv("QDTA_FAULT");
+    return (e && strncmp(e, "alloc:", 6) == 0) ? atoll(e + 6) : 0ll;
+  }();
+  static long long seen = 0;
+  return target > 0 && ++seen == target;
+}
+
 template <class T>
 static int ws_get(qdta_graph *g, const std::string &name, size_t count, T **out) {
   size_t bytes = count * sizeof(T);
   if (bytes == 0) bytes = 16;
   Buf &b = g->ws[name];
   if (b.bytes < bytes) {
+    if (inject_alloc_fault())
+      return fail(QDTA_ENOMEM, "device allocation of %zu bytes for '%s' failed (injected)", bytes, name.c_str());
     if (b.p) {
       cudaDeviceSynchronize();
       cudaFree(b.p);
@@ -1478,9 +1492,15 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   S.n_host = 0; S.n_dev = D.n_items_dev;
   S.root_idx = D.it_root; S.src = D.it_src; S.amount = D.it_amt;
   RC(ws_get(g, "day.f", L, &S.f));
-  // parent ring: keep every tree of an interval when memory allows
+  // parent ring: keep every tree of an interval when memory allows.  The
+  // ring this handle already holds counts as available (a later day must
+  // not shrink the ring because the previous day's ring is still allocated).
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
+  {
+    auto it = g->ws.find("day.parent");
+    if (it != g->ws.end()) free_b += it->second.bytes;
+  }
   const double per_slot = (double)Z * V * 4.0;
   long long ring = p->max_iter + 1;
   long long afford = (long long)((double)free_b * 0.8 / per_slot);

@@ -19,6 +19,14 @@
 
 namespace qdta {
 
+// Round limit of the Bellman-Ford loops (a watchdog: link times >= 1 bound
+// the rounds by V + 1, so hitting it means an error).  QDTA_MAX_ROUNDS lowers
+// it so that tests can exercise the timeout path without faulting anything.
+static int round_limit(int V) {
+  static long long env = [] { const char *e = getenv("QDTA_MAX_ROUNDS"); return e ? atoll(e) : 0ll; }();
+  return (env > 0 && env < (long long)V + 1) ? (int)env : V + 1;
+}
+
 // kernels launched (or captured) by the launchers below, host-side count
 static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
@@ -84,7 +92,7 @@ sssp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__
             const int *__restrict__ roots, int R_host, const int *R_dev,
             unsigned long long *g_state, int *g_stamp, int *g_queue, int *parent,
             const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
-            const int *skip_dev, unsigned long long *roots_counter) {
+            const int *skip_dev, unsigned long long *roots_counter, int max_rounds) {
   extern __shared__ unsigned long long smem_u64[];
   __shared__ int s_cnt[3];
   if (skip_dev && *skip_dev) return;
@@ -154,7 +162,7 @@ sssp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__
       ncur = s_cnt[c];
       int *t = cur; cur = nxt; nxt = t;
       ++round;
-      if (round > V + 1) {  // cannot happen with link times >= 1; bounded anyway
+      if (round > max_rounds) {  // cannot happen with link times >= 1 unless lowered
         if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
         break;
       }
@@ -192,7 +200,7 @@ sssp_ilp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
                 const int *__restrict__ roots, int R_host, const int *R_dev,
                 unsigned long long *g_state, int *g_stamp, int *g_queue, int *parent,
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
-                const int *skip_dev, unsigned long long *roots_counter) {
+                const int *skip_dev, unsigned long long *roots_counter, int max_rounds) {
   __shared__ int s_cnt[3];
   if (skip_dev && *skip_dev) return;
   const int R = R_dev ? *R_dev : R_host;
@@ -286,7 +294,7 @@ sssp_ilp_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
       ncur = s_cnt[c];
       int *t = cur; cur = nxt; nxt = t;
       ++round;
-      if (round > V + 1) {
+      if (round > max_rounds) {
         if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
         break;
       }
@@ -621,7 +629,7 @@ sssp_group_kernel(int V, int LB, const int *__restrict__ off, const int4 *__rest
                   const int *__restrict__ roots, int R_host, const int *R_dev,
                   unsigned long long *g_state, int *g_stamp, int *g_queue, int *parent,
                   const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
-                  const int *skip_dev, unsigned long long *roots_counter) {
+                  const int *skip_dev, unsigned long long *roots_counter, int max_rounds) {
   __shared__ int s_cnt[3];
   if (skip_dev && *skip_dev) return;
   const int R = R_dev ? *R_dev : R_host;
@@ -719,7 +727,7 @@ sssp_group_kernel(int V, int LB, const int *__restrict__ off, const int4 *__rest
       ncur = s_cnt[c];
       int *t = cur; cur = nxt; nxt = t;
       ++round;
-      if (round > V + 1) {
+      if (round > max_rounds) {
         if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
         break;
       }
@@ -769,7 +777,8 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
                 const int *__restrict__ roots, int R_host, const int *R_dev,
                 unsigned long long *g_state, int *g_queue, int *parent,
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
-                const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int) {
+                const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
+                int max_rounds) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
   if (skip_dev && *skip_dev) return;
@@ -867,7 +876,7 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
       t = gcur; gcur = gnxt; gnxt = t;
       unsigned *tb = bcur; bcur = bnxt; bnxt = tb;
       ++round;
-      if (round > V + 1) {
+      if (round > max_rounds) {
         if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
         break;
       }
@@ -878,7 +887,7 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
     }
     __syncthreads();
     // an early exit (timeout) can leave marks behind: clear both bitmaps
-    if (round > V + 1)
+    if (round > max_rounds)
       for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) smq_smem[i] = 0u;
     int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
@@ -936,7 +945,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
     sssp_kernel<true><<<grid, SSSP_THREADS, sm, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
                                                      nullptr, nullptr, nullptr, parent,
                                                      parent_slot_dev, slot_stride, dist, status, skip_dev,
-                                                     roots_counter);
+                                                     roots_counter, round_limit(g.V));
   } else {
     COUNT_LAUNCH();
     // block size of the global-memory variant (QDTA_BF_THREADS: 128, 256, 512 or 1024)
@@ -963,7 +972,8 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       const bool perm = g.node_int != nullptr;
       sssp_smq_kernel<512><<<grid, 512, smq, s>>>(g.V, g.LB, perm ? g.perm_off[direction] : off, adj, roots, R_host,
                                                    R_dev, w.state, w.queue, parent, parent_slot_dev, slot_stride,
-                                                   dist, status, skip_dev, roots_counter, perm ? g.node_int : nullptr);
+                                                   dist, status, skip_dev, roots_counter, perm ? g.node_int : nullptr,
+                                                   round_limit(g.V));
       return;
     }
     if (G == 2) kern = sssp_group_kernel<512, 2>;
@@ -973,7 +983,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
     kern<<<grid, bf_threads, 0, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
                                                      w.state, w.stamp, w.queue, parent,
                                                      parent_slot_dev, slot_stride, dist, status,
-                                                     skip_dev, roots_counter);
+                                                     skip_dev, roots_counter, round_limit(g.V));
   }
 }
 
