@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="day_metro",
-                    choices=["day_metro", "day_small", "sssp_metro", "batch32"])
+                    choices=["day_metro", "day_small", "sssp_metro", "batch32", "adjoint_metro"])
     ap.add_argument("--roots", type=int, default=2000, help="sssp_metro: destination roots per batch")
     ap.add_argument("--intervals", default=None,
                     help="a:b -- run only intervals a..b-1 of the day (profiling captures; not a bench line)")
@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--stop", default="paper_obj", choices=["paper_obj", "rel_gap"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default SSSP launch shape")
     return ap.parse_args()
 
 
@@ -123,6 +124,74 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(values, world, device):
+    """Element-wise maximum over all ranks (the slowest replica defines the
+    job's time); identity for a single process."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_seconds_per_day(ms_max, world):
+    """Whole-job seconds per simulated day: `world` replicas each simulate one
+    day per step in ms_max milliseconds (the slowest rank)."""
+    return ms_max / 1e3 / world
+
+
+# ---------------------------------------------------------------------------
+# root-parallel CPU oracle: the unmodified oracle, one destination root per
+# task, in a process pool started with "spawn" (safe after CUDA is live)
+_POOL_OG, _POOL_Q = None, None
+
+
+def _pool_init(net, q):
+    global _POOL_OG, _POOL_Q
+    import oracle
+    _POOL_OG, _POOL_Q = oracle.OracleGraph(net), q
+
+
+def _pool_root(task):
+    import oracle
+    root, src, amt, dt_q = task
+    od = oracle.OracleOD(np.array([root], np.int32), np.zeros(len(src), np.int32), src, amt)
+    par, _ = oracle.sssp(_POOL_OG, _POOL_Q, od.roots, want_dist=False)
+    oracle.load(_POOL_OG, _POOL_Q, par, od, dt_q)
+    return 1
+
+
+class OraclePool:
+    """Times Dijkstra + loading per destination root on every host core."""
+
+    def __init__(self, net, q):
+        import multiprocessing as mp
+        self.n = max(1, os.cpu_count() or 1)
+        self.pool = mp.get_context("spawn").Pool(self.n, initializer=_pool_init, initargs=(net, q))
+        self.pool.map(_pool_root, [], chunksize=1)
+
+    @staticmethod
+    def tasks(dem, roots):
+        out = []
+        for r in roots:
+            sel = dem.root_idx == r
+            out.append((int(dem.roots[r]), dem.src[sel].copy(), dem.amount_fx[sel].copy(), 90000))
+        return out
+
+    def seconds_per_root(self, tasks):
+        """Wall seconds per root when `tasks` run on all cores (after one warm task per worker)."""
+        self.pool.map(_pool_root, tasks[:self.n], chunksize=1)
+        t0 = time.perf_counter()
+        self.pool.map(_pool_root, tasks, chunksize=1)
+        return (time.perf_counter() - t0) / max(len(tasks), 1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def cpu_baseline(inst, day_stats, budget_s=20.0):
     """Time the CPU oracle on a bounded sample of the same day and scale it
     to the day's work: per-root Dijkstra + walks and per-sweep costs,
@@ -153,42 +222,49 @@ def cpu_baseline(inst, day_stats, budget_s=20.0):
                                       oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_NONE, 20))
     t_pass = (time.perf_counter() - t1) / max(passes, 1)
     n_roots = [len(np.unique(d.root_idx)) for d in inst.demand]
-    est = 0.0
-    for i, st in enumerate(day_stats):
-        aons = st["aon_calls"] + (st["iterations"] + 1 if st["aon_calls"] else 0)  # FW + residual trees
-        est += aons * n_roots[i] * t_root + st["ls_passes"] * t_pass
-    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+
+    def day_seconds(t_r):
+        est = 0.0
+        for i, st in enumerate(day_stats):
+            aons = st["aon_calls"] + (st["iterations"] + 1 if st["aon_calls"] else 0)  # FW + residual trees
+            est += aons * n_roots[i] * t_r + st["ls_passes"] * t_pass
+        return est
+    spent = time.perf_counter() - t0
+    # the same roots again on every host core (the sweeps stay single-core)
+    par = None
+    try:
+        pool = OraclePool(inst.net, q)
+        n_par = min(len(active), max(pool.n * 4, roots_done))
+        t_root_par = pool.seconds_per_root(OraclePool.tasks(dem, active[:n_par]))
+        pool.close()
+        par = {"value": day_seconds(t_root_par), "unit": "s", "cores": pool.n, "sec_per_root": t_root_par,
+               "sample": f"{n_par} destination roots of the peak interval, one process per core"}
+    except Exception as exc:  # no process pool on this host: report the single-core figure only
+        par = {"unavailable": f"{type(exc).__name__}: {exc}"}
+    return {"value": day_seconds(t_root), "unit": "s", "cores": 1, "kind": "oracle",
             "sample": (f"{roots_done} destination roots (Dijkstra + loading) of the peak interval and one "
-                       f"8-point sweep over {L} links, {time.perf_counter() - t0:.1f} s of CPU; scaled by "
+                       f"8-point sweep over {L} links, {spent:.1f} s of CPU; scaled by "
                        "the day's AON / root / sweep counts (extrapolated)"),
-            "sec_per_root": t_root, "sec_per_sweep": t_pass}
+            "sec_per_root": t_root, "sec_per_sweep": t_pass, "all_cores": par}
 
 
 def reference_arm(args, inst, cfg):
-    """CPU oracle timed on a bounded sample per step: one AON + one residual
-    re-walk per interval (a lower bound on the day's work), sampled on a few
-    roots of a few intervals and scaled to every interval's roots."""
-    import oracle
-    og = oracle.OracleGraph(inst.net)
+    """CPU oracle on every host core, timed on a bounded sample per step: one
+    AON + one residual re-walk per interval (a lower bound on the day's work),
+    sampled on a few roots of a few intervals and scaled to every interval's
+    roots."""
+    q = inst.net.fftime_q
+    pool = OraclePool(inst.net, q)
     n_roots = [len(np.unique(d.root_idx)) for d in inst.demand]
     picks = [int(np.argmax([d.n_items for d in inst.demand])), 0, 30, 60]
-    q = inst.net.fftime_q
+    tasks = []
+    for i in picks:
+        dem = inst.demand[i]
+        tasks += OraclePool.tasks(dem, np.unique(dem.root_idx)[:pool.n])
 
     def one_step():
         t0 = time.perf_counter()
-        per = []
-        for i in picks:
-            dem = inst.demand[i]
-            act = np.unique(dem.root_idx)[:3]
-            for r in act:
-                sel = dem.root_idx == r
-                od = oracle.OracleOD(dem.roots[r:r + 1], np.zeros(int(sel.sum()), np.int32), dem.src[sel],
-                                     dem.amount_fx[sel])
-                t = time.perf_counter()
-                par, _ = oracle.sssp(og, q, od.roots, want_dist=False)
-                oracle.load(og, q, par, od, 90000)
-                per.append(time.perf_counter() - t)
-        t_root = float(np.mean(per))
+        t_root = pool.seconds_per_root(tasks)
         est = sum(3 * n * t_root for n in n_roots)  # initial AON + 1 step + 1 residual tree
         return est, time.perf_counter() - t0
 
@@ -199,15 +275,17 @@ def reference_arm(args, inst, cfg):
         v, s = one_step()
         vals.append(v)
         spent += s
+    pool.close()
     value = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": ("3 roots x 4 intervals of Dijkstra + loading per step; day scaled as "
-                                        "3 AONs per interval x active roots (a lower bound: real intervals "
-                                        "need more FW steps)")},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": pool.n, "kind": "oracle",
+                             "sample": (f"{len(tasks)} destination roots (Dijkstra + loading) from 4 intervals per "
+                                        f"step, one process per core on {pool.n} cores; day scaled as 3 AONs per "
+                                        "interval x active roots (a lower bound: real intervals need more FW "
+                                        "steps)")},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -224,6 +302,10 @@ def sssp_only(args):
     g = Q.Graph(net)
     qd = torch.from_numpy(q).cuda()
     roots = torch.from_numpy(zones[:args.roots].astype(np.int32)).cuda()
+    tune = None
+    if not args.no_tune:
+        tune = Q.qdta_autotune(g, qd, roots, reps=max(args.steps, 1))
+        tune = {f'{c["kernel"]}x{c["ctas_per_sm"]}': round(c["ms"], 3) for c in tune["candidates"]}
     for _ in range(args.warmup):
         Q.qdta_sssp_batch(g, qd, roots)
     Q.qdta_profile_enable(g, True)
@@ -233,11 +315,13 @@ def sssp_only(args):
     ms = p["sssp_ms"] / max(p["sssp_launches"], 1)
     V, L, R = net.n_nodes, net.n_links, args.roots
     b_alg = R * 12.0 * V + 4.0 * (V + 1) + 8.0 * L
-    print(json.dumps({"metric": "SSSP batch (metro grid)", "roots": R, "ms_per_launch": ms,
+    print(json.dumps({"metric": "SSSP batch (metro grid)", "kernel": Q.qdta_sssp_kernel_name(g),
+                      "roots": R, "ms_per_launch": ms,
                       "gteps": R * L / (ms * 1e-3) / 1e9, "alg_gbs": b_alg / (ms * 1e-3) / 1e9,
                       "rounds_per_root": p["sssp_rounds"] / max(p["sssp_roots"], 1),
                       "relax_per_link": p["sssp_relaxations"] / max(p["sssp_roots"], 1) / L,
-                      "cell_activations_per_root": p["sssp_cell_activations"] / max(p["sssp_roots"], 1)}),
+                      "cell_activations_per_root": p["sssp_cell_activations"] / max(p["sssp_roots"], 1),
+                      "autotune_ms_per_batch": tune}),
           flush=True)
 
 
@@ -284,6 +368,56 @@ def batch32(args):
                       "stop": args.stop, "max_iter": args.max_iter}), flush=True)
 
 
+def adjoint_metro(args):
+    """Forward solve with a tape, then the adjoint, on the metro grid's peak
+    interval (its original demand, 2000 destination zones): the loss is a
+    link-count misfit L = sum over a 5 % link sample S of (f_a - y_a)^2 with
+    counts y = f * lognormal(0, 0.3) (seed 3) taken from the first solve."""
+    import torch
+    from paper_2104_12911_gb300 import qdta as Q, synth
+    inst = synth.config_day(seed=2)
+    peak = int(np.argmax([d.amount_fx.sum() for d in inst.demand]))
+    dem = inst.demand[peak]
+    net = inst.net
+    g = Q.Graph(net)
+    dev = torch.device("cuda", 0)
+    if not args.no_tune:
+        Q.qdta_autotune(g, torch.from_numpy(net.fftime_q.astype(np.int32)).to(dev),
+                        torch.from_numpy(inst.zones.astype(np.int32)).to(dev), reps=2)
+    od = Q.DeviceOD.of(dem)
+    p = Q.make_params("sweep8", args.stop, args.max_iter, 1e-4, record_tape=True)
+    rng = np.random.default_rng(3)
+    S = torch.from_numpy(rng.choice(net.n_links, net.n_links // 20, replace=False)).to(dev)
+    noise = torch.from_numpy(rng.lognormal(0.0, 0.3, S.shape[0])).to(dev)
+    y = None
+    fwd, bwd = [], []
+    for it in range(args.warmup + args.steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        f, st, rc, tape = Q.qdta_assign_interval(g, od, 900.0, p)
+        e1.record()
+        if y is None:
+            y = f[S] * noise
+        dL = torch.zeros_like(f)
+        dL[S] = 2.0 * (f[S] - y)
+        dd, dc = Q.qdta_backward(tape, dL)
+        e2.record()
+        torch.cuda.synchronize()
+        tape.close()
+        if it >= args.warmup:
+            fwd.append(e0.elapsed_time(e1))
+            bwd.append(e1.elapsed_time(e2))
+    print(json.dumps({"metric": "interval forward (taped) + adjoint, metro peak interval, seconds",
+                      "workload": f"500x500 grid, 2000 zones, interval {peak} ({dem.src.shape[0]} OD items, "
+                                  f"{dem.amount_fx.sum() / 2**32:.0f} trips)",
+                      "forward_s": float(np.mean(fwd)) / 1e3, "backward_s": float(np.mean(bwd)) / 1e3,
+                      "fw_iterations": st["iterations"], "aon_calls": st["aon_calls"],
+                      "sample_links": int(S.shape[0]), "loss": float(((f[S] - y) ** 2).sum()),
+                      "dL_ddemand_absmax": float(dd.abs().max()), "dL_dcap_absmax": float(dc.abs().max()),
+                      "sssp_kernel": Q.qdta_sssp_kernel_name(g), "stop": args.stop}), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "sssp_metro":
@@ -292,6 +426,9 @@ def main():
     if args.workload == "batch32":
         batch32(args)
         return
+    if args.workload == "adjoint_metro":
+        adjoint_metro(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -299,7 +436,7 @@ def main():
         if rank != 0:
             return
         inst, cfg = make_workload(args.workload)
-        cfg["parallelism"] = "cpu oracle, 1 thread"
+        cfg["parallelism"] = f"cpu oracle, one process per core ({os.cpu_count()} cores)"
         reference_arm(args, inst, cfg)
         return
 
@@ -321,6 +458,16 @@ def main():
     t_gen = time.perf_counter() - t_gen
     cfg["parallelism"] = f"replicas x{world} (one independent day per GPU)"
     g = Q.Graph(inst.net, local)
+    if not args.no_tune:
+        # launch shape of the shortest-path batch, chosen by measurement on the
+        # day's destination zones at free-flow costs (setup, untimed)
+        tune = Q.qdta_autotune(g, torch.from_numpy(inst.net.fftime_q.astype(np.int32)).to(dev),
+                               torch.from_numpy(inst.zones.astype(np.int32)).to(dev), reps=2)
+        cfg["sssp_launch"] = {"kernel": tune["best"]["kernel"], "ctas_per_sm": tune["best"]["ctas_per_sm"],
+                              "autotune_ms_per_batch": {f'{c["kernel"]}x{c["ctas_per_sm"]}': round(c["ms"], 3)
+                                                        for c in tune["candidates"]}}
+    torch.cuda.empty_cache()
+
     def upload(dem, pin=False):
         def t(a, dt):
             x = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
@@ -387,10 +534,7 @@ def main():
     clk = clocks.stop()
     ms = float(np.mean(day_list))
     e2e_ms = float(np.mean(e2e_list))
-    if world > 1:
-        t = torch.tensor([ms, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0].item()), float(t[1].item())
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], world, dev)
     if stats_plain is not None:
         cfg["plain_equals_batched"] = all(a["iterations"] == b["iterations"] and a["n_items"] == b["n_items"]
                                           for a, b in zip(stats, stats_plain))
@@ -412,7 +556,7 @@ def main():
         gteps = R_avg * L / (avg_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "traffic": None,
-                    "kernel": "sssp_kernel<true>" if V <= 10240 else "sssp_ilp_kernel<512>",
+                    "kernel": Q.qdta_sssp_kernel_name(g, Q.QDTA_TO_ROOT),
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                     "sssp_avg_ms": avg_ms, "roots_per_launch": R_avg, "gteps": gteps,
                     "sssp_share_of_plain_day": prof["sssp_ms"] / plain_ms if plain_ms else None}
@@ -433,12 +577,12 @@ def main():
         cpu = cpu_baseline(inst, stats)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": ms / 1e3 / world, "unit": "s", "n_gpus": world,
+        line = {"metric": METRIC, "value": job_seconds_per_day(ms, world), "unit": "s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "int32 costs/int64 flows + f64 line search", "data": "synthetic",
                 "config": cfg, "clocks": clk,
-                "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "e2e": {"value": job_seconds_per_day(e2e_ms, world), "unit": "s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(plain_launches * args.steps) if plain_launches else None,
                 "gpu_launches_note": ("kernels per timed step, counted on the plain schedule of the same day "

@@ -284,6 +284,47 @@ int qdta_tape_info(const qdta_tape *tape, int32_t *K_out_host, int64_t *n_items_
 int qdta_sssp_batch_noalloc(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R,
                             int32_t direction, int32_t *parent_link, int64_t *dist, void *stream);
 
+/* ---- launch-shape autotuning ----------------------------------------------
+ * The paper fixes its decomposition by hand (Section 5: processes per node x
+ * threads per process, with the routing of Alg. 7 partitioned over threads).
+ * On one GPU the equivalent choice is the shape of the batched shortest-path
+ * launch, and it is made by measurement: qdta_autotune times every candidate
+ * shape on one caller-supplied batch and keeps the fastest in the handle;
+ * later qdta_sssp_batch / qdta_assign_* / qdta_run_day calls use it.  Every
+ * candidate computes identical distances and parents (the tie rule is
+ * order-free), so tuning changes time only.
+ *
+ * Candidates: for graphs whose per-root state fits in shared memory, only the
+ * shared-memory kernel; otherwise the global-memory Bellman-Ford with
+ * {four-slot, compressed} adjacency (four-slot only when every degree <= 4) x
+ * three ways to apply an offer (returning atomicMin; read, then returning
+ * atomicMin; read, then non-returning atomicMin) x {2, 1} resident CTAs per
+ * SM, plus the cell-partitioned kernel.
+ *
+ * cost_q [L] int32 and roots [R] int32 are device arrays as for
+ * qdta_sssp_batch; parent_scratch is a caller-owned device array of R*V int32
+ * that receives the trees (contents unspecified afterwards).  Each candidate
+ * runs once untimed and then `reps` times between CUDA events on `stream`.
+ * The report (host) lists every candidate with its mean milliseconds per
+ * batch; `best` indexes the one kept.  Errors: QDTA_EINVAL for bad arguments;
+ * a failing candidate (e.g. QDTA_ENOMEM) aborts the tuning, restores the
+ * previous choice and returns its code.  Synchronises `stream`.  Not to be
+ * called during stream capture. */
+#define QDTA_TUNE_MAX 16
+typedef struct qdta_tune_entry {
+  char kernel[40];     /* kernel name, as qdta_sssp_kernel_name reports it */
+  int32_t ctas_per_sm; /* resident CTAs (one root each) per SM */
+  int32_t valid;       /* 1 when timed */
+  float ms;            /* mean milliseconds per batch */
+} qdta_tune_entry;
+typedef struct qdta_tune_report {
+  int32_t n;    /* candidates timed */
+  int32_t best; /* index of the candidate kept */
+  qdta_tune_entry entry[QDTA_TUNE_MAX];
+} qdta_tune_report;
+int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R, int32_t direction,
+                  int32_t reps, int32_t *parent_scratch, qdta_tune_report *out_host, void *stream);
+
 /* Enable / read / reset per-kernel event timings (plain schedule). */
 int qdta_profile_enable(qdta_graph *g, int32_t on);
 int qdta_profile_read(qdta_graph *g, qdta_profile *out_host);
@@ -292,6 +333,12 @@ int qdta_profile_read(qdta_graph *g, qdta_profile *out_host);
 const char *qdta_last_error(void);
 /* Library version string. */
 const char *qdta_version(void);
+
+/* Name of the shortest-path kernel qdta_sssp_batch launches on this graph in
+ * this direction (it depends on the node count, the degree bound and the
+ * QDTA_SSSP / QDTA_BF_* environment).  A static string; "" with QDTA_EINVAL
+ * set for a NULL graph or a bad direction.  No device work. */
+const char *qdta_sssp_kernel_name(const qdta_graph *g, int32_t direction);
 
 #ifdef __cplusplus
 }

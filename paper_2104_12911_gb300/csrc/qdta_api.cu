@@ -80,6 +80,7 @@ struct qdta_graph {
   long long n_xrev[2] = {0, 0};
   long long cell_delta = 0;  // near/far width of the cell kernel, in quanta
   int sssp_kind = 0;  // 0 shared-memory BF, 1 cell, 2 global-memory BF
+  int bf_bpsm = 0;    // resident CTAs per SM of the global-memory BF (0: as many as fit)
 };
 
 struct qdta_tape {
@@ -239,6 +240,15 @@ static int check_params(const qdta_params *p) {
 // ---------------------------------------------------------------------------
 extern "C" const char *qdta_last_error(void) { return g_err.c_str(); }
 extern "C" const char *qdta_version(void) { return "qdta-gb300 0.1 (sm_103a)"; }
+
+extern "C" const char *qdta_sssp_kernel_name(const qdta_graph *g, int32_t direction) {
+  if (!g || (direction != QDTA_TO_ROOT && direction != QDTA_FROM_ROOT)) {
+    fail(QDTA_EINVAL, "qdta_sssp_kernel_name: null graph or bad direction");
+    return "";
+  }
+  if (g->sssp_kind == 1) return "sssp_cell_kernel";
+  return sssp_kernel_name(g->d, direction, g->sssp_smem);
+}
 
 template <class T>
 static int upload(qdta_graph *g, const T *host, size_t n, T **dev) {
@@ -572,6 +582,19 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   // Bellman-Ford (measured fastest on the metro grid); QDTA_SSSP=cell selects
   // the cell-partitioned kernel
   g->sssp_kind = g->sssp_smem ? 0 : 2;
+  // launch choices (environment overrides for experiments; qdta_autotune
+  // replaces them by measurement)
+  g->d.tune_ell = getenv("QDTA_NO_ELL") ? 0 : 1;
+  g->d.tune_relax = 2;
+  if (const char *e = getenv("QDTA_BF_RELAX")) g->d.tune_relax = std::min(2, std::max(0, atoi(e)));
+  g->d.tune_carve = 85;  // rounds to the 196 KB step: 2 CTAs' queues + a 60 KB L1
+  if (const char *e = getenv("QDTA_SMQ_CARVEOUT")) g->d.tune_carve = atoi(e);
+  if (const char *e = getenv("QDTA_BF_BPSM")) g->bf_bpsm = std::max(1, atoi(e));
+  g->d.tune_shape = sssp_smq_shape_fits(V, 0) ? 0 : sssp_smq_shape_fits(V, 2) ? 2 : 0;
+  if (const char *e = getenv("QDTA_BF_SHAPE")) {
+    const int sh = atoi(e);
+    if (sssp_smq_shape_fits(V, sh)) g->d.tune_shape = sh;
+  }
   if (!g->sssp_smem) {
     const char *env = getenv("QDTA_SSSP");
     if (env && strcmp(env, "cell") == 0) g->sssp_kind = 1;
@@ -649,6 +672,9 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
           return rc;
         }
         gd.perm_off[dir] = q1; gd.perm_link[dir] = q2; gd.perm_nb[dir] = q3;
+        int md = 0;
+        for (int u = 0; u < V; ++u) md = std::max(md, po[u + 1] - po[u]);
+        gd.max_deg[dir] = md;
       }
       gd.node_int = C.node_int;
     }
@@ -716,10 +742,10 @@ extern "C" int qdta_profile_read(qdta_graph *g, qdta_profile *out) {
 static int sssp_grid(const qdta_graph *g, int R) {
   long long bpsm = g->sssp_kind == 1 ? g->cell_bpsm : g->sssp_bpsm;
   if (g->sssp_kind == 2) {
-    // resident roots of the global-memory variant: two 512-thread CTAs per
-    // SM keep the wavefronts' working set in L2 (QDTA_BF_BPSM overrides)
-    static int env_bpsm = [] { const char *e = getenv("QDTA_BF_BPSM"); return e ? atoi(e) : 2; }();
-    if (env_bpsm > 0 && env_bpsm < bpsm) bpsm = env_bpsm;
+    // resident roots of the global-memory variant: as many CTAs per SM as
+    // the launch shape was designed for (occupancy-checked), unless capped
+    if (sssp_uses_smq(g->d)) bpsm = sssp_smq_ctas_per_sm(g->d, 0);
+    if (g->bf_bpsm > 0 && g->bf_bpsm < bpsm) bpsm = g->bf_bpsm;
   }
   long long cap = bpsm * g->d.num_sms;
   if (g->sssp_kind == 2) R = (R + sssp_group_size() - 1) / sssp_group_size();  // CTAs, G roots each
@@ -730,7 +756,7 @@ static int sssp_grid(const qdta_graph *g, int R) {
 static int sssp_work(qdta_graph *g, int grid, SsspWork *w) {
   const size_t V = g->d.V;
   w->slots = grid;
-  RC(ws_get(g, "sssp.adj", (size_t)g->d.L, &w->adj));
+  RC(ws_get(g, "sssp.adj", std::max((size_t)g->d.L, (size_t)4 * V), &w->adj));
   if (g->sssp_kind == 1) {
     RC(ws_get(g, "sssp.lrev", (size_t)std::max(g->n_lrev[0], g->n_lrev[1]), &w->lrev));
     RC(ws_get(g, "sssp.prio", (size_t)grid * g->cells.n_cells, &w->prio));
@@ -741,7 +767,8 @@ static int sssp_work(qdta_graph *g, int grid, SsspWork *w) {
   } else if (!g->sssp_smem) {
     const size_t G = (size_t)sssp_group_size();
     RC(ws_get(g, "sssp.state", (size_t)grid * G * V, &w->state));
-    RC(ws_get(g, "sssp.stamp", (size_t)grid * G * V, &w->stamp));
+    if (sssp_uses_smq(g->d)) w->stamp = nullptr;  // marks live in shared memory
+    else RC(ws_get(g, "sssp.stamp", (size_t)grid * G * V, &w->stamp));
     RC(ws_get(g, "sssp.queue", (size_t)grid * 2 * G * V, &w->queue));
   } else {
     w->state = nullptr; w->stamp = nullptr; w->queue = nullptr;
@@ -766,7 +793,8 @@ static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots
                      parent, slot_dev, stride, dist, g->status, s, skip_dev,
                      g->prof_on ? g->prof_roots : nullptr);
   } else {
-    if (g->sssp_kind == 2 && sssp_uses_perm(g->d)) launch_pack_perm_adj(g->d, direction, q, w.adj, s, skip_dev);
+    if (g->sssp_kind == 2 && sssp_uses_ell(g->d, direction)) launch_pack_ell(g->d, direction, q, w.adj, s, skip_dev);
+    else if (g->sssp_kind == 2 && sssp_uses_perm(g->d)) launch_pack_perm_adj(g->d, direction, q, w.adj, s, skip_dev);
     else launch_pack_adj(g->d, direction, q, w.adj, s, skip_dev);
     prof_begin(g, s, &pe, 0, R_host);
     launch_sssp(g->d, direction, w.adj, roots, R_host, R_dev, grid, g->sssp_smem, w, parent, slot_dev,
@@ -789,6 +817,99 @@ extern "C" int qdta_sssp_batch(qdta_graph *g, const int32_t *cost_q, const int32
   RC(run_sssp(g, direction, cost_q, roots, R, nullptr, R, parent_link, nullptr, 0,
               (long long *)dist, s));
   return status_check(g, s);
+}
+
+// ---------------------------------------------------------------------------
+// launch-shape autotuning of the shortest-path batch
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneCfg {
+  int kind, ell, relax, bpsm, shape;
+};
+
+TuneCfg tune_get(const qdta_graph *g) {
+  return {g->sssp_kind, g->d.tune_ell, g->d.tune_relax, g->bf_bpsm, g->d.tune_shape};
+}
+
+void tune_set(qdta_graph *g, const TuneCfg &c) {
+  g->sssp_kind = c.kind;
+  g->d.tune_ell = c.ell;
+  g->d.tune_relax = c.relax;
+  g->bf_bpsm = c.bpsm;
+  g->d.tune_shape = c.shape;
+}
+}  // namespace
+
+extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R,
+                             int32_t direction, int32_t reps, int32_t *parent_scratch, qdta_tune_report *out_host,
+                             void *stream) {
+  RC(check_graph(g));
+  if (R <= 0 || reps <= 0) return fail(QDTA_EINVAL, "qdta_autotune: R and reps must be positive");
+  if (direction != QDTA_TO_ROOT && direction != QDTA_FROM_ROOT) return fail(QDTA_EINVAL, "bad direction");
+  if (!cost_q || !roots || !parent_scratch || !out_host) return fail(QDTA_EINVAL, "NULL argument");
+  DevGuard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const TuneCfg start = tune_get(g);
+  std::vector<TuneCfg> cand;
+  if (g->sssp_smem) {
+    cand.push_back(start);  // whole per-root state in shared memory: one shape
+  } else {
+    // global-memory Bellman-Ford: launch shape x adjacency layout x relaxation
+    // mode (each shape with as many CTAs per SM as it was designed for)
+    const bool ell_ok = g->d.max_deg[direction] <= 4 && g->d.node_int != nullptr;
+    bool any_smq = false;
+    for (int shape = 0; shape < 3; ++shape) {
+      if (!sssp_smq_shape_fits(g->d.V, shape) || getenv("QDTA_BF_NOSMQ")) continue;
+      if (shape == 2 && sssp_smq_shape_fits(g->d.V, 0)) continue;  // same block as shape 0, fewer marks
+      any_smq = true;
+      for (int ell = ell_ok ? 1 : 0; ell >= 0; --ell)
+        for (int relax = 2; relax >= 1; --relax) cand.push_back({2, ell, relax, 0, shape});
+    }
+    if (!any_smq) cand.push_back({2, start.ell, start.relax, start.bpsm, start.shape});  // global queues
+    if (g->has_cells) cand.push_back({1, start.ell, start.relax, start.bpsm, start.shape});  // cell-partitioned
+  }
+  if ((int)cand.size() > QDTA_TUNE_MAX) cand.resize(QDTA_TUNE_MAX);
+  qdta_tune_report rep{};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = QDTA_OK, best = -1;
+  for (size_t i = 0; i < cand.size() && rc == QDTA_OK; ++i) {
+    tune_set(g, cand[i]);
+    qdta_tune_entry &en = rep.entry[rep.n++];
+    const char *name = g->sssp_kind == 1 ? "sssp_cell_kernel" : sssp_kernel_name(g->d, direction, g->sssp_smem);
+    snprintf(en.kernel, sizeof(en.kernel), "%s", name);
+    en.ctas_per_sm = (int32_t)((long long)sssp_grid(g, 1 << 30) / std::max(1, g->d.num_sms));
+    // one untimed batch (workspace sizing, first-touch), then reps timed
+    if ((rc = status_reset(g, s)) ||
+        (rc = run_sssp(g, direction, cost_q, roots, R, nullptr, R, parent_scratch, nullptr, 0, nullptr, s)) ||
+        (rc = status_check(g, s)))
+      break;
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < reps && rc == QDTA_OK; ++k)
+      rc = run_sssp(g, direction, cost_q, roots, R, nullptr, R, parent_scratch, nullptr, 0, nullptr, s);
+    cudaEventRecord(e1, s);
+    if (rc == QDTA_OK) rc = status_check(g, s);
+    if (rc != QDTA_OK) break;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = fail(QDTA_ECUDA, "qdta_autotune: event timing failed");
+      break;
+    }
+    en.ms = ms / reps;
+    en.valid = 1;
+    if (best < 0 || en.ms < rep.entry[best].ms) best = (int)i;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != QDTA_OK || best < 0) {
+    tune_set(g, start);
+    return rc != QDTA_OK ? rc : fail(QDTA_ECUDA, "qdta_autotune: no candidate ran");
+  }
+  tune_set(g, cand[best]);
+  rep.best = best;
+  *out_host = rep;
+  return QDTA_OK;
 }
 
 extern "C" int qdta_load_aon(qdta_graph *g, const int32_t *cost_q, const int32_t *parent_link,
@@ -864,6 +985,11 @@ struct Solver {
   int *tape_q;
   double *tape_alpha, *tape_f;
   int tape_cap;
+  // free-flow trees of every root index (nullable): the initial AON of an
+  // interval runs at q = BPR(0), the same link times every interval, so its
+  // trees are gathered from here (rows by root index) instead of recomputed
+  const int *ff_parent = nullptr;
+  int ff_rows = 0;
 };
 
 static int solver_alloc(Solver &S, const std::string &tag, int ring, bool tape_f) {
@@ -891,11 +1017,15 @@ static int solver_alloc(Solver &S, const std::string &tag, int ring, bool tape_f
   return QDTA_OK;
 }
 
-// AON under the link times in S.q: trees into the parent slot, flows into g_fx
-static int seg_aon(Solver &S, const int *slot_dev) {
+// AON under the link times in S.q: trees into the parent slot, flows into
+// g_fx.  gather_ff: the trees are the free-flow ones, copied from S.ff_parent
+static int seg_aon(Solver &S, const int *slot_dev, bool gather_ff = false) {
   qdta_graph *g = S.g;
-  RC(run_sssp(g, QDTA_TO_ROOT, S.q, S.roots, S.R_host, S.R_dev, S.R_cap, S.parent, slot_dev,
-              S.parent_stride, nullptr, S.s));
+  if (gather_ff)
+    launch_gather_rows(S.ff_parent, S.ff_rows, g->d.V, S.root_slot, S.parent, slot_dev, S.parent_stride, S.s);
+  else
+    RC(run_sssp(g, QDTA_TO_ROOT, S.q, S.roots, S.R_host, S.R_dev, S.R_cap, S.parent, slot_dev,
+                S.parent_stride, nullptr, S.s));
   launch_pack_head_q(g->d, S.q, S.head_q, S.s);
   CK(cudaMemsetAsync(S.g_fx, 0, (size_t)g->d.L * 8, S.s));
   ProfEvent pe;
@@ -915,7 +1045,7 @@ static int seg_init(Solver &S) {
   launch_link_const(g->d, S.dt_h, S.kc, S.s);
   CK(cudaMemsetAsync(S.f, 0, (size_t)g->d.L * 8, S.s));
   launch_bpr(g->d, S.f, S.dt_h, nullptr, S.q, g->status, S.s);
-  RC(seg_aon(S, nullptr));
+  RC(seg_aon(S, nullptr, S.ff_parent != nullptr));
   launch_flow_from_fx(g->d.L, S.g_fx, S.f, S.s);
   launch_tape0(g->d, S.q, S.f, S.tape_q, S.tape_alpha, S.tape_f, S.s);
   return QDTA_OK;
@@ -1502,6 +1632,23 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
     if (it != g->ws.end()) free_b += it->second.bytes;
   }
   const double per_slot = (double)Z * V * 4.0;
+  // free-flow trees of all zones, once per day (skipped when HBM is short:
+  // they cost one ring slot)
+  if (!getenv("QDTA_NO_FF_CACHE") && (double)free_b >= 6.0 * per_slot) {
+    int *ff = nullptr;
+    RC(ws_get(g, "day.ff_parent", (size_t)Z * V, &ff));
+    RC(ws_get(g, "day.f", L, &S.f));
+    CK(cudaMemsetAsync(S.f, 0, L * 8, s));
+    RC(status_reset(g, s));
+    launch_bpr(g->d, S.f, S.dt_h, nullptr, D.q_work, g->status, s);
+    RC(run_sssp(g, QDTA_TO_ROOT, D.q_work, D.zones, Z, nullptr, Z, ff, nullptr, 0, nullptr, s));
+    RC(status_check(g, s));
+    S.ff_parent = ff;
+    S.ff_rows = Z;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    auto it = g->ws.find("day.parent");
+    if (it != g->ws.end()) free_b += it->second.bytes;
+  }
   long long ring = p->max_iter + 1;
   long long afford = (long long)((double)free_b * 0.8 / per_slot);
   if (ring > afford) ring = afford;

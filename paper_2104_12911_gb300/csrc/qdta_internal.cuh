@@ -229,6 +229,14 @@ struct GraphDev {
   const int *perm_off[2];          // [V + 1]
   const int *perm_link[2];         // [L]
   const int *perm_nb[2];           // [L]
+  int max_deg[2];                  // largest degree per direction
+  // launch choices of the global-memory SSSP (set at create, changed by
+  // qdta_autotune): four-slot adjacency when max_deg <= 4, relaxation mode
+  // (0 returning atomic, 1 read then returning atomic, 2 read then
+  // non-returning atomic), shared-memory carveout percentage, launch shape
+  // of the shared-memory-queue kernel (0: 512 threads, two mark bitmaps;
+  // 1: 256 threads, one bitmap; 2: 512 threads, one bitmap)
+  int tune_ell, tune_relax, tune_carve, tune_shape;
 };
 
 // Cell partition for the shared-memory cell SSSP (graphs above the
@@ -299,7 +307,18 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                  unsigned long long *roots_counter = nullptr);
 int sssp_max_smem_nodes();
 int sssp_group_size();  // roots per CTA of the global-memory kernel
+// parent rows by root index: row r of src goes to row root_slot[r] of the
+// parent slot (*slot_dev, or 0), skipped when root_slot[r] < 0
+void launch_gather_rows(const int *src, int rows, int V, const int *root_slot, int *parent, const int *slot_dev,
+                        long long slot_stride, cudaStream_t s);
+bool sssp_uses_smq(const GraphDev &g);   // global-memory launch keeps queues and marks in shared memory
+bool sssp_smq_shape_fits(int V, int shape);
+int sssp_smq_ctas_per_sm(const GraphDev &g, int direction);
 bool sssp_uses_perm(const GraphDev &g);  // global-memory launch reads the locality-ordered adjacency
+bool sssp_uses_ell(const GraphDev &g, int direction);
+const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem);  // ... in the four-slot layout
+void launch_pack_ell(const GraphDev &g, int direction, const int *q, int4 *ell, cudaStream_t s,
+                     const int *skip_dev = nullptr);
 long long launch_count();
 // which: 0 = fw_continue, 1 = need_sweep, 2 = res_continue
 void launch_set_cond(const Ctl *ctl, int which, unsigned long long cond, cudaStream_t s);

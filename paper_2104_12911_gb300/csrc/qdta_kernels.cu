@@ -9,8 +9,11 @@
 //   update / tape         convex flow update f + alpha (g - f)
 //   scatter / compact     residual-demand merge d(i+1) = d_o(i+1) + d_r(i+1) (Alg. 1)
 //   adj_* / gather        adjoint of the unrolled FW map
+#include <algorithm>
 #include <atomic>
 #include <climits>
+#include <string>
+#include <vector>
 #include <cstdlib>
 #include <cstdio>
 
@@ -60,6 +63,31 @@ __global__ void pack_perm_adj_kernel(int L, const int *__restrict__ perm_link, c
     const int e = perm_link[k];
     adj[k] = make_int4(e, perm_nb[k], q[e], 0);
   }
+}
+
+// four fixed slots per node (graphs whose maximum degree is <= 4): slot k of
+// node u holds its k-th link, (-1, 0, 0, 0) when absent
+__global__ void pack_ell_kernel(int V, const int *__restrict__ perm_off, const int *__restrict__ perm_link,
+                                const int *__restrict__ perm_nb, const int *__restrict__ q, int4 *__restrict__ ell,
+                                const int *skip_dev) {
+  if (skip_dev && *skip_dev) return;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 4 * V; t += gridDim.x * blockDim.x) {
+    const int u = t >> 2, k = t & 3;
+    const int a = perm_off[u] + k;
+    if (a < perm_off[u + 1]) {
+      const int e = perm_link[a];
+      ell[t] = make_int4(e, perm_nb[a], q[e], 0);
+    } else {
+      ell[t] = make_int4(-1, 0, 0, 0);
+    }
+  }
+}
+
+void launch_pack_ell(const GraphDev &g, int direction, const int *q, int4 *ell, cudaStream_t s,
+                     const int *skip_dev) {
+  COUNT_LAUNCH();
+  pack_ell_kernel<<<cdiv(4ll * g.V, 256), 256, 0, s>>>(g.V, g.perm_off[direction], g.perm_link[direction],
+                                                       g.perm_nb[direction], q, ell, skip_dev);
 }
 
 void launch_pack_perm_adj(const GraphDev &g, int direction, const int *q, int4 *adj, cudaStream_t s,
@@ -764,29 +792,50 @@ int sssp_group_size() {
 }
 
 // Global-memory keys with the round bookkeeping in shared memory: the
-// frontier queues (with a global overflow) and the "already queued" marks,
-// kept as two bitmaps of V bits that alternate with the round parity (the
-// bits of the queue being read are cleared as it is read, so the bitmap is
-// clean again two rounds later).  This takes the frontier read and the
-// dedupe atomic off the chain of dependent L2 trips of every relaxation.
-constexpr int SMQ_CAP = 3072;  // queue entries per buffer in shared memory
+// frontier queues (with a global overflow) and the "already queued" marks.
+// This takes the frontier read and the dedupe atomic off the chain of
+// dependent L2 trips of every relaxation.  The marks are either
+//  - two bitmaps of V bits that alternate with the round parity (the bits of
+//    the queue being read are cleared as it is read, so the bitmap is clean
+//    again two rounds later), or
+//  - ONEBM: one bitmap; a round first clears the marks of the whole queue it
+//    is about to read, then passes a barrier, so a mark seen set during the
+//    relaxations always means "already in the next queue" (half the shared
+//    memory: four 256-thread CTAs per SM, or graphs up to ~580k nodes).
+// Launch shapes (threads, bitmaps, queue entries per buffer):
+//   0: 512, two, 3072 (two CTAs per SM)   1: 256, one, 2048 (four CTAs per SM)
+//   2: 512, one, 3072 (two CTAs per SM, larger graphs)
+struct SmqShape {
+  int threads, bitmaps, qcap, ctas;
+};
+static const SmqShape kSmqShape[3] = {{512, 2, 3072, 2}, {256, 1, 2048, 4}, {512, 1, 3072, 2}};
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
+// RELAX selects how an offer (cand, link) to neighbour y is applied:
+//   0  returning atomicMin; y is queued when the returned old distance was larger
+//   1  read y's key first, skip when the offer cannot win, else as 0
+//   2  read y's key first; when the offer beats it, a non-returning atomicMin
+//      and y is queued when the read distance was larger.  The queued set is
+//      the same as under 1: whichever offer lowers y's distance in a round read
+//      a key at least as large as the value it replaced (keys only decrease),
+//      so its thread queues y; later reads see the update because the round
+//      ends in a CTA barrier and every state access goes through L2.
+template <int THREADS, bool ELL, int RELAX, bool ONEBM>
+__global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64))
 sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__ adj,
                 const int *__restrict__ roots, int R_host, const int *R_dev,
                 unsigned long long *g_state, int *g_queue, int *parent,
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                 const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
-                int max_rounds) {
+                int max_rounds, int qcap) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
   if (skip_dev && *skip_dev) return;
   const int R = R_dev ? *R_dev : R_host;
   if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
   const int W = (V + 31) >> 5;
-  unsigned *bm0 = smq_smem, *bm1 = smq_smem + W;
-  int *sq0 = reinterpret_cast<int *>(smq_smem + 2 * W), *sq1 = sq0 + SMQ_CAP;
+  constexpr int NBM = ONEBM ? 1 : 2;
+  unsigned *bm0 = smq_smem, *bm1 = smq_smem + (NBM - 1) * W;
+  int *sq0 = reinterpret_cast<int *>(smq_smem + NBM * W), *sq1 = sq0 + qcap;
   const size_t b = blockIdx.x;
   unsigned long long *state = g_state + b * (size_t)V;
   int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;  // overflow beyond SMQ_CAP
@@ -796,7 +845,7 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
   constexpr int NQ = THREADS / 4;
   const int quad = threadIdx.x >> 2, lane4 = threadIdx.x & 3;
   for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = ~0ull;
-  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) smq_smem[i] = 0u;
+  for (int i = threadIdx.x; i < NBM * W; i += blockDim.x) smq_smem[i] = 0u;
   __syncthreads();
   for (int r = blockIdx.x; r < R; r += gridDim.x) {
     const int z = node_int ? node_int[roots[r]] : roots[r];
@@ -813,21 +862,33 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
     while (ncur > 0) {
       const int c = round % 3;
       if (threadIdx.x == 0) s_cnt[(round + 1) % 3] = 0;
+      if (ONEBM) {
+        for (int i = threadIdx.x; i < ncur; i += THREADS) {
+          const int y = i < qcap ? scur[i] : __ldcg(&gcur[i - qcap]);
+          atomicAnd(&bm0[y >> 5], ~(1u << (y & 31)));
+        }
+        __syncthreads();
+      }
       for (int base = 0; base < ncur; base += NQ * SSSP2_NPT) {
         int w[SSSP2_NPT], kb[SSSP2_NPT], ke[SSSP2_NPT];
         unsigned long long dw[SSSP2_NPT];
 #pragma unroll
         for (int j = 0; j < SSSP2_NPT; ++j) {
           const int i = base + j * NQ + quad;
-          w[j] = i < ncur ? (i < SMQ_CAP ? scur[i] : __ldcg(&gcur[i - SMQ_CAP])) : -1;
+          w[j] = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
         }
 #pragma unroll
         for (int j = 0; j < SSSP2_NPT; ++j) {
           kb[j] = 0; ke[j] = 0; dw[j] = 0;
           if (w[j] >= 0) {
-            if (lane4 == 0) atomicAnd(&bcur[w[j] >> 5], ~(1u << (w[j] & 31)));
-            kb[j] = __ldg(&off[w[j]]) + lane4;
-            ke[j] = __ldg(&off[w[j] + 1]);
+            if (!ONEBM && lane4 == 0) atomicAnd(&bcur[w[j] >> 5], ~(1u << (w[j] & 31)));
+            if (ELL) {  // slot lane4 of node w: no offset load on the chain
+              kb[j] = 4 * w[j] + lane4;
+              ke[j] = kb[j] + 1;
+            } else {
+              kb[j] = __ldg(&off[w[j]]) + lane4;
+              ke[j] = __ldg(&off[w[j] + 1]);
+            }
             dw[j] = __ldcg(&state[w[j]]) >> LB;
           }
         }
@@ -839,8 +900,11 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
           for (int j = 0; j < SSSP2_NPT; ++j)
             if (kb[j] < ke[j]) ent[j] = __ldg(&adj[kb[j]]);
 #pragma unroll
-          for (int j = 0; j < SSSP2_NPT; ++j)
-            if (kb[j] < ke[j]) tk[j] = __ldcg(&state[ent[j].y]);
+          for (int j = 0; j < SSSP2_NPT; ++j) {
+            if (ELL && kb[j] < ke[j] && ent[j].x < 0) ke[j] = kb[j];  // absent slot
+            tk[j] = ~0ull;
+            if (RELAX > 0 && kb[j] < ke[j]) tk[j] = __ldcg(&state[ent[j].y]);
+          }
 #pragma unroll
           for (int j = 0; j < SSSP2_NPT; ++j) {
             if (kb[j] < ke[j]) {
@@ -851,12 +915,18 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
               } else {
                 const unsigned long long key = (cand << LB) | (unsigned long long)(unsigned)ent[j].x;
                 if (key < tk[j]) {
-                  const unsigned long long old = atomicMin(&state[ent[j].y], key);
                   const int y = ent[j].y;
-                  if ((old >> LB) > cand && !((atomicOr(&bnxt[y >> 5], 1u << (y & 31)) >> (y & 31)) & 1u)) {
+                  unsigned long long seen;
+                  if (RELAX == 2) {
+                    atomicMin(&state[y], key);  // result unused: no wait on the reply
+                    seen = tk[j];
+                  } else {
+                    seen = atomicMin(&state[y], key);
+                  }
+                  if ((seen >> LB) > cand && !((atomicOr(&bnxt[y >> 5], 1u << (y & 31)) >> (y & 31)) & 1u)) {
                     const int pos = atomicAdd(&s_cnt[c], 1);
-                    if (pos < SMQ_CAP) snxt[pos] = y;
-                    else gnxt[pos - SMQ_CAP] = y;
+                    if (pos < qcap) snxt[pos] = y;
+                    else gnxt[pos - qcap] = y;
                   }
                 }
               }
@@ -888,29 +958,84 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
     __syncthreads();
     // an early exit (timeout) can leave marks behind: clear both bitmaps
     if (round > max_rounds)
-      for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) smq_smem[i] = 0u;
+      for (int i = threadIdx.x; i < NBM * W; i += blockDim.x) smq_smem[i] = 0u;
+    // output in external node order, resetting each key as it is read (every
+    // internal index is read exactly once); four independent loads in flight
+    // per thread instead of one dependent pair per iteration
     int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
-    for (int v = threadIdx.x; v < V; v += blockDim.x) {
-      const unsigned long long key = __ldcg(&state[node_int ? node_int[v] : v]);
-      const unsigned long long lk = key & NOLINK;
-      prow[v] = lk == NOLINK ? -1 : (int)lk;
-      if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
+    for (int v0 = threadIdx.x; v0 < V; v0 += 4 * THREADS) {
+      int u[4];
+      unsigned long long key[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int v = v0 + k * THREADS;
+        u[k] = v < V ? (node_int ? __ldg(&node_int[v]) : v) : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) key[k] = u[k] >= 0 ? __ldcg(&state[u[k]]) : 0ull;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int v = v0 + k * THREADS;
+        if (u[k] < 0) continue;
+        state[u[k]] = ~0ull;
+        const unsigned long long lk = key[k] & NOLINK;
+        prow[v] = lk == NOLINK ? -1 : (int)lk;
+        if (drow) drow[v] = key[k] == ~0ull ? LLONG_MAX : (long long)(key[k] >> LB);
+      }
     }
-    __syncthreads();
-    for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = ~0ull;
     __syncthreads();
   }
 }
 
-size_t sssp_smq_smem_bytes(int V) { return (size_t)2 * ((V + 31) / 32) * 4 + (size_t)2 * SMQ_CAP * 4; }
+size_t sssp_smq_smem_bytes(int V, int shape) {
+  const SmqShape &sh = kSmqShape[shape];
+  return (size_t)sh.bitmaps * ((V + 31) / 32) * 4 + (size_t)2 * sh.qcap * 4;
+}
+
+// does launch shape `shape` fit its CTAs per SM in the 196 KB carveout step
+bool sssp_smq_shape_fits(int V, int shape) {
+  if (shape < 0 || shape > 2) return false;
+  return sssp_smq_smem_bytes(V, shape) * kSmqShape[shape].ctas <= 192 * 1024;
+}
 
 // the global-memory launch runs the shared-memory-queue kernel (which reads
 // the locality-ordered adjacency when the graph has one)
 bool sssp_uses_smq(const GraphDev &g) {
-  return sssp_group_size() == 1 && sssp_smq_smem_bytes(g.V) <= 96 * 1024 && !getenv("QDTA_BF_NOSMQ");
+  return sssp_group_size() == 1 && sssp_smq_shape_fits(g.V, g.tune_shape) && !getenv("QDTA_BF_NOSMQ");
 }
+
+int sssp_smq_threads(const GraphDev &g) { return kSmqShape[g.tune_shape].threads; }
+int sssp_smq_max_ctas(const GraphDev &g) { return kSmqShape[g.tune_shape].ctas; }
 bool sssp_uses_perm(const GraphDev &g) { return g.node_int != nullptr && sssp_uses_smq(g); }
+// fixed four-slot adjacency: locality order present, every degree <= 4
+bool sssp_uses_ell(const GraphDev &g, int direction) {
+  return sssp_uses_perm(g) && g.max_deg[direction] <= 4 && g.tune_ell;
+}
+
+// name of the kernel launch_sssp runs for this graph, direction and storage
+const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
+  if (use_smem) return "sssp_kernel<true>";
+  if (sssp_uses_smq(g)) {
+    static const std::vector<std::string> names = [] {
+      std::vector<std::string> v;
+      for (int sh = 0; sh < 3; ++sh)
+        for (int e = 0; e < 2; ++e)
+          for (int r = 0; r < 3; ++r)
+            v.push_back("sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + (e ? "true" : "false") +
+                        "," + std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") + ">");
+      return v;
+    }();
+    const int r = g.tune_relax < 0 ? 0 : g.tune_relax > 2 ? 2 : g.tune_relax;
+    return names[(g.tune_shape * 2 + (sssp_uses_ell(g, direction) ? 1 : 0)) * 3 + r].c_str();
+  }
+  switch (sssp_group_size()) {
+    case 2: return "sssp_group_kernel<512,2>";
+    case 4: return "sssp_group_kernel<512,4>";
+    case 8: return "sssp_group_kernel<512,8>";
+    default: return "sssp_ilp_kernel<512>";
+  }
+}
 
 int sssp_max_smem_nodes() { return (200 * 1024) / 20; }
 
@@ -926,6 +1051,37 @@ int sssp_blocks_per_sm(bool use_smem, int V) {
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sssp_ilp_kernel<512>, 512, 0);
   }
+  return n > 0 ? n : 1;
+}
+
+using SmqKernel = void (*)(int, int, const int *, const int4 *, const int *, int, const int *, unsigned long long *,
+                          int *, int *, const int *, long long, long long *, unsigned *, const int *,
+                          unsigned long long *, const int *, int, int);
+
+template <int THREADS, bool ONEBM>
+static SmqKernel smq_kernel_relax(bool ell, int relax) {
+  if (ell) return relax == 2 ? sssp_smq_kernel<THREADS, true, 2, ONEBM>
+                : relax == 1 ? sssp_smq_kernel<THREADS, true, 1, ONEBM> : sssp_smq_kernel<THREADS, true, 0, ONEBM>;
+  return relax == 2 ? sssp_smq_kernel<THREADS, false, 2, ONEBM>
+       : relax == 1 ? sssp_smq_kernel<THREADS, false, 1, ONEBM> : sssp_smq_kernel<THREADS, false, 0, ONEBM>;
+}
+
+static SmqKernel smq_kernel_for(int shape, bool ell, int relax) {
+  if (shape == 1) return smq_kernel_relax<256, true>(ell, relax);
+  if (shape == 2) return smq_kernel_relax<512, true>(ell, relax);
+  return smq_kernel_relax<512, false>(ell, relax);
+}
+
+// resident CTAs per SM of the selected shared-memory-queue kernel (occupancy
+// under the pinned carveout, at most the shape's design count)
+int sssp_smq_ctas_per_sm(const GraphDev &g, int direction) {
+  const SmqKernel kern = smq_kernel_for(g.tune_shape, sssp_uses_ell(g, direction), g.tune_relax);
+  const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kSmqShape[g.tune_shape].threads, smq);
+  n = std::min(n, kSmqShape[g.tune_shape].ctas);
   return n > 0 ? n : 1;
 }
 
@@ -957,8 +1113,8 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
     auto kern = bf_threads == 1024 ? sssp_ilp_kernel<1024> : bf_threads == 512 ? sssp_ilp_kernel<512>
               : bf_threads == 256 ? sssp_ilp_kernel<256> : sssp_ilp_kernel<128>;
     const int G = sssp_group_size();
-    const size_t smq = sssp_smq_smem_bytes(g.V);
     if (sssp_uses_smq(g)) {
+      const bool ell = sssp_uses_ell(g, direction);
       // Two 86.5 KB CTAs per SM need a ~196 KB shared-memory carveout; the
       // rest of the unified 256 KB stays L1 (the adjacency gathers want it:
       // 55 ms per batch at 196 KB vs 84 ms at the 228 KB maximum).  Pinning
@@ -966,14 +1122,16 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       // same configuration.  The percentage is rounded up to a supported
       // size: 85 % of 228 KB asks for 194 KB and gets the 196 KB step (86 %
       // would round up to 228 KB).  QDTA_SMQ_CARVEOUT overrides, in percent.
-      cudaFuncSetAttribute(sssp_smq_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
-      static int carve = [] { const char *e = getenv("QDTA_SMQ_CARVEOUT"); return e ? atoi(e) : 85; }();
-      cudaFuncSetAttribute(sssp_smq_kernel<512>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+      const SmqKernel kern = smq_kernel_for(g.tune_shape, ell, g.tune_relax);
+      const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
+      const int threads = kSmqShape[g.tune_shape].threads;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
       const bool perm = g.node_int != nullptr;
-      sssp_smq_kernel<512><<<grid, 512, smq, s>>>(g.V, g.LB, perm ? g.perm_off[direction] : off, adj, roots, R_host,
-                                                   R_dev, w.state, w.queue, parent, parent_slot_dev, slot_stride,
-                                                   dist, status, skip_dev, roots_counter, perm ? g.node_int : nullptr,
-                                                   round_limit(g.V));
+      kern<<<grid, threads, smq, s>>>(g.V, g.LB, perm ? g.perm_off[direction] : off, adj, roots, R_host, R_dev,
+                                      w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip_dev,
+                                      roots_counter, perm ? g.node_int : nullptr, round_limit(g.V),
+                                      kSmqShape[g.tune_shape].qcap);
       return;
     }
     if (G == 2) kern = sssp_group_kernel<512, 2>;
@@ -1868,6 +2026,31 @@ void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *bl
 
 // roots with at least one item, in root order; root_slot maps a root index
 // to its row in the parent arrays (or -1)
+// copy free-flow tree rows into the rows of the active roots (row r ->
+// root_slot[r]); int4 copies when rows are 16-byte aligned
+__global__ void gather_rows_kernel(const int *__restrict__ src, int V, const int *__restrict__ root_slot,
+                                   int *__restrict__ parent, const int *slot_dev, long long slot_stride) {
+  const int r = blockIdx.x;
+  const int k = root_slot[r];
+  if (k < 0) return;
+  int *dst = parent + (slot_dev ? (long long)(*slot_dev) * slot_stride : 0ll) + (long long)k * V;
+  const int *row = src + (long long)r * V;
+  if ((V & 3) == 0 && (reinterpret_cast<size_t>(dst) & 15) == 0 && (reinterpret_cast<size_t>(row) & 15) == 0) {
+    const int4 *a = reinterpret_cast<const int4 *>(row);
+    int4 *b = reinterpret_cast<int4 *>(dst);
+    for (int i = threadIdx.x; i < (V >> 2); i += blockDim.x) b[i] = __ldcs(&a[i]);
+  } else {
+    for (int i = threadIdx.x; i < V; i += blockDim.x) dst[i] = row[i];
+  }
+}
+
+void launch_gather_rows(const int *src, int rows, int V, const int *root_slot, int *parent, const int *slot_dev,
+                        long long slot_stride, cudaStream_t s) {
+  if (rows <= 0 || V <= 0) return;
+  COUNT_LAUNCH();
+  gather_rows_kernel<<<rows, 256, 0, s>>>(src, V, root_slot, parent, slot_dev, slot_stride);
+}
+
 __global__ void active_roots_kernel(int R, const long long *n_dev, long long cap, const int *root_idx,
                                     const int *zone_nodes, int *flag, int *active, int *root_slot,
                                     int *n_active) {

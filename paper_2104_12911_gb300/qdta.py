@@ -76,6 +76,22 @@ class Profile(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+TUNE_MAX = 16
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("kernel", C.c_char * 40), ("ctas_per_sm", C.c_int32), ("valid", C.c_int32), ("ms", C.c_float)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("entry", TuneEntry * TUNE_MAX)]
+
+    def as_dict(self):
+        rows = [{"kernel": e.kernel.decode(), "ctas_per_sm": e.ctas_per_sm, "ms": e.ms}
+                for e in self.entry[:self.n] if e.valid]
+        return {"best": rows[self.best] if rows else None, "candidates": rows}
+
+
 class Instance(C.Structure):
     _fields_ = [("graph", C.c_void_p), ("od", OD), ("dt_s", C.c_double), ("flow_out", C.c_void_p)]
 
@@ -112,6 +128,7 @@ def lib():
                 "qdta_tape_info": [P, P, P],
                 "qdta_profile_enable": [P, I32],
                 "qdta_profile_read": [P, P],
+                "qdta_autotune": [P, P, P, I32, I32, I32, P, P, P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -120,6 +137,8 @@ def lib():
             L.qdta_last_error.restype = C.c_char_p
             L.qdta_last_error.argtypes = []
             L.qdta_version.restype = C.c_char_p
+            L.qdta_sssp_kernel_name.restype = C.c_char_p
+            L.qdta_sssp_kernel_name.argtypes = [P, I32]
             _lib = L
     return _lib
 
@@ -219,6 +238,17 @@ def qdta_sssp_batch_noalloc(g: Graph, cost_q, roots, direction=QDTA_TO_ROOT, wan
     _check(lib().qdta_sssp_batch_noalloc(g.h, _ptr(cost_q), _ptr(roots), R, int(direction), _ptr(parent),
                                          _ptr(dist), _stream()))
     return parent, dist
+
+
+def qdta_autotune(g: Graph, cost_q, roots, direction=QDTA_TO_ROOT, reps=2):
+    """Time every launch shape of the shortest-path batch on (cost_q, roots)
+    and keep the fastest in ``g``; returns the report as a dict."""
+    R = int(roots.shape[0])
+    scratch = torch.empty((R, g.n_nodes), dtype=torch.int32, device=g.device)
+    rep = TuneReport()
+    _check(lib().qdta_autotune(g.h, _ptr(cost_q), _ptr(roots), R, int(direction), int(reps), _ptr(scratch),
+                               C.byref(rep), _stream()))
+    return rep.as_dict()
 
 
 def qdta_load_aon(g: Graph, cost_q, parent, od: DeviceOD, dt_q: int, flow_fx=None, want_stop=False):
@@ -338,3 +368,11 @@ def qdta_profile_read(g: Graph):
 
 def version():
     return lib().qdta_version().decode()
+
+
+def qdta_sssp_kernel_name(g: Graph, direction: int = QDTA_TO_ROOT) -> str:
+    """Name of the shortest-path kernel qdta_sssp_batch launches on ``g``."""
+    name = lib().qdta_sssp_kernel_name(g.h, direction).decode()
+    if not name:
+        raise QdtaError(-1, lib().qdta_last_error().decode())
+    return name

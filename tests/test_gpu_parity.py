@@ -105,17 +105,33 @@ def test_sssp_unreachable_nodes():
     np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-@pytest.mark.parametrize("variant", ["default", "no_reorder", "global_queues", "cell"])
+LARGE_VARIANTS = {
+    "default": ({}, "sssp_smq_kernel<512,true,2,false>"),
+    "csr": ({"QDTA_NO_ELL": "1"}, "sssp_smq_kernel<512,false,2,false>"),
+    "no_reorder": ({"QDTA_NO_REORDER": "1"}, "sssp_smq_kernel<512,false,2,false>"),
+    "returning_atomic": ({"QDTA_BF_RELAX": "1"}, "sssp_smq_kernel<512,true,1,false>"),
+    "atomic_only": ({"QDTA_BF_RELAX": "0"}, "sssp_smq_kernel<512,true,0,false>"),
+    "four_ctas_one_bitmap": ({"QDTA_BF_SHAPE": "1"}, "sssp_smq_kernel<256,true,2,true>"),
+    "four_ctas_csr_returning": ({"QDTA_BF_SHAPE": "1", "QDTA_NO_ELL": "1", "QDTA_BF_RELAX": "1"},
+                                "sssp_smq_kernel<256,false,1,true>"),
+    "one_bitmap": ({"QDTA_BF_SHAPE": "2"}, "sssp_smq_kernel<512,true,2,true>"),
+    "one_cta_per_sm": ({"QDTA_BF_BPSM": "1"}, "sssp_smq_kernel<512,true,2,false>"),
+    "global_queues": ({"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "sssp_ilp_kernel<512>"),
+    "cell": ({"QDTA_SSSP": "cell"}, "sssp_cell_kernel"),
+}
+
+
+@pytest.mark.parametrize("variant", list(LARGE_VARIANTS))
 @pytest.mark.parametrize("direction", [Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT])
 def test_sssp_large_graph_variants(mid, variant, direction, monkeypatch):
     """Graphs above the shared-memory limit: every kernel variant, both
     directions, bit-exact against Dijkstra."""
     net, dem, _, og = mid
-    env = {"default": {}, "no_reorder": {"QDTA_NO_REORDER": "1"},
-           "global_queues": {"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "cell": {"QDTA_SSSP": "cell"}}[variant]
+    env, kernel = LARGE_VARIANTS[variant]
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     g = Q.Graph(net)
+    assert Q.qdta_sssp_kernel_name(g, direction) == kernel
     rng = np.random.default_rng(2)
     q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
     roots = rng.choice(net.n_nodes, 40, replace=False).astype(np.int32)
@@ -123,6 +139,67 @@ def test_sssp_large_graph_variants(mid, variant, direction, monkeypatch):
     p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
     np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
     np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
+def test_sssp_large_irregular_graph_with_ties():
+    """Above the shared-memory limit with degrees above 4 (so the compressed
+    adjacency, not the four-slot one) and many equal-cost ties: bit-exact
+    distances and smallest-link-id parents in both directions."""
+    net = synth.random_graph(12000, 36000, 11, max_q=3)
+    g, og = Q.Graph(net), oracle.OracleGraph(net)
+    rng = np.random.default_rng(12)
+    roots = rng.choice(net.n_nodes, 48, replace=False).astype(np.int32)
+    for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
+        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<512,false,2,false>"
+        p_o, d_o = oracle.sssp(og, net.fftime_q, roots, direction)
+        p_g, d_g = Q.qdta_sssp_batch(g, T(net.fftime_q, np.int32), T(roots, np.int32), direction, True)
+        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
+def test_sssp_graph_beyond_the_two_bitmap_limit():
+    """A 600 x 600 grid (360k nodes): two mark bitmaps per CTA no longer fit
+    twice in shared memory, so the one-bitmap 512-thread shape runs."""
+    net = synth.grid_network(600, 7, freeways=True)
+    g, og = Q.Graph(net), oracle.OracleGraph(net)
+    rng = np.random.default_rng(8)
+    q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
+    roots = rng.choice(net.n_nodes, 6, replace=False).astype(np.int32)
+    for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
+        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<512,true,2,true>"
+        p_o, d_o = oracle.sssp(og, q, roots, direction)
+        p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
+        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
+def test_autotune_keeps_the_fastest_shape_and_stays_bit_exact(mid):
+    net, dem, _, og = mid
+    g = Q.Graph(net)
+    rng = np.random.default_rng(4)
+    q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
+    roots = rng.choice(net.n_nodes, 64, replace=False).astype(np.int32)
+    rep = Q.qdta_autotune(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, reps=1)
+    kernels = {c["kernel"] for c in rep["candidates"]}
+    # launch shapes {512 x 2 CTAs, 256 x 4 CTAs} x four-slot / compressed adjacency x relaxation
+    # modes {1, 2}, plus the cell kernel
+    want = {f"sssp_smq_kernel<{t},{e},{r},{b}>" for t, b in (("512", "false"), ("256", "true"))
+            for e in ("true", "false") for r in (1, 2)} | {"sssp_cell_kernel"}
+    assert kernels == want
+    assert len(rep["candidates"]) == 9
+    assert {c["ctas_per_sm"] for c in rep["candidates"] if c["kernel"].startswith("sssp_smq_kernel<256")} == {4}
+    assert rep["best"]["ms"] == min(c["ms"] for c in rep["candidates"])
+    assert Q.qdta_sssp_kernel_name(g, Q.QDTA_TO_ROOT) == rep["best"]["kernel"]
+    p_o, d_o = oracle.sssp(og, q, roots)
+    p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, True)
+    np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+    np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
+def test_autotune_small_graph_has_one_shape(small):
+    inst, g, og = small
+    rep = Q.qdta_autotune(g, T(inst.net.fftime_q, np.int32), T(inst.zones, np.int32))
+    assert [c["kernel"] for c in rep["candidates"]] == ["sssp_kernel<true>"]
 
 
 def test_empty_batches(small):
@@ -255,6 +332,33 @@ def test_run_day_bit_exact(step, stop, it, schedule):
         for key in ("iterations", "aon_calls", "ls_passes", "converged"):
             assert st_g[i][key] == st_o[i][key], (i, key)
     assert resid[0].shape[0] == rn_o
+
+
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+def test_run_day_without_the_free_flow_tree_cache(schedule, monkeypatch):
+    """The day reuses the free-flow trees for every interval's initial AON;
+    recomputing them instead gives the same bits (and the oracle's)."""
+    day = _day_case(n_int=4)
+    days = list(day.demand)
+    og = oracle.OracleGraph(day.net)
+    f_o, st_o, nit_o, rn_o, _ = oracle.run_day(og, day.zones, days, 900.0,
+                                               oracle.make_params(Q.STEP["sweep8"], Q.STOP["paper_obj"], 60))
+    zones = T(day.zones, np.int32)
+    dd = [Q.DeviceOD(zones, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
+    out = []
+    for off in (False, True):
+        if off:
+            monkeypatch.setenv("QDTA_NO_FF_CACHE", "1")
+        g = Q.Graph(day.net)
+        Q.qdta_profile_enable(g, schedule == "plain")
+        f_g, st_g, _, _ = Q.qdta_run_day(g, dd, 900.0, Q.make_params("sweep8", "paper_obj", 60, schedule=schedule))
+        out.append((f_g.cpu().numpy(), [s["iterations"] for s in st_g],
+                    Q.qdta_profile_read(g)["sssp_launches"] if schedule == "plain" else None))
+        np.testing.assert_array_equal(out[-1][0], f_o)
+    assert out[0][1] == out[1][1] == [s["iterations"] for s in st_o]
+    if schedule == "plain":
+        # cached: one batch for all zones, then no SSSP for the initial AONs
+        assert out[0][2] < out[1][2]
 
 
 @pytest.mark.parametrize("schedule", ["plain", "graph"])

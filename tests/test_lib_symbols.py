@@ -46,3 +46,34 @@ def test_library_rejects_bad_graphs_without_touching_a_gpu():
     assert b"sorted" in lib.qdta_last_error()
     d.beta = 0
     assert lib.qdta_graph_create(ctypes.byref(d), 0, ctypes.byref(h)) == Q.QDTA_EINVAL
+
+
+def test_null_handles_are_rejected_without_touching_a_gpu():
+    from paper_2104_12911_gb300 import qdta as Q
+    lib = Q.lib()
+    rep = Q.TuneReport()
+    assert lib.qdta_autotune(None, None, None, 4, 0, 1, None, ctypes.byref(rep), None) == Q.QDTA_EINVAL
+    assert lib.qdta_sssp_kernel_name(None, 0) == b""
+    assert lib.qdta_last_error()
+
+
+def test_tune_report_layout_matches_the_header():
+    """The ctypes mirror of qdta_tune_report has the C struct's size (compiled here with gcc)."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_2104_12911_gb300 import qdta as Q
+    if not shutil.which("gcc"):
+        import pytest
+        pytest.skip("no gcc")
+    src = ('#include <stdio.h>\n#include "qdta.h"\nint main(void){printf("%zu %zu %zu\\n", '
+           'sizeof(qdta_tune_entry), sizeof(qdta_tune_report), sizeof(qdta_profile)); return 0;}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "sz.c")
+        exe = os.path.join(d, "sz")
+        with open(c, "w") as fh:
+            fh.write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(x) for x in out] == [ctypes.sizeof(Q.TuneEntry), ctypes.sizeof(Q.TuneReport),
+                                     ctypes.sizeof(Q.Profile)]
