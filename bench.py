@@ -31,6 +31,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Full-day QDTA s @rel-gap 1e-4, batched vs plain on 1 GB300; SSSP GTEPS, %HBM"
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per destination
+# root of the SSSP kernels, from one ncu capture each on the 500x500 metro
+# grid (one wave of resident roots); the roofline's `traffic` scales them by
+# the roots per launch.  Only kernels whose code is unchanged since their
+# capture are listed.
+SSSP_DRAM_BYTES_PER_ROOT = {}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -45,6 +52,8 @@ def parse():
                     help="a:b -- run only intervals a..b-1 of the day (profiling captures; not a bench line)")
     ap.add_argument("--max-iter", type=int, default=200)
     ap.add_argument("--stop", default="paper_obj", choices=["paper_obj", "rel_gap"])
+    ap.add_argument("--step", default="sweep8", choices=["sweep8", "paper_qn3", "exact", "msa"],
+                    help="FW step rule (the paper compares its line search with MSA)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default SSSP launch shape")
@@ -347,7 +356,7 @@ def batch32(args):
         links += net.n_links
     res = {}
     for sched in ("graph", "plain"):
-        p = Q.make_params("sweep8", args.stop, args.max_iter, 1e-4, schedule=sched)
+        p = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule=sched)
         for _ in range(args.warmup):
             Q.qdta_assign_batch(items, p)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -385,7 +394,7 @@ def adjoint_metro(args):
         Q.qdta_autotune(g, torch.from_numpy(net.fftime_q.astype(np.int32)).to(dev),
                         torch.from_numpy(inst.zones.astype(np.int32)).to(dev), reps=2)
     od = Q.DeviceOD.of(dem)
-    p = Q.make_params("sweep8", args.stop, args.max_iter, 1e-4, record_tape=True)
+    p = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, record_tape=True)
     rng = np.random.default_rng(3)
     S = torch.from_numpy(rng.choice(net.n_links, net.n_links // 20, replace=False)).to(dev)
     noise = torch.from_numpy(rng.lognormal(0.0, 0.3, S.shape[0])).to(dev)
@@ -476,8 +485,9 @@ def main():
 
     host = [upload(d, pin=True) for d in inst.demand]
     zones_host = torch.from_numpy(inst.zones.astype(np.int32)).pin_memory()
-    params_graph = Q.make_params("sweep8", args.stop, args.max_iter, 1e-4, schedule="graph")
-    params_plain = Q.make_params("sweep8", args.stop, args.max_iter, 1e-4, schedule="plain")
+    params_graph = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="graph")
+    params_plain = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="plain")
+    cfg["step_rule"] = args.step
     flow_out = torch.empty((len(inst.demand), g.n_links), dtype=torch.float64, device=dev)
     flows_host = torch.empty((len(inst.demand), g.n_links), dtype=torch.float64).pin_memory()
     h2d = sum(a.numel() * a.element_size() for h in host for a in h) + zones_host.numel() * 4
@@ -554,9 +564,12 @@ def main():
         b_alg = R_avg * 12.0 * V + 4.0 * (V + 1) + 8.0 * L
         achieved = b_alg / (avg_ms * 1e-3) / 1e9
         gteps = R_avg * L / (avg_ms * 1e-3) / 1e9
+        kname = Q.qdta_sssp_kernel_name(g, Q.QDTA_TO_ROOT)
+        per_root = SSSP_DRAM_BYTES_PER_ROOT.get(kname) if args.workload == "day_metro" else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": None,
-                    "kernel": Q.qdta_sssp_kernel_name(g, Q.QDTA_TO_ROOT),
+                    "frac": achieved / hbm, "traffic": per_root * R_avg if per_root else None,
+                    "traffic_unit": "bytes per launch",
+                    "kernel": kname,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                     "sssp_avg_ms": avg_ms, "roots_per_launch": R_avg, "gteps": gteps,
                     "sssp_share_of_plain_day": prof["sssp_ms"] / plain_ms if plain_ms else None}

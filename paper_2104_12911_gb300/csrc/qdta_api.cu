@@ -590,7 +590,11 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   g->d.tune_carve = 85;  // rounds to the 196 KB step: 2 CTAs' queues + a 60 KB L1
   if (const char *e = getenv("QDTA_SMQ_CARVEOUT")) g->d.tune_carve = atoi(e);
   if (const char *e = getenv("QDTA_BF_BPSM")) g->bf_bpsm = std::max(1, atoi(e));
-  g->d.tune_shape = sssp_smq_shape_fits(V, 0) ? 0 : sssp_smq_shape_fits(V, 2) ? 2 : 0;
+  // default shape: four 256-thread CTAs per SM where their marks fit
+  // (fastest on the metro grid), else two 512-thread CTAs
+  g->d.tune_shape = sssp_smq_shape_fits(V, 1) ? 1 : sssp_smq_shape_fits(V, 0) ? 0 : sssp_smq_shape_fits(V, 2) ? 2 : 0;
+  g->d.tune_out = 1;  // internal-order output pass where the graph is renumbered
+  if (const char *e = getenv("QDTA_SMQ_OUT")) g->d.tune_out = atoi(e) != 0;
   if (const char *e = getenv("QDTA_BF_SHAPE")) {
     const int sh = atoi(e);
     if (sssp_smq_shape_fits(V, sh)) g->d.tune_shape = sh;
@@ -677,6 +681,12 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
         gd.max_deg[dir] = md;
       }
       gd.node_int = C.node_int;
+      int *p_ne = nullptr;
+      if ((rc = upload(g, node_ext.data(), node_ext.size(), &p_ne))) {
+        qdta_graph_destroy(g);
+        return rc;
+      }
+      gd.node_ext = p_ne;
     }
     double mean_q = 0.0;
     for (int e = 0; e < L; ++e) mean_q += d->fftime_q[e];

@@ -226,6 +226,7 @@ struct GraphDev {
   // in cell order; per direction the adjacency of each internal node as link
   // ids and neighbours' internal ids
   const int *node_int;             // [V] external -> internal
+  const int *node_ext;             // [V] internal -> external
   const int *perm_off[2];          // [V + 1]
   const int *perm_link[2];         // [L]
   const int *perm_nb[2];           // [L]
@@ -237,6 +238,7 @@ struct GraphDev {
   // of the shared-memory-queue kernel (0: 512 threads, two mark bitmaps;
   // 1: 256 threads, one bitmap; 2: 512 threads, one bitmap)
   int tune_ell, tune_relax, tune_carve, tune_shape;
+  int tune_out;  // output pass of the queue kernel: 1 internal node order, 0 external order
 };
 
 // Cell partition for the shared-memory cell SSSP (graphs above the

@@ -106,16 +106,18 @@ def test_sssp_unreachable_nodes():
 
 
 LARGE_VARIANTS = {
-    "default": ({}, "sssp_smq_kernel<512,true,2,false>"),
-    "csr": ({"QDTA_NO_ELL": "1"}, "sssp_smq_kernel<512,false,2,false>"),
-    "no_reorder": ({"QDTA_NO_REORDER": "1"}, "sssp_smq_kernel<512,false,2,false>"),
-    "returning_atomic": ({"QDTA_BF_RELAX": "1"}, "sssp_smq_kernel<512,true,1,false>"),
-    "atomic_only": ({"QDTA_BF_RELAX": "0"}, "sssp_smq_kernel<512,true,0,false>"),
-    "four_ctas_one_bitmap": ({"QDTA_BF_SHAPE": "1"}, "sssp_smq_kernel<256,true,2,true>"),
-    "four_ctas_csr_returning": ({"QDTA_BF_SHAPE": "1", "QDTA_NO_ELL": "1", "QDTA_BF_RELAX": "1"},
-                                "sssp_smq_kernel<256,false,1,true>"),
-    "one_bitmap": ({"QDTA_BF_SHAPE": "2"}, "sssp_smq_kernel<512,true,2,true>"),
-    "one_cta_per_sm": ({"QDTA_BF_BPSM": "1"}, "sssp_smq_kernel<512,true,2,false>"),
+    "default": ({}, "sssp_smq_kernel<256,true,2,true>"),
+    "csr": ({"QDTA_NO_ELL": "1"}, "sssp_smq_kernel<256,false,2,true>"),
+    "no_reorder": ({"QDTA_NO_REORDER": "1"}, "sssp_smq_kernel<256,false,2,true>"),
+    "returning_atomic": ({"QDTA_BF_RELAX": "1"}, "sssp_smq_kernel<256,true,1,true>"),
+    "atomic_only": ({"QDTA_BF_RELAX": "0"}, "sssp_smq_kernel<256,true,0,true>"),
+    "two_bitmaps_512": ({"QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,true,2,false>"),
+    "two_bitmaps_512_csr_returning": ({"QDTA_BF_SHAPE": "0", "QDTA_NO_ELL": "1", "QDTA_BF_RELAX": "1"},
+                                      "sssp_smq_kernel<512,false,1,false>"),
+    "one_bitmap_512": ({"QDTA_BF_SHAPE": "2"}, "sssp_smq_kernel<512,true,2,true>"),
+    "one_cta_per_sm": ({"QDTA_BF_BPSM": "1"}, "sssp_smq_kernel<256,true,2,true>"),
+    "output_external_order": ({"QDTA_SMQ_OUT": "0"}, "sssp_smq_kernel<256,true,2,true>"),
+    "output_external_order_512": ({"QDTA_SMQ_OUT": "0", "QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,true,2,false>"),
     "global_queues": ({"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "sssp_ilp_kernel<512>"),
     "cell": ({"QDTA_SSSP": "cell"}, "sssp_cell_kernel"),
 }
@@ -150,7 +152,7 @@ def test_sssp_large_irregular_graph_with_ties():
     rng = np.random.default_rng(12)
     roots = rng.choice(net.n_nodes, 48, replace=False).astype(np.int32)
     for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
-        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<512,false,2,false>"
+        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<256,false,2,true>"
         p_o, d_o = oracle.sssp(og, net.fftime_q, roots, direction)
         p_g, d_g = Q.qdta_sssp_batch(g, T(net.fftime_q, np.int32), T(roots, np.int32), direction, True)
         np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
