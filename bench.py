@@ -36,7 +36,10 @@ METRIC = "Full-day QDTA s @rel-gap 1e-4, batched vs plain on 1 GB300; SSSP GTEPS
 # grid (one wave of resident roots); the roofline's `traffic` scales them by
 # the roots per launch.  Only kernels whose code is unchanged since their
 # capture are listed.
-SSSP_DRAM_BYTES_PER_ROOT = {}
+SSSP_DRAM_BYTES_PER_ROOT = {
+    # profiles/sssp_smq_kernel_rank_metro_R608.md: 2.830261 GB read + 5.333477 GB written, 608 roots
+    "sssp_smq_kernel<256,rank,2,true>": (2.830261e9 + 5.333477e9) / 608,
+}
 
 
 def parse():
@@ -46,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="day_metro",
-                    choices=["day_metro", "day_small", "sssp_metro", "batch32", "adjoint_metro"])
+                    choices=["day_metro", "day_small", "sssp_metro", "batch32", "adjoint_metro", "interval_metro"])
     ap.add_argument("--roots", type=int, default=2000, help="sssp_metro: destination roots per batch")
     ap.add_argument("--intervals", default=None,
                     help="a:b -- run only intervals a..b-1 of the day (profiling captures; not a bench line)")
@@ -427,6 +430,53 @@ def adjoint_metro(args):
                       "sssp_kernel": Q.qdta_sssp_kernel_name(g), "stop": args.stop}), flush=True)
 
 
+def interval_metro(args):
+    """One static interval on the metro grid: 250k gravity trips over 2000
+    zones (lognormal productions, exp(-d/10 km)), Frank-Wolfe with the chosen
+    step rule to the chosen stop rule (max_iter caps it), on the graph
+    schedule; seconds per interval, FW steps, SSSP GTEPS from a plain solve."""
+    import torch
+    from paper_2104_12911_gb300 import qdta as Q, synth
+    inst = synth.config_metro(seed=1)
+    net, dem = inst.net, inst.demand[0]
+    g = Q.Graph(net)
+    dev = torch.device("cuda", 0)
+    if not args.no_tune:
+        Q.qdta_autotune(g, torch.from_numpy(net.fftime_q.astype(np.int32)).to(dev),
+                        torch.from_numpy(inst.zones.astype(np.int32)).to(dev), reps=2)
+    od = Q.DeviceOD.of(dem)
+    # one plain solve with per-kernel events (GTEPS), then timed graph solves
+    Q.qdta_profile_enable(g, True)
+    _, st_p, _, _ = Q.qdta_assign_interval(g, od, 900.0, Q.make_params(args.step, args.stop, args.max_iter, 1e-4))
+    prof = Q.qdta_profile_read(g)
+    Q.qdta_profile_enable(g, False)
+    p = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="graph")
+    for _ in range(args.warmup):
+        Q.qdta_assign_interval(g, od, 900.0, p)
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        _, st, rc, _ = Q.qdta_assign_interval(g, od, 900.0, p)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    V, L = net.n_nodes, net.n_links
+    avg = prof["sssp_ms"] / max(prof["sssp_launches"], 1)
+    R_avg = prof["sssp_roots"] / max(prof["sssp_launches"], 1)
+    print(json.dumps({"metric": "static interval on the metro grid, seconds", "workload":
+                      f"500x500 grid, 2000 zones, 250k trips ({dem.src.shape[0]} OD items), one 15-min interval",
+                      "seconds": float(np.mean(times)) / 1e3, "fw_iterations": st["iterations"],
+                      "aon_calls": st["aon_calls"], "ls_sweeps": st["ls_passes"], "converged": st["converged"],
+                      "stop_measure": st["rel_gap"], "dual_gap": st["dual_gap"], "stop": args.stop,
+                      "step": args.step, "max_iter": args.max_iter, "plain_equals_graph":
+                      st_p["iterations"] == st["iterations"],
+                      "sssp_ms_per_batch": avg, "roots_per_batch": R_avg, "sssp_gteps": R_avg * L / (avg * 1e-3) / 1e9,
+                      "sssp_alg_gbs": (R_avg * 12.0 * V + 4.0 * (V + 1) + 8.0 * L) / (avg * 1e-3) / 1e9,
+                      "sssp_kernel": Q.qdta_sssp_kernel_name(g)}), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "sssp_metro":
@@ -437,6 +487,9 @@ def main():
         return
     if args.workload == "adjoint_metro":
         adjoint_metro(args)
+        return
+    if args.workload == "interval_metro":
+        interval_metro(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -297,9 +297,10 @@ int qdta_sssp_batch_noalloc(qdta_graph *g, const int32_t *cost_q, const int32_t 
  * Candidates: for graphs whose per-root state fits in shared memory, only the
  * shared-memory kernel; otherwise the global-memory Bellman-Ford with
  * {four-slot, compressed} adjacency (four-slot only when every degree <= 4) x
- * three ways to apply an offer (returning atomicMin; read, then returning
- * atomicMin; read, then non-returning atomicMin) x {2, 1} resident CTAs per
- * SM, plus the cell-partitioned kernel.
+ * launch shape {512 threads x 2 CTAs per SM, 256 threads x 4 CTAs per SM,
+ * whichever fit in shared memory} x three ways to apply an offer (read, then
+ * returning atomicMin; read, then non-returning atomicMin; the same with
+ * warp-aggregated queue appends), plus the cell-partitioned kernel.
  *
  * cost_q [L] int32 and roots [R] int32 are device arrays as for
  * qdta_sssp_batch; parent_scratch is a caller-owned device array of R*V int32

@@ -584,9 +584,10 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   g->sssp_kind = g->sssp_smem ? 0 : 2;
   // launch choices (environment overrides for experiments; qdta_autotune
   // replaces them by measurement)
-  g->d.tune_ell = getenv("QDTA_NO_ELL") ? 0 : 1;
+  g->d.tune_adj = getenv("QDTA_NO_ELL") ? 0 : 2;
+  if (const char *e = getenv("QDTA_SSSP_ADJ")) g->d.tune_adj = std::min(2, std::max(0, atoi(e)));
   g->d.tune_relax = 2;
-  if (const char *e = getenv("QDTA_BF_RELAX")) g->d.tune_relax = std::min(2, std::max(0, atoi(e)));
+  if (const char *e = getenv("QDTA_BF_RELAX")) g->d.tune_relax = std::min(3, std::max(0, atoi(e)));
   g->d.tune_carve = 85;  // rounds to the 196 KB step: 2 CTAs' queues + a 60 KB L1
   if (const char *e = getenv("QDTA_SMQ_CARVEOUT")) g->d.tune_carve = atoi(e);
   if (const char *e = getenv("QDTA_BF_BPSM")) g->bf_bpsm = std::max(1, atoi(e));
@@ -687,6 +688,37 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
         return rc;
       }
       gd.node_ext = p_ne;
+      // rank-keyed four-slot adjacency: ranks of links among the candidate
+      // parent links of the node they relax, and the link of each rank
+      if (gd.max_deg[0] <= 4 && gd.max_deg[1] <= 4) {
+        std::vector<int> rk_out(L), rk_in(L);
+        for (int v = 0; v < V; ++v) {
+          for (int k = out_off[v]; k < out_off[v + 1]; ++k) rk_out[out_link[k]] = k - out_off[v];
+          for (int k = in_off[v]; k < in_off[v + 1]; ++k) rk_in[in_link[k]] = k - in_off[v];
+        }
+        std::vector<int> rl0(4 * (size_t)V, -1), rl1(4 * (size_t)V, -1);
+        bool sym = true;
+        for (int u = 0; u < V; ++u) {
+          const int v = node_ext[u];
+          const int dout = out_off[v + 1] - out_off[v], din = in_off[v + 1] - in_off[v];
+          for (int k = 0; k < dout; ++k) rl0[4 * (size_t)u + k] = out_link[out_off[v] + k];
+          for (int k = 0; k < din; ++k) rl1[4 * (size_t)u + k] = in_link[in_off[v] + k];
+          // k-th out-neighbour == k-th in-neighbour (both lists ascending by link id)
+          if (dout != din) sym = false;
+          for (int k = 0; sym && k < dout; ++k)
+            if (d->head[out_link[out_off[v] + k]] != d->tail[in_link[in_off[v] + k]]) sym = false;
+        }
+        int *r0, *r1, *l0, *l1;
+        // TO_ROOT relaxes tails over their out-links, FROM_ROOT heads over their in-links
+        if ((rc = upload(g, rk_out.data(), rk_out.size(), &r0)) || (rc = upload(g, rk_in.data(), rk_in.size(), &r1)) ||
+            (rc = upload(g, rl0.data(), rl0.size(), &l0)) || (rc = upload(g, rl1.data(), rl1.size(), &l1))) {
+          qdta_graph_destroy(g);
+          return rc;
+        }
+        gd.rank_tgt[0] = r0; gd.rank_tgt[1] = r1;
+        gd.rank_link[0] = l0; gd.rank_link[1] = l1;
+        gd.skip_parent = sym && !getenv("QDTA_NO_PARENT_SKIP") ? 1 : 0;
+      }
     }
     double mean_q = 0.0;
     for (int e = 0; e < L; ++e) mean_q += d->fftime_q[e];
@@ -803,7 +835,9 @@ static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots
                      parent, slot_dev, stride, dist, g->status, s, skip_dev,
                      g->prof_on ? g->prof_roots : nullptr);
   } else {
-    if (g->sssp_kind == 2 && sssp_uses_ell(g->d, direction)) launch_pack_ell(g->d, direction, q, w.adj, s, skip_dev);
+    const int adjl = g->sssp_kind == 2 ? sssp_adj(g->d, direction) : 0;
+    if (adjl == 2) launch_pack_ell8(g->d, direction, q, reinterpret_cast<int2 *>(w.adj), s, skip_dev);
+    else if (adjl == 1) launch_pack_ell(g->d, direction, q, w.adj, s, skip_dev);
     else if (g->sssp_kind == 2 && sssp_uses_perm(g->d)) launch_pack_perm_adj(g->d, direction, q, w.adj, s, skip_dev);
     else launch_pack_adj(g->d, direction, q, w.adj, s, skip_dev);
     prof_begin(g, s, &pe, 0, R_host);
@@ -834,16 +868,16 @@ extern "C" int qdta_sssp_batch(qdta_graph *g, const int32_t *cost_q, const int32
 // ---------------------------------------------------------------------------
 namespace {
 struct TuneCfg {
-  int kind, ell, relax, bpsm, shape;
+  int kind, adj, relax, bpsm, shape;
 };
 
 TuneCfg tune_get(const qdta_graph *g) {
-  return {g->sssp_kind, g->d.tune_ell, g->d.tune_relax, g->bf_bpsm, g->d.tune_shape};
+  return {g->sssp_kind, g->d.tune_adj, g->d.tune_relax, g->bf_bpsm, g->d.tune_shape};
 }
 
 void tune_set(qdta_graph *g, const TuneCfg &c) {
   g->sssp_kind = c.kind;
-  g->d.tune_ell = c.ell;
+  g->d.tune_adj = c.adj;
   g->d.tune_relax = c.relax;
   g->bf_bpsm = c.bpsm;
   g->d.tune_shape = c.shape;
@@ -867,16 +901,17 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
     // global-memory Bellman-Ford: launch shape x adjacency layout x relaxation
     // mode (each shape with as many CTAs per SM as it was designed for)
     const bool ell_ok = g->d.max_deg[direction] <= 4 && g->d.node_int != nullptr;
+    const bool rank_ok = ell_ok && g->d.rank_tgt[direction] != nullptr;
     bool any_smq = false;
     for (int shape = 0; shape < 3; ++shape) {
       if (!sssp_smq_shape_fits(g->d.V, shape) || getenv("QDTA_BF_NOSMQ")) continue;
       if (shape == 2 && sssp_smq_shape_fits(g->d.V, 0)) continue;  // same block as shape 0, fewer marks
       any_smq = true;
-      for (int ell = ell_ok ? 1 : 0; ell >= 0; --ell)
-        for (int relax = 2; relax >= 1; --relax) cand.push_back({2, ell, relax, 0, shape});
+      for (int adj = rank_ok ? 2 : ell_ok ? 1 : 0; adj >= 0; --adj)
+        for (int relax = 3; relax >= 2; --relax) cand.push_back({2, adj, relax, 0, shape});
     }
-    if (!any_smq) cand.push_back({2, start.ell, start.relax, start.bpsm, start.shape});  // global queues
-    if (g->has_cells) cand.push_back({1, start.ell, start.relax, start.bpsm, start.shape});  // cell-partitioned
+    if (!any_smq) cand.push_back({2, start.adj, start.relax, start.bpsm, start.shape});  // global queues
+    if (g->has_cells) cand.push_back({1, start.adj, start.relax, start.bpsm, start.shape});  // cell-partitioned
   }
   if ((int)cand.size() > QDTA_TUNE_MAX) cand.resize(QDTA_TUNE_MAX);
   qdta_tune_report rep{};

@@ -231,13 +231,20 @@ struct GraphDev {
   const int *perm_link[2];         // [L]
   const int *perm_nb[2];           // [L]
   int max_deg[2];                  // largest degree per direction
+  // rank-keyed four-slot adjacency (degree <= 4): per link, its rank among the
+  // candidate parent links of the node it relaxes (out-links of the tail for
+  // TO_ROOT, in-links of the head for FROM_ROOT, by link id); per internal
+  // node, the link of each rank (-1 past the degree)
+  const int *rank_tgt[2];          // [L]
+  const int *rank_link[2];         // [4 V]
+  int skip_parent;                 // every link has its reverse, lists share one order
   // launch choices of the global-memory SSSP (set at create, changed by
   // qdta_autotune): four-slot adjacency when max_deg <= 4, relaxation mode
   // (0 returning atomic, 1 read then returning atomic, 2 read then
   // non-returning atomic), shared-memory carveout percentage, launch shape
   // of the shared-memory-queue kernel (0: 512 threads, two mark bitmaps;
   // 1: 256 threads, one bitmap; 2: 512 threads, one bitmap)
-  int tune_ell, tune_relax, tune_carve, tune_shape;
+  int tune_adj, tune_relax, tune_carve, tune_shape;  // tune_adj: 0 compressed, 1 four-slot, 2 rank-keyed
   int tune_out;  // output pass of the queue kernel: 1 internal node order, 0 external order
 };
 
@@ -318,6 +325,9 @@ bool sssp_smq_shape_fits(int V, int shape);
 int sssp_smq_ctas_per_sm(const GraphDev &g, int direction);
 bool sssp_uses_perm(const GraphDev &g);  // global-memory launch reads the locality-ordered adjacency
 bool sssp_uses_ell(const GraphDev &g, int direction);
+int sssp_adj(const GraphDev &g, int direction);  // adjacency layout the queue kernel uses (0, 1, 2)
+void launch_pack_ell8(const GraphDev &g, int direction, const int *q, int2 *ell, cudaStream_t s,
+                      const int *skip_dev = nullptr);
 const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem);  // ... in the four-slot layout
 void launch_pack_ell(const GraphDev &g, int direction, const int *q, int4 *ell, cudaStream_t s,
                      const int *skip_dev = nullptr);

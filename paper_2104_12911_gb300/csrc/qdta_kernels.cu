@@ -90,6 +90,32 @@ void launch_pack_ell(const GraphDev &g, int direction, const int *q, int4 *ell, 
                                                        g.perm_nb[direction], q, ell, skip_dev);
 }
 
+// eight-byte four-slot entries: ((neighbour << 3) | rank, link time), with
+// (-1, 0) for an absent slot
+__global__ void pack_ell8_kernel(int V, const int *__restrict__ perm_off, const int *__restrict__ perm_link,
+                                 const int *__restrict__ perm_nb, const int *__restrict__ rank_tgt,
+                                 const int *__restrict__ q, int2 *__restrict__ ell, const int *skip_dev) {
+  if (skip_dev && *skip_dev) return;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 4 * V; t += gridDim.x * blockDim.x) {
+    const int u = t >> 2, k = t & 3;
+    const int a = perm_off[u] + k;
+    if (a < perm_off[u + 1]) {
+      const int e = perm_link[a];
+      ell[t] = make_int2((perm_nb[a] << 3) | rank_tgt[e], q[e]);
+    } else {
+      ell[t] = make_int2(-1, 0);
+    }
+  }
+}
+
+void launch_pack_ell8(const GraphDev &g, int direction, const int *q, int2 *ell, cudaStream_t s,
+                      const int *skip_dev) {
+  COUNT_LAUNCH();
+  pack_ell8_kernel<<<cdiv(4ll * g.V, 256), 256, 0, s>>>(g.V, g.perm_off[direction], g.perm_link[direction],
+                                                        g.perm_nb[direction], g.rank_tgt[direction], q, ell,
+                                                        skip_dev);
+}
+
 void launch_pack_perm_adj(const GraphDev &g, int direction, const int *q, int4 *adj, cudaStream_t s,
                           const int *skip_dev) {
   if (g.L == 0) return;
@@ -819,14 +845,17 @@ static const SmqShape kSmqShape[3] = {{512, 2, 3072, 2}, {256, 1, 2048, 4}, {512
 //      a key at least as large as the value it replaced (keys only decrease),
 //      so its thread queues y; later reads see the update because the round
 //      ends in a CTA barrier and every state access goes through L2.
-template <int THREADS, bool ELL, int RELAX, bool ONEBM>
+//   3  as 2, with warp-aggregated queue appends (one shared-memory atomicAdd
+//      per warp and offsets from a ballot instead of one per queued node)
+template <int THREADS, int ADJ, int RELAX, bool ONEBM>
 __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64))
-sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restrict__ adj,
+sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__restrict__ adj,
                 const int *__restrict__ roots, int R_host, const int *R_dev,
                 unsigned long long *g_state, int *g_queue, int *parent,
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                 const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
-                int max_rounds, int qcap, const int *__restrict__ node_ext, int out_mode) {
+                int max_rounds, int qcap, const int *__restrict__ node_ext, int out_mode,
+                const int *__restrict__ rank_link, int skip_parent) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
   if (skip_dev && *skip_dev) return;
@@ -834,6 +863,13 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
   if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
   const int W = (V + 31) >> 5;
   constexpr int NBM = ONEBM ? 1 : 2;
+  constexpr bool AGG = RELAX == 3;
+  constexpr int RM = AGG ? 2 : RELAX;
+  constexpr bool ELL = ADJ >= 1;
+  // ADJ 2: the key's low field is the rank (0..3) of the link among the
+  // keyed node's candidate parent links, ordered by link id (so the smallest
+  // rank is the smallest link id); rank_link maps it back to the link
+  const int LB = ADJ == 2 ? 3 : LB_link;
   unsigned *bm0 = smq_smem, *bm1 = smq_smem + (NBM - 1) * W;
   int *sq0 = reinterpret_cast<int *>(smq_smem + NBM * W), *sq1 = sq0 + qcap;
   const size_t b = blockIdx.x;
@@ -872,6 +908,7 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
       for (int base = 0; base < ncur; base += NQ * SSSP2_NPT) {
         int w[SSSP2_NPT], kb[SSSP2_NPT], ke[SSSP2_NPT];
         unsigned long long dw[SSSP2_NPT];
+        unsigned skipj = 0;
 #pragma unroll
         for (int j = 0; j < SSSP2_NPT; ++j) {
           const int i = base + j * NQ + quad;
@@ -889,7 +926,13 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
               kb[j] = __ldg(&off[w[j]]) + lane4;
               ke[j] = __ldg(&off[w[j] + 1]);
             }
-            dw[j] = __ldcg(&state[w[j]]) >> LB;
+            const unsigned long long kw = __ldcg(&state[w[j]]);
+            dw[j] = kw >> LB;
+            // ADJ 2 on graphs where every link has its reverse and both lists
+            // of a node share one order: slot lane4 leads back to w's parent
+            // when it equals the parent's rank; that offer (dist(w) plus a
+            // positive time) cannot beat the parent's key, so it is dropped
+            if (ADJ == 2 && skip_parent && (unsigned long long)lane4 == (kw & NOLINK)) skipj |= 1u << j;
           }
         }
         bool more = true;
@@ -897,16 +940,25 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
           int4 ent[SSSP2_NPT];
           unsigned long long tk[SSSP2_NPT];
 #pragma unroll
-          for (int j = 0; j < SSSP2_NPT; ++j)
-            if (kb[j] < ke[j]) ent[j] = __ldg(&adj[kb[j]]);
-#pragma unroll
           for (int j = 0; j < SSSP2_NPT; ++j) {
-            if (ELL && kb[j] < ke[j] && ent[j].x < 0) ke[j] = kb[j];  // absent slot
-            tk[j] = ~0ull;
-            if (RELAX > 0 && kb[j] < ke[j]) tk[j] = __ldcg(&state[ent[j].y]);
+            if (kb[j] < ke[j]) {
+              if (ADJ == 2) {  // 8-byte entry: ((neighbour << 3) | rank, link time), -1 when absent
+                const int2 e2 = __ldg(&reinterpret_cast<const int2 *>(adj)[kb[j]]);
+                ent[j] = make_int4(e2.x < 0 ? -1 : (e2.x & 7), e2.x >> 3, e2.y, 0);
+              } else {
+                ent[j] = __ldg(&adj[kb[j]]);
+              }
+            }
           }
 #pragma unroll
           for (int j = 0; j < SSSP2_NPT; ++j) {
+            if (ELL && kb[j] < ke[j] && (ent[j].x < 0 || ((skipj >> j) & 1u))) ke[j] = kb[j];  // absent / skipped
+            tk[j] = ~0ull;
+            if (RM > 0 && kb[j] < ke[j]) tk[j] = __ldcg(&state[ent[j].y]);
+          }
+#pragma unroll
+          for (int j = 0; j < SSSP2_NPT; ++j) {
+            int pushy = -1;
             if (kb[j] < ke[j]) {
               ++my_relax;
               const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
@@ -917,17 +969,38 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
                 if (key < tk[j]) {
                   const int y = ent[j].y;
                   unsigned long long seen;
-                  if (RELAX == 2) {
+                  if (RM == 2) {
                     atomicMin(&state[y], key);  // result unused: no wait on the reply
                     seen = tk[j];
                   } else {
                     seen = atomicMin(&state[y], key);
                   }
                   if ((seen >> LB) > cand && !((atomicOr(&bnxt[y >> 5], 1u << (y & 31)) >> (y & 31)) & 1u)) {
-                    const int pos = atomicAdd(&s_cnt[c], 1);
-                    if (pos < qcap) snxt[pos] = y;
-                    else gnxt[pos - qcap] = y;
+                    if (AGG) {
+                      pushy = y;
+                    } else {
+                      const int pos = atomicAdd(&s_cnt[c], 1);
+                      if (pos < qcap) snxt[pos] = y;
+                      else gnxt[pos - qcap] = y;
+                    }
                   }
+                }
+              }
+            }
+            if (AGG) {
+              // the lanes executing here append together: one atomicAdd, ballot offsets
+              const unsigned act = __activemask();
+              const unsigned m = __ballot_sync(act, pushy >= 0);
+              if (m) {
+                const int lane = threadIdx.x & 31;
+                const int leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&s_cnt[c], __popc(m));
+                base = __shfl_sync(act, base, leader);
+                if (pushy >= 0) {
+                  const int pos = base + __popc(m & ((1u << lane) - 1u));
+                  if (pos < qcap) snxt[pos] = pushy;
+                  else gnxt[pos - qcap] = pushy;
                 }
               }
             }
@@ -980,18 +1053,20 @@ sssp_smq_kernel(int V, int LB, const int *__restrict__ off, const int4 *__restri
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (v[k] < 0) continue;
-          state[u0 + k * THREADS] = ~0ull;
+          const int u = u0 + k * THREADS;
+          state[u] = ~0ull;
           const unsigned long long lk = key[k] & NOLINK;
-          prow[v[k]] = lk == NOLINK ? -1 : (int)lk;
+          prow[v[k]] = lk == NOLINK ? -1 : ADJ == 2 ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
           if (drow) drow[v[k]] = key[k] == ~0ull ? LLONG_MAX : (long long)(key[k] >> LB);
         }
       }
     } else {
       // external order, then a separate coalesced reset
       for (int v = threadIdx.x; v < V; v += blockDim.x) {
-        const unsigned long long key = __ldcg(&state[node_int ? node_int[v] : v]);
+        const int u = node_int ? node_int[v] : v;
+        const unsigned long long key = __ldcg(&state[u]);
         const unsigned long long lk = key & NOLINK;
-        prow[v] = lk == NOLINK ? -1 : (int)lk;
+        prow[v] = lk == NOLINK ? -1 : ADJ == 2 ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
         if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
       }
       __syncthreads();
@@ -1023,24 +1098,31 @@ int sssp_smq_max_ctas(const GraphDev &g) { return kSmqShape[g.tune_shape].ctas; 
 bool sssp_uses_perm(const GraphDev &g) { return g.node_int != nullptr && sssp_uses_smq(g); }
 // fixed four-slot adjacency: locality order present, every degree <= 4
 bool sssp_uses_ell(const GraphDev &g, int direction) {
-  return sssp_uses_perm(g) && g.max_deg[direction] <= 4 && g.tune_ell;
+  return sssp_uses_perm(g) && g.max_deg[direction] <= 4 && g.tune_adj >= 1;
+}
+int sssp_adj(const GraphDev &g, int direction) {
+  if (!sssp_uses_ell(g, direction)) return 0;
+  return g.tune_adj >= 2 && g.rank_tgt[direction] && g.rank_link[direction] && g.V < (1 << 28) ? 2 : 1;
 }
 
 // name of the kernel launch_sssp runs for this graph, direction and storage
 const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
   if (use_smem) return "sssp_kernel<true>";
   if (sssp_uses_smq(g)) {
+    static const char *adj_name[3] = {"csr", "ell", "rank"};
     static const std::vector<std::string> names = [] {
       std::vector<std::string> v;
       for (int sh = 0; sh < 3; ++sh)
-        for (int e = 0; e < 2; ++e)
-          for (int r = 0; r < 3; ++r)
-            v.push_back("sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + (e ? "true" : "false") +
-                        "," + std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") + ">");
+        for (int e = 0; e < 3; ++e)
+          for (int r = 0; r < 4; ++r)
+            v.push_back("sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
+                        std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") + ">");
       return v;
     }();
-    const int r = g.tune_relax < 0 ? 0 : g.tune_relax > 2 ? 2 : g.tune_relax;
-    return names[(g.tune_shape * 2 + (sssp_uses_ell(g, direction) ? 1 : 0)) * 3 + r].c_str();
+    const int adj = sssp_adj(g, direction);
+    int r = g.tune_relax < 0 ? 0 : g.tune_relax > 3 ? 3 : g.tune_relax;
+    if (adj == 2 && r < 2) r = 2;
+    return names[(g.tune_shape * 3 + adj) * 4 + r].c_str();
   }
   switch (sssp_group_size()) {
     case 2: return "sssp_group_kernel<512,2>";
@@ -1069,26 +1151,29 @@ int sssp_blocks_per_sm(bool use_smem, int V) {
 
 using SmqKernel = void (*)(int, int, const int *, const int4 *, const int *, int, const int *, unsigned long long *,
                           int *, int *, const int *, long long, long long *, unsigned *, const int *,
-                          unsigned long long *, const int *, int, int, const int *, int);
+                          unsigned long long *, const int *, int, int, const int *, int, const int *, int);
 
 template <int THREADS, bool ONEBM>
-static SmqKernel smq_kernel_relax(bool ell, int relax) {
-  if (ell) return relax == 2 ? sssp_smq_kernel<THREADS, true, 2, ONEBM>
-                : relax == 1 ? sssp_smq_kernel<THREADS, true, 1, ONEBM> : sssp_smq_kernel<THREADS, true, 0, ONEBM>;
-  return relax == 2 ? sssp_smq_kernel<THREADS, false, 2, ONEBM>
-       : relax == 1 ? sssp_smq_kernel<THREADS, false, 1, ONEBM> : sssp_smq_kernel<THREADS, false, 0, ONEBM>;
+static SmqKernel smq_kernel_relax(int adj, int relax) {
+  if (adj == 2) return relax == 3 ? sssp_smq_kernel<THREADS, 2, 3, ONEBM> : sssp_smq_kernel<THREADS, 2, 2, ONEBM>;
+  if (adj == 1) return relax == 3 ? sssp_smq_kernel<THREADS, 1, 3, ONEBM>
+                : relax == 2 ? sssp_smq_kernel<THREADS, 1, 2, ONEBM>
+                : relax == 1 ? sssp_smq_kernel<THREADS, 1, 1, ONEBM> : sssp_smq_kernel<THREADS, 1, 0, ONEBM>;
+  return relax == 3 ? sssp_smq_kernel<THREADS, 0, 3, ONEBM>
+       : relax == 2 ? sssp_smq_kernel<THREADS, 0, 2, ONEBM>
+       : relax == 1 ? sssp_smq_kernel<THREADS, 0, 1, ONEBM> : sssp_smq_kernel<THREADS, 0, 0, ONEBM>;
 }
 
-static SmqKernel smq_kernel_for(int shape, bool ell, int relax) {
-  if (shape == 1) return smq_kernel_relax<256, true>(ell, relax);
-  if (shape == 2) return smq_kernel_relax<512, true>(ell, relax);
-  return smq_kernel_relax<512, false>(ell, relax);
+static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
+  if (shape == 1) return smq_kernel_relax<256, true>(adj, relax);
+  if (shape == 2) return smq_kernel_relax<512, true>(adj, relax);
+  return smq_kernel_relax<512, false>(adj, relax);
 }
 
 // resident CTAs per SM of the selected shared-memory-queue kernel (occupancy
 // under the pinned carveout, at most the shape's design count)
 int sssp_smq_ctas_per_sm(const GraphDev &g, int direction) {
-  const SmqKernel kern = smq_kernel_for(g.tune_shape, sssp_uses_ell(g, direction), g.tune_relax);
+  const SmqKernel kern = smq_kernel_for(g.tune_shape, sssp_adj(g, direction), g.tune_relax);
   const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
@@ -1127,7 +1212,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
               : bf_threads == 256 ? sssp_ilp_kernel<256> : sssp_ilp_kernel<128>;
     const int G = sssp_group_size();
     if (sssp_uses_smq(g)) {
-      const bool ell = sssp_uses_ell(g, direction);
+      const int adjl = sssp_adj(g, direction);
       // Two 86.5 KB CTAs per SM need a ~196 KB shared-memory carveout; the
       // rest of the unified 256 KB stays L1 (the adjacency gathers want it:
       // 55 ms per batch at 196 KB vs 84 ms at the 228 KB maximum).  Pinning
@@ -1135,7 +1220,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       // same configuration.  The percentage is rounded up to a supported
       // size: 85 % of 228 KB asks for 194 KB and gets the 196 KB step (86 %
       // would round up to 228 KB).  QDTA_SMQ_CARVEOUT overrides, in percent.
-      const SmqKernel kern = smq_kernel_for(g.tune_shape, ell, g.tune_relax);
+      const SmqKernel kern = smq_kernel_for(g.tune_shape, adjl, g.tune_relax);
       const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
       const int threads = kSmqShape[g.tune_shape].threads;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
@@ -1144,7 +1229,8 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       kern<<<grid, threads, smq, s>>>(g.V, g.LB, perm ? g.perm_off[direction] : off, adj, roots, R_host, R_dev,
                                       w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip_dev,
                                       roots_counter, perm ? g.node_int : nullptr, round_limit(g.V),
-                                      kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out);
+                                      kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
+                                      g.rank_link[direction], g.skip_parent);
       return;
     }
     if (G == 2) kern = sssp_group_kernel<512, 2>;

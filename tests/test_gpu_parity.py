@@ -106,18 +106,24 @@ def test_sssp_unreachable_nodes():
 
 
 LARGE_VARIANTS = {
-    "default": ({}, "sssp_smq_kernel<256,true,2,true>"),
-    "csr": ({"QDTA_NO_ELL": "1"}, "sssp_smq_kernel<256,false,2,true>"),
-    "no_reorder": ({"QDTA_NO_REORDER": "1"}, "sssp_smq_kernel<256,false,2,true>"),
-    "returning_atomic": ({"QDTA_BF_RELAX": "1"}, "sssp_smq_kernel<256,true,1,true>"),
-    "atomic_only": ({"QDTA_BF_RELAX": "0"}, "sssp_smq_kernel<256,true,0,true>"),
-    "two_bitmaps_512": ({"QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,true,2,false>"),
+    "default": ({}, "sssp_smq_kernel<256,rank,2,true>"),
+    "rank_without_parent_skip": ({"QDTA_NO_PARENT_SKIP": "1"}, "sssp_smq_kernel<256,rank,2,true>"),
+    "ell16": ({"QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
+    "csr": ({"QDTA_NO_ELL": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
+    "no_reorder": ({"QDTA_NO_REORDER": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
+    "returning_atomic": ({"QDTA_BF_RELAX": "1", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,1,true>"),
+    "atomic_only": ({"QDTA_BF_RELAX": "0", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,0,true>"),
+    "two_bitmaps_512": ({"QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,rank,2,false>"),
     "two_bitmaps_512_csr_returning": ({"QDTA_BF_SHAPE": "0", "QDTA_NO_ELL": "1", "QDTA_BF_RELAX": "1"},
-                                      "sssp_smq_kernel<512,false,1,false>"),
-    "one_bitmap_512": ({"QDTA_BF_SHAPE": "2"}, "sssp_smq_kernel<512,true,2,true>"),
-    "one_cta_per_sm": ({"QDTA_BF_BPSM": "1"}, "sssp_smq_kernel<256,true,2,true>"),
-    "output_external_order": ({"QDTA_SMQ_OUT": "0"}, "sssp_smq_kernel<256,true,2,true>"),
-    "output_external_order_512": ({"QDTA_SMQ_OUT": "0", "QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,true,2,false>"),
+                                      "sssp_smq_kernel<512,csr,1,false>"),
+    "one_bitmap_512": ({"QDTA_BF_SHAPE": "2"}, "sssp_smq_kernel<512,rank,2,true>"),
+    "one_cta_per_sm": ({"QDTA_BF_BPSM": "1"}, "sssp_smq_kernel<256,rank,2,true>"),
+    "aggregated_appends": ({"QDTA_BF_RELAX": "3"}, "sssp_smq_kernel<256,rank,3,true>"),
+    "aggregated_appends_csr_512": ({"QDTA_BF_RELAX": "3", "QDTA_NO_ELL": "1", "QDTA_BF_SHAPE": "0"},
+                                   "sssp_smq_kernel<512,csr,3,false>"),
+    "output_external_order": ({"QDTA_SMQ_OUT": "0"}, "sssp_smq_kernel<256,rank,2,true>"),
+    "output_external_order_ell_512": ({"QDTA_SMQ_OUT": "0", "QDTA_BF_SHAPE": "0", "QDTA_SSSP_ADJ": "1"},
+                                      "sssp_smq_kernel<512,ell,2,false>"),
     "global_queues": ({"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "sssp_ilp_kernel<512>"),
     "cell": ({"QDTA_SSSP": "cell"}, "sssp_cell_kernel"),
 }
@@ -143,6 +149,27 @@ def test_sssp_large_graph_variants(mid, variant, direction, monkeypatch):
     np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
+def test_sssp_rank_keys_on_a_graph_with_one_way_links():
+    """Degree <= 4 but 3 % of links lose their reverse: the rank-keyed
+    adjacency runs without the parent-slot skip; bit-exact both ways."""
+    base = synth.grid_network(110, 9, freeways=True)
+    rng = np.random.default_rng(9)
+    keep = rng.random(base.n_links) >= 0.03
+    net = synth.Network(n_nodes=base.n_nodes, tail=base.tail[keep].copy(), head=base.head[keep].copy(),
+                        fftime_q=base.fftime_q[keep].copy(), capacity=base.capacity[keep].copy(),
+                        length_m=base.length_m[keep].copy(), link_class=base.link_class[keep].copy(),
+                        x=base.x, y=base.y)
+    g, og = Q.Graph(net), oracle.OracleGraph(net)
+    q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
+    roots = rng.choice(net.n_nodes, 40, replace=False).astype(np.int32)
+    for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
+        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<256,rank,2,true>"
+        p_o, d_o = oracle.sssp(og, q, roots, direction)
+        p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
+        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
 def test_sssp_large_irregular_graph_with_ties():
     """Above the shared-memory limit with degrees above 4 (so the compressed
     adjacency, not the four-slot one) and many equal-cost ties: bit-exact
@@ -152,7 +179,7 @@ def test_sssp_large_irregular_graph_with_ties():
     rng = np.random.default_rng(12)
     roots = rng.choice(net.n_nodes, 48, replace=False).astype(np.int32)
     for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
-        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<256,false,2,true>"
+        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<256,csr,2,true>"
         p_o, d_o = oracle.sssp(og, net.fftime_q, roots, direction)
         p_g, d_g = Q.qdta_sssp_batch(g, T(net.fftime_q, np.int32), T(roots, np.int32), direction, True)
         np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
@@ -168,7 +195,7 @@ def test_sssp_graph_beyond_the_two_bitmap_limit():
     q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
     roots = rng.choice(net.n_nodes, 6, replace=False).astype(np.int32)
     for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
-        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<512,true,2,true>"
+        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<512,rank,2,true>"
         p_o, d_o = oracle.sssp(og, q, roots, direction)
         p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
         np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
@@ -183,12 +210,12 @@ def test_autotune_keeps_the_fastest_shape_and_stays_bit_exact(mid):
     roots = rng.choice(net.n_nodes, 64, replace=False).astype(np.int32)
     rep = Q.qdta_autotune(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, reps=1)
     kernels = {c["kernel"] for c in rep["candidates"]}
-    # launch shapes {512 x 2 CTAs, 256 x 4 CTAs} x four-slot / compressed adjacency x relaxation
-    # modes {1, 2}, plus the cell kernel
+    # launch shapes {512 x 2 CTAs, 256 x 4 CTAs} x adjacency {rank-keyed, four-slot, compressed} x
+    # relaxation modes {2, 3}, plus the cell kernel
     want = {f"sssp_smq_kernel<{t},{e},{r},{b}>" for t, b in (("512", "false"), ("256", "true"))
-            for e in ("true", "false") for r in (1, 2)} | {"sssp_cell_kernel"}
+            for e in ("rank", "ell", "csr") for r in (2, 3)} | {"sssp_cell_kernel"}
     assert kernels == want
-    assert len(rep["candidates"]) == 9
+    assert len(rep["candidates"]) == 13
     assert {c["ctas_per_sm"] for c in rep["candidates"] if c["kernel"].startswith("sssp_smq_kernel<256")} == {4}
     assert rep["best"]["ms"] == min(c["ms"] for c in rep["candidates"])
     assert Q.qdta_sssp_kernel_name(g, Q.QDTA_TO_ROOT) == rep["best"]["kernel"]
