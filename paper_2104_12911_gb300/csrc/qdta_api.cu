@@ -585,7 +585,7 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   // launch choices (environment overrides for experiments; qdta_autotune
   // replaces them by measurement)
   g->d.tune_adj = getenv("QDTA_NO_ELL") ? 0 : 2;
-  if (const char *e = getenv("QDTA_SSSP_ADJ")) g->d.tune_adj = std::min(2, std::max(0, atoi(e)));
+  if (const char *e = getenv("QDTA_SSSP_ADJ")) g->d.tune_adj = std::min(3, std::max(0, atoi(e)));
   g->d.tune_relax = 2;
   if (const char *e = getenv("QDTA_BF_RELAX")) g->d.tune_relax = std::min(3, std::max(0, atoi(e)));
   g->d.tune_carve = 85;  // rounds to the 196 KB step: 2 CTAs' queues + a 60 KB L1
@@ -799,6 +799,7 @@ static int sssp_work(qdta_graph *g, int grid, SsspWork *w) {
   const size_t V = g->d.V;
   w->slots = grid;
   RC(ws_get(g, "sssp.adj", std::max((size_t)g->d.L, (size_t)4 * V), &w->adj));
+  RC(ws_get(g, "sssp.fb", 4, &w->fb_skip));
   if (g->sssp_kind == 1) {
     RC(ws_get(g, "sssp.lrev", (size_t)std::max(g->n_lrev[0], g->n_lrev[1]), &w->lrev));
     RC(ws_get(g, "sssp.prio", (size_t)grid * g->cells.n_cells, &w->prio));
@@ -907,8 +908,9 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
       if (!sssp_smq_shape_fits(g->d.V, shape) || getenv("QDTA_BF_NOSMQ")) continue;
       if (shape == 2 && sssp_smq_shape_fits(g->d.V, 0)) continue;  // same block as shape 0, fewer marks
       any_smq = true;
-      for (int adj = rank_ok ? 2 : ell_ok ? 1 : 0; adj >= 0; --adj)
-        for (int relax = 3; relax >= 2; --relax) cand.push_back({2, adj, relax, 0, shape});
+      for (int adj = rank_ok ? 3 : ell_ok ? 1 : 0; adj >= 0; --adj)
+        for (int relax = 3; relax >= 2; --relax)
+          if (!(adj == 3 && relax == 3)) cand.push_back({2, adj, relax, 0, shape});
     }
     if (!any_smq) cand.push_back({2, start.adj, start.relax, start.bpsm, start.shape});  // global queues
     if (g->has_cells) cand.push_back({1, start.adj, start.relax, start.bpsm, start.shape});  // cell-partitioned

@@ -22,6 +22,7 @@ enum : unsigned {
   ST_OVERFLOW = 4u,    // a distance exceeded the packed range
   ST_TIMEOUT = 8u,     // a bounded loop hit its limit
   ST_CAPACITY = 16u,   // an output buffer was too small
+  ST_K32 = 32u,        // a 32-bit-key batch met a distance >= 2^29 (redone with 64-bit keys; not an error)
 };
 
 constexpr int SSSP_THREADS = 256;
@@ -244,7 +245,7 @@ struct GraphDev {
   // non-returning atomic), shared-memory carveout percentage, launch shape
   // of the shared-memory-queue kernel (0: 512 threads, two mark bitmaps;
   // 1: 256 threads, one bitmap; 2: 512 threads, one bitmap)
-  int tune_adj, tune_relax, tune_carve, tune_shape;  // tune_adj: 0 compressed, 1 four-slot, 2 rank-keyed
+  int tune_adj, tune_relax, tune_carve, tune_shape;  // tune_adj: 0 compressed, 1 four-slot, 2 rank-keyed, 3 rank-keyed 32-bit
   int tune_out;  // output pass of the queue kernel: 1 internal node order, 0 external order
 };
 
@@ -290,6 +291,7 @@ struct SsspWork {
   uint2 *lrev;                // cell kernel: packed internal reversed links (u << 24 | link, q)
   unsigned long long *prio;   // cell kernel: [slots][cells] wake priorities
   int4 *xrev;                 // cell kernel: packed external readers (link, reader, q, 0)
+  int *fb_skip;               // 32-bit-key batches: 1 unless the 64-bit redo must run
   int slots;
 };
 

@@ -13,6 +13,7 @@
 #include <atomic>
 #include <climits>
 #include <string>
+#include <type_traits>
 #include <vector>
 #include <cstdlib>
 #include <cstdio>
@@ -866,21 +867,26 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   constexpr bool AGG = RELAX == 3;
   constexpr int RM = AGG ? 2 : RELAX;
   constexpr bool ELL = ADJ >= 1;
-  // ADJ 2: the key's low field is the rank (0..3) of the link among the
+  // ADJ 2, 3: the key's low field is the rank (0..3) of the link among the
   // keyed node's candidate parent links, ordered by link id (so the smallest
-  // rank is the smallest link id); rank_link maps it back to the link
-  const int LB = ADJ == 2 ? 3 : LB_link;
+  // rank is the smallest link id); rank_link maps it back to the link.
+  // ADJ 3 keeps the keys in 32 bits (distances below 2^29): a larger
+  // distance sets ST_K32 and the batch is redone with 64-bit keys.
+  constexpr bool RANK = ADJ >= 2;
+  using Key = typename std::conditional<ADJ == 3, unsigned, unsigned long long>::type;
+  constexpr Key KINF = ~Key(0);
+  const int LB = RANK ? 3 : LB_link;
   unsigned *bm0 = smq_smem, *bm1 = smq_smem + (NBM - 1) * W;
   int *sq0 = reinterpret_cast<int *>(smq_smem + NBM * W), *sq1 = sq0 + qcap;
   const size_t b = blockIdx.x;
-  unsigned long long *state = g_state + b * (size_t)V;
+  Key *state = reinterpret_cast<Key *>(g_state) + b * (size_t)V;
   int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;  // overflow beyond SMQ_CAP
   if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
-  const unsigned long long NOLINK = (1ull << LB) - 1ull;
-  const unsigned long long DMAX = (~0ull) >> LB;
+  const Key NOLINK = (Key)((1ull << LB) - 1ull);
+  const unsigned long long DMAX = (unsigned long long)(KINF >> LB);
   constexpr int NQ = THREADS / 4;
   const int quad = threadIdx.x >> 2, lane4 = threadIdx.x & 3;
-  for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = ~0ull;
+  for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
   for (int i = threadIdx.x; i < NBM * W; i += blockDim.x) smq_smem[i] = 0u;
   __syncthreads();
   for (int r = blockIdx.x; r < R; r += gridDim.x) {
@@ -926,23 +932,23 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
               kb[j] = __ldg(&off[w[j]]) + lane4;
               ke[j] = __ldg(&off[w[j] + 1]);
             }
-            const unsigned long long kw = __ldcg(&state[w[j]]);
-            dw[j] = kw >> LB;
+            const Key kw = __ldcg(&state[w[j]]);
+            dw[j] = (unsigned long long)(kw >> LB);
             // ADJ 2 on graphs where every link has its reverse and both lists
             // of a node share one order: slot lane4 leads back to w's parent
             // when it equals the parent's rank; that offer (dist(w) plus a
             // positive time) cannot beat the parent's key, so it is dropped
-            if (ADJ == 2 && skip_parent && (unsigned long long)lane4 == (kw & NOLINK)) skipj |= 1u << j;
+            if (RANK && skip_parent && (Key)lane4 == (kw & NOLINK)) skipj |= 1u << j;
           }
         }
         bool more = true;
         while (more) {
           int4 ent[SSSP2_NPT];
-          unsigned long long tk[SSSP2_NPT];
+          Key tk[SSSP2_NPT];
 #pragma unroll
           for (int j = 0; j < SSSP2_NPT; ++j) {
             if (kb[j] < ke[j]) {
-              if (ADJ == 2) {  // 8-byte entry: ((neighbour << 3) | rank, link time), -1 when absent
+              if (RANK) {  // 8-byte entry: ((neighbour << 3) | rank, link time), -1 when absent
                 const int2 e2 = __ldg(&reinterpret_cast<const int2 *>(adj)[kb[j]]);
                 ent[j] = make_int4(e2.x < 0 ? -1 : (e2.x & 7), e2.x >> 3, e2.y, 0);
               } else {
@@ -953,7 +959,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
 #pragma unroll
           for (int j = 0; j < SSSP2_NPT; ++j) {
             if (ELL && kb[j] < ke[j] && (ent[j].x < 0 || ((skipj >> j) & 1u))) ke[j] = kb[j];  // absent / skipped
-            tk[j] = ~0ull;
+            tk[j] = KINF;
             if (RM > 0 && kb[j] < ke[j]) tk[j] = __ldcg(&state[ent[j].y]);
           }
 #pragma unroll
@@ -963,19 +969,20 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
               ++my_relax;
               const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
               if (cand >= DMAX) {
-                atomicOr(status, ST_OVERFLOW);
+                atomicOr(status, ADJ == 3 ? ST_K32 : ST_OVERFLOW);
               } else {
-                const unsigned long long key = (cand << LB) | (unsigned long long)(unsigned)ent[j].x;
+                const Key key = (Key)((cand << LB) | (unsigned long long)(unsigned)ent[j].x);
                 if (key < tk[j]) {
                   const int y = ent[j].y;
-                  unsigned long long seen;
+                  Key seen;
                   if (RM == 2) {
                     atomicMin(&state[y], key);  // result unused: no wait on the reply
                     seen = tk[j];
                   } else {
                     seen = atomicMin(&state[y], key);
                   }
-                  if ((seen >> LB) > cand && !((atomicOr(&bnxt[y >> 5], 1u << (y & 31)) >> (y & 31)) & 1u)) {
+                  if ((unsigned long long)(seen >> LB) > cand &&
+                      !((atomicOr(&bnxt[y >> 5], 1u << (y & 31)) >> (y & 31)) & 1u)) {
                     if (AGG) {
                       pushy = y;
                     } else {
@@ -1042,35 +1049,35 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
       // external-order pass below and 43.6 ms for an external-order pass
       // that reset each key right after reading it (scattered 8-byte stores)
       for (int u0 = threadIdx.x; u0 < V; u0 += 4 * THREADS) {
-        unsigned long long key[4];
+        Key key[4];
         int v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int u = u0 + k * THREADS;
-          key[k] = u < V ? __ldcg(&state[u]) : 0ull;
+          key[k] = u < V ? __ldcg(&state[u]) : Key(0);
           v[k] = u < V ? __ldg(&node_ext[u]) : -1;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (v[k] < 0) continue;
           const int u = u0 + k * THREADS;
-          state[u] = ~0ull;
-          const unsigned long long lk = key[k] & NOLINK;
-          prow[v[k]] = lk == NOLINK ? -1 : ADJ == 2 ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
-          if (drow) drow[v[k]] = key[k] == ~0ull ? LLONG_MAX : (long long)(key[k] >> LB);
+          state[u] = KINF;
+          const Key lk = key[k] & NOLINK;
+          prow[v[k]] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
+          if (drow) drow[v[k]] = key[k] == KINF ? LLONG_MAX : (long long)(key[k] >> LB);
         }
       }
     } else {
       // external order, then a separate coalesced reset
       for (int v = threadIdx.x; v < V; v += blockDim.x) {
         const int u = node_int ? node_int[v] : v;
-        const unsigned long long key = __ldcg(&state[u]);
-        const unsigned long long lk = key & NOLINK;
-        prow[v] = lk == NOLINK ? -1 : ADJ == 2 ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
-        if (drow) drow[v] = key == ~0ull ? LLONG_MAX : (long long)(key >> LB);
+        const Key key = __ldcg(&state[u]);
+        const Key lk = key & NOLINK;
+        prow[v] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
+        if (drow) drow[v] = key == KINF ? LLONG_MAX : (long long)(key >> LB);
       }
       __syncthreads();
-      for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = ~0ull;
+      for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
     }
     __syncthreads();
   }
@@ -1102,18 +1109,19 @@ bool sssp_uses_ell(const GraphDev &g, int direction) {
 }
 int sssp_adj(const GraphDev &g, int direction) {
   if (!sssp_uses_ell(g, direction)) return 0;
-  return g.tune_adj >= 2 && g.rank_tgt[direction] && g.rank_link[direction] && g.V < (1 << 28) ? 2 : 1;
+  if (g.tune_adj >= 2 && g.rank_tgt[direction] && g.rank_link[direction] && g.V < (1 << 28)) return g.tune_adj;
+  return 1;
 }
 
 // name of the kernel launch_sssp runs for this graph, direction and storage
 const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
   if (use_smem) return "sssp_kernel<true>";
   if (sssp_uses_smq(g)) {
-    static const char *adj_name[3] = {"csr", "ell", "rank"};
+    static const char *adj_name[4] = {"csr", "ell", "rank", "rank32"};
     static const std::vector<std::string> names = [] {
       std::vector<std::string> v;
       for (int sh = 0; sh < 3; ++sh)
-        for (int e = 0; e < 3; ++e)
+        for (int e = 0; e < 4; ++e)
           for (int r = 0; r < 4; ++r)
             v.push_back("sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
                         std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") + ">");
@@ -1121,8 +1129,9 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
     }();
     const int adj = sssp_adj(g, direction);
     int r = g.tune_relax < 0 ? 0 : g.tune_relax > 3 ? 3 : g.tune_relax;
-    if (adj == 2 && r < 2) r = 2;
-    return names[(g.tune_shape * 3 + adj) * 4 + r].c_str();
+    if (adj >= 2 && r < 2) r = 2;
+    if (adj == 3) r = 2;
+    return names[(g.tune_shape * 4 + adj) * 4 + r].c_str();
   }
   switch (sssp_group_size()) {
     case 2: return "sssp_group_kernel<512,2>";
@@ -1149,12 +1158,23 @@ int sssp_blocks_per_sm(bool use_smem, int V) {
   return n > 0 ? n : 1;
 }
 
+// after a 32-bit-key batch: run the 64-bit redo only if the batch overflowed
+// (and was not skipped); clears the overflow bit, which is not an error
+__global__ void k32_redo_flag_kernel(unsigned *status, const int *skip_dev, int *fb_skip) {
+  const unsigned st = *status;
+  const bool skipped = skip_dev && *skip_dev;
+  const bool redo = !skipped && (st & ST_K32);
+  if (st & ST_K32) atomicAnd(status, ~ST_K32);
+  *fb_skip = redo ? 0 : 1;
+}
+
 using SmqKernel = void (*)(int, int, const int *, const int4 *, const int *, int, const int *, unsigned long long *,
                           int *, int *, const int *, long long, long long *, unsigned *, const int *,
                           unsigned long long *, const int *, int, int, const int *, int, const int *, int);
 
 template <int THREADS, bool ONEBM>
 static SmqKernel smq_kernel_relax(int adj, int relax) {
+  if (adj == 3) return sssp_smq_kernel<THREADS, 3, 2, ONEBM>;
   if (adj == 2) return relax == 3 ? sssp_smq_kernel<THREADS, 2, 3, ONEBM> : sssp_smq_kernel<THREADS, 2, 2, ONEBM>;
   if (adj == 1) return relax == 3 ? sssp_smq_kernel<THREADS, 1, 3, ONEBM>
                 : relax == 2 ? sssp_smq_kernel<THREADS, 1, 2, ONEBM>
@@ -1201,7 +1221,6 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                                                      parent_slot_dev, slot_stride, dist, status, skip_dev,
                                                      roots_counter, round_limit(g.V));
   } else {
-    COUNT_LAUNCH();
     // block size of the global-memory variant (QDTA_BF_THREADS: 128, 256, 512 or 1024)
     static int bf_threads = [] {
       const char *e = getenv("QDTA_BF_THREADS");
@@ -1220,23 +1239,35 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       // same configuration.  The percentage is rounded up to a supported
       // size: 85 % of 228 KB asks for 194 KB and gets the 196 KB step (86 %
       // would round up to 228 KB).  QDTA_SMQ_CARVEOUT overrides, in percent.
-      const SmqKernel kern = smq_kernel_for(g.tune_shape, adjl, g.tune_relax);
       const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
       const int threads = kSmqShape[g.tune_shape].threads;
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
-      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
       const bool perm = g.node_int != nullptr;
-      kern<<<grid, threads, smq, s>>>(g.V, g.LB, perm ? g.perm_off[direction] : off, adj, roots, R_host, R_dev,
-                                      w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip_dev,
-                                      roots_counter, perm ? g.node_int : nullptr, round_limit(g.V),
-                                      kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
-                                      g.rank_link[direction], g.skip_parent);
+      auto run = [&](SmqKernel kern, const int *skip) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
+        COUNT_LAUNCH();
+        kern<<<grid, threads, smq, s>>>(g.V, g.LB, perm ? g.perm_off[direction] : off, adj, roots, R_host, R_dev,
+                                        w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip,
+                                        roots_counter, perm ? g.node_int : nullptr, round_limit(g.V),
+                                        kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
+                                        g.rank_link[direction], g.skip_parent);
+      };
+      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev);
+      if (adjl == 3) {
+        // a distance beyond the 32-bit keys' range: redo the batch with 64-bit
+        // keys on the same packed adjacency (decided on the device, so graph
+        // replays need no host round trip)
+        COUNT_LAUNCH();
+        k32_redo_flag_kernel<<<1, 1, 0, s>>>(status, skip_dev, w.fb_skip);
+        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip);
+      }
       return;
     }
     if (G == 2) kern = sssp_group_kernel<512, 2>;
     else if (G == 4) kern = sssp_group_kernel<512, 4>;
     else if (G == 8) kern = sssp_group_kernel<512, 8>;
     if (G > 1) bf_threads = 512;
+    COUNT_LAUNCH();
     kern<<<grid, bf_threads, 0, s>>>(g.V, g.LB, off, adj, roots, R_host, R_dev,
                                                      w.state, w.stamp, w.queue, parent,
                                                      parent_slot_dev, slot_stride, dist, status,

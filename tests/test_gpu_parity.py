@@ -108,6 +108,8 @@ def test_sssp_unreachable_nodes():
 LARGE_VARIANTS = {
     "default": ({}, "sssp_smq_kernel<256,rank,2,true>"),
     "rank_without_parent_skip": ({"QDTA_NO_PARENT_SKIP": "1"}, "sssp_smq_kernel<256,rank,2,true>"),
+    "rank32": ({"QDTA_SSSP_ADJ": "3"}, "sssp_smq_kernel<256,rank32,2,true>"),
+    "rank32_512": ({"QDTA_SSSP_ADJ": "3", "QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,rank32,2,false>"),
     "ell16": ({"QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
     "csr": ({"QDTA_NO_ELL": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
     "no_reorder": ({"QDTA_NO_REORDER": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
@@ -170,6 +172,24 @@ def test_sssp_rank_keys_on_a_graph_with_one_way_links():
         np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
+@pytest.mark.parametrize("adj", ["2", "3"])
+def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, monkeypatch):
+    """Link times of 5e6..1e7 quanta push distances past 2^29: the 32-bit-key
+    batch flags it and the 64-bit redo gives the oracle's bits."""
+    net, dem, _, og = mid
+    monkeypatch.setenv("QDTA_SSSP_ADJ", adj)
+    g = Q.Graph(net)
+    rng = np.random.default_rng(21)
+    q = rng.integers(5_000_000, 10_000_000, net.n_links).astype(np.int32)
+    roots = rng.choice(net.n_nodes, 24, replace=False).astype(np.int32)
+    for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
+        p_o, d_o = oracle.sssp(og, q, roots, direction)
+        assert d_o[d_o < np.iinfo(np.int64).max].max() >= 1 << 29
+        p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
+        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
 def test_sssp_large_irregular_graph_with_ties():
     """Above the shared-memory limit with degrees above 4 (so the compressed
     adjacency, not the four-slot one) and many equal-cost ties: bit-exact
@@ -211,11 +231,12 @@ def test_autotune_keeps_the_fastest_shape_and_stays_bit_exact(mid):
     rep = Q.qdta_autotune(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, reps=1)
     kernels = {c["kernel"] for c in rep["candidates"]}
     # launch shapes {512 x 2 CTAs, 256 x 4 CTAs} x adjacency {rank-keyed, four-slot, compressed} x
-    # relaxation modes {2, 3}, plus the cell kernel
+    # relaxation modes {2, 3}, rank-keyed 32-bit keys (mode 2), plus the cell kernel
     want = {f"sssp_smq_kernel<{t},{e},{r},{b}>" for t, b in (("512", "false"), ("256", "true"))
             for e in ("rank", "ell", "csr") for r in (2, 3)} | {"sssp_cell_kernel"}
+    want |= {f"sssp_smq_kernel<{t},rank32,2,{b}>" for t, b in (("512", "false"), ("256", "true"))}
     assert kernels == want
-    assert len(rep["candidates"]) == 13
+    assert len(rep["candidates"]) == 15
     assert {c["ctas_per_sm"] for c in rep["candidates"] if c["kernel"].startswith("sssp_smq_kernel<256")} == {4}
     assert rep["best"]["ms"] == min(c["ms"] for c in rep["candidates"])
     assert Q.qdta_sssp_kernel_name(g, Q.QDTA_TO_ROOT) == rep["best"]["kernel"]
