@@ -39,6 +39,8 @@ METRIC = "Full-day QDTA s @rel-gap 1e-4, batched vs plain on 1 GB300; SSSP GTEPS
 SSSP_DRAM_BYTES_PER_ROOT = {
     # profiles/sssp_smq_kernel_rank_metro_R608.md: 2.830261 GB read + 5.333477 GB written, 608 roots
     "sssp_smq_kernel<256,rank,2,true>": (2.830261e9 + 5.333477e9) / 608,
+    # profiles/sssp_smq_kernel_rank32_metro_R608.md: 1.309412 GB read + 2.531841 GB written, 608 roots
+    "sssp_smq_kernel<256,rank32,2,true>": (1.309412e9 + 2.531841e9) / 608,
 }
 
 

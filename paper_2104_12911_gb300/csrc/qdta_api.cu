@@ -584,7 +584,7 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   g->sssp_kind = g->sssp_smem ? 0 : 2;
   // launch choices (environment overrides for experiments; qdta_autotune
   // replaces them by measurement)
-  g->d.tune_adj = getenv("QDTA_NO_ELL") ? 0 : 2;
+  g->d.tune_adj = getenv("QDTA_NO_ELL") ? 0 : 3;  // 32-bit rank keys where the degrees allow
   if (const char *e = getenv("QDTA_SSSP_ADJ")) g->d.tune_adj = std::min(3, std::max(0, atoi(e)));
   g->d.tune_relax = 2;
   if (const char *e = getenv("QDTA_BF_RELAX")) g->d.tune_relax = std::min(3, std::max(0, atoi(e)));
@@ -837,7 +837,7 @@ static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots
                      g->prof_on ? g->prof_roots : nullptr);
   } else {
     const int adjl = g->sssp_kind == 2 ? sssp_adj(g->d, direction) : 0;
-    if (adjl == 2) launch_pack_ell8(g->d, direction, q, reinterpret_cast<int2 *>(w.adj), s, skip_dev);
+    if (adjl >= 2) launch_pack_ell8(g->d, direction, q, reinterpret_cast<int2 *>(w.adj), s, skip_dev);
     else if (adjl == 1) launch_pack_ell(g->d, direction, q, w.adj, s, skip_dev);
     else if (g->sssp_kind == 2 && sssp_uses_perm(g->d)) launch_pack_perm_adj(g->d, direction, q, w.adj, s, skip_dev);
     else launch_pack_adj(g->d, direction, q, w.adj, s, skip_dev);

@@ -106,24 +106,26 @@ def test_sssp_unreachable_nodes():
 
 
 LARGE_VARIANTS = {
-    "default": ({}, "sssp_smq_kernel<256,rank,2,true>"),
-    "rank_without_parent_skip": ({"QDTA_NO_PARENT_SKIP": "1"}, "sssp_smq_kernel<256,rank,2,true>"),
-    "rank32": ({"QDTA_SSSP_ADJ": "3"}, "sssp_smq_kernel<256,rank32,2,true>"),
-    "rank32_512": ({"QDTA_SSSP_ADJ": "3", "QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,rank32,2,false>"),
+    "default": ({}, "sssp_smq_kernel<256,rank32,2,true>"),
+    "rank32_without_parent_skip": ({"QDTA_NO_PARENT_SKIP": "1"}, "sssp_smq_kernel<256,rank32,2,true>"),
+    "rank64": ({"QDTA_SSSP_ADJ": "2"}, "sssp_smq_kernel<256,rank,2,true>"),
+    "rank64_without_parent_skip": ({"QDTA_SSSP_ADJ": "2", "QDTA_NO_PARENT_SKIP": "1"},
+                                   "sssp_smq_kernel<256,rank,2,true>"),
+    "rank32_512": ({"QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,rank32,2,false>"),
     "ell16": ({"QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
     "csr": ({"QDTA_NO_ELL": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
     "no_reorder": ({"QDTA_NO_REORDER": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
     "returning_atomic": ({"QDTA_BF_RELAX": "1", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,1,true>"),
     "atomic_only": ({"QDTA_BF_RELAX": "0", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,0,true>"),
-    "two_bitmaps_512": ({"QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,rank,2,false>"),
+    "two_bitmaps_512_rank64": ({"QDTA_BF_SHAPE": "0", "QDTA_SSSP_ADJ": "2"}, "sssp_smq_kernel<512,rank,2,false>"),
     "two_bitmaps_512_csr_returning": ({"QDTA_BF_SHAPE": "0", "QDTA_NO_ELL": "1", "QDTA_BF_RELAX": "1"},
                                       "sssp_smq_kernel<512,csr,1,false>"),
-    "one_bitmap_512": ({"QDTA_BF_SHAPE": "2"}, "sssp_smq_kernel<512,rank,2,true>"),
-    "one_cta_per_sm": ({"QDTA_BF_BPSM": "1"}, "sssp_smq_kernel<256,rank,2,true>"),
-    "aggregated_appends": ({"QDTA_BF_RELAX": "3"}, "sssp_smq_kernel<256,rank,3,true>"),
+    "one_bitmap_512": ({"QDTA_BF_SHAPE": "2"}, "sssp_smq_kernel<512,rank32,2,true>"),
+    "one_cta_per_sm": ({"QDTA_BF_BPSM": "1"}, "sssp_smq_kernel<256,rank32,2,true>"),
+    "aggregated_appends": ({"QDTA_BF_RELAX": "3", "QDTA_SSSP_ADJ": "2"}, "sssp_smq_kernel<256,rank,3,true>"),
     "aggregated_appends_csr_512": ({"QDTA_BF_RELAX": "3", "QDTA_NO_ELL": "1", "QDTA_BF_SHAPE": "0"},
                                    "sssp_smq_kernel<512,csr,3,false>"),
-    "output_external_order": ({"QDTA_SMQ_OUT": "0"}, "sssp_smq_kernel<256,rank,2,true>"),
+    "output_external_order": ({"QDTA_SMQ_OUT": "0"}, "sssp_smq_kernel<256,rank32,2,true>"),
     "output_external_order_ell_512": ({"QDTA_SMQ_OUT": "0", "QDTA_BF_SHAPE": "0", "QDTA_SSSP_ADJ": "1"},
                                       "sssp_smq_kernel<512,ell,2,false>"),
     "global_queues": ({"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "sssp_ilp_kernel<512>"),
@@ -165,7 +167,7 @@ def test_sssp_rank_keys_on_a_graph_with_one_way_links():
     q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
     roots = rng.choice(net.n_nodes, 40, replace=False).astype(np.int32)
     for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
-        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<256,rank,2,true>"
+        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<256,rank32,2,true>"
         p_o, d_o = oracle.sssp(og, q, roots, direction)
         p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
         np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
@@ -215,7 +217,7 @@ def test_sssp_graph_beyond_the_two_bitmap_limit():
     q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
     roots = rng.choice(net.n_nodes, 6, replace=False).astype(np.int32)
     for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
-        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<512,rank,2,true>"
+        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<512,rank32,2,true>"
         p_o, d_o = oracle.sssp(og, q, roots, direction)
         p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
         np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
