@@ -45,7 +45,8 @@ extern "C" {
 #define QDTA_ETIMEOUT (-4)   /* a bounded device wait or loop gave up */
 #define QDTA_ENONFINITE (-5) /* a NaN/inf flow, capacity or cost, or a term beyond 2^68 */
 #define QDTA_EUNREACH (-6)   /* a destination is unreachable from an origin */
-#define QDTA_EOVERFLOW (-7)  /* a distance exceeded the packed range (2^(64-ceil(log2(L+1)))) */
+#define QDTA_EOVERFLOW (-7)  /* a distance exceeded the packed range: 2^(64-ceil(log2(L+1))), or 2^61
+                                 for rank-keyed keys (graphs above 10,240 nodes, all degrees <= 4) */
 #define QDTA_ENOTCONV 1      /* valid result, tolerance not met within max_iter */
 
 #define QDTA_TO_ROOT 0   /* dist/parent toward the root (destination trees, reverse graph) */
@@ -161,7 +162,9 @@ int qdta_graph_destroy(qdta_graph *g);
  * id among the links entering v that end a shortest path from the root.
  * parent = -1 at the root and at unreachable nodes (dist = QDTA_DIST_INF).
  * cost_q [L] int32 >= 1; roots [R]; parent_link [R*V] row-major by root;
- * dist [R*V] or NULL.  QDTA_EOVERFLOW if a distance exceeds the packed range. */
+ * dist [R*V] or NULL.  QDTA_EOVERFLOW if a distance exceeds the packed range.
+ * Results do not depend on the launch shape the handle uses (see
+ * qdta_autotune): the parent rule is order-free. */
 int qdta_sssp_batch(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R,
                     int32_t direction, int32_t *parent_link, int64_t *dist, void *stream);
 

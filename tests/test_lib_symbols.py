@@ -77,3 +77,17 @@ def test_tune_report_layout_matches_the_header():
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     assert [int(x) for x in out] == [ctypes.sizeof(Q.TuneEntry), ctypes.sizeof(Q.TuneReport),
                                      ctypes.sizeof(Q.Profile)]
+
+
+def test_tune_report_as_dict_keeps_valid_rows_and_the_best():
+    from paper_2104_12911_gb300 import qdta as Q
+    rep = Q.TuneReport()
+    rep.n, rep.best = 3, 1
+    for i, (name, ms, valid) in enumerate((("a<1>", 5.0, 1), ("b<2>", 3.0, 1), ("c<3>", 0.0, 0))):
+        rep.entry[i].kernel = name.encode()
+        rep.entry[i].ctas_per_sm = 4
+        rep.entry[i].ms = ms
+        rep.entry[i].valid = valid
+    d = rep.as_dict()
+    assert [c["kernel"] for c in d["candidates"]] == ["a<1>", "b<2>"]
+    assert d["best"]["kernel"] == "b<2>" and d["best"]["ms"] == 3.0
