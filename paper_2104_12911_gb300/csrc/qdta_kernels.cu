@@ -832,10 +832,15 @@ int sssp_group_size() {
 // Launch shapes (threads, bitmaps, queue entries per buffer):
 //   0: 512, two, 3072 (two CTAs per SM)   1: 256, one, 2048 (four CTAs per SM)
 //   2: 512, one, 3072 (two CTAs per SM, larger graphs)
+//   3: 256, one, 768 (five CTAs per SM: at most 51 registers a thread, so
+//      only the 32-bit rank-keyed kernel; wider frontiers spill to the
+//      global overflow queue)
 struct SmqShape {
   int threads, bitmaps, qcap, ctas;
 };
-static const SmqShape kSmqShape[3] = {{512, 2, 3072, 2}, {256, 1, 2048, 4}, {512, 1, 3072, 2}};
+constexpr int kSmqShapes = 4;
+static const SmqShape kSmqShape[kSmqShapes] = {
+    {512, 2, 3072, 2}, {256, 1, 2048, 4}, {512, 1, 3072, 2}, {256, 1, 768, 5}};
 
 // RELAX selects how an offer (cand, link) to neighbour y is applied:
 //   0  returning atomicMin; y is queued when the returned old distance was larger
@@ -848,8 +853,8 @@ static const SmqShape kSmqShape[3] = {{512, 2, 3072, 2}, {256, 1, 2048, 4}, {512
 //      ends in a CTA barrier and every state access goes through L2.
 //   3  as 2, with warp-aggregated queue appends (one shared-memory atomicAdd
 //      per warp and offsets from a ballot instead of one per queued node)
-template <int THREADS, int ADJ, int RELAX, bool ONEBM>
-__global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64))
+template <int THREADS, int ADJ, int RELAX, bool ONEBM, int MINB = 65536 / (THREADS * 64)>
+__global__ void __launch_bounds__(THREADS, MINB)
 sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__restrict__ adj,
                 const int *__restrict__ roots, int R_host, const int *R_dev,
                 unsigned long long *g_state, int *g_queue, int *parent,
@@ -1090,7 +1095,7 @@ size_t sssp_smq_smem_bytes(int V, int shape) {
 
 // does launch shape `shape` fit its CTAs per SM in the 196 KB carveout step
 bool sssp_smq_shape_fits(int V, int shape) {
-  if (shape < 0 || shape > 2) return false;
+  if (shape < 0 || shape >= kSmqShapes) return false;
   return sssp_smq_smem_bytes(V, shape) * kSmqShape[shape].ctas <= 192 * 1024;
 }
 
@@ -1120,11 +1125,12 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
     static const char *adj_name[4] = {"csr", "ell", "rank", "rank32"};
     static const std::vector<std::string> names = [] {
       std::vector<std::string> v;
-      for (int sh = 0; sh < 3; ++sh)
+      for (int sh = 0; sh < kSmqShapes; ++sh)
         for (int e = 0; e < 4; ++e)
           for (int r = 0; r < 4; ++r)
             v.push_back("sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
-                        std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") + ">");
+                        std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") +
+                        (sh == 3 && e == 3 ? ",5" : "") + ">");
       return v;
     }();
     const int adj = sssp_adj(g, direction);
@@ -1185,7 +1191,8 @@ static SmqKernel smq_kernel_relax(int adj, int relax) {
 }
 
 static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
-  if (shape == 1) return smq_kernel_relax<256, true>(adj, relax);
+  if (shape == 3 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 5>;
+  if (shape == 1 || shape == 3) return smq_kernel_relax<256, true>(adj, relax);
   if (shape == 2) return smq_kernel_relax<512, true>(adj, relax);
   return smq_kernel_relax<512, false>(adj, relax);
 }

@@ -112,6 +112,8 @@ LARGE_VARIANTS = {
     "rank64_without_parent_skip": ({"QDTA_SSSP_ADJ": "2", "QDTA_NO_PARENT_SKIP": "1"},
                                    "sssp_smq_kernel<256,rank,2,true>"),
     "rank32_512": ({"QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,rank32,2,false>"),
+    "rank32_five_ctas": ({"QDTA_BF_SHAPE": "3"}, "sssp_smq_kernel<256,rank32,2,true,5>"),
+    "five_cta_shape_ell16": ({"QDTA_BF_SHAPE": "3", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
     "ell16": ({"QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
     "csr": ({"QDTA_NO_ELL": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
     "no_reorder": ({"QDTA_NO_REORDER": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
@@ -237,9 +239,11 @@ def test_autotune_keeps_the_fastest_shape_and_stays_bit_exact(mid):
     want = {f"sssp_smq_kernel<{t},{e},{r},{b}>" for t, b in (("512", "false"), ("256", "true"))
             for e in ("rank", "ell", "csr") for r in (2, 3)} | {"sssp_cell_kernel"}
     want |= {f"sssp_smq_kernel<{t},rank32,2,{b}>" for t, b in (("512", "false"), ("256", "true"))}
+    want |= {"sssp_smq_kernel<256,rank32,2,true,5>"}
     assert kernels == want
-    assert len(rep["candidates"]) == 15
-    assert {c["ctas_per_sm"] for c in rep["candidates"] if c["kernel"].startswith("sssp_smq_kernel<256")} == {4}
+    assert len(rep["candidates"]) == 16
+    ctas = {c["kernel"]: c["ctas_per_sm"] for c in rep["candidates"]}
+    assert ctas["sssp_smq_kernel<256,rank32,2,true>"] == 4 and ctas["sssp_smq_kernel<256,rank32,2,true,5>"] == 5
     assert rep["best"]["ms"] == min(c["ms"] for c in rep["candidates"])
     assert Q.qdta_sssp_kernel_name(g, Q.QDTA_TO_ROOT) == rep["best"]["kernel"]
     p_o, d_o = oracle.sssp(og, q, roots)
