@@ -904,17 +904,17 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
     const bool ell_ok = g->d.max_deg[direction] <= 4 && g->d.node_int != nullptr;
     const bool rank_ok = ell_ok && g->d.rank_tgt[direction] != nullptr;
     bool any_smq = false;
-    for (int shape = 0; shape < 4; ++shape) {
+    for (int shape = 0; shape < 6; ++shape) {
       if (!sssp_smq_shape_fits(g->d.V, shape) || getenv("QDTA_BF_NOSMQ")) continue;
       if (shape == 2 && sssp_smq_shape_fits(g->d.V, 0)) continue;  // same block as shape 0, fewer marks
       any_smq = true;
-      if (shape == 3) {  // five CTAs per SM: 32-bit rank keys only
-        if (rank_ok) cand.push_back({2, 3, 2, 0, 3});
+      if (shape >= 3) {  // five CTAs per SM, or 5 / 6 nodes in flight per lane group: 32-bit rank keys only
+        if (rank_ok) cand.push_back({2, 3, 2, 0, shape});
         continue;
       }
-      for (int adj = rank_ok ? 3 : ell_ok ? 1 : 0; adj >= 0; --adj)
-        for (int relax = 3; relax >= 2; --relax)
-          if (!(adj == 3 && relax == 3)) cand.push_back({2, adj, relax, 0, shape});
+      // relaxation mode 2 only: mode 1 (returning atomic) and mode 3
+      // (aggregated appends) measured slower in every shape and layout
+      for (int adj = rank_ok ? 3 : ell_ok ? 1 : 0; adj >= 0; --adj) cand.push_back({2, adj, 2, 0, shape});
     }
     if (!any_smq) cand.push_back({2, start.adj, start.relax, start.bpsm, start.shape});  // global queues
     if (g->has_cells) cand.push_back({1, start.adj, start.relax, start.bpsm, start.shape});  // cell-partitioned

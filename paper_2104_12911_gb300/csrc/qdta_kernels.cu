@@ -835,12 +835,14 @@ int sssp_group_size() {
 //   3: 256, one, 768 (five CTAs per SM: at most 51 registers a thread, so
 //      only the 32-bit rank-keyed kernel; wider frontiers spill to the
 //      global overflow queue)
+//   4, 5: as 1, with 5 or 6 frontier nodes per lane group in flight instead
+//      of 4 (a pass covers 320 or 384 nodes; 32-bit rank keys only)
 struct SmqShape {
-  int threads, bitmaps, qcap, ctas;
+  int threads, bitmaps, qcap, ctas, npt;
 };
-constexpr int kSmqShapes = 4;
-static const SmqShape kSmqShape[kSmqShapes] = {
-    {512, 2, 3072, 2}, {256, 1, 2048, 4}, {512, 1, 3072, 2}, {256, 1, 768, 5}};
+constexpr int kSmqShapes = 6;
+static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 2048, 4, 4}, {512, 1, 3072, 2, 4},
+                                               {256, 1, 768, 5, 4},  {256, 1, 2048, 4, 5}, {256, 1, 2048, 4, 6}};
 
 // RELAX selects how an offer (cand, link) to neighbour y is applied:
 //   0  returning atomicMin; y is queued when the returned old distance was larger
@@ -853,7 +855,7 @@ static const SmqShape kSmqShape[kSmqShapes] = {
 //      ends in a CTA barrier and every state access goes through L2.
 //   3  as 2, with warp-aggregated queue appends (one shared-memory atomicAdd
 //      per warp and offsets from a ballot instead of one per queued node)
-template <int THREADS, int ADJ, int RELAX, bool ONEBM, int MINB = 65536 / (THREADS * 64)>
+template <int THREADS, int ADJ, int RELAX, bool ONEBM, int MINB = 65536 / (THREADS * 64), int NPT = SSSP2_NPT>
 __global__ void __launch_bounds__(THREADS, MINB)
 sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__restrict__ adj,
                 const int *__restrict__ roots, int R_host, const int *R_dev,
@@ -916,17 +918,17 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
         }
         __syncthreads();
       }
-      for (int base = 0; base < ncur; base += NQ * SSSP2_NPT) {
-        int w[SSSP2_NPT], kb[SSSP2_NPT], ke[SSSP2_NPT];
-        unsigned long long dw[SSSP2_NPT];
+      for (int base = 0; base < ncur; base += NQ * NPT) {
+        int w[NPT], kb[NPT], ke[NPT];
+        unsigned long long dw[NPT];
         unsigned skipj = 0;
 #pragma unroll
-        for (int j = 0; j < SSSP2_NPT; ++j) {
+        for (int j = 0; j < NPT; ++j) {
           const int i = base + j * NQ + quad;
           w[j] = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
         }
 #pragma unroll
-        for (int j = 0; j < SSSP2_NPT; ++j) {
+        for (int j = 0; j < NPT; ++j) {
           kb[j] = 0; ke[j] = 0; dw[j] = 0;
           if (w[j] >= 0) {
             if (!ONEBM && lane4 == 0) atomicAnd(&bcur[w[j] >> 5], ~(1u << (w[j] & 31)));
@@ -948,10 +950,10 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
         }
         bool more = true;
         while (more) {
-          int4 ent[SSSP2_NPT];
-          Key tk[SSSP2_NPT];
+          int4 ent[NPT];
+          Key tk[NPT];
 #pragma unroll
-          for (int j = 0; j < SSSP2_NPT; ++j) {
+          for (int j = 0; j < NPT; ++j) {
             if (kb[j] < ke[j]) {
               if (RANK) {  // 8-byte entry: ((neighbour << 3) | rank, link time), -1 when absent
                 const int2 e2 = __ldg(&reinterpret_cast<const int2 *>(adj)[kb[j]]);
@@ -962,13 +964,13 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
             }
           }
 #pragma unroll
-          for (int j = 0; j < SSSP2_NPT; ++j) {
+          for (int j = 0; j < NPT; ++j) {
             if (ELL && kb[j] < ke[j] && (ent[j].x < 0 || ((skipj >> j) & 1u))) ke[j] = kb[j];  // absent / skipped
             tk[j] = KINF;
             if (RM > 0 && kb[j] < ke[j]) tk[j] = __ldcg(&state[ent[j].y]);
           }
 #pragma unroll
-          for (int j = 0; j < SSSP2_NPT; ++j) {
+          for (int j = 0; j < NPT; ++j) {
             int pushy = -1;
             if (kb[j] < ke[j]) {
               ++my_relax;
@@ -1019,7 +1021,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
           }
           more = false;
 #pragma unroll
-          for (int j = 0; j < SSSP2_NPT; ++j) {
+          for (int j = 0; j < NPT; ++j) {
             kb[j] += 4;
             more |= kb[j] < ke[j];
           }
@@ -1130,7 +1132,8 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
           for (int r = 0; r < 4; ++r)
             v.push_back("sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
                         std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") +
-                        (sh == 3 && e == 3 ? ",5" : "") + ">");
+                        (sh == 3 && e == 3 ? ",5" : "") +
+                        (sh >= 4 && e == 3 ? ",npt" + std::to_string(kSmqShape[sh].npt) : "") + ">");
       return v;
     }();
     const int adj = sssp_adj(g, direction);
@@ -1192,7 +1195,9 @@ static SmqKernel smq_kernel_relax(int adj, int relax) {
 
 static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
   if (shape == 3 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 5>;
-  if (shape == 1 || shape == 3) return smq_kernel_relax<256, true>(adj, relax);
+  if (shape == 4 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 5>;
+  if (shape == 5 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 6>;
+  if (shape == 1 || shape >= 3) return smq_kernel_relax<256, true>(adj, relax);
   if (shape == 2) return smq_kernel_relax<512, true>(adj, relax);
   return smq_kernel_relax<512, false>(adj, relax);
 }

@@ -114,6 +114,8 @@ LARGE_VARIANTS = {
     "rank32_512": ({"QDTA_BF_SHAPE": "0"}, "sssp_smq_kernel<512,rank32,2,false>"),
     "rank32_five_ctas": ({"QDTA_BF_SHAPE": "3"}, "sssp_smq_kernel<256,rank32,2,true,5>"),
     "five_cta_shape_ell16": ({"QDTA_BF_SHAPE": "3", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
+    "rank32_npt5": ({"QDTA_BF_SHAPE": "4"}, "sssp_smq_kernel<256,rank32,2,true,npt5>"),
+    "rank32_npt6": ({"QDTA_BF_SHAPE": "5"}, "sssp_smq_kernel<256,rank32,2,true,npt6>"),
     "ell16": ({"QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
     "csr": ({"QDTA_NO_ELL": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
     "no_reorder": ({"QDTA_NO_REORDER": "1"}, "sssp_smq_kernel<256,csr,2,true>"),
@@ -234,14 +236,15 @@ def test_autotune_keeps_the_fastest_shape_and_stays_bit_exact(mid):
     roots = rng.choice(net.n_nodes, 64, replace=False).astype(np.int32)
     rep = Q.qdta_autotune(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, reps=1)
     kernels = {c["kernel"] for c in rep["candidates"]}
-    # launch shapes {512 x 2 CTAs, 256 x 4 CTAs} x adjacency {rank-keyed, four-slot, compressed} x
-    # relaxation modes {2, 3}, rank-keyed 32-bit keys (mode 2), plus the cell kernel
-    want = {f"sssp_smq_kernel<{t},{e},{r},{b}>" for t, b in (("512", "false"), ("256", "true"))
-            for e in ("rank", "ell", "csr") for r in (2, 3)} | {"sssp_cell_kernel"}
-    want |= {f"sssp_smq_kernel<{t},rank32,2,{b}>" for t, b in (("512", "false"), ("256", "true"))}
-    want |= {"sssp_smq_kernel<256,rank32,2,true,5>"}
+    # launch shapes {512 x 2 CTAs, 256 x 4 CTAs} x adjacency {32-bit rank keys, rank keys, four-slot,
+    # compressed} in relaxation mode 2; the 32-bit kernel also with five CTAs per SM and with 5 or 6
+    # frontier nodes per lane group; the cell kernel
+    want = {f"sssp_smq_kernel<{t},{e},2,{b}>" for t, b in (("512", "false"), ("256", "true"))
+            for e in ("rank32", "rank", "ell", "csr")} | {"sssp_cell_kernel"}
+    want |= {"sssp_smq_kernel<256,rank32,2,true,5>", "sssp_smq_kernel<256,rank32,2,true,npt5>",
+             "sssp_smq_kernel<256,rank32,2,true,npt6>"}
     assert kernels == want
-    assert len(rep["candidates"]) == 16
+    assert len(rep["candidates"]) == 12
     ctas = {c["kernel"]: c["ctas_per_sm"] for c in rep["candidates"]}
     assert ctas["sssp_smq_kernel<256,rank32,2,true>"] == 4 and ctas["sssp_smq_kernel<256,rank32,2,true,5>"] == 5
     assert rep["best"]["ms"] == min(c["ms"] for c in rep["candidates"])
