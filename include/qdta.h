@@ -299,11 +299,13 @@ int qdta_sssp_batch_noalloc(qdta_graph *g, const int32_t *cost_q, const int32_t 
  *
  * Candidates: for graphs whose per-root state fits in shared memory, only the
  * shared-memory kernel; otherwise the global-memory Bellman-Ford with
- * {four-slot, compressed} adjacency (four-slot only when every degree <= 4) x
  * launch shape {512 threads x 2 CTAs per SM, 256 threads x 4 CTAs per SM,
- * whichever fit in shared memory} x three ways to apply an offer (read, then
- * returning atomicMin; read, then non-returning atomicMin; the same with
- * warp-aggregated queue appends), plus the cell-partitioned kernel.
+ * whichever fit in shared memory} x adjacency layout {32-bit rank keys,
+ * 64-bit rank keys, four-slot, compressed; the first three only when every
+ * degree is <= 4}, the 32-bit rank-keyed kernel also with five CTAs per SM
+ * and with 5 or 6 frontier nodes in flight per lane group, plus the
+ * cell-partitioned kernel.  Offers are applied as "read the neighbour's key,
+ * then a non-returning atomicMin" (QDTA_BF_RELAX selects the others).
  *
  * cost_q [L] int32 and roots [R] int32 are device arrays as for
  * qdta_sssp_batch; parent_scratch is a caller-owned device array of R*V int32
