@@ -863,9 +863,10 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                 const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
                 int max_rounds, int qcap, const int *__restrict__ node_ext, int out_mode,
-                const int *__restrict__ rank_link, int skip_parent) {
+                const int *__restrict__ rank_link, int skip_parent, int *root_ovf, const int *redo_only) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
+  __shared__ int s_ovf;
   if (skip_dev && *skip_dev) return;
   const int R = R_dev ? *R_dev : R_host;
   if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
@@ -893,15 +894,23 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   const unsigned long long DMAX = (unsigned long long)(KINF >> LB);
   constexpr int NQ = THREADS / 4;
   const int quad = threadIdx.x >> 2, lane4 = threadIdx.x & 3;
-  for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
-  for (int i = threadIdx.x; i < NBM * W; i += blockDim.x) smq_smem[i] = 0u;
-  __syncthreads();
+  bool ready = false;  // key array and marks initialised (at this CTA's first root)
   for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    // a 64-bit redo after a 32-bit batch solves only the roots that overflowed
+    // (the flag is the same for every thread of the CTA)
+    if (redo_only && __ldcg(&redo_only[r]) == 0) continue;
+    if (!ready) {  // uniform: every thread of the CTA takes the same roots
+      for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
+      for (int i = threadIdx.x; i < NBM * W; i += blockDim.x) smq_smem[i] = 0u;
+      ready = true;
+      __syncthreads();
+    }
     const int z = node_int ? node_int[roots[r]] : roots[r];
     if (threadIdx.x == 0) {
       state[z] = NOLINK;
       sq0[0] = z;
       s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+      s_ovf = 0;
     }
     __syncthreads();
     int ncur = 1, round = 0;
@@ -977,6 +986,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
               const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
               if (cand >= DMAX) {
                 atomicOr(status, ADJ == 3 ? ST_K32 : ST_OVERFLOW);
+                if (ADJ == 3) s_ovf = 1;
               } else {
                 const Key key = (Key)((cand << LB) | (unsigned long long)(unsigned)ent[j].x);
                 if (key < tk[j]) {
@@ -1042,6 +1052,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
       if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
       atomicAdd(roots_counter + 2, my_relax);
     }
+    if (root_ovf && threadIdx.x == 0) root_ovf[r] = s_ovf;  // s_ovf settled at the last round's barrier
     __syncthreads();
     // an early exit (timeout) can leave marks behind: clear both bitmaps
     if (round > max_rounds)
@@ -1107,8 +1118,6 @@ bool sssp_uses_smq(const GraphDev &g) {
   return sssp_group_size() == 1 && sssp_smq_shape_fits(g.V, g.tune_shape) && !getenv("QDTA_BF_NOSMQ");
 }
 
-int sssp_smq_threads(const GraphDev &g) { return kSmqShape[g.tune_shape].threads; }
-int sssp_smq_max_ctas(const GraphDev &g) { return kSmqShape[g.tune_shape].ctas; }
 bool sssp_uses_perm(const GraphDev &g) { return g.node_int != nullptr && sssp_uses_smq(g); }
 // fixed four-slot adjacency: locality order present, every degree <= 4
 bool sssp_uses_ell(const GraphDev &g, int direction) {
@@ -1179,7 +1188,8 @@ __global__ void k32_redo_flag_kernel(unsigned *status, const int *skip_dev, int 
 
 using SmqKernel = void (*)(int, int, const int *, const int4 *, const int *, int, const int *, unsigned long long *,
                           int *, int *, const int *, long long, long long *, unsigned *, const int *,
-                          unsigned long long *, const int *, int, int, const int *, int, const int *, int);
+                          unsigned long long *, const int *, int, int, const int *, int, const int *, int, int *,
+                          const int *);
 
 template <int THREADS, bool ONEBM>
 static SmqKernel smq_kernel_relax(int adj, int relax) {
@@ -1244,17 +1254,19 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
     const int G = sssp_group_size();
     if (sssp_uses_smq(g)) {
       const int adjl = sssp_adj(g, direction);
-      // Two 86.5 KB CTAs per SM need a ~196 KB shared-memory carveout; the
-      // rest of the unified 256 KB stays L1 (the adjacency gathers want it:
-      // 55 ms per batch at 196 KB vs 84 ms at the 228 KB maximum).  Pinning
-      // the preference gives stream launches and graph kernel nodes the
-      // same configuration.  The percentage is rounded up to a supported
-      // size: 85 % of 228 KB asks for 194 KB and gets the 196 KB step (86 %
-      // would round up to 228 KB).  QDTA_SMQ_CARVEOUT overrides, in percent.
+      // Every shape's CTAs fit their marks and queues in the 196 KB
+      // shared-memory step (on the metro grid: two 86.5 KB or four 47.6 KB
+      // CTAs); the rest of the unified 256 KB stays L1, which the memory
+      // requests in flight want (55 ms per batch at 196 KB vs 84 ms at the
+      // 228 KB maximum, measured with two 512-thread CTAs).  Pinning the
+      // preference gives stream launches and graph kernel nodes the same
+      // configuration.  The percentage is rounded up to a supported size:
+      // 85 % of 228 KB asks for 194 KB and gets the 196 KB step (86 % would
+      // round up to 228 KB).  QDTA_SMQ_CARVEOUT overrides, in percent.
       const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
       const int threads = kSmqShape[g.tune_shape].threads;
       const bool perm = g.node_int != nullptr;
-      auto run = [&](SmqKernel kern, const int *skip) {
+      auto run = [&](SmqKernel kern, const int *skip, int *ovf_out, const int *only) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
         COUNT_LAUNCH();
@@ -1262,16 +1274,18 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                                         w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip,
                                         roots_counter, perm ? g.node_int : nullptr, round_limit(g.V),
                                         kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
-                                        g.rank_link[direction], g.skip_parent);
+                                        g.rank_link[direction], g.skip_parent, ovf_out, only);
       };
-      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev);
       if (adjl == 3) {
-        // a distance beyond the 32-bit keys' range: redo the batch with 64-bit
-        // keys on the same packed adjacency (decided on the device, so graph
-        // replays need no host round trip)
+        // a distance beyond the 32-bit keys' range: the roots that met one are
+        // redone with 64-bit keys on the same packed adjacency (decided on the
+        // device, so graph replays need no host round trip)
+        run(smq_kernel_for(g.tune_shape, 3, 2), skip_dev, w.root_ovf, nullptr);
         COUNT_LAUNCH();
         k32_redo_flag_kernel<<<1, 1, 0, s>>>(status, skip_dev, w.fb_skip);
-        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip);
+        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip, nullptr, w.root_ovf);
+      } else {
+        run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev, nullptr, nullptr);
       }
       return;
     }

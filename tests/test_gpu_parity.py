@@ -196,6 +196,27 @@ def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, monkeypatch):
         np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
+def test_sssp_redo_touches_only_the_roots_that_overflowed(mid):
+    """Links entering three nodes cost 2^30: destination trees rooted there
+    pass 2^29 (so those roots are redone with 64-bit keys), the other roots'
+    trees stay below it and keep their 32-bit results; all rows bit-exact."""
+    net, dem, _, og = mid
+    g = Q.Graph(net)
+    rng = np.random.default_rng(31)
+    q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int64)
+    bad = rng.choice(net.n_nodes, 3, replace=False)
+    q[np.isin(net.head, bad)] = 1 << 30
+    q = q.astype(np.int32)
+    others = np.setdiff1d(rng.choice(net.n_nodes, 24, replace=False), bad)
+    roots = np.concatenate([others[:10], bad, others[10:]]).astype(np.int32)
+    p_o, d_o = oracle.sssp(og, q, roots, Q.QDTA_TO_ROOT)
+    big = np.array([d[d < np.iinfo(np.int64).max].max() >= 1 << 29 for d in d_o])
+    assert big.sum() == 3 and set(roots[big]) == set(bad)
+    p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, True)
+    np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+    np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
 def test_sssp_large_irregular_graph_with_ties():
     """Above the shared-memory limit with degrees above 4 (so the compressed
     adjacency, not the four-slot one) and many equal-cost ties: bit-exact
