@@ -795,10 +795,9 @@ static int sssp_grid(const qdta_graph *g, int R) {
   return n < 1 ? 1 : (int)n;
 }
 
-static int sssp_work(qdta_graph *g, int grid, int R_cap, SsspWork *w) {
+static int sssp_work(qdta_graph *g, int grid, SsspWork *w) {
   const size_t V = g->d.V;
   w->slots = grid;
-  RC(ws_get(g, "sssp.root_ovf", (size_t)std::max(R_cap, 1), &w->root_ovf));
   RC(ws_get(g, "sssp.adj", std::max((size_t)g->d.L, (size_t)4 * V), &w->adj));
   RC(ws_get(g, "sssp.fb", 4, &w->fb_skip));
   if (g->sssp_kind == 1) {
@@ -826,7 +825,7 @@ static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots
                     long long *dist, cudaStream_t s, const int *skip_dev = nullptr) {
   SsspWork w;
   const int grid = sssp_grid(g, R_cap);
-  RC(sssp_work(g, grid, R_cap, &w));
+  RC(sssp_work(g, grid, &w));
   ProfEvent pe;
   if (g->sssp_kind == 1) {
     launch_pack_cell_adj(g->d, g->cells, direction, q, w.adj, w.lrev, g->n_lrev[direction], w.xrev,
@@ -1065,7 +1064,7 @@ static int solver_alloc(Solver &S, const std::string &tag, int ring, bool tape_f
   if (tape_f) RC(ws_get(g, tag + ".tape_f", (size_t)S.tape_cap * L, &S.tape_f));
   CK(cudaMemsetAsync(S.counter, 0, 16, S.s));
   SsspWork w;
-  RC(sssp_work(g, sssp_grid(g, S.R_cap), S.R_cap, &w));  // nothing is allocated while capturing
+  RC(sssp_work(g, sssp_grid(g, S.R_cap), &w));  // nothing is allocated while capturing
   return QDTA_OK;
 }
 

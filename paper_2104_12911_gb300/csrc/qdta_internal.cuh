@@ -292,7 +292,6 @@ struct SsspWork {
   unsigned long long *prio;   // cell kernel: [slots][cells] wake priorities
   int4 *xrev;                 // cell kernel: packed external readers (link, reader, q, 0)
   int *fb_skip;               // 32-bit-key batches: 1 unless the 64-bit redo must run
-  int *root_ovf;              // 32-bit-key batches: [roots] 1 where a distance reached 2^29
   int slots;
 };
 

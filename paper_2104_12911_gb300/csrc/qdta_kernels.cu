@@ -863,10 +863,9 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                 const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
                 int max_rounds, int qcap, const int *__restrict__ node_ext, int out_mode,
-                const int *__restrict__ rank_link, int skip_parent, int *root_ovf, const int *redo_only) {
+                const int *__restrict__ rank_link, int skip_parent) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
-  __shared__ int s_ovf;
   if (skip_dev && *skip_dev) return;
   const int R = R_dev ? *R_dev : R_host;
   if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
@@ -894,23 +893,15 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   const unsigned long long DMAX = (unsigned long long)(KINF >> LB);
   constexpr int NQ = THREADS / 4;
   const int quad = threadIdx.x >> 2, lane4 = threadIdx.x & 3;
-  bool ready = false;  // key array and marks initialised (at this CTA's first root)
+  for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
+  for (int i = threadIdx.x; i < NBM * W; i += blockDim.x) smq_smem[i] = 0u;
+  __syncthreads();
   for (int r = blockIdx.x; r < R; r += gridDim.x) {
-    // a 64-bit redo after a 32-bit batch solves only the roots that overflowed
-    // (the flag is the same for every thread of the CTA)
-    if (redo_only && __ldcg(&redo_only[r]) == 0) continue;
-    if (!ready) {  // uniform: every thread of the CTA takes the same roots
-      for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
-      for (int i = threadIdx.x; i < NBM * W; i += blockDim.x) smq_smem[i] = 0u;
-      ready = true;
-      __syncthreads();
-    }
     const int z = node_int ? node_int[roots[r]] : roots[r];
     if (threadIdx.x == 0) {
       state[z] = NOLINK;
       sq0[0] = z;
       s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
-      s_ovf = 0;
     }
     __syncthreads();
     int ncur = 1, round = 0;
@@ -986,7 +977,6 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
               const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
               if (cand >= DMAX) {
                 atomicOr(status, ADJ == 3 ? ST_K32 : ST_OVERFLOW);
-                if (ADJ == 3) s_ovf = 1;
               } else {
                 const Key key = (Key)((cand << LB) | (unsigned long long)(unsigned)ent[j].x);
                 if (key < tk[j]) {
@@ -1052,7 +1042,6 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
       if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
       atomicAdd(roots_counter + 2, my_relax);
     }
-    if (root_ovf && threadIdx.x == 0) root_ovf[r] = s_ovf;  // s_ovf settled at the last round's barrier
     __syncthreads();
     // an early exit (timeout) can leave marks behind: clear both bitmaps
     if (round > max_rounds)
@@ -1188,8 +1177,7 @@ __global__ void k32_redo_flag_kernel(unsigned *status, const int *skip_dev, int 
 
 using SmqKernel = void (*)(int, int, const int *, const int4 *, const int *, int, const int *, unsigned long long *,
                           int *, int *, const int *, long long, long long *, unsigned *, const int *,
-                          unsigned long long *, const int *, int, int, const int *, int, const int *, int, int *,
-                          const int *);
+                          unsigned long long *, const int *, int, int, const int *, int, const int *, int);
 
 template <int THREADS, bool ONEBM>
 static SmqKernel smq_kernel_relax(int adj, int relax) {
@@ -1266,7 +1254,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
       const int threads = kSmqShape[g.tune_shape].threads;
       const bool perm = g.node_int != nullptr;
-      auto run = [&](SmqKernel kern, const int *skip, int *ovf_out, const int *only) {
+      auto run = [&](SmqKernel kern, const int *skip) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
         COUNT_LAUNCH();
@@ -1274,18 +1262,16 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                                         w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip,
                                         roots_counter, perm ? g.node_int : nullptr, round_limit(g.V),
                                         kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
-                                        g.rank_link[direction], g.skip_parent, ovf_out, only);
+                                        g.rank_link[direction], g.skip_parent);
       };
+      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev);
       if (adjl == 3) {
-        // a distance beyond the 32-bit keys' range: the roots that met one are
-        // redone with 64-bit keys on the same packed adjacency (decided on the
-        // device, so graph replays need no host round trip)
-        run(smq_kernel_for(g.tune_shape, 3, 2), skip_dev, w.root_ovf, nullptr);
+        // a distance beyond the 32-bit keys' range: redo the batch with 64-bit
+        // keys on the same packed adjacency (decided on the device, so graph
+        // replays need no host round trip)
         COUNT_LAUNCH();
         k32_redo_flag_kernel<<<1, 1, 0, s>>>(status, skip_dev, w.fb_skip);
-        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip, nullptr, w.root_ovf);
-      } else {
-        run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev, nullptr, nullptr);
+        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip);
       }
       return;
     }
