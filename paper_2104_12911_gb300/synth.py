@@ -7,7 +7,7 @@ shortest paths, no loading) and is the one module that both the CUDA path's
 callers and the CPU oracle's tests draw their inputs from.
 
 The paper's own inputs (a commercial Bay Area map and an activity-based trip
-table, Section 5.1) are not available; these grids stand in for them at the
+table, Section 7.1) are not available; these grids stand in for them at the
 paper's scale (about 0.5M nodes, 1M links and 19M trips per day).
 
 Conventions shared by everything downstream:
