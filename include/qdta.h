@@ -331,6 +331,27 @@ typedef struct qdta_tune_report {
 int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R, int32_t direction,
                   int32_t reps, int32_t *parent_scratch, qdta_tune_report *out_host, void *stream);
 
+/* Scenario metrics of assigned intervals (Section 7.1, the paper's comparison
+ * of a static and a quasi-dynamic morning peak): vehicle kilometres
+ * travelled, average volume over capacity and vehicle hours of delay per
+ * functional class, over the links that carry flow, and the same for the
+ * congested subset (volume over capacity >= congested_voc; the paper uses
+ * 1.0).  flows [N*L] float64 (N <= 65535): trips of interval i on link a at i*L + a,
+ * e.g. the h(i) rows qdta_run_day writes; length_m [L] float64; link_class
+ * [L] int32, links outside [0, n_classes) not counted; n_classes in [1,
+ * QDTA_METRIC_MAX_CLASSES].  With x = f / (C dt_h) and c(f) per Eq. 1,
+ * out [N*n_classes*QDTA_METRICS] float64, row (i, k) =
+ *   links with f > 0, VMT = sum f len / 1000 (veh-km), mean x,
+ *   VHD = sum f (c(f) - c0) * quantum_s / 3600 (veh-h),
+ *   congested links, congested length (km), congested VMT, congested mean x.
+ * Sums are exact fixed-point sums (the result does not depend on the launch
+ * shape).  QDTA_ENONFINITE on a non-finite flow.  Synchronises `stream`. */
+#define QDTA_METRICS 8
+#define QDTA_METRIC_MAX_CLASSES 16
+int qdta_interval_metrics(qdta_graph *g, const double *flows, int32_t N, double dt_s, const double *length_m,
+                          const int32_t *link_class, int32_t n_classes, double congested_voc, double *out,
+                          void *stream);
+
 /* Enable / read / reset per-kernel event timings (plain schedule). */
 int qdta_profile_enable(qdta_graph *g, int32_t on);
 int qdta_profile_read(qdta_graph *g, qdta_profile *out_host);

@@ -91,6 +91,8 @@ def _load():
                 "or_backward": (C.c_int32, [P, P, C.c_double, C.c_int32, C.c_int32, P, P, P, P,
                                             P, P]),
                 "or_replay": (C.c_int32, [P, P, C.c_double, P, C.c_int32, P, P]),
+                "or_interval_metrics": (C.c_int32, [P, P, C.c_int32, C.c_double, P, P, C.c_int32,
+                                                    C.c_double, C.c_double, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -210,6 +212,23 @@ def slope(g: OracleGraph, f, g_fx, dt_s, alpha):
     f = np.ascontiguousarray(f, dtype=np.float64)
     g_fx = np.ascontiguousarray(g_fx, dtype=np.int64)
     return _load().or_slope(g.ref(), _p(f), _p(g_fx), float(dt_s), float(alpha))
+
+
+METRIC_NAMES = ("links", "vmt_km", "voc_mean", "vhd_h", "congested_links", "congested_km",
+                "congested_vmt_km", "congested_voc_mean")
+
+
+def interval_metrics(g: OracleGraph, flows, dt_s, length_m, link_class, n_classes, congested_voc=1.0):
+    """Section 7.1 scenario metrics of N assigned intervals: returns
+    (array [N, n_classes, 8] in METRIC_NAMES order, rc)."""
+    flows = np.ascontiguousarray(np.atleast_2d(flows), dtype=np.float64)
+    n = flows.shape[0]
+    length_m = np.ascontiguousarray(length_m, dtype=np.float64)
+    link_class = np.ascontiguousarray(link_class, dtype=np.int32)
+    out = np.zeros((n, n_classes, 8), dtype=np.float64)
+    rc = _load().or_interval_metrics(g.ref(), _p(flows), n, float(dt_s), _p(length_m), _p(link_class),
+                                     int(n_classes), float(congested_voc), g.quantum_s, _p(out))
+    return out, rc
 
 
 class Tape:

@@ -559,6 +559,67 @@ double or_slope(const or_graph *g, const double *f, const int64_t *g_fx, double 
   return r;
 }
 
+
+/* ------------------------------------------------------------------------ */
+/* Scenario metrics of assigned intervals (Section 7.1: VMT, average volume */
+/* over capacity, vehicle hours of delay by functional class, over links    */
+/* with positive flow; the congested subset has volume over capacity >= a   */
+/* threshold, 1.0 in the paper).  Per interval i and class k, into          */
+/* out[(i * n_classes + k) * 8 + m]:                                         */
+/*   m 0: links with flow > 0                                               */
+/*   m 1: VMT, veh-km        = sum f * len / 1000                           */
+/*   m 2: average VOC        = sum x / count, x = f / (C dt_h)              */
+/*   m 3: VHD, veh-h         = sum f * (c(f) - c0) * quantum_s / 3600       */
+/*   m 4: congested links (x >= threshold)                                  */
+/*   m 5: congested length, km;  m 6: congested VMT;  m 7: congested VOC    */
+/* f = flows[i * L + a] (trips in the interval); c(f) per Eq. 1.  Links     */
+/* whose class is outside [0, n_classes) are not counted.  Every sum is the */
+/* exact sum of per-link terms rounded to 2^-32 (R6).                       */
+/* ------------------------------------------------------------------------ */
+int or_interval_metrics(const or_graph *g, const double *flows, int32_t N, double dt_s,
+                        const double *length_m, const int32_t *link_class, int32_t n_classes,
+                        double congested_voc, double quantum_s, double *out) {
+  if (N < 0 || n_classes < 1 || n_classes > 16 || !(dt_s > 0.0) || !(quantum_s > 0.0)) return OR_EINVAL;
+  const int L = g->n_links;
+  const double dt_h = dt_s / 3600.0;
+  const double hours_per_quantum = quantum_s / 3600.0;
+  int bad = 0;
+  for (int32_t i = 0; i < N; i++) {
+    for (int k = 0; k < n_classes; k++) {
+      i128 vmt = 0, voc = 0, vhd = 0, clen = 0, cvmt = 0, cvoc = 0;
+      int64_t n = 0, cn = 0;
+      for (int a = 0; a < L; a++) {
+        const double f = flows[(int64_t)i * L + a];
+        if (!isfinite(f)) { bad = 1; continue; }
+        if (!(f > 0.0) || link_class[a] != k) continue;
+        const double x = f * inv_cap(g, a, dt_h);
+        const double d = link_cost(g, a, f, dt_h) - (double)g->fftime_q[a];
+        const double fl = f * length_m[a];
+        n += 1;
+        vmt += fx_of(fl, &bad);
+        voc += fx_of(x, &bad);
+        vhd += fx_of(f * d, &bad);
+        if (x >= congested_voc) {
+          cn += 1;
+          clen += fx_of(length_m[a], &bad);
+          cvmt += fx_of(fl, &bad);
+          cvoc += fx_of(x, &bad);
+        }
+      }
+      double *o = out + ((int64_t)i * n_classes + k) * 8;
+      o[0] = (double)n;
+      o[1] = fx_to_double(vmt) * 1e-3;
+      o[2] = n ? fx_to_double(voc) / (double)n : 0.0;
+      o[3] = fx_to_double(vhd) * hours_per_quantum;
+      o[4] = (double)cn;
+      o[5] = fx_to_double(clen) * 1e-3;
+      o[6] = fx_to_double(cvmt) * 1e-3;
+      o[7] = cn ? fx_to_double(cvoc) / (double)cn : 0.0;
+    }
+  }
+  return bad ? OR_ENONFINITE : OR_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Frank-Wolfe per interval (Alg. 2 / Alg. 6).                              */
 /* ------------------------------------------------------------------------ */

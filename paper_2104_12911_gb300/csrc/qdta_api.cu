@@ -963,6 +963,29 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
   return QDTA_OK;
 }
 
+extern "C" int qdta_interval_metrics(qdta_graph *g, const double *flows, int32_t N, double dt_s,
+                                     const double *length_m, const int32_t *link_class, int32_t n_classes,
+                                     double congested_voc, double *out, void *stream) {
+  RC(check_graph(g));
+  if (N < 0 || N > 65535) return fail(QDTA_EINVAL, "qdta_interval_metrics: N must be in [0, 65535]");
+  if (n_classes < 1 || n_classes > QDTA_METRIC_MAX_CLASSES)
+    return fail(QDTA_EINVAL, "qdta_interval_metrics: n_classes must be in [1, %d]", QDTA_METRIC_MAX_CLASSES);
+  if (!(dt_s > 0.0) || !std::isfinite(congested_voc)) return fail(QDTA_EINVAL, "qdta_interval_metrics: bad dt_s or threshold");
+  if (N == 0) return QDTA_OK;
+  if (!out || (g->d.L > 0 && (!flows || !length_m || !link_class)))
+    return fail(QDTA_EINVAL, "qdta_interval_metrics: NULL array");
+  DevGuard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  RC(status_reset(g, s));
+  const size_t words = (size_t)N * n_classes * 16;
+  unsigned long long *acc;
+  RC(ws_get(g, "metrics.acc", words, &acc));
+  CK(cudaMemsetAsync(acc, 0, words * 8, s));
+  launch_metrics(g->d, flows, N, dt_s / 3600.0, length_m, link_class, n_classes, congested_voc, acc, out, g->status,
+                 s);
+  return status_check(g, s);
+}
+
 extern "C" int qdta_load_aon(qdta_graph *g, const int32_t *cost_q, const int32_t *parent_link,
                              const qdta_od *od, int64_t dt_q, int64_t *flow_fx, int32_t *stop_node,
                              void *stream) {

@@ -322,6 +322,10 @@ int sssp_group_size();  // roots per CTA of the global-memory kernel
 // parent slot (*slot_dev, or 0), skipped when root_slot[r] < 0
 void launch_gather_rows(const int *src, int rows, int V, const int *root_slot, int *parent, const int *slot_dev,
                         long long slot_stride, cudaStream_t s);
+// scenario metrics of N intervals' link flows; acc [N*C*16] zeroed by the caller
+void launch_metrics(const GraphDev &g, const double *flows, int N, double dt_h, const double *length_m,
+                    const int *link_class, int C, double congested_voc, unsigned long long *acc, double *out,
+                    unsigned *status, cudaStream_t s);
 bool sssp_uses_smq(const GraphDev &g);   // global-memory launch keeps queues and marks in shared memory
 bool sssp_smq_shape_fits(int V, int shape);
 int sssp_smq_ctas_per_sm(const GraphDev &g, int direction);

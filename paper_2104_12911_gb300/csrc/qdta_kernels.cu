@@ -2168,6 +2168,104 @@ void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *bl
 
 // roots with at least one item, in root order; root_slot maps a root index
 // to its row in the parent arrays (or -1)
+// ============================================================================
+// scenario metrics (Section 7.1): per interval and class, over links with flow
+// ============================================================================
+
+// unsigned 128-bit accumulation with two 64-bit atomics: the low word's carry
+// goes into the high word, so the pair holds the exact total once every add
+// has landed (all terms here are >= 0)
+__device__ __forceinline__ void add_u128(unsigned long long *p, u128 v) {
+  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+  const unsigned long long old = atomicAdd(p, lo);
+  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi | carry) atomicAdd(p + 1, hi + carry);
+}
+
+// acc [N][C][16] words: pairs (lo, hi) at 0 VMT (veh-m), 2 VOC, 4 delay (veh
+// x quanta), 6 congested length (m), 8 congested VMT, 10 congested VOC; 12
+// links with flow, 13 congested links.  blockIdx.y = interval.
+__global__ void __launch_bounds__(256)
+metrics_kernel(int L, const double *__restrict__ flows, const double *__restrict__ length_m,
+               const int *__restrict__ link_class, int C, const int *__restrict__ c0, const double *__restrict__ cap,
+               double dt_h, double alpha, int beta, double congested_voc, unsigned long long *acc,
+               unsigned *status) {
+  __shared__ unsigned long long s[16 * 16];
+  const int i = blockIdx.y;
+  for (int t = threadIdx.x; t < C * 16; t += blockDim.x) s[t] = 0ull;
+  __syncthreads();
+  unsigned bad = 0;
+  const double *fi = flows + (long long)i * L;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
+    const double f = fi[a];
+    if (!isfinite(f)) { bad |= ST_NONFINITE; continue; }
+    const int k = link_class[a];
+    if (!(f > 0.0) || k < 0 || k >= C) continue;
+    const LinkConst kc = link_const(cap[a], dt_h, alpha, beta);
+    const double x = mul(f, kc.inv);
+    const double c0a = (double)c0[a];
+    const double d = sub(link_cost(c0a, kc.inv, alpha, beta, f), c0a);
+    const double fl = mul(f, length_m[a]);
+    unsigned long long *sk = s + k * 16;
+    add_u128(sk + 0, (u128)fx_of(fl, &bad));
+    add_u128(sk + 2, (u128)fx_of(x, &bad));
+    add_u128(sk + 4, (u128)fx_of(mul(f, d), &bad));
+    atomicAdd(sk + 12, 1ull);
+    if (x >= congested_voc) {
+      add_u128(sk + 6, (u128)fx_of(length_m[a], &bad));
+      add_u128(sk + 8, (u128)fx_of(fl, &bad));
+      add_u128(sk + 10, (u128)fx_of(x, &bad));
+      atomicAdd(sk + 13, 1ull);
+    }
+  }
+  if (bad) atomicOr(status, bad);
+  __syncthreads();
+  unsigned long long *g = acc + (long long)i * C * 16;
+  for (int t = threadIdx.x; t < C * 16; t += blockDim.x) {
+    const int w = t & 15;
+    if (w < 12 && (w & 1) == 0) {
+      const u128 v = ((u128)s[t + 1] << 64) | s[t];
+      if (v) add_u128(g + t, v);
+    } else if (w == 12 || w == 13) {
+      if (s[t]) atomicAdd(g + t, s[t]);
+    }
+  }
+}
+
+// out [N][C][8]: links, VMT km, mean VOC, VHD h, congested links, congested
+// km, congested VMT km, congested mean VOC
+__global__ void metrics_finish_kernel(int NC, const unsigned long long *__restrict__ acc, double hours_per_quantum,
+                                      double *__restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NC) return;
+  const unsigned long long *w = acc + (long long)t * 16;
+  auto total = [&](int k) { return fx_to_double((i128)(((u128)w[k + 1] << 64) | w[k])); };
+  const unsigned long long n = w[12], cn = w[13];
+  double *o = out + (long long)t * 8;
+  o[0] = __ull2double_rn(n);
+  o[1] = mul(total(0), 1e-3);
+  o[2] = n ? dvd(total(2), __ull2double_rn(n)) : 0.0;
+  o[3] = mul(total(4), hours_per_quantum);
+  o[4] = __ull2double_rn(cn);
+  o[5] = mul(total(6), 1e-3);
+  o[6] = mul(total(8), 1e-3);
+  o[7] = cn ? dvd(total(10), __ull2double_rn(cn)) : 0.0;
+}
+
+void launch_metrics(const GraphDev &g, const double *flows, int N, double dt_h, const double *length_m,
+                    const int *link_class, int C, double congested_voc, unsigned long long *acc, double *out,
+                    unsigned *status, cudaStream_t s) {
+  if (N <= 0) return;
+  if (g.L > 0) {
+    COUNT_LAUNCH();
+    const int bx = (int)std::min<long long>(cdiv(g.L, 256), 4ll * g.num_sms);
+    metrics_kernel<<<dim3(bx, N), 256, 0, s>>>(g.L, flows, length_m, link_class, C, g.c0, g.cap, dt_h, g.alpha,
+                                               g.beta, congested_voc, acc, status);
+  }
+  COUNT_LAUNCH();
+  metrics_finish_kernel<<<cdiv((long long)N * C, 128), 128, 0, s>>>(N * C, acc, g.quantum_s / 3600.0, out);
+}
+
 // copy free-flow tree rows into the rows of the active roots (row r ->
 // root_slot[r]); int4 copies when rows are 16-byte aligned
 __global__ void gather_rows_kernel(const int *__restrict__ src, int V, const int *__restrict__ root_slot,

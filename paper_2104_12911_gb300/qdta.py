@@ -129,6 +129,7 @@ def lib():
                 "qdta_profile_enable": [P, I32],
                 "qdta_profile_read": [P, P],
                 "qdta_autotune": [P, P, P, I32, I32, I32, P, P, P],
+                "qdta_interval_metrics": [P, P, I32, D, P, P, I32, D, P, P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -249,6 +250,22 @@ def qdta_autotune(g: Graph, cost_q, roots, direction=QDTA_TO_ROOT, reps=2):
     _check(lib().qdta_autotune(g.h, _ptr(cost_q), _ptr(roots), R, int(direction), int(reps), _ptr(scratch),
                                C.byref(rep), _stream()))
     return rep.as_dict()
+
+
+METRIC_NAMES = ("links", "vmt_km", "voc_mean", "vhd_h", "congested_links", "congested_km",
+                "congested_vmt_km", "congested_voc_mean")
+
+
+def qdta_interval_metrics(g: Graph, flows, dt_s, length_m, link_class, n_classes, congested_voc=1.0):
+    """Scenario metrics of N intervals' link flows ([N, L] float64 on the
+    device): returns [N, n_classes, 8] float64 in METRIC_NAMES order."""
+    flows = flows.reshape(-1, g.n_links).contiguous()
+    n = int(flows.shape[0])
+    out = torch.empty((n, int(n_classes), 8), dtype=torch.float64, device=g.device)
+    _check(lib().qdta_interval_metrics(g.h, _ptr(flows), n, float(dt_s), _ptr(length_m.contiguous()),
+                                       _ptr(link_class.contiguous()), int(n_classes), float(congested_voc),
+                                       _ptr(out), _stream()))
+    return out
 
 
 def qdta_load_aon(g: Graph, cost_q, parent, od: DeviceOD, dt_q: int, flow_fx=None, want_stop=False):

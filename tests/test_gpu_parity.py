@@ -531,3 +531,44 @@ def test_autograd_function_matches_oracle_adjoint():
     dd_o, dc_o, _ = oracle.backward(og, ood, 600.0, oracle.STEP_EXACT, tape_o, w.cpu().numpy())
     np.testing.assert_allclose(amounts.grad.cpu().numpy(), dd_o, rtol=1e-9, atol=1e-12 * np.abs(dd_o).max())
     np.testing.assert_allclose(cap.grad.cpu().numpy(), dc_o, rtol=1e-9, atol=1e-12 * max(np.abs(dc_o).max(), 1e-300))
+
+
+# ---------------------------------------------------------------------------
+# Scenario metrics (Section 7.1) of a day's h(i) rows, bit-exact against the oracle
+def test_interval_metrics_of_a_day_match_the_oracle():
+    day = _day_case(n_int=4)
+    net = day.net
+    g = Q.Graph(net)
+    zones = T(day.zones, np.int32)
+    dd = [Q.DeviceOD(zones, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in day.demand]
+    f_g, _, _, _ = Q.qdta_run_day(g, dd, 900.0, Q.make_params("sweep8", "paper_obj", 60, schedule="graph"))
+    cls = net.link_class.astype(np.int32)
+    n_cls = int(cls.max()) + 1
+    got = Q.qdta_interval_metrics(g, f_g, 900.0, T(net.length_m, np.float64), T(cls, np.int32), n_cls)
+    want, rc = oracle.interval_metrics(oracle.OracleGraph(net), f_g.cpu().numpy(), 900.0, net.length_m, cls, n_cls)
+    assert rc == 0
+    np.testing.assert_array_equal(got.cpu().numpy(), want)
+    assert want[:, :, 0].sum() > 0
+
+
+def test_interval_metrics_edge_cases():
+    inst = synth.config_small(0)
+    net = inst.net
+    g = Q.Graph(net)
+    og = oracle.OracleGraph(net)
+    rng = np.random.default_rng(17)
+    L = net.n_links
+    flows = rng.uniform(0, 400, (3, L)) * (rng.random((3, L)) < 0.7)
+    length = rng.uniform(100, 400, L)
+    cls = rng.integers(-1, 6, L).astype(np.int32)  # -1 and 5 fall outside 5 classes
+    got = Q.qdta_interval_metrics(g, T(flows, np.float64), 900.0, T(length, np.float64), T(cls, np.int32), 5, 0.8)
+    want, rc = oracle.interval_metrics(og, flows, 900.0, length, cls, 5, 0.8)
+    assert rc == 0
+    np.testing.assert_array_equal(got.cpu().numpy(), want)
+    empty = Q.qdta_interval_metrics(g, T(np.zeros((0, L)), np.float64), 900.0, T(length, np.float64),
+                                    T(cls, np.int32), 5)
+    assert tuple(empty.shape) == (0, 5, 8)
+    flows[1, 7] = np.nan
+    with pytest.raises(Q.QdtaError) as e:
+        Q.qdta_interval_metrics(g, T(flows, np.float64), 900.0, T(length, np.float64), T(cls, np.int32), 5)
+    assert e.value.code == Q.QDTA_ENONFINITE

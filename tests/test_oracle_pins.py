@@ -491,3 +491,57 @@ def test_adjoint_matches_finite_differences(mode):
                 vals.append(loss(ff))
             fd = (vals[0] - vals[1]) / (2 * hc)
             assert abs(fd - dc[a]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(dc).max()), (a, fd, dc[a])
+
+
+# ---------------------------------------------------------------------------
+# Scenario metrics (Section 7.1): VMT, average VOC, VHD by class; the congested
+# subset has VOC >= 1.0.  Pinned against exact rationals on a hand-sized case.
+def test_interval_metrics_against_exact_rationals():
+    from fractions import Fraction as Fr
+    # four links, 10 s free flow (1000 quanta), 400 veh/h: over 15 min the capacity is
+    # 100 trips, so the flows below give volume/capacity 0.5, 1.0, 1.5 and 0 exactly
+    net = synth.chain_network([10.0] * 4, [400.0] * 4)
+    g = oracle.OracleGraph(net)
+    flows = np.array([[50.0, 100.0, 150.0, 0.0]])
+    length = np.array([100.0, 200.0, 300.0, 400.0])
+    cls = np.array([0, 1, 0, 1], np.int32)
+    out, rc = oracle.interval_metrics(g, flows, 900.0, length, cls, 2)
+    assert rc == 0
+    x = [Fr(1, 2), Fr(1), Fr(3, 2)]
+    f = [Fr(50), Fr(100), Fr(150)]
+    delay_q = [f[a] * 1000 * Fr(15, 100) * x[a] ** 4 for a in range(3)]  # f * (c - c0), quanta
+    to_h = Fr(1, 100) / 3600
+    # class 0: links 0 and 2; class 1: link 1 (link 3 carries no flow and is not counted)
+    want0 = [2, Fr(50 * 100 + 150 * 300, 1000), (x[0] + x[2]) / 2, (delay_q[0] + delay_q[2]) * to_h,
+             1, Fr(300, 1000), Fr(150 * 300, 1000), x[2]]
+    want1 = [1, Fr(100 * 200, 1000), x[1], delay_q[1] * to_h, 1, Fr(200, 1000), Fr(100 * 200, 1000), x[1]]
+    for got, want in ((out[0, 0], want0), (out[0, 1], want1)):
+        for m, w in enumerate(want):
+            assert abs(got[m] - float(w)) <= 1e-12 * max(1.0, abs(float(w))), (m, got[m], float(w))
+
+
+def test_interval_metrics_classes_partition_the_network():
+    inst = synth.config_small(0)
+    net = inst.net
+    g = oracle.OracleGraph(net)
+    rng = np.random.default_rng(5)
+    flows = rng.uniform(0, 250, (3, g.n_links)) * (rng.random((3, g.n_links)) < 0.8)
+    length = rng.uniform(100, 400, g.n_links)
+    cls = rng.integers(0, 3, g.n_links).astype(np.int32)
+    per, rc1 = oracle.interval_metrics(g, flows, 900.0, length, cls, 3)
+    one, rc2 = oracle.interval_metrics(g, flows, 900.0, length, np.zeros(g.n_links, np.int32), 1)
+    assert rc1 == 0 and rc2 == 0
+    for i in range(3):
+        assert per[i, :, 0].sum() == one[i, 0, 0] == np.count_nonzero(flows[i] > 0)
+        assert per[i, :, 4].sum() == one[i, 0, 4]
+        for m in (1, 3, 5, 6):  # additive quantities
+            assert abs(per[i, :, m].sum() - one[i, 0, m]) <= 1e-12 * one[i, 0, m]
+        # averages are count-weighted means of the class averages
+        for m, c in ((2, 0), (7, 4)):
+            assert abs((per[i, :, m] * per[i, :, c]).sum() / one[i, 0, c] - one[i, 0, m]) <= 1e-12
+        assert np.all(per[i, :, 6] <= per[i, :, 1]) and np.all(per[i, :, 4] <= per[i, :, 0])
+        # a class index outside [0, n_classes) is not counted
+    bad = cls.copy()
+    bad[:10] = 7
+    part, rc3 = oracle.interval_metrics(g, flows, 900.0, length, bad, 3)
+    assert rc3 == 0 and part[:, :, 0].sum() == np.count_nonzero(flows[:, 10:] > 0)
