@@ -53,10 +53,13 @@ class OD(C.Structure):
                 ("root_idx", C.c_void_p), ("src", C.c_void_p), ("amount_fx", C.c_void_p)]
 
 
+OBJ_UE, OBJ_SO = 0, 1  # user equilibrium (Beckmann) / system optimum (total cost)
+
+
 class Params(C.Structure):
     _fields_ = [("step", C.c_int32), ("stop", C.c_int32), ("max_iter", C.c_int32),
                 ("ls_max", C.c_int32), ("tol", C.c_double), ("ls_dx", C.c_double),
-                ("ls_t1", C.c_double), ("ls_t2", C.c_double)]
+                ("ls_t1", C.c_double), ("ls_t2", C.c_double), ("objective", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -144,8 +147,8 @@ class OracleOD:
 
 
 def make_params(step=STEP_MSA, stop=STOP_NONE, max_iter=20, tol=1e-4, ls_max=20,
-                ls_dx=1e-4, ls_t1=1e-4, ls_t2=1e-4) -> Params:
-    return Params(step, stop, max_iter, ls_max, tol, ls_dx, ls_t1, ls_t2)
+                ls_dx=1e-4, ls_t1=1e-4, ls_t2=1e-4, objective=OBJ_UE) -> Params:
+    return Params(step, stop, max_iter, ls_max, tol, ls_dx, ls_t1, ls_t2, objective)
 
 
 # --------------------------------------------------------------------------

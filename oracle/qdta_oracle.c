@@ -72,7 +72,11 @@ typedef struct {
 typedef struct {
   int32_t step, stop, max_iter, ls_max;
   double tol, ls_dx, ls_t1, ls_t2;
+  int32_t objective;  /* OBJ_UE (Beckmann, user equilibrium) or OBJ_SO (total cost, system optimum) */
 } or_params;
+
+#define OBJ_UE 0
+#define OBJ_SO 1
 
 typedef struct {
   int32_t iterations;   /* accepted FW steps after the initial AON */
@@ -188,6 +192,46 @@ static double beckmann(const or_graph *g, int a, double t, double dt_h) {
   double w = kb * p;
   double u = t + w;
   return (double)g->fftime_q[a] * u;
+}
+
+/* System optimum (the alternative objective of Sections 3 and 8): the total
+ * cost Z_a(t) = t * c_a(t) replaces the Beckmann integral, and its derivative
+ * m_a(t) = c_a(t) + t * c_a'(t) = c0 * (1 + alpha (beta+1) x^beta), the
+ * marginal cost, replaces c_a in routing and in the slope of the line search. */
+static double link_total(const or_graph *g, int a, double t, double dt_h) {
+  return t * link_cost(g, a, t, dt_h);
+}
+
+static double link_marginal(const or_graph *g, int a, double t, double dt_h) {
+  double x = t * inv_cap(g, a, dt_h);
+  double p = pow_n(x, g->beta);
+  double k = g->alpha * (double)(g->beta + 1);
+  double w = k * p;
+  double u = 1.0 + w;
+  return (double)g->fftime_q[a] * u;
+}
+
+/* d m_a / d t = c0 alpha beta (beta+1) x^(beta-1) / cp */
+static double link_marginal_dt(const or_graph *g, int a, double t, double dt_h) {
+  double inv = inv_cap(g, a, dt_h);
+  double x = t * inv;
+  double p = g->beta > 1 ? pow_n(x, g->beta - 1) : 1.0;
+  double w = (double)g->fftime_q[a] * g->alpha;
+  w = w * (double)g->beta;
+  w = w * (double)(g->beta + 1);
+  w = w * p;
+  return w * inv;
+}
+
+/* objective term, slope cost and slope-cost derivative of link a */
+static double obj_term(const or_graph *g, int a, double t, double dt_h, int obj) {
+  return obj == OBJ_SO ? link_total(g, a, t, dt_h) : beckmann(g, a, t, dt_h);
+}
+static double obj_cost(const or_graph *g, int a, double t, double dt_h, int obj) {
+  return obj == OBJ_SO ? link_marginal(g, a, t, dt_h) : link_cost(g, a, t, dt_h);
+}
+static double obj_cost_dt(const or_graph *g, int a, double t, double dt_h, int obj) {
+  return obj == OBJ_SO ? link_marginal_dt(g, a, t, dt_h) : link_cost_dt(g, a, t, dt_h);
 }
 
 /* nearest integer quantum count, ties up, clamped to [1, 2^31-1] */
@@ -406,33 +450,34 @@ static double step_flow(double f, double gg, double alpha) {
   return f + s;
 }
 
-/* phi(alpha) = sum_a fx(B_a(t_a(alpha)))  (Eq. 6 along the search line, Eq. 8) */
+/* phi(alpha) = sum_a fx(B_a(t_a(alpha)))  (Eq. 6 along the search line, Eq. 8);
+ * Z_a instead of B_a for the system optimum */
 static i128 phi_sum(const or_graph *g, const double *f, const double *gd, double alpha,
-                    double dt_h, int *bad) {
+                    double dt_h, int obj, int *bad) {
   i128 s = 0;
-  for (int a = 0; a < g->n_links; a++) s += fx_of(beckmann(g, a, step_flow(f[a], gd[a], alpha), dt_h), bad);
+  for (int a = 0; a < g->n_links; a++) s += fx_of(obj_term(g, a, step_flow(f[a], gd[a], alpha), dt_h, obj), bad);
   return s;
 }
 
 /* phi'(alpha) = sum_a fx((g_a - f_a) * c_a(t_a(alpha)))  (exact derivative) */
 static i128 dphi_sum(const or_graph *g, const double *f, const double *gd, double alpha,
-                     double dt_h, int *bad) {
+                     double dt_h, int obj, int *bad) {
   i128 s = 0;
   for (int a = 0; a < g->n_links; a++) {
     double d = gd[a] - f[a];
-    s += fx_of(d * link_cost(g, a, step_flow(f[a], gd[a], alpha), dt_h), bad);
+    s += fx_of(d * obj_cost(g, a, step_flow(f[a], gd[a], alpha), dt_h, obj), bad);
   }
   return s;
 }
 
 /* phi''(alpha) = sum_a fx((g_a - f_a)^2 * c_a'(t_a)) */
 static i128 ddphi_sum(const or_graph *g, const double *f, const double *gd, double alpha,
-                      double dt_h, int *bad) {
+                      double dt_h, int obj, int *bad) {
   i128 s = 0;
   for (int a = 0; a < g->n_links; a++) {
     double d = gd[a] - f[a];
     double dd = d * d;
-    s += fx_of(dd * link_cost_dt(g, a, step_flow(f[a], gd[a], alpha), dt_h), bad);
+    s += fx_of(dd * obj_cost_dt(g, a, step_flow(f[a], gd[a], alpha), dt_h, obj), bad);
   }
   return s;
 }
@@ -444,9 +489,9 @@ static double ls_paper_qn3(const or_graph *g, const double *f, const double *gd,
   double alpha = 2.0 / (2.0 + (double)j);
   double dx = p->ls_dx;
   for (int l = 1; l < p->ls_max; l++) {
-    i128 ym = phi_sum(g, f, gd, alpha - dx, dt_h, bad);
-    i128 y0 = phi_sum(g, f, gd, alpha, dt_h, bad);
-    i128 yp = phi_sum(g, f, gd, alpha + dx, dt_h, bad);
+    i128 ym = phi_sum(g, f, gd, alpha - dx, dt_h, p->objective, bad);
+    i128 y0 = phi_sum(g, f, gd, alpha, dt_h, p->objective, bad);
+    i128 yp = phi_sum(g, f, gd, alpha + dx, dt_h, p->objective, bad);
     (*passes)++;
     double c0 = fx_to_double(y0);
     double d1 = fx_to_double(yp - ym) / (2.0 * dx);
@@ -468,7 +513,7 @@ static double ls_sweep8(const or_graph *g, const double *f, const double *gd, do
                         const or_params *p, int *passes, int *bad) {
   i128 D[8];
   double a[8];
-  for (int m = 0; m < 8; m++) { a[m] = (double)m / 7.0; D[m] = dphi_sum(g, f, gd, a[m], dt_h, bad); }
+  for (int m = 0; m < 8; m++) { a[m] = (double)m / 7.0; D[m] = dphi_sum(g, f, gd, a[m], dt_h, p->objective, bad); }
   (*passes)++;
   if (D[7] <= 0) return 1.0;
   if (D[0] >= 0) return 0.0;
@@ -478,7 +523,7 @@ static double ls_sweep8(const or_graph *g, const double *f, const double *gd, do
   i128 Dlo = D[ms - 1], Dhi = D[ms];
   while (hi - lo >= p->ls_t2 && *passes < p->ls_max) {
     double step = (hi - lo) / 9.0;
-    for (int m = 0; m < 8; m++) { a[m] = lo + step * (double)(m + 1); D[m] = dphi_sum(g, f, gd, a[m], dt_h, bad); }
+    for (int m = 0; m < 8; m++) { a[m] = lo + step * (double)(m + 1); D[m] = dphi_sum(g, f, gd, a[m], dt_h, p->objective, bad); }
     (*passes)++;
     int mf = 0;
     while (mf < 8 && D[mf] < 0) mf++;
@@ -498,16 +543,16 @@ static double ls_sweep8(const or_graph *g, const double *f, const double *gd, do
 /* Newton on the exact slope to |step| < 1e-14 inside a maintained bracket;
  * used by the adjoint so that phi'(alpha*) = 0 holds to rounding. */
 static double ls_exact(const or_graph *g, const double *f, const double *gd, double dt_h,
-                       int *passes, int *bad) {
-  i128 D0 = dphi_sum(g, f, gd, 0.0, dt_h, bad);
-  i128 D1 = dphi_sum(g, f, gd, 1.0, dt_h, bad);
+                       int obj, int *passes, int *bad) {
+  i128 D0 = dphi_sum(g, f, gd, 0.0, dt_h, obj, bad);
+  i128 D1 = dphi_sum(g, f, gd, 1.0, dt_h, obj, bad);
   *passes += 2;
   if (D1 <= 0) return 1.0;
   if (D0 >= 0) return 0.0;
   double lo = 0.0, hi = 1.0, alpha = 0.5;
   for (int it = 0; it < 200; it++) {
-    i128 D = dphi_sum(g, f, gd, alpha, dt_h, bad);
-    double H = fx_to_double(ddphi_sum(g, f, gd, alpha, dt_h, bad));
+    i128 D = dphi_sum(g, f, gd, alpha, dt_h, obj, bad);
+    double H = fx_to_double(ddphi_sum(g, f, gd, alpha, dt_h, obj, bad));
     (*passes)++;
     if (D == 0) return alpha;
     if (D < 0) lo = alpha; else hi = alpha;
@@ -525,7 +570,7 @@ static double choose_step(const or_graph *g, const double *f, const double *gd, 
     case STEP_MSA: return 1.0 / ((double)k + 1.0);
     case STEP_PAPER_QN3: return ls_paper_qn3(g, f, gd, dt_h, k - 1, p, passes, bad);
     case STEP_SWEEP8: return ls_sweep8(g, f, gd, dt_h, p, passes, bad);
-    default: return ls_exact(g, f, gd, dt_h, passes, bad);
+    default: return ls_exact(g, f, gd, dt_h, p->objective, passes, bad);
   }
 }
 
@@ -554,7 +599,7 @@ double or_slope(const or_graph *g, const double *f, const int64_t *g_fx, double 
   int L = g->n_links, bad = 0;
   double *gd = (double *)malloc((size_t)L * 8 + 8);
   for (int a = 0; a < L; a++) gd[a] = (double)g_fx[a] * 0x1p-32;
-  double r = fx_to_double(dphi_sum(g, f, gd, alpha, dt_s / 3600.0, &bad));
+  double r = fx_to_double(dphi_sum(g, f, gd, alpha, dt_s / 3600.0, OBJ_UE, &bad));
   free(gd);
   return r;
 }
@@ -637,8 +682,9 @@ static int64_t dt_quanta(const or_graph *g, double dt_s) {
   return (int64_t)floor(dt_s / g->quantum_s + 0.5);
 }
 
-/* one AON: trees from q, loading with truncation under q */
-static int aon(const or_graph *g, const adjacency *adj, const int32_t *q, const or_od *od,
+/* one AON: trees from the routing costs q, loading with truncation under the
+ * travel times qt (the same array for the user equilibrium) */
+static int aon(const or_graph *g, const adjacency *adj, const int32_t *q, const int32_t *qt, const or_od *od,
                int64_t dt_q, int32_t *parent, int64_t *dist, const uint8_t *root_used,
                int64_t *g_fx, heap *h) {
   int64_t V = g->n_nodes;
@@ -647,7 +693,21 @@ static int aon(const or_graph *g, const adjacency *adj, const int32_t *q, const 
     if (dijkstra_one(g, adj, q, od->roots[r], DIR_TO_ROOT, parent + r * V, dist, h)) return OR_ENOMEM;
   }
   memset(g_fx, 0, (size_t)g->n_links * 8);
-  return or_load(g, q, parent, od, dt_q, g_fx, NULL);
+  return or_load(g, qt, parent, od, dt_q, g_fx, NULL);
+}
+
+/* routing costs q and travel times qt at flows f: q = qt = quant(c(f)) for the
+ * user equilibrium, q = quant(m(f)) (marginal cost) for the system optimum */
+static int route_costs(const or_graph *g, const double *f, double dt_s, int obj, int32_t *q, int32_t *qt) {
+  int rc = or_bpr(g, f, dt_s, NULL, qt);
+  if (obj != OBJ_SO) {
+    memcpy(q, qt, (size_t)g->n_links * 4);
+    return rc;
+  }
+  int bad = 0;
+  const double dt_h = dt_s / 3600.0;
+  for (int a = 0; a < g->n_links; a++) q[a] = quantize(link_marginal(g, a, f[a], dt_h), &bad);
+  return bad ? OR_ENONFINITE : rc;
 }
 
 static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or_params *p,
@@ -660,6 +720,7 @@ static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or
   adjacency adj;
   if (build_adj(g, &adj)) return OR_ENOMEM;
   int32_t *q = (int32_t *)malloc((size_t)L * 4 + 4);
+  int32_t *qt = (int32_t *)malloc((size_t)L * 4 + 4);
   int32_t *parent = (int32_t *)malloc((size_t)(od->n_roots ? od->n_roots : 1) * V * 4);
   int64_t *dist = (int64_t *)malloc((size_t)V * 8);
   int64_t *g_fx = (int64_t *)malloc((size_t)L * 8 + 8);
@@ -667,7 +728,7 @@ static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or
   double *fn = (double *)malloc((size_t)L * 8 + 8);
   uint8_t *used = (uint8_t *)calloc((size_t)od->n_roots + 1, 1);
   heap h = {0};
-  if (!q || !parent || !dist || !g_fx || !gd || !fn || !used) { rc = OR_ENOMEM; goto done; }
+  if (!q || !qt || !parent || !dist || !g_fx || !gd || !fn || !used) { rc = OR_ENOMEM; goto done; }
   for (int64_t k = 0; k < od->n_items; k++) used[od->root_idx[k]] = 1;
   memset(st, 0, sizeof(*st));
   st->rel_gap = NAN;
@@ -683,8 +744,8 @@ static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or
                 or_bpr(g, f_out, dt_s, NULL, tape->q); }
     goto done;
   }
-  if (or_bpr(g, f_out, dt_s, NULL, q)) { rc = OR_ENONFINITE; goto done; }
-  rc = aon(g, &adj, q, od, dt_q, parent, dist, used, g_fx, &h);
+  if (route_costs(g, f_out, dt_s, p->objective, q, qt)) { rc = OR_ENONFINITE; goto done; }
+  rc = aon(g, &adj, q, qt, od, dt_q, parent, dist, used, g_fx, &h);
   st->aon_calls = 1;
   if (rc) goto done;
   for (int a = 0; a < L; a++) f_out[a] = (double)g_fx[a] * 0x1p-32;
@@ -697,8 +758,8 @@ static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or
 
   for (int k = 1;; k++) {
     if (k > p->max_iter) { if (p->stop != STOP_NONE) rc = OR_NOTCONV; break; }
-    if (or_bpr(g, f_out, dt_s, NULL, q)) { rc = OR_ENONFINITE; break; }
-    rc = aon(g, &adj, q, od, dt_q, parent, dist, used, g_fx, &h);
+    if (route_costs(g, f_out, dt_s, p->objective, q, qt)) { rc = OR_ENONFINITE; break; }
+    rc = aon(g, &adj, q, qt, od, dt_q, parent, dist, used, g_fx, &h);
     st->aon_calls++;
     if (rc) break;
     for (int a = 0; a < L; a++) gd[a] = (double)g_fx[a] * 0x1p-32;
@@ -723,8 +784,8 @@ static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or
     if (p->stop == STOP_PAPER_OBJ) {
       i128 c1 = 0, c2 = 0;
       for (int a = 0; a < L; a++) {
-        c1 += fx_of(beckmann(g, a, f_out[a], dt_h), &bad);
-        c2 += fx_of(beckmann(g, a, fn[a], dt_h), &bad);
+        c1 += fx_of(obj_term(g, a, f_out[a], dt_h, p->objective), &bad);
+        c2 += fx_of(obj_term(g, a, fn[a], dt_h, p->objective), &bad);
       }
       double rel = fabs(fx_to_double(c1 - c2)) / fx_to_double(c1);
       st->rel_gap = rel;
@@ -743,11 +804,11 @@ static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or
   if (bad && rc >= 0) rc = OR_ENONFINITE;
   {
     i128 obj = 0;
-    for (int a = 0; a < L; a++) obj += fx_of(beckmann(g, a, f_out[a], dt_h), &bad);
+    for (int a = 0; a < L; a++) obj += fx_of(obj_term(g, a, f_out[a], dt_h, p->objective), &bad);
     st->objective = fx_to_double(obj);
   }
 done:
-  free(q); free(parent); free(dist); free(g_fx); free(gd); free(fn); free(used); free(h.a);
+  free(q); free(qt); free(parent); free(dist); free(g_fx); free(gd); free(fn); free(used); free(h.a);
   free_adj(&adj);
   return rc;
 }
@@ -956,7 +1017,7 @@ int32_t or_backward(const or_graph *g, const or_od *od, double dt_s, int32_t ste
   for (int a = 0; a < L; a++) dL_dcap[a] = 0.0;
   for (int k = K; k >= 0 && rc == OR_OK; k--) {
     const int32_t *qk = tape_q + (int64_t)k * L;
-    rc = aon(g, &adj, qk, od, dt_q, parent, dist, used, g_fx, &h);  /* recompute tree k and g_k */
+    rc = aon(g, &adj, qk, qk, od, dt_q, parent, dist, used, g_fx, &h);  /* recompute tree k and g_k */
     if (rc) break;
     if (k == 0) {
       memcpy(gbar, lam, (size_t)L * 8);
@@ -1034,7 +1095,7 @@ int32_t or_replay(const or_graph *g, const or_od *od, double dt_s, const or_para
   int rc = OR_OK, bad = 0;
   for (int64_t k = 0; k < od->n_items; k++) used[od->root_idx[k]] = 1;
   for (int k = 0; k <= K && rc == OR_OK; k++) {
-    rc = aon(g, &adj, tape_q + (int64_t)k * L, od, dt_q, parent, dist, used, g_fx, &h);
+    rc = aon(g, &adj, tape_q + (int64_t)k * L, tape_q + (int64_t)k * L, od, dt_q, parent, dist, used, g_fx, &h);
     if (rc) break;
     for (int a = 0; a < L; a++) gd[a] = (double)g_fx[a] * 0x1p-32;
     if (k == 0) { memcpy(f_out, gd, (size_t)L * 8); continue; }
@@ -1061,4 +1122,11 @@ int32_t or_replay(const or_graph *g, const or_od *od, double dt_s, const or_para
  *  R5 Alg. 4 re-truncates the full (untruncated) path of every AON with the
  *     final costs, weighted by the step weights of the convex combination.
  *  R6 sums over links are exact sums of terms rounded to 2^-32.
+ *  R14 The system optimum (Section 3 names it beside the user equilibrium the
+ *     paper solves; Sections 1 and 8 ask for other objectives) minimises the
+ *     total cost sum t c(t): routing uses the quantised marginal cost
+ *     m = c + t c', the line search the total cost and its slope, the stop
+ *     rules the total cost and the gap in marginal costs, while loading and
+ *     truncation keep the travel times c (a trip still ends its interval
+ *     after dt of travel).
  */

@@ -545,3 +545,88 @@ def test_interval_metrics_classes_partition_the_network():
     bad[:10] = 7
     part, rc3 = oracle.interval_metrics(g, flows, 900.0, length, bad, 3)
     assert rc3 == 0 and part[:, :, 0].sum() == np.count_nonzero(flows[:, 10:] > 0)
+
+
+# ---------------------------------------------------------------------------
+# System-optimal objective (the alternative named in Sections 3 and 8): total
+# cost sum f c(f), routing on marginal costs m = c + f c'.
+def _solve_so(net, demand_trips, mode, it=2000, tol=1e-8, objective=oracle.OBJ_SO):
+    g = oracle.OracleGraph(net)
+    od = oracle.OracleOD(np.array([1], np.int32), np.array([0], np.int32), np.array([0], np.int32),
+                         np.array([int(demand_trips * (1 << 32))], np.int64))
+    return oracle.assign_interval(g, od, 3600.0, oracle.make_params(mode, oracle.STOP_REL_GAP, it, tol,
+                                                                    objective=objective))
+
+
+def test_system_optimum_two_identical_links_split_evenly():
+    for mode in (oracle.STEP_SWEEP8, oracle.STEP_EXACT):
+        f, st, rc = _solve_so(_two_links(60000, 60000, 1000.0, 1000.0), 3000.0, mode, it=400, tol=1e-7)
+        assert rc >= 0 and abs(f[0] - 1500.0) <= 1e-6 * 3000.0
+
+
+def test_system_optimum_equalises_marginal_costs():
+    net = _two_links(60000, 72000, 1200.0, 800.0)
+    D = 2500.0
+
+    def root(fn):
+        lo, hi = 0.0, D
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if fn(mid) < 0 else (lo, mid)
+        return 0.5 * (lo + hi)
+
+    # marginal cost c0 (1 + alpha (beta+1) x^beta) of BPR, hourly flows over one hour
+    x_so = root(lambda x: 60000 * (1 + 0.75 * (x / 1200.0) ** 4) - 72000 * (1 + 0.75 * ((D - x) / 800.0) ** 4))
+    x_ue = root(lambda x: 60000 * (1 + 0.15 * (x / 1200.0) ** 4) - 72000 * (1 + 0.15 * ((D - x) / 800.0) ** 4))
+    assert abs(x_so - x_ue) > 10 * 2e-3 * D  # the two objectives are told apart
+    for mode in (oracle.STEP_SWEEP8, oracle.STEP_EXACT, oracle.STEP_PAPER_QN3):
+        f, st, rc = _solve_so(net, D, mode)
+        assert abs(f[0] - x_so) <= 2e-3 * D, (mode, f, x_so)
+
+
+def test_system_optimum_total_cost_not_above_equilibrium_braess():
+    # Braess network: the equilibrium uses the bridge and costs more in total than the optimum
+    tail = np.array([0, 0, 1, 1, 2], np.int32)
+    head = np.array([1, 2, 2, 3, 3], np.int32)
+    spec = {(0, 1): (60000, 500.0), (0, 2): (150000, 1e9), (1, 2): (6000, 1e9),
+            (1, 3): (150000, 1e9), (2, 3): (60000, 500.0)}
+    fq = np.array([spec[(int(a), int(b))][0] for a, b in zip(tail, head)], np.int32)
+    cp = np.array([spec[(int(a), int(b))][1] for a, b in zip(tail, head)], np.float64)
+    net = synth.Network(n_nodes=4, tail=tail, head=head, fftime_q=fq, capacity=cp, length_m=np.zeros(5),
+                        link_class=np.zeros(5, np.int8), x=np.zeros(4), y=np.zeros(4))
+    g = oracle.OracleGraph(net)
+    od = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([0], np.int32),
+                         np.array([int(1000.0 * (1 << 32))], np.int64))
+
+    def total(obj):
+        f, st, rc = oracle.assign_interval(g, od, 3600.0, oracle.make_params(
+            oracle.STEP_EXACT, oracle.STOP_REL_GAP, 5000, 1e-7, objective=obj))
+        assert rc >= 0
+        _, cost, _ = oracle.bpr(g, f, 3600.0)
+        return float((f * cost).sum()), st
+
+    z_ue, _ = total(oracle.OBJ_UE)
+    z_so, st_so = total(oracle.OBJ_SO)
+    assert z_so <= z_ue * (1 + 1e-9) and z_so < z_ue * (1 - 1e-3)
+    # the optimum's reported objective is its total cost, in quanta x trips (cost above is in seconds)
+    assert abs(st_so["objective"] * net.quantum_s - z_so) <= 1e-9 * z_so
+
+
+def test_system_optimum_equals_equilibrium_for_constant_costs():
+    """alpha = 0: marginal cost = cost, total cost and Beckmann integral agree
+    operation for operation, so both objectives give the same bits."""
+    inst = synth.scaled_day(synth.config_small(0), 40000, n_intervals=2, seed=3)
+    net = inst.net
+    net0 = synth.Network(n_nodes=net.n_nodes, tail=net.tail, head=net.head, fftime_q=net.fftime_q,
+                         capacity=net.capacity, length_m=net.length_m, link_class=net.link_class, x=net.x,
+                         y=net.y, alpha=0.0, beta=net.beta, quantum_s=net.quantum_s)
+    g = oracle.OracleGraph(net0)
+    od = oracle.OracleOD.of(inst.demand[1])
+    out = []
+    for obj in (oracle.OBJ_UE, oracle.OBJ_SO):
+        f, st, rc = oracle.assign_interval(g, od, 900.0, oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_NONE, 5,
+                                                                            objective=obj))
+        assert rc >= 0
+        out.append((f, st["iterations"], st["ls_passes"]))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
