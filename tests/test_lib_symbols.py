@@ -55,6 +55,7 @@ def test_null_handles_are_rejected_without_touching_a_gpu():
     assert lib.qdta_autotune(None, None, None, 4, 0, 1, None, ctypes.byref(rep), None) == Q.QDTA_EINVAL
     assert lib.qdta_sssp_kernel_name(None, 0) == b""
     assert lib.qdta_last_error()
+    assert lib.qdta_interval_metrics(None, None, 1, 900.0, None, None, 3, 1.0, None, None) == Q.QDTA_EINVAL
 
 
 def test_tune_report_layout_matches_the_header():
