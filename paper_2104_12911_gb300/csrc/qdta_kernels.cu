@@ -887,7 +887,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   int *sq0 = reinterpret_cast<int *>(smq_smem + NBM * W), *sq1 = sq0 + qcap;
   const size_t b = blockIdx.x;
   Key *state = reinterpret_cast<Key *>(g_state) + b * (size_t)V;
-  int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;  // overflow beyond SMQ_CAP
+  int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;  // overflow beyond qcap entries
   if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
   const Key NOLINK = (Key)((1ull << LB) - 1ull);
   const unsigned long long DMAX = (unsigned long long)(KINF >> LB);
