@@ -61,6 +61,13 @@ extern "C" {
 #define QDTA_STOP_PAPER_OBJ 1 /* |C(f) - C(f_new)| / C(f) < tol (Section 4, Converged) */
 #define QDTA_STOP_REL_GAP 2   /* (sum c f - sum c g) / sum c f <= tol */
 
+/* Objective (Section 3 names both; the paper solves the user equilibrium).
+ * QDTA_OBJ_SO minimises the total cost sum f c(f): routing on the quantised
+ * marginal costs c + f c', line search and PAPER_OBJ stop on the total cost,
+ * REL_GAP on the marginal costs; loading and truncation keep the link times. */
+#define QDTA_OBJ_UE 0
+#define QDTA_OBJ_SO 1
+
 #define QDTA_SCHEDULE_PLAIN 0 /* host launch loop, one host sync per decision */
 #define QDTA_SCHEDULE_GRAPH 1 /* whole FW loop in one CUDA graph with device-side control */
 
@@ -105,7 +112,8 @@ typedef struct {
   double ls_t1;        /* T1 of Alg. 8 (relative slope: |C'| < T1 |C|) */
   double ls_t2;        /* T2 of Alg. 8 / bracket width of SWEEP8 */
   int32_t schedule;    /* QDTA_SCHEDULE_* */
-  int32_t record_tape; /* qdta_assign_interval: keep what qdta_backward needs */
+  int32_t record_tape; /* qdta_assign_interval: keep what qdta_backward needs (QDTA_OBJ_UE only) */
+  int32_t objective;   /* QDTA_OBJ_UE (the paper's user equilibrium) or QDTA_OBJ_SO */
 } qdta_params;
 
 typedef struct {

@@ -232,6 +232,7 @@ static int check_params(const qdta_params *p) {
     return fail(QDTA_EINVAL, "line-search tolerances must be positive");
   if (p->schedule != QDTA_SCHEDULE_PLAIN && p->schedule != QDTA_SCHEDULE_GRAPH)
     return fail(QDTA_EINVAL, "unknown schedule");
+  if (p->objective != QDTA_OBJ_UE && p->objective != QDTA_OBJ_SO) return fail(QDTA_EINVAL, "unknown objective");
   return QDTA_OK;
 }
 
@@ -1064,12 +1065,19 @@ struct Solver {
   // trees are gathered from here (rows by root index) instead of recomputed
   const int *ff_parent = nullptr;
   int ff_rows = 0;
+  // system optimum: q holds the quantised marginal costs (routing), qt the
+  // link times (loading and truncation); for the user equilibrium qt == q
+  int *qt = nullptr;
+  int so = 0;
 };
 
 static int solver_alloc(Solver &S, const std::string &tag, int ring, bool tape_f) {
   qdta_graph *g = S.g;
   const size_t L = g->d.L;
   RC(ws_get(g, tag + ".q", L, &S.q));
+  S.so = S.p->objective == QDTA_OBJ_SO;
+  if (S.so) RC(ws_get(g, tag + ".qt", L, &S.qt));
+  else S.qt = S.q;
   RC(ws_get(g, tag + ".gfx", L, &S.g_fx));
   RC(ws_get(g, tag + ".kc", L, &S.kc));
   RC(ws_get(g, tag + ".hq", L, &S.head_q));
@@ -1100,7 +1108,7 @@ static int seg_aon(Solver &S, const int *slot_dev, bool gather_ff = false) {
   else
     RC(run_sssp(g, QDTA_TO_ROOT, S.q, S.roots, S.R_host, S.R_dev, S.R_cap, S.parent, slot_dev,
                 S.parent_stride, nullptr, S.s));
-  launch_pack_head_q(g->d, S.q, S.head_q, S.s);
+  launch_pack_head_q(g->d, S.qt, S.head_q, S.s);
   CK(cudaMemsetAsync(S.g_fx, 0, (size_t)g->d.L * 8, S.s));
   ProfEvent pe;
   prof_begin(g, S.s, &pe, 1, 0);
@@ -1118,7 +1126,8 @@ static int seg_init(Solver &S) {
                   S.ring, S.n_host, S.n_dev, 1, S.s);
   launch_link_const(g->d, S.dt_h, S.kc, S.s);
   CK(cudaMemsetAsync(S.f, 0, (size_t)g->d.L * 8, S.s));
-  launch_bpr(g->d, S.f, S.dt_h, nullptr, S.q, g->status, S.s);
+  launch_bpr(g->d, S.f, S.dt_h, nullptr, S.q, g->status, S.s, S.so);
+  if (S.so) launch_bpr(g->d, S.f, S.dt_h, nullptr, S.qt, g->status, S.s);
   RC(seg_aon(S, nullptr, S.ff_parent != nullptr));
   launch_flow_from_fx(g->d.L, S.g_fx, S.f, S.s);
   launch_tape0(g->d, S.q, S.f, S.tape_q, S.tape_alpha, S.tape_f, S.s);
@@ -1127,7 +1136,8 @@ static int seg_init(Solver &S) {
 
 static int seg_iter_head(Solver &S, unsigned long long h_ls, int use_cond) {
   qdta_graph *g = S.g;
-  launch_bpr(g->d, S.f, S.dt_h, nullptr, S.q, g->status, S.s);
+  launch_bpr(g->d, S.f, S.dt_h, nullptr, S.q, g->status, S.s, S.so);
+  if (S.so) launch_bpr(g->d, S.f, S.dt_h, nullptr, S.qt, g->status, S.s);
   RC(seg_aon(S, &S.ctl->tree_slot));
   launch_ctl_begin(S.ctl, h_ls, use_cond, S.s);
   return QDTA_OK;
@@ -1138,7 +1148,7 @@ static int seg_ls_body(Solver &S, unsigned long long h_ls, int use_cond) {
   ProfEvent pe;
   prof_begin(g, S.s, &pe, 2, 0);
   launch_sweep(g->d, S.kc, S.f, (const long long *)S.g_fx, S.q, S.ctl, S.partials, S.counter, S.sgrid,
-               g->status, S.s);
+               g->status, S.s, S.so);
   prof_end(g, S.s, &pe);
   launch_ctl_step(S.ctl, h_ls, use_cond, S.s);
   return QDTA_OK;
@@ -1153,7 +1163,7 @@ static int seg_iter_tail(Solver &S, unsigned long long h_fw, int use_cond) {
 }
 
 static int seg_finish(Solver &S) {
-  launch_objective(S.g->d, S.kc, S.f, S.ctl, S.partials, S.counter, S.sgrid, S.g->status, S.s);
+  launch_objective(S.g->d, S.kc, S.f, S.ctl, S.partials, S.counter, S.sgrid, S.g->status, S.s, S.so);
   return QDTA_OK;
 }
 
@@ -1331,7 +1341,8 @@ extern "C" int qdta_line_search(qdta_graph *g, const double *flow, const int64_t
     CK(cudaMemcpyAsync(h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (!h->need_sweep) break;
-    launch_sweep(g->d, kc, flow, (const long long *)aon_fx, nullptr, ctl, partials, counter, sg, g->status, s);
+    launch_sweep(g->d, kc, flow, (const long long *)aon_fx, nullptr, ctl, partials, counter, sg, g->status, s,
+                 p->objective == QDTA_OBJ_SO);
     launch_ctl_step(ctl, 0, 0, s);
   }
   RC(status_check(g, s));
@@ -1353,6 +1364,8 @@ static int assign_core(qdta_graph *g, const qdta_od *od, double dt_s, const qdta
   S.root_idx = od->root_idx; S.src = od->src; S.amount = (const long long *)od->amount_fx;
   S.f = flow_out;
   const bool want_tape = p->record_tape && tape_out;
+  if (want_tape && p->objective == QDTA_OBJ_SO)
+    return fail(QDTA_EINVAL, "the adjoint (record_tape) covers the user equilibrium only");
   RC(solver_alloc(S, tag, 1, want_tape));
   RC(status_reset(g, s));
   if (p->schedule == QDTA_SCHEDULE_GRAPH) RC(fw_graph(S));

@@ -129,6 +129,28 @@ __device__ __forceinline__ double link_cost(double c0, double inv, double alpha,
   return mul(c0, u);
 }
 
+// System optimum: marginal cost m = c + t c' = c0 (1 + alpha (beta+1) x^beta)
+// and its derivative c0 alpha beta (beta+1) x^(beta-1) / cp; the objective
+// term is the total cost t c(t).  Same operation order as the CPU oracle.
+__device__ __forceinline__ double link_marginal(double c0, double inv, double alpha, int beta, double t) {
+  double x = mul(t, inv);
+  double p = powi(x, beta);
+  double k = mul(alpha, (double)(beta + 1));
+  double w = mul(k, p);
+  double u = add(1.0, w);
+  return mul(c0, u);
+}
+
+__device__ __forceinline__ double link_marginal_dt(double c0, double inv, double alpha, int beta, double t) {
+  double x = mul(t, inv);
+  double p = beta > 1 ? powi(x, beta - 1) : 1.0;
+  double w = mul(c0, alpha);
+  w = mul(w, (double)beta);
+  w = mul(w, (double)(beta + 1));
+  w = mul(w, p);
+  return mul(w, inv);
+}
+
 __device__ __forceinline__ double link_cost_dt(double c0, double inv, double alpha, int beta, double t) {
   double x = mul(t, inv);
   double p = beta > 1 ? powi(x, beta - 1) : 1.0;
@@ -355,17 +377,18 @@ void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *paren
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
                      unsigned long long *dense, unsigned *status, cudaStream_t s);
 
+// marginal = 1: the system optimum's marginal costs instead of link times
 void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,
-                unsigned *status, cudaStream_t s);
+                unsigned *status, cudaStream_t s, int marginal = 0);
 void launch_link_const(const GraphDev &g, double dt_h, LinkConst *kc, cudaStream_t s);
 void launch_flow_from_fx(int L, const unsigned long long *fx, double *f, cudaStream_t s);
 void launch_sweep(const GraphDev &g, const LinkConst *kc, const double *f, const long long *g_fx,
                   const int *q, Ctl *ctl, i128 *partials, unsigned *counter, int grid,
-                  unsigned *status, cudaStream_t s);
+                  unsigned *status, cudaStream_t s, int so = 0);
 int sweep_grid(const GraphDev &g);
 void launch_update(const GraphDev &g, Ctl *ctl, double *f, const long long *g_fx, cudaStream_t s);
 void launch_objective(const GraphDev &g, const LinkConst *kc, const double *f, Ctl *ctl,
-                      i128 *partials, unsigned *counter, int grid, unsigned *status, cudaStream_t s);
+                      i128 *partials, unsigned *counter, int grid, unsigned *status, cudaStream_t s, int so = 0);
 
 void launch_ctl_init(Ctl *ctl, int step, int stop, int max_iter, int ls_max, double tol, double dx,
                      double t1, double t2, int ring, long long n_items_host,

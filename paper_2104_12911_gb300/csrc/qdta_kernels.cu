@@ -1413,28 +1413,31 @@ void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *paren
 // link-parallel passes
 // ============================================================================
 
+// Eq. 1 link times (marginal = 0), or the system optimum's marginal costs
+// c + f c' (marginal = 1), quantised; cost_s (seconds) only for link times
 __global__ void bpr_kernel(int L, const int *__restrict__ c0, const double *__restrict__ cap,
                            double alpha, int beta, double dt_h, double quantum_s,
                            const double *__restrict__ flow, double *cost_s, int *cost_q,
-                           unsigned *status) {
+                           unsigned *status, int marginal) {
   unsigned bad = 0;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
     const double f = flow[a];
     if (!isfinite(f)) bad |= ST_NONFINITE;
     const LinkConst k = link_const(cap[a], dt_h, alpha, beta);
-    const double c = link_cost((double)c0[a], k.inv, alpha, beta, f);
-    if (cost_s) cost_s[a] = mul(c, quantum_s);
+    const double c = marginal ? link_marginal((double)c0[a], k.inv, alpha, beta, f)
+                              : link_cost((double)c0[a], k.inv, alpha, beta, f);
+    if (cost_s && !marginal) cost_s[a] = mul(c, quantum_s);
     cost_q[a] = quantize(c, &bad);
   }
   if (bad) atomicOr(status, bad);
 }
 
 void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,
-                unsigned *status, cudaStream_t s) {
+                unsigned *status, cudaStream_t s, int marginal) {
   if (g.L == 0) return;
   COUNT_LAUNCH();
   bpr_kernel<<<link_grid(g, g.L), LINK_THREADS, 0, s>>>(g.L, g.c0, g.cap, g.alpha, g.beta, dt_h,
-                                                        g.quantum_s, flow, cost_s, cost_q, status);
+                                                        g.quantum_s, flow, cost_s, cost_q, status, marginal);
 }
 
 __global__ void link_const_kernel(int L, const double *__restrict__ cap, double dt_h, double alpha,
@@ -1517,7 +1520,7 @@ __global__ void __launch_bounds__(LINK_THREADS)
 sweep_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict__ kc,
              const double *__restrict__ f, const long long *__restrict__ g_fx,
              const int *__restrict__ q, double alpha_bpr, int beta, Ctl *ctl, i128 *partials,
-             unsigned *counter, unsigned *status) {
+             unsigned *counter, unsigned *status, int so) {
   __shared__ Plan plan;
   if (threadIdx.x == 0) plan = ctl->plan;
   __syncthreads();
@@ -1542,9 +1545,15 @@ sweep_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict__ kc
       if (m < plan.n) {
         const double t = step_flow(fa, ga, plan.alpha[m]);
         double term;
-        if (plan.kind[m] == K_PHI) term = beckmann(c0a, k.inv, k.kb, beta, t);
-        else if (plan.kind[m] == K_DPHI) term = mul(d, link_cost(c0a, k.inv, alpha_bpr, beta, t));
-        else term = mul(mul(d, d), link_cost_dt(c0a, k.inv, alpha_bpr, beta, t));
+        // user equilibrium: Beckmann integral (Eq. 6), link time, its slope;
+        // system optimum: total cost t c(t), marginal cost, its slope
+        if (plan.kind[m] == K_PHI)
+          term = so ? mul(t, link_cost(c0a, k.inv, alpha_bpr, beta, t)) : beckmann(c0a, k.inv, k.kb, beta, t);
+        else if (plan.kind[m] == K_DPHI)
+          term = mul(d, so ? link_marginal(c0a, k.inv, alpha_bpr, beta, t) : link_cost(c0a, k.inv, alpha_bpr, beta, t));
+        else
+          term = mul(mul(d, d), so ? link_marginal_dt(c0a, k.inv, alpha_bpr, beta, t)
+                                   : link_cost_dt(c0a, k.inv, alpha_bpr, beta, t));
         acc[m] += fx_of(term, &bad);
       }
     }
@@ -1562,16 +1571,16 @@ int sweep_grid(const GraphDev &g) {
 
 void launch_sweep(const GraphDev &g, const LinkConst *kc, const double *f, const long long *g_fx,
                   const int *q, Ctl *ctl, i128 *partials, unsigned *counter, int grid,
-                  unsigned *status, cudaStream_t s) {
+                  unsigned *status, cudaStream_t s, int so) {
   COUNT_LAUNCH();
   sweep_kernel<<<grid, LINK_THREADS, 0, s>>>(g.L, g.c0, kc, f, g_fx, q, g.alpha, g.beta, ctl,
-                                             partials, counter, status);
+                                             partials, counter, status, so);
 }
 
 __global__ void __launch_bounds__(LINK_THREADS)
 objective_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict__ kc,
-                 const double *__restrict__ f, int beta, Ctl *ctl, i128 *partials,
-                 unsigned *counter, unsigned *status) {
+                 const double *__restrict__ f, double alpha_bpr, int beta, Ctl *ctl, i128 *partials,
+                 unsigned *counter, unsigned *status, int so) {
   __shared__ i128 out[NSUM];
   i128 acc[NSUM];
 #pragma unroll
@@ -1579,7 +1588,9 @@ objective_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict_
   unsigned bad = 0;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
     const LinkConst k = kc[a];
-    acc[0] += fx_of(beckmann((double)c0[a], k.inv, k.kb, beta, f[a]), &bad);
+    const double term = so ? mul(f[a], link_cost((double)c0[a], k.inv, alpha_bpr, beta, f[a]))
+                           : beckmann((double)c0[a], k.inv, k.kb, beta, f[a]);
+    acc[0] += fx_of(term, &bad);
   }
   if (bad) atomicOr(status, bad);
   if (threadIdx.x == 0) out[0] = 0;
@@ -1588,10 +1599,10 @@ objective_kernel(int L, const int *__restrict__ c0, const LinkConst *__restrict_
 }
 
 void launch_objective(const GraphDev &g, const LinkConst *kc, const double *f, Ctl *ctl,
-                      i128 *partials, unsigned *counter, int grid, unsigned *status, cudaStream_t s) {
+                      i128 *partials, unsigned *counter, int grid, unsigned *status, cudaStream_t s, int so) {
   COUNT_LAUNCH();
-  objective_kernel<<<grid, LINK_THREADS, 0, s>>>(g.L, g.c0, kc, f, g.beta, ctl, partials, counter,
-                                                 status);
+  objective_kernel<<<grid, LINK_THREADS, 0, s>>>(g.L, g.c0, kc, f, g.alpha, g.beta, ctl, partials, counter,
+                                                 status, so);
 }
 
 // f <- f + alpha* (g - f) when the controller accepted the step

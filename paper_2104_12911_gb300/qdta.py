@@ -22,6 +22,7 @@ QDTA_ENONFINITE, QDTA_EUNREACH, QDTA_EOVERFLOW, QDTA_ENOTCONV = -5, -6, -7, 1
 QDTA_TO_ROOT, QDTA_FROM_ROOT = 0, 1
 STEP = {"msa": 0, "paper_qn3": 1, "sweep8": 2, "exact": 3}
 STOP = {"none": 0, "paper_obj": 1, "rel_gap": 2}
+OBJECTIVE = {"ue": 0, "so": 1}
 SCHEDULE = {"plain": 0, "graph": 1}
 DIST_INF = np.iinfo(np.int64).max
 FX_ONE = 1 << 32
@@ -48,7 +49,7 @@ class Params(C.Structure):
     _fields_ = [("step", C.c_int32), ("stop", C.c_int32), ("max_iter", C.c_int32),
                 ("ls_max", C.c_int32), ("tol", C.c_double), ("ls_dx", C.c_double),
                 ("ls_t1", C.c_double), ("ls_t2", C.c_double), ("schedule", C.c_int32),
-                ("record_tape", C.c_int32)]
+                ("record_tape", C.c_int32), ("objective", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -159,12 +160,12 @@ def _stream():
 
 
 def make_params(step="sweep8", stop="rel_gap", max_iter=200, tol=1e-4, ls_max=20, ls_dx=1e-4,
-                ls_t1=1e-4, ls_t2=1e-4, schedule="plain", record_tape=False) -> Params:
+                ls_t1=1e-4, ls_t2=1e-4, schedule="plain", record_tape=False, objective="ue") -> Params:
     return Params(STEP[step] if isinstance(step, str) else int(step),
                   STOP[stop] if isinstance(stop, str) else int(stop), int(max_iter), int(ls_max),
                   float(tol), float(ls_dx), float(ls_t1), float(ls_t2),
                   SCHEDULE[schedule] if isinstance(schedule, str) else int(schedule),
-                  1 if record_tape else 0)
+                  1 if record_tape else 0, OBJECTIVE[objective] if isinstance(objective, str) else int(objective))
 
 
 class Graph:

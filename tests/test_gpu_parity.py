@@ -572,3 +572,60 @@ def test_interval_metrics_edge_cases():
     with pytest.raises(Q.QdtaError) as e:
         Q.qdta_interval_metrics(g, T(flows, np.float64), 900.0, T(length, np.float64), T(cls, np.int32), 5)
     assert e.value.code == Q.QDTA_ENONFINITE
+
+
+# ---------------------------------------------------------------------------
+# System-optimal objective: routing on marginal costs, total-cost line search
+@pytest.mark.parametrize("step", ["paper_qn3", "sweep8", "exact"])
+def test_line_search_system_optimum_bit_exact(small, step):
+    inst, g, og = small
+    f, gfx = _fg(small)
+    a_o, n_o, rc = oracle.line_search(og, f, gfx, 900.0, 3, oracle.make_params(Q.STEP[step], oracle.STOP_NONE, 20,
+                                                                              objective=oracle.OBJ_SO))
+    a_g, n_g = Q.qdta_line_search(g, T(f, np.float64), T(gfx, np.int64), 900.0, 3,
+                                  Q.make_params(step, "none", 20, objective="so"))
+    assert a_g == a_o and n_g == n_o
+    a_ue, _, _ = oracle.line_search(og, f, gfx, 900.0, 3, oracle.make_params(Q.STEP[step], oracle.STOP_NONE, 20))
+    assert step == "paper_qn3" or a_ue != a_o  # the objectives differ on this case
+
+
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+@pytest.mark.parametrize("step,stop,it,tol", CASES)
+def test_assign_interval_system_optimum_bit_exact(small, schedule, step, stop, it, tol):
+    inst, g, og = small
+    od = oracle.OracleOD.of(inst.demand[0])
+    f_o, st_o, rc_o = oracle.assign_interval(og, od, 900.0, oracle.make_params(Q.STEP[step], Q.STOP[stop], it, tol,
+                                                                              objective=oracle.OBJ_SO))
+    f_g, st_g, rc_g, _ = Q.qdta_assign_interval(g, Q.DeviceOD.of(inst.demand[0]), 900.0,
+                                                 Q.make_params(step, stop, it, tol, schedule=schedule, objective="so"))
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    for key in ("iterations", "aon_calls", "ls_passes", "converged", "objective"):
+        assert st_g[key] == st_o[key], key
+    for key in ("rel_gap", "dual_gap"):
+        if not np.isnan(st_o[key]):
+            assert st_g[key] == st_o[key], key
+
+
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+def test_run_day_system_optimum_bit_exact(schedule):
+    day = _day_case(n_int=4)
+    days = list(day.demand)
+    og = oracle.OracleGraph(day.net)
+    f_o, st_o, nit_o, rn_o, _ = oracle.run_day(og, day.zones, days, 900.0, oracle.make_params(
+        Q.STEP["sweep8"], Q.STOP["paper_obj"], 60, objective=oracle.OBJ_SO))
+    g = Q.Graph(day.net)
+    zones = T(day.zones, np.int32)
+    dd = [Q.DeviceOD(zones, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
+    f_g, st_g, _, resid = Q.qdta_run_day(g, dd, 900.0, Q.make_params("sweep8", "paper_obj", 60, schedule=schedule,
+                                                                      objective="so"), resid_capacity=1 << 20)
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    assert [s["iterations"] for s in st_g] == [s["iterations"] for s in st_o]
+    assert resid[0].shape[0] == rn_o
+
+
+def test_system_optimum_rejects_a_tape(small):
+    inst, g, og = small
+    with pytest.raises(Q.QdtaError) as e:
+        Q.qdta_assign_interval(g, Q.DeviceOD.of(inst.demand[0]), 900.0,
+                               Q.make_params("exact", "none", 3, record_tape=True, objective="so"))
+    assert e.value.code == Q.QDTA_EINVAL

@@ -67,8 +67,9 @@ def test_tune_report_layout_matches_the_header():
     if not shutil.which("gcc"):
         import pytest
         pytest.skip("no gcc")
-    src = ('#include <stdio.h>\n#include "qdta.h"\nint main(void){printf("%zu %zu %zu\\n", '
-           'sizeof(qdta_tune_entry), sizeof(qdta_tune_report), sizeof(qdta_profile)); return 0;}\n')
+    src = ('#include <stdio.h>\n#include "qdta.h"\nint main(void){printf("%zu %zu %zu %zu\\n", '
+           'sizeof(qdta_tune_entry), sizeof(qdta_tune_report), sizeof(qdta_profile), sizeof(qdta_params)); '
+           'return 0;}\n')
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "sz.c")
         exe = os.path.join(d, "sz")
@@ -77,7 +78,7 @@ def test_tune_report_layout_matches_the_header():
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     assert [int(x) for x in out] == [ctypes.sizeof(Q.TuneEntry), ctypes.sizeof(Q.TuneReport),
-                                     ctypes.sizeof(Q.Profile)]
+                                     ctypes.sizeof(Q.Profile), ctypes.sizeof(Q.Params)]
 
 
 def test_tune_report_as_dict_keeps_valid_rows_and_the_best():
