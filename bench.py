@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--stop", default="paper_obj", choices=["paper_obj", "rel_gap"])
     ap.add_argument("--step", default="sweep8", choices=["sweep8", "paper_qn3", "exact", "msa"],
                     help="FW step rule (the paper compares its line search with MSA)")
+    ap.add_argument("--objective", default="ue", choices=["ue", "so"],
+                    help="user equilibrium (the paper's) or system optimum")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default SSSP launch shape")
@@ -540,9 +542,10 @@ def main():
 
     host = [upload(d, pin=True) for d in inst.demand]
     zones_host = torch.from_numpy(inst.zones.astype(np.int32)).pin_memory()
-    params_graph = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="graph")
-    params_plain = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="plain")
+    params_graph = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="graph", objective=args.objective)
+    params_plain = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="plain", objective=args.objective)
     cfg["step_rule"] = args.step
+    cfg["objective"] = {"ue": "user equilibrium (Beckmann)", "so": "system optimum (total cost)"}[args.objective]
     flow_out = torch.empty((len(inst.demand), g.n_links), dtype=torch.float64, device=dev)
     flows_host = torch.empty((len(inst.demand), g.n_links), dtype=torch.float64).pin_memory()
     h2d = sum(a.numel() * a.element_size() for h in host for a in h) + zones_host.numel() * 4
