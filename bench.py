@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="day_metro",
-                    choices=["day_metro", "day_small", "sssp_metro", "batch32", "adjoint_metro", "interval_metro"])
+                    choices=["day_metro", "day_small", "sssp_metro", "batch32", "adjoint_metro", "interval_metro",
+                             "sta_vs_qdta"])
     ap.add_argument("--roots", type=int, default=2000, help="sssp_metro: destination roots per batch")
     ap.add_argument("--intervals", default=None,
                     help="a:b -- run only intervals a..b-1 of the day (profiling captures; not a bench line)")
@@ -481,6 +482,77 @@ def interval_metro(args):
                       "sssp_kernel": Q.qdta_sssp_kernel_name(g)}), flush=True)
 
 
+def sta_vs_qdta(args):
+    """The paper's comparison of a static and a quasi-dynamic morning peak
+    (Section 7.1) on the metro day: 07:00-10:00 as one 3-hour static
+    assignment (all of its original trips, no truncation inside the period)
+    vs twelve 15-minute QDTA intervals with residual demand; scenario metrics
+    by link class (over the period for both; the congested subset for the
+    07:45-08:00 interval of QDTA and for the static period)."""
+    import torch
+    from paper_2104_12911_gb300 import qdta as Q, synth
+    inst = synth.config_day(seed=2)
+    net = inst.net
+    dev = torch.device("cuda", 0)
+    g = Q.Graph(net)
+    if not args.no_tune:
+        Q.qdta_autotune(g, torch.from_numpy(net.fftime_q.astype(np.int32)).to(dev),
+                        torch.from_numpy(inst.zones.astype(np.int32)).to(dev), reps=2)
+    first, n_int = 28, 12  # 07:00-10:00
+    days = inst.demand[first:first + n_int]
+    zones = torch.from_numpy(inst.zones.astype(np.int32)).to(dev)
+    length = torch.from_numpy(net.length_m.astype(np.float64)).to(dev)
+    cls = torch.from_numpy(net.link_class.astype(np.int32)).to(dev)
+    n_cls = int(net.link_class.max()) + 1
+    p = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="graph", objective=args.objective)
+    # QDTA: twelve intervals with residual demand
+    dd = [Q.DeviceOD(zones, *(torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+                              for a in (d.root_idx, d.src, d.amount_fx))) for d in days]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h, st_q, _, _ = Q.qdta_run_day(g, dd, 900.0, p)
+    torch.cuda.synchronize()
+    t_qdta = time.perf_counter() - t0
+    m_q = Q.qdta_interval_metrics(g, h, 900.0, length, cls, n_cls).cpu().numpy()
+    # STA: the period's original trips summed per (root, origin), one 3-hour interval
+    ri = np.concatenate([d.root_idx for d in days])
+    si = np.concatenate([d.src for d in days])
+    am = np.concatenate([d.amount_fx for d in days])
+    key = ri.astype(np.int64) * net.n_nodes + si
+    uk, inv = np.unique(key, return_inverse=True)
+    amount = np.zeros(uk.shape[0], np.int64)
+    np.add.at(amount, inv, am)
+    sta_od = Q.DeviceOD(zones, torch.from_numpy((uk // net.n_nodes).astype(np.int32)).to(dev),
+                        torch.from_numpy((uk % net.n_nodes).astype(np.int32)).to(dev),
+                        torch.from_numpy(amount).to(dev))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f_s, st_s, _, _ = Q.qdta_assign_interval(g, sta_od, 3 * 3600.0, p)
+    torch.cuda.synchronize()
+    t_sta = time.perf_counter() - t0
+    m_s = Q.qdta_interval_metrics(g, f_s, 3 * 3600.0, length, cls, n_cls).cpu().numpy()[0]
+    peak = 31 - first  # 07:45-08:00
+
+    def table(rows):
+        return {f"class_{k}": {name: round(float(v), 4) for name, v in zip(Q.METRIC_NAMES, rows[k])}
+                for k in range(n_cls)}
+
+    qdta_period = m_q.sum(axis=0)  # additive metrics summed over the intervals
+    for c in range(n_cls):  # the averages: count-weighted over the intervals
+        n = m_q[:, c, 0].sum()
+        qdta_period[c, 2] = float((m_q[:, c, 2] * m_q[:, c, 0]).sum() / n) if n else 0.0
+        cn = m_q[:, c, 4].sum()
+        qdta_period[c, 7] = float((m_q[:, c, 7] * m_q[:, c, 4]).sum() / cn) if cn else 0.0
+    print(json.dumps({"metric": "static vs quasi-dynamic morning peak (07:00-10:00), scenario metrics",
+                      "workload": "500x500 grid, 2000 zones, metro day intervals 28..39",
+                      "sta": {"seconds": t_sta, "fw_iterations": st_s["iterations"], "metrics": table(m_s)},
+                      "qdta": {"seconds": t_qdta, "fw_iterations": [s["iterations"] for s in st_q],
+                               "metrics_period": table(qdta_period),
+                               "metrics_0745_0800": table(m_q[peak]),
+                               "items_per_interval": [s["n_items"] for s in st_q]},
+                      "step": args.step, "stop": args.stop, "objective": args.objective}), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "sssp_metro":
@@ -494,6 +566,9 @@ def main():
         return
     if args.workload == "interval_metro":
         interval_metro(args)
+        return
+    if args.workload == "sta_vs_qdta":
+        sta_vs_qdta(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
