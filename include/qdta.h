@@ -199,7 +199,8 @@ int qdta_bpr_costs(qdta_graph *g, const double *flow, double dt_s, double *cost_
 
 /* Step size of one FW iteration (Alg. 8 with Alg. 9 / Eq. 7-9, or the
  * SWEEP8 / EXACT / MSA rules): minimise C(f + alpha (g - f)) over [0, 1]
- * with C the Beckmann objective (Eq. 6).  flow [L] f, aon_fx [L] g in fixed
+ * with C the Beckmann objective (Eq. 6), or the total cost sum f c(f) when
+ * p->objective is QDTA_OBJ_SO.  flow [L] f, aon_fx [L] g in fixed
  * point, fw_iter = k >= 1 (the k-th step; Alg. 8 starts from 2/(2+k-1)).
  * alpha_out_host, passes_out_host (nullable) are host scalars; the call
  * synchronises `stream`. */
@@ -210,12 +211,14 @@ int qdta_line_search(qdta_graph *g, const double *flow, const int64_t *aon_fx, d
 /* One interval's static assignment by Frank-Wolfe (Alg. 2 / Alg. 6):
  * initial all-or-nothing at free flow, then repeat {BPR costs; batched
  * shortest paths; truncated loading; step size; convex update} until the
- * stop rule holds or max_iter steps were taken.  flow_out [L] receives f.
+ * stop rule holds or max_iter steps were taken (for QDTA_OBJ_SO the paths
+ * follow marginal costs and the step minimises the total cost; see
+ * QDTA_OBJ_SO).  flow_out [L] receives f.
  * In PAPER_OBJ mode the iterate before the step that met the test is
  * returned (the pseudo-code breaks before h = h_new).  stats_host
  * (nullable).  With p->record_tape, *tape_out receives a tape for
  * qdta_backward (the od arrays must stay alive and unchanged until the tape
- * is destroyed).  Synchronises `stream`.  An interval with no items returns
+ * is destroyed; QDTA_EINVAL with QDTA_OBJ_SO).  Synchronises `stream`.  An interval with no items returns
  * zero flows, converged. */
 int qdta_assign_interval(qdta_graph *g, const qdta_od *od, double dt_s, const qdta_params *p,
                          double *flow_out, qdta_stats *stats_host, qdta_tape **tape_out,
