@@ -630,3 +630,23 @@ def test_system_optimum_equals_equilibrium_for_constant_costs():
         out.append((f, st["iterations"], st["ls_passes"]))
     np.testing.assert_array_equal(out[0][0], out[1][0])
     assert out[0][1:] == out[1][1:]
+
+
+def test_day_advances_a_trip_one_link_per_interval_when_links_outlast_dt():
+    """Links of 20 min, intervals of 15 min: under reading R1 the trip is
+    loaded on one link per interval (the link it is on when the interval
+    starts) and waits at that link's head: no stall at the origin."""
+    net = synth.chain_network([1200.0, 1200.0, 1200.0], [1000.0, 1000.0, 1000.0])
+    g = oracle.OracleGraph(net)
+    zones = np.array([3], np.int32)
+    one = synth.Demand(roots=zones, root_idx=np.array([0], np.int32), src=np.array([0], np.int32),
+                       amount_fx=np.array([1 << 32], np.int64))
+    empty = synth.Demand(roots=zones, root_idx=np.zeros(0, np.int32), src=np.zeros(0, np.int32),
+                         amount_fx=np.zeros(0, np.int64))
+    f, st, nit, rn, rc = oracle.run_day(g, zones, [one, empty, empty, empty], 900.0,
+                                        oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 2))
+    assert rc >= 0
+    f = np.asarray(f).reshape(4, 3)
+    # step-weighted shares are rounded to 2^-32 trips each (R9)
+    np.testing.assert_allclose(f, [[1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, 0]], rtol=0, atol=4 * 2.0 ** -32)
+    assert list(nit) == [1, 1, 1, 0]
