@@ -3,12 +3,22 @@
 
 One step = one full day (96 x 15-minute intervals, Alg. 1): for every
 interval the residual demand is merged, the static user equilibrium is
-solved by Frank-Wolfe to relative gap 1e-4 (batched shortest paths, truncated
-loading, 8-point line search), and the residual demand is re-truncated and
-carried to the next interval.  The timed steps run the graph schedule
+solved by Frank-Wolfe (batched shortest paths, truncated loading, 8-point
+line search) until the paper's Converged test holds (relative objective
+change < 1e-4, Section 4; --stop rel_gap stops on the relative duality gap
+instead), and the residual demand is re-truncated and carried to the next
+interval.  Every interval's duality gap is reported either way.  The timed steps run the graph schedule
 (device-side control, CUDA graphs); one extra day runs the plain host launch
 loop for the batched-vs-plain comparison and for per-kernel CUDA-event
 timings (the SSSP roofline line).
+
+One metro day takes minutes, so the run is bounded by a wall-clock budget
+(--budget-s, counted from process start): at most three warm-up days (the
+plain profiling day and two graph days), then timed days while another one
+still fits the budget, at least one and at most --steps.  The JSON line's
+"steps" and "warmup" are the days actually run; "steps_requested" and
+"warmup_requested" echo the command line.  A progress line per day goes to
+stderr.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -26,6 +36,7 @@ import time
 
 import numpy as np
 
+T_START = time.monotonic()
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -33,15 +44,18 @@ METRIC = "Full-day QDTA s @rel-gap 1e-4, batched vs plain on 1 GB300; SSSP GTEPS
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per destination
 # root of the SSSP kernels, from one ncu capture each on the 500x500 metro
-# grid (one wave of resident roots); the roofline's `traffic` scales them by
-# the roots per launch.  Only kernels whose code is unchanged since their
+# grid (one wave of 608 resident roots); the roofline's `traffic` scales them
+# by the roots per launch.  Only kernels whose code is unchanged since their
 # capture are listed.
 SSSP_DRAM_BYTES_PER_ROOT = {
-    # profiles/sssp_smq_kernel_rank_metro_R608.md: 2.830261 GB read + 5.333477 GB written, 608 roots
     "sssp_smq_kernel<256,rank,2,true>": (2.830261e9 + 5.333477e9) / 608,
-    # profiles/sssp_smq_kernel_rank32_metro_R608.md: 1.309412 GB read + 2.531841 GB written, 608 roots
     "sssp_smq_kernel<256,rank32,2,true>": (1.309412e9 + 2.531841e9) / 608,
 }
+
+
+def progress(msg):
+    """One line on stderr, stamped with the seconds since process start."""
+    print(f"[bench {time.monotonic() - T_START:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def parse():
@@ -65,6 +79,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default SSSP launch shape")
+    ap.add_argument("--budget-s", type=float, default=1350.0,
+                    help="day workloads: wall-clock budget of the whole run, from process start; warm-up is "
+                         "capped at 3 days and timed days stop when the next one would not fit")
+    ap.add_argument("--max-warmup-days", type=int, default=3)
     return ap.parse_args()
 
 
@@ -239,13 +257,11 @@ def cpu_baseline(inst, day_stats, budget_s=20.0):
                                       oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_NONE, 20))
     t_pass = (time.perf_counter() - t1) / max(passes, 1)
     n_roots = [len(np.unique(d.root_idx)) for d in inst.demand]
+    work = {"aon": [st["aon_calls"] for st in day_stats], "fw": [st["iterations"] for st in day_stats],
+            "sweeps": [st["ls_passes"] for st in day_stats]}
 
     def day_seconds(t_r):
-        est = 0.0
-        for i, st in enumerate(day_stats):
-            aons = st["aon_calls"] + (st["iterations"] + 1 if st["aon_calls"] else 0)  # FW + residual trees
-            est += aons * n_roots[i] * t_r + st["ls_passes"] * t_pass
-        return est
+        return day_oracle_seconds(work, n_roots, t_r, t_pass)
     spent = time.perf_counter() - t0
     # the same roots again on every host core (the sweeps stay single-core)
     par = None
@@ -265,12 +281,45 @@ def cpu_baseline(inst, day_stats, budget_s=20.0):
             "sec_per_root": t_root, "sec_per_sweep": t_pass, "all_cores": par}
 
 
+def day_oracle_seconds(day_work, n_roots, t_root, t_sweep):
+    """Seconds the oracle needs for a day whose interval i runs
+    day_work["aon"][i] shortest-path batches over n_roots[i] destination roots
+    (one Dijkstra + the walks of its items per root) and
+    day_work["sweeps"][i] line-search sweeps; the residual pass (Alg. 4)
+    re-walks the iterations + 1 accepted AONs of every interval."""
+    est = 0.0
+    for i, n in enumerate(n_roots):
+        aons = day_work["aon"][i] + (day_work["fw"][i] + 1 if day_work["aon"][i] else 0)
+        est += aons * n * t_root + day_work["sweeps"][i] * t_sweep
+    return est
+
+
+# Work counts of the default metro day (500x500 grid, 2000 zones, 19M trips,
+# sweep8 steps, the paper's stop rule), per interval: shortest-path batches,
+# accepted FW steps and line-search sweeps.  The oracle and the CUDA path
+# compute the same iterates bit for bit, so these counts are the oracle's too;
+# they were recorded from the bench line's "per_interval" entry.  The
+# reference arm scales its timed sample by them.
+METRO_DAY_WORK = None
+
+
 def reference_arm(args, inst, cfg):
-    """CPU oracle on every host core, timed on a bounded sample per step: one
-    AON + one residual re-walk per interval (a lower bound on the day's work),
-    sampled on a few roots of a few intervals and scaled to every interval's
-    roots."""
+    """CPU oracle on every host core, timed on a bounded sample per step:
+    Dijkstra + loading of a few destination roots from four intervals of the
+    day (the busiest and intervals 0, 30, 60), one root per task, one process
+    per core; a line-search sweep timed once on one core.  The day's seconds
+    are those per-root and per-sweep times scaled by the day's work counts."""
+    import oracle
     q = inst.net.fftime_q
+    og = oracle.OracleGraph(inst.net)
+    L = og.n_links
+    rng = np.random.default_rng(0)
+    f = rng.uniform(0, 50, L)
+    gfx = (rng.uniform(0, 50, L) * (1 << 32)).astype(np.int64)
+    t1 = time.perf_counter()
+    _, passes, _ = oracle.line_search(og, f, gfx, 900.0, 1,
+                                      oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_NONE, 20))
+    t_sweep = (time.perf_counter() - t1) / max(passes, 1)
     pool = OraclePool(inst.net, q)
     n_roots = [len(np.unique(d.root_idx)) for d in inst.demand]
     picks = [int(np.argmax([d.n_items for d in inst.demand])), 0, 30, 60]
@@ -278,31 +327,37 @@ def reference_arm(args, inst, cfg):
     for i in picks:
         dem = inst.demand[i]
         tasks += OraclePool.tasks(dem, np.unique(dem.root_idx)[:pool.n])
+    work = METRO_DAY_WORK if args.workload == "day_metro" else None
+    if work is not None and len(work["aon"]) == len(n_roots):
+        scaling = "the day's recorded AON / FW-step / sweep counts per interval"
+    else:
+        work = {"aon": [2] * len(n_roots), "fw": [1] * len(n_roots), "sweeps": [0] * len(n_roots)}
+        scaling = "2 AONs + 2 residual re-walks per interval, no sweeps (a lower bound; no recorded counts)"
 
     def one_step():
         t0 = time.perf_counter()
         t_root = pool.seconds_per_root(tasks)
-        est = sum(3 * n * t_root for n in n_roots)  # initial AON + 1 step + 1 residual tree
-        return est, time.perf_counter() - t0
+        return day_oracle_seconds(work, n_roots, t_root, t_sweep), time.perf_counter() - t0
 
     for _ in range(args.warmup):
         one_step()
-    vals, spent = [], 0.0
+    vals, spent = [], []
     for _ in range(args.steps):
-        v, s = one_step()
+        v, s_ = one_step()
         vals.append(v)
-        spent += s
+        spent.append(s_)
     pool.close()
     value = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64",
             "data": "synthetic", "config": cfg,
+            "timed_s_per_step": float(np.mean(spent)),
             "cpu_baseline": {"value": value, "unit": "s", "cores": pool.n, "kind": "oracle",
                              "sample": (f"{len(tasks)} destination roots (Dijkstra + loading) from 4 intervals per "
-                                        f"step, one process per core on {pool.n} cores; day scaled as 3 AONs per "
-                                        "interval x active roots (a lower bound: real intervals need more FW "
-                                        "steps)")},
+                                        f"step, one process per core on {pool.n} cores ({np.mean(spent):.2f} s "
+                                        f"timed per step), and one 8-point sweep over {L} links on one core "
+                                        f"({t_sweep:.3f} s); extrapolated to the day by {scaling}")},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -650,12 +705,33 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up: the first day runs the plain schedule (host launch loop) with
+    def agree(flag):
+        """True on every rank only if `flag` holds on every rank (replicas stay
+        in step: they run the same number of days)."""
+        if world <= 1:
+            return bool(flag)
+        t = torch.tensor([1.0 if flag else 0.0], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        return bool(t.item() > 0.5)
+
+    # Warm-up: the first day runs the plain schedule (host launch loop) with
     # per-kernel CUDA events: the batched-vs-plain comparison and the SSSP
-    # roofline come from it; the remaining warm-up days run the graph schedule
+    # roofline come from it; the other warm-up days run the graph schedule.
+    # At most --max-warmup-days days, and no more warm-up once another day
+    # plus the first timed day and the CPU leg would not fit the budget.
+    reserve_s = 0.0 if (args.no_cpu or rank != 0) else 90.0
+    budget = args.budget_s
+    progress(f"setup done ({args.workload}, generation {t_gen:.1f} s)")
     plain_ms, prof, plain_launches, stats_plain = None, None, None, None
-    for w in range(args.warmup):
-        if w == 0 and not args.no_plain:
+    day_s = []  # wall seconds of every day run so far
+    warm_done = 0
+    while warm_done < min(args.warmup, max(args.max_warmup_days, 1)):
+        if warm_done >= 1:
+            est = max(day_s)
+            if not agree(time.monotonic() - T_START + 2 * est + reserve_s < budget):
+                break
+        t0 = time.monotonic()
+        if warm_done == 0 and not args.no_plain:
             Q.qdta_profile_enable(g, True)
             barrier()
             p0 = Q.qdta_profile_read(g)["kernel_launches"]
@@ -663,16 +739,29 @@ def main():
             prof = Q.qdta_profile_read(g)
             plain_launches = prof["kernel_launches"] - p0
             Q.qdta_profile_enable(g, False)
+            kind = "plain"
         else:
             one_day(params_graph)
+            kind = "graph"
+        day_s.append(time.monotonic() - t0)
+        warm_done += 1
+        progress(f"warm-up day {warm_done} ({kind} schedule): {day_s[-1]:.1f} s")
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
     e2e_list, day_list, stats = [], [], None
-    for _ in range(args.steps):
+    while len(day_list) < max(args.steps, 1):
+        if day_list:
+            est = max(day_s[-3:])
+            if not agree(time.monotonic() - T_START + est + reserve_s < budget):
+                break
+        t0 = time.monotonic()
         e2e_ms_i, day_ms_i, stats = one_day(params_graph)
+        day_s.append(time.monotonic() - t0)
         e2e_list.append(e2e_ms_i)
         day_list.append(day_ms_i)
+        progress(f"timed day {len(day_list)} (graph schedule): {day_ms_i / 1e3:.2f} s on the device, "
+                 f"{e2e_ms_i / 1e3:.2f} s end to end")
     barrier()
     clk = clocks.stop()
     ms = float(np.mean(day_list))
@@ -716,6 +805,11 @@ def main():
     gaps = [s["dual_gap"] for s in stats if s["aon_calls"]]
     cfg["duality_gap_max"] = max(gaps, default=0.0)
     cfg["duality_gap_median"] = float(np.median(gaps)) if gaps else 0.0
+    cfg["intervals_with_duality_gap_le_1e-4"] = int(sum(1 for x in gaps if 0.0 <= x <= 1e-4))
+    cfg["intervals_with_demand"] = len(gaps)
+    cfg["per_interval"] = {"aon": [s["aon_calls"] for s in stats], "fw": [s["iterations"] for s in stats],
+                           "sweeps": [s["ls_passes"] for s in stats],
+                           "dual_gap": [round(s["dual_gap"], 7) for s in stats]}
     cfg["generation_s"] = t_gen
 
     cpu = None
@@ -724,13 +818,15 @@ def main():
 
     if rank == 0:
         line = {"metric": METRIC, "value": job_seconds_per_day(ms, world), "unit": "s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "steps": len(day_list), "warmup": warm_done, "ms_per_step": ms,
+                "steps_requested": args.steps, "warmup_requested": args.warmup,
+                "budget_s": args.budget_s,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "int32 costs/int64 flows + f64 line search", "data": "synthetic",
                 "config": cfg, "clocks": clk,
                 "e2e": {"value": job_seconds_per_day(e2e_ms, world), "unit": "s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "gpu_launches": int(plain_launches * args.steps) if plain_launches else None,
+                "gpu_launches": int(plain_launches * len(day_list)) if plain_launches else None,
                 "gpu_launches_note": ("kernels per timed step, counted on the plain schedule of the same day "
                                       "(first warm-up step; the graph schedule replays the identical kernel "
                                       "sequence)"),

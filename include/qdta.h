@@ -274,13 +274,12 @@ int qdta_tape_info(const qdta_tape *tape, int32_t *K_out_host, int64_t *n_items_
 /* Batched shortest paths that allocate no device memory.
  *
  * The paper has no counterpart: this exists for callers that cannot call
- * cudaMalloc at the moment they need shortest paths -- for example code that
- * runs while its stream is being captured into a CUDA graph (an allocation
- * there is an illegal call under the default capture mode), latency-critical
- * loops where an allocation can stall, or processes whose device memory is
- * fully reserved up front by another allocator.  qdta_sssp_batch, by
- * contrast, grows a workspace with cudaMalloc the first time it sees a
- * larger graph.
+ * cudaMalloc at the moment they need shortest paths -- for example a process
+ * whose device memory is reserved up front by another allocator (a caching
+ * pool that holds all free memory, so a fresh cudaMalloc fails), or a
+ * latency-critical loop that must not stall in the driver's allocator.
+ * qdta_sssp_batch, by contrast, grows a workspace with cudaMalloc the first
+ * time it sees a larger graph.
  *
  * Same arguments, results and error codes as qdta_sssp_batch, for graphs
  * with at most QDTA_NOALLOC_MAX_LINKS links whose per-root state fits in

@@ -820,13 +820,17 @@ static int sssp_work(qdta_graph *g, int grid, SsspWork *w) {
   return QDTA_OK;
 }
 
-// one batch: pack adjacency for q, then SSSP over the roots
+// one batch: pack adjacency for q, then SSSP over the roots.  `profile`
+// false leaves the launch out of the per-kernel timings (a batch the host
+// knows is skipped on the device: its kernels return at once)
 static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots, int R_host,
                     const int *R_dev, int R_cap, int *parent, const int *slot_dev, long long stride,
-                    long long *dist, cudaStream_t s, const int *skip_dev = nullptr) {
+                    long long *dist, cudaStream_t s, const int *skip_dev = nullptr, bool profile = true) {
   SsspWork w;
   const int grid = sssp_grid(g, R_cap);
   RC(sssp_work(g, grid, &w));
+  const int prof_saved = g->prof_on;
+  if (!profile) g->prof_on = 0;
   ProfEvent pe;
   if (g->sssp_kind == 1) {
     launch_pack_cell_adj(g->d, g->cells, direction, q, w.adj, w.lrev, g->n_lrev[direction], w.xrev,
@@ -847,6 +851,7 @@ static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots
                 stride, dist, g->status, s, skip_dev, g->prof_on ? g->prof_roots : nullptr);
   }
   prof_end(g, s, &pe);
+  g->prof_on = prof_saved;
   return QDTA_OK;
 }
 
@@ -1552,8 +1557,18 @@ static int day_res_body(Day &D, unsigned long long h, int use_cond) {
   Solver &S = D.S;
   cudaStream_t s = S.s;
   launch_res_prep(S.ctl, D.w, S.tape_q, g->d.L, D.q_work, s);
+  // On the plain schedule with profiling on, the host reads whether tree j
+  // is still stored, so that skipped batches do not enter the per-batch
+  // timings.  The kernels are launched either way (and return at once when
+  // skipped), as on the graph schedule.
+  bool real_batch = true;
+  if (!use_cond && g->prof_on) {
+    Ctl *hc = (Ctl *)g->ctl_h;
+    RC(read_ctl(S, hc));
+    real_batch = !hc->res_skip;
+  }
   RC(run_sssp(g, QDTA_TO_ROOT, D.q_work, S.roots, 0, S.R_dev, S.R_cap, S.parent, &S.ctl->res_slot,
-              S.parent_stride, nullptr, s, &S.ctl->res_skip));
+              S.parent_stride, nullptr, s, &S.ctl->res_skip, real_batch));
   launch_residual(g->d, D.hq_fin, S.parent, &S.ctl->res_slot, S.parent_stride, D.root_slot, D.zones,
                   D.n_items_dev, D.cap_items, D.it_root, D.it_src, D.it_amt, &S.ctl->w_cur, S.dt_q, D.h_fx,
                   D.dense, g->status, s);

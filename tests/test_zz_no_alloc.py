@@ -1,7 +1,7 @@
 """The shortest-path entry point that allocates no device memory.
 
 It serves callers that cannot call cudaMalloc when they need shortest paths
-(for example while their stream is being captured into a CUDA graph).  Its
+(for example a process whose device memory is held by another allocator).  Its
 results must equal qdta_sssp_batch's, call after call, even though every call
 reuses one fixed device scratch array.  This file is collected last so that a
 run stopping at the first failure has already run every other test.
