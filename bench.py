@@ -805,7 +805,7 @@ def main():
     gaps = [s["dual_gap"] for s in stats if s["aon_calls"]]
     cfg["duality_gap_max"] = max(gaps, default=0.0)
     cfg["duality_gap_median"] = float(np.median(gaps)) if gaps else 0.0
-    cfg["intervals_with_duality_gap_le_1e-4"] = int(sum(1 for x in gaps if 0.0 <= x <= 1e-4))
+    cfg["intervals_with_duality_gap_le_1e-4"] = int(sum(1 for x in gaps if -1e-12 <= x <= 1e-4))
     cfg["intervals_with_demand"] = len(gaps)
     cfg["per_interval"] = {"aon": [s["aon_calls"] for s in stats], "fw": [s["iterations"] for s in stats],
                            "sweeps": [s["ls_passes"] for s in stats],

@@ -59,7 +59,8 @@ extern "C" {
 
 #define QDTA_STOP_NONE 0      /* run exactly max_iter steps */
 #define QDTA_STOP_PAPER_OBJ 1 /* |C(f) - C(f_new)| / C(f) < tol (Section 4, Converged) */
-#define QDTA_STOP_REL_GAP 2   /* (sum c f - sum c g) / sum c f <= tol */
+#define QDTA_STOP_REL_GAP 2   /* -1e-12 <= (sum c f - sum c g) / sum c f <= tol: a negative gap
+                                 (possible with truncated loading, Eq. 2) does not stop */
 
 /* Objective (Section 3 names both; the paper solves the user equilibrium).
  * QDTA_OBJ_SO minimises the total cost sum f c(f): routing on the quantised
@@ -151,6 +152,7 @@ typedef struct {
   int64_t sssp_rounds;      /* frontier rounds summed over the roots solved */
   int64_t sssp_relaxations; /* link relaxations summed over the roots solved */
   int64_t sssp_cell_activations; /* cell activations (cell-partitioned kernel) */
+  int64_t sssp_redo_batches; /* 32-bit-key batches rerun with 64-bit keys (a distance >= 2^29 quanta) */
 } qdta_profile;
 
 /* ---------------------------------------------------------------------- */

@@ -773,8 +773,14 @@ static int assign_core(const or_graph *g, const or_od *od, double dt_s, const or
       }
       st->dual_gap = fx_to_double(A - B) / fx_to_double(A);
       if (p->stop == STOP_REL_GAP) {
+        /* The gap certifies convergence only when it is not negative.  With
+         * truncated loading (Eq. 2) the all-or-nothing loading g need not
+         * minimise sum c g, so the gap can fall below zero without f being
+         * near an equilibrium; such a value does not stop the iteration.
+         * -1e-12 absorbs the rounding of the per-link products c f at an
+         * exact all-or-nothing equilibrium (gap 0 up to a few ulps). */
         st->rel_gap = st->dual_gap;
-        if (st->rel_gap <= p->tol) { st->converged = 1; break; }
+        if (st->rel_gap <= p->tol && st->rel_gap >= -1e-12) { st->converged = 1; break; }
       }
     }
     int passes = 0;

@@ -752,11 +752,11 @@ extern "C" int qdta_profile_enable(qdta_graph *g, int32_t on) {
   DevGuard guard(g->device);
   if (!g->prof_roots) {
     void *p = nullptr;
-    CK(cudaMalloc(&p, 32));
+    CK(cudaMalloc(&p, 64));
     g->owned.push_back(p);
     g->prof_roots = (unsigned long long *)p;
   }
-  CK(cudaMemset(g->prof_roots, 0, 32));
+  CK(cudaMemset(g->prof_roots, 0, 64));
   g->prof_on = on ? 1 : 0;
   g->prof = qdta_profile{};
   return QDTA_OK;
@@ -768,12 +768,14 @@ extern "C" int qdta_profile_read(qdta_graph *g, qdta_profile *out) {
   DevGuard guard(g->device);
   CK(cudaDeviceSynchronize());
   prof_harvest(g);
-  unsigned long long cnt[4] = {0, 0, 0, 0};
-  if (g->prof_roots) CK(cudaMemcpy(cnt, g->prof_roots, 32, cudaMemcpyDeviceToHost));
+  // device counters: roots, rounds, relaxations, cell activations, redone batches
+  unsigned long long cnt[5] = {0, 0, 0, 0, 0};
+  if (g->prof_roots) CK(cudaMemcpy(cnt, g->prof_roots, sizeof cnt, cudaMemcpyDeviceToHost));
   g->prof.sssp_roots = (int64_t)cnt[0];
   g->prof.sssp_rounds = (int64_t)cnt[1];
   g->prof.sssp_relaxations = (int64_t)cnt[2];
   g->prof.sssp_cell_activations = (int64_t)cnt[3];
+  g->prof.sssp_redo_batches = (int64_t)cnt[4];
   g->prof.kernel_launches = launch_count();
   *out = g->prof;
   return QDTA_OK;
@@ -1754,6 +1756,11 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   long long ring = p->max_iter + 1;
   long long afford = (long long)((double)free_b * 0.8 / per_slot);
   if (ring > afford) ring = afford;
+  // QDTA_TREE_RING=n caps the ring (tests: residual trees rebuilt from the tape)
+  if (const char *e = getenv("QDTA_TREE_RING")) {
+    const long long cap = atoll(e);
+    if (cap >= 2 && cap < ring) ring = cap;
+  }
   if (ring < 2) ring = 2;
   RC(solver_alloc(S, "day", (int)ring, false));
   RC(status_reset(g, s));

@@ -1167,12 +1167,14 @@ int sssp_blocks_per_sm(bool use_smem, int V) {
 
 // after a 32-bit-key batch: run the 64-bit redo only if the batch overflowed
 // (and was not skipped); clears the overflow bit, which is not an error
-__global__ void k32_redo_flag_kernel(unsigned *status, const int *skip_dev, int *fb_skip) {
+__global__ void k32_redo_flag_kernel(unsigned *status, const int *skip_dev, int *fb_skip,
+                                     unsigned long long *redo_counter) {
   const unsigned st = *status;
   const bool skipped = skip_dev && *skip_dev;
   const bool redo = !skipped && (st & ST_K32);
   if (st & ST_K32) atomicAnd(status, ~ST_K32);
   *fb_skip = redo ? 0 : 1;
+  if (redo && redo_counter) atomicAdd(redo_counter, 1ull);
 }
 
 using SmqKernel = void (*)(int, int, const int *, const int4 *, const int *, int, const int *, unsigned long long *,
@@ -1254,24 +1256,26 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
       const int threads = kSmqShape[g.tune_shape].threads;
       const bool perm = g.node_int != nullptr;
-      auto run = [&](SmqKernel kern, const int *skip) {
+      auto run = [&](SmqKernel kern, const int *skip, unsigned long long *counters) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
         COUNT_LAUNCH();
         kern<<<grid, threads, smq, s>>>(g.V, g.LB, perm ? g.perm_off[direction] : off, adj, roots, R_host, R_dev,
                                         w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip,
-                                        roots_counter, perm ? g.node_int : nullptr, round_limit(g.V),
+                                        counters, perm ? g.node_int : nullptr, round_limit(g.V),
                                         kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
                                         g.rank_link[direction], g.skip_parent);
       };
-      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev);
+      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev, roots_counter);
       if (adjl == 3) {
         // a distance beyond the 32-bit keys' range: redo the batch with 64-bit
         // keys on the same packed adjacency (decided on the device, so graph
-        // replays need no host round trip)
+        // replays need no host round trip).  The redo's roots are not counted
+        // again; counter [4] counts redone batches.
         COUNT_LAUNCH();
-        k32_redo_flag_kernel<<<1, 1, 0, s>>>(status, skip_dev, w.fb_skip);
-        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip);
+        k32_redo_flag_kernel<<<1, 1, 0, s>>>(status, skip_dev, w.fb_skip,
+                                             roots_counter ? roots_counter + 4 : nullptr);
+        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip, nullptr);
       }
       return;
     }
@@ -1777,7 +1781,10 @@ __global__ void ctl_step_kernel(Ctl *c, cudaGraphConditionalHandle h_ls, int use
     c->dual_gap = dvd(fx_to_double(A - B), fx_to_double(A));
     c->plan.want_gap = 0;
     if (c->stop == 2) c->rel_gap = c->dual_gap;
-    if (c->stop == 2 && c->rel_gap <= c->tol) {
+    // a negative gap (truncated loading: g need not minimise sum c g) is no
+    // certificate and does not stop; -1e-12 is rounding at an exact
+    // all-or-nothing equilibrium
+    if (c->stop == 2 && c->rel_gap <= c->tol && c->rel_gap >= -1e-12) {
       c->converged = 1;
       c->fw_continue = 0;
       c->do_update = 0;

@@ -71,7 +71,8 @@ class Profile(C.Structure):
                 ("load_launches", C.c_int64), ("load_ms", C.c_double),
                 ("sweep_launches", C.c_int64), ("sweep_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("sssp_rounds", C.c_int64),
-                ("sssp_relaxations", C.c_int64), ("sssp_cell_activations", C.c_int64)]
+                ("sssp_relaxations", C.c_int64), ("sssp_cell_activations", C.c_int64),
+                ("sssp_redo_batches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

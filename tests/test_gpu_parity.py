@@ -387,6 +387,37 @@ def test_empty_interval(small):
         assert float(f.abs().sum()) == 0.0 and st["converged"] == 1 and st["aon_calls"] == 0
 
 
+def _diamond(ff_s, cap):
+    """0 -> 1 -> 3 and 0 -> 2 -> 3 (links 0->1, 0->2, 1->3, 2->3)."""
+    return synth.Network(n_nodes=4, tail=np.array([0, 0, 1, 2], np.int32), head=np.array([1, 2, 3, 3], np.int32),
+                         fftime_q=np.rint(np.array(ff_s, np.float64) / 0.01).astype(np.int32),
+                         capacity=np.array(cap, np.float64), length_m=np.zeros(4), link_class=np.zeros(4, np.int8),
+                         x=np.arange(4.0), y=np.zeros(4))
+
+
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+@pytest.mark.parametrize("cap02,trips,ff", [(632.6, 100, [200, 340, 1000, 400]), (700.0, 100, [200, 340, 1000, 400]),
+                                            (200.0, 150, [301, 340, 1000, 10])])
+def test_rel_gap_stop_with_negative_and_rounding_level_gaps(schedule, cap02, trips, ff):
+    """Truncation (Δt = 300 s) makes the gap negative on the first case (no
+    convergence, every step 0), exactly 0 on the second and a few ulps below 0
+    at an equilibrium on the third (both stop); bit-exact with the oracle."""
+    caps = [5000, cap02, 5000, 5000] if ff[3] == 400 else [400, cap02, 400, 400]
+    net = _diamond(ff, caps)
+    dem = synth.Demand(roots=np.array([3], np.int32), root_idx=np.array([0], np.int32), src=np.array([0], np.int32),
+                       amount_fx=np.array([trips << 32], np.int64))
+    og = oracle.OracleGraph(net)
+    f_o, st_o, rc_o = oracle.assign_interval(og, oracle.OracleOD.of(dem), 300.0,
+                                             oracle.make_params(Q.STEP["sweep8"], Q.STOP["rel_gap"], 12))
+    f_g, st_g, rc_g, _ = Q.qdta_assign_interval(Q.Graph(net), Q.DeviceOD.of(dem), 300.0,
+                                                 Q.make_params("sweep8", "rel_gap", 12, schedule=schedule))
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    for key in ("iterations", "aon_calls", "ls_passes", "converged", "dual_gap", "rel_gap"):
+        assert st_g[key] == st_o[key], key
+    assert (rc_g == Q.QDTA_ENOTCONV) == (rc_o == oracle.NOTCONV)
+    assert st_g["converged"] == (0 if cap02 == 632.6 else 1)
+
+
 # ---------------------------------------------------------------------------
 def _day_case(n_int=6, trips=40000):
     base = synth.config_small(0)
@@ -457,6 +488,97 @@ def test_run_day_worked_example(schedule):
     np.testing.assert_array_equal(f[0], [43.75, 43.75, 0, 0])
     np.testing.assert_array_equal(f[1], [0, 0, 56.25, 12.5])
     assert [s["n_items"] for s in st] == [1, 2, 0, 0]
+
+
+# ---------------------------------------------------------------------------
+# A day on a graph above the shared-memory limit: the kernels the metro day
+# runs (the global-key shortest-path kernel with 32-bit rank keys, the tree
+# ring of the residual pass, the free-flow tree cache, the dense merge).
+def _mid_day():
+    """110 x 110 grid (12,100 nodes) plus a pendant node w hung off a boundary
+    node u by two 100 s links; w -> u has a capacity of 4/3 veh/h, so its 10
+    trips in intervals 1 and 3 price it at about 1.2e9 quanta (Eq. 1).  Every
+    distance from w then exceeds the 32-bit keys' 2^29 range, and those
+    intervals' batches after the first are rerun with 64-bit keys.  150
+    zones, six intervals of uneven gravity demand; at 40 km/h most trips cross
+    several intervals, so residual demand is carried between them."""
+    net = synth.grid_network(110, 5, freeways=True)
+    V = net.n_nodes
+    deg_out = np.bincount(net.tail, minlength=V)
+    deg_in = np.bincount(net.head, minlength=V)
+    u = int(next(c for c in range(5, 100) if deg_out[c] <= 3 and deg_in[c] <= 3))
+    w = V
+    tail = np.concatenate([net.tail, [u, w]]).astype(np.int32)
+    head = np.concatenate([net.head, [w, u]]).astype(np.int32)
+    order = np.lexsort((head, tail))
+
+    def ext(a, extra):
+        return np.concatenate([a, extra])[order]
+    net2 = synth.Network(n_nodes=V + 1, tail=tail[order], head=head[order],
+                         fftime_q=ext(net.fftime_q, np.array([10000, 10000], np.int32)).astype(np.int32),
+                         capacity=ext(net.capacity, np.array([800.0, 4.0 / 3.0])),
+                         length_m=ext(net.length_m, np.array([1000.0, 1000.0])),
+                         link_class=ext(net.link_class, np.array([0, 0], np.int8)),
+                         x=np.concatenate([net.x, [net.x[u]]]), y=np.concatenate([net.y, [net.y[u] - 1000.0]]),
+                         alpha=net.alpha, beta=net.beta, quantum_s=net.quantum_s)
+    zones = synth.pick_zones(net, 150, 5)
+    wts = synth.gravity_weights(net, zones, 5, 4000.0)
+    days = []
+    for i, (t, wt) in enumerate(zip((9000, 40000, 80000, 30000, 8000, 2000), (0, 10, 0, 10, 0, 0))):
+        d = synth.demand_from_matrix(zones, synth.sample_trips(wts, t, 40 + i))
+        if wt:
+            ri = np.concatenate([d.root_idx, [0]])
+            src = np.concatenate([d.src, [w]])
+            am = np.concatenate([d.amount_fx, [wt << 32]])
+            o = np.lexsort((src, ri))
+            d = synth.Demand(roots=d.roots, root_idx=ri[o].astype(np.int32), src=src[o].astype(np.int32),
+                             amount_fx=am[o].astype(np.int64))
+        days.append(d)
+    return net2, zones, days
+
+
+MID_DAY_PARAMS = ("sweep8", "paper_obj", 10)
+
+
+@pytest.fixture(scope="module")
+def mid_day():
+    net, zones, days = _mid_day()
+    og = oracle.OracleGraph(net)
+    ref = oracle.run_day(og, zones, days, 900.0, oracle.make_params(Q.STEP[MID_DAY_PARAMS[0]],
+                                                                     Q.STOP[MID_DAY_PARAMS[1]], MID_DAY_PARAMS[2]))
+    return net, zones, days, ref
+
+
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+@pytest.mark.parametrize("variant", ["default", "ring3", "no_ff_cache"])
+def test_run_day_large_graph_bit_exact(mid_day, schedule, variant, monkeypatch):
+    """Bit-exact h(i) flows, per-interval stats, merged item counts and the
+    final residual against the oracle's day, on both schedules; with the tree
+    ring capped at 3 slots (the residual pass rebuilds trees 2..K from the
+    taped link times) and without the free-flow tree cache."""
+    net, zones, days, (f_o, st_o, nit_o, rn_o, rc_o) = mid_day
+    if variant == "ring3":
+        monkeypatch.setenv("QDTA_TREE_RING", "3")
+    if variant == "no_ff_cache":
+        monkeypatch.setenv("QDTA_NO_FF_CACHE", "1")
+    g = Q.Graph(net)
+    assert "rank32" in Q.qdta_sssp_kernel_name(g)  # the metro day's kernel family
+    zt = T(zones, np.int32)
+    dd = [Q.DeviceOD(zt, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
+    Q.qdta_profile_enable(g, schedule == "plain")
+    f_g, st_g, rc_g, resid = Q.qdta_run_day(g, dd, 900.0, Q.make_params(*MID_DAY_PARAMS, schedule=schedule),
+                                            resid_capacity=1 << 20)
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    for i in range(len(days)):
+        assert st_g[i]["n_items"] == nit_o[i]
+        for key in ("iterations", "aon_calls", "ls_passes", "converged", "rel_gap", "dual_gap", "objective"):
+            if not (isinstance(st_o[i][key], float) and np.isnan(st_o[i][key])):
+                assert st_g[i][key] == st_o[i][key], (i, key)
+    assert resid[0].shape[0] == rn_o
+    assert sum(s["iterations"] for s in st_o) >= 20 and max(nit_o) > max(d.n_items for d in days)
+    if schedule == "plain":
+        prof = Q.qdta_profile_read(g)
+        assert prof["sssp_redo_batches"] > 0  # the 2^29 overflow happened inside the day
 
 
 # ---------------------------------------------------------------------------

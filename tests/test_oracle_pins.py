@@ -297,6 +297,38 @@ def test_line_search_against_dense_grid(mode):
     assert np.all(np.diff(d) >= -1e-6 * np.abs(vals).max())
 
 
+def test_sweep8_returns_the_exact_step_when_the_slope_is_linear():
+    """With BPR beta = 1 the objective (Eq. 6) is quadratic along the FW
+    direction, so its slope is linear in alpha and the step has a closed form:
+    alpha* = -S0 / S1 with S0 = sum c0 (1 + a f/K)(g - f), S1 = sum c0 a (g - f)^2 / K
+    (K = C dt_h).  The 8-point sweep returns the secant zero of the slope
+    inside its final bracket, which is alpha* up to the rounding of the
+    fixed-point sums; a midpoint return would be off by up to T2 / 2."""
+    rng = np.random.default_rng(23)
+    net = synth.random_graph(10, 15, 5)
+    net.beta = 1
+    g = oracle.OracleGraph(net)
+    L = net.n_links
+    K = [Fraction(float(c)) * Fraction(900, 3600) for c in net.capacity]
+    a_bpr = Fraction(net.alpha)
+    checked = 0
+    for trial in range(6):
+        f = rng.uniform(0, 400, L)
+        gfx = (rng.uniform(0, 400, L) * (1 << 32)).astype(np.int64)
+        d = [Fraction(int(gfx[a]), 1 << 32) - Fraction(float(f[a])) for a in range(L)]
+        S0 = sum(int(net.fftime_q[a]) * (1 + a_bpr * Fraction(float(f[a])) / K[a]) * d[a] for a in range(L))
+        S1 = sum(int(net.fftime_q[a]) * a_bpr * d[a] * d[a] / K[a] for a in range(L))
+        if not (S0 < 0 < S0 + S1):  # interior minimiser only
+            continue
+        want = float(-S0 / S1)
+        alpha, passes, rc = oracle.line_search(g, f, gfx, 900.0, 1,
+                                               oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_NONE, 20))
+        assert rc == 0 and abs(alpha - want) < 1e-9, (trial, alpha, want)
+        assert abs(alpha - want) < 1e-3 * 1e-4  # far inside the T2 = 1e-4 bracket
+        checked += 1
+    assert checked >= 2
+
+
 # ----------------------------------------------------------------------------
 # equilibrium closed forms (Eq. 4 with strictly increasing costs)
 # ----------------------------------------------------------------------------
@@ -650,3 +682,63 @@ def test_day_advances_a_trip_one_link_per_interval_when_links_outlast_dt():
     # step-weighted shares are rounded to 2^-32 trips each (R9)
     np.testing.assert_allclose(f, [[1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, 0]], rtol=0, atol=4 * 2.0 ** -32)
     assert list(nit) == [1, 1, 1, 0]
+
+
+# ----------------------------------------------------------------------------
+# the relative-gap stop rule under truncation
+# ----------------------------------------------------------------------------
+def _diamond(ff_s, cap):
+    """0 -> 1 -> 3 and 0 -> 2 -> 3 (links 0->1, 0->2, 1->3, 2->3)."""
+    return synth.Network(n_nodes=4, tail=np.array([0, 0, 1, 2], np.int32), head=np.array([1, 2, 3, 3], np.int32),
+                         fftime_q=np.rint(np.array(ff_s, np.float64) / 0.01).astype(np.int32),
+                         capacity=np.array(cap, np.float64), length_m=np.zeros(4), link_class=np.zeros(4, np.int8),
+                         x=np.arange(4.0), y=np.zeros(4))
+
+
+def _diamond_od(trips):
+    return oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([0], np.int32),
+                           np.array([trips << 32], np.int64))
+
+
+def test_rel_gap_stop_ignores_a_negative_gap():
+    """With Δt = 300 s, route B (0->2 340 s, 2->3 400 s) is shortest at free
+    flow and its trips stop at node 2 (Eq. 2), loading only 0->2.  Congested
+    by 100 trips at 632.6 veh/h, 0->2 costs c02 ≈ 1000 s, so route A (0->1
+    200 s, 1->3 1000 s) becomes shortest and its trips arrive, loading 1200 s.
+    The gap (c02·100 - 1200·100) / (c02·100) is then negative: the truncated
+    all-or-nothing loading does not minimise sum c g.  Moving towards it raises
+    the objective, so every step is 0 and the gap stays; the relative-gap rule
+    must not report convergence on it."""
+    net = _diamond([200, 340, 1000, 400], [5000, 632.6, 5000, 5000])
+    og = oracle.OracleGraph(net)
+    # c02 in quanta by Eq. 1, exact: 34000 (1 + 0.15 x^4), x = 100 / (632.6 · 300/3600)
+    x = Fraction(100) / (Fraction(6326, 10) * Fraction(300, 3600))
+    c02 = Fraction(34000) * (1 + Fraction(15, 100) * x ** 4)
+    q02 = math.floor(c02 + Fraction(1, 2))
+    want_gap = float(Fraction(q02 * 100 - 120000 * 100, q02 * 100))
+    assert want_gap < -0.19
+    f, st, rc = oracle.assign_interval(og, _diamond_od(100), 300.0,
+                                       oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_REL_GAP, 12))
+    assert abs(st["dual_gap"] - want_gap) < 1e-15
+    assert st["converged"] == 0 and rc == oracle.NOTCONV and st["iterations"] == 12
+    np.testing.assert_array_equal(f, [0.0, 100.0, 0.0, 0.0])
+    # the paper's objective-change rule stops at once (the step is 0)
+    f, st, rc = oracle.assign_interval(og, _diamond_od(100), 300.0,
+                                       oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_PAPER_OBJ, 12))
+    assert st["converged"] == 1 and rc == oracle.OK
+
+
+def test_rel_gap_stop_accepts_zero_and_rounding_level_gaps():
+    """Less congestion (700 veh/h): route B stays shortest, g = f and the gap
+    is exactly 0, which stops at the first check.  On a two-route split whose
+    first links tie in cost, the gap of an equilibrium comes out a few ulps
+    below zero from the rounding of the products c f; it still stops."""
+    og = oracle.OracleGraph(_diamond([200, 340, 1000, 400], [5000, 700.0, 5000, 5000]))
+    f, st, rc = oracle.assign_interval(og, _diamond_od(100), 300.0,
+                                       oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_REL_GAP, 12))
+    assert st["dual_gap"] == 0.0 and st["converged"] == 1 and st["iterations"] == 0
+    og = oracle.OracleGraph(_diamond([301, 340, 1000, 10], [400, 200, 400, 400]))
+    f, st, rc = oracle.assign_interval(og, _diamond_od(150), 300.0,
+                                       oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_REL_GAP, 30))
+    assert -1e-15 < st["dual_gap"] <= 0.0 and st["converged"] == 1 and rc == oracle.OK
+    assert abs(f.sum() - 150.0) < 1e-9 and f[2] == f[3] == 0.0
