@@ -164,6 +164,15 @@ typedef struct {
 int qdta_graph_create(const qdta_graph_desc *desc, int device, qdta_graph **out);
 int qdta_graph_destroy(qdta_graph *g);
 
+/* Replace the link capacities C_a (Eq. 1, vehicles per hour) of an existing
+ * graph by capacity_vph [L], a DEVICE array on `stream`, without rebuilding
+ * the graph (for repeated solves over changing capacities, e.g. a training
+ * loop differentiating through qdta_assign_interval).  Every value must be
+ * finite and > 0: otherwise QDTA_EINVAL and the graph keeps its capacities.
+ * Later calls on the graph use the new values; a tape recorded earlier keeps
+ * the capacities of its own solve.  Synchronises `stream`. */
+int qdta_graph_set_capacity(qdta_graph *g, const double *capacity_vph, void *stream);
+
 /* Batched single-source shortest paths (the Get_shortest_path of Alg. 3 and
  * Alg. 7, for all nodes at once).  For each root r and node v:
  * TO_ROOT: dist = shortest time v -> roots[r]; parent = the smallest link id

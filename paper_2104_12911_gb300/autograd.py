@@ -16,11 +16,21 @@ import torch
 from . import qdta as Q
 
 
+def graph_for(net, device: int) -> "Q.Graph":
+    """One graph handle per (network, device), kept on the network object and
+    reused by every solve; capacities are replaced on the device per call
+    (qdta_graph_set_capacity) instead of building a new graph."""
+    cache = net.__dict__.setdefault("_qdta_graphs", {})
+    if device not in cache:
+        cache[device] = Q.Graph(net, device)
+    return cache[device]
+
+
 class QdtaAssign(torch.autograd.Function):
     @staticmethod
     def forward(ctx, amounts, capacity, net, roots, root_idx, src, dt_s, params):
-        cap = capacity.detach().to("cpu", torch.float64).numpy()
-        g = Q.Graph(net, amounts.device.index or 0, capacity=cap)
+        g = graph_for(net, amounts.device.index or 0)
+        g.set_capacity(capacity)
         amount_fx = torch.round(amounts.detach() * float(Q.FX_ONE)).to(torch.int64)
         od = Q.DeviceOD(roots, root_idx, src, amount_fx)
         p = Q.Params.from_buffer_copy(params)

@@ -92,6 +92,7 @@ struct qdta_tape {
   int *q = nullptr;       // [(K+1) * L]
   double *alpha = nullptr; // [K+1]
   double *f = nullptr;    // [(K+1) * L]
+  double *cap = nullptr;  // [L] capacities of the taped solve (the graph's may change later)
 };
 
 // ---------------------------------------------------------------------------
@@ -168,6 +169,7 @@ static int status_check(qdta_graph *g, cudaStream_t s) {
   if (st & ST_OVERFLOW) return fail(QDTA_EOVERFLOW, "a shortest distance exceeded the packed range");
   if (st & ST_UNREACH) return fail(QDTA_EUNREACH, "a destination is unreachable from an origin");
   if (st & ST_CAPACITY) return fail(QDTA_ENOMEM, "an internal item buffer was too small");
+  if (st & ST_BADARG) return fail(QDTA_EINVAL, "a device array argument held an invalid value");
   return QDTA_OK;
 }
 
@@ -731,6 +733,19 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   if (cudaGetLastError() != cudaSuccess) { qdta_graph_destroy(g); return fail(QDTA_ECUDA, "occupancy query failed"); }
   *out = g;
   return QDTA_OK;
+}
+
+extern "C" int qdta_graph_set_capacity(qdta_graph *g, const double *capacity_vph, void *stream) {
+  RC(check_graph(g));
+  if (g->d.L > 0 && !capacity_vph) return fail(QDTA_EINVAL, "capacity_vph is NULL");
+  if (g->d.L == 0) return QDTA_OK;
+  DevGuard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  RC(status_reset(g, s));
+  launch_set_capacity(g->d, capacity_vph, g->status, s);
+  int rc = status_check(g, s);
+  if (rc == QDTA_EINVAL) return fail(QDTA_EINVAL, "capacities must be finite and > 0 (graph unchanged)");
+  return rc;
 }
 
 extern "C" int qdta_graph_destroy(qdta_graph *g) {
@@ -1387,8 +1402,10 @@ static int assign_core(qdta_graph *g, const qdta_od *od, double dt_s, const qdta
     const size_t L = g->d.L, K1 = (size_t)t->K + 1;
     bool ok = cudaMalloc(&t->q, K1 * L * 4 + 16) == cudaSuccess &&
               cudaMalloc(&t->alpha, K1 * 8 + 16) == cudaSuccess &&
-              cudaMalloc(&t->f, K1 * L * 8 + 16) == cudaSuccess;
+              cudaMalloc(&t->f, K1 * L * 8 + 16) == cudaSuccess &&
+              cudaMalloc(&t->cap, L * 8 + 16) == cudaSuccess;
     if (!ok) { cudaGetLastError(); qdta_tape_destroy(t); return fail(QDTA_ENOMEM, "tape allocation"); }
+    CK(cudaMemcpyAsync(t->cap, g->d.cap, L * 8, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(t->q, S.tape_q, K1 * L * 4, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(t->alpha, S.tape_alpha, K1 * 8, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(t->f, S.tape_f, K1 * L * 8, cudaMemcpyDeviceToDevice, s));
@@ -1809,6 +1826,7 @@ extern "C" int qdta_tape_destroy(qdta_tape *t) {
   if (t->q) cudaFree(t->q);
   if (t->alpha) cudaFree(t->alpha);
   if (t->f) cudaFree(t->f);
+  if (t->cap) cudaFree(t->cap);
   delete t;
   return QDTA_OK;
 }
@@ -1851,7 +1869,10 @@ extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_dd
   RC(ws_get(g, "bw.parent", (size_t)R * g->d.V, &parent));
   std::vector<double> alpha(t->K + 1);
   CK(cudaMemcpy(alpha.data(), t->alpha, sizeof(double) * (t->K + 1), cudaMemcpyDeviceToHost));
-  launch_link_const(g->d, dt_h, kc, s);
+  // per-link constants from the capacities the taped solve used
+  GraphDev gd_tape = g->d;
+  gd_tape.cap = t->cap;
+  launch_link_const(gd_tape, dt_h, kc, s);
   CK(cudaMemcpyAsync(lam, dL_dflow, L * 8, cudaMemcpyDeviceToDevice, s));
   if (n > 0) CK(cudaMemsetAsync(dL_ddemand, 0, (size_t)n * 8, s));
   CK(cudaMemsetAsync(dL_dcap, 0, L * 8, s));
@@ -1868,8 +1889,8 @@ extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_dd
       const double *fprev = t->f + (size_t)(k - 1) * L;
       const double a = alpha[k];
       const int implicit = t->step != QDTA_STEP_MSA && a > 0.0 && a < 1.0;
-      launch_adj_reduce(g->d, kc, lam, fprev, (const long long *)gfx, a, implicit, red, muH, grid, s);
-      launch_adj_update(g->d, kc, lam, fprev, (const long long *)gfx, a, implicit, muH, gbar, lam2, dL_dcap, s);
+      launch_adj_reduce(gd_tape, kc, lam, fprev, (const long long *)gfx, a, implicit, red, muH, grid, s);
+      launch_adj_update(gd_tape, kc, lam, fprev, (const long long *)gfx, a, implicit, muH, gbar, lam2, dL_dcap, s);
       gb = gbar;
     }
     launch_gather(g->d, hq, parent, t->od.roots, n, t->od.root_idx, t->od.src, dt_q, gb, dL_ddemand,

@@ -23,6 +23,7 @@ enum : unsigned {
   ST_TIMEOUT = 8u,     // a bounded loop hit its limit
   ST_CAPACITY = 16u,   // an output buffer was too small
   ST_K32 = 32u,        // a 32-bit-key batch met a distance >= 2^29 (redone with 64-bit keys; not an error)
+  ST_BADARG = 64u,     // a device array argument held an invalid value
 };
 
 constexpr int SSSP_THREADS = 256;
@@ -381,6 +382,9 @@ void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *paren
 void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,
                 unsigned *status, cudaStream_t s, int marginal = 0);
 void launch_link_const(const GraphDev &g, double dt_h, LinkConst *kc, cudaStream_t s);
+// replace the graph's capacities by `cap` (device) when every value is finite
+// and > 0; otherwise set ST_BADARG and leave them unchanged
+void launch_set_capacity(const GraphDev &g, const double *cap, unsigned *status, cudaStream_t s);
 void launch_flow_from_fx(int L, const unsigned long long *fx, double *f, cudaStream_t s);
 void launch_sweep(const GraphDev &g, const LinkConst *kc, const double *f, const long long *g_fx,
                   const int *q, Ctl *ctl, i128 *partials, unsigned *counter, int grid,

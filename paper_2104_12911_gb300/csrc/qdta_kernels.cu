@@ -1349,6 +1349,29 @@ static int link_grid(const GraphDev &g, long long n) {
   return want < 1 ? 1 : (int)want;
 }
 
+// capacity update: check every value first, copy only if all are valid
+__global__ void cap_check_kernel(int L, const double *__restrict__ cap, unsigned *status) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) {
+    const double c = cap[a];
+    if (!(c > 0.0) || !isfinite(c)) atomicOr(status, ST_BADARG);
+  }
+}
+
+__global__ void cap_copy_kernel(int L, const double *__restrict__ src, double *__restrict__ dst,
+                                const unsigned *status) {
+  if (*status & ST_BADARG) return;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) dst[a] = src[a];
+}
+
+void launch_set_capacity(const GraphDev &g, const double *cap, unsigned *status, cudaStream_t s) {
+  if (g.L <= 0) return;
+  COUNT_LAUNCH();
+  cap_check_kernel<<<link_grid(g, g.L), 256, 0, s>>>(g.L, cap, status);
+  COUNT_LAUNCH();
+  cap_copy_kernel<<<link_grid(g, g.L), 256, 0, s>>>(g.L, cap, const_cast<double *>(g.cap), status);
+}
+
+
 void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const int *parent_slot_dev,
                  long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
                  const long long *n_items_dev, const int *root_idx, const int *src,

@@ -117,6 +117,7 @@ def lib():
             sig = {
                 "qdta_graph_create": [P, C.c_int, P],
                 "qdta_graph_destroy": [P],
+                "qdta_graph_set_capacity": [P, P, P],
                 "qdta_sssp_batch": [P, P, P, I32, I32, P, P, P],
                 "qdta_sssp_batch_noalloc": [P, P, P, I32, I32, P, P, P],
                 "qdta_load_aon": [P, P, P, P, I64, P, P, P],
@@ -187,6 +188,11 @@ class Graph:
         self.n_links = int(tail.shape[0])
         self.device = torch.device("cuda", device)
         self.quantum_s = float(net.quantum_s)
+
+    def set_capacity(self, capacity):
+        """qdta_graph_set_capacity: capacity is a float64 CUDA tensor [L] (veh/h)."""
+        cap = capacity.detach().to(self.device, torch.float64).contiguous()
+        _check(lib().qdta_graph_set_capacity(self.h, _ptr(cap), _stream()))
 
     def close(self):
         if getattr(self, "h", None):

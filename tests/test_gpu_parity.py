@@ -5,6 +5,8 @@ residual items) must be bit-exact; the FW iteration is bit-exact too because
 every link sum is an exact fixed-point sum and every FP64 operation is
 rounded in the same order on both sides.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -751,3 +753,61 @@ def test_system_optimum_rejects_a_tape(small):
         Q.qdta_assign_interval(g, Q.DeviceOD.of(inst.demand[0]), 900.0,
                                Q.make_params("exact", "none", 3, record_tape=True, objective="so"))
     assert e.value.code == Q.QDTA_EINVAL
+
+
+# ---------------------------------------------------------------------------
+def test_set_capacity_matches_a_fresh_graph_and_keeps_tapes():
+    """qdta_graph_set_capacity on one handle gives the bits of a graph built
+    with those capacities; a bad value is rejected and changes nothing; a
+    tape recorded before the update differentiates with its own capacities."""
+    net = synth.grid_network(12, 4)
+    zones = synth.pick_zones(net, 10, 4)
+    dem = synth.demand_from_matrix(zones, synth.gravity_fixed_pairs(net, zones, 3000, 1500.0))
+    od = Q.DeviceOD.of(dem)
+    p = Q.make_params("exact", "none", 6, record_tape=True)
+    rng = np.random.default_rng(9)
+    cap_b = net.capacity * rng.uniform(0.5, 1.5, net.n_links)
+    g = Q.Graph(net)
+    f_a, _, _, tape_a = Q.qdta_assign_interval(g, od, 600.0, p)
+    dL = T(rng.standard_normal(net.n_links), np.float64)
+    dd_ref, dc_ref = Q.qdta_backward(tape_a, dL)
+    g.set_capacity(T(cap_b, np.float64))
+    dd_a, dc_a = Q.qdta_backward(tape_a, dL)   # the tape keeps the capacities of its solve
+    assert torch.equal(dd_a, dd_ref) and torch.equal(dc_a, dc_ref)
+    f_b, _, _, tape_b = Q.qdta_assign_interval(g, od, 600.0, p)
+    fresh = Q.Graph(dataclasses.replace(net, capacity=cap_b))
+    f_c, _, _, tape_c = Q.qdta_assign_interval(fresh, od, 600.0, p)
+    assert torch.equal(f_b, f_c) and not torch.equal(f_a, f_b)
+    dd_b, dc_b = Q.qdta_backward(tape_b, dL)
+    dd_c, dc_c = Q.qdta_backward(tape_c, dL)
+    assert torch.equal(dd_b, dd_c) and torch.equal(dc_b, dc_c)
+    bad = cap_b.copy()
+    bad[7] = 0.0
+    with pytest.raises(Q.QdtaError) as e:
+        g.set_capacity(T(bad, np.float64))
+    assert e.value.code == Q.QDTA_EINVAL
+    f_d, _, _, _ = Q.qdta_assign_interval(g, od, 600.0, Q.make_params("exact", "none", 6))
+    assert torch.equal(f_d, f_b)   # unchanged by the rejected update
+    for t in (tape_a, tape_b, tape_c):
+        t.close()
+
+
+def test_autograd_reuses_one_graph_handle():
+    from paper_2104_12911_gb300 import autograd as AG
+    net = synth.grid_network(10, 6)
+    zones = synth.pick_zones(net, 8, 6)
+    dem = synth.demand_from_matrix(zones, synth.gravity_fixed_pairs(net, zones, 2000, 1200.0))
+    od = Q.DeviceOD.of(dem)
+    amounts = torch.tensor(dem.amount_fx / float(1 << 32), dtype=torch.float64, device=DEV)
+    params = Q.make_params("exact", "none", 4)
+    handles = set()
+    for scale in (1.0, 0.8):
+        cap = torch.tensor(net.capacity * scale, dtype=torch.float64, device=DEV, requires_grad=True)
+        f = AG.assign(net, od, amounts, cap, 600.0, params)
+        f.sum().backward()
+        handles.add(id(AG.graph_for(net, 0)))
+        og = oracle.OracleGraph(dataclasses.replace(net, capacity=net.capacity * scale))
+        f_o, _, _ = oracle.assign_interval(og, oracle.OracleOD.of(dem), 600.0,
+                                           oracle.make_params(oracle.STEP_EXACT, oracle.STOP_NONE, 4))
+        np.testing.assert_array_equal(f.detach().cpu().numpy(), f_o)
+    assert len(handles) == 1
