@@ -837,12 +837,15 @@ int sssp_group_size() {
 //      global overflow queue)
 //   4, 5: as 1, with 5 or 6 frontier nodes per lane group in flight instead
 //      of 4 (a pass covers 320 or 384 nodes; 32-bit rank keys only)
+//   6, 7: as 1, one lane per frontier node (sssp_lane_kernel below), 1 or 2
+//      nodes per lane per pass (32-bit rank keys only; otherwise as 1)
 struct SmqShape {
   int threads, bitmaps, qcap, ctas, npt;
 };
-constexpr int kSmqShapes = 6;
+constexpr int kSmqShapes = 8;
 static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 2048, 4, 4}, {512, 1, 3072, 2, 4},
-                                               {256, 1, 768, 5, 4},  {256, 1, 2048, 4, 5}, {256, 1, 2048, 4, 6}};
+                                               {256, 1, 768, 5, 4},  {256, 1, 2048, 4, 5}, {256, 1, 2048, 4, 6},
+                                               {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2}};
 
 // RELAX selects how an offer (cand, link) to neighbour y is applied:
 //   0  returning atomicMin; y is queued when the returned old distance was larger
@@ -1090,6 +1093,171 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   }
 }
 
+// Lane-per-node variant of the shared-memory-queue kernel for 32-bit rank
+// keys on the four-slot adjacency (shapes 6 and 7).  One lane owns NPN
+// frontier nodes per pass: it reads a node's key once, its whole 32-byte
+// adjacency row in two vector loads, and relaxes the (up to four) slots with
+// 32-bit arithmetic (distances stay below 2^29 and link times below 2^31, so
+// dist + time fits in 32 bits).  The quad-per-node kernel above repeats the
+// queue read, the key read and the bookkeeping on all four lanes of a node
+// and carries 64-bit distances; the round structure, marks, queues, tie rule
+// (key = (distance << 3) | rank, atomicMin), overflow flag and output pass are
+// the same, so the results are the same bits.  Signature as SmqKernel.
+template <int THREADS, int NPN>
+__global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64))
+sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__restrict__ adj,
+                 const int *__restrict__ roots, int R_host, const int *R_dev,
+                 unsigned long long *g_state, int *g_queue, int *parent,
+                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
+                 const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
+                 int max_rounds, int qcap, const int *__restrict__ node_ext, int /*out_mode*/,
+                 const int *__restrict__ rank_link, int skip_parent) {
+  extern __shared__ __align__(16) unsigned smq_smem[];
+  __shared__ int s_cnt[3];
+  if (skip_dev && *skip_dev) return;
+  const int R = R_dev ? *R_dev : R_host;
+  if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
+  const int W = (V + 31) >> 5;
+  constexpr unsigned KINF = 0xffffffffu, NOLINK = 7u, DMAX = KINF >> 3;
+  unsigned *bm = smq_smem;
+  int *sq0 = reinterpret_cast<int *>(smq_smem + W), *sq1 = sq0 + qcap;
+  const size_t b = blockIdx.x;
+  unsigned *state = reinterpret_cast<unsigned *>(g_state) + b * (size_t)V;
+  int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
+  const int4 *rows = adj;  // node u: slots 0, 1 in rows[2u], slots 2, 3 in rows[2u + 1]
+  for (int v = threadIdx.x; v < V; v += THREADS) state[v] = KINF;
+  for (int i = threadIdx.x; i < W; i += THREADS) bm[i] = 0u;
+  __syncthreads();
+  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    const int z = node_int ? node_int[roots[r]] : roots[r];
+    if (threadIdx.x == 0) {
+      state[z] = NOLINK;
+      sq0[0] = z;
+      s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+    }
+    __syncthreads();
+    int ncur = 1, round = 0;
+    int *scur = sq0, *snxt = sq1, *gcur = gq0, *gnxt = gq1;
+    unsigned my_relax = 0;
+    while (ncur > 0) {
+      const int c = round % 3;
+      if (threadIdx.x == 0) s_cnt[(round + 1) % 3] = 0;
+      // one bitmap: clear the marks of the queue about to be read, then a
+      // barrier, so a set mark during the relaxations means "in the next queue"
+      for (int i = threadIdx.x; i < ncur; i += THREADS) {
+        const int y = i < qcap ? scur[i] : __ldcg(&gcur[i - qcap]);
+        atomicAnd(&bm[y >> 5], ~(1u << (y & 31)));
+      }
+      __syncthreads();
+      for (int base = 0; base < ncur; base += THREADS * NPN) {
+        int w[NPN];
+        unsigned dw[NPN], prank[NPN];
+        int4 ra[NPN], rb[NPN];
+#pragma unroll
+        for (int n = 0; n < NPN; ++n) {
+          const int i = base + n * THREADS + (int)threadIdx.x;
+          w[n] = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
+        }
+#pragma unroll
+        for (int n = 0; n < NPN; ++n) {
+          dw[n] = 0u;
+          prank[n] = 8u;  // no slot
+          ra[n] = make_int4(-1, 0, -1, 0);
+          rb[n] = ra[n];
+          if (w[n] >= 0) {
+            const unsigned kw = __ldcg(&state[w[n]]);
+            dw[n] = kw >> 3;
+            if (skip_parent) prank[n] = kw & NOLINK;
+            ra[n] = __ldg(&rows[2 * w[n]]);
+            rb[n] = __ldg(&rows[2 * w[n] + 1]);
+          }
+        }
+        // slot s of node n: x = (neighbour << 3) | rank (-1 absent), t = link time
+        int sx[NPN][4];
+        unsigned st[NPN][4], tk[NPN][4];
+#pragma unroll
+        for (int n = 0; n < NPN; ++n) {
+          sx[n][0] = ra[n].x; st[n][0] = (unsigned)ra[n].y;
+          sx[n][1] = ra[n].z; st[n][1] = (unsigned)ra[n].w;
+          sx[n][2] = rb[n].x; st[n][2] = (unsigned)rb[n].y;
+          sx[n][3] = rb[n].z; st[n][3] = (unsigned)rb[n].w;
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+            if (sx[n][s] >= 0 && (unsigned)s == prank[n]) sx[n][s] = -1;  // the way back to the parent
+        }
+#pragma unroll
+        for (int n = 0; n < NPN; ++n)
+#pragma unroll
+          for (int s = 0; s < 4; ++s) tk[n][s] = sx[n][s] >= 0 ? __ldcg(&state[sx[n][s] >> 3]) : 0u;
+#pragma unroll
+        for (int n = 0; n < NPN; ++n)
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            if (sx[n][s] < 0) continue;
+            ++my_relax;
+            const unsigned cand = dw[n] + st[n][s];
+            if (cand >= DMAX) {
+              atomicOr(status, ST_K32);
+              continue;
+            }
+            const unsigned key = (cand << 3) | (unsigned)(sx[n][s] & 7);
+            if (key < tk[n][s]) {
+              const int y = sx[n][s] >> 3;
+              atomicMin(&state[y], key);  // result unused: no wait on the reply
+              const unsigned bit = 1u << (y & 31);
+              if ((tk[n][s] >> 3) > cand && !(atomicOr(&bm[y >> 5], bit) & bit)) {
+                const int pos = atomicAdd(&s_cnt[c], 1);
+                if (pos < qcap) snxt[pos] = y;
+                else gnxt[pos - qcap] = y;
+              }
+            }
+          }
+      }
+      __syncthreads();
+      ncur = s_cnt[c];
+      int *t = scur; scur = snxt; snxt = t;
+      t = gcur; gcur = gnxt; gnxt = t;
+      ++round;
+      if (round > max_rounds) {
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        break;
+      }
+    }
+    if (roots_counter) {
+      if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
+      atomicAdd(roots_counter + 2, (unsigned long long)my_relax);
+    }
+    __syncthreads();
+    if (round > max_rounds)  // an early exit can leave marks behind
+      for (int i = threadIdx.x; i < W; i += THREADS) bm[i] = 0u;
+    // output in internal order: coalesced key reads and resets, parents
+    // (and distances) written through the inverse permutation
+    int *prow = parent + (long long)r * V;
+    long long *drow = dist ? dist + (long long)r * V : nullptr;
+    for (int u0 = threadIdx.x; u0 < V; u0 += 4 * THREADS) {
+      unsigned key[4];
+      int v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int u = u0 + k * THREADS;
+        key[k] = u < V ? __ldcg(&state[u]) : 0u;
+        v[k] = u < V ? (node_ext ? __ldg(&node_ext[u]) : u) : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (v[k] < 0) continue;
+        const int u = u0 + k * THREADS;
+        state[u] = KINF;
+        const unsigned lk = key[k] & NOLINK;
+        prow[v[k]] = lk == NOLINK ? -1 : __ldg(&rank_link[4 * u + (int)lk]);
+        if (drow) drow[v[k]] = key[k] == KINF ? LLONG_MAX : (long long)(key[k] >> 3);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 size_t sssp_smq_smem_bytes(int V, int shape) {
   const SmqShape &sh = kSmqShape[shape];
   return (size_t)sh.bitmaps * ((V + 31) / 32) * 4 + (size_t)2 * sh.qcap * 4;
@@ -1128,10 +1296,14 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
       for (int sh = 0; sh < kSmqShapes; ++sh)
         for (int e = 0; e < 4; ++e)
           for (int r = 0; r < 4; ++r)
-            v.push_back("sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
-                        std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") +
-                        (sh == 3 && e == 3 ? ",5" : "") +
-                        (sh >= 4 && e == 3 ? ",npt" + std::to_string(kSmqShape[sh].npt) : "") + ">");
+            v.push_back(sh >= 6 && e == 3
+                            ? "sssp_lane_kernel<" + std::to_string(kSmqShape[sh].threads) + ",npn" +
+                                  std::to_string(kSmqShape[sh].npt) + ">"
+                            : "sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
+                                  std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") +
+                                  (sh == 3 && e == 3 ? ",5" : "") +
+                                  (sh >= 4 && sh <= 5 && e == 3 ? ",npt" + std::to_string(kSmqShape[sh].npt) : "") +
+                                  ">");
       return v;
     }();
     const int adj = sssp_adj(g, direction);
@@ -1194,6 +1366,8 @@ static SmqKernel smq_kernel_relax(int adj, int relax) {
 }
 
 static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
+  if (shape == 6 && adj == 3) return sssp_lane_kernel<256, 1>;
+  if (shape == 7 && adj == 3) return sssp_lane_kernel<256, 2>;
   if (shape == 3 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 5>;
   if (shape == 4 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 5>;
   if (shape == 5 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 6>;

@@ -134,6 +134,12 @@ LARGE_VARIANTS = {
     "output_external_order": ({"QDTA_SMQ_OUT": "0"}, "sssp_smq_kernel<256,rank32,2,true>"),
     "output_external_order_ell_512": ({"QDTA_SMQ_OUT": "0", "QDTA_BF_SHAPE": "0", "QDTA_SSSP_ADJ": "1"},
                                       "sssp_smq_kernel<512,ell,2,false>"),
+    "lane_npn1": ({"QDTA_BF_SHAPE": "6"}, "sssp_lane_kernel<256,npn1>"),
+    "lane_npn2": ({"QDTA_BF_SHAPE": "7"}, "sssp_lane_kernel<256,npn2>"),
+    "lane_npn1_without_parent_skip": ({"QDTA_BF_SHAPE": "6", "QDTA_NO_PARENT_SKIP": "1"},
+                                      "sssp_lane_kernel<256,npn1>"),
+    "lane_npn2_external_order_flag": ({"QDTA_BF_SHAPE": "7", "QDTA_SMQ_OUT": "0"}, "sssp_lane_kernel<256,npn2>"),
+    "lane_shape_ell16": ({"QDTA_BF_SHAPE": "6", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
     "global_queues": ({"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "sssp_ilp_kernel<512>"),
     "cell": ({"QDTA_SSSP": "cell"}, "sssp_cell_kernel"),
 }
@@ -159,9 +165,12 @@ def test_sssp_large_graph_variants(mid, variant, direction, monkeypatch):
     np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-def test_sssp_rank_keys_on_a_graph_with_one_way_links():
+@pytest.mark.parametrize("shape,kernel", [("1", "sssp_smq_kernel<256,rank32,2,true>"),
+                                          ("6", "sssp_lane_kernel<256,npn1>"), ("7", "sssp_lane_kernel<256,npn2>")])
+def test_sssp_rank_keys_on_a_graph_with_one_way_links(shape, kernel, monkeypatch):
     """Degree <= 4 but 3 % of links lose their reverse: the rank-keyed
     adjacency runs without the parent-slot skip; bit-exact both ways."""
+    monkeypatch.setenv("QDTA_BF_SHAPE", shape)
     base = synth.grid_network(110, 9, freeways=True)
     rng = np.random.default_rng(9)
     keep = rng.random(base.n_links) >= 0.03
@@ -173,19 +182,20 @@ def test_sssp_rank_keys_on_a_graph_with_one_way_links():
     q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
     roots = rng.choice(net.n_nodes, 40, replace=False).astype(np.int32)
     for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
-        assert Q.qdta_sssp_kernel_name(g, direction) == "sssp_smq_kernel<256,rank32,2,true>"
+        assert Q.qdta_sssp_kernel_name(g, direction) == kernel
         p_o, d_o = oracle.sssp(og, q, roots, direction)
         p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
         np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
         np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-@pytest.mark.parametrize("adj", ["2", "3"])
-def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, monkeypatch):
+@pytest.mark.parametrize("adj,shape", [("2", "1"), ("3", "1"), ("3", "6"), ("3", "7")])
+def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, shape, monkeypatch):
     """Link times of 5e6..1e7 quanta push distances past 2^29: the 32-bit-key
     batch flags it and the 64-bit redo gives the oracle's bits."""
     net, dem, _, og = mid
     monkeypatch.setenv("QDTA_SSSP_ADJ", adj)
+    monkeypatch.setenv("QDTA_BF_SHAPE", shape)
     g = Q.Graph(net)
     rng = np.random.default_rng(21)
     q = rng.integers(5_000_000, 10_000_000, net.n_links).astype(np.int32)
@@ -198,11 +208,13 @@ def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, monkeypatch):
         np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-def test_sssp_redo_touches_only_the_roots_that_overflowed(mid):
+@pytest.mark.parametrize("shape", ["1", "6", "7"])
+def test_sssp_redo_touches_only_the_roots_that_overflowed(mid, shape, monkeypatch):
     """Links entering three nodes cost 2^30: destination trees rooted there
-    pass 2^29 (so those roots are redone with 64-bit keys), the other roots'
-    trees stay below it and keep their 32-bit results; all rows bit-exact."""
+    pass 2^29 (so the batch is redone with 64-bit keys), the other roots'
+    trees stay below it; all rows bit-exact."""
     net, dem, _, og = mid
+    monkeypatch.setenv("QDTA_BF_SHAPE", shape)
     g = Q.Graph(net)
     rng = np.random.default_rng(31)
     q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int64)
