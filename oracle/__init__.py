@@ -50,16 +50,19 @@ class Graph(C.Structure):
 
 class OD(C.Structure):
     _fields_ = [("n_roots", C.c_int32), ("roots", C.c_void_p), ("n_items", C.c_int64),
-                ("root_idx", C.c_void_p), ("src", C.c_void_p), ("amount_fx", C.c_void_p)]
+                ("root_idx", C.c_void_p), ("src", C.c_void_p), ("amount_fx", C.c_void_p),
+                ("carry_q", C.c_void_p)]
 
 
 OBJ_UE, OBJ_SO = 0, 1  # user equilibrium (Beckmann) / system optimum (total cost)
+TRUNC_NODE, TRUNC_CARRY = 0, 1  # stop at the first node reached at or after dt / carry the partial link
 
 
 class Params(C.Structure):
     _fields_ = [("step", C.c_int32), ("stop", C.c_int32), ("max_iter", C.c_int32),
                 ("ls_max", C.c_int32), ("tol", C.c_double), ("ls_dx", C.c_double),
-                ("ls_t1", C.c_double), ("ls_t2", C.c_double), ("objective", C.c_int32)]
+                ("ls_t1", C.c_double), ("ls_t2", C.c_double), ("objective", C.c_int32),
+                ("truncation", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -82,13 +85,13 @@ def _load():
                 "or_fx_to_double": (C.c_double, [C.c_int64, C.c_uint64]),
                 "or_bpr": (C.c_int32, [P, P, C.c_double, P, P]),
                 "or_sssp": (C.c_int32, [P, P, P, C.c_int32, C.c_int32, P, P]),
-                "or_load": (C.c_int32, [P, P, P, P, C.c_int64, P, P]),
+                "or_load": (C.c_int32, [P, P, P, P, C.c_int64, C.c_int32, P, P, P]),
                 "or_line_search": (C.c_int32, [P, P, P, C.c_double, C.c_int32, P, P, P]),
                 "or_objective": (C.c_double, [P, P, C.c_double]),
                 "or_slope": (C.c_double, [P, P, P, C.c_double, C.c_double]),
                 "or_assign_interval": (C.c_int32, [P, P, C.c_double, P, P, P, C.c_int32, P, P, P, P]),
-                "or_residual": (C.c_int32, [P, P, C.c_double, C.c_int32, P, P, P, P, C.c_int64,
-                                            P, P, P, P]),
+                "or_residual": (C.c_int32, [P, P, C.c_double, C.c_int32, P, P, P, C.c_int32, P, C.c_int64,
+                                            P, P, P, P, P]),
                 "or_run_day": (C.c_int32, [P, C.c_int32, P, C.c_int32, P, P, P, P, C.c_double, P,
                                            P, P, P, P]),
                 "or_backward": (C.c_int32, [P, P, C.c_double, C.c_int32, C.c_int32, P, P, P, P,
@@ -130,13 +133,18 @@ class OracleGraph:
 
 
 class OracleOD:
-    def __init__(self, roots, root_idx, src, amount_fx):
+    """Items (root_idx, src, amount_fx) over `roots`; carry_q (optional) is the
+    time each trip already travelled beyond src in earlier intervals."""
+
+    def __init__(self, roots, root_idx, src, amount_fx, carry_q=None):
         self.roots = np.ascontiguousarray(roots, dtype=np.int32)
         self.root_idx = np.ascontiguousarray(root_idx, dtype=np.int32)
         self.src = np.ascontiguousarray(src, dtype=np.int32)
         self.amount_fx = np.ascontiguousarray(amount_fx, dtype=np.int64)
+        self.carry_q = None if carry_q is None else np.ascontiguousarray(carry_q, dtype=np.int64)
         self.s = OD(int(self.roots.shape[0]), _p(self.roots).value, int(self.src.shape[0]),
-                    _p(self.root_idx).value, _p(self.src).value, _p(self.amount_fx).value)
+                    _p(self.root_idx).value, _p(self.src).value, _p(self.amount_fx).value,
+                    None if self.carry_q is None else _p(self.carry_q).value)
 
     @classmethod
     def of(cls, dem):
@@ -147,8 +155,8 @@ class OracleOD:
 
 
 def make_params(step=STEP_MSA, stop=STOP_NONE, max_iter=20, tol=1e-4, ls_max=20,
-                ls_dx=1e-4, ls_t1=1e-4, ls_t2=1e-4, objective=OBJ_UE) -> Params:
-    return Params(step, stop, max_iter, ls_max, tol, ls_dx, ls_t1, ls_t2, objective)
+                ls_dx=1e-4, ls_t1=1e-4, ls_t2=1e-4, objective=OBJ_UE, truncation=TRUNC_NODE) -> Params:
+    return Params(step, stop, max_iter, ls_max, tol, ls_dx, ls_t1, ls_t2, objective, truncation)
 
 
 # --------------------------------------------------------------------------
@@ -187,14 +195,21 @@ def sssp(g: OracleGraph, q, roots, direction=DIR_TO_ROOT, want_dist=True):
     return parent.reshape(R, V), (dist.reshape(R, V) if want_dist else None)
 
 
-def load(g: OracleGraph, walk_q, parent, od: OracleOD, dt_q: int, flow_fx=None):
+def load(g: OracleGraph, walk_q, parent, od: OracleOD, dt_q: int, flow_fx=None, truncation=TRUNC_NODE,
+         want_carry=False):
+    """Returns (flow_fx, stop nodes, rc), plus the carried times when want_carry."""
     walk_q = np.ascontiguousarray(walk_q, dtype=np.int32)
     parent = np.ascontiguousarray(parent, dtype=np.int32)
     if flow_fx is None:
         flow_fx = np.zeros(g.n_links, dtype=np.int64)
-    stop = np.empty(max(od.src.shape[0], 1), dtype=np.int32)
-    rc = _load().or_load(g.ref(), _p(walk_q), _p(parent), od.ref(), int(dt_q), _p(flow_fx), _p(stop))
-    return flow_fx, stop[:od.src.shape[0]], rc
+    n = od.src.shape[0]
+    stop = np.empty(max(n, 1), dtype=np.int32)
+    carry = np.empty(max(n, 1), dtype=np.int64)
+    rc = _load().or_load(g.ref(), _p(walk_q), _p(parent), od.ref(), int(dt_q), int(truncation), _p(flow_fx),
+                         _p(stop), _p(carry))
+    if want_carry:
+        return flow_fx, stop[:n], carry[:n], rc
+    return flow_fx, stop[:n], rc
 
 
 def line_search(g: OracleGraph, f, g_fx, dt_s, fw_iter, params: Params):
@@ -257,19 +272,21 @@ def assign_interval(g: OracleGraph, od: OracleOD, dt_s: float, params: Params, t
     return f, st.as_dict(), rc
 
 
-def residual(g: OracleGraph, od: OracleOD, dt_s: float, tape: Tape, f_final):
+def residual(g: OracleGraph, od: OracleOD, dt_s: float, tape: Tape, f_final, truncation=TRUNC_NODE):
+    """Returns (h_fx, (stop nodes, root indices, amounts, carried times), rc)."""
     K = tape.K.value
     cap = od.src.shape[0] * (K + 1) + 1
     h = np.zeros(g.n_links, dtype=np.int64)
     rs = np.empty(cap, dtype=np.int32)
     rr = np.empty(cap, dtype=np.int32)
     ra = np.empty(cap, dtype=np.int64)
+    rcy = np.empty(cap, dtype=np.int64)
     n = C.c_int64()
     f_final = np.ascontiguousarray(f_final, dtype=np.float64)
     rc = _load().or_residual(g.ref(), od.ref(), float(dt_s), K, _p(tape.q), _p(tape.alpha),
-                             _p(f_final), _p(h), cap, _p(rs), _p(rr), _p(ra), C.byref(n))
+                             _p(f_final), int(truncation), _p(h), cap, _p(rs), _p(rr), _p(ra), _p(rcy), C.byref(n))
     m = n.value
-    return h, (rs[:m].copy(), rr[:m].copy(), ra[:m].copy()), rc
+    return h, (rs[:m].copy(), rr[:m].copy(), ra[:m].copy(), rcy[:m].copy()), rc
 
 
 def run_day(g: OracleGraph, zones, demands, dt_s: float, params: Params):

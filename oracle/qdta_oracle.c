@@ -67,16 +67,21 @@ typedef struct {
   int64_t n_items;
   const int32_t *root_idx, *src;
   const int64_t *amount_fx;
+  const int64_t *carry_q;  /* nullable: per item, time already travelled beyond src (quanta, >= 0) */
 } or_od;
 
 typedef struct {
   int32_t step, stop, max_iter, ls_max;
   double tol, ls_dx, ls_t1, ls_t2;
   int32_t objective;  /* OBJ_UE (Beckmann, user equilibrium) or OBJ_SO (total cost, system optimum) */
+  int32_t truncation; /* TRUNC_NODE (R1) or TRUNC_CARRY (R17) */
 } or_params;
 
 #define OBJ_UE 0
 #define OBJ_SO 1
+
+#define TRUNC_NODE 0
+#define TRUNC_CARRY 1
 
 typedef struct {
   int32_t iterations;   /* accepted FW steps after the initial AON */
@@ -401,20 +406,33 @@ int32_t or_sssp(const or_graph *g, const int32_t *q, const int32_t *roots, int32
 /* All-or-nothing loading with route truncation (Alg. 3, Eq. 2, Eq. 5).     */
 /* ------------------------------------------------------------------------ */
 
-/* Walk item p -> z along the destination tree.  Link a is loaded iff the
- * elapsed time on reaching its tail is < dt_q; the walk stops at the first
- * node whose elapsed time is >= dt_q (the stop node s), or at z.
- * Returns the stop node, or -1 if z is unreachable from p. */
+/* Walk item p -> z along the destination tree.  The elapsed time starts at
+ * -carry, carry being the time the trip already travelled beyond p in
+ * earlier intervals (0 for a new trip).  Link a is loaded iff the elapsed
+ * time on reaching its tail is < dt_q.
+ *  TRUNC_NODE (R1): the walk stops at the first node whose elapsed time is
+ *    >= dt_q (the stop node s), or at z; *carry_out = 0.
+ *  TRUNC_CARRY (R17, the alternative of Section 3.4): a link that would end
+ *    after dt_q holds the trip at the end of the interval; the walk stops at
+ *    its tail u with *carry_out = dt_q - elapsed(u), the time travelled
+ *    beyond u.  A link ending exactly at dt_q is completed.
+ * Both modes load the same links.  Returns the stop node, or -1 if z is
+ * unreachable from p. */
 static int32_t walk_load(const or_graph *g, const int32_t *walk_q, const int32_t *par,
-                         int32_t p, int32_t z, int64_t dt_q, int64_t amount,
-                         int64_t *flow_fx) {
+                         int32_t p, int32_t z, int64_t dt_q, int64_t carry, int trunc,
+                         int64_t amount, int64_t *flow_fx, int64_t *carry_out) {
   int32_t u = p;
-  int64_t elapsed = 0;
+  int64_t elapsed = -carry;
+  *carry_out = 0;
   while (u != z) {
     if (elapsed >= dt_q) return u;
     int32_t e = par[u];
     if (e < 0) return -1;
     if (flow_fx) flow_fx[e] += amount;
+    if (trunc == TRUNC_CARRY && elapsed + walk_q[e] > dt_q) {
+      *carry_out = dt_q - elapsed;
+      return u;
+    }
     elapsed += walk_q[e];
     u = g->head[e];
   }
@@ -423,18 +441,22 @@ static int32_t walk_load(const or_graph *g, const int32_t *walk_q, const int32_t
 
 /* parent: [n_roots * V] destination-rooted trees built with tree_q.
  * walk_q: link times used for the elapsed-time truncation (tree_q for an
- * AON; the final costs for the residual of Alg. 4).
- * stop_out (nullable): per-item stop node. */
+ * AON; the final costs for the residual of Alg. 4).  Items start with their
+ * od->carry_q (0 when NULL).  stop_out, carry_out (nullable): per-item stop
+ * node and carried time under truncation mode `trunc`. */
 int32_t or_load(const or_graph *g, const int32_t *walk_q, const int32_t *parent,
-                const or_od *od, int64_t dt_q, int64_t *flow_fx, int32_t *stop_out) {
+                const or_od *od, int64_t dt_q, int32_t trunc, int64_t *flow_fx, int32_t *stop_out,
+                int64_t *carry_out) {
   int64_t V = g->n_nodes;
   int rc = OR_OK;
   for (int64_t k = 0; k < od->n_items; k++) {
     int32_t r = od->root_idx[k];
+    int64_t c = 0;
     int32_t s = walk_load(g, walk_q, parent + r * V, od->src[k], od->roots[r], dt_q,
-                          od->amount_fx[k], flow_fx);
+                          od->carry_q ? od->carry_q[k] : 0, trunc, od->amount_fx[k], flow_fx, &c);
     if (s < 0) rc = OR_EUNREACH;
     if (stop_out) stop_out[k] = s;
+    if (carry_out) carry_out[k] = c;
   }
   return rc;
 }
@@ -693,7 +715,8 @@ static int aon(const or_graph *g, const adjacency *adj, const int32_t *q, const 
     if (dijkstra_one(g, adj, q, od->roots[r], DIR_TO_ROOT, parent + r * V, dist, h)) return OR_ENOMEM;
   }
   memset(g_fx, 0, (size_t)g->n_links * 8);
-  return or_load(g, qt, parent, od, dt_q, g_fx, NULL);
+  /* the loaded links do not depend on the truncation mode */
+  return or_load(g, qt, parent, od, dt_q, TRUNC_NODE, g_fx, NULL, NULL);
 }
 
 /* routing costs q and travel times qt at flows f: q = qt = quant(c(f)) for the
@@ -853,13 +876,14 @@ static int64_t scale_amount(int64_t amount_fx, double w) {
 }
 
 /* Re-truncate every path of every accepted AON with the final costs.
- * h_fx[L] receives the truncated link flows h(i); residual triples
- * (stop node, root index, amount) are written up to res_cap, *res_n gets the
- * number produced (before any merge). */
+ * h_fx[L] receives the truncated link flows h(i); residual entries
+ * (stop node, root index, amount, carried time) are written up to res_cap,
+ * *res_n gets the number produced (before any merge).  res_carry (nullable)
+ * receives the carried times (0 under TRUNC_NODE). */
 int32_t or_residual(const or_graph *g, const or_od *od, double dt_s, int32_t K,
                     const int32_t *tape_q, const double *tape_alpha, const double *f_final,
-                    int64_t *h_fx, int64_t res_cap, int32_t *res_stop, int32_t *res_root,
-                    int64_t *res_amount, int64_t *res_n) {
+                    int32_t trunc, int64_t *h_fx, int64_t res_cap, int32_t *res_stop, int32_t *res_root,
+                    int64_t *res_amount, int64_t *res_carry, int64_t *res_n) {
   int L = g->n_links;
   int64_t V = g->n_nodes;
   int64_t dt_q = dt_quanta(g, dt_s);
@@ -889,11 +913,14 @@ int32_t or_residual(const or_graph *g, const or_od *od, double dt_s, int32_t K,
       int64_t amt = scale_amount(od->amount_fx[k], w[j]);
       if (amt == 0) continue;
       int32_t r = od->root_idx[k];
-      int32_t s = walk_load(g, qfin, parent + r * V, od->src[k], od->roots[r], dt_q, amt, h_fx);
+      int64_t c = 0;
+      int32_t s = walk_load(g, qfin, parent + r * V, od->src[k], od->roots[r], dt_q,
+                            od->carry_q ? od->carry_q[k] : 0, trunc, amt, h_fx, &c);
       if (s < 0) { rc = OR_EUNREACH; break; }
       if (s != od->roots[r]) {
         if (*res_n < res_cap) {
           res_stop[*res_n] = s; res_root[*res_n] = r; res_amount[*res_n] = amt;
+          if (res_carry) res_carry[*res_n] = c;
         }
         (*res_n)++;
       }
@@ -908,21 +935,25 @@ done:
 /* Full day (Alg. 1): d(i) = d_o(i) + d_r(i); STA; residual.                */
 /* ------------------------------------------------------------------------ */
 
-typedef struct { int32_t root, src; int64_t amt; } item3;
+typedef struct { int32_t root, src; int64_t amt, carry; } item3;
 
 static int cmp_item3(const void *a, const void *b) {
   const item3 *x = (const item3 *)a, *y = (const item3 *)b;
   if (x->root != y->root) return x->root < y->root ? -1 : 1;
   if (x->src != y->src) return x->src < y->src ? -1 : 1;
+  if (x->carry != y->carry) return x->carry < y->carry ? -1 : 1;
   return 0;
 }
 
-/* merge two item lists by (root, src), summing amounts; returns count */
+/* merge an item list by (root, src, carried time), summing amounts (trips at
+ * the same node with the same time already travelled continue identically);
+ * returns the count */
 static int64_t merge_items(item3 *buf, int64_t n) {
   qsort(buf, (size_t)n, sizeof(item3), cmp_item3);
   int64_t m = 0;
   for (int64_t k = 0; k < n; k++) {
-    if (m > 0 && buf[m - 1].root == buf[k].root && buf[m - 1].src == buf[k].src) buf[m - 1].amt += buf[k].amt;
+    if (m > 0 && buf[m - 1].root == buf[k].root && buf[m - 1].src == buf[k].src && buf[m - 1].carry == buf[k].carry)
+      buf[m - 1].amt += buf[k].amt;
     else buf[m++] = buf[k];
   }
   return m;
@@ -956,18 +987,19 @@ int32_t or_run_day(const or_graph *g, int32_t n_zones, const int32_t *zones, int
     for (int64_t k = 0; k < n0; k++) {
       buf[k].root = root_idx[item_off[i] + k]; buf[k].src = src[item_off[i] + k];
       buf[k].amt = amount_fx[item_off[i] + k];
+      buf[k].carry = 0;
     }
     for (int64_t k = 0; k < rn; k++) buf[n0 + k] = resid[k];
     int64_t n = merge_items(buf, n0 + rn);
     int32_t *ri = (int32_t *)malloc((size_t)(n + 1) * 4), *si = (int32_t *)malloc((size_t)(n + 1) * 4);
-    int64_t *ai = (int64_t *)malloc((size_t)(n + 1) * 8);
-    for (int64_t k = 0; k < n; k++) { ri[k] = buf[k].root; si[k] = buf[k].src; ai[k] = buf[k].amt; }
+    int64_t *ai = (int64_t *)malloc((size_t)(n + 1) * 8), *ci = (int64_t *)malloc((size_t)(n + 1) * 8);
+    for (int64_t k = 0; k < n; k++) { ri[k] = buf[k].root; si[k] = buf[k].src; ai[k] = buf[k].amt; ci[k] = buf[k].carry; }
     free(buf);
     n_items_out[i] = n;
-    or_od od = {n_zones, zones, n, ri, si, ai};
+    or_od od = {n_zones, zones, n, ri, si, ai, ci};
     int32_t K = 0;
     int r1 = or_assign_interval(g, &od, dt_s, p, f, &stats[i], cap, tq, ta, tf, &K);
-    if (r1 < 0) { rc = r1; free(ri); free(si); free(ai); break; }
+    if (r1 < 0) { rc = r1; free(ri); free(si); free(ai); free(ci); break; }
     if (r1 > 0) rc = r1;
     /* residual: at most one triple per item and accepted AON */
     int64_t need = n * ((int64_t)K + 1);
@@ -975,13 +1007,15 @@ int32_t or_run_day(const or_graph *g, int32_t n_zones, const int32_t *zones, int
       free(resid); rcap = need; resid = (item3 *)malloc((size_t)(rcap + 1) * sizeof(item3));
     }
     int32_t *rs = (int32_t *)malloc((size_t)(need + 1) * 4), *rr = (int32_t *)malloc((size_t)(need + 1) * 4);
-    int64_t *ra = (int64_t *)malloc((size_t)(need + 1) * 8);
+    int64_t *ra = (int64_t *)malloc((size_t)(need + 1) * 8), *rcy = (int64_t *)malloc((size_t)(need + 1) * 8);
     int64_t got = 0;
-    int r2 = or_residual(g, &od, dt_s, K, tq, ta, f, hfx, need, rs, rr, ra, &got);
-    for (int64_t k = 0; k < got; k++) { resid[k].root = rr[k]; resid[k].src = rs[k]; resid[k].amt = ra[k]; }
+    int r2 = or_residual(g, &od, dt_s, K, tq, ta, f, p->truncation, hfx, need, rs, rr, ra, rcy, &got);
+    for (int64_t k = 0; k < got; k++) {
+      resid[k].root = rr[k]; resid[k].src = rs[k]; resid[k].amt = ra[k]; resid[k].carry = rcy[k];
+    }
     rn = merge_items(resid, got);
     for (int a = 0; a < L; a++) flows_out[(int64_t)i * L + a] = (double)hfx[a] * 0x1p-32;
-    free(rs); free(rr); free(ra); free(ri); free(si); free(ai);
+    free(rs); free(rr); free(ra); free(rcy); free(ri); free(si); free(ai); free(ci);
     if (r2 < 0) { rc = r2; break; }
   }
   *resid_out_n = rn;
@@ -1062,7 +1096,7 @@ int32_t or_backward(const or_graph *g, const or_od *od, double dt_s, int32_t ste
       int32_t r = od->root_idx[it];
       const int32_t *par = parent + r * V;
       int32_t u = od->src[it], z = od->roots[r];
-      int64_t elapsed = 0;
+      int64_t elapsed = od->carry_q ? -od->carry_q[it] : 0;
       double acc = 0.0;
       while (u != z && elapsed < dt_q) {
         int32_t e = par[u];
@@ -1135,4 +1169,16 @@ int32_t or_replay(const or_graph *g, const or_od *od, double dt_s, const or_para
  *     rules the total cost and the gap in marginal costs, while loading and
  *     truncation keep the travel times c (a trip still ends its interval
  *     after dt of travel).
+ *  R16 The relative-gap stop takes -1e-12 <= gap <= tol: under truncation a
+ *     negative gap certifies nothing (the truncated AON loading need not
+ *     minimise sum c g); -1e-12 absorbs rounding at an exact equilibrium.
+ *  R17 Carried truncation (Section 3.4 proposes tracking how far a trip got
+ *     along a link and adding it up across intervals): a trip whose next
+ *     link would end after dt waits at that link's tail u, carrying the time
+ *     dt - elapsed(u) it has already travelled beyond u; in the next interval
+ *     its elapsed time starts at minus that carry, so a link longer than dt
+ *     is crossed over several intervals.  Time (quanta), not a fraction of
+ *     the link, is carried: the trip is rerouted from u in the next interval
+ *     and may leave u by another link.  Residual items merge by (root, node,
+ *     carried time).
  */

@@ -443,7 +443,7 @@ def test_residual_conserves_trips_and_matches_flows_without_truncation(small_ins
     p = oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_REL_GAP, 60, 1e-3)
     for dt in (600.0, 1e9):
         f, st, rc, tape = oracle.assign_interval(g, od, dt, p, tape=True)
-        h, (rs, rr, ra), rc2 = oracle.residual(g, od, dt, tape, f)
+        h, (rs, rr, ra, _), rc2 = oracle.residual(g, od, dt, tape, f)
         assert rc2 == 0
         K = tape.K.value
         total_in = int(od.amount_fx.sum())
@@ -682,6 +682,73 @@ def test_day_advances_a_trip_one_link_per_interval_when_links_outlast_dt():
     # step-weighted shares are rounded to 2^-32 trips each (R9)
     np.testing.assert_allclose(f, [[1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, 0]], rtol=0, atol=4 * 2.0 ** -32)
     assert list(nit) == [1, 1, 1, 0]
+
+
+def test_carried_truncation_crosses_a_long_link_over_several_intervals():
+    """Section 3.4's alternative to Eq. 2 (reading R17): links of 1000 s on an
+    uncongested chain, intervals of 300 s.  A trip leaving at time 0 is on
+    link k during [1000 k, 1000 (k + 1)) s, so link k must carry it in exactly
+    the intervals that overlap that span, and it arrives at 3000 s, the end of
+    interval 9.  Under the node rule (R1) the same trip advances one link per
+    interval instead."""
+    net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
+    g = oracle.OracleGraph(net)
+    zones = np.array([3], np.int32)
+    one = synth.Demand(roots=zones, root_idx=np.array([0], np.int32), src=np.array([0], np.int32),
+                       amount_fx=np.array([1 << 32], np.int64))
+    empty = synth.Demand(roots=zones, root_idx=np.zeros(0, np.int32), src=np.zeros(0, np.int32),
+                         amount_fx=np.zeros(0, np.int64))
+    N = 11
+    want = np.zeros((N, 3))
+    for i in range(N):
+        for k in range(3):
+            want[i, k] = float(max(300 * i, 1000 * k) < min(300 * (i + 1), 1000 * (k + 1)))
+    f, st, nit, rn, rc = oracle.run_day(g, zones, [one] + [empty] * (N - 1), 300.0,
+                                        oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0,
+                                                           truncation=oracle.TRUNC_CARRY))
+    assert rc >= 0
+    np.testing.assert_array_equal(np.asarray(f).reshape(N, 3), want)
+    assert list(nit) == [1] * 10 + [0] and rn == 0
+    f, st, nit, rn, rc = oracle.run_day(g, zones, [one] + [empty] * 3, 300.0,
+                                        oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0))
+    np.testing.assert_array_equal(np.asarray(f).reshape(4, 3), [[1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, 0]])
+
+
+def test_carried_truncation_stop_node_and_carried_time():
+    """One walk on the same chain from node 0 with a carried time c (time
+    already travelled beyond node 0): after an interval of 300 s the trip is
+    at position t = c + 300 s, i.e. past node floor(t / 1000) by t mod 1000;
+    a trip exactly at a node carries nothing, and one at node 3 has arrived."""
+    net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
+    g = oracle.OracleGraph(net)
+    par, _ = oracle.sssp(g, net.fftime_q, np.array([3], np.int32), want_dist=False)
+    for c_s in (0, 100, 600, 700, 900, 1000, 1750, 2700, 2850):
+        od = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([0], np.int32),
+                             np.array([1 << 32], np.int64), carry_q=np.array([c_s * 100], np.int64))
+        _, stop, carry, rc = oracle.load(g, net.fftime_q, par, od, 30000, truncation=oracle.TRUNC_CARRY,
+                                         want_carry=True)
+        t = c_s + 300
+        node, rem = (3, 0) if t >= 3000 else divmod(t, 1000)
+        assert rc == 0 and (stop[0], carry[0]) == (node, rem * 100), (c_s, stop[0], carry[0])
+
+
+def test_carried_truncation_loads_the_links_of_the_node_rule():
+    """Both truncation rules load a link iff the elapsed time at its tail is
+    below dt; they differ only in where the residual trip waits.  So the
+    first interval of a day (no carried trips yet) has the same h(0) under
+    both, while later intervals differ."""
+    inst = synth.scaled_day(synth.config_small(0), 60000, n_intervals=4, seed=5)
+    g = oracle.OracleGraph(inst.net)
+    out = []
+    for trunc in (oracle.TRUNC_NODE, oracle.TRUNC_CARRY):
+        f, st, nit, rn, rc = oracle.run_day(g, inst.zones, list(inst.demand), 150.0,
+                                            oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_PAPER_OBJ, 30,
+                                                               truncation=trunc))
+        assert rc >= 0
+        out.append((np.asarray(f), nit))
+    np.testing.assert_array_equal(out[0][0][0], out[1][0][0])
+    assert out[0][1][0] == out[1][1][0]
+    assert not np.array_equal(out[0][0][1:], out[1][0][1:]) and out[1][1][1] > out[0][1][1]
 
 
 # ----------------------------------------------------------------------------
