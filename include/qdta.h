@@ -69,6 +69,21 @@ extern "C" {
 #define QDTA_OBJ_UE 0
 #define QDTA_OBJ_SO 1
 
+/* Truncation rule of Eq. 2 (how a trip that does not finish its interval
+ * is carried to the next one).  Both rules load the same links: link a of a
+ * trip's path is loaded iff the elapsed time on reaching its tail is < dt.
+ *  QDTA_TRUNC_NODE: the trip waits at the first node whose elapsed time is
+ *    >= dt (it may overshoot dt by up to one link).
+ *  QDTA_TRUNC_CARRY: Section 3.4's alternative -- a trip whose next link
+ *    would end after dt waits at that link's tail u, carrying the time
+ *    dt - elapsed(u) it already travelled beyond u; in the next interval its
+ *    elapsed time starts at minus that carry, so a link longer than dt is
+ *    crossed over several intervals.  Residual items then merge by (root,
+ *    node, carried time); carried times must stay below 2^(64 - ceil(log2(
+ *    zones x nodes))) quanta (QDTA_EOVERFLOW otherwise). */
+#define QDTA_TRUNC_NODE 0
+#define QDTA_TRUNC_CARRY 1
+
 #define QDTA_SCHEDULE_PLAIN 0 /* host launch loop, one host sync per decision */
 #define QDTA_SCHEDULE_GRAPH 1 /* whole FW loop in one CUDA graph with device-side control */
 
@@ -101,6 +116,9 @@ typedef struct {
   const int32_t *root_idx;   /* [n_items] in [0, n_roots) */
   const int32_t *src;        /* [n_items] origin nodes */
   const int64_t *amount_fx;  /* [n_items] >= 0 */
+  const int64_t *carry_q;    /* [n_items] or NULL (all 0): time each trip already travelled beyond
+                                src in earlier intervals, quanta >= 0 (QDTA_TRUNC_CARRY residuals);
+                                its elapsed time starts at -carry_q */
 } qdta_od;
 
 typedef struct {
@@ -115,6 +133,7 @@ typedef struct {
   int32_t schedule;    /* QDTA_SCHEDULE_* */
   int32_t record_tape; /* qdta_assign_interval: keep what qdta_backward needs (QDTA_OBJ_UE only) */
   int32_t objective;   /* QDTA_OBJ_UE (the paper's user equilibrium) or QDTA_OBJ_SO */
+  int32_t truncation;  /* QDTA_TRUNC_NODE or QDTA_TRUNC_CARRY (qdta_run_day's residual demand) */
 } qdta_params;
 
 typedef struct {
@@ -135,6 +154,7 @@ typedef struct {
   int32_t *src;        /* [capacity] stop node s, the new origin */
   int64_t *amount_fx;  /* [capacity] */
   int64_t count;       /* written by the library (host field): entries produced */
+  int64_t *carry_q;    /* [capacity] carried times; required with QDTA_TRUNC_CARRY, else NULL or zeros */
 } qdta_residual;
 
 /* Per-kernel CUDA-event timings accumulated while profiling is enabled

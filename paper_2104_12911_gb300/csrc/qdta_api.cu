@@ -235,6 +235,8 @@ static int check_params(const qdta_params *p) {
   if (p->schedule != QDTA_SCHEDULE_PLAIN && p->schedule != QDTA_SCHEDULE_GRAPH)
     return fail(QDTA_EINVAL, "unknown schedule");
   if (p->objective != QDTA_OBJ_UE && p->objective != QDTA_OBJ_SO) return fail(QDTA_EINVAL, "unknown objective");
+  if (p->truncation != QDTA_TRUNC_NODE && p->truncation != QDTA_TRUNC_CARRY)
+    return fail(QDTA_EINVAL, "unknown truncation rule %d", p->truncation);
   return QDTA_OK;
 }
 
@@ -1029,7 +1031,7 @@ extern "C" int qdta_load_aon(qdta_graph *g, const int32_t *cost_q, const int32_t
   prof_begin(g, s, &pe, 1, 0);
   launch_load(g->d, hq, parent_link, nullptr, 0, nullptr, od->roots, od->n_items, nullptr, od->root_idx,
               od->src, (const long long *)od->amount_fx, dt_q, (unsigned long long *)flow_fx,
-              stop_node, g->status, s);
+              stop_node, g->status, s, (const long long *)od->carry_q);
   prof_end(g, s, &pe);
   return status_check(g, s);
 }
@@ -1066,6 +1068,7 @@ struct Solver {
   const long long *n_dev;
   const int *root_idx, *src;
   const long long *amount;
+  const long long *carry = nullptr;  // per item, time already travelled beyond src (nullable)
   // link state
   int *q;
   unsigned long long *g_fx;
@@ -1135,7 +1138,7 @@ static int seg_aon(Solver &S, const int *slot_dev, bool gather_ff = false) {
   ProfEvent pe;
   prof_begin(g, S.s, &pe, 1, 0);
   launch_load(g->d, S.head_q, S.parent, slot_dev, S.parent_stride, S.root_slot, S.item_roots, S.n_host,
-              S.n_dev, S.root_idx, S.src, S.amount, S.dt_q, S.g_fx, nullptr, g->status, S.s);
+              S.n_dev, S.root_idx, S.src, S.amount, S.dt_q, S.g_fx, nullptr, g->status, S.s, S.carry);
   prof_end(g, S.s, &pe);
   return QDTA_OK;
 }
@@ -1384,6 +1387,7 @@ static int assign_core(qdta_graph *g, const qdta_od *od, double dt_s, const qdta
   S.root_slot = nullptr; S.item_roots = od->roots;
   S.n_host = od->n_items; S.n_dev = nullptr;
   S.root_idx = od->root_idx; S.src = od->src; S.amount = (const long long *)od->amount_fx;
+  S.carry = (const long long *)od->carry_q;
   S.f = flow_out;
   const bool want_tape = p->record_tape && tape_out;
   if (want_tape && p->objective == QDTA_OBJ_SO)
@@ -1447,6 +1451,7 @@ static int assign_batch_graph(const qdta_instance *inst, int n, const qdta_param
     X.root_slot = nullptr; X.item_roots = od->roots;
     X.n_host = od->n_items; X.n_dev = nullptr;
     X.root_idx = od->root_idx; X.src = od->src; X.amount = (const long long *)od->amount_fx;
+    X.carry = (const long long *)od->carry_q;
     X.f = inst[i].flow_out;
     RC(solver_alloc(X, "batch", 1, false));
     RC(status_reset(g, s));
@@ -1537,6 +1542,9 @@ struct Day {
   long long cap_items;
   int *it_root, *it_src;
   long long *it_amt;
+  long long *it_carry;         // carried times of the items (carried-time table in use), else NULL
+  CarryHash ch;                // carried-time table (mask 0: none)
+  int trunc;                   // QDTA_TRUNC_*
   long long *n_items_dev;
   int *flag, *active, *root_slot, *n_active;
   int *q_fin, *q_work;
@@ -1551,9 +1559,9 @@ struct Day {
 static int day_merge(Day &D) {
   qdta_graph *g = D.S.g;
   cudaStream_t s = D.S.s;
-  launch_scatter_orig(g->d, D.S.ctl, D.tab, D.max_orig, D.dense, s);
+  launch_scatter_orig(g->d, D.S.ctl, D.tab, D.max_orig, D.dense, s, D.ch, g->status);
   launch_compact(g->d, D.Z, D.dense, D.blk_count, D.blk_off, D.cap_items, D.it_root, D.it_src, D.it_amt,
-                 D.n_items_dev, g->status, s);
+                 D.n_items_dev, g->status, s, D.it_carry, D.ch);
   launch_active_roots(D.Z, D.n_items_dev, D.cap_items, D.it_root, D.zones, D.flag, D.active, D.root_slot,
                       D.n_active, s);
   return QDTA_OK;
@@ -1590,7 +1598,7 @@ static int day_res_body(Day &D, unsigned long long h, int use_cond) {
               S.parent_stride, nullptr, s, &S.ctl->res_skip, real_batch));
   launch_residual(g->d, D.hq_fin, S.parent, &S.ctl->res_slot, S.parent_stride, D.root_slot, D.zones,
                   D.n_items_dev, D.cap_items, D.it_root, D.it_src, D.it_amt, &S.ctl->w_cur, S.dt_q, D.h_fx,
-                  D.dense, g->status, s);
+                  D.dense, g->status, s, D.it_carry, D.trunc, D.ch);
   launch_res_next(S.ctl, h, use_cond, s);
   return QDTA_OK;
 }
@@ -1697,6 +1705,11 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
     RC(check_od(g, resid_in));
     if (resid_in->n_items > 0 && resid_in->n_roots != Z) return fail(QDTA_EINVAL, "resid_in must use the zone list");
   }
+  // carried times in play: the carried-time table and per-item carries
+  bool any_carry = p->truncation == QDTA_TRUNC_CARRY || (resid_in && resid_in->carry_q);
+  for (int i = 0; i < N; ++i) any_carry = any_carry || d_orig[i].carry_q != nullptr;
+  if (any_carry && resid_out && !resid_out->carry_q)
+    return fail(QDTA_EINVAL, "resid_out->carry_q is needed when trips carry partial links");
   DevGuard guard(g->device);
   cudaStream_t s = (cudaStream_t)stream;
   const size_t V = g->d.V, L = g->d.L;
@@ -1716,6 +1729,29 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   for (int i = 0; i < N; ++i) max_orig = d_orig[i].n_items > max_orig ? d_orig[i].n_items : max_orig;
   D.max_orig = max_orig;
   D.cap_items = dense_n < (64ll << 20) ? dense_n : (64ll << 20);
+  D.trunc = p->truncation;
+  D.ch = CarryHash{};
+  D.it_carry = nullptr;
+  if (any_carry) {
+    // key = ((root * V + node) << tau_bits) | carried time; the table holds
+    // up to half its slots (at most 32M entries) and items get as many slots
+    int dbits = 1;
+    while ((1ll << dbits) < dense_n) ++dbits;
+    D.ch.tau_bits = 64 - dbits;
+    if (D.ch.tau_bits < 24)
+      return fail(QDTA_EINVAL, "carried truncation: zones x nodes = %lld leaves fewer than 24 bits of carried time",
+                  dense_n);
+    const long long want = std::min<long long>(std::max<long long>(dense_n, 1ll << 16), 32ll << 20);
+    long long H = 1;
+    while (H < 2 * want) H <<= 1;
+    RC(ws_get(g, "day.carry_keys", (size_t)H, &D.ch.keys));
+    RC(ws_get(g, "day.carry_vals", (size_t)H, &D.ch.vals));
+    D.ch.mask = (unsigned long long)(H - 1);
+    CK(cudaMemsetAsync(D.ch.keys, 0xFF, (size_t)H * 8, s));
+    CK(cudaMemsetAsync(D.ch.vals, 0, (size_t)H * 8, s));
+    D.cap_items += H / 2;
+    RC(ws_get(g, "day.it_carry", (size_t)D.cap_items, &D.it_carry));
+  }
   RC(ws_get(g, "day.it_root", (size_t)D.cap_items, &D.it_root));
   RC(ws_get(g, "day.it_src", (size_t)D.cap_items, &D.it_src));
   RC(ws_get(g, "day.it_amt", (size_t)D.cap_items, &D.it_amt));
@@ -1734,7 +1770,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   std::vector<OrigTable> tab(N);
   for (int i = 0; i < N; ++i)
     tab[i] = OrigTable{d_orig[i].root_idx, d_orig[i].src, (const long long *)d_orig[i].amount_fx,
-                       d_orig[i].n_items};
+                       d_orig[i].n_items, (const long long *)d_orig[i].carry_q};
   RC(ws_get(g, "day.tab", (size_t)N, &D.tab));
   CK(cudaMemcpyAsync(D.tab, tab.data(), sizeof(OrigTable) * N, cudaMemcpyHostToDevice, s));
   // solver over the zone list
@@ -1742,6 +1778,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   S.root_slot = D.root_slot; S.item_roots = D.zones;
   S.n_host = 0; S.n_dev = D.n_items_dev;
   S.root_idx = D.it_root; S.src = D.it_src; S.amount = D.it_amt;
+  S.carry = D.it_carry;
   RC(ws_get(g, "day.f", L, &S.f));
   // parent ring: keep every tree of an interval when memory allows.  The
   // ring this handle already holds counts as available (a later day must
@@ -1785,7 +1822,8 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   CK(cudaMemsetAsync(D.dense, 0, (size_t)dense_n * 8, s));
   if (resid_in && resid_in->n_items > 0)
     launch_scatter_items(g->d, resid_in->n_items, resid_in->root_idx, resid_in->src,
-                         (const long long *)resid_in->amount_fx, D.dense, s);
+                         (const long long *)resid_in->amount_fx, D.dense, s,
+                         (const long long *)resid_in->carry_q, D.ch, g->status);
   // day counter lives in the solver's controller
   int dayinit[3] = {0, N, 1};
   CK(cudaMemcpyAsync(&S.ctl->day_i, dayinit, sizeof dayinit, cudaMemcpyHostToDevice, s));
@@ -1806,13 +1844,18 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   // residual after the last interval
   if (resid_out) {
     launch_compact(g->d, Z, D.dense, D.blk_count, D.blk_off, resid_out->capacity, resid_out->root_idx,
-                   resid_out->src, (long long *)resid_out->amount_fx, D.n_items_dev, g->status, s);
+                   resid_out->src, (long long *)resid_out->amount_fx, D.n_items_dev, g->status, s,
+                   (long long *)resid_out->carry_q, D.ch);
     long long cnt = 0;
     CK(cudaMemcpyAsync(&cnt, D.n_items_dev, 8, cudaMemcpyDeviceToHost, s));
     RC(status_check(g, s));
     resid_out->count = cnt;
   } else {
     CK(cudaMemsetAsync(D.dense, 0, (size_t)dense_n * 8, s));
+    if (D.ch.mask) {
+      CK(cudaMemsetAsync(D.ch.keys, 0xFF, (size_t)(D.ch.mask + 1) * 8, s));
+      CK(cudaMemsetAsync(D.ch.vals, 0, (size_t)(D.ch.mask + 1) * 8, s));
+    }
   }
   (void)worst;
   return QDTA_OK;
@@ -1883,7 +1926,8 @@ extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_dd
     launch_pack_head_q(g->d, qk, hq, s);
     CK(cudaMemsetAsync(gfx, 0, L * 8, s));
     launch_load(g->d, hq, parent, nullptr, 0, nullptr, t->od.roots, n, nullptr, t->od.root_idx, t->od.src,
-                (const long long *)t->od.amount_fx, dt_q, gfx, nullptr, g->status, s);
+                (const long long *)t->od.amount_fx, dt_q, gfx, nullptr, g->status, s,
+                (const long long *)t->od.carry_q);
     const double *gb = lam;
     if (k > 0) {
       const double *fprev = t->f + (size_t)(k - 1) * L;
@@ -1894,7 +1938,7 @@ extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_dd
       gb = gbar;
     }
     launch_gather(g->d, hq, parent, t->od.roots, n, t->od.root_idx, t->od.src, dt_q, gb, dL_ddemand,
-                  g->status, s);
+                  g->status, s, (const long long *)t->od.carry_q);
     if (k > 0) std::swap(lam, lam2);
   }
   return status_check(g, s);

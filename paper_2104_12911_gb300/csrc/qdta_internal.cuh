@@ -365,18 +365,33 @@ long long launch_count();
 void launch_set_cond(const Ctl *ctl, int which, unsigned long long cond, cudaStream_t s);
 int sssp_blocks_per_sm(bool use_smem, int V);
 
+// Residual items that carry a partial link (QDTA_TRUNC_CARRY) merge by
+// (root, node, carried time) in an open-addressed table: key = ((root * V +
+// node) << tau_bits) | carried time, ~0 when empty; amounts summed with
+// integer atomics.  mask = 0: no table (QDTA_TRUNC_NODE).
+struct CarryHash {
+  unsigned long long *keys = nullptr;  // [mask + 1]
+  long long *vals = nullptr;           // [mask + 1]
+  unsigned long long mask = 0;
+  int tau_bits = 0;
+};
+
 void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStream_t s);
+// carry [n] (nullable): per item, time already travelled beyond src (the walk starts at -carry)
 void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const int *parent_slot_dev,
                  long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
                  const long long *n_items_dev, const int *root_idx, const int *src,
                  const long long *amount, long long dt_q, unsigned long long *flow_fx, int *stop_out,
-                 unsigned *status, cudaStream_t s);
+                 unsigned *status, cudaStream_t s, const long long *carry = nullptr);
+// trunc 1 (carry): a trip stopping inside a link goes to the table `ch` with
+// its carried time; trips stopping at a node go to `dense`
 void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *parent,
                      const int *parent_slot_dev, long long slot_stride, const int *root_slot,
                      const int *roots, const long long *n_items_dev, long long n_items_cap,
                      const int *root_idx, const int *src, const long long *amount,
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
-                     unsigned long long *dense, unsigned *status, cudaStream_t s);
+                     unsigned long long *dense, unsigned *status, cudaStream_t s,
+                     const long long *carry = nullptr, int trunc = 0, CarryHash ch = CarryHash{});
 
 // marginal = 1: the system optimum's marginal costs instead of link times
 void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,
@@ -406,20 +421,28 @@ void launch_store_interval(const GraphDev &g, const Ctl *ctl, const unsigned lon
                            double *flow_out_rows, void *stats_rows, const long long *n_items_dev,
                            cudaStream_t s);
 void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s);
-struct OrigTable { const int *root_idx; const int *src; const long long *amount; long long n; };
+struct OrigTable { const int *root_idx; const int *src; const long long *amount; long long n; const long long *carry; };
 void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab, long long max_n,
-                         unsigned long long *dense, cudaStream_t s);
+                         unsigned long long *dense, cudaStream_t s, CarryHash ch = CarryHash{},
+                         unsigned *status = nullptr);
 void launch_ctl_begin(Ctl *ctl, unsigned long long cond_fw, int use_cond, cudaStream_t s);
 void launch_ctl_step(Ctl *ctl, unsigned long long cond_ls, int use_cond, cudaStream_t s);
 void launch_ctl_end(Ctl *ctl, unsigned long long cond_fw, int use_cond, cudaStream_t s);
 void launch_tape_record(const GraphDev &g, const Ctl *ctl, const int *q, const double *f,
                         int *tape_q, double *tape_alpha, double *tape_f, int cap, cudaStream_t s);
 
+// items with carry > 0 go to the table `ch` (which must exist then)
 void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, const int *src,
-                          const long long *amount, unsigned long long *dense, cudaStream_t s);
+                          const long long *amount, unsigned long long *dense, cudaStream_t s,
+                          const long long *carry = nullptr, CarryHash ch = CarryHash{},
+                          unsigned *status = nullptr);
+// dense (root, node) accumulator -> items in (root, node) order, then (when
+// ch has a table) its entries appended in table order; carry_out (nullable)
+// receives each item's carried time.  Both sources are cleared.
 void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *blk_count,
                     long long *blk_off, long long cap, int *root_idx, int *src, long long *amount,
-                    long long *n_out_dev, unsigned *status, cudaStream_t s);
+                    long long *n_out_dev, unsigned *status, cudaStream_t s, long long *carry_out = nullptr,
+                    CarryHash ch = CarryHash{});
 void launch_active_roots(int R, const long long *n_items_dev, long long cap_items,
                          const int *root_idx, const int *zone_nodes, int *flag, int *active_roots,
                          int *root_slot, int *n_active_dev, cudaStream_t s);
@@ -437,6 +460,7 @@ void launch_adj_update(const GraphDev &g, const LinkConst *kc, const double *lam
                        double *gbar, double *lam_prev, double *dcap, cudaStream_t s);
 void launch_gather(const GraphDev &g, const int2 *head_q, const int *parent, const int *roots,
                    long long n_items, const int *root_idx, const int *src, long long dt_q,
-                   const double *gbar, double *dd, unsigned *status, cudaStream_t s);
+                   const double *gbar, double *dd, unsigned *status, cudaStream_t s,
+                   const long long *carry = nullptr);
 
 }  // namespace qdta

@@ -1490,7 +1490,7 @@ __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *_
                             long long n_host, const long long *n_dev, const int *__restrict__ root_idx,
                             const int *__restrict__ src, const long long *__restrict__ amount,
                             long long dt_q, unsigned long long *flow_fx, int *stop_out,
-                            unsigned *status) {
+                            unsigned *status, const long long *__restrict__ carry) {
   const long long n = n_dev ? *n_dev : n_host;
   if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -1500,7 +1500,7 @@ __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *_
     const int *par = parent + (long long)(root_slot ? root_slot[r] : r) * V;
     const unsigned long long amt = (unsigned long long)amount[k];
     int u = src[k];
-    long long elapsed = 0;
+    long long elapsed = carry ? -carry[k] : 0;
     int steps = 0;
     while (u != z) {
       if (elapsed >= dt_q) break;
@@ -1550,26 +1550,60 @@ void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const
                  long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
                  const long long *n_items_dev, const int *root_idx, const int *src,
                  const long long *amount, long long dt_q, unsigned long long *flow_fx, int *stop_out,
-                 unsigned *status, cudaStream_t s) {
+                 unsigned *status, cudaStream_t s, const long long *carry) {
   long long n = n_items_dev ? (long long)g.num_sms * 16 * 256 : n_items_host;
   if (n <= 0) return;
   COUNT_LAUNCH();
   load_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, head_q, parent, parent_slot_dev, slot_stride,
                                               root_slot, roots, n_items_host, n_items_dev, root_idx,
-                                              src, amount, dt_q, flow_fx, stop_out, status);
+                                              src, amount, dt_q, flow_fx, stop_out, status, carry);
+}
+
+// one residual entry with a carried time into the table: linear probing,
+// the key claimed by compare-and-swap, amounts summed; a full table (every
+// slot probed) sets ST_CAPACITY, a carried time beyond the key's field
+// ST_OVERFLOW
+__device__ __forceinline__ unsigned long long carry_slot_hash(unsigned long long x) {
+  // the splitmix64 finalizer (Steele, Lea and Flood), as a bit mixer
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+__device__ void carry_add(const CarryHash &ch, long long d, long long tau, long long amt, unsigned *status) {
+  if (ch.mask == 0ull || tau >= (1ll << ch.tau_bits)) {
+    if (status) atomicOr(status, ch.mask == 0ull ? ST_CAPACITY : ST_OVERFLOW);
+    return;
+  }
+  const unsigned long long key = ((unsigned long long)d << ch.tau_bits) | (unsigned long long)tau;
+  unsigned long long h = carry_slot_hash(key) & ch.mask;
+  for (unsigned long long probe = 0; probe <= ch.mask; ++probe) {
+    const unsigned long long prev = atomicCAS(&ch.keys[h], ~0ull, key);
+    if (prev == ~0ull || prev == key) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(&ch.vals[h]), (unsigned long long)amt);
+      return;
+    }
+    h = (h + 1) & ch.mask;
+  }
+  if (status) atomicOr(status, ST_CAPACITY);
 }
 
 // Alg. 4 for one accepted AON j: the item's path on tree j is re-truncated
 // with the final link times (head_q_fin); its share RN(amount * w_j) loads
 // h and, if the walk stops before the root, joins the residual demand of the
-// next interval in the dense (root, node) accumulator.
+// next interval: in the dense (root, node) accumulator, or with trunc = 1
+// (carried truncation) and a partial link, in the carried-time table.
 __global__ void residual_kernel(int V, const int2 *__restrict__ head_q_fin, const int *__restrict__ parent,
                                 const int *parent_slot_dev, long long slot_stride,
                                 const int *__restrict__ root_slot, const int *__restrict__ roots,
                                 const long long *n_dev, const int *__restrict__ root_idx,
                                 const int *__restrict__ src, const long long *__restrict__ amount,
                                 const double *weight_dev, long long dt_q, unsigned long long *h_fx,
-                                unsigned long long *dense, unsigned *status) {
+                                unsigned long long *dense, unsigned *status, const long long *__restrict__ carry,
+                                int trunc, CarryHash ch) {
   const long long n = *n_dev;
   const double w = *weight_dev;
   if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
@@ -1581,7 +1615,7 @@ __global__ void residual_kernel(int V, const int2 *__restrict__ head_q_fin, cons
     const int z = roots[r];
     const int *par = parent + (long long)root_slot[r] * V;
     int u = src[k];
-    long long elapsed = 0;
+    long long elapsed = carry ? -carry[k] : 0, tau = 0;
     int steps = 0;
     while (u != z) {
       if (elapsed >= dt_q) break;
@@ -1589,11 +1623,18 @@ __global__ void residual_kernel(int V, const int2 *__restrict__ head_q_fin, cons
       if (e < 0) { atomicOr(status, ST_UNREACH); break; }
       atomicAdd(&h_fx[e], (unsigned long long)amt);
       const int2 hq = __ldg(&head_q_fin[e]);
+      if (trunc && elapsed + hq.y > dt_q) {  // on this link at the end of the interval
+        tau = dt_q - elapsed;
+        break;
+      }
       elapsed += hq.y;
       u = hq.x;
       if (++steps > V) { atomicOr(status, ST_TIMEOUT); break; }
     }
-    if (u != z) atomicAdd(&dense[(long long)r * V + u], (unsigned long long)amt);
+    if (u != z) {
+      if (tau > 0) carry_add(ch, (long long)r * V + u, tau, amt, status);
+      else atomicAdd(&dense[(long long)r * V + u], (unsigned long long)amt);
+    }
   }
 }
 
@@ -1602,12 +1643,13 @@ void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *paren
                      const int *roots, const long long *n_items_dev, long long n_items_cap,
                      const int *root_idx, const int *src, const long long *amount,
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
-                     unsigned long long *dense, unsigned *status, cudaStream_t s) {
+                     unsigned long long *dense, unsigned *status, cudaStream_t s, const long long *carry,
+                     int trunc, CarryHash ch) {
   if (n_items_cap <= 0) return;
   COUNT_LAUNCH();
   residual_kernel<<<link_grid(g, n_items_cap), 256, 0, s>>>(
       g.V, head_q_fin, parent, parent_slot_dev, slot_stride, root_slot, roots, n_items_dev, root_idx, src, amount, weight_dev,
-      dt_q, h_fx, dense, status);
+      dt_q, h_fx, dense, status, carry, trunc, ch);
 }
 
 // ============================================================================
@@ -2257,19 +2299,22 @@ void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream
 
 // original demand of the current interval into the dense accumulator
 __global__ void scatter_orig_kernel(int V, const Ctl *c, const OrigTable *tab,
-                                    unsigned long long *dense) {
+                                    unsigned long long *dense, CarryHash ch, unsigned *status) {
   const OrigTable t = tab[c->day_i];
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < t.n;
        k += (long long)gridDim.x * blockDim.x) {
     const long long a = t.amount[k];
-    if (a) atomicAdd(&dense[(long long)t.root_idx[k] * V + t.src[k]], (unsigned long long)a);
+    const long long tau = t.carry ? t.carry[k] : 0;
+    const long long d = (long long)t.root_idx[k] * V + t.src[k];
+    if (a && tau > 0) carry_add(ch, d, tau, a, status);
+    else if (a) atomicAdd(&dense[d], (unsigned long long)a);
   }
 }
 
 void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab, long long max_n,
-                         unsigned long long *dense, cudaStream_t s) {
+                         unsigned long long *dense, cudaStream_t s, CarryHash ch, unsigned *status) {
   COUNT_LAUNCH();
-  scatter_orig_kernel<<<link_grid(g, max_n > 0 ? max_n : 1), 256, 0, s>>>(g.V, ctl, tab, dense);
+  scatter_orig_kernel<<<link_grid(g, max_n > 0 ? max_n : 1), 256, 0, s>>>(g.V, ctl, tab, dense, ch, status);
 }
 
 // ============================================================================
@@ -2277,19 +2322,24 @@ void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab
 // ============================================================================
 
 __global__ void scatter_items_kernel(int V, long long n, const int *root_idx, const int *src,
-                                     const long long *amount, unsigned long long *dense) {
+                                     const long long *amount, unsigned long long *dense,
+                                     const long long *carry, CarryHash ch, unsigned *status) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const long long a = amount[k];
-    if (a) atomicAdd(&dense[(long long)root_idx[k] * V + src[k]], (unsigned long long)a);
+    const long long tau = carry ? carry[k] : 0;
+    const long long d = (long long)root_idx[k] * V + src[k];
+    if (a && tau > 0) carry_add(ch, d, tau, a, status);
+    else if (a) atomicAdd(&dense[d], (unsigned long long)a);
   }
 }
 
 void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, const int *src,
-                          const long long *amount, unsigned long long *dense, cudaStream_t s) {
+                          const long long *amount, unsigned long long *dense, cudaStream_t s,
+                          const long long *carry, CarryHash ch, unsigned *status) {
   if (n <= 0) return;
   COUNT_LAUNCH();
-  scatter_items_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, n, root_idx, src, amount, dense);
+  scatter_items_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, n, root_idx, src, amount, dense, carry, ch, status);
 }
 
 constexpr int COMPACT_TILE = 4096;
@@ -2339,7 +2389,7 @@ __global__ void compact_scan_kernel(int nblk, const int *blk_count, long long *b
 // ordered write of the nonzero entries of each tile (root-major, node-minor)
 __global__ void compact_write_kernel(long long total, int V, unsigned long long *dense,
                                      const long long *blk_off, long long cap, int *root_idx,
-                                     int *src, long long *amount) {
+                                     int *src, long long *amount, long long *carry_out) {
   __shared__ int s_warp[32];
   const long long base = (long long)blockIdx.x * COMPACT_TILE;
   long long out = blk_off[blockIdx.x];
@@ -2360,6 +2410,7 @@ __global__ void compact_write_kernel(long long total, int V, unsigned long long 
         root_idx[pos] = (int)(idx / V);
         src[pos] = (int)(idx % V);
         amount[pos] = (long long)v;
+        if (carry_out) carry_out[pos] = 0;
       }
       dense[idx] = 0ull;
     }
@@ -2368,9 +2419,36 @@ __global__ void compact_write_kernel(long long total, int V, unsigned long long 
   }
 }
 
+// carried-time table -> items appended after the n_out the dense pass wrote
+// (positions by atomic counter: the order varies, the multiset does not);
+// every slot is cleared
+__global__ void carry_compact_kernel(CarryHash ch, int V, long long cap, int *root_idx, int *src,
+                                     long long *amount, long long *carry_out, long long *n_out,
+                                     unsigned *status) {
+  const unsigned long long fmask = (1ull << ch.tau_bits) - 1ull;
+  for (unsigned long long h = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; h <= ch.mask;
+       h += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long key = ch.keys[h];
+    if (key == ~0ull) continue;
+    const long long pos = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(n_out), 1ull);
+    const long long d = (long long)(key >> ch.tau_bits);
+    if (pos < cap) {
+      root_idx[pos] = (int)(d / V);
+      src[pos] = (int)(d % V);
+      amount[pos] = ch.vals[h];
+      if (carry_out) carry_out[pos] = (long long)(key & fmask);
+    } else {
+      atomicOr(status, ST_CAPACITY);
+    }
+    ch.keys[h] = ~0ull;
+    ch.vals[h] = 0;
+  }
+}
+
 void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *blk_count,
                     long long *blk_off, long long cap, int *root_idx, int *src, long long *amount,
-                    long long *n_out_dev, unsigned *status, cudaStream_t s) {
+                    long long *n_out_dev, unsigned *status, cudaStream_t s, long long *carry_out,
+                    CarryHash ch) {
   const long long total = (long long)R * g.V;
   const int nblk = cdiv(total > 0 ? total : 1, COMPACT_TILE);
   COUNT_LAUNCH();
@@ -2378,7 +2456,13 @@ void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *bl
   COUNT_LAUNCH();
   compact_scan_kernel<<<1, 1024, 0, s>>>(nblk, blk_count, blk_off, cap, n_out_dev, status);
   COUNT_LAUNCH();
-  compact_write_kernel<<<nblk, 256, 0, s>>>(total, g.V, dense, blk_off, cap, root_idx, src, amount);
+  compact_write_kernel<<<nblk, 256, 0, s>>>(total, g.V, dense, blk_off, cap, root_idx, src, amount, carry_out);
+  if (ch.mask) {
+    const long long slots = (long long)ch.mask + 1;
+    COUNT_LAUNCH();
+    carry_compact_kernel<<<link_grid(g, slots), 256, 0, s>>>(ch, g.V, cap, root_idx, src, amount, carry_out,
+                                                             n_out_dev, status);
+  }
 }
 
 // roots with at least one item, in root order; root_slot maps a root index
@@ -2634,14 +2718,14 @@ void launch_adj_update(const GraphDev &g, const LinkConst *kc, const double *lam
 __global__ void gather_kernel(int V, const int2 *__restrict__ head_q, const int *__restrict__ parent,
                               const int *__restrict__ roots, long long n, const int *__restrict__ root_idx,
                               const int *__restrict__ src, long long dt_q, const double *__restrict__ gbar,
-                              double *dd, unsigned *status) {
+                              double *dd, unsigned *status, const long long *__restrict__ carry) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const int r = root_idx[k];
     const int z = roots[r];
     const int *par = parent + (long long)r * V;
     int u = src[k];
-    long long elapsed = 0;
+    long long elapsed = carry ? -carry[k] : 0;
     double acc = 0.0;
     int steps = 0;
     while (u != z && elapsed < dt_q) {
@@ -2659,11 +2743,11 @@ __global__ void gather_kernel(int V, const int2 *__restrict__ head_q, const int 
 
 void launch_gather(const GraphDev &g, const int2 *head_q, const int *parent, const int *roots,
                    long long n_items, const int *root_idx, const int *src, long long dt_q,
-                   const double *gbar, double *dd, unsigned *status, cudaStream_t s) {
+                   const double *gbar, double *dd, unsigned *status, cudaStream_t s, const long long *carry) {
   if (n_items <= 0) return;
   COUNT_LAUNCH();
   gather_kernel<<<link_grid(g, n_items), 256, 0, s>>>(g.V, head_q, parent, roots, n_items, root_idx,
-                                                      src, dt_q, gbar, dd, status);
+                                                      src, dt_q, gbar, dd, status, carry);
 }
 
 }  // namespace qdta

@@ -23,6 +23,7 @@ QDTA_TO_ROOT, QDTA_FROM_ROOT = 0, 1
 STEP = {"msa": 0, "paper_qn3": 1, "sweep8": 2, "exact": 3}
 STOP = {"none": 0, "paper_obj": 1, "rel_gap": 2}
 OBJECTIVE = {"ue": 0, "so": 1}
+TRUNCATION = {"node": 0, "carry": 1}
 SCHEDULE = {"plain": 0, "graph": 1}
 DIST_INF = np.iinfo(np.int64).max
 FX_ONE = 1 << 32
@@ -42,14 +43,15 @@ class GraphDesc(C.Structure):
 
 class OD(C.Structure):
     _fields_ = [("n_roots", C.c_int32), ("roots", C.c_void_p), ("n_items", C.c_int64),
-                ("root_idx", C.c_void_p), ("src", C.c_void_p), ("amount_fx", C.c_void_p)]
+                ("root_idx", C.c_void_p), ("src", C.c_void_p), ("amount_fx", C.c_void_p),
+                ("carry_q", C.c_void_p)]
 
 
 class Params(C.Structure):
     _fields_ = [("step", C.c_int32), ("stop", C.c_int32), ("max_iter", C.c_int32),
                 ("ls_max", C.c_int32), ("tol", C.c_double), ("ls_dx", C.c_double),
                 ("ls_t1", C.c_double), ("ls_t2", C.c_double), ("schedule", C.c_int32),
-                ("record_tape", C.c_int32), ("objective", C.c_int32)]
+                ("record_tape", C.c_int32), ("objective", C.c_int32), ("truncation", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -63,7 +65,7 @@ class Stats(C.Structure):
 
 class Residual(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("root_idx", C.c_void_p), ("src", C.c_void_p),
-                ("amount_fx", C.c_void_p), ("count", C.c_int64)]
+                ("amount_fx", C.c_void_p), ("count", C.c_int64), ("carry_q", C.c_void_p)]
 
 
 class Profile(C.Structure):
@@ -162,12 +164,14 @@ def _stream():
 
 
 def make_params(step="sweep8", stop="rel_gap", max_iter=200, tol=1e-4, ls_max=20, ls_dx=1e-4,
-                ls_t1=1e-4, ls_t2=1e-4, schedule="plain", record_tape=False, objective="ue") -> Params:
+                ls_t1=1e-4, ls_t2=1e-4, schedule="plain", record_tape=False, objective="ue",
+                truncation="node") -> Params:
     return Params(STEP[step] if isinstance(step, str) else int(step),
                   STOP[stop] if isinstance(stop, str) else int(stop), int(max_iter), int(ls_max),
                   float(tol), float(ls_dx), float(ls_t1), float(ls_t2),
                   SCHEDULE[schedule] if isinstance(schedule, str) else int(schedule),
-                  1 if record_tape else 0, OBJECTIVE[objective] if isinstance(objective, str) else int(objective))
+                  1 if record_tape else 0, OBJECTIVE[objective] if isinstance(objective, str) else int(objective),
+                  TRUNCATION[truncation] if isinstance(truncation, str) else int(truncation))
 
 
 class Graph:
@@ -212,6 +216,7 @@ class DeviceOD:
     root_idx: torch.Tensor
     src: torch.Tensor
     amount_fx: torch.Tensor
+    carry_q: torch.Tensor = None  # int64 per item (time already travelled beyond src), or None
 
     @classmethod
     def of(cls, dem, device="cuda", pin=False):
@@ -227,7 +232,8 @@ class DeviceOD:
 
     def struct(self) -> OD:
         return OD(int(self.roots.shape[0]), self.roots.data_ptr(), self.n_items,
-                  self.root_idx.data_ptr(), self.src.data_ptr(), self.amount_fx.data_ptr())
+                  self.root_idx.data_ptr(), self.src.data_ptr(), self.amount_fx.data_ptr(),
+                  self.carry_q.data_ptr() if self.carry_q is not None else None)
 
 
 # ---------------------------------------------------------------------------
@@ -360,15 +366,17 @@ def qdta_run_day(g: Graph, days, dt_s: float, params: Params, resid_in: DeviceOD
     if resid_capacity > 0:
         bufs = (torch.empty(resid_capacity, dtype=torch.int32, device=g.device),
                 torch.empty(resid_capacity, dtype=torch.int32, device=g.device),
+                torch.empty(resid_capacity, dtype=torch.int64, device=g.device),
                 torch.empty(resid_capacity, dtype=torch.int64, device=g.device))
-        rout = Residual(resid_capacity, bufs[0].data_ptr(), bufs[1].data_ptr(), bufs[2].data_ptr(), 0)
+        rout = Residual(resid_capacity, bufs[0].data_ptr(), bufs[1].data_ptr(), bufs[2].data_ptr(), 0,
+                        bufs[3].data_ptr())
     rc = _check(lib().qdta_run_day(g.h, arr, N, float(dt_s), C.byref(params),
                                    C.byref(rin) if rin is not None else None, _ptr(flow_out), st,
                                    C.byref(rout) if rout is not None else None, _stream()))
     resid = None
     if rout is not None:
         n = rout.count
-        resid = (bufs[0][:n], bufs[1][:n], bufs[2][:n])
+        resid = (bufs[0][:n], bufs[1][:n], bufs[2][:n], bufs[3][:n])  # root index, stop node, amount, carry
     return flow_out, [s.as_dict() for s in st], rc, resid
 
 

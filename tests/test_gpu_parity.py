@@ -595,6 +595,25 @@ def test_run_day_large_graph_bit_exact(mid_day, schedule, variant, monkeypatch):
         assert prof["sssp_redo_batches"] > 0  # the 2^29 overflow happened inside the day
 
 
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+def test_run_day_large_graph_carried_truncation_bit_exact(schedule):
+    """The large-graph day of the test above under carried truncation."""
+    net, zones, days = _mid_day()
+    og = oracle.OracleGraph(net)
+    f_o, st_o, nit_o, rn_o, rc_o = oracle.run_day(og, zones, days, 900.0, oracle.make_params(
+        Q.STEP[MID_DAY_PARAMS[0]], Q.STOP[MID_DAY_PARAMS[1]], MID_DAY_PARAMS[2], truncation=oracle.TRUNC_CARRY))
+    g = Q.Graph(net)
+    zt = T(zones, np.int32)
+    dd = [Q.DeviceOD(zt, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
+    f_g, st_g, rc_g, resid = Q.qdta_run_day(g, dd, 900.0, Q.make_params(*MID_DAY_PARAMS, schedule=schedule,
+                                                                          truncation="carry"),
+                                            resid_capacity=1 << 21)
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    assert [s["n_items"] for s in st_g] == list(nit_o)
+    assert [s["iterations"] for s in st_g] == [s["iterations"] for s in st_o]
+    assert resid[0].shape[0] == rn_o
+
+
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("step", ["exact", "msa"])
 def test_backward_matches_oracle(step):
@@ -823,3 +842,92 @@ def test_autograd_reuses_one_graph_handle():
                                            oracle.make_params(oracle.STEP_EXACT, oracle.STOP_NONE, 4))
         np.testing.assert_array_equal(f.detach().cpu().numpy(), f_o)
     assert len(handles) == 1
+
+
+# ---------------------------------------------------------------------------
+# Carried partial-link truncation (Section 3.4's alternative to Eq. 2)
+def _carry_day_case():
+    # 150 s intervals on the 32 x 32 grid: most trips cross several intervals
+    return synth.scaled_day(synth.config_small(0), 60000, n_intervals=5, seed=5)
+
+
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+@pytest.mark.parametrize("step,stop,it", [("msa", "none", 6), ("sweep8", "paper_obj", 40)])
+def test_run_day_carried_truncation_bit_exact(schedule, step, stop, it):
+    day = _carry_day_case()
+    days = list(day.demand)
+    og = oracle.OracleGraph(day.net)
+    f_o, st_o, nit_o, rn_o, rc_o = oracle.run_day(og, day.zones, days, 150.0, oracle.make_params(
+        Q.STEP[step], Q.STOP[stop], it, truncation=oracle.TRUNC_CARRY))
+    g = Q.Graph(day.net)
+    zones = T(day.zones, np.int32)
+    dd = [Q.DeviceOD(zones, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
+    f_g, st_g, rc_g, resid = Q.qdta_run_day(g, dd, 150.0, Q.make_params(step, stop, it, schedule=schedule,
+                                                                          truncation="carry"),
+                                            resid_capacity=1 << 21)
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    for i in range(len(days)):
+        assert st_g[i]["n_items"] == nit_o[i], i
+        for key in ("iterations", "aon_calls", "ls_passes", "converged"):
+            assert st_g[i][key] == st_o[i][key], (i, key)
+    assert resid[0].shape[0] == rn_o and int((resid[3] > 0).sum()) > 0
+    # the node rule differs on the same inputs (the carried trips wait elsewhere)
+    f_n, _, _, _ = Q.qdta_run_day(g, dd, 150.0, Q.make_params(step, stop, it, schedule=schedule))
+    assert not torch.equal(f_n[1:], f_g[1:])
+
+
+def test_carried_truncation_crosses_a_long_link_on_the_gpu():
+    """The uncongested chain of 1000 s links with 300 s intervals: link k
+    carries the trip in exactly the intervals overlapping [1000 k, 1000 (k + 1)) s."""
+    net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
+    g = Q.Graph(net)
+    zones = T([3], np.int32)
+    N = 11
+    one = Q.DeviceOD(zones, T([0], np.int32), T([0], np.int32), T([1 << 32], np.int64))
+    empty = Q.DeviceOD(zones, T([], np.int32), T([], np.int32), T([], np.int64))
+    want = np.zeros((N, 3))
+    for i in range(N):
+        for k in range(3):
+            want[i, k] = float(max(300 * i, 1000 * k) < min(300 * (i + 1), 1000 * (k + 1)))
+    for schedule in ("plain", "graph"):
+        f, st, rc, _ = Q.qdta_run_day(g, [one] + [empty] * (N - 1), 300.0,
+                                      Q.make_params("msa", "none", 0, schedule=schedule, truncation="carry"))
+        np.testing.assert_array_equal(f.cpu().numpy(), want)
+        assert [s["n_items"] for s in st] == [1] * 10 + [0]
+
+
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+def test_carried_day_resumes_from_its_residual(schedule):
+    """Run intervals 0-1, take the residual (with its carried times) out,
+    resume intervals 2-4 from it: the same h(i) as the oracle's whole day."""
+    day = _carry_day_case()
+    days = list(day.demand)
+    og = oracle.OracleGraph(day.net)
+    p_o = oracle.make_params(Q.STEP["sweep8"], Q.STOP["paper_obj"], 40, truncation=oracle.TRUNC_CARRY)
+    f_o, st_o, nit_o, rn_o, _ = oracle.run_day(og, day.zones, days, 150.0, p_o)
+    g = Q.Graph(day.net)
+    zones = T(day.zones, np.int32)
+    dd = [Q.DeviceOD(zones, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
+    p = Q.make_params("sweep8", "paper_obj", 40, schedule=schedule, truncation="carry")
+    f_a, _, _, res = Q.qdta_run_day(g, dd[:2], 150.0, p, resid_capacity=1 << 21)
+    rin = Q.DeviceOD(zones, res[0].clone(), res[1].clone(), res[2].clone(), res[3].clone())
+    f_b, st_b, _, _ = Q.qdta_run_day(g, dd[2:], 150.0, p, resid_in=rin)
+    np.testing.assert_array_equal(torch.cat([f_a, f_b]).cpu().numpy(), f_o)
+    assert [s["n_items"] for s in st_b] == list(nit_o[2:])
+
+
+def test_load_aon_with_carried_times_matches_the_oracle(small):
+    inst, g, og = small
+    dem = inst.demand[0]
+    rng = np.random.default_rng(4)
+    carry = rng.integers(0, 40000, dem.n_items).astype(np.int64) * (rng.random(dem.n_items) < 0.5)
+    q = (inst.net.fftime_q * rng.uniform(1.0, 2.0, og.n_links)).astype(np.int32)
+    par_o, _ = oracle.sssp(og, q, dem.roots, want_dist=False)
+    od_o = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_q=carry)
+    for dt_q in (6000, 30000):
+        f_o, s_o, rc = oracle.load(og, q, par_o, od_o, dt_q)
+        od_g = Q.DeviceOD(T(dem.roots, np.int32), T(dem.root_idx, np.int32), T(dem.src, np.int32),
+                          T(dem.amount_fx, np.int64), T(carry, np.int64))
+        f_g, s_g = Q.qdta_load_aon(g, T(q, np.int32), T(par_o, np.int32), od_g, dt_q, want_stop=True)
+        np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+        np.testing.assert_array_equal(s_g.cpu().numpy(), s_o)
