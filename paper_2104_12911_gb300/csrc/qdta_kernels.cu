@@ -839,13 +839,15 @@ int sssp_group_size() {
 //      of 4 (a pass covers 320 or 384 nodes; 32-bit rank keys only)
 //   6, 7: as 1, one lane per frontier node (sssp_lane_kernel below), 1 or 2
 //      nodes per lane per pass (32-bit rank keys only; otherwise as 1)
+//   8, 9: as 6, with chained relaxation 2 or 4 hops deep
 struct SmqShape {
   int threads, bitmaps, qcap, ctas, npt;
 };
-constexpr int kSmqShapes = 8;
+constexpr int kSmqShapes = 10;
 static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 2048, 4, 4}, {512, 1, 3072, 2, 4},
                                                {256, 1, 768, 5, 4},  {256, 1, 2048, 4, 5}, {256, 1, 2048, 4, 6},
-                                               {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2}};
+                                               {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2},
+                                               {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 1}};
 
 // RELAX selects how an offer (cand, link) to neighbour y is applied:
 //   0  returning atomicMin; y is queued when the returned old distance was larger
@@ -1103,7 +1105,15 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
 // and carries 64-bit distances; the round structure, marks, queues, tie rule
 // (key = (distance << 3) | rank, atomicMin), overflow flag and output pass are
 // the same, so the results are the same bits.  Signature as SmqKernel.
-template <int THREADS, int NPN>
+//
+// CHAIN > 0 (NPN 1 only): a lane whose offer lowers a neighbour's distance
+// relaxes that neighbour itself right away, up to CHAIN hops deep, instead of
+// queueing it for the next round, so the frontier can advance several hops
+// per round.  The offers stay lengths of real paths, and a node that another
+// lane lowers further is queued by that lane (its mark is unset), so the
+// distances, the keys and hence the parents are unchanged.  A neighbour
+// already marked for the next queue is not adopted.
+template <int THREADS, int NPN, int CHAIN = 0>
 __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64))
 sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__restrict__ adj,
                  const int *__restrict__ roots, int R_host, const int *R_dev,
@@ -1150,69 +1160,126 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
         atomicAnd(&bm[y >> 5], ~(1u << (y & 31)));
       }
       __syncthreads();
-      for (int base = 0; base < ncur; base += THREADS * NPN) {
-        int w[NPN];
-        unsigned dw[NPN], prank[NPN];
-        int4 ra[NPN], rb[NPN];
-#pragma unroll
-        for (int n = 0; n < NPN; ++n) {
-          const int i = base + n * THREADS + (int)threadIdx.x;
-          w[n] = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
-        }
-#pragma unroll
-        for (int n = 0; n < NPN; ++n) {
-          dw[n] = 0u;
-          prank[n] = 8u;  // no slot
-          ra[n] = make_int4(-1, 0, -1, 0);
-          rb[n] = ra[n];
-          if (w[n] >= 0) {
-            const unsigned kw = __ldcg(&state[w[n]]);
-            dw[n] = kw >> 3;
-            if (skip_parent) prank[n] = kw & NOLINK;
-            ra[n] = __ldg(&rows[2 * w[n]]);
-            rb[n] = __ldg(&rows[2 * w[n] + 1]);
+      if constexpr (CHAIN > 0) {
+        static_assert(NPN == 1, "chained relaxation runs one node per lane");
+        for (int base = 0; base < ncur; base += THREADS) {
+          const int i = base + (int)threadIdx.x;
+          int w = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
+          unsigned dw = 0u, prank = 8u;
+          if (w >= 0) {
+            const unsigned kw = __ldcg(&state[w]);
+            dw = kw >> 3;
+            if (skip_parent) prank = kw & NOLINK;
           }
-        }
-        // slot s of node n: x = (neighbour << 3) | rank (-1 absent), t = link time
-        int sx[NPN][4];
-        unsigned st[NPN][4], tk[NPN][4];
+          for (int depth = 0; depth <= CHAIN && w >= 0; ++depth) {
+            const int4 ra = __ldg(&rows[2 * w]), rb = __ldg(&rows[2 * w + 1]);
+            int sx[4] = {ra.x, ra.z, rb.x, rb.z};
+            const unsigned st[4] = {(unsigned)ra.y, (unsigned)ra.w, (unsigned)rb.y, (unsigned)rb.w};
+            unsigned tk[4];
 #pragma unroll
-        for (int n = 0; n < NPN; ++n) {
-          sx[n][0] = ra[n].x; st[n][0] = (unsigned)ra[n].y;
-          sx[n][1] = ra[n].z; st[n][1] = (unsigned)ra[n].w;
-          sx[n][2] = rb[n].x; st[n][2] = (unsigned)rb[n].y;
-          sx[n][3] = rb[n].z; st[n][3] = (unsigned)rb[n].w;
-#pragma unroll
-          for (int s = 0; s < 4; ++s)
-            if (sx[n][s] >= 0 && (unsigned)s == prank[n]) sx[n][s] = -1;  // the way back to the parent
-        }
-#pragma unroll
-        for (int n = 0; n < NPN; ++n)
-#pragma unroll
-          for (int s = 0; s < 4; ++s) tk[n][s] = sx[n][s] >= 0 ? __ldcg(&state[sx[n][s] >> 3]) : 0u;
-#pragma unroll
-        for (int n = 0; n < NPN; ++n)
-#pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            if (sx[n][s] < 0) continue;
-            ++my_relax;
-            const unsigned cand = dw[n] + st[n][s];
-            if (cand >= DMAX) {
-              atomicOr(status, ST_K32);
-              continue;
+            for (int s = 0; s < 4; ++s) {
+              if (sx[s] >= 0 && (unsigned)s == prank) sx[s] = -1;  // the way back to the parent
+              tk[s] = sx[s] >= 0 ? __ldcg(&state[sx[s] >> 3]) : 0u;
             }
-            const unsigned key = (cand << 3) | (unsigned)(sx[n][s] & 7);
-            if (key < tk[n][s]) {
-              const int y = sx[n][s] >> 3;
-              atomicMin(&state[y], key);  // result unused: no wait on the reply
-              const unsigned bit = 1u << (y & 31);
-              if ((tk[n][s] >> 3) > cand && !(atomicOr(&bm[y >> 5], bit) & bit)) {
-                const int pos = atomicAdd(&s_cnt[c], 1);
-                if (pos < qcap) snxt[pos] = y;
-                else gnxt[pos - qcap] = y;
+            int nw = -1;
+            unsigned ndw = 0u, nrank = 8u;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              if (sx[s] < 0) continue;
+              ++my_relax;
+              const unsigned cand = dw + st[s];
+              if (cand >= DMAX) {
+                atomicOr(status, ST_K32);
+                continue;
+              }
+              const unsigned key = (cand << 3) | (unsigned)(sx[s] & 7);
+              if (key < tk[s]) {
+                const int y = sx[s] >> 3;
+                atomicMin(&state[y], key);
+                if ((tk[s] >> 3) > cand) {
+                  const unsigned bit = 1u << (y & 31);
+                  if (depth < CHAIN && nw < 0 && !(bm[y >> 5] & bit)) {
+                    nw = y;  // relax y next, from the distance just offered
+                    ndw = cand;
+                    nrank = skip_parent ? (unsigned)(sx[s] & 7) : 8u;
+                  } else if (!(atomicOr(&bm[y >> 5], bit) & bit)) {
+                    const int pos = atomicAdd(&s_cnt[c], 1);
+                    if (pos < qcap) snxt[pos] = y;
+                    else gnxt[pos - qcap] = y;
+                  }
+                }
               }
             }
+            w = nw;
+            dw = ndw;
+            prank = nrank;
           }
+        }
+      } else {
+        for (int base = 0; base < ncur; base += THREADS * NPN) {
+          int w[NPN];
+          unsigned dw[NPN], prank[NPN];
+          int4 ra[NPN], rb[NPN];
+  #pragma unroll
+          for (int n = 0; n < NPN; ++n) {
+            const int i = base + n * THREADS + (int)threadIdx.x;
+            w[n] = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
+          }
+  #pragma unroll
+          for (int n = 0; n < NPN; ++n) {
+            dw[n] = 0u;
+            prank[n] = 8u;  // no slot
+            ra[n] = make_int4(-1, 0, -1, 0);
+            rb[n] = ra[n];
+            if (w[n] >= 0) {
+              const unsigned kw = __ldcg(&state[w[n]]);
+              dw[n] = kw >> 3;
+              if (skip_parent) prank[n] = kw & NOLINK;
+              ra[n] = __ldg(&rows[2 * w[n]]);
+              rb[n] = __ldg(&rows[2 * w[n] + 1]);
+            }
+          }
+          // slot s of node n: x = (neighbour << 3) | rank (-1 absent), t = link time
+          int sx[NPN][4];
+          unsigned st[NPN][4], tk[NPN][4];
+  #pragma unroll
+          for (int n = 0; n < NPN; ++n) {
+            sx[n][0] = ra[n].x; st[n][0] = (unsigned)ra[n].y;
+            sx[n][1] = ra[n].z; st[n][1] = (unsigned)ra[n].w;
+            sx[n][2] = rb[n].x; st[n][2] = (unsigned)rb[n].y;
+            sx[n][3] = rb[n].z; st[n][3] = (unsigned)rb[n].w;
+  #pragma unroll
+            for (int s = 0; s < 4; ++s)
+              if (sx[n][s] >= 0 && (unsigned)s == prank[n]) sx[n][s] = -1;  // the way back to the parent
+          }
+  #pragma unroll
+          for (int n = 0; n < NPN; ++n)
+  #pragma unroll
+            for (int s = 0; s < 4; ++s) tk[n][s] = sx[n][s] >= 0 ? __ldcg(&state[sx[n][s] >> 3]) : 0u;
+  #pragma unroll
+          for (int n = 0; n < NPN; ++n)
+  #pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              if (sx[n][s] < 0) continue;
+              ++my_relax;
+              const unsigned cand = dw[n] + st[n][s];
+              if (cand >= DMAX) {
+                atomicOr(status, ST_K32);
+                continue;
+              }
+              const unsigned key = (cand << 3) | (unsigned)(sx[n][s] & 7);
+              if (key < tk[n][s]) {
+                const int y = sx[n][s] >> 3;
+                atomicMin(&state[y], key);  // result unused: no wait on the reply
+                const unsigned bit = 1u << (y & 31);
+                if ((tk[n][s] >> 3) > cand && !(atomicOr(&bm[y >> 5], bit) & bit)) {
+                  const int pos = atomicAdd(&s_cnt[c], 1);
+                  if (pos < qcap) snxt[pos] = y;
+                  else gnxt[pos - qcap] = y;
+                }
+              }
+            }
+        }
       }
       __syncthreads();
       ncur = s_cnt[c];
@@ -1298,7 +1365,8 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
           for (int r = 0; r < 4; ++r)
             v.push_back(sh >= 6 && e == 3
                             ? "sssp_lane_kernel<" + std::to_string(kSmqShape[sh].threads) + ",npn" +
-                                  std::to_string(kSmqShape[sh].npt) + ">"
+                                  std::to_string(kSmqShape[sh].npt) +
+                                  (sh == 8 ? ",chain2" : sh == 9 ? ",chain4" : "") + ">"
                             : "sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
                                   std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") +
                                   (sh == 3 && e == 3 ? ",5" : "") +
@@ -1368,6 +1436,8 @@ static SmqKernel smq_kernel_relax(int adj, int relax) {
 static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
   if (shape == 6 && adj == 3) return sssp_lane_kernel<256, 1>;
   if (shape == 7 && adj == 3) return sssp_lane_kernel<256, 2>;
+  if (shape == 8 && adj == 3) return sssp_lane_kernel<256, 1, 2>;
+  if (shape == 9 && adj == 3) return sssp_lane_kernel<256, 1, 4>;
   if (shape == 3 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 5>;
   if (shape == 4 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 5>;
   if (shape == 5 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 6>;

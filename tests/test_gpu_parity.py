@@ -140,6 +140,10 @@ LARGE_VARIANTS = {
                                       "sssp_lane_kernel<256,npn1>"),
     "lane_npn2_external_order_flag": ({"QDTA_BF_SHAPE": "7", "QDTA_SMQ_OUT": "0"}, "sssp_lane_kernel<256,npn2>"),
     "lane_shape_ell16": ({"QDTA_BF_SHAPE": "6", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
+    "lane_chain2": ({"QDTA_BF_SHAPE": "8"}, "sssp_lane_kernel<256,npn1,chain2>"),
+    "lane_chain4": ({"QDTA_BF_SHAPE": "9"}, "sssp_lane_kernel<256,npn1,chain4>"),
+    "lane_chain4_without_parent_skip": ({"QDTA_BF_SHAPE": "9", "QDTA_NO_PARENT_SKIP": "1"},
+                                        "sssp_lane_kernel<256,npn1,chain4>"),
     "global_queues": ({"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "sssp_ilp_kernel<512>"),
     "cell": ({"QDTA_SSSP": "cell"}, "sssp_cell_kernel"),
 }
@@ -166,7 +170,8 @@ def test_sssp_large_graph_variants(mid, variant, direction, monkeypatch):
 
 
 @pytest.mark.parametrize("shape,kernel", [("1", "sssp_smq_kernel<256,rank32,2,true>"),
-                                          ("6", "sssp_lane_kernel<256,npn1>"), ("7", "sssp_lane_kernel<256,npn2>")])
+                                          ("6", "sssp_lane_kernel<256,npn1>"), ("7", "sssp_lane_kernel<256,npn2>"),
+                                          ("9", "sssp_lane_kernel<256,npn1,chain4>")])
 def test_sssp_rank_keys_on_a_graph_with_one_way_links(shape, kernel, monkeypatch):
     """Degree <= 4 but 3 % of links lose their reverse: the rank-keyed
     adjacency runs without the parent-slot skip; bit-exact both ways."""
@@ -189,7 +194,7 @@ def test_sssp_rank_keys_on_a_graph_with_one_way_links(shape, kernel, monkeypatch
         np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-@pytest.mark.parametrize("adj,shape", [("2", "1"), ("3", "1"), ("3", "6"), ("3", "7")])
+@pytest.mark.parametrize("adj,shape", [("2", "1"), ("3", "1"), ("3", "6"), ("3", "7"), ("3", "8"), ("3", "9")])
 def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, shape, monkeypatch):
     """Link times of 5e6..1e7 quanta push distances past 2^29: the 32-bit-key
     batch flags it and the 64-bit redo gives the oracle's bits."""
@@ -208,7 +213,7 @@ def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, shape, monkeypatch)
         np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-@pytest.mark.parametrize("shape", ["1", "6", "7"])
+@pytest.mark.parametrize("shape", ["1", "6", "7", "9"])
 def test_sssp_redo_touches_only_the_roots_that_overflowed(mid, shape, monkeypatch):
     """Links entering three nodes cost 2^30: destination trees rooted there
     pass 2^29 (so the batch is redone with 64-bit keys), the other roots'
