@@ -26,6 +26,7 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -66,7 +67,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="day_metro",
                     choices=["day_metro", "day_small", "sssp_metro", "batch32", "adjoint_metro", "interval_metro",
-                             "sta_vs_qdta"])
+                             "sta_vs_qdta", "gap_peak", "floor_small"])
     ap.add_argument("--roots", type=int, default=2000, help="sssp_metro: destination roots per batch")
     ap.add_argument("--intervals", default=None,
                     help="a:b -- run only intervals a..b-1 of the day (profiling captures; not a bench line)")
@@ -608,8 +609,81 @@ def sta_vs_qdta(args):
                       "step": args.step, "stop": args.stop, "objective": args.objective}), flush=True)
 
 
+def gap_peak(args):
+    """The relative duality gap target on the metro day's busiest hour: the
+    day runs under the paper's stop rule up to the hour, and the hour's four
+    intervals are then solved from that residual demand with the relative-gap
+    stop (tolerance 1e-4, at most --max-iter FW steps each), on the graph
+    schedule.  Reports per interval the FW steps, whether 1e-4 was reached,
+    the gap at the end and the seconds."""
+    import torch
+    from paper_2104_12911_gb300 import qdta as Q, synth
+    inst = synth.config_day(seed=2)
+    net = inst.net
+    dev = torch.device("cuda", 0)
+    g = Q.Graph(net)
+    if not args.no_tune:
+        Q.qdta_autotune(g, torch.from_numpy(net.fftime_q.astype(np.int32)).to(dev),
+                        torch.from_numpy(inst.zones.astype(np.int32)).to(dev), reps=2)
+    totals = [d.amount_fx.sum() for d in inst.demand]
+    first = max(0, int(np.argmax(totals)) - 1)
+    zones = torch.from_numpy(inst.zones.astype(np.int32)).to(dev)
+    dd = [Q.DeviceOD(zones, *(torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+                              for a in (d.root_idx, d.src, d.amount_fx))) for d in inst.demand]
+    p0 = Q.make_params(args.step, "paper_obj", 200, 1e-4, schedule="graph")
+    _, _, _, res = Q.qdta_run_day(g, dd[:first], 900.0, p0, resid_capacity=64 << 20)
+    rin = Q.DeviceOD(zones, res[0].clone(), res[1].clone(), res[2].clone())
+    p1 = Q.make_params(args.step, "rel_gap", args.max_iter, 1e-4, schedule="graph")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st, rc, _ = Q.qdta_run_day(g, dd[first:first + 4], 900.0, p1, resid_in=rin)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    rows = [{"interval": first + i, "trips_original": round(float(totals[first + i]) / 2**32),
+             "items": s["n_items"], "fw_steps": s["iterations"], "converged_1e-4": bool(s["converged"]),
+             "dual_gap_end": s["dual_gap"]} for i, s in enumerate(st)]
+    print(json.dumps({"metric": "FW steps to relative duality gap 1e-4, metro day's busiest hour",
+                      "workload": f"500x500 grid, 2000 zones, 19M trips/day: intervals {first}..{first + 3} "
+                                  f"resumed from the residual of intervals 0..{first - 1} (paper's rule)",
+                      "stop": "relative duality gap <= 1e-4 (a negative gap does not stop)",
+                      "max_iter": args.max_iter, "step": args.step, "seconds_for_the_hour": secs,
+                      "intervals": rows, "sssp_kernel": Q.qdta_sssp_kernel_name(g)}), flush=True)
+
+
+def floor_small(args):
+    """How low the relative duality gap goes on the 32 x 32 network (64
+    zones, 20k trips, one 15-minute interval) with sweep8 steps, at the 0.01 s
+    time quantum and at a 100x finer one: the gap after K FW steps."""
+    import torch
+    from paper_2104_12911_gb300 import qdta as Q, synth
+    inst = synth.config_small(0)
+    dem = inst.demand[0]
+    out = {}
+    for quantum in (0.01, 0.0001):
+        net = dataclasses.replace(inst.net, quantum_s=quantum,
+                                  fftime_q=np.maximum(1, np.rint(inst.net.fftime_q * (0.01 / quantum))).astype(np.int32))
+        g = Q.Graph(net)
+        od = Q.DeviceOD.of(dem)
+        row = {}
+        for K in (10, 20, 40, 80, 160, 320, 640, 1280):
+            _, st, _, _ = Q.qdta_assign_interval(g, od, 900.0, Q.make_params(args.step, "none", K, schedule="graph"))
+            row[K] = st["dual_gap"]
+        _, st, rc, _ = Q.qdta_assign_interval(g, od, 900.0, Q.make_params(args.step, "rel_gap", 5000, 1e-4,
+                                                                          schedule="graph"))
+        out[f"quantum_{quantum}s"] = {"dual_gap_after_K_steps": row, "steps_to_1e-4": st["iterations"],
+                                      "converged": bool(st["converged"])}
+    print(json.dumps({"metric": "relative duality gap floor, 32x32 network (config 1 inputs), one interval",
+                      "step": args.step, "results": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "gap_peak":
+        gap_peak(args)
+        return
+    if args.workload == "floor_small":
+        floor_small(args)
+        return
     if args.workload == "sssp_metro":
         sssp_only(args)
         return
