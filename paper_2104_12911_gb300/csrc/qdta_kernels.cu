@@ -981,7 +981,12 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
               ++my_relax;
               const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
               if (cand >= DMAX) {
-                atomicOr(status, ADJ == 3 ? ST_K32 : ST_OVERFLOW);
+                // 64-bit keys: a distance beyond 2^61 is an error.  32-bit
+                // keys: the offer is dropped; a node whose shortest distance
+                // is below 2^29 gets all its offers below 2^29 (so its key,
+                // tie rule included, is exact), and one at or beyond 2^29 is
+                // left unreached, which the output pass flags for the redo
+                if (ADJ != 3) atomicOr(status, ST_OVERFLOW);
               } else {
                 const Key key = (Key)((cand << LB) | (unsigned long long)(unsigned)ent[j].x);
                 if (key < tk[j]) {
@@ -1054,6 +1059,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
     // output: parent link (and distance) per external node id, keys reset
     int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
+    bool unreached = false;  // 32-bit keys: a node left at KINF asks for the 64-bit redo
     if (out_mode != 0 && node_ext) {
       // internal order: coalesced key reads and resets, parent writes through
       // the inverse permutation (runs of consecutive ids inside a cell); on
@@ -1074,6 +1080,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
           if (v[k] < 0) continue;
           const int u = u0 + k * THREADS;
           state[u] = KINF;
+          unreached |= key[k] == KINF;
           const Key lk = key[k] & NOLINK;
           prow[v[k]] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
           if (drow) drow[v[k]] = key[k] == KINF ? LLONG_MAX : (long long)(key[k] >> LB);
@@ -1084,6 +1091,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
       for (int v = threadIdx.x; v < V; v += blockDim.x) {
         const int u = node_int ? node_int[v] : v;
         const Key key = __ldcg(&state[u]);
+        unreached |= key == KINF;
         const Key lk = key & NOLINK;
         prow[v] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
         if (drow) drow[v] = key == KINF ? LLONG_MAX : (long long)(key >> LB);
@@ -1091,6 +1099,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
       __syncthreads();
       for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
     }
+    if (ADJ == 3 && unreached) atomicOr(status, ST_K32);
     __syncthreads();
   }
 }
@@ -1188,10 +1197,7 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
               if (sx[s] < 0) continue;
               ++my_relax;
               const unsigned cand = dw + st[s];
-              if (cand >= DMAX) {
-                atomicOr(status, ST_K32);
-                continue;
-              }
+              if (cand >= DMAX) continue;  // see the output pass
               const unsigned key = (cand << 3) | (unsigned)(sx[s] & 7);
               if (key < tk[s]) {
                 const int y = sx[s] >> 3;
@@ -1263,10 +1269,7 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
               if (sx[n][s] < 0) continue;
               ++my_relax;
               const unsigned cand = dw[n] + st[n][s];
-              if (cand >= DMAX) {
-                atomicOr(status, ST_K32);
-                continue;
-              }
+              if (cand >= DMAX) continue;  // see the output pass
               const unsigned key = (cand << 3) | (unsigned)(sx[n][s] & 7);
               if (key < tk[n][s]) {
                 const int y = sx[n][s] >> 3;
@@ -1299,9 +1302,13 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
     if (round > max_rounds)  // an early exit can leave marks behind
       for (int i = threadIdx.x; i < W; i += THREADS) bm[i] = 0u;
     // output in internal order: coalesced key reads and resets, parents
-    // (and distances) written through the inverse permutation
+    // (and distances) written through the inverse permutation.  Offers of
+    // 2^29 or more were dropped: nodes whose shortest distance is below 2^29
+    // have exact keys, and a node left unreached (distance at or beyond 2^29,
+    // or no path) sets ST_K32 so the batch is redone with 64-bit keys.
     int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
+    bool unreached = false;
     for (int u0 = threadIdx.x; u0 < V; u0 += 4 * THREADS) {
       unsigned key[4];
       int v[4];
@@ -1316,11 +1323,13 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
         if (v[k] < 0) continue;
         const int u = u0 + k * THREADS;
         state[u] = KINF;
+        unreached |= key[k] == KINF;
         const unsigned lk = key[k] & NOLINK;
         prow[v[k]] = lk == NOLINK ? -1 : __ldg(&rank_link[4 * u + (int)lk]);
         if (drow) drow[v[k]] = key[k] == KINF ? LLONG_MAX : (long long)(key[k] >> 3);
       }
     }
+    if (unreached) atomicOr(status, ST_K32);
     __syncthreads();
   }
 }
