@@ -301,7 +301,20 @@ def day_oracle_seconds(day_work, n_roots, t_root, t_sweep):
 # compute the same iterates bit for bit, so these counts are the oracle's too;
 # they were recorded from the bench line's "per_interval" entry.  The
 # reference arm scales its timed sample by them.
-METRO_DAY_WORK = None
+METRO_DAY_WORK = {
+    "aon": [2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 3, 3, 14, 30, 61, 94, 112, 92, 103,
+             96, 97, 77, 56, 61, 75, 63, 55, 48, 37, 52, 55, 41, 51, 41, 46, 3, 29, 27, 3, 3, 14, 13, 13, 16, 47, 47,
+             27, 3, 8, 32, 61, 71, 104, 126, 143, 114, 92, 93, 47, 51, 63, 45, 49, 56, 58, 55, 59, 45, 42, 51, 3, 24,
+             33, 36, 4, 46, 43, 33, 43, 34, 11, 35, 11],
+    "fw": [0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 12, 28, 59, 92, 110, 90, 101,
+             94, 95, 75, 54, 59, 73, 61, 53, 46, 35, 50, 53, 39, 49, 39, 44, 1, 27, 25, 1, 1, 12, 11, 11, 14, 45, 45,
+             25, 1, 6, 30, 59, 69, 102, 124, 141, 112, 90, 91, 45, 49, 61, 43, 47, 54, 56, 53, 57, 43, 40, 49, 1, 22,
+             31, 34, 2, 44, 41, 31, 41, 32, 9, 33, 9],
+    "sweeps": [1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 6, 10, 65, 145, 300, 465, 555,
+             455, 510, 475, 480, 380, 275, 300, 370, 310, 266, 235, 176, 255, 266, 196, 246, 196, 225, 6, 136, 126,
+             6, 6, 65, 60, 60, 75, 230, 230, 130, 10, 35, 155, 300, 350, 515, 625, 710, 565, 455, 460, 230, 246, 310,
+             220, 240, 271, 281, 266, 286, 216, 205, 246, 6, 111, 156, 171, 15, 221, 210, 156, 206, 161, 50, 170, 50],
+}
 
 
 def reference_arm(args, inst, cfg):
