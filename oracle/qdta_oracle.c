@@ -941,21 +941,31 @@ static int cmp_item3(const void *a, const void *b) {
   const item3 *x = (const item3 *)a, *y = (const item3 *)b;
   if (x->root != y->root) return x->root < y->root ? -1 : 1;
   if (x->src != y->src) return x->src < y->src ? -1 : 1;
-  if (x->carry != y->carry) return x->carry < y->carry ? -1 : 1;
+  if ((x->carry > 0) != (y->carry > 0)) return x->carry > 0 ? 1 : -1;
   return 0;
 }
 
-/* merge an item list by (root, src, carried time), summing amounts (trips at
- * the same node with the same time already travelled continue identically);
- * returns the count */
+/* merge an item list by (root, src) as the paper's residual demand d_{s,q}
+ * is kept, summing amounts; trips that carry a partial link (carry > 0, R17)
+ * merge apart from those waiting at the node, and a merged carried item takes
+ * the amount-weighted mean carried time, floor(sum amt * carry / sum amt),
+ * computed exactly in 128-bit integers; returns the count */
 static int64_t merge_items(item3 *buf, int64_t n) {
   qsort(buf, (size_t)n, sizeof(item3), cmp_item3);
   int64_t m = 0;
+  i128 tsum = 0;
   for (int64_t k = 0; k < n; k++) {
-    if (m > 0 && buf[m - 1].root == buf[k].root && buf[m - 1].src == buf[k].src && buf[m - 1].carry == buf[k].carry)
+    const int carried = buf[k].carry > 0;
+    if (m > 0 && buf[m - 1].root == buf[k].root && buf[m - 1].src == buf[k].src && (buf[m - 1].carry > 0) == carried) {
       buf[m - 1].amt += buf[k].amt;
-    else buf[m++] = buf[k];
+    } else {
+      if (m > 0 && buf[m - 1].carry > 0) buf[m - 1].carry = buf[m - 1].amt > 0 ? (int64_t)(tsum / buf[m - 1].amt) : 1;
+      buf[m++] = buf[k];
+      tsum = 0;
+    }
+    if (carried) tsum += (i128)buf[k].amt * buf[k].carry;
   }
+  if (m > 0 && buf[m - 1].carry > 0) buf[m - 1].carry = buf[m - 1].amt > 0 ? (int64_t)(tsum / buf[m - 1].amt) : 1;
   return m;
 }
 
@@ -1179,6 +1189,9 @@ int32_t or_replay(const or_graph *g, const or_od *od, double dt_s, const or_para
  *     its elapsed time starts at minus that carry, so a link longer than dt
  *     is crossed over several intervals.  Time (quanta), not a fraction of
  *     the link, is carried: the trip is rerouted from u in the next interval
- *     and may leave u by another link.  Residual items merge by (root, node,
- *     carried time).
+ *     and may leave u by another link.  Residual demand stays keyed by
+ *     (root, node) as the paper's d_{s,q}: carried trips merge apart from
+ *     trips waiting at the node, with the amount-weighted mean carried time
+ *     (exact merging by carried time grows the items about fourfold per
+ *     interval on short intervals, without bound).
  */

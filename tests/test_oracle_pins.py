@@ -714,6 +714,36 @@ def test_carried_truncation_crosses_a_long_link_over_several_intervals():
     np.testing.assert_array_equal(np.asarray(f).reshape(4, 3), [[1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, 0]])
 
 
+def test_carried_trips_merge_with_their_mean_carried_time():
+    """Reading R17's merge: trips waiting at the same node for the same zone
+    are one residual item (the paper's d_{s,q}); trips carrying a partial
+    link merge apart from those at the node, with the amount-weighted mean
+    carried time.  Chain of 1000 s links, 300 s intervals: trip A (1 trip)
+    leaves node 0 in interval 0, B (3 trips) in interval 1.  After interval 1
+    A carries 600 s and B 300 s beyond node 0, so interval 2 starts one item
+    of 4 trips carrying (600 + 3 * 300) / 4 = 375 s.  From there, by hand:
+    the group is on link 0 until it reaches node 1 at 25 s into interval 4,
+    on link 1 until 125 s into interval 7, and arrives 225 s into interval 10."""
+    net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
+    g = oracle.OracleGraph(net)
+    zones = np.array([3], np.int32)
+
+    def trips(n):
+        return synth.Demand(roots=zones, root_idx=np.array([0], np.int32), src=np.array([0], np.int32),
+                            amount_fx=np.array([n << 32], np.int64))
+    empty = synth.Demand(roots=zones, root_idx=np.zeros(0, np.int32), src=np.zeros(0, np.int32),
+                         amount_fx=np.zeros(0, np.int64))
+    N = 12
+    f, st, nit, rn, rc = oracle.run_day(g, zones, [trips(1), trips(3)] + [empty] * (N - 2), 300.0,
+                                        oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0,
+                                                           truncation=oracle.TRUNC_CARRY))
+    assert rc >= 0
+    want = [[1, 0, 0], [4, 0, 0], [4, 0, 0], [4, 0, 0], [4, 4, 0], [0, 4, 0], [0, 4, 0], [0, 4, 4],
+            [0, 0, 4], [0, 0, 4], [0, 0, 4], [0, 0, 0]]
+    np.testing.assert_array_equal(np.asarray(f).reshape(N, 3), want)
+    assert list(nit) == [1, 2] + [1] * 9 + [0] and rn == 0
+
+
 def test_carried_truncation_stop_node_and_carried_time():
     """One walk on the same chain from node 0 with a carried time c (time
     already travelled beyond node 0): after an interval of 300 s the trip is
