@@ -407,6 +407,7 @@ def sssp_only(args):
                       "rounds_per_root": p["sssp_rounds"] / max(p["sssp_roots"], 1),
                       "relax_per_link": p["sssp_relaxations"] / max(p["sssp_roots"], 1) / L,
                       "cell_activations_per_root": p["sssp_cell_activations"] / max(p["sssp_roots"], 1),
+                      "redo_batches_64bit": p["sssp_redo_batches"], "batches": p["sssp_launches"],
                       "autotune_ms_per_batch": tune}),
           flush=True)
 

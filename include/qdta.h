@@ -78,9 +78,9 @@ extern "C" {
  *    would end after dt waits at that link's tail u, carrying the time
  *    dt - elapsed(u) it already travelled beyond u; in the next interval its
  *    elapsed time starts at minus that carry, so a link longer than dt is
- *    crossed over several intervals.  Residual items then merge by (root,
- *    node, carried time); carried times must stay below 2^(64 - ceil(log2(
- *    zones x nodes))) quanta (QDTA_EOVERFLOW otherwise). */
+ *    crossed over several intervals.  Residual demand stays keyed by
+ *    (root, node): carried trips merge apart from those waiting at the node,
+ *    with the amount-weighted mean carried time (floor, exact integers). */
 #define QDTA_TRUNC_NODE 0
 #define QDTA_TRUNC_CARRY 1
 

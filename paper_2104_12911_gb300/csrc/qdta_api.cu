@@ -929,7 +929,7 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
     const bool ell_ok = g->d.max_deg[direction] <= 4 && g->d.node_int != nullptr;
     const bool rank_ok = ell_ok && g->d.rank_tgt[direction] != nullptr;
     bool any_smq = false;
-    for (int shape = 0; shape < 10; ++shape) {
+    for (int shape = 0; shape < 8; ++shape) {
       if (!sssp_smq_shape_fits(g->d.V, shape) || getenv("QDTA_BF_NOSMQ")) continue;
       if (shape == 2 && sssp_smq_shape_fits(g->d.V, 0)) continue;  // same block as shape 0, fewer marks
       any_smq = true;
@@ -1542,8 +1542,8 @@ struct Day {
   long long cap_items;
   int *it_root, *it_src;
   long long *it_amt;
-  long long *it_carry;         // carried times of the items (carried-time table in use), else NULL
-  CarryHash ch;                // carried-time table (mask 0: none)
+  long long *it_carry;         // carried times of the items (carried trips in play), else NULL
+  CarryAcc ca;                 // carried accumulator (amt NULL: none)
   int trunc;                   // QDTA_TRUNC_*
   long long *n_items_dev;
   int *flag, *active, *root_slot, *n_active;
@@ -1559,9 +1559,9 @@ struct Day {
 static int day_merge(Day &D) {
   qdta_graph *g = D.S.g;
   cudaStream_t s = D.S.s;
-  launch_scatter_orig(g->d, D.S.ctl, D.tab, D.max_orig, D.dense, s, D.ch, g->status);
+  launch_scatter_orig(g->d, D.S.ctl, D.tab, D.max_orig, D.dense, s, D.ca, g->status);
   launch_compact(g->d, D.Z, D.dense, D.blk_count, D.blk_off, D.cap_items, D.it_root, D.it_src, D.it_amt,
-                 D.n_items_dev, g->status, s, D.it_carry, D.ch);
+                 D.n_items_dev, g->status, s, D.it_carry, D.ca);
   launch_active_roots(D.Z, D.n_items_dev, D.cap_items, D.it_root, D.zones, D.flag, D.active, D.root_slot,
                       D.n_active, s);
   return QDTA_OK;
@@ -1598,7 +1598,7 @@ static int day_res_body(Day &D, unsigned long long h, int use_cond) {
               S.parent_stride, nullptr, s, &S.ctl->res_skip, real_batch));
   launch_residual(g->d, D.hq_fin, S.parent, &S.ctl->res_slot, S.parent_stride, D.root_slot, D.zones,
                   D.n_items_dev, D.cap_items, D.it_root, D.it_src, D.it_amt, &S.ctl->w_cur, S.dt_q, D.h_fx,
-                  D.dense, g->status, s, D.it_carry, D.trunc, D.ch);
+                  D.dense, g->status, s, D.it_carry, D.trunc, D.ca);
   launch_res_next(S.ctl, h, use_cond, s);
   return QDTA_OK;
 }
@@ -1730,26 +1730,16 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   D.max_orig = max_orig;
   D.cap_items = dense_n < (64ll << 20) ? dense_n : (64ll << 20);
   D.trunc = p->truncation;
-  D.ch = CarryHash{};
+  D.ca = CarryAcc{};
   D.it_carry = nullptr;
   if (any_carry) {
-    // key = ((root * V + node) << tau_bits) | carried time; the table holds
-    // up to half its slots (at most 32M entries) and items get as many slots
-    int dbits = 1;
-    while ((1ll << dbits) < dense_n) ++dbits;
-    D.ch.tau_bits = 64 - dbits;
-    if (D.ch.tau_bits < 24)
-      return fail(QDTA_EINVAL, "carried truncation: zones x nodes = %lld leaves fewer than 24 bits of carried time",
-                  dense_n);
-    const long long want = std::min<long long>(std::max<long long>(dense_n, 1ll << 16), 32ll << 20);
-    long long H = 1;
-    while (H < 2 * want) H <<= 1;
-    RC(ws_get(g, "day.carry_keys", (size_t)H, &D.ch.keys));
-    RC(ws_get(g, "day.carry_vals", (size_t)H, &D.ch.vals));
-    D.ch.mask = (unsigned long long)(H - 1);
-    CK(cudaMemsetAsync(D.ch.keys, 0xFF, (size_t)H * 8, s));
-    CK(cudaMemsetAsync(D.ch.vals, 0, (size_t)H * 8, s));
-    D.cap_items += H / 2;
+    // carried trips: a second (root, node) accumulator of amounts and exact
+    // 128-bit sums of amount x carried time; items get room for both parts
+    RC(ws_get(g, "day.carry_amt", (size_t)dense_n, &D.ca.amt));
+    RC(ws_get(g, "day.carry_tsum", (size_t)dense_n * 2, &D.ca.tsum));
+    CK(cudaMemsetAsync(D.ca.amt, 0, (size_t)dense_n * 8, s));
+    CK(cudaMemsetAsync(D.ca.tsum, 0, (size_t)dense_n * 16, s));
+    D.cap_items *= 2;
     RC(ws_get(g, "day.it_carry", (size_t)D.cap_items, &D.it_carry));
   }
   RC(ws_get(g, "day.it_root", (size_t)D.cap_items, &D.it_root));
@@ -1823,7 +1813,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   if (resid_in && resid_in->n_items > 0)
     launch_scatter_items(g->d, resid_in->n_items, resid_in->root_idx, resid_in->src,
                          (const long long *)resid_in->amount_fx, D.dense, s,
-                         (const long long *)resid_in->carry_q, D.ch, g->status);
+                         (const long long *)resid_in->carry_q, D.ca, g->status);
   // day counter lives in the solver's controller
   int dayinit[3] = {0, N, 1};
   CK(cudaMemcpyAsync(&S.ctl->day_i, dayinit, sizeof dayinit, cudaMemcpyHostToDevice, s));
@@ -1845,16 +1835,16 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   if (resid_out) {
     launch_compact(g->d, Z, D.dense, D.blk_count, D.blk_off, resid_out->capacity, resid_out->root_idx,
                    resid_out->src, (long long *)resid_out->amount_fx, D.n_items_dev, g->status, s,
-                   (long long *)resid_out->carry_q, D.ch);
+                   (long long *)resid_out->carry_q, D.ca);
     long long cnt = 0;
     CK(cudaMemcpyAsync(&cnt, D.n_items_dev, 8, cudaMemcpyDeviceToHost, s));
     RC(status_check(g, s));
     resid_out->count = cnt;
   } else {
     CK(cudaMemsetAsync(D.dense, 0, (size_t)dense_n * 8, s));
-    if (D.ch.mask) {
-      CK(cudaMemsetAsync(D.ch.keys, 0xFF, (size_t)(D.ch.mask + 1) * 8, s));
-      CK(cudaMemsetAsync(D.ch.vals, 0, (size_t)(D.ch.mask + 1) * 8, s));
+    if (D.ca.amt) {
+      CK(cudaMemsetAsync(D.ca.amt, 0, (size_t)dense_n * 8, s));
+      CK(cudaMemsetAsync(D.ca.tsum, 0, (size_t)dense_n * 16, s));
     }
   }
   (void)worst;

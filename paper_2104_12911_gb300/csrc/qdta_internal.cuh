@@ -366,15 +366,14 @@ long long launch_count();
 void launch_set_cond(const Ctl *ctl, int which, unsigned long long cond, cudaStream_t s);
 int sssp_blocks_per_sm(bool use_smem, int V);
 
-// Residual items that carry a partial link (QDTA_TRUNC_CARRY) merge by
-// (root, node, carried time) in an open-addressed table: key = ((root * V +
-// node) << tau_bits) | carried time, ~0 when empty; amounts summed with
-// integer atomics.  mask = 0: no table (QDTA_TRUNC_NODE).
-struct CarryHash {
-  unsigned long long *keys = nullptr;  // [mask + 1]
-  long long *vals = nullptr;           // [mask + 1]
-  unsigned long long mask = 0;
-  int tau_bits = 0;
+// Residual trips that carry a partial link (QDTA_TRUNC_CARRY) merge per
+// (root, node), apart from the trips waiting at the node: their amount and
+// the exact sum of amount x carried time (two 64-bit words, low then high)
+// per entry root * V + node; the merged item carries the floor of the mean.
+// amt == NULL: no carried trips (QDTA_TRUNC_NODE).
+struct CarryAcc {
+  unsigned long long *amt = nullptr;   // [R * V]
+  unsigned long long *tsum = nullptr;  // [2 * R * V]
 };
 
 void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStream_t s);
@@ -384,15 +383,15 @@ void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const
                  const long long *n_items_dev, const int *root_idx, const int *src,
                  const long long *amount, long long dt_q, unsigned long long *flow_fx, int *stop_out,
                  unsigned *status, cudaStream_t s, const long long *carry = nullptr);
-// trunc 1 (carry): a trip stopping inside a link goes to the table `ch` with
-// its carried time; trips stopping at a node go to `dense`
+// trunc 1 (carry): a trip stopping inside a link goes to the carried
+// accumulator `ca` with its carried time; trips stopping at a node go to `dense`
 void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *parent,
                      const int *parent_slot_dev, long long slot_stride, const int *root_slot,
                      const int *roots, const long long *n_items_dev, long long n_items_cap,
                      const int *root_idx, const int *src, const long long *amount,
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
                      unsigned long long *dense, unsigned *status, cudaStream_t s,
-                     const long long *carry = nullptr, int trunc = 0, CarryHash ch = CarryHash{});
+                     const long long *carry = nullptr, int trunc = 0, CarryAcc ca = CarryAcc{});
 
 // marginal = 1: the system optimum's marginal costs instead of link times
 void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,
@@ -424,7 +423,7 @@ void launch_store_interval(const GraphDev &g, const Ctl *ctl, const unsigned lon
 void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s);
 struct OrigTable { const int *root_idx; const int *src; const long long *amount; long long n; const long long *carry; };
 void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab, long long max_n,
-                         unsigned long long *dense, cudaStream_t s, CarryHash ch = CarryHash{},
+                         unsigned long long *dense, cudaStream_t s, CarryAcc ca = CarryAcc{},
                          unsigned *status = nullptr);
 void launch_ctl_begin(Ctl *ctl, unsigned long long cond_fw, int use_cond, cudaStream_t s);
 void launch_ctl_step(Ctl *ctl, unsigned long long cond_ls, int use_cond, cudaStream_t s);
@@ -432,18 +431,20 @@ void launch_ctl_end(Ctl *ctl, unsigned long long cond_fw, int use_cond, cudaStre
 void launch_tape_record(const GraphDev &g, const Ctl *ctl, const int *q, const double *f,
                         int *tape_q, double *tape_alpha, double *tape_f, int cap, cudaStream_t s);
 
-// items with carry > 0 go to the table `ch` (which must exist then)
+// items with carry > 0 go to the carried accumulator `ca` (which must exist then)
 void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, const int *src,
                           const long long *amount, unsigned long long *dense, cudaStream_t s,
-                          const long long *carry = nullptr, CarryHash ch = CarryHash{},
+                          const long long *carry = nullptr, CarryAcc ca = CarryAcc{},
                           unsigned *status = nullptr);
 // dense (root, node) accumulator -> items in (root, node) order, then (when
-// ch has a table) its entries appended in table order; carry_out (nullable)
-// receives each item's carried time.  Both sources are cleared.
+// ca.amt is set) the carried accumulator's entries appended in (root, node)
+// order with their mean carried times; carry_out (nullable) receives each
+// item's carried time (0 for the first part).  Both sources are cleared; the
+// item count never exceeds cap (ST_CAPACITY when entries were dropped).
 void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *blk_count,
                     long long *blk_off, long long cap, int *root_idx, int *src, long long *amount,
                     long long *n_out_dev, unsigned *status, cudaStream_t s, long long *carry_out = nullptr,
-                    CarryHash ch = CarryHash{});
+                    CarryAcc ca = CarryAcc{});
 void launch_active_roots(int R, const long long *n_items_dev, long long cap_items,
                          const int *root_idx, const int *zone_nodes, int *flag, int *active_roots,
                          int *root_slot, int *n_active_dev, cudaStream_t s);

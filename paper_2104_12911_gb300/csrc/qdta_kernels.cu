@@ -839,15 +839,13 @@ int sssp_group_size() {
 //      of 4 (a pass covers 320 or 384 nodes; 32-bit rank keys only)
 //   6, 7: as 1, one lane per frontier node (sssp_lane_kernel below), 1 or 2
 //      nodes per lane per pass (32-bit rank keys only; otherwise as 1)
-//   8, 9: as 6, with chained relaxation 2 or 4 hops deep
 struct SmqShape {
   int threads, bitmaps, qcap, ctas, npt;
 };
-constexpr int kSmqShapes = 10;
+constexpr int kSmqShapes = 8;
 static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 2048, 4, 4}, {512, 1, 3072, 2, 4},
                                                {256, 1, 768, 5, 4},  {256, 1, 2048, 4, 5}, {256, 1, 2048, 4, 6},
-                                               {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2},
-                                               {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 1}};
+                                               {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2}};
 
 // RELAX selects how an offer (cand, link) to neighbour y is applied:
 //   0  returning atomicMin; y is queued when the returned old distance was larger
@@ -1114,15 +1112,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
 // and carries 64-bit distances; the round structure, marks, queues, tie rule
 // (key = (distance << 3) | rank, atomicMin), overflow flag and output pass are
 // the same, so the results are the same bits.  Signature as SmqKernel.
-//
-// CHAIN > 0 (NPN 1 only): a lane whose offer lowers a neighbour's distance
-// relaxes that neighbour itself right away, up to CHAIN hops deep, instead of
-// queueing it for the next round, so the frontier can advance several hops
-// per round.  The offers stay lengths of real paths, and a node that another
-// lane lowers further is queued by that lane (its mark is unset), so the
-// distances, the keys and hence the parents are unchanged.  A neighbour
-// already marked for the next queue is not adopted.
-template <int THREADS, int NPN, int CHAIN = 0>
+template <int THREADS, int NPN>
 __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64))
 sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__restrict__ adj,
                  const int *__restrict__ roots, int R_host, const int *R_dev,
@@ -1169,120 +1159,66 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
         atomicAnd(&bm[y >> 5], ~(1u << (y & 31)));
       }
       __syncthreads();
-      if constexpr (CHAIN > 0) {
-        static_assert(NPN == 1, "chained relaxation runs one node per lane");
-        for (int base = 0; base < ncur; base += THREADS) {
-          const int i = base + (int)threadIdx.x;
-          int w = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
-          unsigned dw = 0u, prank = 8u;
-          if (w >= 0) {
-            const unsigned kw = __ldcg(&state[w]);
-            dw = kw >> 3;
-            if (skip_parent) prank = kw & NOLINK;
-          }
-          for (int depth = 0; depth <= CHAIN && w >= 0; ++depth) {
-            const int4 ra = __ldg(&rows[2 * w]), rb = __ldg(&rows[2 * w + 1]);
-            int sx[4] = {ra.x, ra.z, rb.x, rb.z};
-            const unsigned st[4] = {(unsigned)ra.y, (unsigned)ra.w, (unsigned)rb.y, (unsigned)rb.w};
-            unsigned tk[4];
+      for (int base = 0; base < ncur; base += THREADS * NPN) {
+        int w[NPN];
+        unsigned dw[NPN], prank[NPN];
+        int4 ra[NPN], rb[NPN];
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-              if (sx[s] >= 0 && (unsigned)s == prank) sx[s] = -1;  // the way back to the parent
-              tk[s] = sx[s] >= 0 ? __ldcg(&state[sx[s] >> 3]) : 0u;
-            }
-            int nw = -1;
-            unsigned ndw = 0u, nrank = 8u;
+        for (int n = 0; n < NPN; ++n) {
+          const int i = base + n * THREADS + (int)threadIdx.x;
+          w[n] = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
+        }
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-              if (sx[s] < 0) continue;
-              ++my_relax;
-              const unsigned cand = dw + st[s];
-              if (cand >= DMAX) continue;  // see the output pass
-              const unsigned key = (cand << 3) | (unsigned)(sx[s] & 7);
-              if (key < tk[s]) {
-                const int y = sx[s] >> 3;
-                atomicMin(&state[y], key);
-                if ((tk[s] >> 3) > cand) {
-                  const unsigned bit = 1u << (y & 31);
-                  if (depth < CHAIN && nw < 0 && !(bm[y >> 5] & bit)) {
-                    nw = y;  // relax y next, from the distance just offered
-                    ndw = cand;
-                    nrank = skip_parent ? (unsigned)(sx[s] & 7) : 8u;
-                  } else if (!(atomicOr(&bm[y >> 5], bit) & bit)) {
-                    const int pos = atomicAdd(&s_cnt[c], 1);
-                    if (pos < qcap) snxt[pos] = y;
-                    else gnxt[pos - qcap] = y;
-                  }
-                }
-              }
-            }
-            w = nw;
-            dw = ndw;
-            prank = nrank;
+        for (int n = 0; n < NPN; ++n) {
+          dw[n] = 0u;
+          prank[n] = 8u;  // no slot
+          ra[n] = make_int4(-1, 0, -1, 0);
+          rb[n] = ra[n];
+          if (w[n] >= 0) {
+            const unsigned kw = __ldcg(&state[w[n]]);
+            dw[n] = kw >> 3;
+            if (skip_parent) prank[n] = kw & NOLINK;
+            ra[n] = __ldg(&rows[2 * w[n]]);
+            rb[n] = __ldg(&rows[2 * w[n] + 1]);
           }
         }
-      } else {
-        for (int base = 0; base < ncur; base += THREADS * NPN) {
-          int w[NPN];
-          unsigned dw[NPN], prank[NPN];
-          int4 ra[NPN], rb[NPN];
-  #pragma unroll
-          for (int n = 0; n < NPN; ++n) {
-            const int i = base + n * THREADS + (int)threadIdx.x;
-            w[n] = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
-          }
-  #pragma unroll
-          for (int n = 0; n < NPN; ++n) {
-            dw[n] = 0u;
-            prank[n] = 8u;  // no slot
-            ra[n] = make_int4(-1, 0, -1, 0);
-            rb[n] = ra[n];
-            if (w[n] >= 0) {
-              const unsigned kw = __ldcg(&state[w[n]]);
-              dw[n] = kw >> 3;
-              if (skip_parent) prank[n] = kw & NOLINK;
-              ra[n] = __ldg(&rows[2 * w[n]]);
-              rb[n] = __ldg(&rows[2 * w[n] + 1]);
-            }
-          }
-          // slot s of node n: x = (neighbour << 3) | rank (-1 absent), t = link time
-          int sx[NPN][4];
-          unsigned st[NPN][4], tk[NPN][4];
-  #pragma unroll
-          for (int n = 0; n < NPN; ++n) {
-            sx[n][0] = ra[n].x; st[n][0] = (unsigned)ra[n].y;
-            sx[n][1] = ra[n].z; st[n][1] = (unsigned)ra[n].w;
-            sx[n][2] = rb[n].x; st[n][2] = (unsigned)rb[n].y;
-            sx[n][3] = rb[n].z; st[n][3] = (unsigned)rb[n].w;
-  #pragma unroll
-            for (int s = 0; s < 4; ++s)
-              if (sx[n][s] >= 0 && (unsigned)s == prank[n]) sx[n][s] = -1;  // the way back to the parent
-          }
-  #pragma unroll
-          for (int n = 0; n < NPN; ++n)
-  #pragma unroll
-            for (int s = 0; s < 4; ++s) tk[n][s] = sx[n][s] >= 0 ? __ldcg(&state[sx[n][s] >> 3]) : 0u;
-  #pragma unroll
-          for (int n = 0; n < NPN; ++n)
-  #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-              if (sx[n][s] < 0) continue;
-              ++my_relax;
-              const unsigned cand = dw[n] + st[n][s];
-              if (cand >= DMAX) continue;  // see the output pass
-              const unsigned key = (cand << 3) | (unsigned)(sx[n][s] & 7);
-              if (key < tk[n][s]) {
-                const int y = sx[n][s] >> 3;
-                atomicMin(&state[y], key);  // result unused: no wait on the reply
-                const unsigned bit = 1u << (y & 31);
-                if ((tk[n][s] >> 3) > cand && !(atomicOr(&bm[y >> 5], bit) & bit)) {
-                  const int pos = atomicAdd(&s_cnt[c], 1);
-                  if (pos < qcap) snxt[pos] = y;
-                  else gnxt[pos - qcap] = y;
-                }
+        // slot s of node n: x = (neighbour << 3) | rank (-1 absent), t = link time
+        int sx[NPN][4];
+        unsigned st[NPN][4], tk[NPN][4];
+#pragma unroll
+        for (int n = 0; n < NPN; ++n) {
+          sx[n][0] = ra[n].x; st[n][0] = (unsigned)ra[n].y;
+          sx[n][1] = ra[n].z; st[n][1] = (unsigned)ra[n].w;
+          sx[n][2] = rb[n].x; st[n][2] = (unsigned)rb[n].y;
+          sx[n][3] = rb[n].z; st[n][3] = (unsigned)rb[n].w;
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+            if (sx[n][s] >= 0 && (unsigned)s == prank[n]) sx[n][s] = -1;  // the way back to the parent
+        }
+#pragma unroll
+        for (int n = 0; n < NPN; ++n)
+#pragma unroll
+          for (int s = 0; s < 4; ++s) tk[n][s] = sx[n][s] >= 0 ? __ldcg(&state[sx[n][s] >> 3]) : 0u;
+#pragma unroll
+        for (int n = 0; n < NPN; ++n)
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            if (sx[n][s] < 0) continue;
+            ++my_relax;
+            const unsigned cand = dw[n] + st[n][s];
+            if (cand >= DMAX) continue;  // see the output pass
+            const unsigned key = (cand << 3) | (unsigned)(sx[n][s] & 7);
+            if (key < tk[n][s]) {
+              const int y = sx[n][s] >> 3;
+              atomicMin(&state[y], key);  // result unused: no wait on the reply
+              const unsigned bit = 1u << (y & 31);
+              if ((tk[n][s] >> 3) > cand && !(atomicOr(&bm[y >> 5], bit) & bit)) {
+                const int pos = atomicAdd(&s_cnt[c], 1);
+                if (pos < qcap) snxt[pos] = y;
+                else gnxt[pos - qcap] = y;
               }
             }
-        }
+          }
       }
       __syncthreads();
       ncur = s_cnt[c];
@@ -1374,8 +1310,7 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
           for (int r = 0; r < 4; ++r)
             v.push_back(sh >= 6 && e == 3
                             ? "sssp_lane_kernel<" + std::to_string(kSmqShape[sh].threads) + ",npn" +
-                                  std::to_string(kSmqShape[sh].npt) +
-                                  (sh == 8 ? ",chain2" : sh == 9 ? ",chain4" : "") + ">"
+                                  std::to_string(kSmqShape[sh].npt) + ">"
                             : "sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
                                   std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") +
                                   (sh == 3 && e == 3 ? ",5" : "") +
@@ -1445,8 +1380,6 @@ static SmqKernel smq_kernel_relax(int adj, int relax) {
 static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
   if (shape == 6 && adj == 3) return sssp_lane_kernel<256, 1>;
   if (shape == 7 && adj == 3) return sssp_lane_kernel<256, 2>;
-  if (shape == 8 && adj == 3) return sssp_lane_kernel<256, 1, 2>;
-  if (shape == 9 && adj == 3) return sssp_lane_kernel<256, 1, 4>;
   if (shape == 3 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 5>;
   if (shape == 4 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 5>;
   if (shape == 5 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 6>;
@@ -1638,36 +1571,26 @@ void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const
                                               src, amount, dt_q, flow_fx, stop_out, status, carry);
 }
 
-// one residual entry with a carried time into the table: linear probing,
-// the key claimed by compare-and-swap, amounts summed; a full table (every
-// slot probed) sets ST_CAPACITY, a carried time beyond the key's field
-// ST_OVERFLOW
-__device__ __forceinline__ unsigned long long carry_slot_hash(unsigned long long x) {
-  // the splitmix64 finalizer (Steele, Lea and Flood), as a bit mixer
-  x ^= x >> 30;
-  x *= 0xbf58476d1ce4e5b9ull;
-  x ^= x >> 27;
-  x *= 0x94d049bb133111ebull;
-  x ^= x >> 31;
-  return x;
+// unsigned 128-bit accumulation with two 64-bit atomics: the low word's carry
+// goes into the high word, so the pair holds the exact total once every add
+// has landed (all terms here are >= 0)
+__device__ __forceinline__ void add_u128(unsigned long long *p, u128 v) {
+  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+  const unsigned long long old = atomicAdd(p, lo);
+  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi | carry) atomicAdd(p + 1, hi + carry);
 }
 
-__device__ void carry_add(const CarryHash &ch, long long d, long long tau, long long amt, unsigned *status) {
-  if (ch.mask == 0ull || tau >= (1ll << ch.tau_bits)) {
-    if (status) atomicOr(status, ch.mask == 0ull ? ST_CAPACITY : ST_OVERFLOW);
+// one residual entry carrying a partial link: amount and amount x carried
+// time into entry d = root * V + node of the carried accumulator
+__device__ __forceinline__ void carry_add(const CarryAcc &ca, long long d, long long tau, long long amt,
+                                          unsigned *status) {
+  if (!ca.amt) {
+    if (status) atomicOr(status, ST_CAPACITY);
     return;
   }
-  const unsigned long long key = ((unsigned long long)d << ch.tau_bits) | (unsigned long long)tau;
-  unsigned long long h = carry_slot_hash(key) & ch.mask;
-  for (unsigned long long probe = 0; probe <= ch.mask; ++probe) {
-    const unsigned long long prev = atomicCAS(&ch.keys[h], ~0ull, key);
-    if (prev == ~0ull || prev == key) {
-      atomicAdd(reinterpret_cast<unsigned long long *>(&ch.vals[h]), (unsigned long long)amt);
-      return;
-    }
-    h = (h + 1) & ch.mask;
-  }
-  if (status) atomicOr(status, ST_CAPACITY);
+  atomicAdd(&ca.amt[d], (unsigned long long)amt);
+  add_u128(ca.tsum + 2 * d, (u128)(unsigned long long)amt * (u128)(unsigned long long)tau);
 }
 
 // Alg. 4 for one accepted AON j: the item's path on tree j is re-truncated
@@ -1682,7 +1605,7 @@ __global__ void residual_kernel(int V, const int2 *__restrict__ head_q_fin, cons
                                 const int *__restrict__ src, const long long *__restrict__ amount,
                                 const double *weight_dev, long long dt_q, unsigned long long *h_fx,
                                 unsigned long long *dense, unsigned *status, const long long *__restrict__ carry,
-                                int trunc, CarryHash ch) {
+                                int trunc, CarryAcc ca) {
   const long long n = *n_dev;
   const double w = *weight_dev;
   if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
@@ -1711,7 +1634,7 @@ __global__ void residual_kernel(int V, const int2 *__restrict__ head_q_fin, cons
       if (++steps > V) { atomicOr(status, ST_TIMEOUT); break; }
     }
     if (u != z) {
-      if (tau > 0) carry_add(ch, (long long)r * V + u, tau, amt, status);
+      if (tau > 0) carry_add(ca, (long long)r * V + u, tau, amt, status);
       else atomicAdd(&dense[(long long)r * V + u], (unsigned long long)amt);
     }
   }
@@ -1723,12 +1646,12 @@ void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *paren
                      const int *root_idx, const int *src, const long long *amount,
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
                      unsigned long long *dense, unsigned *status, cudaStream_t s, const long long *carry,
-                     int trunc, CarryHash ch) {
+                     int trunc, CarryAcc ca) {
   if (n_items_cap <= 0) return;
   COUNT_LAUNCH();
   residual_kernel<<<link_grid(g, n_items_cap), 256, 0, s>>>(
       g.V, head_q_fin, parent, parent_slot_dev, slot_stride, root_slot, roots, n_items_dev, root_idx, src, amount, weight_dev,
-      dt_q, h_fx, dense, status, carry, trunc, ch);
+      dt_q, h_fx, dense, status, carry, trunc, ca);
 }
 
 // ============================================================================
@@ -2378,22 +2301,22 @@ void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream
 
 // original demand of the current interval into the dense accumulator
 __global__ void scatter_orig_kernel(int V, const Ctl *c, const OrigTable *tab,
-                                    unsigned long long *dense, CarryHash ch, unsigned *status) {
+                                    unsigned long long *dense, CarryAcc ca, unsigned *status) {
   const OrigTable t = tab[c->day_i];
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < t.n;
        k += (long long)gridDim.x * blockDim.x) {
     const long long a = t.amount[k];
     const long long tau = t.carry ? t.carry[k] : 0;
     const long long d = (long long)t.root_idx[k] * V + t.src[k];
-    if (a && tau > 0) carry_add(ch, d, tau, a, status);
+    if (a && tau > 0) carry_add(ca, d, tau, a, status);
     else if (a) atomicAdd(&dense[d], (unsigned long long)a);
   }
 }
 
 void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab, long long max_n,
-                         unsigned long long *dense, cudaStream_t s, CarryHash ch, unsigned *status) {
+                         unsigned long long *dense, cudaStream_t s, CarryAcc ca, unsigned *status) {
   COUNT_LAUNCH();
-  scatter_orig_kernel<<<link_grid(g, max_n > 0 ? max_n : 1), 256, 0, s>>>(g.V, ctl, tab, dense, ch, status);
+  scatter_orig_kernel<<<link_grid(g, max_n > 0 ? max_n : 1), 256, 0, s>>>(g.V, ctl, tab, dense, ca, status);
 }
 
 // ============================================================================
@@ -2402,23 +2325,23 @@ void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab
 
 __global__ void scatter_items_kernel(int V, long long n, const int *root_idx, const int *src,
                                      const long long *amount, unsigned long long *dense,
-                                     const long long *carry, CarryHash ch, unsigned *status) {
+                                     const long long *carry, CarryAcc ca, unsigned *status) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const long long a = amount[k];
     const long long tau = carry ? carry[k] : 0;
     const long long d = (long long)root_idx[k] * V + src[k];
-    if (a && tau > 0) carry_add(ch, d, tau, a, status);
+    if (a && tau > 0) carry_add(ca, d, tau, a, status);
     else if (a) atomicAdd(&dense[d], (unsigned long long)a);
   }
 }
 
 void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, const int *src,
                           const long long *amount, unsigned long long *dense, cudaStream_t s,
-                          const long long *carry, CarryHash ch, unsigned *status) {
+                          const long long *carry, CarryAcc ca, unsigned *status) {
   if (n <= 0) return;
   COUNT_LAUNCH();
-  scatter_items_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, n, root_idx, src, amount, dense, carry, ch, status);
+  scatter_items_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, n, root_idx, src, amount, dense, carry, ca, status);
 }
 
 constexpr int COMPACT_TILE = 4096;
@@ -2439,9 +2362,12 @@ __global__ void compact_count_kernel(long long total, const unsigned long long *
 }
 
 __global__ void compact_scan_kernel(int nblk, const int *blk_count, long long *blk_off, long long cap,
-                                    long long *n_out, unsigned *status) {
-  // single block, 1024 threads: chunked exclusive scan
+                                    long long *n_out, unsigned *status, int append) {
+  // single block, 1024 threads: chunked exclusive scan; with `append` the
+  // offsets start at the count already in *n_out
   __shared__ long long s_part[1024];
+  __shared__ long long s_base;
+  if (threadIdx.x == 0) s_base = append ? *n_out : 0;
   const int per = (nblk + 1023) / 1024;
   const int b0 = threadIdx.x * per;
   long long t = 0;
@@ -2454,21 +2380,25 @@ __global__ void compact_scan_kernel(int nblk, const int *blk_count, long long *b
     s_part[threadIdx.x] += v;
     __syncthreads();
   }
-  long long run = s_part[threadIdx.x] - t;
+  long long run = s_base + s_part[threadIdx.x] - t;
   for (int i = 0; i < per; ++i) {
     if (b0 + i < nblk) { blk_off[b0 + i] = run; run += blk_count[b0 + i]; }
   }
+  __syncthreads();  // every thread has read s_base before *n_out changes
   if (threadIdx.x == 1023) {
-    long long total = s_part[1023];
+    long long total = s_base + s_part[1023];
     if (total > cap) { atomicOr(status, ST_CAPACITY); total = cap; }
     *n_out = total;
   }
 }
 
 // ordered write of the nonzero entries of each tile (root-major, node-minor)
+// tsum (nullable): the carried accumulator's sums; an item then carries
+// floor(sum amount x carried time / amount), and the sums are cleared
 __global__ void compact_write_kernel(long long total, int V, unsigned long long *dense,
                                      const long long *blk_off, long long cap, int *root_idx,
-                                     int *src, long long *amount, long long *carry_out) {
+                                     int *src, long long *amount, long long *carry_out,
+                                     unsigned long long *tsum) {
   __shared__ int s_warp[32];
   const long long base = (long long)blockIdx.x * COMPACT_TILE;
   long long out = blk_off[blockIdx.x];
@@ -2485,11 +2415,18 @@ __global__ void compact_write_kernel(long long total, int V, unsigned long long 
     for (int w = 0; w < nw; ++w) { if (w < wid) before += s_warp[w]; all += s_warp[w]; }
     if (nz) {
       const long long pos = out + before + __popc(m & ((1u << lane) - 1u));
+      long long tau = 0;
+      if (tsum) {
+        const u128 t = ((u128)tsum[2 * idx + 1] << 64) | (u128)tsum[2 * idx];
+        tau = (long long)(t / (u128)v);
+        tsum[2 * idx] = 0ull;
+        tsum[2 * idx + 1] = 0ull;
+      }
       if (pos < cap) {
         root_idx[pos] = (int)(idx / V);
         src[pos] = (int)(idx % V);
         amount[pos] = (long long)v;
-        if (carry_out) carry_out[pos] = 0;
+        if (carry_out) carry_out[pos] = tau;
       }
       dense[idx] = 0ull;
     }
@@ -2498,49 +2435,21 @@ __global__ void compact_write_kernel(long long total, int V, unsigned long long 
   }
 }
 
-// carried-time table -> items appended after the n_out the dense pass wrote
-// (positions by atomic counter: the order varies, the multiset does not);
-// every slot is cleared
-__global__ void carry_compact_kernel(CarryHash ch, int V, long long cap, int *root_idx, int *src,
-                                     long long *amount, long long *carry_out, long long *n_out,
-                                     unsigned *status) {
-  const unsigned long long fmask = (1ull << ch.tau_bits) - 1ull;
-  for (unsigned long long h = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; h <= ch.mask;
-       h += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long key = ch.keys[h];
-    if (key == ~0ull) continue;
-    const long long pos = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(n_out), 1ull);
-    const long long d = (long long)(key >> ch.tau_bits);
-    if (pos < cap) {
-      root_idx[pos] = (int)(d / V);
-      src[pos] = (int)(d % V);
-      amount[pos] = ch.vals[h];
-      if (carry_out) carry_out[pos] = (long long)(key & fmask);
-    } else {
-      atomicOr(status, ST_CAPACITY);
-    }
-    ch.keys[h] = ~0ull;
-    ch.vals[h] = 0;
-  }
-}
-
 void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *blk_count,
                     long long *blk_off, long long cap, int *root_idx, int *src, long long *amount,
                     long long *n_out_dev, unsigned *status, cudaStream_t s, long long *carry_out,
-                    CarryHash ch) {
+                    CarryAcc ca) {
   const long long total = (long long)R * g.V;
   const int nblk = cdiv(total > 0 ? total : 1, COMPACT_TILE);
-  COUNT_LAUNCH();
-  compact_count_kernel<<<nblk, 256, 0, s>>>(total, dense, blk_count);
-  COUNT_LAUNCH();
-  compact_scan_kernel<<<1, 1024, 0, s>>>(nblk, blk_count, blk_off, cap, n_out_dev, status);
-  COUNT_LAUNCH();
-  compact_write_kernel<<<nblk, 256, 0, s>>>(total, g.V, dense, blk_off, cap, root_idx, src, amount, carry_out);
-  if (ch.mask) {
-    const long long slots = (long long)ch.mask + 1;
+  for (int part = 0; part < (ca.amt ? 2 : 1); ++part) {
+    unsigned long long *src_acc = part == 0 ? dense : ca.amt;
     COUNT_LAUNCH();
-    carry_compact_kernel<<<link_grid(g, slots), 256, 0, s>>>(ch, g.V, cap, root_idx, src, amount, carry_out,
-                                                             n_out_dev, status);
+    compact_count_kernel<<<nblk, 256, 0, s>>>(total, src_acc, blk_count);
+    COUNT_LAUNCH();
+    compact_scan_kernel<<<1, 1024, 0, s>>>(nblk, blk_count, blk_off, cap, n_out_dev, status, part);
+    COUNT_LAUNCH();
+    compact_write_kernel<<<nblk, 256, 0, s>>>(total, g.V, src_acc, blk_off, cap, root_idx, src, amount, carry_out,
+                                              part == 0 ? nullptr : ca.tsum);
   }
 }
 
@@ -2550,15 +2459,6 @@ void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *bl
 // scenario metrics (Section 7.1): per interval and class, over links with flow
 // ============================================================================
 
-// unsigned 128-bit accumulation with two 64-bit atomics: the low word's carry
-// goes into the high word, so the pair holds the exact total once every add
-// has landed (all terms here are >= 0)
-__device__ __forceinline__ void add_u128(unsigned long long *p, u128 v) {
-  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
-  const unsigned long long old = atomicAdd(p, lo);
-  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-  if (hi | carry) atomicAdd(p + 1, hi + carry);
-}
 
 // acc [N][C][16] words: pairs (lo, hi) at 0 VMT (veh-m), 2 VOC, 4 delay (veh
 // x quanta), 6 congested length (m), 8 congested VMT, 10 congested VOC; 12
