@@ -22,8 +22,8 @@ enum : unsigned {
   ST_OVERFLOW = 4u,    // a distance exceeded the packed range
   ST_TIMEOUT = 8u,     // a bounded loop hit its limit
   ST_CAPACITY = 16u,   // an output buffer was too small
-  ST_K32 = 32u,        // a 32-bit-key batch left a node unreached: distance >= 2^29 or no path
-                       // (redone with 64-bit keys; not an error)
+  ST_K32 = 32u,        // a 32-bit-key batch has a node at distance >= 2^29 (offered only dropped
+                       // offers; redone with 64-bit keys; not an error)
   ST_BADARG = 64u,     // a device array argument held an invalid value
 };
 

@@ -980,11 +980,16 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
               const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
               if (cand >= DMAX) {
                 // 64-bit keys: a distance beyond 2^61 is an error.  32-bit
-                // keys: the offer is dropped; a node whose shortest distance
-                // is below 2^29 gets all its offers below 2^29 (so its key,
-                // tie rule included, is exact), and one at or beyond 2^29 is
-                // left unreached, which the output pass flags for the redo
+                // keys: the offer is dropped, and a node that had no key yet
+                // gets the sentinel KINF - 1 (above every real key).  A node
+                // whose shortest distance is below 2^29 receives all its
+                // offers below 2^29, so its key, tie rule included, is exact;
+                // on the shortest path of a node at or beyond 2^29 the first
+                // such node is offered only dropped offers and keeps the
+                // sentinel, which the output pass flags for the 64-bit redo.
+                // Nodes with no path keep KINF and need no redo.
                 if (ADJ != 3) atomicOr(status, ST_OVERFLOW);
+                else if (tk[j] == KINF) atomicMin(&state[ent[j].y], (Key)(KINF - 1));
               } else {
                 const Key key = (Key)((cand << LB) | (unsigned long long)(unsigned)ent[j].x);
                 if (key < tk[j]) {
@@ -1057,7 +1062,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
     // output: parent link (and distance) per external node id, keys reset
     int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
-    bool unreached = false;  // 32-bit keys: a node left at KINF asks for the 64-bit redo
+    bool unreached = false;  // 32-bit keys: a node left at the sentinel asks for the 64-bit redo
     if (out_mode != 0 && node_ext) {
       // internal order: coalesced key reads and resets, parent writes through
       // the inverse permutation (runs of consecutive ids inside a cell); on
@@ -1078,7 +1083,10 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
           if (v[k] < 0) continue;
           const int u = u0 + k * THREADS;
           state[u] = KINF;
-          unreached |= key[k] == KINF;
+          if (ADJ == 3 && key[k] == (Key)(KINF - 1)) {  // offered only beyond 2^29
+            unreached = true;
+            key[k] = KINF;
+          }
           const Key lk = key[k] & NOLINK;
           prow[v[k]] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
           if (drow) drow[v[k]] = key[k] == KINF ? LLONG_MAX : (long long)(key[k] >> LB);
@@ -1088,8 +1096,11 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
       // external order, then a separate coalesced reset
       for (int v = threadIdx.x; v < V; v += blockDim.x) {
         const int u = node_int ? node_int[v] : v;
-        const Key key = __ldcg(&state[u]);
-        unreached |= key == KINF;
+        Key key = __ldcg(&state[u]);
+        if (ADJ == 3 && key == (Key)(KINF - 1)) {  // offered only beyond 2^29
+          unreached = true;
+          key = KINF;
+        }
         const Key lk = key & NOLINK;
         prow[v] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
         if (drow) drow[v] = key == KINF ? LLONG_MAX : (long long)(key >> LB);
@@ -1206,7 +1217,10 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
             if (sx[n][s] < 0) continue;
             ++my_relax;
             const unsigned cand = dw[n] + st[n][s];
-            if (cand >= DMAX) continue;  // see the output pass
+            if (cand >= DMAX) {  // dropped; a node without a key gets the sentinel (see the output pass)
+              if (tk[n][s] == KINF) atomicMin(&state[sx[n][s] >> 3], KINF - 1u);
+              continue;
+            }
             const unsigned key = (cand << 3) | (unsigned)(sx[n][s] & 7);
             if (key < tk[n][s]) {
               const int y = sx[n][s] >> 3;
@@ -1240,8 +1254,9 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
     // output in internal order: coalesced key reads and resets, parents
     // (and distances) written through the inverse permutation.  Offers of
     // 2^29 or more were dropped: nodes whose shortest distance is below 2^29
-    // have exact keys, and a node left unreached (distance at or beyond 2^29,
-    // or no path) sets ST_K32 so the batch is redone with 64-bit keys.
+    // have exact keys, and a node left at the sentinel KINF - 1 (offered
+    // only beyond 2^29: distance at or beyond 2^29) sets ST_K32 so the batch
+    // is redone with 64-bit keys.
     int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
     bool unreached = false;
@@ -1259,7 +1274,10 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
         if (v[k] < 0) continue;
         const int u = u0 + k * THREADS;
         state[u] = KINF;
-        unreached |= key[k] == KINF;
+        if (key[k] == KINF - 1u) {  // offered only beyond 2^29
+          unreached = true;
+          key[k] = KINF;
+        }
         const unsigned lk = key[k] & NOLINK;
         prow[v[k]] = lk == NOLINK ? -1 : __ldg(&rank_link[4 * u + (int)lk]);
         if (drow) drow[v[k]] = key[k] == KINF ? LLONG_MAX : (long long)(key[k] >> 3);

@@ -115,7 +115,8 @@ def grid_network(n: int, seed: int, *, freeways: bool = False,
     w = rng.uniform(1.0, 2.0, u.shape[0])
     m = coo_matrix((w, (u, v)), shape=(n * n, n * n)).tocsr()
     t = minimum_spanning_tree(m).tocoo()
-    tree_key = set((np.minimum(t.row, t.col) * (n * n) + np.maximum(t.row, t.col)).tolist())
+    tr, tc = t.row.astype(np.int64), t.col.astype(np.int64)  # int64: the key exceeds 2^31 on large grids
+    tree_key = set((np.minimum(tr, tc) * (n * n) + np.maximum(tr, tc)).tolist())
     key = np.minimum(u, v) * (n * n) + np.maximum(u, v)
     in_tree = np.fromiter((k in tree_key for k in key.tolist()), dtype=bool, count=key.shape[0])
     cand = np.flatnonzero((cls == LOCAL) & ~in_tree)

@@ -231,6 +231,32 @@ def test_sssp_redo_touches_only_the_roots_that_overflowed(mid, shape, monkeypatc
     np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
+@pytest.mark.parametrize("shape", ["1", "6"])
+def test_sssp_32_bit_keys_redo_only_on_distances_beyond_2_29(mid, shape, monkeypatch):
+    """An isolated node (no path to or from anything) stays unreached and
+    must not trigger the 64-bit redo; a node whose distance passes 2^29 must.
+    Bit-exact against Dijkstra either way."""
+    net, dem, _, og = mid
+    monkeypatch.setenv("QDTA_BF_SHAPE", shape)
+    V = net.n_nodes
+    iso = synth.Network(n_nodes=V + 1, tail=net.tail, head=net.head, fftime_q=net.fftime_q, capacity=net.capacity,
+                        length_m=net.length_m, link_class=net.link_class, x=np.append(net.x, 0.0),
+                        y=np.append(net.y, 0.0))
+    g, og2 = Q.Graph(iso), oracle.OracleGraph(iso)
+    rng = np.random.default_rng(8)
+    roots = rng.choice(V, 24, replace=False).astype(np.int32)
+    for scale, want_redo in ((1, False), (60_000, True)):
+        q = np.minimum(net.fftime_q.astype(np.int64) * scale, 2**31 - 1).astype(np.int32)
+        Q.qdta_profile_enable(g, True)
+        p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, True)
+        prof = Q.qdta_profile_read(g)
+        p_o, d_o = oracle.sssp(og2, q, roots)
+        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+        assert (prof["sssp_redo_batches"] > 0) == want_redo, (scale, prof["sssp_redo_batches"])
+        assert (d_o[:, V] == np.iinfo(np.int64).max).all()
+
+
 def test_sssp_large_irregular_graph_with_ties():
     """Above the shared-memory limit with degrees above 4 (so the compressed
     adjacency, not the four-slot one) and many equal-cost ties: bit-exact

@@ -11,9 +11,12 @@ from scipy.sparse.csgraph import connected_components
 from paper_2104_12911_gb300 import synth
 
 
-@pytest.mark.parametrize("n,freeways", [(32, False), (64, True), (110, True)])
-def test_grid_network_properties(n, freeways):
-    net = synth.grid_network(n, 5, freeways=freeways)
+@pytest.mark.parametrize("n,freeways,seed", [(32, False, 5), (64, True, 5), (110, True, 5), (500, True, 2),
+                                             (500, True, 1)])
+def test_grid_network_properties(n, freeways, seed):
+    """(500, seed 2) is the metro grid of the benchmark day; its node ids are
+    large enough that the spanning-tree keys need 64 bits."""
+    net = synth.grid_network(n, seed, freeways=freeways)
     V, L = net.n_nodes, net.n_links
     assert V == n * n
     key = net.tail.astype(np.int64) * V + net.head
