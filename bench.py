@@ -49,8 +49,6 @@ METRIC = "Full-day QDTA s @rel-gap 1e-4, batched vs plain on 1 GB300; SSSP GTEPS
 # by the roots per launch.  Only kernels whose code is unchanged since their
 # capture are listed.
 SSSP_DRAM_BYTES_PER_ROOT = {
-    "sssp_smq_kernel<256,rank,2,true>": (2.830261e9 + 5.333477e9) / 608,
-    "sssp_smq_kernel<256,rank32,2,true>": (1.309412e9 + 2.531841e9) / 608,
 }
 
 
