@@ -884,6 +884,9 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   // distance sets ST_K32 and the batch is redone with 64-bit keys.
   constexpr bool RANK = ADJ >= 2;
   using Key = typename std::conditional<ADJ == 3, unsigned, unsigned long long>::type;
+  // distances and offers in 32 bits with 32-bit keys: distances stay below
+  // 2^29 and link times below 2^31, so a distance plus a link time fits
+  using Dist = Key;
   constexpr Key KINF = ~Key(0);
   const int LB = RANK ? 3 : LB_link;
   unsigned *bm0 = smq_smem, *bm1 = smq_smem + (NBM - 1) * W;
@@ -893,7 +896,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;  // overflow beyond qcap entries
   if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
   const Key NOLINK = (Key)((1ull << LB) - 1ull);
-  const unsigned long long DMAX = (unsigned long long)(KINF >> LB);
+  const Dist DMAX = (Dist)(KINF >> LB);
   constexpr int NQ = THREADS / 4;
   const int quad = threadIdx.x >> 2, lane4 = threadIdx.x & 3;
   for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
@@ -910,7 +913,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
     int ncur = 1, round = 0;
     int *scur = sq0, *snxt = sq1, *gcur = gq0, *gnxt = gq1;
     unsigned *bcur = bm1, *bnxt = bm0;  // the root's queue entry has no mark
-    unsigned long long my_relax = 0;
+    unsigned my_relax = 0;
     while (ncur > 0) {
       const int c = round % 3;
       if (threadIdx.x == 0) s_cnt[(round + 1) % 3] = 0;
@@ -923,7 +926,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
       }
       for (int base = 0; base < ncur; base += NQ * NPT) {
         int w[NPT], kb[NPT], ke[NPT];
-        unsigned long long dw[NPT];
+        Dist dw[NPT];
         unsigned skipj = 0;
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
@@ -943,7 +946,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
               ke[j] = __ldg(&off[w[j] + 1]);
             }
             const Key kw = __ldcg(&state[w[j]]);
-            dw[j] = (unsigned long long)(kw >> LB);
+            dw[j] = (Dist)(kw >> LB);
             // ADJ 2 on graphs where every link has its reverse and both lists
             // of a node share one order: slot lane4 leads back to w's parent
             // when it equals the parent's rank; that offer (dist(w) plus a
@@ -977,7 +980,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
             int pushy = -1;
             if (kb[j] < ke[j]) {
               ++my_relax;
-              const unsigned long long cand = dw[j] + (unsigned long long)(unsigned)ent[j].z;
+              const Dist cand = dw[j] + (Dist)(unsigned)ent[j].z;
               if (cand >= DMAX) {
                 // 64-bit keys: a distance beyond 2^61 is an error.  32-bit
                 // keys: the offer is dropped, and a node that had no key yet
@@ -991,7 +994,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
                 if (ADJ != 3) atomicOr(status, ST_OVERFLOW);
                 else if (tk[j] == KINF) atomicMin(&state[ent[j].y], (Key)(KINF - 1));
               } else {
-                const Key key = (Key)((cand << LB) | (unsigned long long)(unsigned)ent[j].x);
+                const Key key = (Key)((cand << LB) | (Dist)(unsigned)ent[j].x);
                 if (key < tk[j]) {
                   const int y = ent[j].y;
                   Key seen;
@@ -1001,7 +1004,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
                   } else {
                     seen = atomicMin(&state[y], key);
                   }
-                  if ((unsigned long long)(seen >> LB) > cand &&
+                  if ((Dist)(seen >> LB) > cand &&
                       !((atomicOr(&bnxt[y >> 5], 1u << (y & 31)) >> (y & 31)) & 1u)) {
                     if (AGG) {
                       pushy = y;
@@ -1033,10 +1036,12 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
             }
           }
           more = false;
+          if (!ELL) {  // four-slot layouts hold every slot of a node: one step
 #pragma unroll
-          for (int j = 0; j < NPT; ++j) {
-            kb[j] += 4;
-            more |= kb[j] < ke[j];
+            for (int j = 0; j < NPT; ++j) {
+              kb[j] += 4;
+              more |= kb[j] < ke[j];
+            }
           }
         }
       }
@@ -1053,7 +1058,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
     }
     if (roots_counter) {
       if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
-      atomicAdd(roots_counter + 2, my_relax);
+      atomicAdd(roots_counter + 2, (unsigned long long)my_relax);
     }
     __syncthreads();
     // an early exit (timeout) can leave marks behind: clear both bitmaps
