@@ -929,7 +929,7 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
     const bool ell_ok = g->d.max_deg[direction] <= 4 && g->d.node_int != nullptr;
     const bool rank_ok = ell_ok && g->d.rank_tgt[direction] != nullptr;
     bool any_smq = false;
-    for (int shape = 0; shape < 8; ++shape) {
+    for (int shape = 0; shape < 10; ++shape) {
       if (!sssp_smq_shape_fits(g->d.V, shape) || getenv("QDTA_BF_NOSMQ")) continue;
       if (shape == 2 && sssp_smq_shape_fits(g->d.V, 0)) continue;  // same block as shape 0, fewer marks
       any_smq = true;

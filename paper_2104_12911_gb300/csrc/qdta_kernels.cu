@@ -839,13 +839,17 @@ int sssp_group_size() {
 //      of 4 (a pass covers 320 or 384 nodes; 32-bit rank keys only)
 //   6, 7: as 1, one lane per frontier node (sssp_lane_kernel below), 1 or 2
 //      nodes per lane per pass (32-bit rank keys only; otherwise as 1)
+//   8: as 1 with the L2 prefetch of key blocks (32-bit rank keys only)
+//   9: 192 threads, one bitmap, 960 entries, five CTAs per SM (32-bit rank
+//      keys only: up to 68 registers a thread)
 struct SmqShape {
   int threads, bitmaps, qcap, ctas, npt;
 };
-constexpr int kSmqShapes = 8;
+constexpr int kSmqShapes = 10;
 static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 2048, 4, 4}, {512, 1, 3072, 2, 4},
                                                {256, 1, 768, 5, 4},  {256, 1, 2048, 4, 5}, {256, 1, 2048, 4, 6},
-                                               {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2}};
+                                               {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2},
+                                               {256, 1, 2048, 4, 4}, {192, 1, 960, 5, 4}};
 
 // RELAX selects how an offer (cand, link) to neighbour y is applied:
 //   0  returning atomicMin; y is queued when the returned old distance was larger
@@ -858,7 +862,15 @@ static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 20
 //      ends in a CTA barrier and every state access goes through L2.
 //   3  as 2, with warp-aggregated queue appends (one shared-memory atomicAdd
 //      per warp and offsets from a ballot instead of one per queued node)
-template <int THREADS, int ADJ, int RELAX, bool ONEBM, int MINB = 65536 / (THREADS * 64), int NPT = SSSP2_NPT>
+//
+// PF (32-bit keys): when an offer first reaches a 1 KB block of a root's keys
+// (256 consecutive internal ids, a cell of the locality order), the whole
+// block is prefetched into L2, so the rounds that follow find those keys in
+// L2 instead of DRAM (a root's 1 MB of keys does not stay in L2 between its
+// first touch and its reset).  A small shared bitmap marks the blocks
+// prefetched for the current root.
+template <int THREADS, int ADJ, int RELAX, bool ONEBM, int MINB = 65536 / (THREADS * 64), int NPT = SSSP2_NPT,
+          bool PF = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__restrict__ adj,
                 const int *__restrict__ roots, int R_host, const int *R_dev,
@@ -891,6 +903,8 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   const int LB = RANK ? 3 : LB_link;
   unsigned *bm0 = smq_smem, *bm1 = smq_smem + (NBM - 1) * W;
   int *sq0 = reinterpret_cast<int *>(smq_smem + NBM * W), *sq1 = sq0 + qcap;
+  unsigned *pfm = reinterpret_cast<unsigned *>(sq1 + qcap);  // PF: blocks prefetched (V / 8192 + 1 words)
+  const int WPF = (V >> 13) + 1;
   const size_t b = blockIdx.x;
   Key *state = reinterpret_cast<Key *>(g_state) + b * (size_t)V;
   int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;  // overflow beyond qcap entries
@@ -901,6 +915,8 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   const int quad = threadIdx.x >> 2, lane4 = threadIdx.x & 3;
   for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
   for (int i = threadIdx.x; i < NBM * W; i += blockDim.x) smq_smem[i] = 0u;
+  if (PF)
+    for (int i = threadIdx.x; i < WPF; i += blockDim.x) pfm[i] = 0u;
   __syncthreads();
   for (int r = blockIdx.x; r < R; r += gridDim.x) {
     const int z = node_int ? node_int[roots[r]] : roots[r];
@@ -974,6 +990,18 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
             if (ELL && kb[j] < ke[j] && (ent[j].x < 0 || ((skipj >> j) & 1u))) ke[j] = kb[j];  // absent / skipped
             tk[j] = KINF;
             if (RM > 0 && kb[j] < ke[j]) tk[j] = __ldcg(&state[ent[j].y]);
+            if (PF && kb[j] < ke[j]) {
+              // first offer into this 1 KB block of keys: prefetch the block
+              // (the plain read may race; a repeated prefetch is harmless)
+              const int blk = ent[j].y >> 8;
+              const unsigned bit = 1u << (blk & 31);
+              if (!(pfm[blk >> 5] & bit)) {
+                atomicOr(&pfm[blk >> 5], bit);
+                const char *base = reinterpret_cast<const char *>(state + ((size_t)blk << 8));
+#pragma unroll
+                for (int i = 0; i < 8; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + i * 128));
+              }
+            }
           }
 #pragma unroll
           for (int j = 0; j < NPT; ++j) {
@@ -1114,6 +1142,8 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
       for (int v = threadIdx.x; v < V; v += blockDim.x) state[v] = KINF;
     }
     if (ADJ == 3 && unreached) atomicOr(status, ST_K32);
+    if (PF)
+      for (int i = threadIdx.x; i < WPF; i += blockDim.x) pfm[i] = 0u;
     __syncthreads();
   }
 }
@@ -1295,7 +1325,8 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
 
 size_t sssp_smq_smem_bytes(int V, int shape) {
   const SmqShape &sh = kSmqShape[shape];
-  return (size_t)sh.bitmaps * ((V + 31) / 32) * 4 + (size_t)2 * sh.qcap * 4;
+  // marks, two queues, and the prefetch bitmap of shape 8 (V / 8192 + 1 words)
+  return (size_t)sh.bitmaps * ((V + 31) / 32) * 4 + (size_t)2 * sh.qcap * 4 + (size_t)((V >> 13) + 1) * 4;
 }
 
 // does launch shape `shape` fit its CTAs per SM in the 196 KB carveout step
@@ -1331,7 +1362,9 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
       for (int sh = 0; sh < kSmqShapes; ++sh)
         for (int e = 0; e < 4; ++e)
           for (int r = 0; r < 4; ++r)
-            v.push_back(sh >= 6 && e == 3
+            v.push_back(sh == 8 && e == 3   ? std::string("sssp_smq_kernel<256,rank32,2,true,pf>")
+                        : sh == 9 && e == 3 ? std::string("sssp_smq_kernel<192,rank32,2,true,5>")
+                        : sh >= 6 && sh <= 7 && e == 3
                             ? "sssp_lane_kernel<" + std::to_string(kSmqShape[sh].threads) + ",npn" +
                                   std::to_string(kSmqShape[sh].npt) + ">"
                             : "sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
@@ -1403,9 +1436,12 @@ static SmqKernel smq_kernel_relax(int adj, int relax) {
 static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
   if (shape == 6 && adj == 3) return sssp_lane_kernel<256, 1>;
   if (shape == 7 && adj == 3) return sssp_lane_kernel<256, 2>;
+  if (shape == 8 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 4, true>;
+  if (shape == 9 && adj == 3) return sssp_smq_kernel<192, 3, 2, true, 5>;
   if (shape == 3 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 5>;
   if (shape == 4 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 5>;
   if (shape == 5 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 6>;
+  if (shape == 9) return smq_kernel_relax<192, true>(adj, relax);
   if (shape == 1 || shape >= 3) return smq_kernel_relax<256, true>(adj, relax);
   if (shape == 2) return smq_kernel_relax<512, true>(adj, relax);
   return smq_kernel_relax<512, false>(adj, relax);

@@ -140,6 +140,11 @@ LARGE_VARIANTS = {
                                       "sssp_lane_kernel<256,npn1>"),
     "lane_npn2_external_order_flag": ({"QDTA_BF_SHAPE": "7", "QDTA_SMQ_OUT": "0"}, "sssp_lane_kernel<256,npn2>"),
     "lane_shape_ell16": ({"QDTA_BF_SHAPE": "6", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<256,ell,2,true>"),
+    "rank32_prefetch": ({"QDTA_BF_SHAPE": "8"}, "sssp_smq_kernel<256,rank32,2,true,pf>"),
+    "rank32_192x5": ({"QDTA_BF_SHAPE": "9"}, "sssp_smq_kernel<192,rank32,2,true,5>"),
+    "shape_192x5_ell16": ({"QDTA_BF_SHAPE": "9", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<192,ell,2,true>"),
+    "shape_192x5_csr_returning": ({"QDTA_BF_SHAPE": "9", "QDTA_NO_ELL": "1", "QDTA_BF_RELAX": "1"},
+                                  "sssp_smq_kernel<192,csr,1,true>"),
     "global_queues": ({"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "sssp_ilp_kernel<512>"),
     "cell": ({"QDTA_SSSP": "cell"}, "sssp_cell_kernel"),
 }
@@ -189,7 +194,8 @@ def test_sssp_rank_keys_on_a_graph_with_one_way_links(shape, kernel, monkeypatch
         np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-@pytest.mark.parametrize("adj,shape", [("2", "1"), ("3", "1"), ("3", "6"), ("3", "7")])
+@pytest.mark.parametrize("adj,shape", [("2", "1"), ("3", "1"), ("3", "6"), ("3", "7"), ("3", "8"), ("3", "9"),
+                                       ("2", "9")])
 def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, shape, monkeypatch):
     """Link times of 5e6..1e7 quanta push distances past 2^29: the 32-bit-key
     batch flags it and the 64-bit redo gives the oracle's bits."""
@@ -208,7 +214,7 @@ def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, shape, monkeypatch)
         np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-@pytest.mark.parametrize("shape", ["1", "6", "7"])
+@pytest.mark.parametrize("shape", ["1", "6", "7", "8", "9"])
 def test_sssp_redo_touches_only_the_roots_that_overflowed(mid, shape, monkeypatch):
     """Links entering three nodes cost 2^30: destination trees rooted there
     pass 2^29 (so the batch is redone with 64-bit keys), the other roots'
@@ -231,7 +237,7 @@ def test_sssp_redo_touches_only_the_roots_that_overflowed(mid, shape, monkeypatc
     np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-@pytest.mark.parametrize("shape", ["1", "6"])
+@pytest.mark.parametrize("shape", ["1", "6", "8", "9"])
 def test_sssp_32_bit_keys_redo_only_on_distances_beyond_2_29(mid, shape, monkeypatch):
     """An isolated node (no path to or from anything) stays unreached and
     must not trigger the 64-bit redo; a node whose distance passes 2^29 must.
@@ -298,14 +304,16 @@ def test_autotune_keeps_the_fastest_shape_and_stays_bit_exact(mid):
     rep = Q.qdta_autotune(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, reps=1)
     kernels = {c["kernel"] for c in rep["candidates"]}
     # launch shapes {512 x 2 CTAs, 256 x 4 CTAs} x adjacency {32-bit rank keys, rank keys, four-slot,
-    # compressed} in relaxation mode 2; the 32-bit kernel also with five CTAs per SM, with 5 or 6
-    # frontier nodes per lane group and lane per node (1 or 2 nodes per lane); the cell kernel
+    # compressed} in relaxation mode 2; the 32-bit kernel also with five CTAs per SM (256 and 192
+    # threads), with 5 or 6 frontier nodes per lane group, lane per node (1 or 2 nodes per lane) and
+    # with the L2 prefetch of key blocks; the cell kernel
     want = {f"sssp_smq_kernel<{t},{e},2,{b}>" for t, b in (("512", "false"), ("256", "true"))
             for e in ("rank32", "rank", "ell", "csr")} | {"sssp_cell_kernel"}
     want |= {"sssp_smq_kernel<256,rank32,2,true,5>", "sssp_smq_kernel<256,rank32,2,true,npt5>",
-             "sssp_smq_kernel<256,rank32,2,true,npt6>", "sssp_lane_kernel<256,npn1>", "sssp_lane_kernel<256,npn2>"}
+             "sssp_smq_kernel<256,rank32,2,true,npt6>", "sssp_lane_kernel<256,npn1>", "sssp_lane_kernel<256,npn2>",
+             "sssp_smq_kernel<256,rank32,2,true,pf>", "sssp_smq_kernel<192,rank32,2,true,5>"}
     assert kernels == want
-    assert len(rep["candidates"]) == 14
+    assert len(rep["candidates"]) == 16
     ctas = {c["kernel"]: c["ctas_per_sm"] for c in rep["candidates"]}
     assert ctas["sssp_smq_kernel<256,rank32,2,true>"] == 4 and ctas["sssp_smq_kernel<256,rank32,2,true,5>"] == 5
     assert rep["best"]["ms"] == min(c["ms"] for c in rep["candidates"])
