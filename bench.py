@@ -300,18 +300,18 @@ def day_oracle_seconds(day_work, n_roots, t_root, t_sweep):
 # they were recorded from the bench line's "per_interval" entry.  The
 # reference arm scales its timed sample by them.
 METRO_DAY_WORK = {
-    "aon": [2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 3, 3, 14, 30, 61, 94, 112, 92, 103,
-             96, 97, 77, 56, 61, 75, 63, 55, 48, 37, 52, 55, 41, 51, 41, 46, 3, 29, 27, 3, 3, 14, 13, 13, 16, 47, 47,
-             27, 3, 8, 32, 61, 71, 104, 126, 143, 114, 92, 93, 47, 51, 63, 45, 49, 56, 58, 55, 59, 45, 42, 51, 3, 24,
-             33, 36, 4, 46, 43, 33, 43, 34, 11, 35, 11],
-    "fw": [0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 12, 28, 59, 92, 110, 90, 101,
-             94, 95, 75, 54, 59, 73, 61, 53, 46, 35, 50, 53, 39, 49, 39, 44, 1, 27, 25, 1, 1, 12, 11, 11, 14, 45, 45,
-             25, 1, 6, 30, 59, 69, 102, 124, 141, 112, 90, 91, 45, 49, 61, 43, 47, 54, 56, 53, 57, 43, 40, 49, 1, 22,
-             31, 34, 2, 44, 41, 31, 41, 32, 9, 33, 9],
-    "sweeps": [1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 6, 10, 65, 145, 300, 465, 555,
-             455, 510, 475, 480, 380, 275, 300, 370, 310, 266, 235, 176, 255, 266, 196, 246, 196, 225, 6, 136, 126,
-             6, 6, 65, 60, 60, 75, 230, 230, 130, 10, 35, 155, 300, 350, 515, 625, 710, 565, 455, 460, 230, 246, 310,
-             220, 240, 271, 281, 266, 286, 216, 205, 246, 6, 111, 156, 171, 15, 221, 210, 156, 206, 161, 50, 170, 50],
+    "aon": [2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 3, 4, 8, 37, 56, 92, 182, 115, 116,
+             120, 116, 94, 67, 44, 62, 77, 69, 55, 50, 54, 51, 48, 45, 2, 2, 43, 34, 33, 14, 24, 35, 21, 2, 2, 2, 2,
+             4, 4, 7, 41, 52, 84, 191, 158, 112, 114, 68, 69, 82, 54, 60, 55, 71, 45, 62, 69, 61, 78, 37, 3, 44, 53,
+             38, 49, 46, 75, 20, 26, 26, 32, 40, 10, 2],
+    "fw": [0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 2, 6, 35, 54, 90, 180, 113, 114,
+             118, 114, 92, 65, 42, 60, 75, 67, 53, 48, 52, 49, 46, 43, 0, 0, 41, 32, 31, 12, 22, 33, 19, 0, 0, 0, 0,
+             2, 2, 5, 39, 50, 82, 189, 156, 110, 112, 66, 67, 80, 52, 58, 53, 69, 43, 60, 67, 59, 76, 35, 1, 42, 51,
+             36, 47, 44, 73, 18, 24, 24, 30, 38, 8, 0],
+    "sweeps": [1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 5, 1, 1, 5, 1, 1, 5, 1, 6, 15, 35, 180, 275, 455, 905,
+             570, 575, 595, 575, 465, 330, 215, 305, 380, 336, 266, 241, 261, 246, 231, 220, 1, 1, 206, 161, 160, 65,
+             115, 170, 100, 1, 1, 5, 5, 11, 15, 30, 200, 255, 415, 950, 785, 555, 565, 335, 340, 405, 265, 295, 270,
+             350, 216, 305, 340, 296, 385, 180, 6, 211, 256, 181, 236, 225, 370, 95, 125, 125, 155, 195, 45, 5],
 }
 
 
