@@ -49,6 +49,7 @@ METRIC = "Full-day QDTA s @rel-gap 1e-4, batched vs plain on 1 GB300; SSSP GTEPS
 # by the roots per launch.  Only kernels whose code is unchanged since their
 # capture are listed.
 SSSP_DRAM_BYTES_PER_ROOT = {
+    "sssp_smq_kernel<256,rank32,2,true>": (1.324410e9 + 2.547958e9) / 608,
 }
 
 

@@ -352,8 +352,10 @@ int qdta_sssp_batch_noalloc(qdta_graph *g, const int32_t *cost_q, const int32_t 
  * qdta_sssp_batch; parent_scratch is a caller-owned device array of R*V int32
  * that receives the trees (contents unspecified afterwards).  Each candidate
  * runs once untimed and then `reps` times between CUDA events on `stream`.
- * The report (host) lists every candidate with its mean milliseconds per
- * batch; `best` indexes the one kept.  Errors: QDTA_EINVAL for bad arguments;
+ * The handle's current choice is kept unless another candidate is at least
+ * 2 % faster (closer timings are within run-to-run noise).  The report
+ * (host) lists every candidate with its mean milliseconds per batch; `best`
+ * indexes the one kept.  Errors: QDTA_EINVAL for bad arguments;
  * a failing candidate (e.g. QDTA_ENOMEM) aborts the tuning, restores the
  * previous choice and returns its code.  Synchronises `stream`.  Not to be
  * called during stream capture. */

@@ -982,6 +982,14 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
     tune_set(g, start);
     return rc != QDTA_OK ? rc : fail(QDTA_ECUDA, "qdta_autotune: no candidate ran");
   }
+  // keep the handle's current choice unless another candidate is at least 2 %
+  // faster: closer timings are within run-to-run noise
+  for (size_t i = 0; i < cand.size() && i < (size_t)rep.n; ++i) {
+    const TuneCfg &c = cand[i];
+    if (c.kind == start.kind && c.adj == start.adj && c.relax == start.relax && c.bpsm == start.bpsm &&
+        c.shape == start.shape && rep.entry[i].valid && rep.entry[best].ms > 0.98f * rep.entry[i].ms)
+      best = (int)i;
+  }
   tune_set(g, cand[best]);
   rep.best = best;
   *out_host = rep;

@@ -316,7 +316,10 @@ def test_autotune_keeps_the_fastest_shape_and_stays_bit_exact(mid):
     assert len(rep["candidates"]) == 16
     ctas = {c["kernel"]: c["ctas_per_sm"] for c in rep["candidates"]}
     assert ctas["sssp_smq_kernel<256,rank32,2,true>"] == 4 and ctas["sssp_smq_kernel<256,rank32,2,true,5>"] == 5
-    assert rep["best"]["ms"] == min(c["ms"] for c in rep["candidates"])
+    fastest = min(c["ms"] for c in rep["candidates"])
+    default = [c for c in rep["candidates"] if c["kernel"] == "sssp_smq_kernel<256,rank32,2,true>"][0]
+    # the default shape is kept unless another is at least 2 % faster
+    assert rep["best"]["ms"] == fastest or (rep["best"] == default and default["ms"] * 0.98 <= fastest)
     assert Q.qdta_sssp_kernel_name(g, Q.QDTA_TO_ROOT) == rep["best"]["kernel"]
     p_o, d_o = oracle.sssp(og, q, roots)
     p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, True)
@@ -965,3 +968,55 @@ def test_load_aon_with_carried_times_matches_the_oracle(small):
         f_g, s_g = Q.qdta_load_aon(g, T(q, np.int32), T(par_o, np.int32), od_g, dt_q, want_stop=True)
         np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
         np.testing.assert_array_equal(s_g.cpu().numpy(), s_o)
+
+
+# ---------------------------------------------------------------------------
+# Full size: the metro grid of the benchmark day (250k nodes, 954k links)
+@pytest.fixture(scope="module")
+def metro():
+    inst = synth.config_day(seed=2)
+    return inst, Q.Graph(inst.net), oracle.OracleGraph(inst.net)
+
+
+def test_metro_batch_sampled_parity(metro):
+    """One batch over all 2,000 zones in the launch shape the benchmark picks
+    (autotuned on free-flow costs), at congested link times (the BPR costs of
+    the busiest interval's all-or-nothing flows): 12 sampled roots' parent and
+    distance rows, and the truncated loading of those roots' items, against
+    the oracle, bit-exact."""
+    inst, g, og = metro
+    net = inst.net
+    zones = T(inst.zones, np.int32)
+    Q.qdta_autotune(g, T(net.fftime_q, np.int32), zones, Q.QDTA_TO_ROOT, reps=1)
+    peak = int(np.argmax([d.amount_fx.sum() for d in inst.demand]))
+    dem = inst.demand[peak]
+    # congested costs: BPR of the free-flow all-or-nothing flows of the busiest interval
+    par_ff, _ = Q.qdta_sssp_batch(g, T(net.fftime_q, np.int32), zones)
+    g_fx, _ = Q.qdta_load_aon(g, T(net.fftime_q, np.int32), par_ff, Q.DeviceOD.of(dem), 90000)
+    del par_ff
+    f = g_fx.to(torch.float64) / float(1 << 32)
+    q_g, _ = Q.qdta_bpr_costs(g, f, 900.0)
+    q = q_g.cpu().numpy()
+    q_o, _, _ = oracle.bpr(og, f.cpu().numpy(), 900.0)
+    np.testing.assert_array_equal(q, q_o)
+    assert q.max() > 10 * net.fftime_q.max()  # congested
+    parent, dist = Q.qdta_sssp_batch(g, q_g, zones, Q.QDTA_TO_ROOT, want_dist=True)
+    rng = np.random.default_rng(12)
+    sample = np.sort(rng.choice(inst.zones.shape[0], 12, replace=False))
+    p_o, d_o = oracle.sssp(og, q, inst.zones[sample])
+    np.testing.assert_array_equal(dist[T(sample, np.int64)].cpu().numpy(), d_o)
+    np.testing.assert_array_equal(parent[T(sample, np.int64)].cpu().numpy(), p_o)
+    del dist
+    # loading of the sampled roots' items (root indices remapped to the sample)
+    remap = -np.ones(inst.zones.shape[0], np.int64)
+    remap[sample] = np.arange(sample.shape[0])
+    sel = remap[dem.root_idx] >= 0
+    ri = remap[dem.root_idx[sel]].astype(np.int32)
+    od_o = oracle.OracleOD(inst.zones[sample], ri, dem.src[sel], dem.amount_fx[sel])
+    f_o, s_o, rc = oracle.load(og, q, p_o, od_o, 90000)
+    od_g = Q.DeviceOD(T(inst.zones[sample], np.int32), T(ri, np.int32), T(dem.src[sel], np.int32),
+                      T(dem.amount_fx[sel], np.int64))
+    f_g, s_g = Q.qdta_load_aon(g, q_g, parent[T(sample, np.int64)].contiguous(), od_g, 90000, want_stop=True)
+    np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+    np.testing.assert_array_equal(s_g.cpu().numpy(), s_o)
+    assert rc == 0 and int(sel.sum()) > 1000
