@@ -414,8 +414,9 @@ def sssp_only(args):
 def batch32(args):
     """Many independent networks, one interval each: 32 grids with n spaced
     geometrically from 64 to 700, zones 100 -> 3,000 and trips 10k -> 400k,
-    solved as parallel branches of one CUDA graph launch vs one network at a
-    time (plain launches)."""
+    each with its autotuned shortest-path launch shape, solved as parallel
+    branches of one CUDA graph launch vs one network at a time (plain
+    launches); --stop rel_gap for the relative-gap target."""
     import torch
     from paper_2104_12911_gb300 import qdta as Q, synth
     k = np.arange(32)
@@ -429,6 +430,9 @@ def batch32(args):
         dem = synth.demand_from_matrix(zones, synth.sample_trips(
             synth.gravity_weights(net, zones, 100 + i, 10000.0), int(ts[i]), 200 + i))
         g = Q.Graph(net)
+        if not args.no_tune:  # each network's shortest-path launch shape, by measurement on its zones
+            Q.qdta_autotune(g, torch.from_numpy(net.fftime_q.astype(np.int32)).cuda(),
+                            torch.from_numpy(zones.astype(np.int32)).cuda(), reps=1)
         items.append((g, Q.DeviceOD.of(dem), 900.0, torch.empty(net.n_links, dtype=torch.float64, device="cuda")))
         links += net.n_links
     res = {}
