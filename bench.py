@@ -76,6 +76,8 @@ def parse():
                     help="FW step rule (the paper compares its line search with MSA)")
     ap.add_argument("--objective", default="ue", choices=["ue", "so"],
                     help="user equilibrium (the paper's) or system optimum")
+    ap.add_argument("--truncation", default="node", choices=["node", "carry"],
+                    help="day workloads: Eq. 2's node rule, or Section 3.4's carried partial links")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default SSSP launch shape")
@@ -577,7 +579,8 @@ def sta_vs_qdta(args):
     length = torch.from_numpy(net.length_m.astype(np.float64)).to(dev)
     cls = torch.from_numpy(net.link_class.astype(np.int32)).to(dev)
     n_cls = int(net.link_class.max()) + 1
-    p = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="graph", objective=args.objective)
+    p = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="graph", objective=args.objective,
+                      truncation=args.truncation)
     # QDTA: twelve intervals with residual demand
     dd = [Q.DeviceOD(zones, *(torch.from_numpy(np.ascontiguousarray(a)).to(dev)
                               for a in (d.root_idx, d.src, d.amount_fx))) for d in days]
@@ -763,10 +766,14 @@ def main():
 
     host = [upload(d, pin=True) for d in inst.demand]
     zones_host = torch.from_numpy(inst.zones.astype(np.int32)).pin_memory()
-    params_graph = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="graph", objective=args.objective)
-    params_plain = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="plain", objective=args.objective)
+    params_graph = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="graph", objective=args.objective,
+                                 truncation=args.truncation)
+    params_plain = Q.make_params(args.step, args.stop, args.max_iter, 1e-4, schedule="plain", objective=args.objective,
+                                 truncation=args.truncation)
     cfg["step_rule"] = args.step
     cfg["objective"] = {"ue": "user equilibrium (Beckmann)", "so": "system optimum (total cost)"}[args.objective]
+    cfg["truncation"] = {"node": "Eq. 2: first node reached at or after dt",
+                         "carry": "Section 3.4: partial links carried across intervals"}[args.truncation]
     flow_out = torch.empty((len(inst.demand), g.n_links), dtype=torch.float64, device=dev)
     flows_host = torch.empty((len(inst.demand), g.n_links), dtype=torch.float64).pin_memory()
     h2d = sum(a.numel() * a.element_size() for h in host for a in h) + zones_host.numel() * 4
