@@ -358,7 +358,14 @@ int qdta_sssp_batch_noalloc(qdta_graph *g, const int32_t *cost_q, const int32_t 
  * indexes the one kept.  Errors: QDTA_EINVAL for bad arguments;
  * a failing candidate (e.g. QDTA_ENOMEM) aborts the tuning, restores the
  * previous choice and returns its code.  Synchronises `stream`.  Not to be
- * called during stream capture. */
+ * called during stream capture.
+ *
+ * Tuning cache per graph signature and GPU model, opt-in through the
+ * environment variable QDTA_TUNE_CACHE: "mem" keeps each choice for the rest
+ * of the process; a file path also reads earlier choices from that file and
+ * appends new ones.  The key is a hash of the GPU model (name, SM count), the
+ * network (nodes, links, tails, heads, free-flow times) and the direction; a
+ * hit applies the stored choice without timing and sets `cached`. */
 #define QDTA_TUNE_MAX 16
 typedef struct qdta_tune_entry {
   char kernel[40];     /* kernel name, as qdta_sssp_kernel_name reports it */
@@ -370,6 +377,7 @@ typedef struct qdta_tune_report {
   int32_t n;    /* candidates timed */
   int32_t best; /* index of the candidate kept */
   qdta_tune_entry entry[QDTA_TUNE_MAX];
+  int32_t cached; /* 1: the choice came from the tuning cache (entry[0], nothing timed) */
 } qdta_tune_report;
 int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R, int32_t direction,
                   int32_t reps, int32_t *parent_scratch, qdta_tune_report *out_host, void *stream);

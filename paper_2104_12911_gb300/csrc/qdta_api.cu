@@ -81,6 +81,7 @@ struct qdta_graph {
   long long cell_delta = 0;  // near/far width of the cell kernel, in quanta
   int sssp_kind = 0;  // 0 shared-memory BF, 1 cell, 2 global-memory BF
   int bf_bpsm = 0;    // resident CTAs per SM of the global-memory BF (0: as many as fit)
+  unsigned long long sig = 0;  // graph signature (structure, free-flow times, device) for the tuning cache
 };
 
 struct qdta_tape {
@@ -540,6 +541,27 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   CK(cudaGetDeviceCount(&ndev));
   if (device < 0 || device >= ndev) return fail(QDTA_EINVAL, "device %d out of range", device);
   DevGuard guard(device);
+  // FNV-1a over the device's name and SM count and the network (nodes, links,
+  // tails, heads, free-flow times): the key of the launch-shape tuning cache
+  unsigned long long sig = 1469598103934665603ull;
+  auto mix = [&](const void *p, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) { sig ^= b[i]; sig *= 1099511628211ull; }
+  };
+  {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) {
+      mix(prop.name, strnlen(prop.name, sizeof prop.name));
+      mix(&prop.multiProcessorCount, sizeof prop.multiProcessorCount);
+    }
+    mix(&V, sizeof V);
+    mix(&L, sizeof L);
+    if (L > 0) {
+      mix(d->tail, (size_t)L * 4);
+      mix(d->head, (size_t)L * 4);
+      mix(d->fftime_q, (size_t)L * 4);
+    }
+  }
 
   std::vector<int> out_off(V + 1, 0), in_off(V + 1, 0), out_link(L), in_link(L);
   for (int e = 0; e < L; ++e) { out_off[d->tail[e] + 1]++; in_off[d->head[e] + 1]++; }
@@ -550,6 +572,7 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   }
   qdta_graph *g = new qdta_graph();
   g->device = device;
+  g->sig = sig;
   GraphDev &gd = g->d;
   gd.V = V;
   gd.L = L;
@@ -908,6 +931,68 @@ void tune_set(qdta_graph *g, const TuneCfg &c) {
   g->bf_bpsm = c.bpsm;
   g->d.tune_shape = c.shape;
 }
+
+// Launch-shape tuning cache, keyed by (graph signature, direction); opt-in
+// with QDTA_TUNE_CACHE: "mem" keeps the choices of this process, a file path
+// also reads and appends them there (one line per choice: signature,
+// direction, the five choice fields, milliseconds, kernel name), so that
+// later processes on the same GPU model skip the timing.
+struct TuneHit {
+  TuneCfg cfg;
+  qdta_tune_entry entry;
+};
+std::mutex g_tune_mu;
+std::map<std::pair<unsigned long long, int>, TuneHit> g_tune_cache;
+
+const char *tune_cache_path() {
+  const char *e = getenv("QDTA_TUNE_CACHE");
+  return (e && *e) ? e : nullptr;
+}
+
+bool tune_cache_find(unsigned long long sig, int dir, TuneHit *hit) {
+  const char *path = tune_cache_path();
+  if (!path) return false;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune_cache.find({sig, dir});
+  if (it != g_tune_cache.end()) { *hit = it->second; return true; }
+  if (strcmp(path, "mem") == 0) return false;
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  char line[256];
+  bool found = false;
+  while (!found && fgets(line, sizeof line, f)) {
+    unsigned long long s2 = 0;
+    int d2 = 0, k = 0, a = 0, r = 0, b = 0, sh = 0, ctas = 0;
+    float ms = 0.f;
+    char name[40] = {0};
+    if (sscanf(line, "%llx %d %d %d %d %d %d %d %f %39s", &s2, &d2, &k, &a, &r, &b, &sh, &ctas, &ms, name) == 10 &&
+        s2 == sig && d2 == dir && sh >= 0 && sh < 10) {
+      hit->cfg = TuneCfg{k, a, r, b, sh};
+      hit->entry = qdta_tune_entry{};
+      snprintf(hit->entry.kernel, sizeof hit->entry.kernel, "%s", name);
+      hit->entry.ctas_per_sm = ctas;
+      hit->entry.valid = 1;
+      hit->entry.ms = ms;
+      g_tune_cache[{sig, dir}] = *hit;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_cache_store(unsigned long long sig, int dir, const TuneCfg &c, const qdta_tune_entry &e) {
+  const char *path = tune_cache_path();
+  if (!path) return;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[{sig, dir}] = TuneHit{c, e};
+  if (strcmp(path, "mem") == 0) return;
+  if (FILE *f = fopen(path, "a")) {
+    fprintf(f, "%llx %d %d %d %d %d %d %d %.4f %s\n", sig, dir, c.kind, c.adj, c.relax, c.bpsm, c.shape,
+            e.ctas_per_sm, e.ms, e.kernel);
+    fclose(f);
+  }
+}
 }  // namespace
 
 extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t *roots, int32_t R,
@@ -919,6 +1004,19 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
   if (!cost_q || !roots || !parent_scratch || !out_host) return fail(QDTA_EINVAL, "NULL argument");
   DevGuard guard(g->device);
   cudaStream_t s = (cudaStream_t)stream;
+  {
+    TuneHit hit;
+    if (tune_cache_find(g->sig, direction, &hit)) {
+      tune_set(g, hit.cfg);
+      qdta_tune_report rep{};
+      rep.n = 1;
+      rep.best = 0;
+      rep.entry[0] = hit.entry;
+      rep.cached = 1;
+      *out_host = rep;
+      return QDTA_OK;
+    }
+  }
   const TuneCfg start = tune_get(g);
   std::vector<TuneCfg> cand;
   if (g->sssp_smem) {
@@ -992,6 +1090,7 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
   }
   tune_set(g, cand[best]);
   rep.best = best;
+  tune_cache_store(g->sig, direction, cand[best], rep.entry[best]);
   *out_host = rep;
   return QDTA_OK;
 }

@@ -88,12 +88,12 @@ class TuneEntry(C.Structure):
 
 
 class TuneReport(C.Structure):
-    _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("entry", TuneEntry * TUNE_MAX)]
+    _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("entry", TuneEntry * TUNE_MAX), ("cached", C.c_int32)]
 
     def as_dict(self):
         rows = [{"kernel": e.kernel.decode(), "ctas_per_sm": e.ctas_per_sm, "ms": e.ms}
                 for e in self.entry[:self.n] if e.valid]
-        return {"best": rows[self.best] if rows else None, "candidates": rows}
+        return {"best": rows[self.best] if rows else None, "candidates": rows, "cached": bool(self.cached)}
 
 
 class Instance(C.Structure):

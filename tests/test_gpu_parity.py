@@ -1020,3 +1020,41 @@ def test_metro_batch_sampled_parity(metro):
     np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
     np.testing.assert_array_equal(s_g.cpu().numpy(), s_o)
     assert rc == 0 and int(sel.sum()) > 1000
+
+
+def test_autotune_cache_reuses_the_choice(mid, monkeypatch, tmp_path):
+    """QDTA_TUNE_CACHE: a second handle on the same network (and a second
+    process reading the cache file) applies the first tuning's choice without
+    timing; the trees stay bit-exact."""
+    import json
+    import os
+    import subprocess
+    import sys
+    net, dem, _, og = mid
+    path = tmp_path / "tune_cache.txt"
+    monkeypatch.setenv("QDTA_TUNE_CACHE", str(path))
+    rng = np.random.default_rng(4)
+    q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
+    roots = rng.choice(net.n_nodes, 64, replace=False).astype(np.int32)
+    rep1 = Q.qdta_autotune(Q.Graph(net), T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, reps=1)
+    assert not rep1["cached"] and len(rep1["candidates"]) > 1
+    g2 = Q.Graph(net)
+    rep2 = Q.qdta_autotune(g2, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, reps=1)
+    assert rep2["cached"] and len(rep2["candidates"]) == 1
+    assert rep2["best"]["kernel"] == rep1["best"]["kernel"] == Q.qdta_sssp_kernel_name(g2, Q.QDTA_TO_ROOT)
+    assert path.read_text().count("\n") == 1
+    p_o, d_o = oracle.sssp(og, q, roots)
+    p_g, d_g = Q.qdta_sssp_batch(g2, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, True)
+    np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = ("import json, sys, numpy as np, torch; sys.path.insert(0, %r)\n"
+             "from paper_2104_12911_gb300 import qdta as Q, synth\n"
+             "net = synth.grid_network(110, 5, freeways=True)\n"
+             "q = torch.from_numpy(net.fftime_q).cuda(); r = torch.arange(8, dtype=torch.int32, device='cuda')\n"
+             "g = Q.Graph(net); rep = Q.qdta_autotune(g, q, r, Q.QDTA_TO_ROOT, reps=1)\n"
+             "print(json.dumps({'cached': rep['cached'], 'kernel': rep['best']['kernel']}))\n") % root
+    out = subprocess.run([sys.executable, "-c", child], capture_output=True, text=True, timeout=600,
+                         env={**os.environ, "QDTA_TUNE_CACHE": str(path)})
+    assert out.returncode == 0, out.stderr[-2000:]
+    got = json.loads(out.stdout.strip().splitlines()[-1])
+    assert got == {"cached": True, "kernel": rep1["best"]["kernel"]}
