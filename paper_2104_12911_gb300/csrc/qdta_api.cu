@@ -624,6 +624,8 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   g->d.tune_shape = sssp_smq_shape_fits(V, 1) ? 1 : sssp_smq_shape_fits(V, 0) ? 0 : sssp_smq_shape_fits(V, 2) ? 2 : 0;
   g->d.tune_out = 1;  // internal-order output pass where the graph is renumbered
   if (const char *e = getenv("QDTA_SMQ_OUT")) g->d.tune_out = atoi(e) != 0;
+  g->d.tune_dyn = 0;  // round-robin roots (QDTA_BF_DYNAMIC=1: from an atomic counter)
+  if (const char *e = getenv("QDTA_BF_DYNAMIC")) g->d.tune_dyn = atoi(e) != 0;
   if (const char *e = getenv("QDTA_BF_SHAPE")) {
     const int sh = atoi(e);
     if (sssp_smq_shape_fits(V, sh)) g->d.tune_shape = sh;

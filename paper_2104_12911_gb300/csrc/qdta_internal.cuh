@@ -271,6 +271,7 @@ struct GraphDev {
   // 1: 256 threads, one bitmap; 2: 512 threads, one bitmap)
   int tune_adj, tune_relax, tune_carve, tune_shape;  // tune_adj: 0 compressed, 1 four-slot, 2 rank-keyed, 3 rank-keyed 32-bit
   int tune_out;  // output pass of the queue kernel: 1 internal node order, 0 external order
+  int tune_dyn;  // queue kernels: roots after the first wave from an atomic counter (1) or round-robin (0)
 };
 
 // Cell partition for the shared-memory cell SSSP (graphs above the

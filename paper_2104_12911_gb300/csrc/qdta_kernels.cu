@@ -851,6 +851,19 @@ static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 20
                                                {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2},
                                                {256, 1, 2048, 4, 4}, {192, 1, 960, 5, 4}};
 
+// Next destination root of this CTA: every gridDim-th one, or, with a fetch
+// counter, the next one handed out by that counter (dynamic balance over the
+// CTAs; the counter is zeroed before each launch and numbers the roots after
+// the first wave).  Called by every thread of the CTA.
+__device__ __forceinline__ int next_root(int r, int *fetch, int *s_next) {
+  if (!fetch) return r + (int)gridDim.x;
+  if (threadIdx.x == 0) *s_next = (int)gridDim.x + atomicAdd(fetch, 1);
+  __syncthreads();
+  const int n = *s_next;
+  __syncthreads();  // read by every thread before thread 0 may write the next one
+  return n;
+}
+
 // RELAX selects how an offer (cand, link) to neighbour y is applied:
 //   0  returning atomicMin; y is queued when the returned old distance was larger
 //   1  read y's key first, skip when the offer cannot win, else as 0
@@ -878,9 +891,10 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                 const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
                 int max_rounds, int qcap, const int *__restrict__ node_ext, int out_mode,
-                const int *__restrict__ rank_link, int skip_parent) {
+                const int *__restrict__ rank_link, int skip_parent, int *fetch) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
+  __shared__ int s_next;
   if (skip_dev && *skip_dev) return;
   const int R = R_dev ? *R_dev : R_host;
   if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
@@ -918,7 +932,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   if (PF)
     for (int i = threadIdx.x; i < WPF; i += blockDim.x) pfm[i] = 0u;
   __syncthreads();
-  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+  for (int r = blockIdx.x; r < R; r = next_root(r, fetch, &s_next)) {
     const int z = node_int ? node_int[roots[r]] : roots[r];
     if (threadIdx.x == 0) {
       state[z] = NOLINK;
@@ -1166,9 +1180,10 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
                  const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                  const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
                  int max_rounds, int qcap, const int *__restrict__ node_ext, int /*out_mode*/,
-                 const int *__restrict__ rank_link, int skip_parent) {
+                 const int *__restrict__ rank_link, int skip_parent, int *fetch) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
+  __shared__ int s_next;
   if (skip_dev && *skip_dev) return;
   const int R = R_dev ? *R_dev : R_host;
   if (roots_counter && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(roots_counter, (unsigned long long)R);
@@ -1184,7 +1199,7 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
   for (int v = threadIdx.x; v < V; v += THREADS) state[v] = KINF;
   for (int i = threadIdx.x; i < W; i += THREADS) bm[i] = 0u;
   __syncthreads();
-  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+  for (int r = blockIdx.x; r < R; r = next_root(r, fetch, &s_next)) {
     const int z = node_int ? node_int[roots[r]] : roots[r];
     if (threadIdx.x == 0) {
       state[z] = NOLINK;
@@ -1419,7 +1434,7 @@ __global__ void k32_redo_flag_kernel(unsigned *status, const int *skip_dev, int 
 
 using SmqKernel = void (*)(int, int, const int *, const int4 *, const int *, int, const int *, unsigned long long *,
                           int *, int *, const int *, long long, long long *, unsigned *, const int *,
-                          unsigned long long *, const int *, int, int, const int *, int, const int *, int);
+                          unsigned long long *, const int *, int, int, const int *, int, const int *, int, int *);
 
 template <int THREADS, bool ONEBM>
 static SmqKernel smq_kernel_relax(int adj, int relax) {
@@ -1501,7 +1516,11 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
       const int threads = kSmqShape[g.tune_shape].threads;
       const bool perm = g.node_int != nullptr;
-      auto run = [&](SmqKernel kern, const int *skip, unsigned long long *counters) {
+      // QDTA_BF_DYNAMIC: roots after the first wave come from an atomic
+      // counter (w.fb_skip[1] for the kernel, [2] for the redo), zeroed here
+      int *fetch = g.tune_dyn ? w.fb_skip + 1 : nullptr;
+      if (fetch) cudaMemsetAsync(fetch, 0, 2 * sizeof(int), s);
+      auto run = [&](SmqKernel kern, const int *skip, unsigned long long *counters, int *fetch_ctr) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
         COUNT_LAUNCH();
@@ -1509,9 +1528,9 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                                         w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip,
                                         counters, perm ? g.node_int : nullptr, round_limit(g.V),
                                         kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
-                                        g.rank_link[direction], g.skip_parent);
+                                        g.rank_link[direction], g.skip_parent, fetch_ctr);
       };
-      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev, roots_counter);
+      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev, roots_counter, fetch);
       if (adjl == 3) {
         // a distance beyond the 32-bit keys' range: redo the batch with 64-bit
         // keys on the same packed adjacency (decided on the device, so graph
@@ -1520,7 +1539,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
         COUNT_LAUNCH();
         k32_redo_flag_kernel<<<1, 1, 0, s>>>(status, skip_dev, w.fb_skip,
                                              roots_counter ? roots_counter + 4 : nullptr);
-        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip, nullptr);
+        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip, nullptr, fetch ? fetch + 1 : nullptr);
       }
       return;
     }

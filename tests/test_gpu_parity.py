@@ -263,6 +263,24 @@ def test_sssp_32_bit_keys_redo_only_on_distances_beyond_2_29(mid, shape, monkeyp
         assert (d_o[:, V] == np.iinfo(np.int64).max).all()
 
 
+@pytest.mark.parametrize("shape", ["1", "6"])
+def test_sssp_dynamic_root_fetch_covers_every_root(mid, shape, monkeypatch):
+    """QDTA_BF_DYNAMIC: more roots than resident CTAs, handed out by an atomic
+    counter after the first wave; every row bit-exact, in both directions."""
+    net, dem, _, og = mid
+    monkeypatch.setenv("QDTA_BF_DYNAMIC", "1")
+    monkeypatch.setenv("QDTA_BF_SHAPE", shape)
+    g = Q.Graph(net)
+    rng = np.random.default_rng(13)
+    q = (net.fftime_q * rng.uniform(1.0, 3.0, net.n_links)).astype(np.int32)
+    roots = rng.choice(net.n_nodes, 1500, replace=False).astype(np.int32)
+    for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
+        p_o, d_o = oracle.sssp(og, q, roots, direction)
+        p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
+        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
 def test_sssp_large_irregular_graph_with_ties():
     """Above the shared-memory limit with degrees above 4 (so the compressed
     adjacency, not the four-slot one) and many equal-cost ties: bit-exact
