@@ -308,7 +308,7 @@ int qdta_tape_info(const qdta_tape *tape, int32_t *K_out_host, int64_t *n_items_
  * cudaMalloc at the moment they need shortest paths -- for example a process
  * whose device memory is reserved up front by another allocator (a caching
  * pool that holds all free memory, so a fresh cudaMalloc fails), or a
- * latency-critical loop that must not stall in the driver's allocator.
+ * latency-critical loop that must not stall in CUDA's allocator.
  * qdta_sssp_batch, by contrast, grows a workspace with cudaMalloc the first
  * time it sees a larger graph.
  *
