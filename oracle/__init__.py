@@ -51,7 +51,7 @@ class Graph(C.Structure):
 class OD(C.Structure):
     _fields_ = [("n_roots", C.c_int32), ("roots", C.c_void_p), ("n_items", C.c_int64),
                 ("root_idx", C.c_void_p), ("src", C.c_void_p), ("amount_fx", C.c_void_p),
-                ("carry_q", C.c_void_p)]
+                ("carry_q", C.c_void_p), ("carry_link", C.c_void_p)]
 
 
 OBJ_UE, OBJ_SO = 0, 1  # user equilibrium (Beckmann) / system optimum (total cost)
@@ -85,13 +85,13 @@ def _load():
                 "or_fx_to_double": (C.c_double, [C.c_int64, C.c_uint64]),
                 "or_bpr": (C.c_int32, [P, P, C.c_double, P, P]),
                 "or_sssp": (C.c_int32, [P, P, P, C.c_int32, C.c_int32, P, P]),
-                "or_load": (C.c_int32, [P, P, P, P, C.c_int64, C.c_int32, P, P, P]),
+                "or_load": (C.c_int32, [P, P, P, P, C.c_int64, C.c_int32, P, P, P, P]),
                 "or_line_search": (C.c_int32, [P, P, P, C.c_double, C.c_int32, P, P, P]),
                 "or_objective": (C.c_double, [P, P, C.c_double]),
                 "or_slope": (C.c_double, [P, P, P, C.c_double, C.c_double]),
                 "or_assign_interval": (C.c_int32, [P, P, C.c_double, P, P, P, C.c_int32, P, P, P, P]),
                 "or_residual": (C.c_int32, [P, P, C.c_double, C.c_int32, P, P, P, C.c_int32, P, C.c_int64,
-                                            P, P, P, P, P]),
+                                            P, P, P, P, P, P]),
                 "or_run_day": (C.c_int32, [P, C.c_int32, P, C.c_int32, P, P, P, P, C.c_double, P,
                                            P, P, P, P]),
                 "or_backward": (C.c_int32, [P, P, C.c_double, C.c_int32, C.c_int32, P, P, P, P,
@@ -133,18 +133,21 @@ class OracleGraph:
 
 
 class OracleOD:
-    """Items (root_idx, src, amount_fx) over `roots`; carry_q (optional) is the
-    time each trip already travelled beyond src in earlier intervals."""
+    """Items (root_idx, src, amount_fx) over `roots`.  Optionally, carry_link
+    puts an item on a link (src its tail; -1: at src) having travelled
+    carry_q quanta along it."""
 
-    def __init__(self, roots, root_idx, src, amount_fx, carry_q=None):
+    def __init__(self, roots, root_idx, src, amount_fx, carry_q=None, carry_link=None):
         self.roots = np.ascontiguousarray(roots, dtype=np.int32)
         self.root_idx = np.ascontiguousarray(root_idx, dtype=np.int32)
         self.src = np.ascontiguousarray(src, dtype=np.int32)
         self.amount_fx = np.ascontiguousarray(amount_fx, dtype=np.int64)
         self.carry_q = None if carry_q is None else np.ascontiguousarray(carry_q, dtype=np.int64)
+        self.carry_link = None if carry_link is None else np.ascontiguousarray(carry_link, dtype=np.int32)
         self.s = OD(int(self.roots.shape[0]), _p(self.roots).value, int(self.src.shape[0]),
                     _p(self.root_idx).value, _p(self.src).value, _p(self.amount_fx).value,
-                    None if self.carry_q is None else _p(self.carry_q).value)
+                    None if self.carry_q is None else _p(self.carry_q).value,
+                    None if self.carry_link is None else _p(self.carry_link).value)
 
     @classmethod
     def of(cls, dem):
@@ -197,7 +200,8 @@ def sssp(g: OracleGraph, q, roots, direction=DIR_TO_ROOT, want_dist=True):
 
 def load(g: OracleGraph, walk_q, parent, od: OracleOD, dt_q: int, flow_fx=None, truncation=TRUNC_NODE,
          want_carry=False):
-    """Returns (flow_fx, stop nodes, rc), plus the carried times when want_carry."""
+    """Returns (flow_fx, stop nodes, rc), or with want_carry (flow_fx, stop
+    nodes, carried times, carrying links, rc)."""
     walk_q = np.ascontiguousarray(walk_q, dtype=np.int32)
     parent = np.ascontiguousarray(parent, dtype=np.int32)
     if flow_fx is None:
@@ -205,10 +209,11 @@ def load(g: OracleGraph, walk_q, parent, od: OracleOD, dt_q: int, flow_fx=None, 
     n = od.src.shape[0]
     stop = np.empty(max(n, 1), dtype=np.int32)
     carry = np.empty(max(n, 1), dtype=np.int64)
+    link = np.empty(max(n, 1), dtype=np.int32)
     rc = _load().or_load(g.ref(), _p(walk_q), _p(parent), od.ref(), int(dt_q), int(truncation), _p(flow_fx),
-                         _p(stop), _p(carry))
+                         _p(stop), _p(carry), _p(link))
     if want_carry:
-        return flow_fx, stop[:n], carry[:n], rc
+        return flow_fx, stop[:n], carry[:n], link[:n], rc
     return flow_fx, stop[:n], rc
 
 
@@ -273,7 +278,7 @@ def assign_interval(g: OracleGraph, od: OracleOD, dt_s: float, params: Params, t
 
 
 def residual(g: OracleGraph, od: OracleOD, dt_s: float, tape: Tape, f_final, truncation=TRUNC_NODE):
-    """Returns (h_fx, (stop nodes, root indices, amounts, carried times), rc)."""
+    """Returns (h_fx, (stop nodes, root indices, amounts, carried times, carrying links), rc)."""
     K = tape.K.value
     cap = od.src.shape[0] * (K + 1) + 1
     h = np.zeros(g.n_links, dtype=np.int64)
@@ -281,12 +286,14 @@ def residual(g: OracleGraph, od: OracleOD, dt_s: float, tape: Tape, f_final, tru
     rr = np.empty(cap, dtype=np.int32)
     ra = np.empty(cap, dtype=np.int64)
     rcy = np.empty(cap, dtype=np.int64)
+    rl = np.empty(cap, dtype=np.int32)
     n = C.c_int64()
     f_final = np.ascontiguousarray(f_final, dtype=np.float64)
     rc = _load().or_residual(g.ref(), od.ref(), float(dt_s), K, _p(tape.q), _p(tape.alpha),
-                             _p(f_final), int(truncation), _p(h), cap, _p(rs), _p(rr), _p(ra), _p(rcy), C.byref(n))
+                             _p(f_final), int(truncation), _p(h), cap, _p(rs), _p(rr), _p(ra), _p(rcy), _p(rl),
+                             C.byref(n))
     m = n.value
-    return h, (rs[:m].copy(), rr[:m].copy(), ra[:m].copy(), rcy[:m].copy()), rc
+    return h, (rs[:m].copy(), rr[:m].copy(), ra[:m].copy(), rcy[:m].copy(), rl[:m].copy()), rc
 
 
 def run_day(g: OracleGraph, zones, demands, dt_s: float, params: Params):

@@ -67,7 +67,11 @@ typedef struct {
   int64_t n_items;
   const int32_t *root_idx, *src;
   const int64_t *amount_fx;
-  const int64_t *carry_q;  /* nullable: per item, time already travelled beyond src (quanta, >= 0) */
+  /* Trips carried on a link (R17; both nullable): carry_link[k] >= 0 puts
+   * item k on that link (src is its tail) having travelled carry_q[k] quanta
+   * along it; -1 (or NULL) starts the item at src. */
+  const int64_t *carry_q;
+  const int32_t *carry_link;
 } or_od;
 
 typedef struct {
@@ -406,24 +410,40 @@ int32_t or_sssp(const or_graph *g, const int32_t *q, const int32_t *roots, int32
 /* All-or-nothing loading with route truncation (Alg. 3, Eq. 2, Eq. 5).     */
 /* ------------------------------------------------------------------------ */
 
-/* Walk item p -> z along the destination tree.  The elapsed time starts at
- * -carry, carry being the time the trip already travelled beyond p in
- * earlier intervals (0 for a new trip).  Link a is loaded iff the elapsed
- * time on reaching its tail is < dt_q.
+/* Walk item p -> z along the destination tree and load the links it
+ * traverses before dt_q: a link is loaded iff the elapsed time on reaching
+ * its tail is < dt_q.
  *  TRUNC_NODE (R1): the walk stops at the first node whose elapsed time is
- *    >= dt_q (the stop node s), or at z; *carry_out = 0.
+ *    >= dt_q (the stop node s), or at z.
  *  TRUNC_CARRY (R17, the alternative of Section 3.4): a link that would end
- *    after dt_q holds the trip at the end of the interval; the walk stops at
- *    its tail u with *carry_out = dt_q - elapsed(u), the time travelled
- *    beyond u.  A link ending exactly at dt_q is completed.
- * Both modes load the same links.  Returns the stop node, or -1 if z is
+ *    after dt_q holds the trip at the end of the interval; the walk stops on
+ *    that link, *link_out = the link, *carry_out = dt_q - elapsed(tail), the
+ *    time travelled along it (the returned stop node is its tail).  A link
+ *    ending exactly at dt_q is completed.
+ * An item carried on a link (carry_link >= 0, p its tail, carry the time
+ * already travelled on it) first finishes that link: the link is loaded, the
+ * trip reaches its head at max(q - carry, 0), or is still on it after dt_q
+ * (then carry + dt_q is carried on); from the head it follows the tree.
+ * Both rules load the same links.  Returns the stop node, or -1 if z is
  * unreachable from p. */
 static int32_t walk_load(const or_graph *g, const int32_t *walk_q, const int32_t *par,
-                         int32_t p, int32_t z, int64_t dt_q, int64_t carry, int trunc,
-                         int64_t amount, int64_t *flow_fx, int64_t *carry_out) {
+                         int32_t p, int32_t z, int64_t dt_q, int64_t carry, int32_t carry_link, int trunc,
+                         int64_t amount, int64_t *flow_fx, int64_t *carry_out, int32_t *link_out) {
   int32_t u = p;
-  int64_t elapsed = -carry;
+  int64_t elapsed = 0;
   *carry_out = 0;
+  *link_out = -1;
+  if (carry_link >= 0) {
+    if (flow_fx) flow_fx[carry_link] += amount;
+    const int64_t at_head = (int64_t)walk_q[carry_link] - carry;
+    if (at_head > dt_q) {  /* still on the link at the end of this interval */
+      *carry_out = carry + dt_q;
+      *link_out = carry_link;
+      return u;
+    }
+    elapsed = at_head > 0 ? at_head : 0;
+    u = g->head[carry_link];
+  }
   while (u != z) {
     if (elapsed >= dt_q) return u;
     int32_t e = par[u];
@@ -431,6 +451,7 @@ static int32_t walk_load(const or_graph *g, const int32_t *walk_q, const int32_t
     if (flow_fx) flow_fx[e] += amount;
     if (trunc == TRUNC_CARRY && elapsed + walk_q[e] > dt_q) {
       *carry_out = dt_q - elapsed;
+      *link_out = e;
       return u;
     }
     elapsed += walk_q[e];
@@ -441,22 +462,31 @@ static int32_t walk_load(const or_graph *g, const int32_t *walk_q, const int32_t
 
 /* parent: [n_roots * V] destination-rooted trees built with tree_q.
  * walk_q: link times used for the elapsed-time truncation (tree_q for an
- * AON; the final costs for the residual of Alg. 4).  Items start with their
- * od->carry_q (0 when NULL).  stop_out, carry_out (nullable): per-item stop
- * node and carried time under truncation mode `trunc`. */
+ * AON; the final costs for the residual of Alg. 4).  Items carried on a link
+ * (od->carry_link) finish it first.  stop_out, carry_out, link_out
+ * (nullable): per-item stop node, carried time and carrying link (-1 when
+ * the trip waits at the node or arrived) under truncation mode `trunc`. */
+static void item_carry(const or_od *od, int64_t k, int64_t *c, int32_t *l) {
+  *l = od->carry_link ? od->carry_link[k] : -1;
+  *c = (*l >= 0 && od->carry_q) ? od->carry_q[k] : 0;
+}
+
 int32_t or_load(const or_graph *g, const int32_t *walk_q, const int32_t *parent,
                 const or_od *od, int64_t dt_q, int32_t trunc, int64_t *flow_fx, int32_t *stop_out,
-                int64_t *carry_out) {
+                int64_t *carry_out, int32_t *link_out) {
   int64_t V = g->n_nodes;
   int rc = OR_OK;
   for (int64_t k = 0; k < od->n_items; k++) {
     int32_t r = od->root_idx[k];
-    int64_t c = 0;
-    int32_t s = walk_load(g, walk_q, parent + r * V, od->src[k], od->roots[r], dt_q,
-                          od->carry_q ? od->carry_q[k] : 0, trunc, od->amount_fx[k], flow_fx, &c);
+    int64_t c0, c = 0;
+    int32_t l0, l = -1;
+    item_carry(od, k, &c0, &l0);
+    int32_t s = walk_load(g, walk_q, parent + r * V, od->src[k], od->roots[r], dt_q, c0, l0, trunc,
+                          od->amount_fx[k], flow_fx, &c, &l);
     if (s < 0) rc = OR_EUNREACH;
     if (stop_out) stop_out[k] = s;
     if (carry_out) carry_out[k] = c;
+    if (link_out) link_out[k] = l;
   }
   return rc;
 }
@@ -716,7 +746,7 @@ static int aon(const or_graph *g, const adjacency *adj, const int32_t *q, const 
   }
   memset(g_fx, 0, (size_t)g->n_links * 8);
   /* the loaded links do not depend on the truncation mode */
-  return or_load(g, qt, parent, od, dt_q, TRUNC_NODE, g_fx, NULL, NULL);
+  return or_load(g, qt, parent, od, dt_q, TRUNC_NODE, g_fx, NULL, NULL, NULL);
 }
 
 /* routing costs q and travel times qt at flows f: q = qt = quant(c(f)) for the
@@ -878,12 +908,13 @@ static int64_t scale_amount(int64_t amount_fx, double w) {
 /* Re-truncate every path of every accepted AON with the final costs.
  * h_fx[L] receives the truncated link flows h(i); residual entries
  * (stop node, root index, amount, carried time) are written up to res_cap,
- * *res_n gets the number produced (before any merge).  res_carry (nullable)
- * receives the carried times (0 under TRUNC_NODE). */
+ * *res_n gets the number produced (before any merge).  res_carry, res_link
+ * (nullable) receive the carried time and carrying link of each entry (0 and
+ * -1 for a trip waiting at its stop node). */
 int32_t or_residual(const or_graph *g, const or_od *od, double dt_s, int32_t K,
                     const int32_t *tape_q, const double *tape_alpha, const double *f_final,
                     int32_t trunc, int64_t *h_fx, int64_t res_cap, int32_t *res_stop, int32_t *res_root,
-                    int64_t *res_amount, int64_t *res_carry, int64_t *res_n) {
+                    int64_t *res_amount, int64_t *res_carry, int32_t *res_link, int64_t *res_n) {
   int L = g->n_links;
   int64_t V = g->n_nodes;
   int64_t dt_q = dt_quanta(g, dt_s);
@@ -913,14 +944,17 @@ int32_t or_residual(const or_graph *g, const or_od *od, double dt_s, int32_t K,
       int64_t amt = scale_amount(od->amount_fx[k], w[j]);
       if (amt == 0) continue;
       int32_t r = od->root_idx[k];
-      int64_t c = 0;
-      int32_t s = walk_load(g, qfin, parent + r * V, od->src[k], od->roots[r], dt_q,
-                            od->carry_q ? od->carry_q[k] : 0, trunc, amt, h_fx, &c);
+      int64_t c0, c = 0;
+      int32_t l0, l = -1;
+      item_carry(od, k, &c0, &l0);
+      int32_t s = walk_load(g, qfin, parent + r * V, od->src[k], od->roots[r], dt_q, c0, l0, trunc, amt, h_fx,
+                            &c, &l);
       if (s < 0) { rc = OR_EUNREACH; break; }
-      if (s != od->roots[r]) {
+      if (s != od->roots[r] || l >= 0) {
         if (*res_n < res_cap) {
           res_stop[*res_n] = s; res_root[*res_n] = r; res_amount[*res_n] = amt;
           if (res_carry) res_carry[*res_n] = c;
+          if (res_link) res_link[*res_n] = l;
         }
         (*res_n)++;
       }
@@ -935,37 +969,36 @@ done:
 /* Full day (Alg. 1): d(i) = d_o(i) + d_r(i); STA; residual.                */
 /* ------------------------------------------------------------------------ */
 
-typedef struct { int32_t root, src; int64_t amt, carry; } item3;
+typedef struct { int32_t root, src; int64_t amt, carry; int32_t link; } item3;
 
 static int cmp_item3(const void *a, const void *b) {
   const item3 *x = (const item3 *)a, *y = (const item3 *)b;
   if (x->root != y->root) return x->root < y->root ? -1 : 1;
+  if (x->link != y->link) return x->link < y->link ? -1 : 1;
   if (x->src != y->src) return x->src < y->src ? -1 : 1;
-  if ((x->carry > 0) != (y->carry > 0)) return x->carry > 0 ? 1 : -1;
   return 0;
 }
 
-/* merge an item list by (root, src) as the paper's residual demand d_{s,q}
- * is kept, summing amounts; trips that carry a partial link (carry > 0, R17)
- * merge apart from those waiting at the node, and a merged carried item takes
- * the amount-weighted mean carried time, floor(sum amt * carry / sum amt),
- * computed exactly in 128-bit integers; returns the count */
+/* merge an item list as the paper keeps residual demand d_{s,q}: trips
+ * waiting at a node (link -1) by (root, node), summing amounts; trips on a
+ * link (R17) by (root, link), with the amount-weighted mean carried time
+ * floor(sum amt * carry / sum amt) in exact 128-bit integers; returns the
+ * count */
 static int64_t merge_items(item3 *buf, int64_t n) {
   qsort(buf, (size_t)n, sizeof(item3), cmp_item3);
   int64_t m = 0;
   i128 tsum = 0;
   for (int64_t k = 0; k < n; k++) {
-    const int carried = buf[k].carry > 0;
-    if (m > 0 && buf[m - 1].root == buf[k].root && buf[m - 1].src == buf[k].src && (buf[m - 1].carry > 0) == carried) {
+    if (m > 0 && buf[m - 1].root == buf[k].root && buf[m - 1].link == buf[k].link && buf[m - 1].src == buf[k].src) {
       buf[m - 1].amt += buf[k].amt;
     } else {
-      if (m > 0 && buf[m - 1].carry > 0) buf[m - 1].carry = buf[m - 1].amt > 0 ? (int64_t)(tsum / buf[m - 1].amt) : 1;
+      if (m > 0 && buf[m - 1].link >= 0) buf[m - 1].carry = buf[m - 1].amt > 0 ? (int64_t)(tsum / buf[m - 1].amt) : 0;
       buf[m++] = buf[k];
       tsum = 0;
     }
-    if (carried) tsum += (i128)buf[k].amt * buf[k].carry;
+    if (buf[k].link >= 0) tsum += (i128)buf[k].amt * buf[k].carry;
   }
-  if (m > 0 && buf[m - 1].carry > 0) buf[m - 1].carry = buf[m - 1].amt > 0 ? (int64_t)(tsum / buf[m - 1].amt) : 1;
+  if (m > 0 && buf[m - 1].link >= 0) buf[m - 1].carry = buf[m - 1].amt > 0 ? (int64_t)(tsum / buf[m - 1].amt) : 0;
   return m;
 }
 
@@ -998,18 +1031,22 @@ int32_t or_run_day(const or_graph *g, int32_t n_zones, const int32_t *zones, int
       buf[k].root = root_idx[item_off[i] + k]; buf[k].src = src[item_off[i] + k];
       buf[k].amt = amount_fx[item_off[i] + k];
       buf[k].carry = 0;
+      buf[k].link = -1;
     }
     for (int64_t k = 0; k < rn; k++) buf[n0 + k] = resid[k];
     int64_t n = merge_items(buf, n0 + rn);
     int32_t *ri = (int32_t *)malloc((size_t)(n + 1) * 4), *si = (int32_t *)malloc((size_t)(n + 1) * 4);
     int64_t *ai = (int64_t *)malloc((size_t)(n + 1) * 8), *ci = (int64_t *)malloc((size_t)(n + 1) * 8);
-    for (int64_t k = 0; k < n; k++) { ri[k] = buf[k].root; si[k] = buf[k].src; ai[k] = buf[k].amt; ci[k] = buf[k].carry; }
+    int32_t *li = (int32_t *)malloc((size_t)(n + 1) * 4);
+    for (int64_t k = 0; k < n; k++) {
+      ri[k] = buf[k].root; si[k] = buf[k].src; ai[k] = buf[k].amt; ci[k] = buf[k].carry; li[k] = buf[k].link;
+    }
     free(buf);
     n_items_out[i] = n;
-    or_od od = {n_zones, zones, n, ri, si, ai, ci};
+    or_od od = {n_zones, zones, n, ri, si, ai, ci, li};
     int32_t K = 0;
     int r1 = or_assign_interval(g, &od, dt_s, p, f, &stats[i], cap, tq, ta, tf, &K);
-    if (r1 < 0) { rc = r1; free(ri); free(si); free(ai); free(ci); break; }
+    if (r1 < 0) { rc = r1; free(ri); free(si); free(ai); free(ci); free(li); break; }
     if (r1 > 0) rc = r1;
     /* residual: at most one triple per item and accepted AON */
     int64_t need = n * ((int64_t)K + 1);
@@ -1018,14 +1055,16 @@ int32_t or_run_day(const or_graph *g, int32_t n_zones, const int32_t *zones, int
     }
     int32_t *rs = (int32_t *)malloc((size_t)(need + 1) * 4), *rr = (int32_t *)malloc((size_t)(need + 1) * 4);
     int64_t *ra = (int64_t *)malloc((size_t)(need + 1) * 8), *rcy = (int64_t *)malloc((size_t)(need + 1) * 8);
+    int32_t *rl = (int32_t *)malloc((size_t)(need + 1) * 4);
     int64_t got = 0;
-    int r2 = or_residual(g, &od, dt_s, K, tq, ta, f, p->truncation, hfx, need, rs, rr, ra, rcy, &got);
+    int r2 = or_residual(g, &od, dt_s, K, tq, ta, f, p->truncation, hfx, need, rs, rr, ra, rcy, rl, &got);
     for (int64_t k = 0; k < got; k++) {
       resid[k].root = rr[k]; resid[k].src = rs[k]; resid[k].amt = ra[k]; resid[k].carry = rcy[k];
+      resid[k].link = rl[k];
     }
     rn = merge_items(resid, got);
     for (int a = 0; a < L; a++) flows_out[(int64_t)i * L + a] = (double)hfx[a] * 0x1p-32;
-    free(rs); free(rr); free(ra); free(rcy); free(ri); free(si); free(ai); free(ci);
+    free(rs); free(rr); free(ra); free(rcy); free(rl); free(ri); free(si); free(ai); free(ci); free(li);
     if (r2 < 0) { rc = r2; break; }
   }
   *resid_out_n = rn;
@@ -1106,8 +1145,17 @@ int32_t or_backward(const or_graph *g, const or_od *od, double dt_s, int32_t ste
       int32_t r = od->root_idx[it];
       const int32_t *par = parent + r * V;
       int32_t u = od->src[it], z = od->roots[r];
-      int64_t elapsed = od->carry_q ? -od->carry_q[it] : 0;
+      int64_t elapsed = 0, c0;
+      int32_t l0;
       double acc = 0.0;
+      item_carry(od, it, &c0, &l0);
+      if (l0 >= 0) {  /* the carried link first, then on from its head (as walk_load) */
+        acc += gbar[l0];
+        const int64_t at_head = (int64_t)qk[l0] - c0;
+        if (at_head > dt_q) { dL_dd[it] += acc; continue; }
+        elapsed = at_head > 0 ? at_head : 0;
+        u = g->head[l0];
+      }
       while (u != z && elapsed < dt_q) {
         int32_t e = par[u];
         if (e < 0) { rc = OR_EUNREACH; break; }
@@ -1182,16 +1230,16 @@ int32_t or_replay(const or_graph *g, const or_od *od, double dt_s, const or_para
  *  R16 The relative-gap stop takes -1e-12 <= gap <= tol: under truncation a
  *     negative gap certifies nothing (the truncated AON loading need not
  *     minimise sum c g); -1e-12 absorbs rounding at an exact equilibrium.
- *  R17 Carried truncation (Section 3.4 proposes tracking how far a trip got
- *     along a link and adding it up across intervals): a trip whose next
- *     link would end after dt waits at that link's tail u, carrying the time
- *     dt - elapsed(u) it has already travelled beyond u; in the next interval
- *     its elapsed time starts at minus that carry, so a link longer than dt
- *     is crossed over several intervals.  Time (quanta), not a fraction of
- *     the link, is carried: the trip is rerouted from u in the next interval
- *     and may leave u by another link.  Residual demand stays keyed by
- *     (root, node) as the paper's d_{s,q}: carried trips merge apart from
- *     trips waiting at the node, with the amount-weighted mean carried time
- *     (exact merging by carried time grows the items about fourfold per
- *     interval on short intervals, without bound).
+ *  R17 Carried truncation (Section 3.4 proposes tracking how far the flow
+ *     got along a link and adding it up across intervals while it cannot be
+ *     propagated to the next link): a trip whose next link would end after
+ *     dt stays on that link, carrying the time it has travelled along it; in
+ *     the next interval it first finishes that link (reaching the head at
+ *     max(q - carry, 0), or staying on it with carry + dt), then follows the
+ *     tree from the head (rerouted there, as every interval reroutes).  A
+ *     link longer than dt is thus crossed over several intervals.  Residual
+ *     demand keeps the paper's d_{s,q} form: trips at a node merge per
+ *     (root, node); trips on a link per (root, link) with the
+ *     amount-weighted mean carried time (exact merging by carried time
+ *     grows the items about fourfold per interval on short intervals).
  */

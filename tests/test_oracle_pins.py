@@ -443,7 +443,7 @@ def test_residual_conserves_trips_and_matches_flows_without_truncation(small_ins
     p = oracle.make_params(oracle.STEP_SWEEP8, oracle.STOP_REL_GAP, 60, 1e-3)
     for dt in (600.0, 1e9):
         f, st, rc, tape = oracle.assign_interval(g, od, dt, p, tape=True)
-        h, (rs, rr, ra, _), rc2 = oracle.residual(g, od, dt, tape, f)
+        h, (rs, rr, ra, _, _), rc2 = oracle.residual(g, od, dt, tape, f)
         assert rc2 == 0
         K = tape.K.value
         total_in = int(od.amount_fx.sum())
@@ -745,21 +745,47 @@ def test_carried_trips_merge_with_their_mean_carried_time():
 
 
 def test_carried_truncation_stop_node_and_carried_time():
-    """One walk on the same chain from node 0 with a carried time c (time
-    already travelled beyond node 0): after an interval of 300 s the trip is
-    at position t = c + 300 s, i.e. past node floor(t / 1000) by t mod 1000;
-    a trip exactly at a node carries nothing, and one at node 3 has arrived."""
+    """One walk on the uncongested chain of 1000 s links for a trip already at
+    position P seconds from node 0 (on link P // 1000 having travelled
+    P mod 1000 along it, or at the node when that is 0): after an interval of
+    300 s it is at position P + 300, on link (P + 300) // 1000 with carried time
+    (P + 300) mod 1000, at a node when that is 0, and has arrived at node 3
+    when P + 300 >= 3000."""
     net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
     g = oracle.OracleGraph(net)
     par, _ = oracle.sssp(g, net.fftime_q, np.array([3], np.int32), want_dist=False)
-    for c_s in (0, 100, 600, 700, 900, 1000, 1750, 2700, 2850):
-        od = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([0], np.int32),
-                             np.array([1 << 32], np.int64), carry_q=np.array([c_s * 100], np.int64))
-        _, stop, carry, rc = oracle.load(g, net.fftime_q, par, od, 30000, truncation=oracle.TRUNC_CARRY,
-                                         want_carry=True)
-        t = c_s + 300
-        node, rem = (3, 0) if t >= 3000 else divmod(t, 1000)
-        assert rc == 0 and (stop[0], carry[0]) == (node, rem * 100), (c_s, stop[0], carry[0])
+    for pos in (0, 100, 600, 700, 900, 1000, 1750, 2700, 2850):
+        node, along = divmod(pos, 1000)
+        od = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([node], np.int32),
+                             np.array([1 << 32], np.int64), carry_q=np.array([along * 100], np.int64),
+                             carry_link=np.array([node if along else -1], np.int32))
+        _, stop, carry, link, rc = oracle.load(g, net.fftime_q, par, od, 30000, truncation=oracle.TRUNC_CARRY,
+                                               want_carry=True)
+        t = pos + 300
+        want = (3, 0, -1) if t >= 3000 else (t // 1000, (t % 1000) * 100, (t // 1000) if t % 1000 else -1)
+        assert rc == 0 and (stop[0], carry[0], link[0]) == want, (pos, stop[0], carry[0], link[0])
+
+
+def test_carried_trip_finishes_its_link_before_rerouting():
+    """A trip carried on link 0->2 of the diamond (routes 0->1->3 and
+    0->2->3) stays on it although the tree from node 0 leads through node 1:
+    it loads 0->2, then follows the tree from node 2.  The same trip waiting
+    at node 0 instead (no carry) takes 0->1."""
+    net = _diamond([200, 340, 1000, 400], [1e9, 1e9, 1e9, 1e9])  # links 0->1, 0->2, 1->3, 2->3
+    g = oracle.OracleGraph(net)
+    q = np.array([20000, 90000, 20000, 20000], np.int32)  # 0->1->3 is shorter than 0->2->3
+    par, _ = oracle.sssp(g, q, np.array([3], np.int32), want_dist=False)
+    assert par[0][0] == 0  # the tree leaves node 0 by link 0->1
+    on = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([0], np.int32),
+                         np.array([1 << 32], np.int64), carry_q=np.array([60000], np.int64),
+                         carry_link=np.array([1], np.int32))
+    f, stop, carry, link, rc = oracle.load(g, q, par, on, 90000, truncation=oracle.TRUNC_CARRY, want_carry=True)
+    # 300 s left on 0->2 (reaching node 2 at 300 s), then 200 s on 2->3: arrived at 500 s
+    assert rc == 0 and list(f >> 32) == [0, 1, 0, 1] and (stop[0], carry[0], link[0]) == (3, 0, -1)
+    at = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([0], np.int32),
+                         np.array([1 << 32], np.int64))
+    f, stop, rc = oracle.load(g, q, par, at, 90000, truncation=oracle.TRUNC_CARRY)
+    assert list(f >> 32) == [1, 0, 1, 0] and stop[0] == 3
 
 
 def test_carried_truncation_loads_the_links_of_the_node_rule():
