@@ -75,11 +75,11 @@ extern "C" {
  *  QDTA_TRUNC_NODE: the trip waits at the first node whose elapsed time is
  *    >= dt (it may overshoot dt by up to one link).
  *  QDTA_TRUNC_CARRY: Section 3.4's alternative -- a trip whose next link
- *    would end after dt waits at that link's tail u, carrying the time
- *    dt - elapsed(u) it already travelled beyond u; in the next interval its
- *    elapsed time starts at minus that carry, so a link longer than dt is
- *    crossed over several intervals.  Residual demand stays keyed by
- *    (root, node): carried trips merge apart from those waiting at the node,
+ *    would end after dt stays on that link, carrying the time it travelled
+ *    along it; in the next interval it first finishes the link (reaching its
+ *    head at max(q - carry, 0) quanta, or staying on it with carry + dt) and
+ *    is rerouted from the head.  A link longer than dt is crossed over
+ *    several intervals.  Residual trips on a link merge per (root, link)
  *    with the amount-weighted mean carried time (floor, exact integers). */
 #define QDTA_TRUNC_NODE 0
 #define QDTA_TRUNC_CARRY 1
@@ -116,9 +116,12 @@ typedef struct {
   const int32_t *root_idx;   /* [n_items] in [0, n_roots) */
   const int32_t *src;        /* [n_items] origin nodes */
   const int64_t *amount_fx;  /* [n_items] >= 0 */
-  const int64_t *carry_q;    /* [n_items] or NULL (all 0): time each trip already travelled beyond
-                                src in earlier intervals, quanta >= 0 (QDTA_TRUNC_CARRY residuals);
-                                its elapsed time starts at -carry_q */
+  /* Trips carried on a link (QDTA_TRUNC_CARRY residuals; both nullable):
+   * carry_link[k] >= 0 puts item k on that link, whose tail must be src[k],
+   * having travelled carry_q[k] >= 0 quanta along it; -1 (or NULL) starts
+   * the item at src[k]. */
+  const int64_t *carry_q;
+  const int32_t *carry_link;
 } qdta_od;
 
 typedef struct {
@@ -154,7 +157,8 @@ typedef struct {
   int32_t *src;        /* [capacity] stop node s, the new origin */
   int64_t *amount_fx;  /* [capacity] */
   int64_t count;       /* written by the library (host field): entries produced */
-  int64_t *carry_q;    /* [capacity] carried times; required with QDTA_TRUNC_CARRY, else NULL or zeros */
+  int64_t *carry_q;    /* [capacity] carried times (0 at a node); required with QDTA_TRUNC_CARRY */
+  int32_t *carry_link; /* [capacity] carrying link, -1 at a node; required with QDTA_TRUNC_CARRY */
 } qdta_residual;
 
 /* Per-kernel CUDA-event timings accumulated while profiling is enabled

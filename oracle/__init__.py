@@ -93,7 +93,7 @@ def _load():
                 "or_residual": (C.c_int32, [P, P, C.c_double, C.c_int32, P, P, P, C.c_int32, P, C.c_int64,
                                             P, P, P, P, P, P]),
                 "or_run_day": (C.c_int32, [P, C.c_int32, P, C.c_int32, P, P, P, P, C.c_double, P,
-                                           P, P, P, P]),
+                                           P, P, P, P, C.c_int64, P, P, P, P, P]),
                 "or_backward": (C.c_int32, [P, P, C.c_double, C.c_int32, C.c_int32, P, P, P, P,
                                             P, P]),
                 "or_replay": (C.c_int32, [P, P, C.c_double, P, C.c_int32, P, P]),
@@ -296,7 +296,11 @@ def residual(g: OracleGraph, od: OracleOD, dt_s: float, tape: Tape, f_final, tru
     return h, (rs[:m].copy(), rr[:m].copy(), ra[:m].copy(), rcy[:m].copy(), rl[:m].copy()), rc
 
 
-def run_day(g: OracleGraph, zones, demands, dt_s: float, params: Params):
+def run_day(g: OracleGraph, zones, demands, dt_s: float, params: Params, want_resid=False):
+    """Returns (flows [N, L], stats, merged item counts, residual count, rc);
+    with want_resid a sixth entry, the residual left after the last interval
+    as arrays (root index, src, amount_fx, carried time, link), sorted by
+    root, link, src."""
     zones = np.ascontiguousarray(zones, dtype=np.int32)
     N = len(demands)
     off = np.zeros(N + 1, dtype=np.int64)
@@ -309,9 +313,18 @@ def run_day(g: OracleGraph, zones, demands, dt_s: float, params: Params):
     stats = (Stats * N)()
     nit = np.zeros(N, dtype=np.int64)
     rn = C.c_int64()
+    # distinct residual keys: (root, node) and (root, link)
+    cap = int(zones.shape[0]) * (g.n_nodes + g.n_links) if want_resid else 0
+    rr = np.zeros(cap, dtype=np.int32); rs = np.zeros(cap, dtype=np.int32)
+    ra = np.zeros(cap, dtype=np.int64); rcy = np.zeros(cap, dtype=np.int64); rl = np.zeros(cap, dtype=np.int32)
+    out = [_p(a) for a in (rr, rs, ra, rcy, rl)] if want_resid else [None] * 5
     rc = _load().or_run_day(g.ref(), zones.shape[0], _p(zones), N, _p(off), _p(ri), _p(si), _p(ai),
-                            float(dt_s), C.byref(params), _p(flows), stats, _p(nit), C.byref(rn))
-    return flows.reshape(N, g.n_links), [s.as_dict() for s in stats], nit, rn.value, rc
+                            float(dt_s), C.byref(params), _p(flows), stats, _p(nit), C.byref(rn), cap, *out)
+    res = (flows.reshape(N, g.n_links), [s.as_dict() for s in stats], nit, rn.value, rc)
+    if want_resid:
+        m = min(rn.value, cap)
+        res += ((rr[:m], rs[:m], ra[:m], rcy[:m], rl[:m]),)
+    return res
 
 
 def backward(g: OracleGraph, od: OracleOD, dt_s: float, step_mode: int, tape: Tape, dL_df):

@@ -1006,12 +1006,15 @@ static int64_t merge_items(item3 *buf, int64_t n) {
  * interval).  Interval i's original items are [item_off[i], item_off[i+1])
  * of (root_idx, src, amount_fx).  flows_out [N * L] receives h(i) (trips);
  * stats [N]; n_items_out [N] the merged item count of each interval;
- * resid_out_n receives the residual items left after the last interval. */
+ * resid_out_n receives the count of residual items left after the last
+ * interval (merged, sorted by root, link, src); the first res_cap of them
+ * go to res_root/src/amt/carry/link when res_root is not NULL. */
 int32_t or_run_day(const or_graph *g, int32_t n_zones, const int32_t *zones, int32_t N,
                    const int64_t *item_off, const int32_t *root_idx, const int32_t *src,
                    const int64_t *amount_fx, double dt_s, const or_params *p,
                    double *flows_out, or_stats *stats, int64_t *n_items_out,
-                   int64_t *resid_out_n) {
+                   int64_t *resid_out_n, int64_t res_cap, int32_t *res_root, int32_t *res_src,
+                   int64_t *res_amt, int64_t *res_carry, int32_t *res_link) {
   int L = g->n_links;
   int rc = OR_OK;
   int cap = p->max_iter + 2;
@@ -1068,6 +1071,10 @@ int32_t or_run_day(const or_graph *g, int32_t n_zones, const int32_t *zones, int
     if (r2 < 0) { rc = r2; break; }
   }
   *resid_out_n = rn;
+  for (int64_t k = 0; res_root && k < rn && k < res_cap; k++) {
+    res_root[k] = resid[k].root; res_src[k] = resid[k].src; res_amt[k] = resid[k].amt;
+    res_carry[k] = resid[k].carry; res_link[k] = resid[k].link;
+  }
 done:
   free(resid); free(tq); free(ta); free(tf); free(f); free(hfx);
   return rc;

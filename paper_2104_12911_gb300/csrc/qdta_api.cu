@@ -1120,6 +1120,8 @@ extern "C" int qdta_interval_metrics(qdta_graph *g, const double *flows, int32_t
   return status_check(g, s);
 }
 
+static int check_carry_items(qdta_graph *g, const qdta_od *od, cudaStream_t s);
+
 extern "C" int qdta_load_aon(qdta_graph *g, const int32_t *cost_q, const int32_t *parent_link,
                              const qdta_od *od, int64_t dt_q, int64_t *flow_fx, int32_t *stop_node,
                              void *stream) {
@@ -1132,6 +1134,7 @@ extern "C" int qdta_load_aon(qdta_graph *g, const int32_t *cost_q, const int32_t
   if (dt_q < 0) return fail(QDTA_EINVAL, "dt_q must be >= 0");
   DevGuard guard(g->device);
   cudaStream_t s = (cudaStream_t)stream;
+  RC(check_carry_items(g, od, s));
   RC(status_reset(g, s));
   int2 *hq;
   RC(ws_get(g, "load.head_q", (size_t)g->d.L, &hq));
@@ -1140,7 +1143,7 @@ extern "C" int qdta_load_aon(qdta_graph *g, const int32_t *cost_q, const int32_t
   prof_begin(g, s, &pe, 1, 0);
   launch_load(g->d, hq, parent_link, nullptr, 0, nullptr, od->roots, od->n_items, nullptr, od->root_idx,
               od->src, (const long long *)od->amount_fx, dt_q, (unsigned long long *)flow_fx,
-              stop_node, g->status, s, (const long long *)od->carry_q);
+              stop_node, g->status, s, (const long long *)od->carry_q, od->carry_link);
   prof_end(g, s, &pe);
   return status_check(g, s);
 }
@@ -1177,7 +1180,9 @@ struct Solver {
   const long long *n_dev;
   const int *root_idx, *src;
   const long long *amount;
-  const long long *carry = nullptr;  // per item, time already travelled beyond src (nullable)
+  // per item (nullable): the link carrying the trip (-1: none) and the time travelled along it
+  const long long *carry = nullptr;
+  const int *carry_link = nullptr;
   // link state
   int *q;
   unsigned long long *g_fx;
@@ -1247,7 +1252,8 @@ static int seg_aon(Solver &S, const int *slot_dev, bool gather_ff = false) {
   ProfEvent pe;
   prof_begin(g, S.s, &pe, 1, 0);
   launch_load(g->d, S.head_q, S.parent, slot_dev, S.parent_stride, S.root_slot, S.item_roots, S.n_host,
-              S.n_dev, S.root_idx, S.src, S.amount, S.dt_q, S.g_fx, nullptr, g->status, S.s, S.carry);
+              S.n_dev, S.root_idx, S.src, S.amount, S.dt_q, S.g_fx, nullptr, g->status, S.s, S.carry,
+              S.carry_link);
   prof_end(g, S.s, &pe);
   return QDTA_OK;
 }
@@ -1440,6 +1446,15 @@ static int check_od(const qdta_graph *g, const qdta_od *od) {
   return QDTA_OK;
 }
 
+// items carried on a link, checked on the device: the link exists, its
+// tail is the item's src, the carried time is >= 0 (QDTA_EINVAL otherwise)
+static int check_carry_items(qdta_graph *g, const qdta_od *od, cudaStream_t s) {
+  if (!od || !od->carry_link || od->n_items <= 0) return QDTA_OK;
+  RC(status_reset(g, s));
+  launch_check_carry(g->d, od->n_items, od->src, (const long long *)od->carry_q, od->carry_link, g->status, s);
+  return status_check(g, s);
+}
+
 extern "C" int qdta_line_search(qdta_graph *g, const double *flow, const int64_t *aon_fx, double dt_s,
                                 int32_t fw_iter, const qdta_params *p, double *alpha_out,
                                 int32_t *passes_out, void *stream) {
@@ -1497,6 +1512,7 @@ static int assign_core(qdta_graph *g, const qdta_od *od, double dt_s, const qdta
   S.n_host = od->n_items; S.n_dev = nullptr;
   S.root_idx = od->root_idx; S.src = od->src; S.amount = (const long long *)od->amount_fx;
   S.carry = (const long long *)od->carry_q;
+  S.carry_link = od->carry_link;
   S.f = flow_out;
   const bool want_tape = p->record_tape && tape_out;
   if (want_tape && p->objective == QDTA_OBJ_SO)
@@ -1538,6 +1554,7 @@ extern "C" int qdta_assign_interval(qdta_graph *g, const qdta_od *od, double dt_
   if (g->d.L > 0 && !flow_out) return fail(QDTA_EINVAL, "flow_out is NULL");
   if (tape_out) *tape_out = nullptr;
   DevGuard guard(g->device);
+  RC(check_carry_items(g, od, (cudaStream_t)stream));
   return assign_core(g, od, dt_s, p, flow_out, stats, tape_out, (cudaStream_t)stream, "fw");
 }
 
@@ -1561,6 +1578,7 @@ static int assign_batch_graph(const qdta_instance *inst, int n, const qdta_param
     X.n_host = od->n_items; X.n_dev = nullptr;
     X.root_idx = od->root_idx; X.src = od->src; X.amount = (const long long *)od->amount_fx;
     X.carry = (const long long *)od->carry_q;
+    X.carry_link = od->carry_link;
     X.f = inst[i].flow_out;
     RC(solver_alloc(X, "batch", 1, false));
     RC(status_reset(g, s));
@@ -1626,6 +1644,7 @@ extern "C" int qdta_assign_batch(const qdta_instance *inst, int32_t n_inst, cons
   }
   if (n_inst == 0) return QDTA_OK;
   DevGuard guard(inst[0].graph->device);
+  for (int i = 0; i < n_inst; ++i) RC(check_carry_items(inst[i].graph, &inst[i].od, s));
   if (p->schedule == QDTA_SCHEDULE_GRAPH && !inst[0].graph->prof_on)
     return assign_batch_graph(inst, n_inst, p, stats, s);
   int worst = QDTA_OK;
@@ -1651,8 +1670,9 @@ struct Day {
   long long cap_items;
   int *it_root, *it_src;
   long long *it_amt;
-  long long *it_carry;         // carried times of the items (carried trips in play), else NULL
-  CarryAcc ca;                 // carried accumulator (amt NULL: none)
+  long long *it_carry;         // items' carried times and links (carried trips in play), else NULL
+  int *it_link;
+  CarryAcc ca;                 // carried (root, link) table (mask 0: none)
   int trunc;                   // QDTA_TRUNC_*
   long long *n_items_dev;
   int *flag, *active, *root_slot, *n_active;
@@ -1670,7 +1690,7 @@ static int day_merge(Day &D) {
   cudaStream_t s = D.S.s;
   launch_scatter_orig(g->d, D.S.ctl, D.tab, D.max_orig, D.dense, s, D.ca, g->status);
   launch_compact(g->d, D.Z, D.dense, D.blk_count, D.blk_off, D.cap_items, D.it_root, D.it_src, D.it_amt,
-                 D.n_items_dev, g->status, s, D.it_carry, D.ca);
+                 D.n_items_dev, g->status, s, D.it_carry, D.it_link, D.ca);
   launch_active_roots(D.Z, D.n_items_dev, D.cap_items, D.it_root, D.zones, D.flag, D.active, D.root_slot,
                       D.n_active, s);
   return QDTA_OK;
@@ -1707,7 +1727,7 @@ static int day_res_body(Day &D, unsigned long long h, int use_cond) {
               S.parent_stride, nullptr, s, &S.ctl->res_skip, real_batch));
   launch_residual(g->d, D.hq_fin, S.parent, &S.ctl->res_slot, S.parent_stride, D.root_slot, D.zones,
                   D.n_items_dev, D.cap_items, D.it_root, D.it_src, D.it_amt, &S.ctl->w_cur, S.dt_q, D.h_fx,
-                  D.dense, g->status, s, D.it_carry, D.trunc, D.ca);
+                  D.dense, g->status, s, D.it_carry, D.it_link, D.trunc, D.ca);
   launch_res_next(S.ctl, h, use_cond, s);
   return QDTA_OK;
 }
@@ -1814,13 +1834,15 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
     RC(check_od(g, resid_in));
     if (resid_in->n_items > 0 && resid_in->n_roots != Z) return fail(QDTA_EINVAL, "resid_in must use the zone list");
   }
-  // carried times in play: the carried-time table and per-item carries
-  bool any_carry = p->truncation == QDTA_TRUNC_CARRY || (resid_in && resid_in->carry_q);
-  for (int i = 0; i < N; ++i) any_carry = any_carry || d_orig[i].carry_q != nullptr;
-  if (any_carry && resid_out && !resid_out->carry_q)
-    return fail(QDTA_EINVAL, "resid_out->carry_q is needed when trips carry partial links");
+  // trips on links in play: the carried (root, link) table and per-item carries
+  bool any_carry = p->truncation == QDTA_TRUNC_CARRY || (resid_in && resid_in->carry_link);
+  for (int i = 0; i < N; ++i) any_carry = any_carry || d_orig[i].carry_link != nullptr;
+  if (any_carry && resid_out && (!resid_out->carry_q || !resid_out->carry_link))
+    return fail(QDTA_EINVAL, "resid_out->carry_q and carry_link are needed when trips are carried on links");
   DevGuard guard(g->device);
   cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < N; ++i) RC(check_carry_items(g, &d_orig[i], s));
+  if (resid_in) RC(check_carry_items(g, resid_in, s));
   const size_t V = g->d.V, L = g->d.L;
   Day D{};
   Solver &S = D.S;
@@ -1831,9 +1853,6 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   D.zones = d_orig[0].roots;
   const long long dense_n = (long long)Z * (long long)V;
   RC(ws_get(g, "day.dense", (size_t)dense_n, &D.dense));
-  const int nblk = (int)((dense_n + 4095) / 4096);
-  RC(ws_get(g, "day.blk_count", (size_t)nblk, &D.blk_count));
-  RC(ws_get(g, "day.blk_off", (size_t)nblk, &D.blk_off));
   long long max_orig = resid_in ? resid_in->n_items : 0;
   for (int i = 0; i < N; ++i) max_orig = d_orig[i].n_items > max_orig ? d_orig[i].n_items : max_orig;
   D.max_orig = max_orig;
@@ -1841,16 +1860,31 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   D.trunc = p->truncation;
   D.ca = CarryAcc{};
   D.it_carry = nullptr;
+  D.it_link = nullptr;
+  long long table_n = 0;
   if (any_carry) {
-    // carried trips: a second (root, node) accumulator of amounts and exact
-    // 128-bit sums of amount x carried time; items get room for both parts
-    RC(ws_get(g, "day.carry_amt", (size_t)dense_n, &D.ca.amt));
-    RC(ws_get(g, "day.carry_tsum", (size_t)dense_n * 2, &D.ca.tsum));
-    CK(cudaMemsetAsync(D.ca.amt, 0, (size_t)dense_n * 8, s));
-    CK(cudaMemsetAsync(D.ca.tsum, 0, (size_t)dense_n * 16, s));
+    // trips on links: an open-addressed (root, link) table of amounts and
+    // exact 128-bit sums of amount x carried time, at most half full when
+    // it holds as many entries as the dense part can; items get room for both
+    const long long zl = (long long)Z * (long long)L;
+    const long long want = 2 * (D.cap_items < zl ? D.cap_items : zl);
+    table_n = 1024;
+    while (table_n < want) table_n <<= 1;
+    D.ca.mask = (unsigned long long)(table_n - 1);
+    RC(ws_get(g, "day.carry_key", (size_t)table_n, &D.ca.key));
+    RC(ws_get(g, "day.carry_amt", (size_t)table_n, &D.ca.amt));
+    RC(ws_get(g, "day.carry_tsum", (size_t)table_n * 2, &D.ca.tsum));
+    CK(cudaMemsetAsync(D.ca.key, 0xff, (size_t)table_n * 8, s));
+    CK(cudaMemsetAsync(D.ca.amt, 0, (size_t)table_n * 8, s));
+    CK(cudaMemsetAsync(D.ca.tsum, 0, (size_t)table_n * 16, s));
     D.cap_items *= 2;
     RC(ws_get(g, "day.it_carry", (size_t)D.cap_items, &D.it_carry));
+    RC(ws_get(g, "day.it_link", (size_t)D.cap_items, &D.it_link));
   }
+  const long long scan_n = dense_n > table_n ? dense_n : table_n;
+  const int nblk = (int)((scan_n + 4095) / 4096);
+  RC(ws_get(g, "day.blk_count", (size_t)nblk, &D.blk_count));
+  RC(ws_get(g, "day.blk_off", (size_t)nblk, &D.blk_off));
   RC(ws_get(g, "day.it_root", (size_t)D.cap_items, &D.it_root));
   RC(ws_get(g, "day.it_src", (size_t)D.cap_items, &D.it_src));
   RC(ws_get(g, "day.it_amt", (size_t)D.cap_items, &D.it_amt));
@@ -1869,7 +1903,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   std::vector<OrigTable> tab(N);
   for (int i = 0; i < N; ++i)
     tab[i] = OrigTable{d_orig[i].root_idx, d_orig[i].src, (const long long *)d_orig[i].amount_fx,
-                       d_orig[i].n_items, (const long long *)d_orig[i].carry_q};
+                       d_orig[i].n_items, (const long long *)d_orig[i].carry_q, d_orig[i].carry_link};
   RC(ws_get(g, "day.tab", (size_t)N, &D.tab));
   CK(cudaMemcpyAsync(D.tab, tab.data(), sizeof(OrigTable) * N, cudaMemcpyHostToDevice, s));
   // solver over the zone list
@@ -1878,6 +1912,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   S.n_host = 0; S.n_dev = D.n_items_dev;
   S.root_idx = D.it_root; S.src = D.it_src; S.amount = D.it_amt;
   S.carry = D.it_carry;
+  S.carry_link = D.it_link;
   RC(ws_get(g, "day.f", L, &S.f));
   // parent ring: keep every tree of an interval when memory allows.  The
   // ring this handle already holds counts as available (a later day must
@@ -1922,7 +1957,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   if (resid_in && resid_in->n_items > 0)
     launch_scatter_items(g->d, resid_in->n_items, resid_in->root_idx, resid_in->src,
                          (const long long *)resid_in->amount_fx, D.dense, s,
-                         (const long long *)resid_in->carry_q, D.ca, g->status);
+                         (const long long *)resid_in->carry_q, resid_in->carry_link, D.ca, g->status);
   // day counter lives in the solver's controller
   int dayinit[3] = {0, N, 1};
   CK(cudaMemcpyAsync(&S.ctl->day_i, dayinit, sizeof dayinit, cudaMemcpyHostToDevice, s));
@@ -1944,16 +1979,17 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   if (resid_out) {
     launch_compact(g->d, Z, D.dense, D.blk_count, D.blk_off, resid_out->capacity, resid_out->root_idx,
                    resid_out->src, (long long *)resid_out->amount_fx, D.n_items_dev, g->status, s,
-                   (long long *)resid_out->carry_q, D.ca);
+                   (long long *)resid_out->carry_q, resid_out->carry_link, D.ca);
     long long cnt = 0;
     CK(cudaMemcpyAsync(&cnt, D.n_items_dev, 8, cudaMemcpyDeviceToHost, s));
     RC(status_check(g, s));
     resid_out->count = cnt;
   } else {
     CK(cudaMemsetAsync(D.dense, 0, (size_t)dense_n * 8, s));
-    if (D.ca.amt) {
-      CK(cudaMemsetAsync(D.ca.amt, 0, (size_t)dense_n * 8, s));
-      CK(cudaMemsetAsync(D.ca.tsum, 0, (size_t)dense_n * 16, s));
+    if (D.ca.mask) {
+      CK(cudaMemsetAsync(D.ca.key, 0xff, (size_t)table_n * 8, s));
+      CK(cudaMemsetAsync(D.ca.amt, 0, (size_t)table_n * 8, s));
+      CK(cudaMemsetAsync(D.ca.tsum, 0, (size_t)table_n * 16, s));
     }
   }
   (void)worst;
@@ -2026,7 +2062,7 @@ extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_dd
     CK(cudaMemsetAsync(gfx, 0, L * 8, s));
     launch_load(g->d, hq, parent, nullptr, 0, nullptr, t->od.roots, n, nullptr, t->od.root_idx, t->od.src,
                 (const long long *)t->od.amount_fx, dt_q, gfx, nullptr, g->status, s,
-                (const long long *)t->od.carry_q);
+                (const long long *)t->od.carry_q, t->od.carry_link);
     const double *gb = lam;
     if (k > 0) {
       const double *fprev = t->f + (size_t)(k - 1) * L;
@@ -2037,7 +2073,7 @@ extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_dd
       gb = gbar;
     }
     launch_gather(g->d, hq, parent, t->od.roots, n, t->od.root_idx, t->od.src, dt_q, gb, dL_ddemand,
-                  g->status, s, (const long long *)t->od.carry_q);
+                  g->status, s, (const long long *)t->od.carry_q, t->od.carry_link);
     if (k > 0) std::swap(lam, lam2);
   }
   return status_check(g, s);

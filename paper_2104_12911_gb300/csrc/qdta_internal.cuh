@@ -367,37 +367,46 @@ long long launch_count();
 void launch_set_cond(const Ctl *ctl, int which, unsigned long long cond, cudaStream_t s);
 int sssp_blocks_per_sm(bool use_smem, int V);
 
-// Residual trips that carry a partial link (QDTA_TRUNC_CARRY) merge per
-// (root, node), apart from the trips waiting at the node: their amount and
-// the exact sum of amount x carried time (two 64-bit words, low then high)
-// per entry root * V + node; the merged item carries the floor of the mean.
-// amt == NULL: no carried trips (QDTA_TRUNC_NODE).
+// Residual trips on a link (QDTA_TRUNC_CARRY) merge per (root, link) in an
+// open-addressed table: key root * L + link (~0 when empty), the amount, and
+// the exact sum of amount x carried time (two 64-bit words, low then high);
+// the merged item carries the floor of the mean.  mask == 0: no table.
 struct CarryAcc {
-  unsigned long long *amt = nullptr;   // [R * V]
-  unsigned long long *tsum = nullptr;  // [2 * R * V]
+  unsigned long long *key = nullptr;   // [mask + 1]
+  unsigned long long *amt = nullptr;   // [mask + 1]
+  unsigned long long *tsum = nullptr;  // [2 * (mask + 1)]
+  unsigned long long mask = 0;
 };
 
 void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStream_t s);
-// carry [n] (nullable): per item, time already travelled beyond src (the walk starts at -carry)
+// carry, carry_link [n] (nullable): an item with carry_link >= 0 is on that
+// link having travelled carry quanta; it finishes the link, then follows its tree
 void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const int *parent_slot_dev,
                  long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
                  const long long *n_items_dev, const int *root_idx, const int *src,
                  const long long *amount, long long dt_q, unsigned long long *flow_fx, int *stop_out,
-                 unsigned *status, cudaStream_t s, const long long *carry = nullptr);
-// trunc 1 (carry): a trip stopping inside a link goes to the carried
-// accumulator `ca` with its carried time; trips stopping at a node go to `dense`
+                 unsigned *status, cudaStream_t s, const long long *carry = nullptr,
+                 const int *carry_link = nullptr);
+// trunc 1 (carry): a trip still on a link at the end of the interval goes
+// to the carried table `ca` with its carried time; trips stopping at a node
+// go to `dense`
 void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *parent,
                      const int *parent_slot_dev, long long slot_stride, const int *root_slot,
                      const int *roots, const long long *n_items_dev, long long n_items_cap,
                      const int *root_idx, const int *src, const long long *amount,
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
                      unsigned long long *dense, unsigned *status, cudaStream_t s,
-                     const long long *carry = nullptr, int trunc = 0, CarryAcc ca = CarryAcc{});
+                     const long long *carry = nullptr, const int *carry_link = nullptr, int trunc = 0,
+                     CarryAcc ca = CarryAcc{});
 
 // marginal = 1: the system optimum's marginal costs instead of link times
 void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,
                 unsigned *status, cudaStream_t s, int marginal = 0);
 void launch_link_const(const GraphDev &g, double dt_h, LinkConst *kc, cudaStream_t s);
+// ST_BADARG unless every item with carry_link >= 0 names a link whose tail
+// is its src and carries a time >= 0 (carry nullable)
+void launch_check_carry(const GraphDev &g, long long n, const int *src, const long long *carry,
+                        const int *carry_link, unsigned *status, cudaStream_t s);
 // replace the graph's capacities by `cap` (device) when every value is finite
 // and > 0; otherwise set ST_BADARG and leave them unchanged
 void launch_set_capacity(const GraphDev &g, const double *cap, unsigned *status, cudaStream_t s);
@@ -422,7 +431,10 @@ void launch_store_interval(const GraphDev &g, const Ctl *ctl, const unsigned lon
                            double *flow_out_rows, void *stats_rows, const long long *n_items_dev,
                            cudaStream_t s);
 void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream_t s);
-struct OrigTable { const int *root_idx; const int *src; const long long *amount; long long n; const long long *carry; };
+struct OrigTable {
+  const int *root_idx; const int *src; const long long *amount; long long n;
+  const long long *carry; const int *carry_link;  // nullable: items on a link
+};
 void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab, long long max_n,
                          unsigned long long *dense, cudaStream_t s, CarryAcc ca = CarryAcc{},
                          unsigned *status = nullptr);
@@ -432,20 +444,22 @@ void launch_ctl_end(Ctl *ctl, unsigned long long cond_fw, int use_cond, cudaStre
 void launch_tape_record(const GraphDev &g, const Ctl *ctl, const int *q, const double *f,
                         int *tape_q, double *tape_alpha, double *tape_f, int cap, cudaStream_t s);
 
-// items with carry > 0 go to the carried accumulator `ca` (which must exist then)
+// items on a link (carry_link >= 0) go to the carried table `ca` (which must exist then)
 void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, const int *src,
                           const long long *amount, unsigned long long *dense, cudaStream_t s,
-                          const long long *carry = nullptr, CarryAcc ca = CarryAcc{},
-                          unsigned *status = nullptr);
+                          const long long *carry = nullptr, const int *carry_link = nullptr,
+                          CarryAcc ca = CarryAcc{}, unsigned *status = nullptr);
 // dense (root, node) accumulator -> items in (root, node) order, then (when
-// ca.amt is set) the carried accumulator's entries appended in (root, node)
-// order with their mean carried times; carry_out (nullable) receives each
-// item's carried time (0 for the first part).  Both sources are cleared; the
-// item count never exceeds cap (ST_CAPACITY when entries were dropped).
+// ca.mask is set) the carried table's entries appended in slot order with
+// their mean carried times and links (src = the link's tail); carry_out and
+// link_out (nullable) receive each item's carried time and link (0 and -1
+// for the first part).  Both sources are cleared; the item count never
+// exceeds cap (ST_CAPACITY when entries were dropped).  blk_count / blk_off
+// must hold max(R * V, ca.mask + 1) / 4096 + 1 entries.
 void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *blk_count,
                     long long *blk_off, long long cap, int *root_idx, int *src, long long *amount,
                     long long *n_out_dev, unsigned *status, cudaStream_t s, long long *carry_out = nullptr,
-                    CarryAcc ca = CarryAcc{});
+                    int *link_out = nullptr, CarryAcc ca = CarryAcc{});
 void launch_active_roots(int R, const long long *n_items_dev, long long cap_items,
                          const int *root_idx, const int *zone_nodes, int *flag, int *active_roots,
                          int *root_slot, int *n_active_dev, cudaStream_t s);
@@ -464,6 +478,6 @@ void launch_adj_update(const GraphDev &g, const LinkConst *kc, const double *lam
 void launch_gather(const GraphDev &g, const int2 *head_q, const int *parent, const int *roots,
                    long long n_items, const int *root_idx, const int *src, long long dt_q,
                    const double *gbar, double *dd, unsigned *status, cudaStream_t s,
-                   const long long *carry = nullptr);
+                   const long long *carry = nullptr, const int *carry_link = nullptr);
 
 }  // namespace qdta

@@ -1571,16 +1571,33 @@ void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStrea
   pack_head_q_kernel<<<cdiv(g.L, 256), 256, 0, s>>>(g.L, g.head, q, head_q);
 }
 
+// A trip carried on link cl (carry_link >= 0) with c quanta travelled along
+// it reaches the link's head at max(q - c, 0), or is still on the link at
+// the end of the interval when q - c > dt_q (Section 3.4, carried
+// truncation).  Returns false in the second case; else sets u and elapsed.
+__device__ __forceinline__ bool finish_carried_link(const int2 *__restrict__ head_q, int cl, long long c,
+                                                    long long dt_q, int &u, long long &elapsed) {
+  const int2 hq = __ldg(&head_q[cl]);
+  const long long at_head = (long long)hq.y - c;
+  if (at_head > dt_q) return false;
+  elapsed = at_head > 0 ? at_head : 0;
+  u = hq.x;
+  return true;
+}
+
 // One thread per item: walk origin -> root along the destination tree.  A
 // link is loaded iff the elapsed time at its tail is < dt_q; the walk ends
-// at the first node reached at >= dt_q (the stop node) or at the root.
+// at the first node reached at >= dt_q (the stop node) or at the root.  An
+// item carried on a link loads it and walks on from its head; one still on
+// it at the end of the interval stops at src (the link's tail).
 __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *__restrict__ parent,
                             const int *parent_slot_dev, long long slot_stride,
                             const int *__restrict__ root_slot, const int *__restrict__ roots,
                             long long n_host, const long long *n_dev, const int *__restrict__ root_idx,
                             const int *__restrict__ src, const long long *__restrict__ amount,
                             long long dt_q, unsigned long long *flow_fx, int *stop_out,
-                            unsigned *status, const long long *__restrict__ carry) {
+                            unsigned *status, const long long *__restrict__ carry,
+                            const int *__restrict__ carry_link) {
   const long long n = n_dev ? *n_dev : n_host;
   if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -1590,7 +1607,15 @@ __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *_
     const int *par = parent + (long long)(root_slot ? root_slot[r] : r) * V;
     const unsigned long long amt = (unsigned long long)amount[k];
     int u = src[k];
-    long long elapsed = carry ? -carry[k] : 0;
+    long long elapsed = 0;
+    const int cl = carry_link ? carry_link[k] : -1;
+    if (cl >= 0) {
+      if (amt) atomicAdd(&flow_fx[cl], amt);
+      if (!finish_carried_link(head_q, cl, carry ? carry[k] : 0, dt_q, u, elapsed)) {
+        if (stop_out) stop_out[k] = u;
+        continue;
+      }
+    }
     int steps = 0;
     while (u != z) {
       if (elapsed >= dt_q) break;
@@ -1627,6 +1652,26 @@ __global__ void cap_copy_kernel(int L, const double *__restrict__ src, double *_
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < L; a += gridDim.x * blockDim.x) dst[a] = src[a];
 }
 
+// items carried on a link: the link exists, starts at the item's src, and
+// the carried time is >= 0 (ST_BADARG otherwise)
+__global__ void check_carry_kernel(int L, long long n, const int *__restrict__ src,
+                                   const long long *__restrict__ carry, const int *__restrict__ carry_link,
+                                   const int *__restrict__ tail, unsigned *status) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int cl = carry_link[k];
+    if (cl < 0) continue;
+    if (cl >= L || tail[cl] != src[k] || (carry && carry[k] < 0)) atomicOr(status, ST_BADARG);
+  }
+}
+
+void launch_check_carry(const GraphDev &g, long long n, const int *src, const long long *carry,
+                        const int *carry_link, unsigned *status, cudaStream_t s) {
+  if (n <= 0 || !carry_link) return;
+  COUNT_LAUNCH();
+  check_carry_kernel<<<link_grid(g, n), 256, 0, s>>>(g.L, n, src, carry, carry_link, g.tail, status);
+}
+
 void launch_set_capacity(const GraphDev &g, const double *cap, unsigned *status, cudaStream_t s) {
   if (g.L <= 0) return;
   COUNT_LAUNCH();
@@ -1640,13 +1685,14 @@ void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const
                  long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
                  const long long *n_items_dev, const int *root_idx, const int *src,
                  const long long *amount, long long dt_q, unsigned long long *flow_fx, int *stop_out,
-                 unsigned *status, cudaStream_t s, const long long *carry) {
+                 unsigned *status, cudaStream_t s, const long long *carry, const int *carry_link) {
   long long n = n_items_dev ? (long long)g.num_sms * 16 * 256 : n_items_host;
   if (n <= 0) return;
   COUNT_LAUNCH();
   load_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, head_q, parent, parent_slot_dev, slot_stride,
                                               root_slot, roots, n_items_host, n_items_dev, root_idx,
-                                              src, amount, dt_q, flow_fx, stop_out, status, carry);
+                                              src, amount, dt_q, flow_fx, stop_out, status, carry,
+                                              carry_link);
 }
 
 // unsigned 128-bit accumulation with two 64-bit atomics: the low word's carry
@@ -1659,30 +1705,56 @@ __device__ __forceinline__ void add_u128(unsigned long long *p, u128 v) {
   if (hi | carry) atomicAdd(p + 1, hi + carry);
 }
 
-// one residual entry carrying a partial link: amount and amount x carried
-// time into entry d = root * V + node of the carried accumulator
-__device__ __forceinline__ void carry_add(const CarryAcc &ca, long long d, long long tau, long long amt,
-                                          unsigned *status) {
-  if (!ca.amt) {
+constexpr unsigned long long CARRY_KEY_EMPTY = ~0ull;
+
+// slot of a (root, link) key: the splitmix64 finaliser (Steele, Lea and
+// Flood, 2014) spreads the consecutive link ids of one root over the table
+__device__ __forceinline__ unsigned long long carry_hash(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// one residual trip on a link: its amount and amount x carried time join
+// the entry of key root * L + link (linear probing; a key, once claimed,
+// stays until the compaction clears the table).  A full table sets
+// ST_CAPACITY and drops the trip.
+__device__ __forceinline__ void carry_add(const CarryAcc &ca, unsigned long long key, long long tau,
+                                          long long amt, unsigned *status) {
+  if (!ca.mask) {
     if (status) atomicOr(status, ST_CAPACITY);
     return;
   }
-  atomicAdd(&ca.amt[d], (unsigned long long)amt);
-  add_u128(ca.tsum + 2 * d, (u128)(unsigned long long)amt * (u128)(unsigned long long)tau);
+  unsigned long long h = carry_hash(key) & ca.mask;
+  for (unsigned long long probe = 0; probe <= ca.mask; ++probe) {
+    unsigned long long cur = __ldcg(&ca.key[h]);
+    if (cur == CARRY_KEY_EMPTY) cur = atomicCAS(&ca.key[h], CARRY_KEY_EMPTY, key);
+    if (cur == CARRY_KEY_EMPTY || cur == key) {
+      atomicAdd(&ca.amt[h], (unsigned long long)amt);
+      add_u128(ca.tsum + 2 * h, (u128)(unsigned long long)amt * (u128)(unsigned long long)tau);
+      return;
+    }
+    h = (h + 1) & ca.mask;
+  }
+  if (status) atomicOr(status, ST_CAPACITY);
 }
 
 // Alg. 4 for one accepted AON j: the item's path on tree j is re-truncated
 // with the final link times (head_q_fin); its share RN(amount * w_j) loads
 // h and, if the walk stops before the root, joins the residual demand of the
-// next interval: in the dense (root, node) accumulator, or with trunc = 1
-// (carried truncation) and a partial link, in the carried-time table.
-__global__ void residual_kernel(int V, const int2 *__restrict__ head_q_fin, const int *__restrict__ parent,
-                                const int *parent_slot_dev, long long slot_stride,
-                                const int *__restrict__ root_slot, const int *__restrict__ roots,
-                                const long long *n_dev, const int *__restrict__ root_idx,
-                                const int *__restrict__ src, const long long *__restrict__ amount,
-                                const double *weight_dev, long long dt_q, unsigned long long *h_fx,
-                                unsigned long long *dense, unsigned *status, const long long *__restrict__ carry,
+// next interval: in the dense (root, node) accumulator, or, when the trip is
+// still on a link (trunc = 1, or an item carried on a link that it does not
+// finish), in the carried table under (root, link) with its carried time.
+__global__ void residual_kernel(int V, int L, const int2 *__restrict__ head_q_fin,
+                                const int *__restrict__ parent, const int *parent_slot_dev,
+                                long long slot_stride, const int *__restrict__ root_slot,
+                                const int *__restrict__ roots, const long long *n_dev,
+                                const int *__restrict__ root_idx, const int *__restrict__ src,
+                                const long long *__restrict__ amount, const double *weight_dev, long long dt_q,
+                                unsigned long long *h_fx, unsigned long long *dense, unsigned *status,
+                                const long long *__restrict__ carry, const int *__restrict__ carry_link,
                                 int trunc, CarryAcc ca) {
   const long long n = *n_dev;
   const double w = *weight_dev;
@@ -1695,15 +1767,26 @@ __global__ void residual_kernel(int V, const int2 *__restrict__ head_q_fin, cons
     const int z = roots[r];
     const int *par = parent + (long long)root_slot[r] * V;
     int u = src[k];
-    long long elapsed = carry ? -carry[k] : 0, tau = 0;
+    long long elapsed = 0, tau = 0;
+    int on_link = -1;  // the link holding the trip at the end of the interval
+    const int cl = carry_link ? carry_link[k] : -1;
+    if (cl >= 0) {
+      const long long c0 = carry ? carry[k] : 0;
+      atomicAdd(&h_fx[cl], (unsigned long long)amt);
+      if (!finish_carried_link(head_q_fin, cl, c0, dt_q, u, elapsed)) {
+        on_link = cl;
+        tau = c0 + dt_q;
+      }
+    }
     int steps = 0;
-    while (u != z) {
+    while (on_link < 0 && u != z) {
       if (elapsed >= dt_q) break;
       const int e = par[u];
       if (e < 0) { atomicOr(status, ST_UNREACH); break; }
       atomicAdd(&h_fx[e], (unsigned long long)amt);
       const int2 hq = __ldg(&head_q_fin[e]);
       if (trunc && elapsed + hq.y > dt_q) {  // on this link at the end of the interval
+        on_link = e;
         tau = dt_q - elapsed;
         break;
       }
@@ -1711,10 +1794,8 @@ __global__ void residual_kernel(int V, const int2 *__restrict__ head_q_fin, cons
       u = hq.x;
       if (++steps > V) { atomicOr(status, ST_TIMEOUT); break; }
     }
-    if (u != z) {
-      if (tau > 0) carry_add(ca, (long long)r * V + u, tau, amt, status);
-      else atomicAdd(&dense[(long long)r * V + u], (unsigned long long)amt);
-    }
+    if (on_link >= 0) carry_add(ca, (unsigned long long)r * (unsigned long long)L + on_link, tau, amt, status);
+    else if (u != z) atomicAdd(&dense[(long long)r * V + u], (unsigned long long)amt);
   }
 }
 
@@ -1724,12 +1805,12 @@ void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *paren
                      const int *root_idx, const int *src, const long long *amount,
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
                      unsigned long long *dense, unsigned *status, cudaStream_t s, const long long *carry,
-                     int trunc, CarryAcc ca) {
+                     const int *carry_link, int trunc, CarryAcc ca) {
   if (n_items_cap <= 0) return;
   COUNT_LAUNCH();
   residual_kernel<<<link_grid(g, n_items_cap), 256, 0, s>>>(
-      g.V, head_q_fin, parent, parent_slot_dev, slot_stride, root_slot, roots, n_items_dev, root_idx, src, amount, weight_dev,
-      dt_q, h_fx, dense, status, carry, trunc, ca);
+      g.V, g.L, head_q_fin, parent, parent_slot_dev, slot_stride, root_slot, roots, n_items_dev, root_idx, src,
+      amount, weight_dev, dt_q, h_fx, dense, status, carry, carry_link, trunc, ca);
 }
 
 // ============================================================================
@@ -2377,49 +2458,56 @@ void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream
   day_next_kernel<<<1, 1, 0, s>>>(ctl, (cudaGraphConditionalHandle)cond, use_cond);
 }
 
-// original demand of the current interval into the dense accumulator
-__global__ void scatter_orig_kernel(int V, const Ctl *c, const OrigTable *tab,
+// one demand item into the merge: waiting at src -> the dense (root, node)
+// accumulator; on a link -> the carried table
+__device__ __forceinline__ void scatter_one(int V, int L, int r, int src, long long a, long long tau, int link,
+                                            unsigned long long *dense, const CarryAcc &ca, unsigned *status) {
+  if (!a) return;
+  if (link >= 0) carry_add(ca, (unsigned long long)r * (unsigned long long)L + link, tau, a, status);
+  else atomicAdd(&dense[(long long)r * V + src], (unsigned long long)a);
+}
+
+// original demand of the current interval into the merge
+__global__ void scatter_orig_kernel(int V, int L, const Ctl *c, const OrigTable *tab,
                                     unsigned long long *dense, CarryAcc ca, unsigned *status) {
   const OrigTable t = tab[c->day_i];
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < t.n;
        k += (long long)gridDim.x * blockDim.x) {
-    const long long a = t.amount[k];
-    const long long tau = t.carry ? t.carry[k] : 0;
-    const long long d = (long long)t.root_idx[k] * V + t.src[k];
-    if (a && tau > 0) carry_add(ca, d, tau, a, status);
-    else if (a) atomicAdd(&dense[d], (unsigned long long)a);
+    const int link = t.carry_link ? t.carry_link[k] : -1;
+    scatter_one(V, L, t.root_idx[k], t.src[k], t.amount[k], link >= 0 && t.carry ? t.carry[k] : 0, link, dense,
+                ca, status);
   }
 }
 
 void launch_scatter_orig(const GraphDev &g, const Ctl *ctl, const OrigTable *tab, long long max_n,
                          unsigned long long *dense, cudaStream_t s, CarryAcc ca, unsigned *status) {
   COUNT_LAUNCH();
-  scatter_orig_kernel<<<link_grid(g, max_n > 0 ? max_n : 1), 256, 0, s>>>(g.V, ctl, tab, dense, ca, status);
+  scatter_orig_kernel<<<link_grid(g, max_n > 0 ? max_n : 1), 256, 0, s>>>(g.V, g.L, ctl, tab, dense, ca,
+                                                                          status);
 }
 
 // ============================================================================
 // residual-demand merge: dense (root, node) accumulator -> sorted items
 // ============================================================================
 
-__global__ void scatter_items_kernel(int V, long long n, const int *root_idx, const int *src,
+__global__ void scatter_items_kernel(int V, int L, long long n, const int *root_idx, const int *src,
                                      const long long *amount, unsigned long long *dense,
-                                     const long long *carry, CarryAcc ca, unsigned *status) {
+                                     const long long *carry, const int *carry_link, CarryAcc ca,
+                                     unsigned *status) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    const long long a = amount[k];
-    const long long tau = carry ? carry[k] : 0;
-    const long long d = (long long)root_idx[k] * V + src[k];
-    if (a && tau > 0) carry_add(ca, d, tau, a, status);
-    else if (a) atomicAdd(&dense[d], (unsigned long long)a);
+    const int link = carry_link ? carry_link[k] : -1;
+    scatter_one(V, L, root_idx[k], src[k], amount[k], link >= 0 && carry ? carry[k] : 0, link, dense, ca, status);
   }
 }
 
 void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, const int *src,
                           const long long *amount, unsigned long long *dense, cudaStream_t s,
-                          const long long *carry, CarryAcc ca, unsigned *status) {
+                          const long long *carry, const int *carry_link, CarryAcc ca, unsigned *status) {
   if (n <= 0) return;
   COUNT_LAUNCH();
-  scatter_items_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, n, root_idx, src, amount, dense, carry, ca, status);
+  scatter_items_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, g.L, n, root_idx, src, amount, dense, carry,
+                                                       carry_link, ca, status);
 }
 
 constexpr int COMPACT_TILE = 4096;
@@ -2470,21 +2558,30 @@ __global__ void compact_scan_kernel(int nblk, const int *blk_count, long long *b
   }
 }
 
-// ordered write of the nonzero entries of each tile (root-major, node-minor)
-// tsum (nullable): the carried accumulator's sums; an item then carries
-// floor(sum amount x carried time / amount), and the sums are cleared
+// ordered write of the nonzero entries of each tile.  Dense part (keys ==
+// NULL): entry root * V + node, written root-major, node-minor, carried time
+// 0 and link -1.  Carried part: slot order of the table; the key gives
+// (root, link), src is the link's tail, the carried time is
+// floor(sum amount x carried time / amount); keys and sums are cleared.
 __global__ void compact_write_kernel(long long total, int V, unsigned long long *dense,
                                      const long long *blk_off, long long cap, int *root_idx,
                                      int *src, long long *amount, long long *carry_out,
-                                     unsigned long long *tsum) {
+                                     int *link_out, unsigned long long *keys, unsigned long long *tsum,
+                                     int L, const int *__restrict__ tail) {
   __shared__ int s_warp[32];
   const long long base = (long long)blockIdx.x * COMPACT_TILE;
   long long out = blk_off[blockIdx.x];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c0 = 0; c0 < COMPACT_TILE; c0 += blockDim.x) {
     const long long idx = base + c0 + threadIdx.x;
-    unsigned long long v = 0ull;
-    if (idx < total) v = dense[idx];
+    unsigned long long v = 0ull, key = CARRY_KEY_EMPTY;
+    if (idx < total) {
+      v = dense[idx];
+      if (keys) {
+        key = keys[idx];
+        keys[idx] = CARRY_KEY_EMPTY;
+      }
+    }
     const bool nz = v != 0ull;
     const unsigned m = __ballot_sync(0xffffffffu, nz);
     if (lane == 0) s_warp[wid] = __popc(m);
@@ -2494,17 +2591,25 @@ __global__ void compact_write_kernel(long long total, int V, unsigned long long 
     if (nz) {
       const long long pos = out + before + __popc(m & ((1u << lane) - 1u));
       long long tau = 0;
-      if (tsum) {
+      int r, node, link = -1;
+      if (keys) {
         const u128 t = ((u128)tsum[2 * idx + 1] << 64) | (u128)tsum[2 * idx];
         tau = (long long)(t / (u128)v);
         tsum[2 * idx] = 0ull;
         tsum[2 * idx + 1] = 0ull;
+        r = (int)(key / (unsigned long long)L);
+        link = (int)(key % (unsigned long long)L);
+        node = __ldg(&tail[link]);
+      } else {
+        r = (int)(idx / V);
+        node = (int)(idx % V);
       }
       if (pos < cap) {
-        root_idx[pos] = (int)(idx / V);
-        src[pos] = (int)(idx % V);
+        root_idx[pos] = r;
+        src[pos] = node;
         amount[pos] = (long long)v;
         if (carry_out) carry_out[pos] = tau;
+        if (link_out) link_out[pos] = link;
       }
       dense[idx] = 0ull;
     }
@@ -2516,10 +2621,10 @@ __global__ void compact_write_kernel(long long total, int V, unsigned long long 
 void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *blk_count,
                     long long *blk_off, long long cap, int *root_idx, int *src, long long *amount,
                     long long *n_out_dev, unsigned *status, cudaStream_t s, long long *carry_out,
-                    CarryAcc ca) {
-  const long long total = (long long)R * g.V;
-  const int nblk = cdiv(total > 0 ? total : 1, COMPACT_TILE);
-  for (int part = 0; part < (ca.amt ? 2 : 1); ++part) {
+                    int *link_out, CarryAcc ca) {
+  for (int part = 0; part < (ca.mask ? 2 : 1); ++part) {
+    const long long total = part == 0 ? (long long)R * g.V : (long long)ca.mask + 1;
+    const int nblk = cdiv(total > 0 ? total : 1, COMPACT_TILE);
     unsigned long long *src_acc = part == 0 ? dense : ca.amt;
     COUNT_LAUNCH();
     compact_count_kernel<<<nblk, 256, 0, s>>>(total, src_acc, blk_count);
@@ -2527,7 +2632,8 @@ void launch_compact(const GraphDev &g, int R, unsigned long long *dense, int *bl
     compact_scan_kernel<<<1, 1024, 0, s>>>(nblk, blk_count, blk_off, cap, n_out_dev, status, part);
     COUNT_LAUNCH();
     compact_write_kernel<<<nblk, 256, 0, s>>>(total, g.V, src_acc, blk_off, cap, root_idx, src, amount, carry_out,
-                                              part == 0 ? nullptr : ca.tsum);
+                                              link_out, part == 0 ? nullptr : ca.key,
+                                              part == 0 ? nullptr : ca.tsum, g.L, g.tail);
   }
 }
 
@@ -2775,15 +2881,24 @@ void launch_adj_update(const GraphDev &g, const LinkConst *kc, const double *lam
 __global__ void gather_kernel(int V, const int2 *__restrict__ head_q, const int *__restrict__ parent,
                               const int *__restrict__ roots, long long n, const int *__restrict__ root_idx,
                               const int *__restrict__ src, long long dt_q, const double *__restrict__ gbar,
-                              double *dd, unsigned *status, const long long *__restrict__ carry) {
+                              double *dd, unsigned *status, const long long *__restrict__ carry,
+                              const int *__restrict__ carry_link) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const int r = root_idx[k];
     const int z = roots[r];
     const int *par = parent + (long long)r * V;
     int u = src[k];
-    long long elapsed = carry ? -carry[k] : 0;
+    long long elapsed = 0;
     double acc = 0.0;
+    const int cl = carry_link ? carry_link[k] : -1;
+    if (cl >= 0) {  // the carried link first, then on from its head
+      acc = add(acc, gbar[cl]);
+      if (!finish_carried_link(head_q, cl, carry ? carry[k] : 0, dt_q, u, elapsed)) {
+        dd[k] = add(dd[k], acc);
+        continue;
+      }
+    }
     int steps = 0;
     while (u != z && elapsed < dt_q) {
       const int e = par[u];
@@ -2800,11 +2915,12 @@ __global__ void gather_kernel(int V, const int2 *__restrict__ head_q, const int 
 
 void launch_gather(const GraphDev &g, const int2 *head_q, const int *parent, const int *roots,
                    long long n_items, const int *root_idx, const int *src, long long dt_q,
-                   const double *gbar, double *dd, unsigned *status, cudaStream_t s, const long long *carry) {
+                   const double *gbar, double *dd, unsigned *status, cudaStream_t s, const long long *carry,
+                   const int *carry_link) {
   if (n_items <= 0) return;
   COUNT_LAUNCH();
   gather_kernel<<<link_grid(g, n_items), 256, 0, s>>>(g.V, head_q, parent, roots, n_items, root_idx,
-                                                      src, dt_q, gbar, dd, status, carry);
+                                                      src, dt_q, gbar, dd, status, carry, carry_link);
 }
 
 }  // namespace qdta

@@ -44,7 +44,7 @@ class GraphDesc(C.Structure):
 class OD(C.Structure):
     _fields_ = [("n_roots", C.c_int32), ("roots", C.c_void_p), ("n_items", C.c_int64),
                 ("root_idx", C.c_void_p), ("src", C.c_void_p), ("amount_fx", C.c_void_p),
-                ("carry_q", C.c_void_p)]
+                ("carry_q", C.c_void_p), ("carry_link", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -65,7 +65,8 @@ class Stats(C.Structure):
 
 class Residual(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("root_idx", C.c_void_p), ("src", C.c_void_p),
-                ("amount_fx", C.c_void_p), ("count", C.c_int64), ("carry_q", C.c_void_p)]
+                ("amount_fx", C.c_void_p), ("count", C.c_int64), ("carry_q", C.c_void_p),
+                ("carry_link", C.c_void_p)]
 
 
 class Profile(C.Structure):
@@ -216,7 +217,10 @@ class DeviceOD:
     root_idx: torch.Tensor
     src: torch.Tensor
     amount_fx: torch.Tensor
-    carry_q: torch.Tensor = None  # int64 per item (time already travelled beyond src), or None
+    # trips carried on a link (both None, or int64 / int32 per item): the
+    # time travelled along carry_link (-1: the trip waits at src)
+    carry_q: torch.Tensor = None
+    carry_link: torch.Tensor = None
 
     @classmethod
     def of(cls, dem, device="cuda", pin=False):
@@ -233,7 +237,8 @@ class DeviceOD:
     def struct(self) -> OD:
         return OD(int(self.roots.shape[0]), self.roots.data_ptr(), self.n_items,
                   self.root_idx.data_ptr(), self.src.data_ptr(), self.amount_fx.data_ptr(),
-                  self.carry_q.data_ptr() if self.carry_q is not None else None)
+                  self.carry_q.data_ptr() if self.carry_q is not None else None,
+                  self.carry_link.data_ptr() if self.carry_link is not None else None)
 
 
 # ---------------------------------------------------------------------------
@@ -367,16 +372,18 @@ def qdta_run_day(g: Graph, days, dt_s: float, params: Params, resid_in: DeviceOD
         bufs = (torch.empty(resid_capacity, dtype=torch.int32, device=g.device),
                 torch.empty(resid_capacity, dtype=torch.int32, device=g.device),
                 torch.empty(resid_capacity, dtype=torch.int64, device=g.device),
-                torch.empty(resid_capacity, dtype=torch.int64, device=g.device))
+                torch.empty(resid_capacity, dtype=torch.int64, device=g.device),
+                torch.empty(resid_capacity, dtype=torch.int32, device=g.device))
         rout = Residual(resid_capacity, bufs[0].data_ptr(), bufs[1].data_ptr(), bufs[2].data_ptr(), 0,
-                        bufs[3].data_ptr())
+                        bufs[3].data_ptr(), bufs[4].data_ptr())
     rc = _check(lib().qdta_run_day(g.h, arr, N, float(dt_s), C.byref(params),
                                    C.byref(rin) if rin is not None else None, _ptr(flow_out), st,
                                    C.byref(rout) if rout is not None else None, _stream()))
     resid = None
     if rout is not None:
         n = rout.count
-        resid = (bufs[0][:n], bufs[1][:n], bufs[2][:n], bufs[3][:n])  # root index, stop node, amount, carry
+        # root index, stop node (a carried trip: its link's tail), amount, carried time, link (-1: none)
+        resid = tuple(b[:n] for b in bufs)
     return flow_out, [s.as_dict() for s in st], rc, resid
 
 

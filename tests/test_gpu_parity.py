@@ -655,8 +655,9 @@ def test_run_day_large_graph_carried_truncation_bit_exact(schedule):
     """The large-graph day of the test above under carried truncation."""
     net, zones, days = _mid_day()
     og = oracle.OracleGraph(net)
-    f_o, st_o, nit_o, rn_o, rc_o = oracle.run_day(og, zones, days, 900.0, oracle.make_params(
-        Q.STEP[MID_DAY_PARAMS[0]], Q.STOP[MID_DAY_PARAMS[1]], MID_DAY_PARAMS[2], truncation=oracle.TRUNC_CARRY))
+    f_o, st_o, nit_o, rn_o, rc_o, res_o = oracle.run_day(og, zones, days, 900.0, oracle.make_params(
+        Q.STEP[MID_DAY_PARAMS[0]], Q.STOP[MID_DAY_PARAMS[1]], MID_DAY_PARAMS[2], truncation=oracle.TRUNC_CARRY),
+        want_resid=True)
     g = Q.Graph(net)
     zt = T(zones, np.int32)
     dd = [Q.DeviceOD(zt, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
@@ -667,20 +668,26 @@ def test_run_day_large_graph_carried_truncation_bit_exact(schedule):
     assert [s["n_items"] for s in st_g] == list(nit_o)
     assert [s["iterations"] for s in st_g] == [s["iterations"] for s in st_o]
     assert resid[0].shape[0] == rn_o
+    assert _sorted_resid([r.cpu().numpy() for r in resid]) == _sorted_resid(res_o)
 
 
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("carried", [False, True])
 @pytest.mark.parametrize("step", ["exact", "msa"])
-def test_backward_matches_oracle(step):
+def test_backward_matches_oracle(step, carried):
     net = synth.grid_network(12, 4)
     zones = synth.pick_zones(net, 10, 4)
     dem = synth.demand_from_matrix(zones, synth.gravity_fixed_pairs(net, zones, 3000, 1500.0))
     og = oracle.OracleGraph(net)
     od = oracle.OracleOD.of(dem)
+    dod = Q.DeviceOD.of(dem)
+    if carried:  # half of the trips start on a link (the adjoint gathers it first)
+        carry, link = _carried_items(net, dem, 3)
+        od = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_q=carry, carry_link=link)
+        dod.carry_q, dod.carry_link = T(carry, np.int64), T(link, np.int32)
     p = oracle.make_params(Q.STEP[step], oracle.STOP_NONE, 10)
     f_o, st_o, rc, tape_o = oracle.assign_interval(og, od, 600.0, p, tape=True)
     g = Q.Graph(net)
-    dod = Q.DeviceOD.of(dem)
     f_g, st_g, rc, tape = Q.qdta_assign_interval(g, dod, 600.0, Q.make_params(step, "none", 10, record_tape=True))
     np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
     rng = np.random.default_rng(0)
@@ -901,6 +908,13 @@ def test_autograd_reuses_one_graph_handle():
 
 # ---------------------------------------------------------------------------
 # Carried partial-link truncation (Section 3.4's alternative to Eq. 2)
+def _sorted_resid(r):
+    """residual arrays (root index, src, amount, carried time, link) as a
+    sorted list of tuples: the GPU writes carried entries in table order"""
+    root, src, amt, carry, link = (np.asarray(a).astype(np.int64) for a in r)
+    return sorted(zip(root.tolist(), link.tolist(), src.tolist(), amt.tolist(), carry.tolist()))
+
+
 def _carry_day_case():
     # 150 s intervals on the 32 x 32 grid: most trips cross several intervals
     return synth.scaled_day(synth.config_small(0), 60000, n_intervals=5, seed=5)
@@ -912,8 +926,8 @@ def test_run_day_carried_truncation_bit_exact(schedule, step, stop, it):
     day = _carry_day_case()
     days = list(day.demand)
     og = oracle.OracleGraph(day.net)
-    f_o, st_o, nit_o, rn_o, rc_o = oracle.run_day(og, day.zones, days, 150.0, oracle.make_params(
-        Q.STEP[step], Q.STOP[stop], it, truncation=oracle.TRUNC_CARRY))
+    f_o, st_o, nit_o, rn_o, rc_o, res_o = oracle.run_day(og, day.zones, days, 150.0, oracle.make_params(
+        Q.STEP[step], Q.STOP[stop], it, truncation=oracle.TRUNC_CARRY), want_resid=True)
     g = Q.Graph(day.net)
     zones = T(day.zones, np.int32)
     dd = [Q.DeviceOD(zones, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
@@ -925,7 +939,10 @@ def test_run_day_carried_truncation_bit_exact(schedule, step, stop, it):
         assert st_g[i]["n_items"] == nit_o[i], i
         for key in ("iterations", "aon_calls", "ls_passes", "converged"):
             assert st_g[i][key] == st_o[i][key], (i, key)
-    assert resid[0].shape[0] == rn_o and int((resid[3] > 0).sum()) > 0
+    assert resid[0].shape[0] == rn_o and int((resid[4] >= 0).sum()) > 0
+    # the residual itself: (root, link, src) keys, amounts, mean carried times
+    assert _sorted_resid([r.cpu().numpy() for r in resid]) == _sorted_resid(
+        [res_o[0], res_o[1], res_o[2], res_o[3], res_o[4]])
     # the node rule differs on the same inputs (the carried trips wait elsewhere)
     f_n, _, _, _ = Q.qdta_run_day(g, dd, 150.0, Q.make_params(step, stop, it, schedule=schedule))
     assert not torch.equal(f_n[1:], f_g[1:])
@@ -965,27 +982,79 @@ def test_carried_day_resumes_from_its_residual(schedule):
     dd = [Q.DeviceOD(zones, T(d.root_idx, np.int32), T(d.src, np.int32), T(d.amount_fx, np.int64)) for d in days]
     p = Q.make_params("sweep8", "paper_obj", 40, schedule=schedule, truncation="carry")
     f_a, _, _, res = Q.qdta_run_day(g, dd[:2], 150.0, p, resid_capacity=1 << 21)
-    rin = Q.DeviceOD(zones, res[0].clone(), res[1].clone(), res[2].clone(), res[3].clone())
+    rin = Q.DeviceOD(zones, *(r.clone() for r in res))
     f_b, st_b, _, _ = Q.qdta_run_day(g, dd[2:], 150.0, p, resid_in=rin)
     np.testing.assert_array_equal(torch.cat([f_a, f_b]).cpu().numpy(), f_o)
     assert [s["n_items"] for s in st_b] == list(nit_o[2:])
 
 
-def test_load_aon_with_carried_times_matches_the_oracle(small):
+def _carried_items(net, dem, seed):
+    """half of the items put on a random out-link of their src, with carried
+    times from 0 to past the link's free-flow time"""
+    rng = np.random.default_rng(seed)
+    out = [[] for _ in range(net.n_nodes)]
+    for a, t in enumerate(np.asarray(net.tail)):
+        out[int(t)].append(a)
+    link = np.full(dem.n_items, -1, dtype=np.int32)
+    carry = np.zeros(dem.n_items, dtype=np.int64)
+    for k in np.flatnonzero(rng.random(dem.n_items) < 0.5):
+        a = out[int(dem.src[k])][rng.integers(len(out[int(dem.src[k])]))]
+        link[k] = a
+        carry[k] = rng.integers(0, int(net.fftime_q[a]) * 2 + 2)
+    return carry, link
+
+
+def test_load_aon_with_carried_trips_matches_the_oracle(small):
     inst, g, og = small
     dem = inst.demand[0]
     rng = np.random.default_rng(4)
-    carry = rng.integers(0, 40000, dem.n_items).astype(np.int64) * (rng.random(dem.n_items) < 0.5)
+    carry, link = _carried_items(inst.net, dem, 4)
     q = (inst.net.fftime_q * rng.uniform(1.0, 2.0, og.n_links)).astype(np.int32)
     par_o, _ = oracle.sssp(og, q, dem.roots, want_dist=False)
-    od_o = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_q=carry)
-    for dt_q in (6000, 30000):
+    od_o = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_q=carry, carry_link=link)
+    for dt_q in (600, 6000, 30000):
         f_o, s_o, rc = oracle.load(og, q, par_o, od_o, dt_q)
         od_g = Q.DeviceOD(T(dem.roots, np.int32), T(dem.root_idx, np.int32), T(dem.src, np.int32),
-                          T(dem.amount_fx, np.int64), T(carry, np.int64))
+                          T(dem.amount_fx, np.int64), T(carry, np.int64), T(link, np.int32))
         f_g, s_g = Q.qdta_load_aon(g, T(q, np.int32), T(par_o, np.int32), od_g, dt_q, want_stop=True)
         np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
         np.testing.assert_array_equal(s_g.cpu().numpy(), s_o)
+
+
+@pytest.mark.parametrize("schedule", ["plain", "graph"])
+def test_interval_with_carried_trips_matches_the_oracle(small, schedule):
+    """One interval whose items are partly carried on links (the node rule
+    and the carried rule), against the oracle, bit-exact."""
+    inst, g, og = small
+    dem = inst.demand[0]
+    carry, link = _carried_items(inst.net, dem, 9)
+    od_o = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_q=carry, carry_link=link)
+    od_g = Q.DeviceOD(T(dem.roots, np.int32), T(dem.root_idx, np.int32), T(dem.src, np.int32),
+                      T(dem.amount_fx, np.int64), T(carry, np.int64), T(link, np.int32))
+    for trunc in ("node", "carry"):
+        f_o, st_o, _ = oracle.assign_interval(og, od_o, 300.0, oracle.make_params(
+            Q.STEP["sweep8"], Q.STOP["paper_obj"], 30, truncation=Q.TRUNCATION[trunc]))
+        f_g, st_g, _, _ = Q.qdta_assign_interval(g, od_g, 300.0, Q.make_params(
+            "sweep8", "paper_obj", 30, schedule=schedule, truncation=trunc))
+        np.testing.assert_array_equal(f_g.cpu().numpy(), f_o)
+        for key in ("iterations", "aon_calls", "ls_passes", "converged"):
+            assert st_g[key] == st_o[key], (trunc, key)
+
+
+def test_carried_item_on_a_link_that_does_not_start_at_src_is_rejected(small):
+    inst, g, og = small
+    dem = inst.demand[0]
+    tail = np.asarray(inst.net.tail)
+    link = np.full(dem.n_items, -1, dtype=np.int32)
+    link[0] = int(np.flatnonzero(tail != dem.src[0])[0])
+    od_g = Q.DeviceOD(T(dem.roots, np.int32), T(dem.root_idx, np.int32), T(dem.src, np.int32),
+                      T(dem.amount_fx, np.int64), T(np.zeros(dem.n_items), np.int64), T(link, np.int32))
+    with pytest.raises(Q.QdtaError):
+        Q.qdta_assign_interval(g, od_g, 300.0, Q.make_params("msa", "none", 2))
+    link[0] = og.n_links  # no such link
+    od_g.carry_link = T(link, np.int32)
+    with pytest.raises(Q.QdtaError):
+        Q.qdta_assign_interval(g, od_g, 300.0, Q.make_params("msa", "none", 2))
 
 
 # ---------------------------------------------------------------------------

@@ -744,6 +744,29 @@ def test_carried_trips_merge_with_their_mean_carried_time():
     assert list(nit) == [1, 2] + [1] * 9 + [0] and rn == 0
 
 
+def test_day_residual_holds_the_merged_carried_group():
+    """The residual a day leaves, for the two trip groups of the test above:
+    after intervals 0-1 one item of 4 trips on link 0 carrying 375 s; after
+    intervals 0-4 the group is on link 1 (tail node 1), 275 s along it (it
+    reached node 1 at 25 s into interval 4).  Carried times are in quanta of
+    0.01 s."""
+    net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
+    g = oracle.OracleGraph(net)
+    zones = np.array([3], np.int32)
+
+    def trips(n):
+        return synth.Demand(roots=zones, root_idx=np.array([0], np.int32), src=np.array([0], np.int32),
+                            amount_fx=np.array([n << 32], np.int64))
+    empty = synth.Demand(roots=zones, root_idx=np.zeros(0, np.int32), src=np.zeros(0, np.int32),
+                         amount_fx=np.zeros(0, np.int64))
+    p = oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0, truncation=oracle.TRUNC_CARRY)
+    for n_int, want in ((2, (0, 0, 4 << 32, 37500, 0)), (5, (0, 1, 4 << 32, 27500, 1))):
+        *_, rn, rc, res = oracle.run_day(g, zones, [trips(1), trips(3)] + [empty] * (n_int - 2), 300.0, p,
+                                         want_resid=True)
+        assert rc >= 0 and rn == 1
+        assert tuple(int(a[0]) for a in res) == want, res
+
+
 def test_carried_truncation_stop_node_and_carried_time():
     """One walk on the uncongested chain of 1000 s links for a trip already at
     position P seconds from node 0 (on link P // 1000 having travelled
