@@ -81,6 +81,7 @@ struct qdta_graph {
   long long cell_delta = 0;  // near/far width of the cell kernel, in quanta
   int sssp_kind = 0;  // 0 shared-memory BF, 1 cell, 2 global-memory BF
   int bf_bpsm = 0;    // resident CTAs per SM of the global-memory BF (0: as many as fit)
+  int bf_lpt = 1;     // dynamic fetch of the queue kernels: longest roots first
   unsigned long long sig = 0;  // graph signature (structure, free-flow times, device) for the tuning cache
 };
 
@@ -599,6 +600,14 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   if (cudaMalloc(&p, 64) != cudaSuccess) { qdta_graph_destroy(g); return fail(QDTA_ENOMEM, "status word"); }
   g->owned.push_back(p);
   g->status = (unsigned *)p;
+  p = nullptr;
+  if (cudaMalloc(&p, (size_t)V * 4 + 16) != cudaSuccess || cudaMemset(p, 0, (size_t)V * 4 + 16) != cudaSuccess) {
+    if (p) cudaFree(p);
+    qdta_graph_destroy(g);
+    return fail(QDTA_ENOMEM, "per-root round counts");
+  }
+  g->owned.push_back(p);
+  gd.root_rounds = (int *)p;
   if (cudaMallocHost(&g->status_h, 64) != cudaSuccess ||
       cudaMallocHost(&g->ctl_h, sizeof(Ctl)) != cudaSuccess) {
     qdta_graph_destroy(g);
@@ -624,8 +633,13 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   g->d.tune_shape = sssp_smq_shape_fits(V, 1) ? 1 : sssp_smq_shape_fits(V, 0) ? 0 : sssp_smq_shape_fits(V, 2) ? 2 : 0;
   g->d.tune_out = 1;  // internal-order output pass where the graph is renumbered
   if (const char *e = getenv("QDTA_SMQ_OUT")) g->d.tune_out = atoi(e) != 0;
-  g->d.tune_dyn = 0;  // round-robin roots (QDTA_BF_DYNAMIC=1: from an atomic counter)
+  // queue kernels: roots after the first wave from an atomic counter, the
+  // longest of their last batch first (QDTA_BF_DYNAMIC=0: round-robin;
+  // QDTA_BF_LPT=0: in batch order)
+  g->d.tune_dyn = 1;
   if (const char *e = getenv("QDTA_BF_DYNAMIC")) g->d.tune_dyn = atoi(e) != 0;
+  g->bf_lpt = 1;
+  if (const char *e = getenv("QDTA_BF_LPT")) g->bf_lpt = atoi(e) != 0;
   if (const char *e = getenv("QDTA_BF_SHAPE")) {
     const int sh = atoi(e);
     if (sssp_smq_shape_fits(V, sh)) g->d.tune_shape = sh;
@@ -840,11 +854,15 @@ static int sssp_grid(const qdta_graph *g, int R) {
   return n < 1 ? 1 : (int)n;
 }
 
-static int sssp_work(qdta_graph *g, int grid, SsspWork *w) {
+static int sssp_work(qdta_graph *g, int grid, int R_cap, SsspWork *w) {
   const size_t V = g->d.V;
   w->slots = grid;
   RC(ws_get(g, "sssp.adj", std::max((size_t)g->d.L, (size_t)4 * V), &w->adj));
   RC(ws_get(g, "sssp.fb", 4, &w->fb_skip));
+  // longest-first order of the dynamic fetch (queue kernels)
+  w->order = nullptr;
+  if (g->sssp_kind == 2 && !g->sssp_smem && sssp_uses_smq(g->d) && g->d.tune_dyn && g->bf_lpt)
+    RC(ws_get(g, "sssp.order", (size_t)std::max(R_cap, 1), &w->order));
   if (g->sssp_kind == 1) {
     RC(ws_get(g, "sssp.lrev", (size_t)std::max(g->n_lrev[0], g->n_lrev[1]), &w->lrev));
     RC(ws_get(g, "sssp.prio", (size_t)grid * g->cells.n_cells, &w->prio));
@@ -872,7 +890,7 @@ static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots
                     long long *dist, cudaStream_t s, const int *skip_dev = nullptr, bool profile = true) {
   SsspWork w;
   const int grid = sssp_grid(g, R_cap);
-  RC(sssp_work(g, grid, &w));
+  RC(sssp_work(g, grid, R_cap, &w));
   const int prof_saved = g->prof_on;
   if (!profile) g->prof_on = 0;
   ProfEvent pe;
@@ -1234,7 +1252,7 @@ static int solver_alloc(Solver &S, const std::string &tag, int ring, bool tape_f
   if (tape_f) RC(ws_get(g, tag + ".tape_f", (size_t)S.tape_cap * L, &S.tape_f));
   CK(cudaMemsetAsync(S.counter, 0, 16, S.s));
   SsspWork w;
-  RC(sssp_work(g, sssp_grid(g, S.R_cap), &w));  // nothing is allocated while capturing
+  RC(sssp_work(g, sssp_grid(g, S.R_cap), S.R_cap, &w));  // nothing is allocated while capturing
   return QDTA_OK;
 }
 

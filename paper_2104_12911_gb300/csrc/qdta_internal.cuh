@@ -272,6 +272,18 @@ struct GraphDev {
   int tune_adj, tune_relax, tune_carve, tune_shape;  // tune_adj: 0 compressed, 1 four-slot, 2 rank-keyed, 3 rank-keyed 32-bit
   int tune_out;  // output pass of the queue kernel: 1 internal node order, 0 external order
   int tune_dyn;  // queue kernels: roots after the first wave from an atomic counter (1) or round-robin (0)
+  // rounds each root node took in its last queue-kernel batch ([V], zeroed
+  // at create; nullable): the dynamic fetch hands out the longest first
+  int *root_rounds;
+};
+
+// root scheduling of the queue kernels: fetch (nullable) hands out root
+// positions after the first wave; order (nullable) maps a position to the
+// root's row (longest first); hint (nullable) receives each root node's rounds
+struct RootSched {
+  int *fetch;
+  const int *order;
+  int *hint;
 };
 
 // Cell partition for the shared-memory cell SSSP (graphs above the
@@ -317,6 +329,7 @@ struct SsspWork {
   unsigned long long *prio;   // cell kernel: [slots][cells] wake priorities
   int4 *xrev;                 // cell kernel: packed external readers (link, reader, q, 0)
   int *fb_skip;               // 32-bit-key batches: 1 unless the 64-bit redo must run
+  int *order;                 // [R_cap] root order of the dynamic fetch (nullable)
   int slots;
 };
 

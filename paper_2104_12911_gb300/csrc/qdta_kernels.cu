@@ -851,10 +851,10 @@ static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 20
                                                {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2},
                                                {256, 1, 2048, 4, 4}, {192, 1, 960, 5, 4}};
 
-// Next destination root of this CTA: every gridDim-th one, or, with a fetch
-// counter, the next one handed out by that counter (dynamic balance over the
-// CTAs; the counter is zeroed before each launch and numbers the roots after
-// the first wave).  Called by every thread of the CTA.
+// Next destination root position of this CTA: every gridDim-th one, or,
+// with a fetch counter, the next one handed out by that counter (dynamic
+// balance over the CTAs; the counter is zeroed before each launch and numbers
+// the positions after the first wave).  Called by every thread of the CTA.
 __device__ __forceinline__ int next_root(int r, int *fetch, int *s_next) {
   if (!fetch) return r + (int)gridDim.x;
   if (threadIdx.x == 0) *s_next = (int)gridDim.x + atomicAdd(fetch, 1);
@@ -891,7 +891,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                 const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
                 int max_rounds, int qcap, const int *__restrict__ node_ext, int out_mode,
-                const int *__restrict__ rank_link, int skip_parent, int *fetch) {
+                const int *__restrict__ rank_link, int skip_parent, RootSched sched) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
   __shared__ int s_next;
@@ -932,7 +932,8 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   if (PF)
     for (int i = threadIdx.x; i < WPF; i += blockDim.x) pfm[i] = 0u;
   __syncthreads();
-  for (int r = blockIdx.x; r < R; r = next_root(r, fetch, &s_next)) {
+  for (int pos = blockIdx.x; pos < R; pos = next_root(pos, sched.fetch, &s_next)) {
+    const int r = sched.order ? sched.order[pos] : pos;
     const int z = node_int ? node_int[roots[r]] : roots[r];
     if (threadIdx.x == 0) {
       state[z] = NOLINK;
@@ -1102,6 +1103,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
       if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
       atomicAdd(roots_counter + 2, (unsigned long long)my_relax);
     }
+    if (sched.hint && threadIdx.x == 0) sched.hint[roots[r]] = round;
     __syncthreads();
     // an early exit (timeout) can leave marks behind: clear both bitmaps
     if (round > max_rounds)
@@ -1180,7 +1182,7 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
                  const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                  const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
                  int max_rounds, int qcap, const int *__restrict__ node_ext, int /*out_mode*/,
-                 const int *__restrict__ rank_link, int skip_parent, int *fetch) {
+                 const int *__restrict__ rank_link, int skip_parent, RootSched sched) {
   extern __shared__ __align__(16) unsigned smq_smem[];
   __shared__ int s_cnt[3];
   __shared__ int s_next;
@@ -1199,7 +1201,8 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
   for (int v = threadIdx.x; v < V; v += THREADS) state[v] = KINF;
   for (int i = threadIdx.x; i < W; i += THREADS) bm[i] = 0u;
   __syncthreads();
-  for (int r = blockIdx.x; r < R; r = next_root(r, fetch, &s_next)) {
+  for (int pos = blockIdx.x; pos < R; pos = next_root(pos, sched.fetch, &s_next)) {
+    const int r = sched.order ? sched.order[pos] : pos;
     const int z = node_int ? node_int[roots[r]] : roots[r];
     if (threadIdx.x == 0) {
       state[z] = NOLINK;
@@ -1298,6 +1301,7 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
       if (threadIdx.x == 0) atomicAdd(roots_counter + 1, (unsigned long long)round);
       atomicAdd(roots_counter + 2, (unsigned long long)my_relax);
     }
+    if (sched.hint && threadIdx.x == 0) sched.hint[roots[r]] = round;
     __syncthreads();
     if (round > max_rounds)  // an early exit can leave marks behind
       for (int i = threadIdx.x; i < W; i += THREADS) bm[i] = 0u;
@@ -1422,6 +1426,46 @@ int sssp_blocks_per_sm(bool use_smem, int V) {
 
 // after a 32-bit-key batch: run the 64-bit redo only if the batch overflowed
 // (and was not skipped); clears the overflow bit, which is not an error
+// Longest-first order of the batch's roots for the dynamic fetch: by the
+// rounds each root node took in its last batch (hint, 0 when never run),
+// descending, ties by position.  One CTA, a bitonic sort of up to
+// ORDER_MAX keys in shared memory; larger batches keep their order.
+constexpr int ORDER_MAX = 4096;
+__global__ void __launch_bounds__(1024)
+order_roots_kernel(int R_host, const int *R_dev, const int *__restrict__ roots, const int *__restrict__ hint,
+                   int *order, const int *skip_dev) {
+  __shared__ unsigned long long key[ORDER_MAX];
+  if (skip_dev && *skip_dev) return;
+  const int R = R_dev ? *R_dev : R_host;
+  if (R > ORDER_MAX) {
+    for (int i = threadIdx.x; i < R; i += blockDim.x) order[i] = i;
+    return;
+  }
+  int n = 1;
+  while (n < R) n <<= 1;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int h = i < R ? max(hint[roots[i]], 0) : 0;
+    key[i] = i < R ? ((unsigned long long)(0x7fffffff - h) << 32) | (unsigned)i : ~0ull;
+  }
+  __syncthreads();
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = key[i], b = key[ixj];
+          if (((i & k) == 0) == (a > b)) {
+            key[i] = b;
+            key[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < R; i += blockDim.x) order[i] = (int)(key[i] & 0xffffffffu);
+}
+
 __global__ void k32_redo_flag_kernel(unsigned *status, const int *skip_dev, int *fb_skip,
                                      unsigned long long *redo_counter) {
   const unsigned st = *status;
@@ -1434,7 +1478,7 @@ __global__ void k32_redo_flag_kernel(unsigned *status, const int *skip_dev, int 
 
 using SmqKernel = void (*)(int, int, const int *, const int4 *, const int *, int, const int *, unsigned long long *,
                           int *, int *, const int *, long long, long long *, unsigned *, const int *,
-                          unsigned long long *, const int *, int, int, const int *, int, const int *, int, int *);
+                          unsigned long long *, const int *, int, int, const int *, int, const int *, int, RootSched);
 
 template <int THREADS, bool ONEBM>
 static SmqKernel smq_kernel_relax(int adj, int relax) {
@@ -1516,11 +1560,19 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
       const int threads = kSmqShape[g.tune_shape].threads;
       const bool perm = g.node_int != nullptr;
-      // QDTA_BF_DYNAMIC: roots after the first wave come from an atomic
-      // counter (w.fb_skip[1] for the kernel, [2] for the redo), zeroed here
-      int *fetch = g.tune_dyn ? w.fb_skip + 1 : nullptr;
-      if (fetch) cudaMemsetAsync(fetch, 0, 2 * sizeof(int), s);
-      auto run = [&](SmqKernel kern, const int *skip, unsigned long long *counters, int *fetch_ctr) {
+      // dynamic fetch: roots after the first wave come from an atomic
+      // counter (w.fb_skip[1] for the kernel, [2] for the redo), zeroed
+      // here; with an order buffer, longest roots of their last batch first
+      RootSched sched{g.tune_dyn ? w.fb_skip + 1 : nullptr, nullptr, g.root_rounds};
+      if (sched.fetch) {
+        cudaMemsetAsync(sched.fetch, 0, 2 * sizeof(int), s);
+        if (w.order && g.root_rounds) {
+          COUNT_LAUNCH();
+          order_roots_kernel<<<1, 1024, 0, s>>>(R_host, R_dev, roots, g.root_rounds, w.order, skip_dev);
+          sched.order = w.order;
+        }
+      }
+      auto run = [&](SmqKernel kern, const int *skip, unsigned long long *counters, RootSched rs) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
         COUNT_LAUNCH();
@@ -1528,9 +1580,9 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                                         w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip,
                                         counters, perm ? g.node_int : nullptr, round_limit(g.V),
                                         kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
-                                        g.rank_link[direction], g.skip_parent, fetch_ctr);
+                                        g.rank_link[direction], g.skip_parent, rs);
       };
-      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev, roots_counter, fetch);
+      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev, roots_counter, sched);
       if (adjl == 3) {
         // a distance beyond the 32-bit keys' range: redo the batch with 64-bit
         // keys on the same packed adjacency (decided on the device, so graph
@@ -1539,7 +1591,9 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
         COUNT_LAUNCH();
         k32_redo_flag_kernel<<<1, 1, 0, s>>>(status, skip_dev, w.fb_skip,
                                              roots_counter ? roots_counter + 4 : nullptr);
-        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip, nullptr, fetch ? fetch + 1 : nullptr);
+        RootSched redo = sched;
+        if (redo.fetch) redo.fetch += 1;
+        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip, nullptr, redo);
       }
       return;
     }

@@ -264,11 +264,16 @@ def test_sssp_32_bit_keys_redo_only_on_distances_beyond_2_29(mid, shape, monkeyp
 
 
 @pytest.mark.parametrize("shape", ["1", "6"])
-def test_sssp_dynamic_root_fetch_covers_every_root(mid, shape, monkeypatch):
-    """QDTA_BF_DYNAMIC: more roots than resident CTAs, handed out by an atomic
-    counter after the first wave; every row bit-exact, in both directions."""
+@pytest.mark.parametrize("schedule", ["round_robin", "fetch", "fetch_longest_first"])
+def test_sssp_dynamic_root_fetch_covers_every_root(mid, shape, schedule, monkeypatch):
+    """More roots than resident CTAs: handed out round-robin, by an atomic
+    counter after the first wave, or by the counter in longest-first order
+    (the rounds each root took in the previous batch, so the second batch
+    runs in a different order from the first); every row bit-exact, in both
+    directions, in both batches."""
     net, dem, _, og = mid
-    monkeypatch.setenv("QDTA_BF_DYNAMIC", "1")
+    monkeypatch.setenv("QDTA_BF_DYNAMIC", "0" if schedule == "round_robin" else "1")
+    monkeypatch.setenv("QDTA_BF_LPT", "1" if schedule == "fetch_longest_first" else "0")
     monkeypatch.setenv("QDTA_BF_SHAPE", shape)
     g = Q.Graph(net)
     rng = np.random.default_rng(13)
@@ -276,9 +281,10 @@ def test_sssp_dynamic_root_fetch_covers_every_root(mid, shape, monkeypatch):
     roots = rng.choice(net.n_nodes, 1500, replace=False).astype(np.int32)
     for direction in (Q.QDTA_TO_ROOT, Q.QDTA_FROM_ROOT):
         p_o, d_o = oracle.sssp(og, q, roots, direction)
-        p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
-        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
-        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+        for _ in range(2):
+            p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), direction, True)
+            np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+            np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
 def test_sssp_large_irregular_graph_with_ties():
