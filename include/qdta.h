@@ -71,16 +71,19 @@ extern "C" {
 
 /* Truncation rule of Eq. 2 (how a trip that does not finish its interval
  * is carried to the next one).  Both rules load the same links: link a of a
- * trip's path is loaded iff the elapsed time on reaching its tail is < dt.
+ * trip's path is loaded in the interval the trip enters it, i.e. iff the
+ * elapsed time on reaching its tail is < dt.
  *  QDTA_TRUNC_NODE: the trip waits at the first node whose elapsed time is
  *    >= dt (it may overshoot dt by up to one link).
  *  QDTA_TRUNC_CARRY: Section 3.4's alternative -- a trip whose next link
- *    would end after dt stays on that link, carrying the time it travelled
- *    along it; in the next interval it first finishes the link (reaching its
- *    head at max(q - carry, 0) quanta, or staying on it with carry + dt) and
- *    is rerouted from the head.  A link longer than dt is crossed over
- *    several intervals.  Residual trips on a link merge per (root, link)
- *    with the amount-weighted mean carried time (floor, exact integers). */
+ *    would end after dt stays on that link, carrying the fraction of it
+ *    covered, f = floor((dt - elapsed) 2^32 / q) in units of 2^-32.  In the
+ *    next interval it first covers the rest of the link at that interval's
+ *    time q, q - round(q f / 2^32) quanta (halves up), or, when the rest
+ *    exceeds dt, stays on it with f + floor(dt 2^32 / q); from the head it is
+ *    rerouted.  A link longer than dt is crossed over several intervals.
+ *    Residual trips on a link merge per (root, link) with the amount-weighted
+ *    mean fraction (floor, exact integers). */
 #define QDTA_TRUNC_NODE 0
 #define QDTA_TRUNC_CARRY 1
 
@@ -118,9 +121,9 @@ typedef struct {
   const int64_t *amount_fx;  /* [n_items] >= 0 */
   /* Trips carried on a link (QDTA_TRUNC_CARRY residuals; both nullable):
    * carry_link[k] >= 0 puts item k on that link, whose tail must be src[k],
-   * having travelled carry_q[k] >= 0 quanta along it; -1 (or NULL) starts
-   * the item at src[k]. */
-  const int64_t *carry_q;
+   * having covered the fraction carry_frac[k] / 2^32 of it
+   * (0 <= carry_frac < 2^32); -1 (or NULL) starts the item at src[k]. */
+  const int64_t *carry_frac;
   const int32_t *carry_link;
 } qdta_od;
 
@@ -157,7 +160,7 @@ typedef struct {
   int32_t *src;        /* [capacity] stop node s, the new origin */
   int64_t *amount_fx;  /* [capacity] */
   int64_t count;       /* written by the library (host field): entries produced */
-  int64_t *carry_q;    /* [capacity] carried times (0 at a node); required with QDTA_TRUNC_CARRY */
+  int64_t *carry_frac; /* [capacity] covered fractions (0 at a node); required with QDTA_TRUNC_CARRY */
   int32_t *carry_link; /* [capacity] carrying link, -1 at a node; required with QDTA_TRUNC_CARRY */
 } qdta_residual;
 

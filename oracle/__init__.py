@@ -51,7 +51,7 @@ class Graph(C.Structure):
 class OD(C.Structure):
     _fields_ = [("n_roots", C.c_int32), ("roots", C.c_void_p), ("n_items", C.c_int64),
                 ("root_idx", C.c_void_p), ("src", C.c_void_p), ("amount_fx", C.c_void_p),
-                ("carry_q", C.c_void_p), ("carry_link", C.c_void_p)]
+                ("carry_frac", C.c_void_p), ("carry_link", C.c_void_p)]
 
 
 OBJ_UE, OBJ_SO = 0, 1  # user equilibrium (Beckmann) / system optimum (total cost)
@@ -134,19 +134,19 @@ class OracleGraph:
 
 class OracleOD:
     """Items (root_idx, src, amount_fx) over `roots`.  Optionally, carry_link
-    puts an item on a link (src its tail; -1: at src) having travelled
-    carry_q quanta along it."""
+    puts an item on a link (src its tail; -1: at src) having covered the
+    fraction carry_frac / 2^32 of it."""
 
-    def __init__(self, roots, root_idx, src, amount_fx, carry_q=None, carry_link=None):
+    def __init__(self, roots, root_idx, src, amount_fx, carry_frac=None, carry_link=None):
         self.roots = np.ascontiguousarray(roots, dtype=np.int32)
         self.root_idx = np.ascontiguousarray(root_idx, dtype=np.int32)
         self.src = np.ascontiguousarray(src, dtype=np.int32)
         self.amount_fx = np.ascontiguousarray(amount_fx, dtype=np.int64)
-        self.carry_q = None if carry_q is None else np.ascontiguousarray(carry_q, dtype=np.int64)
+        self.carry_frac = None if carry_frac is None else np.ascontiguousarray(carry_frac, dtype=np.int64)
         self.carry_link = None if carry_link is None else np.ascontiguousarray(carry_link, dtype=np.int32)
         self.s = OD(int(self.roots.shape[0]), _p(self.roots).value, int(self.src.shape[0]),
                     _p(self.root_idx).value, _p(self.src).value, _p(self.amount_fx).value,
-                    None if self.carry_q is None else _p(self.carry_q).value,
+                    None if self.carry_frac is None else _p(self.carry_frac).value,
                     None if self.carry_link is None else _p(self.carry_link).value)
 
     @classmethod
@@ -201,7 +201,7 @@ def sssp(g: OracleGraph, q, roots, direction=DIR_TO_ROOT, want_dist=True):
 def load(g: OracleGraph, walk_q, parent, od: OracleOD, dt_q: int, flow_fx=None, truncation=TRUNC_NODE,
          want_carry=False):
     """Returns (flow_fx, stop nodes, rc), or with want_carry (flow_fx, stop
-    nodes, carried times, carrying links, rc)."""
+    nodes, covered fractions (2^-32 units), carrying links, rc)."""
     walk_q = np.ascontiguousarray(walk_q, dtype=np.int32)
     parent = np.ascontiguousarray(parent, dtype=np.int32)
     if flow_fx is None:
@@ -278,7 +278,7 @@ def assign_interval(g: OracleGraph, od: OracleOD, dt_s: float, params: Params, t
 
 
 def residual(g: OracleGraph, od: OracleOD, dt_s: float, tape: Tape, f_final, truncation=TRUNC_NODE):
-    """Returns (h_fx, (stop nodes, root indices, amounts, carried times, carrying links), rc)."""
+    """Returns (h_fx, (stop nodes, root indices, amounts, covered fractions, carrying links), rc)."""
     K = tape.K.value
     cap = od.src.shape[0] * (K + 1) + 1
     h = np.zeros(g.n_links, dtype=np.int64)
@@ -299,7 +299,7 @@ def residual(g: OracleGraph, od: OracleOD, dt_s: float, tape: Tape, f_final, tru
 def run_day(g: OracleGraph, zones, demands, dt_s: float, params: Params, want_resid=False):
     """Returns (flows [N, L], stats, merged item counts, residual count, rc);
     with want_resid a sixth entry, the residual left after the last interval
-    as arrays (root index, src, amount_fx, carried time, link), sorted by
+    as arrays (root index, src, amount_fx, covered fraction, link), sorted by
     root, link, src."""
     zones = np.ascontiguousarray(zones, dtype=np.int32)
     N = len(demands)

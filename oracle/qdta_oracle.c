@@ -68,9 +68,10 @@ typedef struct {
   const int32_t *root_idx, *src;
   const int64_t *amount_fx;
   /* Trips carried on a link (R17; both nullable): carry_link[k] >= 0 puts
-   * item k on that link (src is its tail) having travelled carry_q[k] quanta
-   * along it; -1 (or NULL) starts the item at src. */
-  const int64_t *carry_q;
+   * item k on that link (src is its tail) having covered the fraction
+   * carry_frac[k] / 2^32 of it, 0 <= carry_frac < 2^32; -1 (or NULL) starts
+   * the item at src. */
+  const int64_t *carry_frac;
   const int32_t *carry_link;
 } or_od;
 
@@ -417,15 +418,27 @@ int32_t or_sssp(const or_graph *g, const int32_t *q, const int32_t *roots, int32
  *    >= dt_q (the stop node s), or at z.
  *  TRUNC_CARRY (R17, the alternative of Section 3.4): a link that would end
  *    after dt_q holds the trip at the end of the interval; the walk stops on
- *    that link, *link_out = the link, *carry_out = dt_q - elapsed(tail), the
- *    time travelled along it (the returned stop node is its tail).  A link
- *    ending exactly at dt_q is completed.
- * An item carried on a link (carry_link >= 0, p its tail, carry the time
- * already travelled on it) first finishes that link: the link is loaded, the
- * trip reaches its head at max(q - carry, 0), or is still on it after dt_q
- * (then carry + dt_q is carried on); from the head it follows the tree.
- * Both rules load the same links.  Returns the stop node, or -1 if z is
- * unreachable from p. */
+ *    that link, *link_out = the link, *carry_out = the fraction of it covered,
+ *    floor((dt_q - elapsed(tail)) 2^32 / q) (the returned stop node is its
+ *    tail).  A link ending exactly at dt_q is completed.
+ * An item carried on a link (carry_link >= 0, p its tail, carry the fraction
+ * covered) first finishes that link: it covered round(q carry / 2^32) of the
+ * link's q quanta and reaches the head after the rest; if the rest exceeds
+ * dt_q it is still on the link, having covered carry + floor(dt_q 2^32 / q).
+ * From the head it follows the tree.  A link is loaded in the interval the
+ * trip enters it (its tail reached before dt_q), so a carried link is not
+ * loaded again and both rules load the same links.  Returns the stop node,
+ * or -1 if z is unreachable from p. */
+/* R17's position on a link: the fraction covered in units of 2^-32.  The
+ * quanta a fraction f of a link of q quanta stands for, rounded to nearest
+ * (halves up); the fraction that t < q quanta of such a link cover, floor. */
+static int64_t carried_quanta(int64_t q, int64_t f) {
+  return (int64_t)(((uint64_t)q * (uint64_t)f + (1ull << 31)) >> 32);
+}
+static int64_t frac_of(int64_t t, int64_t q) {
+  return (int64_t)(((uint64_t)t << 32) / (uint64_t)q);
+}
+
 static int32_t walk_load(const or_graph *g, const int32_t *walk_q, const int32_t *par,
                          int32_t p, int32_t z, int64_t dt_q, int64_t carry, int32_t carry_link, int trunc,
                          int64_t amount, int64_t *flow_fx, int64_t *carry_out, int32_t *link_out) {
@@ -434,14 +447,14 @@ static int32_t walk_load(const or_graph *g, const int32_t *walk_q, const int32_t
   *carry_out = 0;
   *link_out = -1;
   if (carry_link >= 0) {
-    if (flow_fx) flow_fx[carry_link] += amount;
-    const int64_t at_head = (int64_t)walk_q[carry_link] - carry;
-    if (at_head > dt_q) {  /* still on the link at the end of this interval */
-      *carry_out = carry + dt_q;
+    const int64_t q = walk_q[carry_link];
+    const int64_t rest = q - carried_quanta(q, carry);
+    if (rest > dt_q) {  /* still on the link at the end of this interval */
+      *carry_out = carry + frac_of(dt_q, q);
       *link_out = carry_link;
       return u;
     }
-    elapsed = at_head > 0 ? at_head : 0;
+    elapsed = rest;
     u = g->head[carry_link];
   }
   while (u != z) {
@@ -450,7 +463,7 @@ static int32_t walk_load(const or_graph *g, const int32_t *walk_q, const int32_t
     if (e < 0) return -1;
     if (flow_fx) flow_fx[e] += amount;
     if (trunc == TRUNC_CARRY && elapsed + walk_q[e] > dt_q) {
-      *carry_out = dt_q - elapsed;
+      *carry_out = frac_of(dt_q - elapsed, walk_q[e]);
       *link_out = e;
       return u;
     }
@@ -464,11 +477,11 @@ static int32_t walk_load(const or_graph *g, const int32_t *walk_q, const int32_t
  * walk_q: link times used for the elapsed-time truncation (tree_q for an
  * AON; the final costs for the residual of Alg. 4).  Items carried on a link
  * (od->carry_link) finish it first.  stop_out, carry_out, link_out
- * (nullable): per-item stop node, carried time and carrying link (-1 when
+ * (nullable): per-item stop node, covered fraction and carrying link (-1 when
  * the trip waits at the node or arrived) under truncation mode `trunc`. */
 static void item_carry(const or_od *od, int64_t k, int64_t *c, int32_t *l) {
   *l = od->carry_link ? od->carry_link[k] : -1;
-  *c = (*l >= 0 && od->carry_q) ? od->carry_q[k] : 0;
+  *c = (*l >= 0 && od->carry_frac) ? od->carry_frac[k] : 0;
 }
 
 int32_t or_load(const or_graph *g, const int32_t *walk_q, const int32_t *parent,
@@ -907,9 +920,10 @@ static int64_t scale_amount(int64_t amount_fx, double w) {
 
 /* Re-truncate every path of every accepted AON with the final costs.
  * h_fx[L] receives the truncated link flows h(i); residual entries
- * (stop node, root index, amount, carried time) are written up to res_cap,
- * *res_n gets the number produced (before any merge).  res_carry, res_link
- * (nullable) receive the carried time and carrying link of each entry (0 and
+ * (stop node, root index, amount, covered fraction) are written up to
+ * res_cap, *res_n gets the number produced (before any merge).  res_carry,
+ * res_link (nullable) receive the covered fraction and carrying link of each
+ * entry (0 and
  * -1 for a trip waiting at its stop node). */
 int32_t or_residual(const or_graph *g, const or_od *od, double dt_s, int32_t K,
                     const int32_t *tape_q, const double *tape_alpha, const double *f_final,
@@ -981,9 +995,9 @@ static int cmp_item3(const void *a, const void *b) {
 
 /* merge an item list as the paper keeps residual demand d_{s,q}: trips
  * waiting at a node (link -1) by (root, node), summing amounts; trips on a
- * link (R17) by (root, link), with the amount-weighted mean carried time
- * floor(sum amt * carry / sum amt) in exact 128-bit integers; returns the
- * count */
+ * link (R17) by (root, link), with the amount-weighted mean covered
+ * fraction floor(sum amt * carry / sum amt) in exact 128-bit integers;
+ * returns the count */
 static int64_t merge_items(item3 *buf, int64_t n) {
   qsort(buf, (size_t)n, sizeof(item3), cmp_item3);
   int64_t m = 0;
@@ -1156,11 +1170,10 @@ int32_t or_backward(const or_graph *g, const or_od *od, double dt_s, int32_t ste
       int32_t l0;
       double acc = 0.0;
       item_carry(od, it, &c0, &l0);
-      if (l0 >= 0) {  /* the carried link first, then on from its head (as walk_load) */
-        acc += gbar[l0];
-        const int64_t at_head = (int64_t)qk[l0] - c0;
-        if (at_head > dt_q) { dL_dd[it] += acc; continue; }
-        elapsed = at_head > 0 ? at_head : 0;
+      if (l0 >= 0) {  /* the rest of the carried link (not loaded), then on from its head */
+        const int64_t rest = (int64_t)qk[l0] - carried_quanta(qk[l0], c0);
+        if (rest > dt_q) continue;
+        elapsed = rest;
         u = g->head[l0];
       }
       while (u != z && elapsed < dt_q) {
@@ -1237,16 +1250,19 @@ int32_t or_replay(const or_graph *g, const or_od *od, double dt_s, const or_para
  *  R16 The relative-gap stop takes -1e-12 <= gap <= tol: under truncation a
  *     negative gap certifies nothing (the truncated AON loading need not
  *     minimise sum c g); -1e-12 absorbs rounding at an exact equilibrium.
- *  R17 Carried truncation (Section 3.4 proposes tracking how far the flow
- *     got along a link and adding it up across intervals while it cannot be
- *     propagated to the next link): a trip whose next link would end after
- *     dt stays on that link, carrying the time it has travelled along it; in
- *     the next interval it first finishes that link (reaching the head at
- *     max(q - carry, 0), or staying on it with carry + dt), then follows the
- *     tree from the head (rerouted there, as every interval reroutes).  A
- *     link longer than dt is thus crossed over several intervals.  Residual
- *     demand keeps the paper's d_{s,q} form: trips at a node merge per
- *     (root, node); trips on a link per (root, link) with the
- *     amount-weighted mean carried time (exact merging by carried time
- *     grows the items about fourfold per interval on short intervals).
+ *  R17 Carried truncation (Section 3.4 proposes tracking the distance the
+ *     flow got along a link and adding it up across intervals while it
+ *     cannot be propagated to the next link): a trip whose next link would
+ *     end after dt stays on that link, carrying the fraction of the link it
+ *     covered (2^-32 units); in the next interval it first finishes that
+ *     link at that interval's link time (reaching the head after the
+ *     uncovered rest, or staying on it with the fraction grown by dt / q),
+ *     then follows the tree from the head (rerouted there, as every
+ *     interval reroutes).  A link longer than dt is thus crossed over
+ *     several intervals.  A trip loads a link in the interval it enters it,
+ *     as under R1, so every trip loads each link of its route once.
+ *     Residual demand keeps the paper's d_{s,q} form: trips at a node merge
+ *     per (root, node); trips on a link per (root, link) with the
+ *     amount-weighted mean fraction (exact merging would grow the items
+ *     about fourfold per interval on short intervals).
  */

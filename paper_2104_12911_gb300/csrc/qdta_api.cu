@@ -1161,7 +1161,7 @@ extern "C" int qdta_load_aon(qdta_graph *g, const int32_t *cost_q, const int32_t
   prof_begin(g, s, &pe, 1, 0);
   launch_load(g->d, hq, parent_link, nullptr, 0, nullptr, od->roots, od->n_items, nullptr, od->root_idx,
               od->src, (const long long *)od->amount_fx, dt_q, (unsigned long long *)flow_fx,
-              stop_node, g->status, s, (const long long *)od->carry_q, od->carry_link);
+              stop_node, g->status, s, (const long long *)od->carry_frac, od->carry_link);
   prof_end(g, s, &pe);
   return status_check(g, s);
 }
@@ -1465,11 +1465,11 @@ static int check_od(const qdta_graph *g, const qdta_od *od) {
 }
 
 // items carried on a link, checked on the device: the link exists, its
-// tail is the item's src, the carried time is >= 0 (QDTA_EINVAL otherwise)
+// tail is the item's src, the covered fraction is in [0, 2^32) (QDTA_EINVAL otherwise)
 static int check_carry_items(qdta_graph *g, const qdta_od *od, cudaStream_t s) {
   if (!od || !od->carry_link || od->n_items <= 0) return QDTA_OK;
   RC(status_reset(g, s));
-  launch_check_carry(g->d, od->n_items, od->src, (const long long *)od->carry_q, od->carry_link, g->status, s);
+  launch_check_carry(g->d, od->n_items, od->src, (const long long *)od->carry_frac, od->carry_link, g->status, s);
   return status_check(g, s);
 }
 
@@ -1529,7 +1529,7 @@ static int assign_core(qdta_graph *g, const qdta_od *od, double dt_s, const qdta
   S.root_slot = nullptr; S.item_roots = od->roots;
   S.n_host = od->n_items; S.n_dev = nullptr;
   S.root_idx = od->root_idx; S.src = od->src; S.amount = (const long long *)od->amount_fx;
-  S.carry = (const long long *)od->carry_q;
+  S.carry = (const long long *)od->carry_frac;
   S.carry_link = od->carry_link;
   S.f = flow_out;
   const bool want_tape = p->record_tape && tape_out;
@@ -1595,7 +1595,7 @@ static int assign_batch_graph(const qdta_instance *inst, int n, const qdta_param
     X.root_slot = nullptr; X.item_roots = od->roots;
     X.n_host = od->n_items; X.n_dev = nullptr;
     X.root_idx = od->root_idx; X.src = od->src; X.amount = (const long long *)od->amount_fx;
-    X.carry = (const long long *)od->carry_q;
+    X.carry = (const long long *)od->carry_frac;
     X.carry_link = od->carry_link;
     X.f = inst[i].flow_out;
     RC(solver_alloc(X, "batch", 1, false));
@@ -1688,7 +1688,7 @@ struct Day {
   long long cap_items;
   int *it_root, *it_src;
   long long *it_amt;
-  long long *it_carry;         // items' carried times and links (carried trips in play), else NULL
+  long long *it_carry;         // items' covered fractions and links (carried trips in play), else NULL
   int *it_link;
   CarryAcc ca;                 // carried (root, link) table (mask 0: none)
   int trunc;                   // QDTA_TRUNC_*
@@ -1855,8 +1855,8 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   // trips on links in play: the carried (root, link) table and per-item carries
   bool any_carry = p->truncation == QDTA_TRUNC_CARRY || (resid_in && resid_in->carry_link);
   for (int i = 0; i < N; ++i) any_carry = any_carry || d_orig[i].carry_link != nullptr;
-  if (any_carry && resid_out && (!resid_out->carry_q || !resid_out->carry_link))
-    return fail(QDTA_EINVAL, "resid_out->carry_q and carry_link are needed when trips are carried on links");
+  if (any_carry && resid_out && (!resid_out->carry_frac || !resid_out->carry_link))
+    return fail(QDTA_EINVAL, "resid_out->carry_frac and carry_link are needed when trips are carried on links");
   DevGuard guard(g->device);
   cudaStream_t s = (cudaStream_t)stream;
   for (int i = 0; i < N; ++i) RC(check_carry_items(g, &d_orig[i], s));
@@ -1882,7 +1882,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   long long table_n = 0;
   if (any_carry) {
     // trips on links: an open-addressed (root, link) table of amounts and
-    // exact 128-bit sums of amount x carried time, at most half full when
+    // exact 128-bit sums of amount x covered fraction, at most half full when
     // it holds as many entries as the dense part can; items get room for both
     const long long zl = (long long)Z * (long long)L;
     const long long want = 2 * (D.cap_items < zl ? D.cap_items : zl);
@@ -1921,7 +1921,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   std::vector<OrigTable> tab(N);
   for (int i = 0; i < N; ++i)
     tab[i] = OrigTable{d_orig[i].root_idx, d_orig[i].src, (const long long *)d_orig[i].amount_fx,
-                       d_orig[i].n_items, (const long long *)d_orig[i].carry_q, d_orig[i].carry_link};
+                       d_orig[i].n_items, (const long long *)d_orig[i].carry_frac, d_orig[i].carry_link};
   RC(ws_get(g, "day.tab", (size_t)N, &D.tab));
   CK(cudaMemcpyAsync(D.tab, tab.data(), sizeof(OrigTable) * N, cudaMemcpyHostToDevice, s));
   // solver over the zone list
@@ -1975,7 +1975,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   if (resid_in && resid_in->n_items > 0)
     launch_scatter_items(g->d, resid_in->n_items, resid_in->root_idx, resid_in->src,
                          (const long long *)resid_in->amount_fx, D.dense, s,
-                         (const long long *)resid_in->carry_q, resid_in->carry_link, D.ca, g->status);
+                         (const long long *)resid_in->carry_frac, resid_in->carry_link, D.ca, g->status);
   // day counter lives in the solver's controller
   int dayinit[3] = {0, N, 1};
   CK(cudaMemcpyAsync(&S.ctl->day_i, dayinit, sizeof dayinit, cudaMemcpyHostToDevice, s));
@@ -1997,7 +1997,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   if (resid_out) {
     launch_compact(g->d, Z, D.dense, D.blk_count, D.blk_off, resid_out->capacity, resid_out->root_idx,
                    resid_out->src, (long long *)resid_out->amount_fx, D.n_items_dev, g->status, s,
-                   (long long *)resid_out->carry_q, resid_out->carry_link, D.ca);
+                   (long long *)resid_out->carry_frac, resid_out->carry_link, D.ca);
     long long cnt = 0;
     CK(cudaMemcpyAsync(&cnt, D.n_items_dev, 8, cudaMemcpyDeviceToHost, s));
     RC(status_check(g, s));
@@ -2080,7 +2080,7 @@ extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_dd
     CK(cudaMemsetAsync(gfx, 0, L * 8, s));
     launch_load(g->d, hq, parent, nullptr, 0, nullptr, t->od.roots, n, nullptr, t->od.root_idx, t->od.src,
                 (const long long *)t->od.amount_fx, dt_q, gfx, nullptr, g->status, s,
-                (const long long *)t->od.carry_q, t->od.carry_link);
+                (const long long *)t->od.carry_frac, t->od.carry_link);
     const double *gb = lam;
     if (k > 0) {
       const double *fprev = t->f + (size_t)(k - 1) * L;
@@ -2091,7 +2091,7 @@ extern "C" int qdta_backward(qdta_tape *t, const double *dL_dflow, double *dL_dd
       gb = gbar;
     }
     launch_gather(g->d, hq, parent, t->od.roots, n, t->od.root_idx, t->od.src, dt_q, gb, dL_ddemand,
-                  g->status, s, (const long long *)t->od.carry_q, t->od.carry_link);
+                  g->status, s, (const long long *)t->od.carry_frac, t->od.carry_link);
     if (k > 0) std::swap(lam, lam2);
   }
   return status_check(g, s);

@@ -382,7 +382,7 @@ int sssp_blocks_per_sm(bool use_smem, int V);
 
 // Residual trips on a link (QDTA_TRUNC_CARRY) merge per (root, link) in an
 // open-addressed table: key root * L + link (~0 when empty), the amount, and
-// the exact sum of amount x carried time (two 64-bit words, low then high);
+// the exact sum of amount x covered fraction (two 64-bit words, low then high);
 // the merged item carries the floor of the mean.  mask == 0: no table.
 struct CarryAcc {
   unsigned long long *key = nullptr;   // [mask + 1]
@@ -401,7 +401,7 @@ void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const
                  unsigned *status, cudaStream_t s, const long long *carry = nullptr,
                  const int *carry_link = nullptr);
 // trunc 1 (carry): a trip still on a link at the end of the interval goes
-// to the carried table `ca` with its carried time; trips stopping at a node
+// to the carried table `ca` with the fraction covered; trips stopping at a node
 // go to `dense`
 void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *parent,
                      const int *parent_slot_dev, long long slot_stride, const int *root_slot,
@@ -464,8 +464,8 @@ void launch_scatter_items(const GraphDev &g, long long n, const int *root_idx, c
                           CarryAcc ca = CarryAcc{}, unsigned *status = nullptr);
 // dense (root, node) accumulator -> items in (root, node) order, then (when
 // ca.mask is set) the carried table's entries appended in slot order with
-// their mean carried times and links (src = the link's tail); carry_out and
-// link_out (nullable) receive each item's carried time and link (0 and -1
+// their mean covered fractions and links (src = the link's tail); carry_out and
+// link_out (nullable) receive each item's covered fraction and link (0 and -1
 // for the first part).  Both sources are cleared; the item count never
 // exceeds cap (ST_CAPACITY when entries were dropped).  blk_count / blk_off
 // must hold max(R * V, ca.mask + 1) / 4096 + 1 entries.

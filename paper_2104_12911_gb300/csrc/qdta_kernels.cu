@@ -1625,16 +1625,27 @@ void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStrea
   pack_head_q_kernel<<<cdiv(g.L, 256), 256, 0, s>>>(g.L, g.head, q, head_q);
 }
 
-// A trip carried on link cl (carry_link >= 0) with c quanta travelled along
-// it reaches the link's head at max(q - c, 0), or is still on the link at
-// the end of the interval when q - c > dt_q (Section 3.4, carried
-// truncation).  Returns false in the second case; else sets u and elapsed.
-__device__ __forceinline__ bool finish_carried_link(const int2 *__restrict__ head_q, int cl, long long c,
+// Carried truncation (Section 3.4): a position on a link is the fraction f
+// of it covered, in units of 2^-32.  On a link of q quanta, f stands for
+// round(q f / 2^32) quanta (halves up); t < q quanta cover floor(t 2^32 / q).
+__device__ __forceinline__ long long carried_quanta(long long q, long long f) {
+  return (long long)(((unsigned long long)q * (unsigned long long)f + (1ull << 31)) >> 32);
+}
+__device__ __forceinline__ long long frac_of(long long t, long long q) {
+  return (long long)(((unsigned long long)t << 32) / (unsigned long long)q);
+}
+
+// A trip carried on link cl (carry_link >= 0) having covered the fraction f
+// of it reaches the link's head after the uncovered rest, or is still on the
+// link at the end of the interval when the rest exceeds dt_q.  Returns false
+// in the second case; else sets u and elapsed.  The link itself is not
+// loaded again: a trip loads a link in the interval it enters it.
+__device__ __forceinline__ bool finish_carried_link(const int2 *__restrict__ head_q, int cl, long long f,
                                                     long long dt_q, int &u, long long &elapsed) {
   const int2 hq = __ldg(&head_q[cl]);
-  const long long at_head = (long long)hq.y - c;
-  if (at_head > dt_q) return false;
-  elapsed = at_head > 0 ? at_head : 0;
+  const long long rest = (long long)hq.y - carried_quanta(hq.y, f);
+  if (rest > dt_q) return false;
+  elapsed = rest;
   u = hq.x;
   return true;
 }
@@ -1642,8 +1653,9 @@ __device__ __forceinline__ bool finish_carried_link(const int2 *__restrict__ hea
 // One thread per item: walk origin -> root along the destination tree.  A
 // link is loaded iff the elapsed time at its tail is < dt_q; the walk ends
 // at the first node reached at >= dt_q (the stop node) or at the root.  An
-// item carried on a link loads it and walks on from its head; one still on
-// it at the end of the interval stops at src (the link's tail).
+// item carried on a link walks on from its head (the link was loaded when
+// the trip entered it); one still on it at the end of the interval stops at
+// src (the link's tail).
 __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *__restrict__ parent,
                             const int *parent_slot_dev, long long slot_stride,
                             const int *__restrict__ root_slot, const int *__restrict__ roots,
@@ -1664,7 +1676,6 @@ __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *_
     long long elapsed = 0;
     const int cl = carry_link ? carry_link[k] : -1;
     if (cl >= 0) {
-      if (amt) atomicAdd(&flow_fx[cl], amt);
       if (!finish_carried_link(head_q, cl, carry ? carry[k] : 0, dt_q, u, elapsed)) {
         if (stop_out) stop_out[k] = u;
         continue;
@@ -1707,7 +1718,7 @@ __global__ void cap_copy_kernel(int L, const double *__restrict__ src, double *_
 }
 
 // items carried on a link: the link exists, starts at the item's src, and
-// the carried time is >= 0 (ST_BADARG otherwise)
+// the covered fraction is in [0, 2^32) (ST_BADARG otherwise)
 __global__ void check_carry_kernel(int L, long long n, const int *__restrict__ src,
                                    const long long *__restrict__ carry, const int *__restrict__ carry_link,
                                    const int *__restrict__ tail, unsigned *status) {
@@ -1715,7 +1726,8 @@ __global__ void check_carry_kernel(int L, long long n, const int *__restrict__ s
        k += (long long)gridDim.x * blockDim.x) {
     const int cl = carry_link[k];
     if (cl < 0) continue;
-    if (cl >= L || tail[cl] != src[k] || (carry && carry[k] < 0)) atomicOr(status, ST_BADARG);
+    if (cl >= L || tail[cl] != src[k] || (carry && (carry[k] < 0 || carry[k] >= (1ll << 32))))
+      atomicOr(status, ST_BADARG);
   }
 }
 
@@ -1771,7 +1783,7 @@ __device__ __forceinline__ unsigned long long carry_hash(unsigned long long x) {
   return x ^ (x >> 31);
 }
 
-// one residual trip on a link: its amount and amount x carried time join
+// one residual trip on a link: its amount and amount x covered fraction join
 // the entry of key root * L + link (linear probing; a key, once claimed,
 // stays until the compaction clears the table).  A full table sets
 // ST_CAPACITY and drops the trip.
@@ -1800,7 +1812,8 @@ __device__ __forceinline__ void carry_add(const CarryAcc &ca, unsigned long long
 // h and, if the walk stops before the root, joins the residual demand of the
 // next interval: in the dense (root, node) accumulator, or, when the trip is
 // still on a link (trunc = 1, or an item carried on a link that it does not
-// finish), in the carried table under (root, link) with its carried time.
+// finish), in the carried table under (root, link) with the fraction of the
+// link covered.
 __global__ void residual_kernel(int V, int L, const int2 *__restrict__ head_q_fin,
                                 const int *__restrict__ parent, const int *parent_slot_dev,
                                 long long slot_stride, const int *__restrict__ root_slot,
@@ -1826,10 +1839,9 @@ __global__ void residual_kernel(int V, int L, const int2 *__restrict__ head_q_fi
     const int cl = carry_link ? carry_link[k] : -1;
     if (cl >= 0) {
       const long long c0 = carry ? carry[k] : 0;
-      atomicAdd(&h_fx[cl], (unsigned long long)amt);
       if (!finish_carried_link(head_q_fin, cl, c0, dt_q, u, elapsed)) {
         on_link = cl;
-        tau = c0 + dt_q;
+        tau = c0 + frac_of(dt_q, __ldg(&head_q_fin[cl]).y);
       }
     }
     int steps = 0;
@@ -1841,7 +1853,7 @@ __global__ void residual_kernel(int V, int L, const int2 *__restrict__ head_q_fi
       const int2 hq = __ldg(&head_q_fin[e]);
       if (trunc && elapsed + hq.y > dt_q) {  // on this link at the end of the interval
         on_link = e;
-        tau = dt_q - elapsed;
+        tau = frac_of(dt_q - elapsed, hq.y);
         break;
       }
       elapsed += hq.y;
@@ -2613,10 +2625,10 @@ __global__ void compact_scan_kernel(int nblk, const int *blk_count, long long *b
 }
 
 // ordered write of the nonzero entries of each tile.  Dense part (keys ==
-// NULL): entry root * V + node, written root-major, node-minor, carried time
+// NULL): entry root * V + node, written root-major, node-minor, covered fraction
 // 0 and link -1.  Carried part: slot order of the table; the key gives
-// (root, link), src is the link's tail, the carried time is
-// floor(sum amount x carried time / amount); keys and sums are cleared.
+// (root, link), src is the link's tail, the covered fraction is
+// floor(sum amount x fraction / amount); keys and sums are cleared.
 __global__ void compact_write_kernel(long long total, int V, unsigned long long *dense,
                                      const long long *blk_off, long long cap, int *root_idx,
                                      int *src, long long *amount, long long *carry_out,
@@ -2946,13 +2958,8 @@ __global__ void gather_kernel(int V, const int2 *__restrict__ head_q, const int 
     long long elapsed = 0;
     double acc = 0.0;
     const int cl = carry_link ? carry_link[k] : -1;
-    if (cl >= 0) {  // the carried link first, then on from its head
-      acc = add(acc, gbar[cl]);
-      if (!finish_carried_link(head_q, cl, carry ? carry[k] : 0, dt_q, u, elapsed)) {
-        dd[k] = add(dd[k], acc);
-        continue;
-      }
-    }
+    if (cl >= 0 && !finish_carried_link(head_q, cl, carry ? carry[k] : 0, dt_q, u, elapsed))
+      continue;  // the rest of the carried link (not loaded), then on from its head
     int steps = 0;
     while (u != z && elapsed < dt_q) {
       const int e = par[u];

@@ -44,7 +44,7 @@ class GraphDesc(C.Structure):
 class OD(C.Structure):
     _fields_ = [("n_roots", C.c_int32), ("roots", C.c_void_p), ("n_items", C.c_int64),
                 ("root_idx", C.c_void_p), ("src", C.c_void_p), ("amount_fx", C.c_void_p),
-                ("carry_q", C.c_void_p), ("carry_link", C.c_void_p)]
+                ("carry_frac", C.c_void_p), ("carry_link", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -65,7 +65,7 @@ class Stats(C.Structure):
 
 class Residual(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("root_idx", C.c_void_p), ("src", C.c_void_p),
-                ("amount_fx", C.c_void_p), ("count", C.c_int64), ("carry_q", C.c_void_p),
+                ("amount_fx", C.c_void_p), ("count", C.c_int64), ("carry_frac", C.c_void_p),
                 ("carry_link", C.c_void_p)]
 
 
@@ -219,7 +219,7 @@ class DeviceOD:
     amount_fx: torch.Tensor
     # trips carried on a link (both None, or int64 / int32 per item): the
     # time travelled along carry_link (-1: the trip waits at src)
-    carry_q: torch.Tensor = None
+    carry_frac: torch.Tensor = None
     carry_link: torch.Tensor = None
 
     @classmethod
@@ -237,7 +237,7 @@ class DeviceOD:
     def struct(self) -> OD:
         return OD(int(self.roots.shape[0]), self.roots.data_ptr(), self.n_items,
                   self.root_idx.data_ptr(), self.src.data_ptr(), self.amount_fx.data_ptr(),
-                  self.carry_q.data_ptr() if self.carry_q is not None else None,
+                  self.carry_frac.data_ptr() if self.carry_frac is not None else None,
                   self.carry_link.data_ptr() if self.carry_link is not None else None)
 
 
@@ -382,7 +382,7 @@ def qdta_run_day(g: Graph, days, dt_s: float, params: Params, resid_in: DeviceOD
     resid = None
     if rout is not None:
         n = rout.count
-        # root index, stop node (a carried trip: its link's tail), amount, carried time, link (-1: none)
+        # root index, stop node (a carried trip: its link's tail), amount, covered fraction (2^-32 units), link (-1: none)
         resid = tuple(b[:n] for b in bufs)
     return flow_out, [s.as_dict() for s in st], rc, resid
 

@@ -689,8 +689,8 @@ def test_backward_matches_oracle(step, carried):
     dod = Q.DeviceOD.of(dem)
     if carried:  # half of the trips start on a link (the adjoint gathers it first)
         carry, link = _carried_items(net, dem, 3)
-        od = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_q=carry, carry_link=link)
-        dod.carry_q, dod.carry_link = T(carry, np.int64), T(link, np.int32)
+        od = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_frac=carry, carry_link=link)
+        dod.carry_frac, dod.carry_link = T(carry, np.int64), T(link, np.int32)
     p = oracle.make_params(Q.STEP[step], oracle.STOP_NONE, 10)
     f_o, st_o, rc, tape_o = oracle.assign_interval(og, od, 600.0, p, tape=True)
     g = Q.Graph(net)
@@ -955,8 +955,8 @@ def test_run_day_carried_truncation_bit_exact(schedule, step, stop, it):
 
 
 def test_carried_truncation_crosses_a_long_link_on_the_gpu():
-    """The uncongested chain of 1000 s links with 300 s intervals: link k
-    carries the trip in exactly the intervals overlapping [1000 k, 1000 (k + 1)) s."""
+    """The uncongested chain of 1000 s links with 300 s intervals: link k is
+    loaded in the interval the trip enters it, the one containing 1000 k s."""
     net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
     g = Q.Graph(net)
     zones = T([3], np.int32)
@@ -964,9 +964,8 @@ def test_carried_truncation_crosses_a_long_link_on_the_gpu():
     one = Q.DeviceOD(zones, T([0], np.int32), T([0], np.int32), T([1 << 32], np.int64))
     empty = Q.DeviceOD(zones, T([], np.int32), T([], np.int32), T([], np.int64))
     want = np.zeros((N, 3))
-    for i in range(N):
-        for k in range(3):
-            want[i, k] = float(max(300 * i, 1000 * k) < min(300 * (i + 1), 1000 * (k + 1)))
+    for k in range(3):
+        want[(1000 * k) // 300, k] = 1.0
     for schedule in ("plain", "graph"):
         f, st, rc, _ = Q.qdta_run_day(g, [one] + [empty] * (N - 1), 300.0,
                                       Q.make_params("msa", "none", 0, schedule=schedule, truncation="carry"))
@@ -995,8 +994,8 @@ def test_carried_day_resumes_from_its_residual(schedule):
 
 
 def _carried_items(net, dem, seed):
-    """half of the items put on a random out-link of their src, with carried
-    times from 0 to past the link's free-flow time"""
+    """half of the items put on a random out-link of their src, having
+    covered a random fraction of it (0 included)"""
     rng = np.random.default_rng(seed)
     out = [[] for _ in range(net.n_nodes)]
     for a, t in enumerate(np.asarray(net.tail)):
@@ -1006,7 +1005,7 @@ def _carried_items(net, dem, seed):
     for k in np.flatnonzero(rng.random(dem.n_items) < 0.5):
         a = out[int(dem.src[k])][rng.integers(len(out[int(dem.src[k])]))]
         link[k] = a
-        carry[k] = rng.integers(0, int(net.fftime_q[a]) * 2 + 2)
+        carry[k] = 0 if rng.random() < 0.1 else rng.integers(0, 1 << 32)
     return carry, link
 
 
@@ -1017,7 +1016,7 @@ def test_load_aon_with_carried_trips_matches_the_oracle(small):
     carry, link = _carried_items(inst.net, dem, 4)
     q = (inst.net.fftime_q * rng.uniform(1.0, 2.0, og.n_links)).astype(np.int32)
     par_o, _ = oracle.sssp(og, q, dem.roots, want_dist=False)
-    od_o = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_q=carry, carry_link=link)
+    od_o = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_frac=carry, carry_link=link)
     for dt_q in (600, 6000, 30000):
         f_o, s_o, rc = oracle.load(og, q, par_o, od_o, dt_q)
         od_g = Q.DeviceOD(T(dem.roots, np.int32), T(dem.root_idx, np.int32), T(dem.src, np.int32),
@@ -1034,7 +1033,7 @@ def test_interval_with_carried_trips_matches_the_oracle(small, schedule):
     inst, g, og = small
     dem = inst.demand[0]
     carry, link = _carried_items(inst.net, dem, 9)
-    od_o = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_q=carry, carry_link=link)
+    od_o = oracle.OracleOD(dem.roots, dem.root_idx, dem.src, dem.amount_fx, carry_frac=carry, carry_link=link)
     od_g = Q.DeviceOD(T(dem.roots, np.int32), T(dem.root_idx, np.int32), T(dem.src, np.int32),
                       T(dem.amount_fx, np.int64), T(carry, np.int64), T(link, np.int32))
     for trunc in ("node", "carry"):
@@ -1047,7 +1046,9 @@ def test_interval_with_carried_trips_matches_the_oracle(small, schedule):
             assert st_g[key] == st_o[key], (trunc, key)
 
 
-def test_carried_item_on_a_link_that_does_not_start_at_src_is_rejected(small):
+def test_carried_items_are_checked(small):
+    """A carried link must start at the item's src and exist; the covered
+    fraction must lie in [0, 2^32)."""
     inst, g, og = small
     dem = inst.demand[0]
     tail = np.asarray(inst.net.tail)
@@ -1061,6 +1062,13 @@ def test_carried_item_on_a_link_that_does_not_start_at_src_is_rejected(small):
     od_g.carry_link = T(link, np.int32)
     with pytest.raises(Q.QdtaError):
         Q.qdta_assign_interval(g, od_g, 300.0, Q.make_params("msa", "none", 2))
+    link[0] = int(np.flatnonzero(tail == dem.src[0])[0])  # a link from src, but a whole link covered
+    od_g.carry_link = T(link, np.int32)
+    od_g.carry_frac = T(np.full(dem.n_items, 1 << 32), np.int64)
+    with pytest.raises(Q.QdtaError):
+        Q.qdta_assign_interval(g, od_g, 300.0, Q.make_params("msa", "none", 2))
+    od_g.carry_frac = T(np.full(dem.n_items, (1 << 32) - 1), np.int64)  # the largest valid fraction
+    Q.qdta_assign_interval(g, od_g, 300.0, Q.make_params("msa", "none", 2))
 
 
 # ---------------------------------------------------------------------------

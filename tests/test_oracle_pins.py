@@ -684,13 +684,18 @@ def test_day_advances_a_trip_one_link_per_interval_when_links_outlast_dt():
     assert list(nit) == [1, 1, 1, 0]
 
 
+def _frac(x):
+    """a fraction of a link in the 2^-32 units of the carried position"""
+    return x * 2.0 ** -32
+
+
 def test_carried_truncation_crosses_a_long_link_over_several_intervals():
     """Section 3.4's alternative to Eq. 2 (reading R17): links of 1000 s on an
-    uncongested chain, intervals of 300 s.  A trip leaving at time 0 is on
-    link k during [1000 k, 1000 (k + 1)) s, so link k must carry it in exactly
-    the intervals that overlap that span, and it arrives at 3000 s, the end of
-    interval 9.  Under the node rule (R1) the same trip advances one link per
-    interval instead."""
+    uncongested chain, intervals of 300 s.  A trip leaving node 0 at time 0
+    enters link k at 1000 k s, so link k is loaded in exactly the interval
+    containing 1000 k s (0, 3 and 6); the trip is in the network until it
+    arrives at 3000 s, the end of interval 9.  Under the node rule (R1) the
+    same trip advances one link per interval instead."""
     net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
     g = oracle.OracleGraph(net)
     zones = np.array([3], np.int32)
@@ -700,9 +705,8 @@ def test_carried_truncation_crosses_a_long_link_over_several_intervals():
                          amount_fx=np.zeros(0, np.int64))
     N = 11
     want = np.zeros((N, 3))
-    for i in range(N):
-        for k in range(3):
-            want[i, k] = float(max(300 * i, 1000 * k) < min(300 * (i + 1), 1000 * (k + 1)))
+    for k in range(3):
+        want[(1000 * k) // 300, k] = 1.0
     f, st, nit, rn, rc = oracle.run_day(g, zones, [one] + [empty] * (N - 1), 300.0,
                                         oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0,
                                                            truncation=oracle.TRUNC_CARRY))
@@ -714,18 +718,10 @@ def test_carried_truncation_crosses_a_long_link_over_several_intervals():
     np.testing.assert_array_equal(np.asarray(f).reshape(4, 3), [[1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, 0]])
 
 
-def test_carried_trips_merge_with_their_mean_carried_time():
-    """Reading R17's merge: trips waiting at the same node for the same zone
-    are one residual item (the paper's d_{s,q}); trips carrying a partial
-    link merge apart from those at the node, with the amount-weighted mean
-    carried time.  Chain of 1000 s links, 300 s intervals: trip A (1 trip)
-    leaves node 0 in interval 0, B (3 trips) in interval 1.  After interval 1
-    A carries 600 s and B 300 s beyond node 0, so interval 2 starts one item
-    of 4 trips carrying (600 + 3 * 300) / 4 = 375 s.  From there, by hand:
-    the group is on link 0 until it reaches node 1 at 25 s into interval 4,
-    on link 1 until 125 s into interval 7, and arrives 225 s into interval 10."""
+def _two_groups(N):
+    """chain of 1000 s links, 300 s intervals: 1 trip leaves node 0 in
+    interval 0, 3 trips in interval 1"""
     net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
-    g = oracle.OracleGraph(net)
     zones = np.array([3], np.int32)
 
     def trips(n):
@@ -733,78 +729,118 @@ def test_carried_trips_merge_with_their_mean_carried_time():
                             amount_fx=np.array([n << 32], np.int64))
     empty = synth.Demand(roots=zones, root_idx=np.zeros(0, np.int32), src=np.zeros(0, np.int32),
                          amount_fx=np.zeros(0, np.int64))
+    return oracle.OracleGraph(net), zones, [trips(1), trips(3)] + [empty] * (N - 2)
+
+
+def test_carried_trips_merge_with_their_mean_covered_fraction():
+    """Reading R17's merge: trips waiting at the same node for the same zone
+    are one residual item (the paper's d_{s,q}); trips on a link merge per
+    (zone, link) with the amount-weighted mean fraction of the link covered.
+    After interval 1 the first trip has covered 0.6 of link 0 and the three
+    later ones 0.3, so interval 2 starts one item of 4 trips at
+    (0.6 + 3 x 0.3) / 4 = 0.375.  From there, by hand: the group reaches
+    node 1 at 25 s into interval 4 (entering link 1 then), node 2 at 125 s
+    into interval 7, and arrives 225 s into interval 10.  Each link is loaded
+    in the interval the trips enter it."""
     N = 12
-    f, st, nit, rn, rc = oracle.run_day(g, zones, [trips(1), trips(3)] + [empty] * (N - 2), 300.0,
-                                        oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0,
-                                                           truncation=oracle.TRUNC_CARRY))
+    g, zones, days = _two_groups(N)
+    f, st, nit, rn, rc = oracle.run_day(g, zones, days, 300.0, oracle.make_params(
+        oracle.STEP_MSA, oracle.STOP_NONE, 0, truncation=oracle.TRUNC_CARRY))
     assert rc >= 0
-    want = [[1, 0, 0], [4, 0, 0], [4, 0, 0], [4, 0, 0], [4, 4, 0], [0, 4, 0], [0, 4, 0], [0, 4, 4],
-            [0, 0, 4], [0, 0, 4], [0, 0, 4], [0, 0, 0]]
+    want = np.zeros((N, 3))
+    want[0, 0], want[1, 0], want[4, 1], want[7, 2] = 1, 3, 4, 4
     np.testing.assert_array_equal(np.asarray(f).reshape(N, 3), want)
     assert list(nit) == [1, 2] + [1] * 9 + [0] and rn == 0
 
 
 def test_day_residual_holds_the_merged_carried_group():
     """The residual a day leaves, for the two trip groups of the test above:
-    after intervals 0-1 one item of 4 trips on link 0 carrying 375 s; after
-    intervals 0-4 the group is on link 1 (tail node 1), 275 s along it (it
-    reached node 1 at 25 s into interval 4).  Carried times are in quanta of
-    0.01 s."""
-    net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
-    g = oracle.OracleGraph(net)
-    zones = np.array([3], np.int32)
-
-    def trips(n):
-        return synth.Demand(roots=zones, root_idx=np.array([0], np.int32), src=np.array([0], np.int32),
-                            amount_fx=np.array([n << 32], np.int64))
-    empty = synth.Demand(roots=zones, root_idx=np.zeros(0, np.int32), src=np.zeros(0, np.int32),
-                         amount_fx=np.zeros(0, np.int64))
-    p = oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0, truncation=oracle.TRUNC_CARRY)
-    for n_int, want in ((2, (0, 0, 4 << 32, 37500, 0)), (5, (0, 1, 4 << 32, 27500, 1))):
-        *_, rn, rc, res = oracle.run_day(g, zones, [trips(1), trips(3)] + [empty] * (n_int - 2), 300.0, p,
-                                         want_resid=True)
+    after intervals 0-1 one item of 4 trips on link 0 having covered 0.375 of
+    it; after intervals 0-4 the group is on link 1 (tail node 1), 0.275 along
+    it (it reached node 1 at 25 s into interval 4).  Fractions in units of
+    2^-32, floored at each step, so within a few units of the exact value."""
+    for n_int, (src, link, frac) in ((2, (0, 0, 0.375)), (5, (1, 1, 0.275))):
+        g, zones, days = _two_groups(n_int)
+        p = oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0, truncation=oracle.TRUNC_CARRY)
+        *_, rn, rc, res = oracle.run_day(g, zones, days, 300.0, p, want_resid=True)
         assert rc >= 0 and rn == 1
-        assert tuple(int(a[0]) for a in res) == want, res
+        root, s_, amt, f_, l_ = (int(a[0]) for a in res)
+        assert (root, s_, amt, l_) == (0, src, 4 << 32, link)
+        assert abs(_frac(f_) - frac) < 8 * 2.0 ** -32, _frac(f_)
 
 
-def test_carried_truncation_stop_node_and_carried_time():
+def test_carried_truncation_stop_node_and_covered_fraction():
     """One walk on the uncongested chain of 1000 s links for a trip already at
-    position P seconds from node 0 (on link P // 1000 having travelled
-    P mod 1000 along it, or at the node when that is 0): after an interval of
-    300 s it is at position P + 300, on link (P + 300) // 1000 with carried time
-    (P + 300) mod 1000, at a node when that is 0, and has arrived at node 3
-    when P + 300 >= 3000."""
+    position P seconds from node 0 (on link P // 1000 having covered
+    (P mod 1000) / 1000 of it, or at the node when that is 0): after an
+    interval of 300 s it is at position P + 300, on link (P + 300) // 1000
+    having covered ((P + 300) mod 1000) / 1000 of it, at a node when that is
+    0, and has arrived at node 3 when P + 300 >= 3000.  It loads only the
+    links it enters."""
     net = synth.chain_network([1000.0, 1000.0, 1000.0], [1e9, 1e9, 1e9])
     g = oracle.OracleGraph(net)
     par, _ = oracle.sssp(g, net.fftime_q, np.array([3], np.int32), want_dist=False)
     for pos in (0, 100, 600, 700, 900, 1000, 1750, 2700, 2850):
         node, along = divmod(pos, 1000)
         od = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([node], np.int32),
-                             np.array([1 << 32], np.int64), carry_q=np.array([along * 100], np.int64),
+                             np.array([1 << 32], np.int64),
+                             carry_frac=np.array([(along << 32) // 1000], np.int64),
                              carry_link=np.array([node if along else -1], np.int32))
-        _, stop, carry, link, rc = oracle.load(g, net.fftime_q, par, od, 30000, truncation=oracle.TRUNC_CARRY,
+        f, stop, carry, link, rc = oracle.load(g, net.fftime_q, par, od, 30000, truncation=oracle.TRUNC_CARRY,
                                                want_carry=True)
         t = pos + 300
-        want = (3, 0, -1) if t >= 3000 else (t // 1000, (t % 1000) * 100, (t // 1000) if t % 1000 else -1)
-        assert rc == 0 and (stop[0], carry[0], link[0]) == want, (pos, stop[0], carry[0], link[0])
+        entered = [k for k in range(3) if pos <= 1000 * k < t and (1000 * k > pos or along == 0)]
+        assert rc == 0 and list(f >> 32) == [int(k in entered) for k in range(3)], (pos, f >> 32)
+        if t >= 3000:
+            assert (stop[0], carry[0], link[0]) == (3, 0, -1)
+        elif t % 1000 == 0:
+            assert (stop[0], carry[0], link[0]) == (t // 1000, 0, -1), pos
+        else:
+            assert (stop[0], link[0]) == (t // 1000, t // 1000), pos
+            assert abs(_frac(carry[0]) - (t % 1000) / 1000) < 4 * 2.0 ** -32, (pos, _frac(carry[0]))
+
+
+def test_carried_position_is_a_fraction_of_the_link():
+    """Section 3.4 tracks the distance covered on a link: a trip that covered
+    0.3 of a link whose time then doubles has 0.7 x 2000 s = 1400 s left, not
+    the 1700 s a carried time would leave.  Chain of one 1000 s link, link
+    time 2000 s in the next interval (given directly as the walk's link
+    times), interval of 1000 s: 0.3 + 1000 / 2000 = 0.8 covered; with 1500 s
+    it arrives at 1400 s."""
+    net = synth.chain_network([1000.0], [1e9])
+    g = oracle.OracleGraph(net)
+    q2 = np.array([200000], np.int32)
+    par, _ = oracle.sssp(g, q2, np.array([1], np.int32), want_dist=False)
+    od = oracle.OracleOD(np.array([1], np.int32), np.array([0], np.int32), np.array([0], np.int32),
+                         np.array([1 << 32], np.int64), carry_frac=np.array([(3 << 32) // 10], np.int64),
+                         carry_link=np.array([0], np.int32))
+    f, stop, carry, link, rc = oracle.load(g, q2, par, od, 100000, truncation=oracle.TRUNC_CARRY, want_carry=True)
+    assert rc == 0 and int(f[0]) == 0 and (stop[0], link[0]) == (0, 0)
+    assert abs(_frac(carry[0]) - 0.8) < 4 * 2.0 ** -32
+    f, stop, carry, link, rc = oracle.load(g, q2, par, od, 150000, truncation=oracle.TRUNC_CARRY, want_carry=True)
+    assert rc == 0 and (stop[0], carry[0], link[0]) == (1, 0, -1)
+    for dt_q in (139999, 140000):  # the rest is exactly 140000 quanta
+        _, stop, _, link, _ = oracle.load(g, q2, par, od, dt_q, truncation=oracle.TRUNC_CARRY, want_carry=True)
+        assert (stop[0], link[0]) == ((0, 0) if dt_q < 140000 else (1, -1))
 
 
 def test_carried_trip_finishes_its_link_before_rerouting():
     """A trip carried on link 0->2 of the diamond (routes 0->1->3 and
     0->2->3) stays on it although the tree from node 0 leads through node 1:
-    it loads 0->2, then follows the tree from node 2.  The same trip waiting
-    at node 0 instead (no carry) takes 0->1."""
+    it covers the rest of 0->2, then follows the tree from node 2, loading
+    only 2->3 (0->2 was loaded when it was entered).  The same trip waiting
+    at node 0 instead takes 0->1."""
     net = _diamond([200, 340, 1000, 400], [1e9, 1e9, 1e9, 1e9])  # links 0->1, 0->2, 1->3, 2->3
     g = oracle.OracleGraph(net)
     q = np.array([20000, 90000, 20000, 20000], np.int32)  # 0->1->3 is shorter than 0->2->3
     par, _ = oracle.sssp(g, q, np.array([3], np.int32), want_dist=False)
     assert par[0][0] == 0  # the tree leaves node 0 by link 0->1
     on = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([0], np.int32),
-                         np.array([1 << 32], np.int64), carry_q=np.array([60000], np.int64),
+                         np.array([1 << 32], np.int64), carry_frac=np.array([(2 << 32) // 3], np.int64),
                          carry_link=np.array([1], np.int32))
     f, stop, carry, link, rc = oracle.load(g, q, par, on, 90000, truncation=oracle.TRUNC_CARRY, want_carry=True)
-    # 300 s left on 0->2 (reaching node 2 at 300 s), then 200 s on 2->3: arrived at 500 s
-    assert rc == 0 and list(f >> 32) == [0, 1, 0, 1] and (stop[0], carry[0], link[0]) == (3, 0, -1)
+    # 1/3 of 900 s left on 0->2 (node 2 at 300 s), then 200 s on 2->3: arrived at 500 s
+    assert rc == 0 and list(f >> 32) == [0, 0, 0, 1] and (stop[0], carry[0], link[0]) == (3, 0, -1)
     at = oracle.OracleOD(np.array([3], np.int32), np.array([0], np.int32), np.array([0], np.int32),
                          np.array([1 << 32], np.int64))
     f, stop, rc = oracle.load(g, q, par, at, 90000, truncation=oracle.TRUNC_CARRY)
