@@ -49,7 +49,7 @@ METRIC = "Full-day QDTA s @rel-gap 1e-4, batched vs plain on 1 GB300; SSSP GTEPS
 # by the roots per launch.  Only kernels whose code is unchanged since their
 # capture are listed.
 SSSP_DRAM_BYTES_PER_ROOT = {
-    "sssp_smq_kernel<256,rank32,2,true>": (1.324410e9 + 2.547958e9) / 608,
+    "sssp_smq_kernel<256,rank32,2,true>": (1.338081e9 + 2.564112e9) / 608,
 }
 
 
@@ -892,7 +892,9 @@ def main():
                     "kernel": kname,
                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                     "sssp_avg_ms": avg_ms, "roots_per_launch": R_avg, "gteps": gteps,
-                    "sssp_share_of_plain_day": prof["sssp_ms"] / plain_ms if plain_ms else None}
+                    "sssp_share_of_plain_day": prof["sssp_ms"] / plain_ms if plain_ms else None,
+                    "load_share_of_plain_day": prof["load_ms"] / plain_ms if plain_ms else None,
+                    "sweep_share_of_plain_day": prof["sweep_ms"] / plain_ms if plain_ms else None}
 
     tot = {k: sum(s[k] for s in stats) for k in ("iterations", "aon_calls", "ls_passes")}
     cfg["fw_iterations_per_day"] = tot["iterations"]
