@@ -382,8 +382,10 @@ int sssp_blocks_per_sm(bool use_smem, int V);
 
 // Residual trips on a link (QDTA_TRUNC_CARRY) merge per (root, link) in an
 // open-addressed table: key root * L + link (~0 when empty), the amount, and
-// the exact sum of amount x covered fraction (two 64-bit words, low then high);
-// the merged item carries the floor of the mean.  mask == 0: no table.
+// the exact sum of amount x covered fraction as two 64-bit words: the sum of
+// the terms' low 32 bits, then the sum of their parts above 2^32 (sum =
+// word1 * 2^32 + word0); the merged item carries the floor of the mean.
+// mask == 0: no table.
 struct CarryAcc {
   unsigned long long *key = nullptr;   // [mask + 1]
   unsigned long long *amt = nullptr;   // [mask + 1]

@@ -1787,7 +1787,7 @@ __device__ __forceinline__ unsigned long long carry_hash(unsigned long long x) {
 // the entry of key root * L + link (linear probing; a key, once claimed,
 // stays until the compaction clears the table).  A full table sets
 // ST_CAPACITY and drops the trip.
-__device__ __forceinline__ void carry_add(const CarryAcc &ca, unsigned long long key, long long tau,
+__device__ __forceinline__ void carry_add(const CarryAcc &ca, unsigned long long key, long long frac,
                                           long long amt, unsigned *status) {
   if (!ca.mask) {
     if (status) atomicOr(status, ST_CAPACITY);
@@ -1798,8 +1798,13 @@ __device__ __forceinline__ void carry_add(const CarryAcc &ca, unsigned long long
     unsigned long long cur = __ldcg(&ca.key[h]);
     if (cur == CARRY_KEY_EMPTY) cur = atomicCAS(&ca.key[h], CARRY_KEY_EMPTY, key);
     if (cur == CARRY_KEY_EMPTY || cur == key) {
+      // amount x fraction < 2^95 in two non-returning adds: the part above
+      // 2^32 (below the amount, so the sums stay below 2^63) and the low 32
+      // bits (below 2^64 for fewer than 2^32 entries per key)
+      const u128 v = (u128)(unsigned long long)amt * (u128)(unsigned long long)frac;
       atomicAdd(&ca.amt[h], (unsigned long long)amt);
-      add_u128(ca.tsum + 2 * h, (u128)(unsigned long long)amt * (u128)(unsigned long long)tau);
+      atomicAdd(&ca.tsum[2 * h], (unsigned long long)(v & 0xffffffffull));
+      atomicAdd(&ca.tsum[2 * h + 1], (unsigned long long)(v >> 32));
       return;
     }
     h = (h + 1) & ca.mask;
@@ -1834,14 +1839,14 @@ __global__ void residual_kernel(int V, int L, const int2 *__restrict__ head_q_fi
     const int z = roots[r];
     const int *par = parent + (long long)root_slot[r] * V;
     int u = src[k];
-    long long elapsed = 0, tau = 0;
+    long long elapsed = 0, frac = 0;
     int on_link = -1;  // the link holding the trip at the end of the interval
     const int cl = carry_link ? carry_link[k] : -1;
     if (cl >= 0) {
       const long long c0 = carry ? carry[k] : 0;
       if (!finish_carried_link(head_q_fin, cl, c0, dt_q, u, elapsed)) {
         on_link = cl;
-        tau = c0 + frac_of(dt_q, __ldg(&head_q_fin[cl]).y);
+        frac = c0 + frac_of(dt_q, __ldg(&head_q_fin[cl]).y);
       }
     }
     int steps = 0;
@@ -1853,14 +1858,14 @@ __global__ void residual_kernel(int V, int L, const int2 *__restrict__ head_q_fi
       const int2 hq = __ldg(&head_q_fin[e]);
       if (trunc && elapsed + hq.y > dt_q) {  // on this link at the end of the interval
         on_link = e;
-        tau = frac_of(dt_q - elapsed, hq.y);
+        frac = frac_of(dt_q - elapsed, hq.y);
         break;
       }
       elapsed += hq.y;
       u = hq.x;
       if (++steps > V) { atomicOr(status, ST_TIMEOUT); break; }
     }
-    if (on_link >= 0) carry_add(ca, (unsigned long long)r * (unsigned long long)L + on_link, tau, amt, status);
+    if (on_link >= 0) carry_add(ca, (unsigned long long)r * (unsigned long long)L + on_link, frac, amt, status);
     else if (u != z) atomicAdd(&dense[(long long)r * V + u], (unsigned long long)amt);
   }
 }
@@ -2526,10 +2531,10 @@ void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream
 
 // one demand item into the merge: waiting at src -> the dense (root, node)
 // accumulator; on a link -> the carried table
-__device__ __forceinline__ void scatter_one(int V, int L, int r, int src, long long a, long long tau, int link,
+__device__ __forceinline__ void scatter_one(int V, int L, int r, int src, long long a, long long frac, int link,
                                             unsigned long long *dense, const CarryAcc &ca, unsigned *status) {
   if (!a) return;
-  if (link >= 0) carry_add(ca, (unsigned long long)r * (unsigned long long)L + link, tau, a, status);
+  if (link >= 0) carry_add(ca, (unsigned long long)r * (unsigned long long)L + link, frac, a, status);
   else atomicAdd(&dense[(long long)r * V + src], (unsigned long long)a);
 }
 
@@ -2656,11 +2661,11 @@ __global__ void compact_write_kernel(long long total, int V, unsigned long long 
     for (int w = 0; w < nw; ++w) { if (w < wid) before += s_warp[w]; all += s_warp[w]; }
     if (nz) {
       const long long pos = out + before + __popc(m & ((1u << lane) - 1u));
-      long long tau = 0;
+      long long frac = 0;
       int r, node, link = -1;
       if (keys) {
-        const u128 t = ((u128)tsum[2 * idx + 1] << 64) | (u128)tsum[2 * idx];
-        tau = (long long)(t / (u128)v);
+        const u128 t = ((u128)tsum[2 * idx + 1] << 32) + (u128)tsum[2 * idx];
+        frac = (long long)(t / (u128)v);
         tsum[2 * idx] = 0ull;
         tsum[2 * idx + 1] = 0ull;
         r = (int)(key / (unsigned long long)L);
@@ -2674,7 +2679,7 @@ __global__ void compact_write_kernel(long long total, int V, unsigned long long 
         root_idx[pos] = r;
         src[pos] = node;
         amount[pos] = (long long)v;
-        if (carry_out) carry_out[pos] = tau;
+        if (carry_out) carry_out[pos] = frac;
         if (link_out) link_out[pos] = link;
       }
       dense[idx] = 0ull;
