@@ -909,7 +909,8 @@ def main():
     cfg["intervals_with_demand"] = len(gaps)
     cfg["per_interval"] = {"aon": [s["aon_calls"] for s in stats], "fw": [s["iterations"] for s in stats],
                            "sweeps": [s["ls_passes"] for s in stats],
-                           "dual_gap": [round(s["dual_gap"], 7) for s in stats]}
+                           "dual_gap": [round(s["dual_gap"], 7) for s in stats],
+                           "items": [s["n_items"] for s in stats]}
     cfg["generation_s"] = t_gen
 
     cpu = None
