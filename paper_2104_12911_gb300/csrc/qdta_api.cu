@@ -1889,6 +1889,7 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
     table_n = 1024;
     while (table_n < want) table_n <<= 1;
     D.ca.mask = (unsigned long long)(table_n - 1);
+    D.ca.seg = (unsigned long long)std::max(1ll, table_n / Z);
     RC(ws_get(g, "day.carry_key", (size_t)table_n, &D.ca.key));
     RC(ws_get(g, "day.carry_amt", (size_t)table_n, &D.ca.amt));
     RC(ws_get(g, "day.carry_tsum", (size_t)table_n * 2, &D.ca.tsum));

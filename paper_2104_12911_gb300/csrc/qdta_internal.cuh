@@ -391,6 +391,7 @@ struct CarryAcc {
   unsigned long long *amt = nullptr;   // [mask + 1]
   unsigned long long *tsum = nullptr;  // [2 * (mask + 1)]
   unsigned long long mask = 0;
+  unsigned long long seg = 1;           // slots per root segment, (mask + 1) / roots
 };
 
 void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStream_t s);

@@ -1773,8 +1773,8 @@ __device__ __forceinline__ void add_u128(unsigned long long *p, u128 v) {
 
 constexpr unsigned long long CARRY_KEY_EMPTY = ~0ull;
 
-// slot of a (root, link) key: the splitmix64 finaliser (Steele, Lea and
-// Flood, 2014) spreads the consecutive link ids of one root over the table
+// the splitmix64 finaliser (Steele, Lea and Flood, 2014): spreads the
+// consecutive link ids of one root over that root's segment of the table
 __device__ __forceinline__ unsigned long long carry_hash(unsigned long long x) {
   x ^= x >> 30;
   x *= 0xbf58476d1ce4e5b9ull;
@@ -1784,16 +1784,21 @@ __device__ __forceinline__ unsigned long long carry_hash(unsigned long long x) {
 }
 
 // one residual trip on a link: its amount and amount x covered fraction join
-// the entry of key root * L + link (linear probing; a key, once claimed,
-// stays until the compaction clears the table).  A full table sets
-// ST_CAPACITY and drops the trip.
-__device__ __forceinline__ void carry_add(const CarryAcc &ca, unsigned long long key, long long frac,
+// the entry of key root * L + link.  Root r's keys start probing in its own
+// segment [r seg, (r + 1) seg) of the table, so the compaction's slot order
+// is nearly root-major, as the dense part's is (later walks of a root's items
+// then share its tree in L2); linear probing, a key once claimed stays until
+// the compaction clears the table.  A full table sets ST_CAPACITY and drops
+// the trip.
+__device__ __forceinline__ void carry_add(const CarryAcc &ca, int r, int L, int link, long long frac,
                                           long long amt, unsigned *status) {
   if (!ca.mask) {
     if (status) atomicOr(status, ST_CAPACITY);
     return;
   }
-  unsigned long long h = carry_hash(key) & ca.mask;
+  const unsigned long long key = (unsigned long long)r * (unsigned long long)L + (unsigned long long)link;
+  unsigned long long h = ((unsigned long long)r * ca.seg + (((carry_hash((unsigned long long)link) >> 32) * ca.seg) >> 32)) &
+                         ca.mask;
   for (unsigned long long probe = 0; probe <= ca.mask; ++probe) {
     unsigned long long cur = __ldcg(&ca.key[h]);
     if (cur == CARRY_KEY_EMPTY) cur = atomicCAS(&ca.key[h], CARRY_KEY_EMPTY, key);
@@ -1865,7 +1870,7 @@ __global__ void residual_kernel(int V, int L, const int2 *__restrict__ head_q_fi
       u = hq.x;
       if (++steps > V) { atomicOr(status, ST_TIMEOUT); break; }
     }
-    if (on_link >= 0) carry_add(ca, (unsigned long long)r * (unsigned long long)L + on_link, frac, amt, status);
+    if (on_link >= 0) carry_add(ca, r, L, on_link, frac, amt, status);
     else if (u != z) atomicAdd(&dense[(long long)r * V + u], (unsigned long long)amt);
   }
 }
@@ -2534,7 +2539,7 @@ void launch_day_next(Ctl *ctl, unsigned long long cond, int use_cond, cudaStream
 __device__ __forceinline__ void scatter_one(int V, int L, int r, int src, long long a, long long frac, int link,
                                             unsigned long long *dense, const CarryAcc &ca, unsigned *status) {
   if (!a) return;
-  if (link >= 0) carry_add(ca, (unsigned long long)r * (unsigned long long)L + link, frac, a, status);
+  if (link >= 0) carry_add(ca, r, L, link, frac, a, status);
   else atomicAdd(&dense[(long long)r * V + src], (unsigned long long)a);
 }
 

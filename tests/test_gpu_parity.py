@@ -287,6 +287,24 @@ def test_sssp_dynamic_root_fetch_covers_every_root(mid, shape, schedule, monkeyp
             np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
+def test_sssp_batch_beyond_the_sort_limit_keeps_batch_order(mid, monkeypatch):
+    """More than 4,096 roots: the longest-first sort leaves the batch in its
+    own order (the fetch still hands the roots out); two batches, every row
+    bit-exact against the oracle."""
+    net, dem, _, og = mid
+    monkeypatch.setenv("QDTA_BF_DYNAMIC", "1")
+    monkeypatch.setenv("QDTA_BF_LPT", "1")
+    g = Q.Graph(net)
+    rng = np.random.default_rng(17)
+    q = (net.fftime_q * rng.uniform(1.0, 2.0, net.n_links)).astype(np.int32)
+    roots = rng.choice(net.n_nodes, 4100, replace=False).astype(np.int32)
+    p_o, d_o = oracle.sssp(og, q, roots, Q.QDTA_TO_ROOT)
+    for _ in range(2):
+        p_g, d_g = Q.qdta_sssp_batch(g, T(q, np.int32), T(roots, np.int32), Q.QDTA_TO_ROOT, True)
+        np.testing.assert_array_equal(d_g.cpu().numpy(), d_o)
+        np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
+
+
 def test_sssp_large_irregular_graph_with_ties():
     """Above the shared-memory limit with degrees above 4 (so the compressed
     adjacency, not the four-slot one) and many equal-cost ties: bit-exact
