@@ -842,14 +842,18 @@ int sssp_group_size() {
 //   8: as 1 with the L2 prefetch of key blocks (32-bit rank keys only)
 //   9: 192 threads, one bitmap, 960 entries, five CTAs per SM (32-bit rank
 //      keys only: up to 68 registers a thread)
+//  10: as 1 with quad-major passes: a lane group's NPT nodes are consecutive
+//      queue entries, so a pass with few nodes occupies only the first warps
+//      and the others skip it (32-bit rank keys only)
 struct SmqShape {
   int threads, bitmaps, qcap, ctas, npt;
 };
-constexpr int kSmqShapes = 10;
+constexpr int kSmqShapes = 11;
 static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 2048, 4, 4}, {512, 1, 3072, 2, 4},
                                                {256, 1, 768, 5, 4},  {256, 1, 2048, 4, 5}, {256, 1, 2048, 4, 6},
                                                {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2},
-                                               {256, 1, 2048, 4, 4}, {192, 1, 960, 5, 4}};
+                                               {256, 1, 2048, 4, 4}, {192, 1, 960, 5, 4},
+                                               {256, 1, 2048, 4, 4}};
 
 // Next destination root position of this CTA: every gridDim-th one, or,
 // with a fetch counter, the next one handed out by that counter (dynamic
@@ -883,7 +887,7 @@ __device__ __forceinline__ int next_root(int r, int *fetch, int *s_next) {
 // first touch and its reset).  A small shared bitmap marks the blocks
 // prefetched for the current root.
 template <int THREADS, int ADJ, int RELAX, bool ONEBM, int MINB = 65536 / (THREADS * 64), int NPT = SSSP2_NPT,
-          bool PF = false>
+          bool PF = false, bool QMAJ = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__restrict__ adj,
                 const int *__restrict__ roots, int R_host, const int *R_dev,
@@ -956,12 +960,16 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
         __syncthreads();
       }
       for (int base = 0; base < ncur; base += NQ * NPT) {
+        // quad-major: a warp's eight lane groups take 8 NPT consecutive
+        // entries; a warp past the end of the queue skips the pass (no
+        // barrier inside a pass, so a warp-uniform skip is safe)
+        if (QMAJ && base + (threadIdx.x >> 5) * 8 * NPT >= ncur) continue;
         int w[NPT], kb[NPT], ke[NPT];
         Dist dw[NPT];
         unsigned skipj = 0;
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
-          const int i = base + j * NQ + quad;
+          const int i = QMAJ ? base + quad * NPT + j : base + j * NQ + quad;
           w[j] = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
         }
 #pragma unroll
@@ -1383,6 +1391,7 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
           for (int r = 0; r < 4; ++r)
             v.push_back(sh == 8 && e == 3   ? std::string("sssp_smq_kernel<256,rank32,2,true,pf>")
                         : sh == 9 && e == 3 ? std::string("sssp_smq_kernel<192,rank32,2,true,5>")
+                        : sh == 10 && e == 3 ? std::string("sssp_smq_kernel<256,rank32,2,true,qmaj>")
                         : sh >= 6 && sh <= 7 && e == 3
                             ? "sssp_lane_kernel<" + std::to_string(kSmqShape[sh].threads) + ",npn" +
                                   std::to_string(kSmqShape[sh].npt) + ">"
@@ -1497,6 +1506,7 @@ static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
   if (shape == 7 && adj == 3) return sssp_lane_kernel<256, 2>;
   if (shape == 8 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 4, true>;
   if (shape == 9 && adj == 3) return sssp_smq_kernel<192, 3, 2, true, 5>;
+  if (shape == 10 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 4, false, true>;
   if (shape == 3 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 5>;
   if (shape == 4 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 5>;
   if (shape == 5 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 6>;
@@ -1773,23 +1783,14 @@ __device__ __forceinline__ void add_u128(unsigned long long *p, u128 v) {
 
 constexpr unsigned long long CARRY_KEY_EMPTY = ~0ull;
 
-// the splitmix64 finaliser (Steele, Lea and Flood, 2014): spreads the
-// consecutive link ids of one root over that root's segment of the table
-__device__ __forceinline__ unsigned long long carry_hash(unsigned long long x) {
-  x ^= x >> 30;
-  x *= 0xbf58476d1ce4e5b9ull;
-  x ^= x >> 27;
-  x *= 0x94d049bb133111ebull;
-  return x ^ (x >> 31);
-}
-
 // one residual trip on a link: its amount and amount x covered fraction join
 // the entry of key root * L + link.  Root r's keys start probing in its own
-// segment [r seg, (r + 1) seg) of the table, so the compaction's slot order
-// is nearly root-major, as the dense part's is (later walks of a root's items
-// then share its tree in L2); linear probing, a key once claimed stays until
-// the compaction clears the table.  A full table sets ST_CAPACITY and drops
-// the trip.
+// segment [r seg, (r + 1) seg) of the table, at the link's id scaled to the
+// segment, so the compaction's slot order is nearly root-major and link-
+// ordered, as the dense part's is root-major and node-ordered (neighbouring
+// threads of the later walks then start near each other on the same tree);
+// linear probing, a key once claimed stays until the compaction clears the
+// table.  A full table sets ST_CAPACITY and drops the trip.
 __device__ __forceinline__ void carry_add(const CarryAcc &ca, int r, int L, int link, long long frac,
                                           long long amt, unsigned *status) {
   if (!ca.mask) {
@@ -1797,8 +1798,8 @@ __device__ __forceinline__ void carry_add(const CarryAcc &ca, int r, int L, int 
     return;
   }
   const unsigned long long key = (unsigned long long)r * (unsigned long long)L + (unsigned long long)link;
-  unsigned long long h = ((unsigned long long)r * ca.seg + (((carry_hash((unsigned long long)link) >> 32) * ca.seg) >> 32)) &
-                         ca.mask;
+  unsigned long long h =
+      ((unsigned long long)r * ca.seg + (unsigned long long)link * ca.seg / (unsigned long long)L) & ca.mask;
   for (unsigned long long probe = 0; probe <= ca.mask; ++probe) {
     unsigned long long cur = __ldcg(&ca.key[h]);
     if (cur == CARRY_KEY_EMPTY) cur = atomicCAS(&ca.key[h], CARRY_KEY_EMPTY, key);
