@@ -842,18 +842,14 @@ int sssp_group_size() {
 //   8: as 1 with the L2 prefetch of key blocks (32-bit rank keys only)
 //   9: 192 threads, one bitmap, 960 entries, five CTAs per SM (32-bit rank
 //      keys only: up to 68 registers a thread)
-//  10: as 1 with quad-major passes: a lane group's NPT nodes are consecutive
-//      queue entries, so a pass with few nodes occupies only the first warps
-//      and the others skip it (32-bit rank keys only)
 struct SmqShape {
   int threads, bitmaps, qcap, ctas, npt;
 };
-constexpr int kSmqShapes = 11;
+constexpr int kSmqShapes = 10;
 static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 2048, 4, 4}, {512, 1, 3072, 2, 4},
                                                {256, 1, 768, 5, 4},  {256, 1, 2048, 4, 5}, {256, 1, 2048, 4, 6},
                                                {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2},
-                                               {256, 1, 2048, 4, 4}, {192, 1, 960, 5, 4},
-                                               {256, 1, 2048, 4, 4}};
+                                               {256, 1, 2048, 4, 4}, {192, 1, 960, 5, 4}};
 
 // Next destination root position of this CTA: every gridDim-th one, or,
 // with a fetch counter, the next one handed out by that counter (dynamic
@@ -887,7 +883,7 @@ __device__ __forceinline__ int next_root(int r, int *fetch, int *s_next) {
 // first touch and its reset).  A small shared bitmap marks the blocks
 // prefetched for the current root.
 template <int THREADS, int ADJ, int RELAX, bool ONEBM, int MINB = 65536 / (THREADS * 64), int NPT = SSSP2_NPT,
-          bool PF = false, bool QMAJ = false>
+          bool PF = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__restrict__ adj,
                 const int *__restrict__ roots, int R_host, const int *R_dev,
@@ -960,16 +956,12 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
         __syncthreads();
       }
       for (int base = 0; base < ncur; base += NQ * NPT) {
-        // quad-major: a warp's eight lane groups take 8 NPT consecutive
-        // entries; a warp past the end of the queue skips the pass (no
-        // barrier inside a pass, so a warp-uniform skip is safe)
-        if (QMAJ && base + (threadIdx.x >> 5) * 8 * NPT >= ncur) continue;
         int w[NPT], kb[NPT], ke[NPT];
         Dist dw[NPT];
         unsigned skipj = 0;
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
-          const int i = QMAJ ? base + quad * NPT + j : base + j * NQ + quad;
+          const int i = base + j * NQ + quad;
           w[j] = i < ncur ? (i < qcap ? scur[i] : __ldcg(&gcur[i - qcap])) : -1;
         }
 #pragma unroll
@@ -1391,7 +1383,6 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
           for (int r = 0; r < 4; ++r)
             v.push_back(sh == 8 && e == 3   ? std::string("sssp_smq_kernel<256,rank32,2,true,pf>")
                         : sh == 9 && e == 3 ? std::string("sssp_smq_kernel<192,rank32,2,true,5>")
-                        : sh == 10 && e == 3 ? std::string("sssp_smq_kernel<256,rank32,2,true,qmaj>")
                         : sh >= 6 && sh <= 7 && e == 3
                             ? "sssp_lane_kernel<" + std::to_string(kSmqShape[sh].threads) + ",npn" +
                                   std::to_string(kSmqShape[sh].npt) + ">"
@@ -1506,7 +1497,6 @@ static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
   if (shape == 7 && adj == 3) return sssp_lane_kernel<256, 2>;
   if (shape == 8 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 4, true>;
   if (shape == 9 && adj == 3) return sssp_smq_kernel<192, 3, 2, true, 5>;
-  if (shape == 10 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 4, false, true>;
   if (shape == 3 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 5>;
   if (shape == 4 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 5>;
   if (shape == 5 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 6>;
