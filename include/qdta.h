@@ -373,7 +373,7 @@ int qdta_sssp_batch_noalloc(qdta_graph *g, const int32_t *cost_q, const int32_t 
  * appends new ones.  The key is a hash of the GPU model (name, SM count), the
  * network (nodes, links, tails, heads, free-flow times) and the direction; a
  * hit applies the stored choice without timing and sets `cached`. */
-#define QDTA_TUNE_MAX 16
+#define QDTA_TUNE_MAX 24
 typedef struct qdta_tune_entry {
   char kernel[40];     /* kernel name, as qdta_sssp_kernel_name reports it */
   int32_t ctas_per_sm; /* resident CTAs (one root each) per SM */

@@ -842,14 +842,24 @@ int sssp_group_size() {
 //   8: as 1 with the L2 prefetch of key blocks (32-bit rank keys only)
 //   9: 192 threads, one bitmap, 960 entries, five CTAs per SM (32-bit rank
 //      keys only: up to 68 registers a thread)
+//  10: as 1 with 288 threads (a pass covers 288 frontier nodes; 32-bit rank
+//      keys only, 56 registers a thread so that four CTAs fit; other
+//      adjacency layouts run shape 1)
 struct SmqShape {
   int threads, bitmaps, qcap, ctas, npt;
 };
-constexpr int kSmqShapes = 10;
+constexpr int kSmqShapes = 11;
 static const SmqShape kSmqShape[kSmqShapes] = {{512, 2, 3072, 2, 4}, {256, 1, 2048, 4, 4}, {512, 1, 3072, 2, 4},
                                                {256, 1, 768, 5, 4},  {256, 1, 2048, 4, 5}, {256, 1, 2048, 4, 6},
                                                {256, 1, 2048, 4, 1}, {256, 1, 2048, 4, 2},
-                                               {256, 1, 2048, 4, 4}, {192, 1, 960, 5, 4}};
+                                               {256, 1, 2048, 4, 4}, {192, 1, 960, 5, 4},
+                                               {288, 1, 2048, 4, 4}};
+
+// threads of the kernel a shape runs with adjacency layout `adj` (shape 10
+// falls back to shape 1 off the 32-bit rank keys)
+static int smq_threads(int shape, int adj) {
+  return shape == 10 && adj != 3 ? 256 : kSmqShape[shape].threads;
+}
 
 // Next destination root position of this CTA: every gridDim-th one, or,
 // with a fetch counter, the next one handed out by that counter (dynamic
@@ -1386,7 +1396,7 @@ const char *sssp_kernel_name(const GraphDev &g, int direction, bool use_smem) {
                         : sh >= 6 && sh <= 7 && e == 3
                             ? "sssp_lane_kernel<" + std::to_string(kSmqShape[sh].threads) + ",npn" +
                                   std::to_string(kSmqShape[sh].npt) + ">"
-                            : "sssp_smq_kernel<" + std::to_string(kSmqShape[sh].threads) + "," + adj_name[e] + "," +
+                            : "sssp_smq_kernel<" + std::to_string(smq_threads(sh, e)) + "," + adj_name[e] + "," +
                                   std::to_string(r) + "," + (kSmqShape[sh].bitmaps == 1 ? "true" : "false") +
                                   (sh == 3 && e == 3 ? ",5" : "") +
                                   (sh >= 4 && sh <= 5 && e == 3 ? ",npt" + std::to_string(kSmqShape[sh].npt) : "") +
@@ -1497,6 +1507,7 @@ static SmqKernel smq_kernel_for(int shape, int adj, int relax) {
   if (shape == 7 && adj == 3) return sssp_lane_kernel<256, 2>;
   if (shape == 8 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 4, true>;
   if (shape == 9 && adj == 3) return sssp_smq_kernel<192, 3, 2, true, 5>;
+  if (shape == 10 && adj == 3) return sssp_smq_kernel<288, 3, 2, true, 4>;
   if (shape == 3 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 5>;
   if (shape == 4 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 5>;
   if (shape == 5 && adj == 3) return sssp_smq_kernel<256, 3, 2, true, 4, 6>;
@@ -1514,7 +1525,7 @@ int sssp_smq_ctas_per_sm(const GraphDev &g, int direction) {
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kSmqShape[g.tune_shape].threads, smq);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, smq_threads(g.tune_shape, sssp_adj(g, direction)), smq);
   n = std::min(n, kSmqShape[g.tune_shape].ctas);
   return n > 0 ? n : 1;
 }
@@ -1558,7 +1569,6 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
       // 85 % of 228 KB asks for 194 KB and gets the 196 KB step (86 % would
       // round up to 228 KB).  QDTA_SMQ_CARVEOUT overrides, in percent.
       const size_t smq = sssp_smq_smem_bytes(g.V, g.tune_shape);
-      const int threads = kSmqShape[g.tune_shape].threads;
       const bool perm = g.node_int != nullptr;
       // dynamic fetch: roots after the first wave come from an atomic
       // counter (w.fb_skip[1] for the kernel, [2] for the redo), zeroed
@@ -1572,7 +1582,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
           sched.order = w.order;
         }
       }
-      auto run = [&](SmqKernel kern, const int *skip, unsigned long long *counters, RootSched rs) {
+      auto run = [&](SmqKernel kern, int threads, const int *skip, unsigned long long *counters, RootSched rs) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
         COUNT_LAUNCH();
@@ -1582,7 +1592,8 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                                         kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
                                         g.rank_link[direction], g.skip_parent, rs);
       };
-      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), skip_dev, roots_counter, sched);
+      run(smq_kernel_for(g.tune_shape, adjl, g.tune_relax), smq_threads(g.tune_shape, adjl), skip_dev, roots_counter,
+          sched);
       if (adjl == 3) {
         // a distance beyond the 32-bit keys' range: redo the batch with 64-bit
         // keys on the same packed adjacency (decided on the device, so graph
@@ -1593,7 +1604,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
                                              roots_counter ? roots_counter + 4 : nullptr);
         RootSched redo = sched;
         if (redo.fetch) redo.fetch += 1;
-        run(smq_kernel_for(g.tune_shape, 2, 2), w.fb_skip, nullptr, redo);
+        run(smq_kernel_for(g.tune_shape, 2, 2), smq_threads(g.tune_shape, 2), w.fb_skip, nullptr, redo);
       }
       return;
     }

@@ -81,7 +81,7 @@ class Profile(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-TUNE_MAX = 16
+TUNE_MAX = 24
 
 
 class TuneEntry(C.Structure):

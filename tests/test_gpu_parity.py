@@ -143,6 +143,8 @@ LARGE_VARIANTS = {
     "rank32_prefetch": ({"QDTA_BF_SHAPE": "8"}, "sssp_smq_kernel<256,rank32,2,true,pf>"),
     "rank32_192x5": ({"QDTA_BF_SHAPE": "9"}, "sssp_smq_kernel<192,rank32,2,true,5>"),
     "shape_192x5_ell16": ({"QDTA_BF_SHAPE": "9", "QDTA_SSSP_ADJ": "1"}, "sssp_smq_kernel<192,ell,2,true>"),
+    "rank32_288x4": ({"QDTA_BF_SHAPE": "10"}, "sssp_smq_kernel<288,rank32,2,true>"),
+    "shape_288x4_rank64": ({"QDTA_BF_SHAPE": "10", "QDTA_SSSP_ADJ": "2"}, "sssp_smq_kernel<256,rank,2,true>"),
     "shape_192x5_csr_returning": ({"QDTA_BF_SHAPE": "9", "QDTA_NO_ELL": "1", "QDTA_BF_RELAX": "1"},
                                   "sssp_smq_kernel<192,csr,1,true>"),
     "global_queues": ({"QDTA_BF_NOSMQ": "1", "QDTA_NO_REORDER": "1"}, "sssp_ilp_kernel<512>"),
@@ -214,7 +216,7 @@ def test_sssp_long_distances_redo_with_64_bit_keys(mid, adj, shape, monkeypatch)
         np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-@pytest.mark.parametrize("shape", ["1", "6", "7", "8", "9"])
+@pytest.mark.parametrize("shape", ["1", "6", "7", "8", "9", "10"])
 def test_sssp_redo_touches_only_the_roots_that_overflowed(mid, shape, monkeypatch):
     """Links entering three nodes cost 2^30: destination trees rooted there
     pass 2^29 (so the batch is redone with 64-bit keys), the other roots'
@@ -237,7 +239,7 @@ def test_sssp_redo_touches_only_the_roots_that_overflowed(mid, shape, monkeypatc
     np.testing.assert_array_equal(p_g.cpu().numpy(), p_o)
 
 
-@pytest.mark.parametrize("shape", ["1", "6", "8", "9"])
+@pytest.mark.parametrize("shape", ["1", "6", "8", "9", "10"])
 def test_sssp_32_bit_keys_redo_only_on_distances_beyond_2_29(mid, shape, monkeypatch):
     """An isolated node (no path to or from anything) stays unreached and
     must not trigger the 64-bit redo; a node whose distance passes 2^29 must.
@@ -263,7 +265,7 @@ def test_sssp_32_bit_keys_redo_only_on_distances_beyond_2_29(mid, shape, monkeyp
         assert (d_o[:, V] == np.iinfo(np.int64).max).all()
 
 
-@pytest.mark.parametrize("shape", ["1", "6"])
+@pytest.mark.parametrize("shape", ["1", "6", "10"])
 @pytest.mark.parametrize("schedule", ["round_robin", "fetch", "fetch_longest_first"])
 def test_sssp_dynamic_root_fetch_covers_every_root(mid, shape, schedule, monkeypatch):
     """More roots than resident CTAs: handed out round-robin, by an atomic
@@ -347,15 +349,16 @@ def test_autotune_keeps_the_fastest_shape_and_stays_bit_exact(mid):
     kernels = {c["kernel"] for c in rep["candidates"]}
     # launch shapes {512 x 2 CTAs, 256 x 4 CTAs} x adjacency {32-bit rank keys, rank keys, four-slot,
     # compressed} in relaxation mode 2; the 32-bit kernel also with five CTAs per SM (256 and 192
-    # threads), with 5 or 6 frontier nodes per lane group, lane per node (1 or 2 nodes per lane) and
-    # with the L2 prefetch of key blocks; the cell kernel
+    # threads), with 5 or 6 frontier nodes per lane group, lane per node (1 or 2 nodes per lane),
+    # with the L2 prefetch of key blocks and with 288 threads; the cell kernel
     want = {f"sssp_smq_kernel<{t},{e},2,{b}>" for t, b in (("512", "false"), ("256", "true"))
             for e in ("rank32", "rank", "ell", "csr")} | {"sssp_cell_kernel"}
     want |= {"sssp_smq_kernel<256,rank32,2,true,5>", "sssp_smq_kernel<256,rank32,2,true,npt5>",
              "sssp_smq_kernel<256,rank32,2,true,npt6>", "sssp_lane_kernel<256,npn1>", "sssp_lane_kernel<256,npn2>",
-             "sssp_smq_kernel<256,rank32,2,true,pf>", "sssp_smq_kernel<192,rank32,2,true,5>"}
+             "sssp_smq_kernel<256,rank32,2,true,pf>", "sssp_smq_kernel<192,rank32,2,true,5>",
+             "sssp_smq_kernel<288,rank32,2,true>"}
     assert kernels == want
-    assert len(rep["candidates"]) == 16
+    assert len(rep["candidates"]) == 17
     ctas = {c["kernel"]: c["ctas_per_sm"] for c in rep["candidates"]}
     assert ctas["sssp_smq_kernel<256,rank32,2,true>"] == 4 and ctas["sssp_smq_kernel<256,rank32,2,true,5>"] == 5
     fastest = min(c["ms"] for c in rep["candidates"])
