@@ -1198,7 +1198,7 @@ struct Solver {
   const long long *n_dev;
   const int *root_idx, *src;
   const long long *amount;
-  // per item (nullable): the link carrying the trip (-1: none) and the time travelled along it
+  // per item (nullable): the fraction of its link covered (2^-32 units) and the link carrying the trip (-1: none)
   const long long *carry = nullptr;
   const int *carry_link = nullptr;
   // link state

@@ -396,7 +396,8 @@ struct CarryAcc {
 
 void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStream_t s);
 // carry, carry_link [n] (nullable): an item with carry_link >= 0 is on that
-// link having travelled carry quanta; it finishes the link, then follows its tree
+// link having covered the fraction carry / 2^32 of it; it finishes the link,
+// then follows its tree
 void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const int *parent_slot_dev,
                  long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
                  const long long *n_items_dev, const int *root_idx, const int *src,
@@ -420,7 +421,7 @@ void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost
                 unsigned *status, cudaStream_t s, int marginal = 0);
 void launch_link_const(const GraphDev &g, double dt_h, LinkConst *kc, cudaStream_t s);
 // ST_BADARG unless every item with carry_link >= 0 names a link whose tail
-// is its src and carries a time >= 0 (carry nullable)
+// is its src and carries a fraction in [0, 2^32) (carry nullable)
 void launch_check_carry(const GraphDev &g, long long n, const int *src, const long long *carry,
                         const int *carry_link, unsigned *status, cudaStream_t s);
 // replace the graph's capacities by `cap` (device) when every value is finite

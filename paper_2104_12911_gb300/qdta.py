@@ -218,7 +218,7 @@ class DeviceOD:
     src: torch.Tensor
     amount_fx: torch.Tensor
     # trips carried on a link (both None, or int64 / int32 per item): the
-    # time travelled along carry_link (-1: the trip waits at src)
+    # fraction of carry_link covered, in 2^-32 units (-1: the trip waits at src)
     carry_frac: torch.Tensor = None
     carry_link: torch.Tensor = None
 

@@ -936,7 +936,7 @@ def test_autograd_reuses_one_graph_handle():
 # ---------------------------------------------------------------------------
 # Carried partial-link truncation (Section 3.4's alternative to Eq. 2)
 def _sorted_resid(r):
-    """residual arrays (root index, src, amount, carried time, link) as a
+    """residual arrays (root index, src, amount, covered fraction, link) as a
     sorted list of tuples: the GPU writes carried entries in table order"""
     root, src, amt, carry, link = (np.asarray(a).astype(np.int64) for a in r)
     return sorted(zip(root.tolist(), link.tolist(), src.tolist(), amt.tolist(), carry.tolist()))
@@ -967,7 +967,7 @@ def test_run_day_carried_truncation_bit_exact(schedule, step, stop, it):
         for key in ("iterations", "aon_calls", "ls_passes", "converged"):
             assert st_g[i][key] == st_o[i][key], (i, key)
     assert resid[0].shape[0] == rn_o and int((resid[4] >= 0).sum()) > 0
-    # the residual itself: (root, link, src) keys, amounts, mean carried times
+    # the residual itself: (root, link, src) keys, amounts, mean covered fractions
     assert _sorted_resid([r.cpu().numpy() for r in resid]) == _sorted_resid(
         [res_o[0], res_o[1], res_o[2], res_o[3], res_o[4]])
     # the node rule differs on the same inputs (the carried trips wait elsewhere)
@@ -996,7 +996,7 @@ def test_carried_truncation_crosses_a_long_link_on_the_gpu():
 
 @pytest.mark.parametrize("schedule", ["plain", "graph"])
 def test_carried_day_resumes_from_its_residual(schedule):
-    """Run intervals 0-1, take the residual (with its carried times) out,
+    """Run intervals 0-1, take the residual (with its carried links) out,
     resume intervals 2-4 from it: the same h(i) as the oracle's whole day."""
     day = _carry_day_case()
     days = list(day.demand)
