@@ -640,12 +640,6 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   if (const char *e = getenv("QDTA_BF_DYNAMIC")) g->d.tune_dyn = atoi(e) != 0;
   g->bf_lpt = 1;
   if (const char *e = getenv("QDTA_BF_LPT")) g->bf_lpt = atoi(e) != 0;
-  // loading: walks in flight per thread (QDTA_LOAD_WALKS: 1, 2 or 4)
-  g->d.load_walks = 1;
-  if (const char *e = getenv("QDTA_LOAD_WALKS")) {
-    const int w = atoi(e);
-    if (w == 2 || w == 4) g->d.load_walks = w;
-  }
   if (const char *e = getenv("QDTA_BF_SHAPE")) {
     const int sh = atoi(e);
     if (sssp_smq_shape_fits(V, sh)) g->d.tune_shape = sh;

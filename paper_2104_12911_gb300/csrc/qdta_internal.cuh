@@ -275,7 +275,6 @@ struct GraphDev {
   // rounds each root node took in its last queue-kernel batch ([V], zeroed
   // at create; nullable): the dynamic fetch hands out the longest first
   int *root_rounds;
-  int load_walks;  // walks in flight per thread of the loading kernel (1, 2 or 4)
 };
 
 // root scheduling of the queue kernels: fetch (nullable) hands out root

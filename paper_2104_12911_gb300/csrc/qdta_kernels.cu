@@ -1667,7 +1667,6 @@ __device__ __forceinline__ bool finish_carried_link(const int2 *__restrict__ hea
 // item carried on a link walks on from its head (the link was loaded when
 // the trip entered it); one still on it at the end of the interval stops at
 // src (the link's tail).
-template <int NW>
 __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *__restrict__ parent,
                             const int *parent_slot_dev, long long slot_stride,
                             const int *__restrict__ root_slot, const int *__restrict__ roots,
@@ -1676,76 +1675,35 @@ __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *_
                             long long dt_q, unsigned long long *flow_fx, int *stop_out,
                             unsigned *status, const long long *__restrict__ carry,
                             const int *__restrict__ carry_link) {
-  // NW walks per thread in lockstep: each step issues the NW walks' parent
-  // reads together, then their link reads, so NW chains of dependent loads
-  // are in flight per thread
   const long long n = n_dev ? *n_dev : n_host;
   if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
-  const long long T = (long long)gridDim.x * blockDim.x;
-  for (long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; k0 < n; k0 += NW * T) {
-    int u[NW], z[NW], steps[NW];
-    long long elapsed[NW];
-    const int *par[NW];
-    unsigned long long amt[NW];
-    bool act[NW];
-    bool any = false;
-#pragma unroll
-    for (int j = 0; j < NW; ++j) {
-      const long long k = k0 + j * T;
-      act[j] = false;
-      u[j] = -1;
-      z[j] = -1;
-      steps[j] = 0;
-      elapsed[j] = 0;
-      par[j] = parent;
-      amt[j] = 0;
-      if (k < n) {
-        const int r = root_idx[k];
-        z[j] = roots[r];
-        par[j] = parent + (long long)(root_slot ? root_slot[r] : r) * V;
-        amt[j] = (unsigned long long)amount[k];
-        u[j] = src[k];
-        const int cl = carry_link ? carry_link[k] : -1;
-        act[j] = cl < 0 || finish_carried_link(head_q, cl, carry ? carry[k] : 0, dt_q, u[j], elapsed[j]);
-        act[j] = act[j] && u[j] != z[j] && elapsed[j] < dt_q;
-        any |= act[j];
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int r = root_idx[k];
+    const int z = roots[r];
+    const int *par = parent + (long long)(root_slot ? root_slot[r] : r) * V;
+    const unsigned long long amt = (unsigned long long)amount[k];
+    int u = src[k];
+    long long elapsed = 0;
+    const int cl = carry_link ? carry_link[k] : -1;
+    if (cl >= 0) {
+      if (!finish_carried_link(head_q, cl, carry ? carry[k] : 0, dt_q, u, elapsed)) {
+        if (stop_out) stop_out[k] = u;
+        continue;
       }
     }
-    while (any) {
-      int e[NW];
-#pragma unroll
-      for (int j = 0; j < NW; ++j) e[j] = act[j] ? par[j][u[j]] : 0;
-#pragma unroll
-      for (int j = 0; j < NW; ++j) {
-        if (act[j] && e[j] < 0) {
-          atomicOr(status, ST_UNREACH);
-          act[j] = false;
-        }
-        if (act[j] && amt[j]) atomicAdd(&flow_fx[e[j]], amt[j]);
-      }
-      int2 hq[NW];
-#pragma unroll
-      for (int j = 0; j < NW; ++j) hq[j] = act[j] ? __ldg(&head_q[e[j]]) : make_int2(0, 0);
-      any = false;
-#pragma unroll
-      for (int j = 0; j < NW; ++j) {
-        if (!act[j]) continue;
-        elapsed[j] += hq[j].y;
-        u[j] = hq[j].x;
-        if (++steps[j] > V) {
-          atomicOr(status, ST_TIMEOUT);
-          act[j] = false;
-        } else {
-          act[j] = u[j] != z[j] && elapsed[j] < dt_q;
-        }
-        any |= act[j];
-      }
+    int steps = 0;
+    while (u != z) {
+      if (elapsed >= dt_q) break;
+      const int e = par[u];
+      if (e < 0) { atomicOr(status, ST_UNREACH); break; }
+      if (amt) atomicAdd(&flow_fx[e], amt);
+      const int2 hq = __ldg(&head_q[e]);
+      elapsed += hq.y;
+      u = hq.x;
+      if (++steps > V) { atomicOr(status, ST_TIMEOUT); break; }
     }
-    if (stop_out) {
-#pragma unroll
-      for (int j = 0; j < NW; ++j)
-        if (k0 + j * T < n) stop_out[k0 + j * T] = u[j];
-    }
+    if (stop_out) stop_out[k] = u;
   }
 }
 
@@ -1807,11 +1765,11 @@ void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const
                  unsigned *status, cudaStream_t s, const long long *carry, const int *carry_link) {
   long long n = n_items_dev ? (long long)g.num_sms * 16 * 256 : n_items_host;
   if (n <= 0) return;
-  auto kern = g.load_walks == 4 ? load_kernel<4> : g.load_walks == 2 ? load_kernel<2> : load_kernel<1>;
   COUNT_LAUNCH();
-  kern<<<link_grid(g, n), 256, 0, s>>>(g.V, head_q, parent, parent_slot_dev, slot_stride, root_slot, roots,
-                                       n_items_host, n_items_dev, root_idx, src, amount, dt_q, flow_fx,
-                                       stop_out, status, carry, carry_link);
+  load_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, head_q, parent, parent_slot_dev, slot_stride,
+                                              root_slot, roots, n_items_host, n_items_dev, root_idx,
+                                              src, amount, dt_q, flow_fx, stop_out, status, carry,
+                                              carry_link);
 }
 
 // unsigned 128-bit accumulation with two 64-bit atomics: the low word's carry

@@ -388,14 +388,9 @@ def test_empty_batches(small):
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("walks", ["1", "2", "4"])
 @pytest.mark.parametrize("dt_q", [0, 1, 20000, 90000, np.iinfo(np.int64).max])
-def test_load_bit_exact(small, dt_q, walks, monkeypatch):
-    """Loaded flows and stop nodes at five truncation times, with 1, 2 or 4
-    walks in flight per thread of the loading kernel."""
-    inst, _, og = small
-    monkeypatch.setenv("QDTA_LOAD_WALKS", walks)
-    g = Q.Graph(inst.net)
+def test_load_bit_exact(small, dt_q):
+    inst, g, og = small
     dem = synth.random_demand(inst.net, 64, 3000, 7, fractional=True)
     rng = np.random.default_rng(3)
     q = (inst.net.fftime_q * rng.uniform(1, 4, og.n_links)).astype(np.int32)
@@ -1035,11 +1030,8 @@ def _carried_items(net, dem, seed):
     return carry, link
 
 
-@pytest.mark.parametrize("walks", ["1", "4"])
-def test_load_aon_with_carried_trips_matches_the_oracle(small, walks, monkeypatch):
-    inst, _, og = small
-    monkeypatch.setenv("QDTA_LOAD_WALKS", walks)
-    g = Q.Graph(inst.net)
+def test_load_aon_with_carried_trips_matches_the_oracle(small):
+    inst, g, og = small
     dem = inst.demand[0]
     rng = np.random.default_rng(4)
     carry, link = _carried_items(inst.net, dem, 4)
