@@ -341,7 +341,7 @@ def reference_arm(args, inst, cfg):
     tasks = []
     for i in picks:
         dem = inst.demand[i]
-        tasks += OraclePool.tasks(dem, np.unique(dem.root_idx)[:pool.n])
+        tasks += OraclePool.tasks(dem, np.unique(dem.root_idx)[:4 * pool.n])  # four roots per core
     work = METRO_DAY_WORK if args.workload == "day_metro" else None
     if work is not None and len(work["aon"]) == len(n_roots):
         scaling = "the day's recorded AON / FW-step / sweep counts per interval"
