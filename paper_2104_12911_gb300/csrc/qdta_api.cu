@@ -584,8 +584,8 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
   gd.alpha = d->alpha;
   gd.quantum_s = d->quantum_s;
   int rc = QDTA_OK;
-  int *tail, *head, *c0, *oo, *io, *ol, *il;
-  double *cap;
+  int *tail = nullptr, *head = nullptr, *c0 = nullptr, *oo = nullptr, *io = nullptr, *ol = nullptr, *il = nullptr;
+  double *cap = nullptr;
   if ((rc = upload(g, d->tail, L, &tail)) || (rc = upload(g, d->head, L, &head)) ||
       (rc = upload(g, d->fftime_q, L, &c0)) || (rc = upload(g, d->capacity_vph, L, &cap)) ||
       (rc = upload(g, out_off.data(), V + 1, &oo)) || (rc = upload(g, in_off.data(), V + 1, &io)) ||
@@ -673,8 +673,8 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
       }
       C.ent_off[dir] = a1; C.ent_link[dir] = a2; C.ent_code[dir] = a3; C.ext_off[dir] = a4;
       C.ext_node[dir] = a5; C.dep_off[dir] = a6; C.dep_cell[dir] = a7;
-      int *b1, *b2, *b3;
-      unsigned char *b4;
+      int *b1 = nullptr, *b2 = nullptr, *b3 = nullptr;
+      unsigned char *b4 = nullptr;
       if ((rc = upload(g, H.lrev_off[dir].data(), H.lrev_off[dir].size(), &b1)) ||
           (rc = upload(g, H.lrev_link[dir].data(), H.lrev_link[dir].size(), &b2)) ||
           (rc = upload(g, H.lrev_src[dir].data(), H.lrev_src[dir].size(), &b3)) ||
@@ -1990,7 +1990,6 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   RC(status_check(g, s));
   std::vector<qdta_stats> st(N);
   CK(cudaMemcpy(st.data(), D.stats_dev, sizeof(qdta_stats) * N, cudaMemcpyDeviceToHost));
-  int worst = QDTA_OK;
   for (int i = 0; i < N; ++i) {
     if (stats) stats[i] = st[i];
   }
@@ -2011,7 +2010,6 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
       CK(cudaMemsetAsync(D.ca.tsum, 0, (size_t)table_n * 16, s));
     }
   }
-  (void)worst;
   return QDTA_OK;
 }
 

@@ -468,8 +468,6 @@ sssp_cell_kernel(int V, int LB, CellDev C, int dir, const int4 *__restrict__ adj
   const int *__restrict__ ent_off = C.ent_off[dir];
   const int *__restrict__ ext_off = C.ext_off[dir];
   const int *__restrict__ ext_node = C.ext_node[dir];
-  const int *__restrict__ dep_off = C.dep_off[dir];
-  const int *__restrict__ dep_cell = C.dep_cell[dir];
   const int *__restrict__ lrev_off = C.lrev_off[dir];
   const unsigned char *__restrict__ nflag = C.node_flags[dir];
   const int *__restrict__ xrev_off = C.xrev_off[dir];
