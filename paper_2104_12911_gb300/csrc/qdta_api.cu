@@ -151,15 +151,6 @@ static int ws_get(qdta_graph *g, const std::string &name, size_t count, T **out)
   return QDTA_OK;
 }
 
-// release a named workspace buffer (a later ws_get allocates it again)
-static void ws_drop(qdta_graph *g, const std::string &name) {
-  auto it = g->ws.find(name);
-  if (it == g->ws.end() || !it->second.p) return;
-  cudaDeviceSynchronize();
-  cudaFree(it->second.p);
-  g->ws.erase(it);
-}
-
 static int status_reset(qdta_graph *g, cudaStream_t s) {
   CK(cudaMemsetAsync(g->status, 0, sizeof(unsigned), s));
   return QDTA_OK;
@@ -770,15 +761,6 @@ extern "C" int qdta_graph_create(const qdta_graph_desc *d, int device, qdta_grap
         }
         gd.rank_tgt[0] = r0; gd.rank_tgt[1] = r1;
         gd.rank_link[0] = l0; gd.rank_link[1] = l1;
-        std::vector<int> rle(4 * (size_t)V, -1);
-        for (int v = 0; v < V; ++v)
-          for (int k = out_off[v]; k < out_off[v + 1]; ++k) rle[4 * (size_t)v + (k - out_off[v])] = out_link[k];
-        int *le = nullptr;
-        if ((rc = upload(g, rle.data(), rle.size(), &le))) {
-          qdta_graph_destroy(g);
-          return rc;
-        }
-        gd.rank_link_ext = le;
         gd.skip_parent = sym && !getenv("QDTA_NO_PARENT_SKIP") ? 1 : 0;
       }
     }
@@ -905,8 +887,7 @@ static int sssp_work(qdta_graph *g, int grid, int R_cap, SsspWork *w) {
 // knows is skipped on the device: its kernels return at once)
 static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots, int R_host,
                     const int *R_dev, int R_cap, int *parent, const int *slot_dev, long long stride,
-                    long long *dist, cudaStream_t s, const int *skip_dev = nullptr, bool profile = true,
-                    unsigned char *parent8 = nullptr) {
+                    long long *dist, cudaStream_t s, const int *skip_dev = nullptr, bool profile = true) {
   SsspWork w;
   const int grid = sssp_grid(g, R_cap);
   RC(sssp_work(g, grid, R_cap, &w));
@@ -929,7 +910,7 @@ static int run_sssp(qdta_graph *g, int direction, const int *q, const int *roots
     else launch_pack_adj(g->d, direction, q, w.adj, s, skip_dev);
     prof_begin(g, s, &pe, 0, R_host);
     launch_sssp(g->d, direction, w.adj, roots, R_host, R_dev, grid, g->sssp_smem, w, parent, slot_dev,
-                stride, dist, g->status, s, skip_dev, g->prof_on ? g->prof_roots : nullptr, parent8);
+                stride, dist, g->status, s, skip_dev, g->prof_on ? g->prof_roots : nullptr);
   }
   prof_end(g, s, &pe);
   g->prof_on = prof_saved;
@@ -1228,11 +1209,6 @@ struct Solver {
   int2 *head_q;
   int *parent;
   long long parent_stride;
-  // trees as rank bytes (the day on rank-keyed layouts): parent8 replaces
-  // parent, and the free-flow trees are ff_parent8
-  bool tree8 = false;
-  unsigned char *parent8 = nullptr;
-  const unsigned char *ff_parent8 = nullptr;
   int ring;
   Ctl *ctl;
   i128 *partials;
@@ -1264,13 +1240,7 @@ static int solver_alloc(Solver &S, const std::string &tag, int ring, bool tape_f
   RC(ws_get(g, tag + ".hq", L, &S.head_q));
   S.parent_stride = (long long)S.R_cap * g->d.V;
   S.ring = ring;
-  if (S.tree8) {
-    S.parent = nullptr;
-    RC(ws_get(g, tag + ".parent8", (size_t)S.parent_stride * ring, &S.parent8));
-  } else {
-    S.parent8 = nullptr;
-    RC(ws_get(g, tag + ".parent", (size_t)S.parent_stride * ring, &S.parent));
-  }
+  RC(ws_get(g, tag + ".parent", (size_t)S.parent_stride * ring, &S.parent));
   RC(ws_get(g, tag + ".ctl", 1, &S.ctl));
   S.sgrid = sweep_grid(g->d);
   RC(ws_get(g, tag + ".partials", (size_t)S.sgrid * NSUM, &S.partials));
@@ -1290,20 +1260,18 @@ static int solver_alloc(Solver &S, const std::string &tag, int ring, bool tape_f
 // g_fx.  gather_ff: the trees are the free-flow ones, copied from S.ff_parent
 static int seg_aon(Solver &S, const int *slot_dev, bool gather_ff = false) {
   qdta_graph *g = S.g;
-  if (gather_ff && S.tree8)
-    launch_gather_rows8(S.ff_parent8, S.ff_rows, g->d.V, S.root_slot, S.parent8, slot_dev, S.parent_stride, S.s);
-  else if (gather_ff)
+  if (gather_ff)
     launch_gather_rows(S.ff_parent, S.ff_rows, g->d.V, S.root_slot, S.parent, slot_dev, S.parent_stride, S.s);
   else
     RC(run_sssp(g, QDTA_TO_ROOT, S.q, S.roots, S.R_host, S.R_dev, S.R_cap, S.parent, slot_dev,
-                S.parent_stride, nullptr, S.s, nullptr, true, S.parent8));
+                S.parent_stride, nullptr, S.s));
   launch_pack_head_q(g->d, S.qt, S.head_q, S.s);
   CK(cudaMemsetAsync(S.g_fx, 0, (size_t)g->d.L * 8, S.s));
   ProfEvent pe;
   prof_begin(g, S.s, &pe, 1, 0);
   launch_load(g->d, S.head_q, S.parent, slot_dev, S.parent_stride, S.root_slot, S.item_roots, S.n_host,
               S.n_dev, S.root_idx, S.src, S.amount, S.dt_q, S.g_fx, nullptr, g->status, S.s, S.carry,
-              S.carry_link, S.parent8);
+              S.carry_link);
   prof_end(g, S.s, &pe);
   return QDTA_OK;
 }
@@ -1318,7 +1286,7 @@ static int seg_init(Solver &S) {
   CK(cudaMemsetAsync(S.f, 0, (size_t)g->d.L * 8, S.s));
   launch_bpr(g->d, S.f, S.dt_h, nullptr, S.q, g->status, S.s, S.so);
   if (S.so) launch_bpr(g->d, S.f, S.dt_h, nullptr, S.qt, g->status, S.s);
-  RC(seg_aon(S, nullptr, S.ff_parent != nullptr || S.ff_parent8 != nullptr));
+  RC(seg_aon(S, nullptr, S.ff_parent != nullptr));
   launch_flow_from_fx(g->d.L, S.g_fx, S.f, S.s);
   launch_tape0(g->d, S.q, S.f, S.tape_q, S.tape_alpha, S.tape_f, S.s);
   return QDTA_OK;
@@ -1774,10 +1742,10 @@ static int day_res_body(Day &D, unsigned long long h, int use_cond) {
     real_batch = !hc->res_skip;
   }
   RC(run_sssp(g, QDTA_TO_ROOT, D.q_work, S.roots, 0, S.R_dev, S.R_cap, S.parent, &S.ctl->res_slot,
-              S.parent_stride, nullptr, s, &S.ctl->res_skip, real_batch, S.parent8));
+              S.parent_stride, nullptr, s, &S.ctl->res_skip, real_batch));
   launch_residual(g->d, D.hq_fin, S.parent, &S.ctl->res_slot, S.parent_stride, D.root_slot, D.zones,
                   D.n_items_dev, D.cap_items, D.it_root, D.it_src, D.it_amt, &S.ctl->w_cur, S.dt_q, D.h_fx,
-                  D.dense, g->status, s, D.it_carry, D.it_link, D.trunc, D.ca, S.parent8);
+                  D.dense, g->status, s, D.it_carry, D.it_link, D.trunc, D.ca);
   launch_res_next(S.ctl, h, use_cond, s);
   return QDTA_OK;
 }
@@ -1965,43 +1933,31 @@ extern "C" int qdta_run_day(qdta_graph *g, const qdta_od *d_orig, int32_t N, dou
   S.carry = D.it_carry;
   S.carry_link = D.it_link;
   RC(ws_get(g, "day.f", L, &S.f));
-  // trees as rank bytes where the queue kernels run on a rank-keyed layout
-  // (a quarter of the HBM, so the ring holds four times the trees);
-  // QDTA_TREE_INT32 keeps int32 link ids
-  S.tree8 = g->sssp_kind == 2 && g->d.rank_link_ext &&
-            sssp_writes_rank_bytes(g->d, QDTA_TO_ROOT, g->sssp_smem) && !getenv("QDTA_TREE_INT32");
-  // the other format's ring and free-flow trees of an earlier day are released
-  ws_drop(g, S.tree8 ? "day.parent" : "day.parent8");
-  ws_drop(g, S.tree8 ? "day.ff_parent" : "day.ff_parent8");
   // parent ring: keep every tree of an interval when memory allows.  The
   // ring this handle already holds counts as available (a later day must
   // not shrink the ring because the previous day's ring is still allocated).
-  const char *ring_name = S.tree8 ? "day.parent8" : "day.parent";
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
   {
-    auto it = g->ws.find(ring_name);
+    auto it = g->ws.find("day.parent");
     if (it != g->ws.end()) free_b += it->second.bytes;
   }
-  const double per_slot = (double)Z * V * (S.tree8 ? 1.0 : 4.0);
+  const double per_slot = (double)Z * V * 4.0;
   // free-flow trees of all zones, once per day (skipped when HBM is short:
   // they cost one ring slot)
   if (!getenv("QDTA_NO_FF_CACHE") && (double)free_b >= 6.0 * per_slot) {
     int *ff = nullptr;
-    unsigned char *ff8 = nullptr;
-    if (S.tree8) RC(ws_get(g, "day.ff_parent8", (size_t)Z * V, &ff8));
-    else RC(ws_get(g, "day.ff_parent", (size_t)Z * V, &ff));
+    RC(ws_get(g, "day.ff_parent", (size_t)Z * V, &ff));
     RC(ws_get(g, "day.f", L, &S.f));
     CK(cudaMemsetAsync(S.f, 0, L * 8, s));
     RC(status_reset(g, s));
     launch_bpr(g->d, S.f, S.dt_h, nullptr, D.q_work, g->status, s);
-    RC(run_sssp(g, QDTA_TO_ROOT, D.q_work, D.zones, Z, nullptr, Z, ff, nullptr, 0, nullptr, s, nullptr, true, ff8));
+    RC(run_sssp(g, QDTA_TO_ROOT, D.q_work, D.zones, Z, nullptr, Z, ff, nullptr, 0, nullptr, s));
     RC(status_check(g, s));
     S.ff_parent = ff;
-    S.ff_parent8 = ff8;
     S.ff_rows = Z;
     CK(cudaMemGetInfo(&free_b, &total_b));
-    auto it = g->ws.find(ring_name);
+    auto it = g->ws.find("day.parent");
     if (it != g->ws.end()) free_b += it->second.bytes;
   }
   long long ring = p->max_iter + 1;

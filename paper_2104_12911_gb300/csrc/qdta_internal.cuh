@@ -262,10 +262,6 @@ struct GraphDev {
   // node, the link of each rank (-1 past the degree)
   const int *rank_tgt[2];          // [L]
   const int *rank_link[2];         // [4 V]
-  // destination trees stored as rank bytes decode through this table: per
-  // external node v, the out-link of each rank (TO_ROOT candidates), -1 past
-  // the degree (nullable)
-  const int *rank_link_ext;        // [4 V]
   int skip_parent;                 // every link has its reverse, lists share one order
   // launch choices of the global-memory SSSP (set at create, changed by
   // qdta_autotune): four-slot adjacency when max_deg <= 4, relaxation mode
@@ -353,25 +349,17 @@ void launch_sssp_cell(const GraphDev &g, const CellDev &c, int direction, const 
                       unsigned *status, cudaStream_t s, const int *skip_dev,
                       unsigned long long *roots_counter);
 int sssp_cell_blocks_per_sm();
-// parent8 (nullable, only where sssp_writes_rank_bytes): trees as one byte
-// per node, the parent's rank (see rank_link_ext), instead of `parent`
 void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *roots,
                  int R_host, const int *R_dev, int grid, bool use_smem, const SsspWork &w,
                  int *parent, const int *parent_slot_dev, long long slot_stride, long long *dist,
                  unsigned *status, cudaStream_t s, const int *skip_dev = nullptr,
-                 unsigned long long *roots_counter = nullptr, unsigned char *parent8 = nullptr);
-// the queue kernels on a rank-keyed layout run for this graph and direction,
-// so trees can be written as rank bytes
-bool sssp_writes_rank_bytes(const GraphDev &g, int direction, bool use_smem);
+                 unsigned long long *roots_counter = nullptr);
 int sssp_max_smem_nodes();
 int sssp_group_size();  // roots per CTA of the global-memory kernel
 // parent rows by root index: row r of src goes to row root_slot[r] of the
 // parent slot (*slot_dev, or 0), skipped when root_slot[r] < 0
 void launch_gather_rows(const int *src, int rows, int V, const int *root_slot, int *parent, const int *slot_dev,
                         long long slot_stride, cudaStream_t s);
-// the same for trees stored as rank bytes
-void launch_gather_rows8(const unsigned char *src, int rows, int V, const int *root_slot, unsigned char *parent,
-                         const int *slot_dev, long long slot_stride, cudaStream_t s);
 // scenario metrics of N intervals' link flows; acc [N*C*16] zeroed by the caller
 void launch_metrics(const GraphDev &g, const double *flows, int N, double dt_h, const double *length_m,
                     const int *link_class, int C, double congested_voc, unsigned long long *acc, double *out,
@@ -409,14 +397,13 @@ struct CarryAcc {
 void launch_pack_head_q(const GraphDev &g, const int *q, int2 *head_q, cudaStream_t s);
 // carry, carry_link [n] (nullable): an item with carry_link >= 0 is on that
 // link having covered the fraction carry / 2^32 of it; it finishes the link,
-// then follows its tree.  parent8 (nullable): the trees as rank bytes
-// (decoded through g.rank_link_ext) instead of `parent`
+// then follows its tree
 void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const int *parent_slot_dev,
                  long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
                  const long long *n_items_dev, const int *root_idx, const int *src,
                  const long long *amount, long long dt_q, unsigned long long *flow_fx, int *stop_out,
                  unsigned *status, cudaStream_t s, const long long *carry = nullptr,
-                 const int *carry_link = nullptr, const unsigned char *parent8 = nullptr);
+                 const int *carry_link = nullptr);
 // trunc 1 (carry): a trip still on a link at the end of the interval goes
 // to the carried table `ca` with the fraction covered; trips stopping at a node
 // go to `dense`
@@ -427,7 +414,7 @@ void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *paren
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
                      unsigned long long *dense, unsigned *status, cudaStream_t s,
                      const long long *carry = nullptr, const int *carry_link = nullptr, int trunc = 0,
-                     CarryAcc ca = CarryAcc{}, const unsigned char *parent8 = nullptr);
+                     CarryAcc ca = CarryAcc{});
 
 // marginal = 1: the system optimum's marginal costs instead of link times
 void launch_bpr(const GraphDev &g, const double *flow, double dt_h, double *cost_s, int *cost_q,

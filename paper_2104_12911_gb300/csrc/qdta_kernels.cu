@@ -895,7 +895,7 @@ template <int THREADS, int ADJ, int RELAX, bool ONEBM, int MINB = 65536 / (THREA
 __global__ void __launch_bounds__(THREADS, MINB)
 sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__restrict__ adj,
                 const int *__restrict__ roots, int R_host, const int *R_dev,
-                unsigned long long *g_state, int *g_queue, int *parent, unsigned char *parent8,
+                unsigned long long *g_state, int *g_queue, int *parent,
                 const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                 const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
                 int max_rounds, int qcap, const int *__restrict__ node_ext, int out_mode,
@@ -930,11 +930,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
   const size_t b = blockIdx.x;
   Key *state = reinterpret_cast<Key *>(g_state) + b * (size_t)V;
   int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;  // overflow beyond qcap entries
-  if (parent_slot_dev) {
-    const long long slot_off = (long long)(*parent_slot_dev) * slot_stride;
-    if (parent8) parent8 += slot_off;
-    else parent += slot_off;
-  }
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
   const Key NOLINK = (Key)((1ull << LB) - 1ull);
   const Dist DMAX = (Dist)(KINF >> LB);
   constexpr int NQ = THREADS / 4;
@@ -1121,10 +1117,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
     if (round > max_rounds)
       for (int i = threadIdx.x; i < NBM * W; i += blockDim.x) smq_smem[i] = 0u;
     // output: parent link (and distance) per external node id, keys reset
-    // parent8 (rank-keyed layouts): one byte per node, the parent's rank among
-    // the node's candidate links, 0xFF for none; else the int32 link id
-    unsigned char *p8row = RANK && parent8 ? parent8 + (long long)r * V : nullptr;
-    int *prow = p8row ? nullptr : parent + (long long)r * V;
+    int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
     bool unreached = false;  // 32-bit keys: a node left at the sentinel asks for the 64-bit redo
     if (out_mode != 0 && node_ext) {
@@ -1152,8 +1145,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
             key[k] = KINF;
           }
           const Key lk = key[k] & NOLINK;
-          if (p8row) p8row[v[k]] = lk == NOLINK ? (unsigned char)0xFF : (unsigned char)lk;
-          else prow[v[k]] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
+          prow[v[k]] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
           if (drow) drow[v[k]] = key[k] == KINF ? LLONG_MAX : (long long)(key[k] >> LB);
         }
       }
@@ -1167,8 +1159,7 @@ sssp_smq_kernel(int V, int LB_link, const int *__restrict__ off, const int4 *__r
           key = KINF;
         }
         const Key lk = key & NOLINK;
-        if (p8row) p8row[v] = lk == NOLINK ? (unsigned char)0xFF : (unsigned char)lk;
-        else prow[v] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
+        prow[v] = lk == NOLINK ? -1 : RANK ? __ldg(&rank_link[4 * u + (int)lk]) : (int)lk;
         if (drow) drow[v] = key == KINF ? LLONG_MAX : (long long)(key >> LB);
       }
       __syncthreads();
@@ -1195,7 +1186,7 @@ template <int THREADS, int NPN>
 __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 64))
 sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__restrict__ adj,
                  const int *__restrict__ roots, int R_host, const int *R_dev,
-                 unsigned long long *g_state, int *g_queue, int *parent, unsigned char *parent8,
+                 unsigned long long *g_state, int *g_queue, int *parent,
                  const int *parent_slot_dev, long long slot_stride, long long *dist, unsigned *status,
                  const int *skip_dev, unsigned long long *roots_counter, const int *__restrict__ node_int,
                  int max_rounds, int qcap, const int *__restrict__ node_ext, int /*out_mode*/,
@@ -1213,11 +1204,7 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
   const size_t b = blockIdx.x;
   unsigned *state = reinterpret_cast<unsigned *>(g_state) + b * (size_t)V;
   int *gq0 = g_queue + b * 2 * (size_t)V, *gq1 = gq0 + V;
-  if (parent_slot_dev) {
-    const long long slot_off = (long long)(*parent_slot_dev) * slot_stride;
-    if (parent8) parent8 += slot_off;
-    else parent += slot_off;
-  }
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
   const int4 *rows = adj;  // node u: slots 0, 1 in rows[2u], slots 2, 3 in rows[2u + 1]
   for (int v = threadIdx.x; v < V; v += THREADS) state[v] = KINF;
   for (int i = threadIdx.x; i < W; i += THREADS) bm[i] = 0u;
@@ -1332,8 +1319,7 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
     // have exact keys, and a node left at the sentinel KINF - 1 (offered
     // only beyond 2^29: distance at or beyond 2^29) sets ST_K32 so the batch
     // is redone with 64-bit keys.
-    unsigned char *p8row = parent8 ? parent8 + (long long)r * V : nullptr;  // rank bytes (see above)
-    int *prow = p8row ? nullptr : parent + (long long)r * V;
+    int *prow = parent + (long long)r * V;
     long long *drow = dist ? dist + (long long)r * V : nullptr;
     bool unreached = false;
     for (int u0 = threadIdx.x; u0 < V; u0 += 4 * THREADS) {
@@ -1355,8 +1341,7 @@ sssp_lane_kernel(int V, int /*LB_link*/, const int * /*off*/, const int4 *__rest
           key[k] = KINF;
         }
         const unsigned lk = key[k] & NOLINK;
-        if (p8row) p8row[v[k]] = lk == NOLINK ? (unsigned char)0xFF : (unsigned char)lk;
-        else prow[v[k]] = lk == NOLINK ? -1 : __ldg(&rank_link[4 * u + (int)lk]);
+        prow[v[k]] = lk == NOLINK ? -1 : __ldg(&rank_link[4 * u + (int)lk]);
         if (drow) drow[v[k]] = key[k] == KINF ? LLONG_MAX : (long long)(key[k] >> 3);
       }
     }
@@ -1500,7 +1485,7 @@ __global__ void k32_redo_flag_kernel(unsigned *status, const int *skip_dev, int 
 }
 
 using SmqKernel = void (*)(int, int, const int *, const int4 *, const int *, int, const int *, unsigned long long *,
-                          int *, int *, unsigned char *, const int *, long long, long long *, unsigned *, const int *,
+                          int *, int *, const int *, long long, long long *, unsigned *, const int *,
                           unsigned long long *, const int *, int, int, const int *, int, const int *, int, RootSched);
 
 template <int THREADS, bool ONEBM>
@@ -1543,16 +1528,11 @@ int sssp_smq_ctas_per_sm(const GraphDev &g, int direction) {
   return n > 0 ? n : 1;
 }
 
-bool sssp_writes_rank_bytes(const GraphDev &g, int direction, bool use_smem) {
-  return !use_smem && sssp_uses_smq(g) && sssp_adj(g, direction) >= 2;
-}
-
 void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *roots, int R_host,
                  const int *R_dev, int grid, bool use_smem, const SsspWork &w, int *parent,
                  const int *parent_slot_dev, long long slot_stride, long long *dist,
                  unsigned *status, cudaStream_t s, const int *skip_dev,
-                 unsigned long long *roots_counter, unsigned char *parent8) {
-  if (parent8 && !sssp_writes_rank_bytes(g, direction, use_smem)) return;  // callers check first
+                 unsigned long long *roots_counter) {
   const int *off = direction == 0 ? g.in_off : g.out_off;
   if (grid <= 0) return;
   if (use_smem) {
@@ -1605,8 +1585,7 @@ void launch_sssp(const GraphDev &g, int direction, const int4 *adj, const int *r
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g.tune_carve);
         COUNT_LAUNCH();
         kern<<<grid, threads, smq, s>>>(g.V, g.LB, perm ? g.perm_off[direction] : off, adj, roots, R_host, R_dev,
-                                        w.state, w.queue, parent, parent8, parent_slot_dev, slot_stride, dist, status,
-                                        skip,
+                                        w.state, w.queue, parent, parent_slot_dev, slot_stride, dist, status, skip,
                                         counters, perm ? g.node_int : nullptr, round_limit(g.V),
                                         kSmqShape[g.tune_shape].qcap, perm ? g.node_ext : nullptr, g.tune_out,
                                         g.rank_link[direction], g.skip_parent, rs);
@@ -1680,17 +1659,6 @@ __device__ __forceinline__ bool finish_carried_link(const int2 *__restrict__ hea
   return true;
 }
 
-// Parent link of node u in a destination tree row: int32 link ids, or (par8
-// set) rank bytes decoded through the external-order rank table
-__device__ __forceinline__ int tree_parent(const int *__restrict__ par, const unsigned char *__restrict__ par8,
-                                           const int *__restrict__ rle, int u) {
-  if (par8) {
-    const unsigned b = par8[u];
-    return b == 0xFFu ? -1 : __ldg(&rle[4 * u + (int)b]);
-  }
-  return par[u];
-}
-
 // One thread per item: walk origin -> root along the destination tree.  A
 // link is loaded iff the elapsed time at its tail is < dt_q; the walk ends
 // at the first node reached at >= dt_q (the stop node) or at the root.  An
@@ -1704,21 +1672,14 @@ __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *_
                             const int *__restrict__ src, const long long *__restrict__ amount,
                             long long dt_q, unsigned long long *flow_fx, int *stop_out,
                             unsigned *status, const long long *__restrict__ carry,
-                            const int *__restrict__ carry_link, const unsigned char *parent8,
-                            const int *__restrict__ rle) {
+                            const int *__restrict__ carry_link) {
   const long long n = n_dev ? *n_dev : n_host;
-  if (parent_slot_dev) {
-    const long long slot_off = (long long)(*parent_slot_dev) * slot_stride;
-    if (parent8) parent8 += slot_off;
-    else parent += slot_off;
-  }
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const int r = root_idx[k];
     const int z = roots[r];
-    const long long row = (long long)(root_slot ? root_slot[r] : r) * V;
-    const int *par = parent8 ? nullptr : parent + row;
-    const unsigned char *par8 = parent8 ? parent8 + row : nullptr;
+    const int *par = parent + (long long)(root_slot ? root_slot[r] : r) * V;
     const unsigned long long amt = (unsigned long long)amount[k];
     int u = src[k];
     long long elapsed = 0;
@@ -1732,7 +1693,7 @@ __global__ void load_kernel(int V, const int2 *__restrict__ head_q, const int *_
     int steps = 0;
     while (u != z) {
       if (elapsed >= dt_q) break;
-      const int e = tree_parent(par, par8, rle, u);
+      const int e = par[u];
       if (e < 0) { atomicOr(status, ST_UNREACH); break; }
       if (amt) atomicAdd(&flow_fx[e], amt);
       const int2 hq = __ldg(&head_q[e]);
@@ -1799,15 +1760,14 @@ void launch_load(const GraphDev &g, const int2 *head_q, const int *parent, const
                  long long slot_stride, const int *root_slot, const int *roots, long long n_items_host,
                  const long long *n_items_dev, const int *root_idx, const int *src,
                  const long long *amount, long long dt_q, unsigned long long *flow_fx, int *stop_out,
-                 unsigned *status, cudaStream_t s, const long long *carry, const int *carry_link,
-                 const unsigned char *parent8) {
+                 unsigned *status, cudaStream_t s, const long long *carry, const int *carry_link) {
   long long n = n_items_dev ? (long long)g.num_sms * 16 * 256 : n_items_host;
   if (n <= 0) return;
   COUNT_LAUNCH();
   load_kernel<<<link_grid(g, n), 256, 0, s>>>(g.V, head_q, parent, parent_slot_dev, slot_stride,
                                               root_slot, roots, n_items_host, n_items_dev, root_idx,
                                               src, amount, dt_q, flow_fx, stop_out, status, carry,
-                                              carry_link, parent8, g.rank_link_ext);
+                                              carry_link);
 }
 
 // unsigned 128-bit accumulation with two 64-bit atomics: the low word's carry
@@ -1872,23 +1832,17 @@ __global__ void residual_kernel(int V, int L, const int2 *__restrict__ head_q_fi
                                 const long long *__restrict__ amount, const double *weight_dev, long long dt_q,
                                 unsigned long long *h_fx, unsigned long long *dense, unsigned *status,
                                 const long long *__restrict__ carry, const int *__restrict__ carry_link,
-                                int trunc, CarryAcc ca, const unsigned char *parent8, const int *__restrict__ rle) {
+                                int trunc, CarryAcc ca) {
   const long long n = *n_dev;
   const double w = *weight_dev;
-  if (parent_slot_dev) {
-    const long long slot_off = (long long)(*parent_slot_dev) * slot_stride;
-    if (parent8) parent8 += slot_off;
-    else parent += slot_off;
-  }
+  if (parent_slot_dev) parent += (long long)(*parent_slot_dev) * slot_stride;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
     const long long amt = __double2ll_rn(mul(__ll2double_rn(amount[k]), w));
     if (amt == 0) continue;
     const int r = root_idx[k];
     const int z = roots[r];
-    const long long row = (long long)root_slot[r] * V;
-    const int *par = parent8 ? nullptr : parent + row;
-    const unsigned char *par8 = parent8 ? parent8 + row : nullptr;
+    const int *par = parent + (long long)root_slot[r] * V;
     int u = src[k];
     long long elapsed = 0, frac = 0;
     int on_link = -1;  // the link holding the trip at the end of the interval
@@ -1903,7 +1857,7 @@ __global__ void residual_kernel(int V, int L, const int2 *__restrict__ head_q_fi
     int steps = 0;
     while (on_link < 0 && u != z) {
       if (elapsed >= dt_q) break;
-      const int e = tree_parent(par, par8, rle, u);
+      const int e = par[u];
       if (e < 0) { atomicOr(status, ST_UNREACH); break; }
       atomicAdd(&h_fx[e], (unsigned long long)amt);
       const int2 hq = __ldg(&head_q_fin[e]);
@@ -1927,12 +1881,12 @@ void launch_residual(const GraphDev &g, const int2 *head_q_fin, const int *paren
                      const int *root_idx, const int *src, const long long *amount,
                      const double *weight_dev, long long dt_q, unsigned long long *h_fx,
                      unsigned long long *dense, unsigned *status, cudaStream_t s, const long long *carry,
-                     const int *carry_link, int trunc, CarryAcc ca, const unsigned char *parent8) {
+                     const int *carry_link, int trunc, CarryAcc ca) {
   if (n_items_cap <= 0) return;
   COUNT_LAUNCH();
   residual_kernel<<<link_grid(g, n_items_cap), 256, 0, s>>>(
       g.V, g.L, head_q_fin, parent, parent_slot_dev, slot_stride, root_slot, roots, n_items_dev, root_idx, src,
-      amount, weight_dev, dt_q, h_fx, dense, status, carry, carry_link, trunc, ca, parent8, g.rank_link_ext);
+      amount, weight_dev, dt_q, h_fx, dense, status, carry, carry_link, trunc, ca);
 }
 
 // ============================================================================
@@ -2852,20 +2806,17 @@ void launch_metrics(const GraphDev &g, const double *flows, int N, double dt_h, 
 
 // copy free-flow tree rows into the rows of the active roots (row r ->
 // root_slot[r]); int4 copies when rows are 16-byte aligned
-// T: int (link ids) or unsigned char (rank bytes)
-template <typename T>
-__global__ void gather_rows_kernel(const T *__restrict__ src, int V, const int *__restrict__ root_slot,
-                                   T *__restrict__ parent, const int *slot_dev, long long slot_stride) {
+__global__ void gather_rows_kernel(const int *__restrict__ src, int V, const int *__restrict__ root_slot,
+                                   int *__restrict__ parent, const int *slot_dev, long long slot_stride) {
   const int r = blockIdx.x;
   const int k = root_slot[r];
   if (k < 0) return;
-  T *dst = parent + (slot_dev ? (long long)(*slot_dev) * slot_stride : 0ll) + (long long)k * V;
-  const T *row = src + (long long)r * V;
-  constexpr int PER = 16 / sizeof(T);  // elements per 16-byte copy
-  if ((V % PER) == 0 && (reinterpret_cast<size_t>(dst) & 15) == 0 && (reinterpret_cast<size_t>(row) & 15) == 0) {
+  int *dst = parent + (slot_dev ? (long long)(*slot_dev) * slot_stride : 0ll) + (long long)k * V;
+  const int *row = src + (long long)r * V;
+  if ((V & 3) == 0 && (reinterpret_cast<size_t>(dst) & 15) == 0 && (reinterpret_cast<size_t>(row) & 15) == 0) {
     const int4 *a = reinterpret_cast<const int4 *>(row);
     int4 *b = reinterpret_cast<int4 *>(dst);
-    for (int i = threadIdx.x; i < V / PER; i += blockDim.x) b[i] = __ldcs(&a[i]);
+    for (int i = threadIdx.x; i < (V >> 2); i += blockDim.x) b[i] = __ldcs(&a[i]);
   } else {
     for (int i = threadIdx.x; i < V; i += blockDim.x) dst[i] = row[i];
   }
@@ -2875,14 +2826,7 @@ void launch_gather_rows(const int *src, int rows, int V, const int *root_slot, i
                         long long slot_stride, cudaStream_t s) {
   if (rows <= 0 || V <= 0) return;
   COUNT_LAUNCH();
-  gather_rows_kernel<int><<<rows, 256, 0, s>>>(src, V, root_slot, parent, slot_dev, slot_stride);
-}
-
-void launch_gather_rows8(const unsigned char *src, int rows, int V, const int *root_slot, unsigned char *parent,
-                         const int *slot_dev, long long slot_stride, cudaStream_t s) {
-  if (rows <= 0 || V <= 0) return;
-  COUNT_LAUNCH();
-  gather_rows_kernel<unsigned char><<<rows, 256, 0, s>>>(src, V, root_slot, parent, slot_dev, slot_stride);
+  gather_rows_kernel<<<rows, 256, 0, s>>>(src, V, root_slot, parent, slot_dev, slot_stride);
 }
 
 __global__ void active_roots_kernel(int R, const long long *n_dev, long long cap, const int *root_idx,

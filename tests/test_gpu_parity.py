@@ -646,20 +646,17 @@ def mid_day():
 
 
 @pytest.mark.parametrize("schedule", ["plain", "graph"])
-@pytest.mark.parametrize("variant", ["default", "ring3", "no_ff_cache", "int32_trees", "int32_trees_ring3"])
+@pytest.mark.parametrize("variant", ["default", "ring3", "no_ff_cache"])
 def test_run_day_large_graph_bit_exact(mid_day, schedule, variant, monkeypatch):
     """Bit-exact h(i) flows, per-interval stats, merged item counts and the
     final residual against the oracle's day, on both schedules; with the tree
     ring capped at 3 slots (the residual pass rebuilds trees 2..K from the
-    taped link times), without the free-flow tree cache, and with the trees
-    kept as int32 link ids instead of rank bytes."""
+    taped link times) and without the free-flow tree cache."""
     net, zones, days, (f_o, st_o, nit_o, rn_o, rc_o) = mid_day
-    if variant.endswith("ring3"):
+    if variant == "ring3":
         monkeypatch.setenv("QDTA_TREE_RING", "3")
     if variant == "no_ff_cache":
         monkeypatch.setenv("QDTA_NO_FF_CACHE", "1")
-    if variant.startswith("int32_trees"):
-        monkeypatch.setenv("QDTA_TREE_INT32", "1")
     g = Q.Graph(net)
     assert "rank32" in Q.qdta_sssp_kernel_name(g)  # the metro day's kernel family
     zt = T(zones, np.int32)
