@@ -350,10 +350,15 @@ int qdta_sssp_batch_noalloc(qdta_graph *g, const int32_t *cost_q, const int32_t 
  * launch shape {512 threads x 2 CTAs per SM, 256 threads x 4 CTAs per SM,
  * whichever fit in shared memory} x adjacency layout {32-bit rank keys,
  * 64-bit rank keys, four-slot, compressed; the first three only when every
- * degree is <= 4}, the 32-bit rank-keyed kernel also with five CTAs per SM
- * and with 5 or 6 frontier nodes in flight per lane group, plus the
- * cell-partitioned kernel.  Offers are applied as "read the neighbour's key,
- * then a non-returning atomicMin" (QDTA_BF_RELAX selects the others).
+ * degree is <= 4}, the 32-bit rank-keyed kernel also in further shapes
+ * (five CTAs per SM with 256 or 192 threads, 5 or 6 frontier nodes in flight
+ * per lane group, one lane per node, an L2 prefetch of key blocks, 288
+ * threads x 4 CTAs), plus the cell-partitioned kernel.  Offers are applied
+ * as "read the neighbour's key, then a non-returning atomicMin"
+ * (QDTA_BF_RELAX selects the others).  Within a batch the resident CTAs take
+ * roots from an atomic counter, longest first by the rounds each root took
+ * in the handle's previous batch (QDTA_BF_DYNAMIC=0, QDTA_BF_LPT=0 turn this
+ * off); the order does not change the results.
  *
  * cost_q [L] int32 and roots [R] int32 are device arrays as for
  * qdta_sssp_batch; parent_scratch is a caller-owned device array of R*V int32
