@@ -958,3 +958,37 @@ def test_day_conserves_trips_on_a_congested_chain(trunc):
     assert int(flows_fx[:, 3].sum()) > 0 and waiting > 0  # trips both arrive and remain
     if trunc == oracle.TRUNC_CARRY:
         assert (link >= 0).any()  # some trips end the day on a link
+
+
+@pytest.mark.parametrize("trunc", [oracle.TRUNC_NODE, oracle.TRUNC_CARRY])
+def test_day_conserves_trips_per_destination_on_a_grid(trunc):
+    """The chain test above on a small grid: every trip goes from one of five
+    zones to a sixth, z, and loads exactly one link into z, on its last step
+    (a trip that reaches z stops there).  With one AON per interval the trips
+    of all intervals therefore equal the loads of z's in-links summed over the
+    intervals plus the residual that has not entered an in-link of z.  One-
+    minute intervals make trips cross several of them."""
+    net = synth.grid_network(8, 3)
+    g = oracle.OracleGraph(net)
+    zones = synth.pick_zones(net, 6, 3)
+    sink = int(zones[0])
+    rng = np.random.default_rng(5)
+    N = 8
+    days = []
+    for i in range(N):
+        others = np.array([z for z in zones if z != sink], np.int32)
+        amt = (rng.integers(0, 30, others.shape[0]).astype(np.int64) << 32) + rng.integers(0, 1 << 32, others.shape[0])
+        days.append(synth.Demand(roots=zones.astype(np.int32), root_idx=np.zeros(others.shape[0], np.int32),
+                                 src=others, amount_fx=amt))
+    p = oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0, truncation=trunc)
+    f, st, nit, rn, rc, res = oracle.run_day(g, zones.astype(np.int32), days, 60.0, p, want_resid=True)
+    assert rc >= 0
+    flows_fx = np.rint(np.asarray(f).reshape(N, -1) * 2.0 ** 32).astype(np.int64)
+    into = np.flatnonzero(np.asarray(net.head) == sink)
+    arrived = int(flows_fx[:, into].sum())
+    root_idx, src, amt, carry, link = res
+    head = np.asarray(net.head)
+    left = int(sum(a for a, l in zip(amt, link) if l < 0 or head[l] != sink))
+    total = sum(int(d.amount_fx.sum()) for d in days)
+    assert total == arrived + left
+    assert arrived > 0 and left > 0
