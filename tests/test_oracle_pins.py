@@ -926,8 +926,9 @@ def test_rel_gap_stop_accepts_zero_and_rounding_level_gaps():
     assert abs(f.sum() - 150.0) < 1e-9 and f[2] == f[3] == 0.0
 
 
+@pytest.mark.parametrize("steps", [(oracle.STEP_MSA, 0), (oracle.STEP_MSA, 5), (oracle.STEP_SWEEP8, 5)])
 @pytest.mark.parametrize("trunc", [oracle.TRUNC_NODE, oracle.TRUNC_CARRY])
-def test_day_conserves_trips_on_a_congested_chain(trunc):
+def test_day_conserves_trips_on_a_congested_chain(trunc, steps):
     """Every trip of a single-destination chain loads the chain's last link
     exactly once, in the interval it enters it, under both truncation rules
     (a link is loaded when entered).  With one AON per interval (no FW steps,
@@ -936,7 +937,10 @@ def test_day_conserves_trips_on_a_congested_chain(trunc):
     intervals + the residual left that has not entered the last link (trips
     waiting at a node, or carried on an earlier link).  The chain is congested
     (link times change with the interval's flows), so carried positions are
-    scaled by changing link times on the way."""
+    scaled by changing link times on the way.  With K FW steps the residual
+    pass splits each item over the K + 1 accepted AONs by their step weights,
+    rounding each share to the nearest fixed-point unit, so the balance holds
+    to within half a unit per share."""
     net = synth.chain_network([400.0, 250.0, 700.0, 150.0], [900.0, 300.0, 1200.0, 500.0])
     g = oracle.OracleGraph(net)
     zones = np.array([4], np.int32)
@@ -947,14 +951,16 @@ def test_day_conserves_trips_on_a_congested_chain(trunc):
         src = np.array([0, 1, 2], np.int32)
         amt = (rng.integers(0, 40, 3).astype(np.int64) << 32) + rng.integers(0, 1 << 32, 3)
         days.append(synth.Demand(roots=zones, root_idx=np.zeros(3, np.int32), src=src, amount_fx=amt))
-    p = oracle.make_params(oracle.STEP_MSA, oracle.STOP_NONE, 0, truncation=trunc)
+    step, K = steps
+    p = oracle.make_params(step, oracle.STOP_NONE, K, truncation=trunc)
     f, st, nit, rn, rc, res = oracle.run_day(g, zones, days, 300.0, p, want_resid=True)
     assert rc >= 0
     flows_fx = np.rint(np.asarray(f).reshape(N, 4) * 2.0 ** 32).astype(np.int64)
     total = sum(int(d.amount_fx.sum()) for d in days)
     root_idx, src, amt, carry, link = res
     waiting = int(sum(a for a, l in zip(amt, link) if l != 3))
-    assert total == int(flows_fx[:, 3].sum()) + waiting
+    shares = sum(int(n) for n in nit) * (K + 1)  # items x accepted AONs, an upper bound on the roundings
+    assert abs(total - (int(flows_fx[:, 3].sum()) + waiting)) <= shares // 2 + 1
     assert int(flows_fx[:, 3].sum()) > 0 and waiting > 0  # trips both arrive and remain
     if trunc == oracle.TRUNC_CARRY:
         assert (link >= 0).any()  # some trips end the day on a link
