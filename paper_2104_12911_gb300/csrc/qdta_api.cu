@@ -986,7 +986,7 @@ bool tune_cache_find(unsigned long long sig, int dir, TuneHit *hit) {
     float ms = 0.f;
     char name[40] = {0};
     if (sscanf(line, "%llx %d %d %d %d %d %d %d %f %39s", &s2, &d2, &k, &a, &r, &b, &sh, &ctas, &ms, name) == 10 &&
-        s2 == sig && d2 == dir && sh >= 0 && sh < 11) {
+        s2 == sig && d2 == dir && sh >= 0 && sh < sssp_smq_shape_count()) {
       hit->cfg = TuneCfg{k, a, r, b, sh};
       hit->entry = qdta_tune_entry{};
       snprintf(hit->entry.kernel, sizeof hit->entry.kernel, "%s", name);
@@ -1047,7 +1047,7 @@ extern "C" int qdta_autotune(qdta_graph *g, const int32_t *cost_q, const int32_t
     const bool ell_ok = g->d.max_deg[direction] <= 4 && g->d.node_int != nullptr;
     const bool rank_ok = ell_ok && g->d.rank_tgt[direction] != nullptr;
     bool any_smq = false;
-    for (int shape = 0; shape < 11; ++shape) {
+    for (int shape = 0; shape < sssp_smq_shape_count(); ++shape) {
       if (!sssp_smq_shape_fits(g->d.V, shape) || getenv("QDTA_BF_NOSMQ")) continue;
       if (shape == 2 && sssp_smq_shape_fits(g->d.V, 0)) continue;  // same block as shape 0, fewer marks
       any_smq = true;

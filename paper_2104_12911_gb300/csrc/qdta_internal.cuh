@@ -365,6 +365,7 @@ void launch_metrics(const GraphDev &g, const double *flows, int N, double dt_h, 
                     const int *link_class, int C, double congested_voc, unsigned long long *acc, double *out,
                     unsigned *status, cudaStream_t s);
 bool sssp_uses_smq(const GraphDev &g);   // global-memory launch keeps queues and marks in shared memory
+int sssp_smq_shape_count();  // launch shapes of the shared-memory-queue kernel
 bool sssp_smq_shape_fits(int V, int shape);
 int sssp_smq_ctas_per_sm(const GraphDev &g, int direction);
 bool sssp_uses_perm(const GraphDev &g);  // global-memory launch reads the locality-ordered adjacency

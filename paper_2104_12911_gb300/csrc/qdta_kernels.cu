@@ -1357,6 +1357,8 @@ size_t sssp_smq_smem_bytes(int V, int shape) {
 }
 
 // does launch shape `shape` fit its CTAs per SM in the 196 KB carveout step
+int sssp_smq_shape_count() { return kSmqShapes; }
+
 bool sssp_smq_shape_fits(int V, int shape) {
   if (shape < 0 || shape >= kSmqShapes) return false;
   return sssp_smq_smem_bytes(V, shape) * kSmqShape[shape].ctas <= 192 * 1024;
