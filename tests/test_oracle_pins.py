@@ -926,7 +926,8 @@ def test_rel_gap_stop_accepts_zero_and_rounding_level_gaps():
     assert abs(f.sum() - 150.0) < 1e-9 and f[2] == f[3] == 0.0
 
 
-@pytest.mark.parametrize("steps", [(oracle.STEP_MSA, 0), (oracle.STEP_MSA, 5), (oracle.STEP_SWEEP8, 5)])
+@pytest.mark.parametrize("steps", [(oracle.STEP_MSA, 0, oracle.OBJ_UE), (oracle.STEP_MSA, 5, oracle.OBJ_UE),
+                                   (oracle.STEP_SWEEP8, 5, oracle.OBJ_UE), (oracle.STEP_SWEEP8, 5, oracle.OBJ_SO)])
 @pytest.mark.parametrize("trunc", [oracle.TRUNC_NODE, oracle.TRUNC_CARRY])
 def test_day_conserves_trips_on_a_congested_chain(trunc, steps):
     """Every trip of a single-destination chain loads the chain's last link
@@ -940,7 +941,8 @@ def test_day_conserves_trips_on_a_congested_chain(trunc, steps):
     scaled by changing link times on the way.  With K FW steps the residual
     pass splits each item over the K + 1 accepted AONs by their step weights,
     rounding each share to the nearest fixed-point unit, so the balance holds
-    to within half a unit per share."""
+    to within half a unit per share, for the system optimum too (routing on
+    marginal costs, loading on travel times)."""
     net = synth.chain_network([400.0, 250.0, 700.0, 150.0], [900.0, 300.0, 1200.0, 500.0])
     g = oracle.OracleGraph(net)
     zones = np.array([4], np.int32)
@@ -951,8 +953,8 @@ def test_day_conserves_trips_on_a_congested_chain(trunc, steps):
         src = np.array([0, 1, 2], np.int32)
         amt = (rng.integers(0, 40, 3).astype(np.int64) << 32) + rng.integers(0, 1 << 32, 3)
         days.append(synth.Demand(roots=zones, root_idx=np.zeros(3, np.int32), src=src, amount_fx=amt))
-    step, K = steps
-    p = oracle.make_params(step, oracle.STOP_NONE, K, truncation=trunc)
+    step, K, objective = steps
+    p = oracle.make_params(step, oracle.STOP_NONE, K, objective=objective, truncation=trunc)
     f, st, nit, rn, rc, res = oracle.run_day(g, zones, days, 300.0, p, want_resid=True)
     assert rc >= 0
     flows_fx = np.rint(np.asarray(f).reshape(N, 4) * 2.0 ** 32).astype(np.int64)
