@@ -99,6 +99,12 @@ def _load():
                 "or_replay": (C.c_int32, [P, P, C.c_double, P, C.c_int32, P, P]),
                 "or_interval_metrics": (C.c_int32, [P, P, C.c_int32, C.c_double, P, P, C.c_int32,
                                                     C.c_double, C.c_double, P]),
+                "or_cch_build": (C.c_int32, [P, P, P]),
+                "or_cch_free": (None, [P]),
+                "or_cch_edges": (C.c_int64, [P]),
+                "or_cch_customize": (C.c_int32, [P, P]),
+                "or_cch_distance": (C.c_int32, [P, C.c_int32, P, P, P]),
+                "or_cch_to_root": (C.c_int32, [P, C.c_int32, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -347,3 +353,72 @@ def dt_quanta(dt_s: float, quantum_s: float) -> int:
     if not np.isfinite(dt_s):
         return np.iinfo(np.int64).max
     return int(np.floor(dt_s / quantum_s + 0.5))
+
+
+class CCH:
+    """Customizable contraction hierarchy over an OracleGraph: build once for
+    a contraction order (a permutation of the nodes), customize per metric,
+    then query exact shortest times (equal to Dijkstra's)."""
+
+    def __init__(self, g: OracleGraph, order):
+        self.g = g
+        self.order = np.ascontiguousarray(order, dtype=np.int32)
+        h = C.c_void_p()
+        rc = _load().or_cch_build(g.ref(), _p(self.order), C.byref(h))
+        if rc:
+            raise RuntimeError(f"or_cch_build failed: {rc}")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.or_cch_free(self.h)
+            self.h = None
+
+    @property
+    def n_edges(self):
+        return int(_load().or_cch_edges(self.h))
+
+    def customize(self, q):
+        q = np.ascontiguousarray(q, dtype=np.int32)
+        rc = _load().or_cch_customize(self.h, _p(q))
+        if rc:
+            raise RuntimeError(f"or_cch_customize failed: {rc}")
+
+    def distance(self, s, t):
+        s = np.ascontiguousarray(s, dtype=np.int32)
+        t = np.ascontiguousarray(t, dtype=np.int32)
+        out = np.empty(max(s.shape[0], 1), dtype=np.int64)
+        rc = _load().or_cch_distance(self.h, s.shape[0], _p(s), _p(t), _p(out))
+        if rc:
+            raise RuntimeError(f"or_cch_distance failed: {rc}")
+        return out[:s.shape[0]]
+
+    def to_root(self, z):
+        out = np.empty(self.g.n_nodes, dtype=np.int64)
+        rc = _load().or_cch_to_root(self.h, int(z), _p(out))
+        if rc:
+            raise RuntimeError(f"or_cch_to_root failed: {rc}")
+        return out
+
+
+def nested_dissection_order(x, y, nodes=None, leaf=64):
+    """Contraction order of a planar-ish graph from node coordinates:
+    recursive bisection at the median of the wider coordinate; each half is
+    ordered first, the cut band (the nodes nearest the median) last.  Any
+    permutation gives the same distances; this one keeps the fill small."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if nodes is None:
+        nodes = np.arange(x.shape[0], dtype=np.int32)
+    if nodes.shape[0] <= leaf:
+        return list(nodes)
+    xs, ys = x[nodes], y[nodes]
+    c = xs if np.ptp(xs) >= np.ptp(ys) else ys
+    order = np.argsort(c, kind="stable")
+    n = nodes.shape[0]
+    band = max(1, int(round(np.sqrt(n))))  # about one grid line
+    lo, hi = (n - band) // 2, (n - band) // 2 + band
+    left, cut, right = nodes[order[:lo]], nodes[order[lo:hi]], nodes[order[hi:]]
+    return (nested_dissection_order(x, y, left, leaf) + nested_dissection_order(x, y, right, leaf)
+            + list(cut))
+

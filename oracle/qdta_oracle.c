@@ -1225,6 +1225,242 @@ int32_t or_replay(const or_graph *g, const or_od *od, double dt_s, const or_para
   return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Customizable contraction hierarchy (Section 5.1 routes with RoutingKit's  */
+/* customizable contraction hierarchies; here an alternative route to the    */
+/* same exact distances as the Dijkstra above).                              */
+/*   Build (metric-independent): nodes are contracted in a given order;      */
+/*   contracting v joins every pair of its neighbours of higher rank, so the */
+/*   upward neighbours of every node form a clique (the graph becomes        */
+/*   chordal).  Each upward edge {x, y}, rank x < rank y, carries two        */
+/*   weights: fw = cost x -> y, bw = cost y -> x.                            */
+/*   Customization (per metric): fw / bw start at the cheapest original link */
+/*   in that direction (infinite if none); then, for v in increasing rank,   */
+/*   every lower triangle {v, u, w} with u, w upward neighbours of v lowers  */
+/*   the edge {u, w} by the path through v.  After it, every shortest path   */
+/*   has an up-down form in the upward graph.                                */
+/*   Queries: s -> t is the minimum over meeting nodes m of an upward search */
+/*   from s (fw) plus an upward search from t (bw, the path read backwards); */
+/*   all v -> z distances take the upward search from z, then one sweep in   */
+/*   decreasing rank: D(v) = min(down(v), min over upward u of fw(v,u)+D(u)).*/
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t V, L;
+  int32_t *rank;    /* [V] */
+  int64_t *up_off;  /* [V + 1] */
+  int32_t *up_node; /* [E] upward neighbours of each node, by increasing rank */
+  int64_t *fw, *bw; /* [E] */
+  int32_t *tail, *head;
+  int64_t E;
+} or_cch;
+
+typedef struct { int32_t *a; int64_t n, cap; } ivec;
+
+static int ivec_push(ivec *v, int32_t x) {
+  if (v->n == v->cap) {
+    int64_t c = v->cap ? 2 * v->cap : 8;
+    int32_t *p = (int32_t *)realloc(v->a, (size_t)c * 4);
+    if (!p) return 1;
+    v->a = p;
+    v->cap = c;
+  }
+  v->a[v->n++] = x;
+  return 0;
+}
+
+static const int32_t *g_rank_for_sort;
+static int cmp_by_rank(const void *a, const void *b) {
+  int32_t x = g_rank_for_sort[*(const int32_t *)a], y = g_rank_for_sort[*(const int32_t *)b];
+  return (x > y) - (x < y);
+}
+
+void or_cch_free(or_cch *c) {
+  if (!c) return;
+  free(c->rank); free(c->up_off); free(c->up_node); free(c->fw); free(c->bw); free(c->tail); free(c->head);
+  free(c);
+}
+
+/* order [V]: the nodes in contraction order (a permutation of 0..V-1) */
+int32_t or_cch_build(const or_graph *g, const int32_t *order, or_cch **out) {
+  const int32_t V = g->n_nodes, L = g->n_links;
+  *out = NULL;
+  or_cch *c = (or_cch *)calloc(1, sizeof(or_cch));
+  ivec *up = (ivec *)calloc((size_t)V + 1, sizeof(ivec));
+  if (!c || !up) { free(c); free(up); return OR_ENOMEM; }
+  c->V = V; c->L = L;
+  c->rank = (int32_t *)malloc((size_t)V * 4 + 4);
+  c->tail = (int32_t *)malloc((size_t)L * 4 + 4);
+  c->head = (int32_t *)malloc((size_t)L * 4 + 4);
+  int rc = OR_OK;
+  if (!c->rank || !c->tail || !c->head) { rc = OR_ENOMEM; goto fail; }
+  for (int32_t v = 0; v < V; v++) c->rank[v] = -1;
+  for (int32_t i = 0; i < V; i++) {
+    if (order[i] < 0 || order[i] >= V || c->rank[order[i]] >= 0) { rc = OR_EINVAL; goto fail; }
+    c->rank[order[i]] = i;
+  }
+  memcpy(c->tail, g->tail, (size_t)L * 4);
+  memcpy(c->head, g->head, (size_t)L * 4);
+  /* undirected neighbours, each stored at its lower end */
+  for (int32_t a = 0; a < L; a++) {
+    int32_t x = g->tail[a], y = g->head[a];
+    if (x == y) continue;
+    if (c->rank[x] > c->rank[y]) { int32_t t = x; x = y; y = t; }
+    if (ivec_push(&up[x], y)) { rc = OR_ENOMEM; goto fail; }
+  }
+  /* contraction in order: sort and deduplicate v's upward neighbours, then
+   * join every pair of them at the lower end of the pair */
+  g_rank_for_sort = c->rank;
+  for (int32_t i = 0; i < V; i++) {
+    const int32_t v = order[i];
+    ivec *U = &up[v];
+    qsort(U->a, (size_t)U->n, 4, cmp_by_rank);
+    int64_t m = 0;
+    for (int64_t k = 0; k < U->n; k++)
+      if (m == 0 || U->a[m - 1] != U->a[k]) U->a[m++] = U->a[k];
+    U->n = m;
+    for (int64_t p = 0; p < m; p++)
+      for (int64_t q = p + 1; q < m; q++)
+        if (ivec_push(&up[U->a[p]], U->a[q])) { rc = OR_ENOMEM; goto fail; }
+  }
+  c->up_off = (int64_t *)malloc(((size_t)V + 1) * 8);
+  if (!c->up_off) { rc = OR_ENOMEM; goto fail; }
+  c->up_off[0] = 0;
+  for (int32_t v = 0; v < V; v++) c->up_off[v + 1] = c->up_off[v] + up[v].n;
+  c->E = c->up_off[V];
+  c->up_node = (int32_t *)malloc((size_t)c->E * 4 + 4);
+  c->fw = (int64_t *)malloc((size_t)c->E * 8 + 8);
+  c->bw = (int64_t *)malloc((size_t)c->E * 8 + 8);
+  if (!c->up_node || !c->fw || !c->bw) { rc = OR_ENOMEM; goto fail; }
+  for (int32_t v = 0; v < V; v++)
+    if (up[v].n) memcpy(c->up_node + c->up_off[v], up[v].a, (size_t)up[v].n * 4);
+  for (int32_t v = 0; v <= V; v++) free(up[v].a);
+  free(up);
+  *out = c;
+  return OR_OK;
+fail:
+  for (int32_t v = 0; v <= V; v++) free(up[v].a);
+  free(up);
+  or_cch_free(c);
+  return rc;
+}
+
+int64_t or_cch_edges(const or_cch *c) { return c->E; }
+
+/* index of the upward edge {x, y} (rank x < rank y), or -1 */
+static int64_t cch_edge(const or_cch *c, int32_t x, int32_t y) {
+  int64_t lo = c->up_off[x], hi = c->up_off[x + 1] - 1;
+  const int32_t ry = c->rank[y];
+  while (lo <= hi) {
+    int64_t mid = (lo + hi) / 2;
+    int32_t r = c->rank[c->up_node[mid]];
+    if (r == ry) return mid;
+    if (r < ry) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+static int64_t add_sat(int64_t a, int64_t b) { return (a == DIST_INF || b == DIST_INF) ? DIST_INF : a + b; }
+
+int32_t or_cch_customize(or_cch *c, const int32_t *q) {
+  for (int64_t e = 0; e < c->E; e++) c->fw[e] = c->bw[e] = DIST_INF;
+  for (int32_t a = 0; a < c->L; a++) {
+    int32_t x = c->tail[a], y = c->head[a];
+    if (x == y) continue;
+    if (q[a] < 1) return OR_EINVAL;
+    if (c->rank[x] < c->rank[y]) {
+      int64_t e = cch_edge(c, x, y);
+      if (q[a] < c->fw[e]) c->fw[e] = q[a];
+    } else {
+      int64_t e = cch_edge(c, y, x);
+      if (q[a] < c->bw[e]) c->bw[e] = q[a];
+    }
+  }
+  /* lower triangles, bottom up: v lowest, then u below w */
+  int32_t *by_rank = (int32_t *)malloc((size_t)c->V * 4 + 4);
+  if (!by_rank) return OR_ENOMEM;
+  for (int32_t v = 0; v < c->V; v++) by_rank[c->rank[v]] = v;
+  for (int32_t r = 0; r < c->V; r++) {
+    const int32_t v = by_rank[r];
+    for (int64_t i = c->up_off[v]; i < c->up_off[v + 1]; i++) {
+      for (int64_t j = i + 1; j < c->up_off[v + 1]; j++) {
+        const int32_t u = c->up_node[i], w = c->up_node[j];  /* rank u < rank w */
+        const int64_t e3 = cch_edge(c, u, w);
+        if (e3 < 0) { free(by_rank); return OR_EINVAL; }  /* not chordal: cannot happen */
+        int64_t t = add_sat(c->bw[i], c->fw[j]);           /* u -> v -> w */
+        if (t < c->fw[e3]) c->fw[e3] = t;
+        t = add_sat(c->bw[j], c->fw[i]);                   /* w -> v -> u */
+        if (t < c->bw[e3]) c->bw[e3] = t;
+      }
+    }
+  }
+  free(by_rank);
+  return OR_OK;
+}
+
+/* Dijkstra over upward edges from s: dist [V] (DIST_INF where not reached);
+ * weights fw (use_bw = 0) or bw (use_bw = 1) */
+static int cch_upward(const or_cch *c, int32_t s, int use_bw, int64_t *dist, heap *h) {
+  for (int32_t v = 0; v < c->V; v++) dist[v] = DIST_INF;
+  h->n = 0;
+  dist[s] = 0;
+  if (heap_push(h, 0, s)) return 1;
+  while (h->n) {
+    hitem it = heap_pop(h);
+    if (it.d != dist[it.v]) continue;
+    for (int64_t e = c->up_off[it.v]; e < c->up_off[it.v + 1]; e++) {
+      const int64_t nd = add_sat(it.d, use_bw ? c->bw[e] : c->fw[e]);
+      const int32_t u = c->up_node[e];
+      if (nd < dist[u]) {
+        dist[u] = nd;
+        if (heap_push(h, nd, u)) return 1;
+      }
+    }
+  }
+  return 0;
+}
+
+/* dist [n] receives the shortest time s[k] -> t[k] (DIST_INF if none) */
+int32_t or_cch_distance(const or_cch *c, int32_t n, const int32_t *s, const int32_t *t, int64_t *dist) {
+  int64_t *df = (int64_t *)malloc((size_t)c->V * 8 + 8), *db = (int64_t *)malloc((size_t)c->V * 8 + 8);
+  heap h = {0};
+  int rc = OR_OK;
+  if (!df || !db) { rc = OR_ENOMEM; goto done; }
+  for (int32_t k = 0; k < n; k++) {
+    if (cch_upward(c, s[k], 0, df, &h) || cch_upward(c, t[k], 1, db, &h)) { rc = OR_ENOMEM; break; }
+    int64_t best = DIST_INF;
+    for (int32_t v = 0; v < c->V; v++) {
+      const int64_t x = add_sat(df[v], db[v]);
+      if (x < best) best = x;
+    }
+    dist[k] = best;
+  }
+done:
+  free(df); free(db); free(h.a);
+  return rc;
+}
+
+/* dist [V]: the shortest time v -> z for every node v (DIST_INF if none) */
+int32_t or_cch_to_root(const or_cch *c, int32_t z, int64_t *dist) {
+  int32_t *by_rank = (int32_t *)malloc((size_t)c->V * 4 + 4);
+  heap h = {0};
+  int rc = OR_OK;
+  if (!by_rank) return OR_ENOMEM;
+  if (cch_upward(c, z, 1, dist, &h)) { rc = OR_ENOMEM; goto done; }  /* down-paths m -> z */
+  for (int32_t v = 0; v < c->V; v++) by_rank[c->rank[v]] = v;
+  for (int32_t r = c->V - 1; r >= 0; r--) {
+    const int32_t v = by_rank[r];
+    for (int64_t e = c->up_off[v]; e < c->up_off[v + 1]; e++) {
+      const int64_t x = add_sat(c->fw[e], dist[c->up_node[e]]);
+      if (x < dist[v]) dist[v] = x;
+    }
+  }
+done:
+  free(by_rank); free(h.a);
+  return rc;
+}
+
 /*
  * Readings of the paper taken here (each also listed in the design notes):
  *  R1 Eq. 2's argmin is garbled; the stop node is the first node on the path

@@ -1000,3 +1000,66 @@ def test_day_conserves_trips_per_destination_on_a_grid(trunc):
     total = sum(int(d.amount_fx.sum()) for d in days)
     assert total == arrived + left
     assert arrived > 0 and left > 0
+
+
+# ----------------------------------------------------------------------------
+# customizable contraction hierarchy (the routing alternative of Section 5.1)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_cch_distances_equal_dijkstra_on_random_graphs_with_ties(seed):
+    """Any contraction order gives exact shortest times: all-pairs P2P
+    queries and every one-to-all sweep against Dijkstra (itself pinned to
+    Floyd-Warshall above), for two orders and two metrics (the hierarchy is
+    built once and customized per metric), with many equal-cost ties.  Two
+    extra nodes hang off the strongly connected graph by one link each, one
+    leaving it (nothing reaches that node) and one entering it (that node
+    reaches nothing): their pairs must stay infinite."""
+    base = synth.random_graph(60, 120, seed, max_q=3)
+    V0 = base.n_nodes
+    tail = np.concatenate([base.tail, [V0, 5]]).astype(np.int32)  # links V0 -> 3 and 5 -> V0 + 1
+    head = np.concatenate([base.head, [3, V0 + 1]]).astype(np.int32)
+    order_l = np.lexsort((head, tail))
+    net = synth.Network(n_nodes=V0 + 2, tail=tail[order_l], head=head[order_l],
+                        fftime_q=np.concatenate([base.fftime_q, [2, 1]]).astype(np.int32)[order_l],
+                        capacity=np.concatenate([base.capacity, [100.0, 100.0]])[order_l],
+                        length_m=np.zeros(tail.shape[0]), link_class=np.zeros(tail.shape[0], np.int8),
+                        x=np.zeros(V0 + 2), y=np.zeros(V0 + 2))
+    g = oracle.OracleGraph(net)
+    rng = np.random.default_rng(seed)
+    V = net.n_nodes
+    roots = np.arange(V, dtype=np.int32)
+    for order in (rng.permutation(V), np.argsort(np.bincount(net.tail, minlength=V), kind="stable")):
+        c = oracle.CCH(g, order)
+        for q in (net.fftime_q, rng.integers(1, 4, net.tail.shape[0])):
+            q = np.asarray(q, np.int32)
+            c.customize(q)
+            _, d = oracle.sssp(g, q, roots)  # d[z][v] = time v -> z
+            assert (d[V0] == np.iinfo(np.int64).max).sum() == V - 1  # only V0 itself reaches V0
+            assert (d[:, V0 + 1] == np.iinfo(np.int64).max).sum() == V - 1  # V0 + 1 reaches only itself
+            s, t = np.meshgrid(np.arange(V, dtype=np.int32), roots)
+            np.testing.assert_array_equal(c.distance(s.ravel(), t.ravel()).reshape(V, V), d)
+            for z in range(V):
+                np.testing.assert_array_equal(c.to_root(z), d[z])
+
+
+def test_cch_one_to_all_on_a_grid_with_a_nested_dissection_order():
+    """The 32 x 32 grid with a coordinate nested-dissection order and
+    congested link times: every node's time to 12 roots, against Dijkstra."""
+    net = synth.grid_network(32, 4)
+    g = oracle.OracleGraph(net)
+    c = oracle.CCH(g, oracle.nested_dissection_order(net.x, net.y))
+    rng = np.random.default_rng(4)
+    q = (net.fftime_q * rng.uniform(1.0, 3.0, net.tail.shape[0])).astype(np.int32)
+    c.customize(q)
+    roots = rng.choice(net.n_nodes, 12, replace=False).astype(np.int32)
+    _, d = oracle.sssp(g, q, roots)
+    for i, z in enumerate(roots):
+        np.testing.assert_array_equal(c.to_root(z), d[i])
+
+
+def test_cch_rejects_an_order_that_is_not_a_permutation():
+    net = synth.grid_network(4, 1)
+    g = oracle.OracleGraph(net)
+    bad = np.zeros(net.n_nodes, np.int32)
+    with pytest.raises(RuntimeError):
+        oracle.CCH(g, bad)
