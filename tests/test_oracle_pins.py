@@ -1044,7 +1044,11 @@ def test_cch_distances_equal_dijkstra_on_random_graphs_with_ties(seed):
 
 def test_cch_one_to_all_on_a_grid_with_a_nested_dissection_order():
     """The 32 x 32 grid with a coordinate nested-dissection order and
-    congested link times: every node's time to 12 roots, against Dijkstra."""
+    congested link times: every node's time to 12 roots, against Dijkstra.
+    The destination trees then follow from those times by the tie rule
+    (each node's parent is the smallest link id among its out-links that
+    begin a shortest path), and equal Dijkstra's trees: a hierarchy can
+    stand in for Bellman-Ford without changing a loaded flow."""
     net = synth.grid_network(32, 4)
     g = oracle.OracleGraph(net)
     c = oracle.CCH(g, oracle.nested_dissection_order(net.x, net.y))
@@ -1052,9 +1056,17 @@ def test_cch_one_to_all_on_a_grid_with_a_nested_dissection_order():
     q = (net.fftime_q * rng.uniform(1.0, 3.0, net.tail.shape[0])).astype(np.int32)
     c.customize(q)
     roots = rng.choice(net.n_nodes, 12, replace=False).astype(np.int32)
-    _, d = oracle.sssp(g, q, roots)
+    par, d = oracle.sssp(g, q, roots)
+    tail, head = np.asarray(net.tail), np.asarray(net.head)
     for i, z in enumerate(roots):
-        np.testing.assert_array_equal(c.to_root(z), d[i])
+        dz = c.to_root(z)
+        np.testing.assert_array_equal(dz, d[i])
+        tight = dz[head] + q.astype(np.int64) == dz[tail]
+        tree = np.full(net.n_nodes, -1, np.int64)
+        for a in np.flatnonzero(tight)[::-1]:  # descending, so the smallest id is written last
+            if tail[a] != z:
+                tree[tail[a]] = a
+        np.testing.assert_array_equal(tree, par[i])
 
 
 def test_cch_rejects_an_order_that_is_not_a_permutation():
