@@ -401,24 +401,34 @@ class CCH:
         return out
 
 
-def nested_dissection_order(x, y, nodes=None, leaf=64):
-    """Contraction order of a planar-ish graph from node coordinates:
-    recursive bisection at the median of the wider coordinate; each half is
-    ordered first, the cut band (the nodes nearest the median) last.  Any
-    permutation gives the same distances; this one keeps the fill small."""
+def nested_dissection_order(x, y, tail, head, nodes=None, leaf=64):
+    """Contraction order from node coordinates by nested dissection: split
+    the nodes at the median of the wider coordinate; the nodes of the lower
+    side that have a link to the upper side form a vertex separator (no link
+    joins the two sides once they are removed).  Each side is ordered first,
+    recursively, the separator last.  Any permutation gives the same
+    distances; this one keeps the fill small."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
+    tail = np.asarray(tail)
+    head = np.asarray(head)
     if nodes is None:
-        nodes = np.arange(x.shape[0], dtype=np.int32)
+        nodes = np.arange(x.shape[0], dtype=np.int64)
     if nodes.shape[0] <= leaf:
-        return list(nodes)
+        return [int(v) for v in nodes]
     xs, ys = x[nodes], y[nodes]
     c = xs if np.ptp(xs) >= np.ptp(ys) else ys
-    order = np.argsort(c, kind="stable")
-    n = nodes.shape[0]
-    band = max(1, int(round(np.sqrt(n))))  # about one grid line
-    lo, hi = (n - band) // 2, (n - band) // 2 + band
-    left, cut, right = nodes[order[:lo]], nodes[order[lo:hi]], nodes[order[hi:]]
-    return (nested_dissection_order(x, y, left, leaf) + nested_dissection_order(x, y, right, leaf)
-            + list(cut))
-
+    o = np.argsort(c, kind="stable")
+    half = nodes.shape[0] // 2
+    lower, upper = nodes[o[:half]], nodes[o[half:]]
+    in_upper = np.zeros(x.shape[0], dtype=bool)
+    in_upper[upper] = True
+    in_lower = np.zeros(x.shape[0], dtype=bool)
+    in_lower[lower] = True
+    crossing = (in_lower[tail] & in_upper[head]) | (in_upper[tail] & in_lower[head])
+    sep = np.zeros(x.shape[0], dtype=bool)
+    sep[np.where(in_lower[tail], tail, head)[crossing]] = True
+    side = lower[~sep[lower]]
+    return (nested_dissection_order(x, y, tail, head, side, leaf)
+            + nested_dissection_order(x, y, tail, head, upper, leaf)
+            + [int(v) for v in lower[sep[lower]]])

@@ -1051,7 +1051,7 @@ def test_cch_one_to_all_on_a_grid_with_a_nested_dissection_order():
     stand in for Bellman-Ford without changing a loaded flow."""
     net = synth.grid_network(32, 4)
     g = oracle.OracleGraph(net)
-    c = oracle.CCH(g, oracle.nested_dissection_order(net.x, net.y))
+    c = oracle.CCH(g, oracle.nested_dissection_order(net.x, net.y, net.tail, net.head))
     rng = np.random.default_rng(4)
     q = (net.fftime_q * rng.uniform(1.0, 3.0, net.tail.shape[0])).astype(np.int32)
     c.customize(q)
